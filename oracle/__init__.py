@@ -1,0 +1,106 @@
+"""FP64 CPU oracle for the spin-orbital CCSD residual (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  It wraps ``cc_oracle.c`` (plain C, explicit loops,
+OpenMP over outer loops) through ctypes and shares no code with the CUDA path.
+
+Parity pins (all in ``tests/test_oracle_pins.py``):
+* residual elements vs a determinant-space brute force of
+  <Phi_l| exp(-T) H_N exp(T) |Phi_0> (Eq. amp), random T, tiny o/v;
+* converged CCSD energy vs FCI for two electrons;
+* first-iteration energy vs the MP2 closed form computed in determinant space;
+* antisymmetry of the residual; lambda-scaling of the energy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cc_oracle.c")
+_LIB = os.path.join(_HERE, "libccoracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile cc_oracle.c into libccoracle.so (gcc -O2 -fopenmp)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_antisym_integrals.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        L.orc_ccsd_residual.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+        L.orc_ccsd_energy.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.orc_ccsd_energy.restype = ctypes.c_double
+        L.orc_diis_coeffs.argtypes = [ctypes.c_int, dp, dp]
+        L.orc_ccsd_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int)]
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def antisym_integrals(o: int, v: int, B: np.ndarray) -> np.ndarray:
+    """Full <pq||rs> tensor [n][n][n][n] from B[L][n][n] (Eq. ham2q)."""
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    n = o + v
+    V = np.empty((n, n, n, n))
+    if lib().orc_antisym_integrals(o, v, B.shape[0], _p(B), _p(V)) != 0:
+        raise MemoryError("oracle integral build failed")
+    return V
+
+
+def ccsd_residual(o, v, eps, V, t1, t2):
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    t1 = np.ascontiguousarray(t1, dtype=np.float64)
+    t2 = np.ascontiguousarray(t2, dtype=np.float64)
+    r1 = np.empty((o, v)); r2 = np.empty((o, o, v, v))
+    if lib().orc_ccsd_residual(o, v, _p(eps), _p(V), _p(t1), _p(t2), _p(r1), _p(r2)) != 0:
+        raise MemoryError("oracle residual failed")
+    return r1, r2
+
+
+def ccsd_energy(o, v, V, t1, t2) -> float:
+    t1 = np.ascontiguousarray(t1, dtype=np.float64)
+    t2 = np.ascontiguousarray(t2, dtype=np.float64)
+    return lib().orc_ccsd_energy(o, v, _p(V), _p(t1), _p(t2))
+
+
+def diis_coeffs(Bmat: np.ndarray):
+    Bmat = np.ascontiguousarray(Bmat, dtype=np.float64)
+    m = Bmat.shape[0]
+    c = np.empty(m)
+    rc = lib().orc_diis_coeffs(m, _p(Bmat), _p(c))
+    return (c if rc == 0 else None)
+
+
+def ccsd_solve(o, v, eps, V, t1=None, t2=None, tol=1e-8, maxiter=100, diis_max=8):
+    """Jacobi + DIIS from (t1, t2) (zeros by default).  Returns a dict."""
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    t1 = np.zeros((o, v)) if t1 is None else np.array(t1, dtype=np.float64, order="C")
+    t2 = np.zeros((o, o, v, v)) if t2 is None else np.array(t2, dtype=np.float64, order="C")
+    en = np.zeros(maxiter); rn = np.zeros(maxiter); it = ctypes.c_int(0)
+    st = lib().orc_ccsd_solve(o, v, _p(eps), _p(V), _p(t1), _p(t2), tol, maxiter, diis_max,
+                              _p(en), _p(rn), ctypes.byref(it))
+    k = it.value
+    return dict(status=st, iters=k, energies=en[:k], rnorms=rn[:k], t1=t1, t2=t2,
+                energy=en[k - 1] if k else float("nan"))

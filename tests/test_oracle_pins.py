@@ -1,0 +1,109 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+* determinant-space brute force of <Phi_l| exp(-T) H_N exp(T) |Phi_0> (Eq. amp)
+  for random, non-converged T at tiny o/v: every residual element and the energy;
+* the converged CCSD energy equals FCI for two electrons (CCSD is exact there);
+* the first Jacobi step from T = 0 gives the MP2 energy, computed here by
+  second-order Moller-Plesset perturbation theory on determinant-space H elements;
+* antisymmetry of R2 in (ij) and (ab); integral symmetries;
+* DIIS coefficients vs the closed form c = B^-1 1 / (1^T B^-1 1);
+* lambda scaling: E(lambda V) = lambda^2 E2 + O(lambda^3), E2 the MP2 energy.
+"""
+import numpy as np
+import pytest
+
+import ccinputs
+import detspace
+import oracle
+
+
+def _system(o, v, seed, scale=6.0):
+    s = ccinputs.make_system(o, v, L=6, seed=seed)
+    return s, s.B * scale
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 1), (3, 4, 2), (3, 5, 3), (4, 4, 4), (2, 6, 5)])
+def test_residual_matches_determinant_brute_force(o, v, seed):
+    s, B = _system(o, v, seed)
+    V = oracle.antisym_integrals(o, v, B)
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=seed, scale1=0.1, scale2=0.1)
+    e_b, r1_b, r2_b = detspace.brute_residual(o, v, s.eps, detspace.antisym_from_B(B), t1, t2)
+    r1, r2 = oracle.ccsd_residual(o, v, s.eps, V, t1, t2)
+    e = oracle.ccsd_energy(o, v, V, t1, t2)
+    scale = max(np.abs(r2_b).max(), np.abs(r1_b).max())
+    assert np.abs(r1 - r1_b).max() < 1e-12 * scale
+    assert np.abs(r2 - r2_b).max() < 1e-12 * scale
+    assert abs(e - e_b) < 1e-13
+
+
+def test_single_t1t1_sign_rule():
+    """One T1*T1 product into R2: the sign of R_ij^ab fixed by 'the line from i ends in a'."""
+    o, v = 2, 2
+    s, B = _system(o, v, 9)
+    V = oracle.antisym_integrals(o, v, B)
+    t1 = np.zeros((o, v)); t1[0, 0] = 0.3; t1[1, 1] = 0.2
+    t2 = np.zeros((o, o, v, v))
+    _, _, r2_b = detspace.brute_residual(o, v, s.eps, V, t1, t2)
+    _, r2 = oracle.ccsd_residual(o, v, s.eps, V, t1, t2)
+    assert np.abs(r2 - r2_b).max() < 1e-14
+    assert np.sign(r2[0, 1, 0, 1]) == np.sign(r2_b[0, 1, 0, 1])
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 4, 11), (2, 6, 12)])
+def test_ccsd_equals_fci_for_two_electrons(o, v, seed):
+    s, B = _system(o, v, seed)
+    V = oracle.antisym_integrals(o, v, B)
+    res = oracle.ccsd_solve(o, v, s.eps, V, tol=1e-12, maxiter=200)
+    assert res["status"] == 0
+    assert abs(res["energy"] - detspace.fci_correlation(o, v, s.eps, V)) < 1e-12
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 4, 21), (3, 4, 22), (3, 5, 23)])
+def test_first_iteration_is_mp2(o, v, seed):
+    s, B = _system(o, v, seed)
+    V = oracle.antisym_integrals(o, v, B)
+    res = oracle.ccsd_solve(o, v, s.eps, V, tol=0.0, maxiter=2)
+    assert res["energies"][0] == 0.0
+    assert abs(res["energies"][1] - detspace.mp2_det_space(o, v, s.eps, V)) < 1e-14
+
+
+def test_residual_antisymmetry_and_integral_symmetry():
+    o, v = 4, 6
+    s, B = _system(o, v, 31)
+    V = oracle.antisym_integrals(o, v, B)
+    assert np.abs(V + V.transpose(1, 0, 2, 3)).max() < 1e-15
+    assert np.abs(V + V.transpose(0, 1, 3, 2)).max() < 1e-15
+    assert np.abs(V - V.transpose(2, 3, 0, 1)).max() < 1e-15
+    assert np.abs(V - detspace.antisym_from_B(B)).max() < 1e-14
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=31, scale1=0.1, scale2=0.1)
+    _, r2 = oracle.ccsd_residual(o, v, s.eps, V, t1, t2)
+    assert np.abs(r2 + r2.transpose(1, 0, 2, 3)).max() < 1e-14
+    assert np.abs(r2 + r2.transpose(0, 1, 3, 2)).max() < 1e-14
+
+
+@pytest.mark.parametrize("m", [2, 3, 5, 8])
+def test_diis_coefficients_closed_form(m):
+    rng = np.random.default_rng(m)
+    E = rng.standard_normal((m, 50))
+    Bm = E @ E.T
+    c = oracle.diis_coeffs(Bm)
+    w = np.linalg.solve(Bm, np.ones(m))
+    ref = w / w.sum()
+    assert np.abs(c - ref).max() < 1e-10
+    assert abs(c.sum() - 1.0) < 1e-13
+
+
+def test_energy_lambda_scaling_leading_order_is_mp2():
+    o, v = 2, 4
+    s, B = _system(o, v, 41)
+    V = oracle.antisym_integrals(o, v, B)
+    e2 = detspace.mp2_det_space(o, v, s.eps, V)
+    lam = np.array([0.02, 0.04, 0.08])
+    es = []
+    for x in lam:
+        res = oracle.ccsd_solve(o, v, s.eps, V * x, tol=1e-13, maxiter=100)
+        es.append(res["energy"])
+    # E(l) = l^2 E2 + l^3 E3 + l^4 E4 + ...: fit the first three coefficients
+    A = np.stack([lam ** 2, lam ** 3, lam ** 4], 1)
+    coef = np.linalg.solve(A, np.array(es))
+    assert abs(coef[0] - e2) < 1e-6 * abs(e2) + 1e-12
