@@ -1,0 +1,221 @@
+/*
+ * cc.h -- C ABI of ccb300: the coupled-cluster amplitude residual, energy and
+ * Jacobi+DIIS iteration on one NVIDIA B300 (sm_103a).
+ *
+ * The method (arxiv 2409.06759, "Generating coupled cluster code for modern
+ * distributed memory tensor software"):
+ *   * Sec. II A, Eq. amp: the CC equations <Phi_l| exp(-T) H_N exp(T) |Phi_0> = 0
+ *     and the energy <Phi_0| exp(-T) H_N exp(T) |Phi_0> = E - E_HF, with
+ *     T1 = sum t_i^a a+_a a_i and T2 = 1/4 sum t_ij^ab a+_a a+_b a_j a_i
+ *     (amplitudes stored unpacked and fully antisymmetric);
+ *   * Sec. II C: the residual is evaluated as an ordered list of binary tensor
+ *     contractions ("Contraction" objects: a factor, permutation operators, at
+ *     most two tensors, an output), written in text as
+ *       OUT[idx] (=|+=|-=) factor P(..) A[idx] * B[idx]
+ *     and executed transpose-transpose-GEMM-transpose (TTGT, Sec. I C);
+ *   * Sec. III B, Eq. ham2q: the Hamiltonian with antisymmetrised integrals
+ *     <pq||rs>; i,j,k,l (and m,n) are occupied, a..h are virtual (Sec. II A).
+ *
+ * Conventions shared by every call:
+ *   * All tensors are caller-owned DEVICE memory, row-major, in the orders
+ *     given below.  The library never frees them.  Scratch comes from the
+ *     caller's workspace argument; the hot path allocates no device memory.
+ *   * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and return without synchronising,
+ *     except cc_solve, which reads |R| back to the host once per iteration.
+ *   * Errors: every call returns a cc_status and never aborts.  On error the
+ *     outputs are unspecified, the inputs are untouched, and cc_last_error()
+ *     returns a message (thread-local, valid until the next call).
+ *   * dtype CC_F64: double.  CC_C128: interleaved complex double (re, im);
+ *     orbital energies stay real.  This build implements CC_F64.
+ */
+#ifndef CCB300_CC_H
+#define CCB300_CC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CC_API __attribute__((visibility("default")))
+#else
+#define CC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CC_OK = 0,
+    CC_ERR_INVALID_ARG = 1,   /* NULL pointer, bad size or option */
+    CC_ERR_PARSE = 2,         /* contraction text does not parse */
+    CC_ERR_SHAPE = 3,         /* index spaces / extents inconsistent */
+    CC_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement */
+    CC_ERR_OOM = 5,           /* host allocation failed */
+    CC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    CC_ERR_NOT_CONVERGED = 7, /* cc_solve: maxiter reached or divergence */
+    CC_ERR_TIMEOUT = 8,       /* a bounded device wait expired */
+    CC_ERR_WORKSPACE = 9      /* workspace too small or misaligned */
+} cc_status;
+
+typedef enum { CC_F64 = 0, CC_C128 = 1 } cc_dtype;
+
+/* Arithmetic of the bulk contractions.
+ *   CC_PREC_FP64:   every GEMM in FP64 (SIMT DFMA).
+ *   CC_PREC_BF16X3: each FP64 operand split into bf16 hi + lo planes, products
+ *                   hi*hi + hi*lo + lo*hi on tcgen05 tensor cores with FP32
+ *                   accumulation in TMEM, recombined into FP64 outputs.
+ *   CC_PREC_BF16X6: three planes (hi, mid, lo), six products.
+ * Contractions below 4e9 flops stay in FP64 on every precision. */
+typedef enum { CC_PREC_FP64 = 0, CC_PREC_BF16X3 = 2, CC_PREC_BF16X6 = 3 } cc_precision;
+
+typedef struct cc_plan_s *cc_plan;
+
+/* Antisymmetrised integrals <pq||rs> (Eq. ham2q) in six canonical blocks, each
+ * dense [p][q][r][s] with the spaces in its name (o = occupied, v = virtual),
+ * every element stored (no permutational packing).  Any other space pattern
+ * is read from these through <pq||rs> = -<qp||rs> = -<pq||sr> and
+ * <rs||pq> = conj(<pq||rs>).  f_occ[o], f_vir[v]: the diagonal Fock matrix
+ * (orbital energies, always double). */
+typedef struct {
+    const double *f_occ;
+    const double *f_vir;
+    const void *oooo;   /* [o][o][o][o] */
+    const void *ooov;   /* [o][o][o][v] */
+    const void *oovv;   /* [o][o][v][v] */
+    const void *ovov;   /* [o][v][o][v] */
+    const void *ovvv;   /* [o][v][v][v] */
+    const void *vvvv;   /* [v][v][v][v] */
+} cc_integrals;
+
+/* Cluster amplitudes: t1[i][a], t2[i][j][a][b], t3[i][j][k][a][b][c] (NULL when
+ * the plan has no triples).  Antisymmetric in occupied and in virtual indices. */
+typedef struct {
+    void *t1;
+    void *t2;
+    void *t3;
+} cc_amps;
+
+/* Residuals R = <Phi_l|Hbar|Phi_0>, same layouts as the amplitudes. */
+typedef struct {
+    void *r1;
+    void *r2;
+    void *r3;
+} cc_resid;
+
+typedef struct {
+    int struct_size;      /* sizeof(cc_plan_opts) */
+    int verbose;          /* 1: print the plan to stderr at creation */
+    int fuse_permutes;    /* reserved, 0 */
+} cc_plan_opts;
+
+/* cc_plan_create -- parse a contraction list and plan its execution.
+ *   text: one statement per line, '#' starts a comment:
+ *       OUT[idx]..  (=|+=|-=)  [factor] [P(pq)|P(p/qr)]...  A[idx].. [* B[idx]..]
+ *     Index letters i..n (or h1, h2, ...) are occupied, a..h (or p1, p2, ...)
+ *     virtual.  Reserved tensors: T1 T2 T3 (amplitudes; occupied indices are
+ *     matched to the occupied slots and virtual to the virtual slots, so
+ *     t[ab][ij] and T2[ijab] name the same tensor), R1 R2 R3 (residual
+ *     outputs, same rule), V (integrals, <pq||rs> = V[pq][rs]).  Any other name
+ *     is an intermediate; its first statement must be '=' and fixes its index
+ *     order (storage order).  P(pq) = 1 - (p<->q); P(p/qr) = 1 - (p<->q) - (p<->r).
+ *     The list must not contain the diagonal Fock terms: cc_residual adds
+ *     -D*t itself (D_i^a = f_ii - f_aa, D_ij^ab = f_ii + f_jj - f_aa - f_bb).
+ *   o, v: occupied / virtual extents (>= 1).
+ *   opts: NULL for defaults.
+ *   out: receives the plan (host object; creating it touches no GPU).
+ * Errors: CC_ERR_PARSE / CC_ERR_SHAPE with the line number in cc_last_error(). */
+CC_API cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_precision precision,
+                                const cc_plan_opts *opts, cc_plan *out);
+
+/* Device workspace that cc_residual needs (bytes, 256-byte aligned base). */
+CC_API cc_status cc_plan_workspace_bytes(cc_plan plan, size_t *bytes);
+
+/* Writes a JSON description of the planned steps (permutes, GEMMs with
+ * M,N,K and flops, epilogues) into buf (NUL-terminated, truncated at len);
+ * *needed receives the full length + 1.  Host only. */
+CC_API cc_status cc_plan_describe(cc_plan plan, char *buf, size_t len, size_t *needed);
+
+/* Total dense GEMM flops of one residual evaluation (2*M*N*K summed). */
+CC_API cc_status cc_plan_flops(cc_plan plan, double *flops);
+
+CC_API cc_status cc_plan_destroy(cc_plan plan);
+
+/* cc_residual -- evaluate R1, R2 (, R3) for the given amplitudes.
+ *   ints, amps: inputs (device, unchanged).  res: outputs (device), fully
+ *   overwritten.  ws: device workspace of at least cc_plan_workspace_bytes.
+ * Ownership: nothing is retained after the call returns. */
+CC_API cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res,
+                             void *ws, size_t ws_bytes, void *stream);
+
+/* cc_energy -- E_CC - E_ref = 1/4 sum <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b
+ * (f_ia = 0).  e_dev: device double[2] receiving (Re E, Im E).  Uses the first
+ * 8 KiB of ws as scratch. */
+CC_API cc_status cc_energy(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, double *e_dev,
+                           void *ws, size_t ws_bytes, void *stream);
+
+typedef struct {
+    int struct_size;          /* sizeof(cc_solve_opts) */
+    int max_iter;             /* iterations of this call (default 100) */
+    double tol;               /* stop when |R|_2 < tol (default 1e-8); 0 = never */
+    int diis_max;             /* stored vectors (default 8, 0 = plain Jacobi) */
+    int resume;               /* 1: continue the DIIS history kept in ws */
+    cc_plan refine_plan;      /* optional FP64 plan used after the switch */
+    double switch_tol;        /* switch to refine_plan when |R| < switch_tol */
+    int verbose;              /* 1: one line per iteration on stderr */
+} cc_solve_opts;
+
+typedef struct {
+    int iterations;           /* iterations done by this call */
+    int converged;            /* 1 when |R| < tol */
+    int switched_at;          /* iteration index of the switch to refine_plan, -1 if none */
+    double energy;            /* E(x_k) of the last evaluated iterate */
+    double rnorm;             /* |R(x_k)|_2 of the last evaluated iterate */
+    double *energies;         /* optional host array [max_iter] (NULL = skip) */
+    double *rnorms;           /* optional host array [max_iter] (NULL = skip) */
+} cc_solve_report;
+
+/* Workspace of cc_solve: cc_plan_workspace_bytes plus the DIIS history and
+ * residual buffers (and the refine plan's workspace when given). */
+CC_API cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opts, size_t *bytes);
+
+/* cc_solve -- Jacobi + DIIS on x = (t1, t2[, t3]).  Iteration k evaluates
+ * R_k = R(x_k), E_k = E(x_k) and |R_k|_2 (Frobenius norm over the full stored
+ * residual arrays) and stops when |R_k| < tol; otherwise x'_{k+1} = x_k + R_k/D,
+ * e_k = R_k/D, the last diis_max pairs (x', e) are kept and, once two are
+ * stored, x_{k+1} = sum_l c_l x'_l with [B 1; 1^T 0][c; lambda] = [0; 1],
+ * B_kl = <e_k|e_l>, solved in FP64 on the device (B scaled by 1/max diag,
+ * partial pivoting, the oldest vector dropped while a pivot is below 1e-14).
+ *   amps: in = start (zeros give MP2 at k = 1); out = the converged x_k, or,
+ *   when max_iter ends the call, the next iterate x_{k+1} (resume = 1 continues
+ *   from it with the DIIS history kept in ws).
+ * With refine_plan, iterations run on `plan` until |R| < max(switch_tol, tol)
+ * or |R| stops improving for three iterations, then on refine_plan (DIIS
+ * restarted) until convergence.
+ * Returns CC_OK when converged, CC_ERR_NOT_CONVERGED when max_iter is reached
+ * or |R| stops being finite or grows 1e3 times above its best value. */
+CC_API cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const cc_solve_opts *opts,
+                          cc_solve_report *report, void *ws, size_t ws_bytes, void *stream);
+
+/* Integral construction (setup step):  (pq|rs) = sum_L B[L][p][q] B[L][r][s]
+ * and <pq||rs> = (pr|qs) - (ps|qr) for the six canonical blocks (Eq. ham2q).
+ *   B: device [L][n][n] (n = o + v, occupied first), double.
+ *   blocks: device outputs (NULL skips a block), sizes from
+ *   cc_integral_block_elems (elements).
+ *   ws: device workspace of cc_build_integrals_workspace_bytes. */
+CC_API cc_status cc_integral_block_elems(int o, int v, size_t elems[6]);
+CC_API cc_status cc_build_integrals_workspace_bytes(int o, int v, int L, cc_dtype dtype, size_t *bytes);
+CC_API cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B, void *oooo, void *ooov,
+                                    void *oovv, void *ovov, void *ovvv, void *vvvv, void *ws, size_t ws_bytes,
+                                    void *stream);
+
+CC_API const char *cc_status_string(cc_status s);
+CC_API const char *cc_last_error(void);
+
+/* Library version and the device architecture it was built for. */
+CC_API const char *cc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCB300_CC_H */

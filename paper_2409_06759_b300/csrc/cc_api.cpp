@@ -1,0 +1,543 @@
+// cc_api.cpp -- the C ABI of include/cc.h: plan objects, the residual
+// executor, energy, the Jacobi+DIIS solver and the integral builder.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cc.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace ccb;
+
+namespace {
+
+thread_local std::string g_err;
+
+cc_status fail(cc_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CC_CUDA(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return fail(CC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct SolverState {
+    int nstored = 0;
+    int order[16] = {0};        // history slots, oldest first
+    int pending_m = 0;          // m passed to the last device DIIS solve (0 = none)
+    int iter = 0;
+    double best = INFINITY;
+    int phase = 0;              // 0: plan, 1: refine plan
+    int stall = 0;
+};
+
+}  // namespace
+
+struct cc_plan_s {
+    Plan plan;
+    bool cache_filled = false;  // static split planes valid (inside one cc_solve call)
+    SolverState solver;
+};
+
+namespace {
+
+const void *block_ptr(const cc_integrals *I, int b) {
+    const void *p[6] = {I->oooo, I->ooov, I->oovv, I->ovov, I->ovvv, I->vvvv};
+    return p[b];
+}
+
+double *resolve(const BufRef &r, const cc_integrals *I, const cc_amps *A, const cc_resid *R, char *ws) {
+    switch (r.where) {
+        case BufRef::AMP: return (double *)(r.slot == 1 ? A->t1 : r.slot == 2 ? A->t2 : A->t3);
+        case BufRef::RES: return (double *)(r.slot == 1 ? R->r1 : r.slot == 2 ? R->r2 : R->r3);
+        case BufRef::INTEG: return (double *)block_ptr(I, r.slot);
+        case BufRef::WS: return (double *)(ws + r.off);
+        default: return nullptr;
+    }
+}
+
+bool aligned256(const void *p) { return ((uintptr_t)p & 255) == 0; }
+
+cc_status check_inputs(const Plan &P, const cc_integrals *I, const cc_amps *A, const cc_resid *R, void *ws,
+                       size_t wsb) {
+    if (!I || !A || !R) return fail(CC_ERR_INVALID_ARG, "NULL integrals, amplitudes or residual struct");
+    if (!I->f_occ || !I->f_vir) return fail(CC_ERR_INVALID_ARG, "NULL orbital energies");
+    for (auto &t : P.tensors) {
+        if (t.kind == TKind::INTEGRAL) {
+            if (!block_ptr(I, t.slot))
+                return fail(CC_ERR_INVALID_ARG, "integral block " + t.name + " is NULL but the list uses it");
+        } else if (t.kind == TKind::AMP) {
+            void *p = t.slot == 1 ? A->t1 : t.slot == 2 ? A->t2 : A->t3;
+            if (!p) return fail(CC_ERR_INVALID_ARG, "amplitude " + t.name + " is NULL but the list uses it");
+        } else if (t.kind == TKind::RES) {
+            void *p = t.slot == 1 ? R->r1 : t.slot == 2 ? R->r2 : R->r3;
+            if (!p) return fail(CC_ERR_INVALID_ARG, "residual " + t.name + " is NULL but the list writes it");
+        }
+    }
+    if ((int64_t)wsb < P.ws_bytes)
+        return fail(CC_ERR_WORKSPACE, "workspace too small: need " + std::to_string(P.ws_bytes) + " bytes");
+    if (!ws || !aligned256(ws)) return fail(CC_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
+    return CC_OK;
+}
+
+cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, const cc_resid *R, void *ws,
+                       size_t wsb, cudaStream_t s, bool use_cache) {
+    const Plan &P = pl->plan;
+    cc_status st = check_inputs(P, I, A, R, ws, wsb);
+    if (st != CC_OK) return st;
+    char *w = (char *)ws;
+    if (!use_cache) pl->cache_filled = false;
+    for (const Step &stp : P.steps) {
+        switch (stp.kind) {
+            case StepKind::ZERO:
+                CC_CUDA(launch_zero(resolve(stp.out, I, A, R, w), stp.zero_elems, s));
+                break;
+            case StepKind::ACCUM:
+                CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s));
+                break;
+            case StepKind::GEMM:
+                if (!stp.mixed) {
+                    CC_CUDA(launch_gemm_f64(stp.gemm, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
+                                            resolve(stp.out, I, A, R, w), s));
+                } else {
+                    void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
+                    if (!(stp.a_static && pl->cache_filled))
+                        CC_CUDA(launch_split_bf16(stp.split_a, resolve(stp.a, I, A, R, w), pa, s));
+                    if (!(stp.b_static && pl->cache_filled))
+                        CC_CUDA(launch_split_bf16(stp.split_b, resolve(stp.b, I, A, R, w), pb, s));
+                    CC_CUDA(launch_tc_gemm(stp.tc, pa, pb, resolve(stp.out, I, A, R, w), (int *)(w + P.flags_off), s));
+                }
+                break;
+        }
+    }
+    if (use_cache) pl->cache_filled = true;
+    // R -= D * t for every residual the list writes
+    for (int l = 1; l <= 3; l++) {
+        if (!P.res_used[l]) continue;
+        const double *t = (const double *)(l == 1 ? A->t1 : l == 2 ? A->t2 : A->t3);
+        double *r = (double *)(l == 1 ? R->r1 : l == 2 ? R->r2 : R->r3);
+        if (t) CC_CUDA(launch_denom_sub(l, P.o, P.v, I->f_occ, I->f_vir, t, r, s));
+    }
+    return CC_OK;
+}
+
+int64_t amp_count(int rank, int o, int v) {
+    int64_t n = 1;
+    for (int k = 0; k < rank; k++) n *= (int64_t)o * v;
+    return n;
+}
+
+constexpr int64_t kAlign = 256;
+int64_t al(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// solver region layout (bytes, relative to its start)
+struct SolverLayout {
+    int64_t n[4] = {0, 0, 0, 0};    // elements per rank (1..3)
+    int64_t nx = 0;                 // elements of x = concatenation of the ranks in use
+    int64_t r_off[4] = {0, 0, 0, 0};
+    int64_t hist_x = 0, hist_e = 0; // diis_max vectors of nx each
+    int64_t gram = 0, coef = 0, used = 0, scal = 0, partials = 0;
+    int64_t bytes = 0;
+    int diis = 0;
+};
+
+SolverLayout solver_layout(const Plan &P, int diis_max) {
+    SolverLayout L;
+    int64_t off = 0;
+    for (int l = 1; l <= 3; l++) {
+        if (!P.res_used[l]) continue;
+        L.n[l] = amp_count(l, P.o, P.v);
+        L.nx += L.n[l];
+        L.r_off[l] = off;
+        off += al(L.n[l] * 8);
+    }
+    L.diis = std::max(diis_max, 1);
+    L.hist_x = off;
+    off += al((int64_t)L.diis * L.nx * 8);
+    L.hist_e = off;
+    off += al((int64_t)L.diis * L.nx * 8);
+    L.gram = off; off += al(256 * 8);
+    L.coef = off; off += al(16 * 8);
+    L.used = off; off += al(16);
+    L.scal = off; off += al(8 * 8);
+    L.partials = off; off += al((int64_t)20 * kRedBlocks * 8);
+    L.bytes = off;
+    return L;
+}
+
+// scal[0] = E, scal[1..] = |R_l|^2 for the residual ranks in use
+cc_status reduce_energy_norm(const Plan &P, const cc_integrals *I, const cc_amps *A, double *const r[4],
+                             const int64_t n[4], double *partials, double *scal, cudaStream_t s) {
+    CC_CUDA(launch_energy_partials(P.o, P.v, (const double *)I->oovv, (const double *)A->t1, (const double *)A->t2,
+                                   partials, s));
+    int cnt = 1;
+    for (int l = 1; l <= 3; l++) {
+        if (!r[l]) continue;
+        CC_CUDA(launch_dot_partials(r[l], r[l], n[l], partials + (int64_t)cnt * kRedBlocks, s));
+        cnt++;
+    }
+    CC_CUDA(launch_reduce_partials(partials, cnt, scal, s));
+    return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cc_status_string(cc_status s) {
+    switch (s) {
+        case CC_OK: return "ok";
+        case CC_ERR_INVALID_ARG: return "invalid argument";
+        case CC_ERR_PARSE: return "parse error";
+        case CC_ERR_SHAPE: return "shape error";
+        case CC_ERR_UNSUPPORTED: return "unsupported";
+        case CC_ERR_OOM: return "out of memory";
+        case CC_ERR_CUDA: return "CUDA error";
+        case CC_ERR_NOT_CONVERGED: return "not converged";
+        case CC_ERR_TIMEOUT: return "device wait timed out";
+        case CC_ERR_WORKSPACE: return "workspace error";
+    }
+    return "unknown status";
+}
+
+const char *cc_last_error(void) { return g_err.c_str(); }
+
+const char *cc_version(void) { return "ccb300 0.1 (sm_103a)"; }
+
+cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_precision precision,
+                         const cc_plan_opts *opts, cc_plan *out) {
+    if (!text || !out) return fail(CC_ERR_INVALID_ARG, "NULL text or output handle");
+    if (o < 1 || v < 1) return fail(CC_ERR_INVALID_ARG, "o and v must be >= 1");
+    if (dtype != CC_F64) return fail(CC_ERR_UNSUPPORTED, "only CC_F64 is implemented in this build");
+    const int prec = (int)precision;
+    const int base = prec >= 100 ? prec - 100 : prec;
+    if (base != CC_PREC_FP64 && base != CC_PREC_BF16X3 && base != CC_PREC_BF16X6)
+        return fail(CC_ERR_INVALID_ARG, "unknown precision");
+    cc_plan_s *pl = new (std::nothrow) cc_plan_s();
+    if (!pl) return fail(CC_ERR_OOM, "plan allocation failed");
+    std::string err;
+    if (!build_plan(text, o, v, (int)dtype, prec, pl->plan, err)) {
+        delete pl;
+        return fail(err.find("index spaces") != std::string::npos ? CC_ERR_SHAPE : CC_ERR_PARSE, err);
+    }
+    if (opts && opts->struct_size >= (int)(2 * sizeof(int)) && opts->verbose) {
+        pl->plan.verbose = 1;
+        std::fprintf(stderr, "%s\n", describe_plan(pl->plan).c_str());
+    }
+    *out = pl;
+    return CC_OK;
+}
+
+cc_status cc_plan_workspace_bytes(cc_plan plan, size_t *bytes) {
+    if (!plan || !bytes) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    *bytes = (size_t)plan->plan.ws_bytes;
+    return CC_OK;
+}
+
+cc_status cc_plan_describe(cc_plan plan, char *buf, size_t len, size_t *needed) {
+    if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
+    std::string d = describe_plan(plan->plan);
+    if (needed) *needed = d.size() + 1;
+    if (buf && len) {
+        size_t n = std::min(len - 1, d.size());
+        std::memcpy(buf, d.data(), n);
+        buf[n] = 0;
+    }
+    return CC_OK;
+}
+
+cc_status cc_plan_flops(cc_plan plan, double *flops) {
+    if (!plan || !flops) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    *flops = plan->plan.flops;
+    return CC_OK;
+}
+
+cc_status cc_plan_destroy(cc_plan plan) {
+    delete plan;
+    return CC_OK;
+}
+
+cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res, void *ws,
+                      size_t ws_bytes, void *stream) {
+    if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
+    return run_residual(plan, ints, amps, res, ws, ws_bytes, (cudaStream_t)stream, false);
+}
+
+cc_status cc_energy(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, double *e_dev, void *ws,
+                    size_t ws_bytes, void *stream) {
+    if (!plan || !ints || !amps || !e_dev) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    if (!ints->oovv || !amps->t2) return fail(CC_ERR_INVALID_ARG, "energy needs the oovv block and t2");
+    if (!ws || ws_bytes < (size_t)kRedBlocks * 8 || !aligned256(ws))
+        return fail(CC_ERR_WORKSPACE, "energy needs 8 KiB of 256-byte aligned workspace");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partials = (double *)ws;
+    CC_CUDA(launch_energy_partials(plan->plan.o, plan->plan.v, (const double *)ints->oovv, (const double *)amps->t1,
+                                   (const double *)amps->t2, partials, s));
+    CC_CUDA(launch_reduce_partials(partials, 1, e_dev, s));
+    CC_CUDA(cudaMemsetAsync(e_dev + 1, 0, sizeof(double), s));
+    return CC_OK;
+}
+
+cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opts, size_t *bytes) {
+    if (!plan || !bytes) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    int diis = opts ? opts->diis_max : 8;
+    if (diis < 0 || diis > 16) return fail(CC_ERR_INVALID_ARG, "diis_max must be in [0, 16]");
+    int64_t pw = plan->plan.ws_bytes;
+    if (opts && opts->refine_plan) pw = std::max(pw, opts->refine_plan->plan.ws_bytes);
+    *bytes = (size_t)(al(pw) + solver_layout(plan->plan, diis).bytes);
+    return CC_OK;
+}
+
+cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const cc_solve_opts *opts,
+                   cc_solve_report *report, void *ws, size_t ws_bytes, void *stream) {
+    if (!plan || !ints || !amps) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    cc_solve_opts o{};
+    o.struct_size = sizeof(o);
+    o.max_iter = 100;
+    o.tol = 1e-8;
+    o.diis_max = 8;
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || o.diis_max < 0 || o.diis_max > 16) return fail(CC_ERR_INVALID_ARG, "bad solve options");
+    cc_plan refine = o.refine_plan;
+    if (refine && (refine->plan.o != plan->plan.o || refine->plan.v != plan->plan.v))
+        return fail(CC_ERR_INVALID_ARG, "refine plan has different o/v");
+    const Plan &P = plan->plan;
+    if (!P.res_used[2]) return fail(CC_ERR_INVALID_ARG, "cc_solve needs a list that writes R2");
+    if (refine) {
+        for (int l = 1; l <= 3; l++)
+            if (refine->plan.res_used[l] != P.res_used[l])
+                return fail(CC_ERR_INVALID_ARG, "refine plan writes different residuals");
+    }
+    size_t need = 0;
+    cc_status st = cc_solve_workspace_bytes(plan, &o, &need);
+    if (st != CC_OK) return st;
+    if (ws_bytes < need || !ws || !aligned256(ws))
+        return fail(CC_ERR_WORKSPACE, "solve workspace too small: need " + std::to_string(need));
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t pw = P.ws_bytes;
+    if (refine) pw = std::max(pw, refine->plan.ws_bytes);
+    char *pws = (char *)ws;
+    char *sreg = (char *)ws + al(pw);
+    SolverLayout L = solver_layout(P, o.diis_max);
+    const int o_ = P.o, v_ = P.v;
+    double *r[4] = {nullptr, nullptr, nullptr, nullptr};
+    double *t[4] = {nullptr, (double *)amps->t1, (double *)amps->t2, (double *)amps->t3};
+    for (int l = 1; l <= 3; l++)
+        if (P.res_used[l]) {
+            r[l] = (double *)(sreg + L.r_off[l]);
+            if (!t[l]) return fail(CC_ERR_INVALID_ARG, "amplitude buffer missing for a residual the list writes");
+        }
+    cc_resid R{r[1], r[2], r[3]};
+    double *hx = (double *)(sreg + L.hist_x), *he = (double *)(sreg + L.hist_e);
+    double *gram = (double *)(sreg + L.gram), *coef = (double *)(sreg + L.coef);
+    int *used_dev = (int *)(sreg + L.used);
+    double *scal = (double *)(sreg + L.scal), *partials = (double *)(sreg + L.partials);
+    SolverState &S = plan->solver;
+    if (!o.resume) {
+        S = SolverState();
+        CC_CUDA(cudaMemsetAsync(used_dev, 0, 16, s));
+    }
+    // pinned host staging for the per-iteration scalars (one per thread)
+    static thread_local double *h_scal = nullptr;
+    if (!h_scal) CC_CUDA(cudaMallocHost(&h_scal, 64));
+    if (report) { report->iterations = 0; report->converged = 0; report->switched_at = -1; }
+    plan->cache_filled = false;
+    if (refine) refine->cache_filled = false;
+    g_err.clear();
+    cc_status result = CC_ERR_NOT_CONVERGED;
+    double last_e = NAN, last_rn = NAN;
+    int k = 0;
+    for (k = 0; k < o.max_iter; k++) {
+        cc_plan_s *cur = (S.phase == 1 && refine) ? refine : plan;
+        st = run_residual(cur, ints, amps, &R, pws, (size_t)pw, s, true);
+        if (st != CC_OK) return st;
+        st = reduce_energy_norm(P, ints, amps, r, L.n, partials, scal, s);
+        if (st != CC_OK) return st;
+        CC_CUDA(cudaMemcpyAsync(h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(h_scal + 4, used_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaStreamSynchronize(s));
+        // history bookkeeping of the previous device DIIS solve: drop what it dropped
+        if (S.pending_m >= 2) {
+            int used = *(int *)(h_scal + 4);
+            int keep = used == 0 ? 2 : used;
+            while (S.nstored > keep) {
+                for (int q = 0; q + 1 < S.nstored; q++) S.order[q] = S.order[q + 1];
+                S.nstored--;
+            }
+            S.pending_m = 0;
+        }
+        double rr = 0.0;
+        for (int l = 1, c = 1; l <= 3; l++)
+            if (r[l]) rr += h_scal[c++];
+        const double e = h_scal[0], rn = std::sqrt(rr);
+        last_e = e;
+        last_rn = rn;
+        if (report && report->energies) report->energies[k] = e;
+        if (report && report->rnorms) report->rnorms[k] = rn;
+        if (o.verbose) std::fprintf(stderr, "cc_solve iter %d phase %d E %.14f |R| %.3e\n", S.iter, S.phase, e, rn);
+        S.iter++;
+        if (!std::isfinite(rn) || rn > 1e3 * S.best) {
+            g_err = "divergence: |R| not finite or 1e3 above its best value";
+            k++;
+            break;
+        }
+        if (rn < S.best) { S.best = rn; S.stall = 0; } else S.stall++;
+        if (refine && S.phase == 0 && (rn < std::max(o.switch_tol, o.tol) || S.stall >= 3)) {
+            // switch to the refine plan and re-evaluate at the same amplitudes
+            S.phase = 1;
+            S.nstored = 0;
+            S.best = INFINITY;
+            S.stall = 0;
+            if (report) report->switched_at = k;
+            continue;
+        }
+        if (o.tol > 0 && rn < o.tol) { result = CC_OK; k++; break; }
+        // Jacobi step into a history slot
+        int slot = 0;
+        if (o.diis_max > 0 && S.nstored == o.diis_max) {
+            slot = S.order[0];
+            for (int q = 0; q + 1 < S.nstored; q++) S.order[q] = S.order[q + 1];
+            S.nstored--;
+        } else if (o.diis_max > 0) {
+            for (;; slot++) {
+                bool busy = false;
+                for (int q = 0; q < S.nstored; q++) busy |= S.order[q] == slot;
+                if (!busy) break;
+            }
+        }
+        double *xs = hx + (int64_t)slot * L.nx, *es = he + (int64_t)slot * L.nx;
+        int64_t off = 0;
+        for (int l = 1; l <= 3; l++) {
+            if (!r[l]) continue;
+            CC_CUDA(launch_jacobi(l, o_, v_, ints->f_occ, ints->f_vir, t[l], r[l], xs + off, es + off, s));
+            off += L.n[l];
+        }
+        if (o.diis_max > 0) {
+            S.order[S.nstored++] = slot;
+            int a_[16], b_[16];
+            for (int q = 0; q < S.nstored; q++) {
+                const int sq = S.order[q];
+                CC_CUDA(launch_dot_partials(es, he + (int64_t)sq * L.nx, L.nx, partials + (int64_t)q * kRedBlocks, s));
+                a_[q] = slot;
+                b_[q] = sq;
+            }
+            CC_CUDA(launch_gram_scatter(partials, S.nstored, a_, b_, gram, s));
+        }
+        if (S.nstored >= 2) {
+            CC_CUDA(launch_diis_solve(gram, S.order, S.nstored, coef, used_dev, s));
+            int64_t off2 = 0;
+            for (int l = 1; l <= 3; l++) {
+                if (!r[l]) continue;
+                const double *xq[16];
+                for (int q = 0; q < S.nstored; q++) xq[q] = hx + (int64_t)S.order[q] * L.nx + off2;
+                CC_CUDA(launch_combine(xq, coef, used_dev, S.nstored, L.n[l], t[l], s));
+                off2 += L.n[l];
+            }
+            S.pending_m = S.nstored;
+        } else {
+            int64_t off2 = 0;
+            for (int l = 1; l <= 3; l++) {
+                if (!r[l]) continue;
+                CC_CUDA(cudaMemcpyAsync(t[l], xs + off2, L.n[l] * 8, cudaMemcpyDeviceToDevice, s));
+                off2 += L.n[l];
+            }
+        }
+    }
+    if (report) {
+        report->iterations = k;
+        report->converged = result == CC_OK;
+        report->energy = last_e;
+        report->rnorm = last_rn;
+    }
+    if (result != CC_OK && g_err.empty()) g_err = "maximum iterations reached";
+    return result;
+}
+
+cc_status cc_integral_block_elems(int o, int v, size_t elems[6]) {
+    if (o < 1 || v < 1 || !elems) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    for (int b = 0; b < 6; b++) {
+        int64_t e[4];
+        integral_block_dims(o, v, b, e);
+        elems[b] = (size_t)(e[0] * e[1] * e[2] * e[3]);
+    }
+    return CC_OK;
+}
+
+cc_status cc_build_integrals_workspace_bytes(int o, int v, int L, cc_dtype dtype, size_t *bytes) {
+    if (o < 1 || v < 1 || L < 1 || !bytes) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    if (dtype != CC_F64) return fail(CC_ERR_UNSUPPORTED, "only CC_F64 is implemented in this build");
+    const int64_t n = o + v;
+    *bytes = (size_t)(al((int64_t)L * n * n * 8) + 4 * kAlign);
+    return CC_OK;
+}
+
+cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B, void *oooo, void *ooov, void *oovv,
+                             void *ovov, void *ovvv, void *vvvv, void *ws, size_t ws_bytes, void *stream) {
+    if (dtype != CC_F64) return fail(CC_ERR_UNSUPPORTED, "only CC_F64 is implemented in this build");
+    size_t need = 0;
+    cc_status st = cc_build_integrals_workspace_bytes(o, v, L, dtype, &need);
+    if (st != CC_OK) return st;
+    if (!B || !ws || ws_bytes < need || !aligned256(ws)) return fail(CC_ERR_WORKSPACE, "bad B or workspace");
+    void *blocks[6] = {oooo, ooov, oovv, ovov, ovvv, vvvv};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = o + v;
+    const int64_t ext[2] = {o, v}, base[2] = {0, o};
+    // sub-blocks Bsub[x][y] = B[L][x-range][y-range], contiguous [L][X][Y]
+    double *sub[2][2];
+    int64_t off = 0;
+    for (int x = 0; x < 2; x++)
+        for (int y = 0; y < 2; y++) {
+            sub[x][y] = (double *)((char *)ws + off);
+            off += (int64_t)L * ext[x] * ext[y] * 8;
+            AccumDesc d{};
+            d.nd = 3;
+            d.nperm = 1;
+            d.ext[0] = L; d.ext[1] = ext[x]; d.ext[2] = ext[y];
+            d.ostr[0] = ext[x] * ext[y]; d.ostr[1] = ext[y]; d.ostr[2] = 1;
+            d.sstr[0][0] = n * n; d.sstr[0][1] = n; d.sstr[0][2] = 1;
+            d.total = (int64_t)L * ext[x] * ext[y];
+            d.sign[0] = 1.0;
+            d.alpha = 1.0;
+            d.beta = 0.0;
+            CC_CUDA(launch_accum(d, (const double *)B + base[x] * n + base[y], sub[x][y], s));
+        }
+    static const char *nm[6] = {"oooo", "ooov", "oovv", "ovov", "ovvv", "vvvv"};
+    for (int b = 0; b < 6; b++) {
+        if (!blocks[b]) continue;
+        int64_t e[4];
+        integral_block_dims(o, v, b, e);
+        int sp[4];
+        for (int q = 0; q < 4; q++) sp[q] = nm[b][q] == 'o' ? 0 : 1;
+        const int64_t str[4] = {e[1] * e[2] * e[3], e[2] * e[3], e[3], 1};
+        // <pq||rs> = sum_L B_pr B_qs - sum_L B_ps B_qr  (rows: (p, r|s), columns: (q, s|r))
+        for (int term = 0; term < 2; term++) {
+            const int ri = term == 0 ? 2 : 3, si = term == 0 ? 3 : 2;
+            GemmF64Desc g{};
+            g.M = e[0] * e[ri];
+            g.N = e[1] * e[si];
+            g.K = L;
+            g.sAm = 1;
+            g.sAk = e[0] * e[ri];
+            g.sBk = e[1] * e[si];
+            g.sBn = 1;
+            g.cm.nd = 2; g.cm.ext[0] = e[0]; g.cm.ext[1] = e[ri]; g.cm.str[0] = str[0]; g.cm.str[1] = str[ri];
+            g.cn.nd = 2; g.cn.ext[0] = e[1]; g.cn.ext[1] = e[si]; g.cn.str[0] = str[1]; g.cn.str[1] = str[si];
+            g.alpha = term == 0 ? 1.0 : -1.0;
+            g.beta = term == 0 ? 0.0 : 1.0;
+            CC_CUDA(launch_gemm_f64(g, sub[sp[0]][sp[ri]], sub[sp[1]][sp[si]], (double *)blocks[b], s));
+        }
+    }
+    return CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,438 @@
+// kernels.cu -- FP64 kernels of the TTGT residual path (sm_103a):
+//   accum        generic strided permute / copy / antisymmetrising epilogue
+//   gemm_f64     FP64 SIMT GEMM with generalised (mixed-radix) output addressing
+//   denom/jacobi/energy/dot reductions and the DIIS solve of the iteration
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace ccb {
+
+// ------------------------------------------------------------------ accum
+// Each warp owns a contiguous run of 32*kAccChunk output elements; lane l
+// visits run_start + l + 32*j, so stores to a contiguous output coalesce.
+// The multi-index is decomposed once per run and advanced as an odometer.
+constexpr int kAccChunk = 8;
+
+__global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const double *__restrict__ src,
+                                                    double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t run = 32 * kAccChunk;
+    for (int64_t r0 = warp * run; r0 < d.total; r0 += nwarps * run) {
+        int64_t e = r0 + lane;
+        if (e >= d.total) continue;
+        int dig[kMaxDims];
+        {
+            int64_t x = e;
+            for (int k = d.nd - 1; k >= 0; k--) {
+                dig[k] = (int)(x % d.ext[k]);
+                x /= d.ext[k];
+            }
+        }
+        for (int j = 0; j < kAccChunk && e < d.total; j++) {
+            int64_t oo = 0;
+            for (int k = 0; k < d.nd; k++) oo += dig[k] * d.ostr[k];
+            double acc = 0.0;
+            for (int p = 0; p < d.nperm; p++) {
+                int64_t so = 0;
+                for (int k = 0; k < d.nd; k++) so += dig[k] * d.sstr[p][k];
+                acc += d.sign[p] * __ldg(src + so);
+            }
+            double val = d.alpha * acc;
+            if (d.beta != 0.0) val += d.beta * out[oo];
+            out[oo] = val;
+            // advance by 32 elements
+            e += 32;
+            int carry = 32;
+            for (int k = d.nd - 1; k >= 0 && carry; k--) {
+                int64_t t = dig[k] + carry;
+                dig[k] = (int)(t % d.ext[k]);
+                carry = (int)(t / d.ext[k]);
+            }
+        }
+    }
+}
+
+cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s) {
+    if (d.total <= 0) return cudaSuccess;
+    int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
+    int64_t blocks = (runs + 7) / 8;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    accum_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, src, out);
+    return cudaGetLastError();
+}
+
+__global__ void zero_kernel(double *p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = 0.0;
+}
+
+cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    zero_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, n);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- gemm_f64
+// 64x64 output tile, BK = 16, 256 threads as 16x16, each thread a 4x4
+// strided micro-tile.  Operand tiles go global -> registers -> shared memory
+// (k-major, padded), double-buffered through registers.  The FP64 pipe of
+// sm_103a is narrow, so the kernel is built to keep it issuing: 16 DFMA per
+// 8 shared loads.
+constexpr int GBM = 64, GBN = 64, GBK = 16, GPAD = 1;
+
+__device__ __forceinline__ int64_t grp_offset(const Grp &g, int64_t x) {
+    if (g.nd == 1) return x * g.str[0];
+    int64_t off = 0;
+    for (int k = g.nd - 1; k >= 0; k--) {
+        int64_t q = x / g.ext[k];
+        off += (x - q * g.ext[k]) * g.str[k];
+        x = q;
+    }
+    return off;
+}
+
+template <bool A_KCONTIG, bool B_KCONTIG>
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, const double *__restrict__ A,
+                                                       const double *__restrict__ B, double *__restrict__ C,
+                                                       int thread_m_fast) {
+    __shared__ double As[GBK][GBM + GPAD];
+    __shared__ double Bs[GBK][GBN + GPAD];
+    const int tid = threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.x * GBM;
+    const int64_t n0 = (int64_t)blockIdx.y * GBN;
+    const int tm = thread_m_fast ? (tid & 15) : (tid >> 4);
+    const int tn = thread_m_fast ? (tid >> 4) : (tid & 15);
+
+    double ra[4], rb[4];
+    auto load_tiles = [&](int64_t k0) {
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            int e = tid + 256 * r;
+            int mm, kk;
+            if (A_KCONTIG) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
+            int64_t gm = m0 + mm, gk = k0 + kk;
+            ra[r] = (gm < d.M && gk < d.K) ? __ldg(A + gm * d.sAm + gk * d.sAk) : 0.0;
+            int nn;
+            if (B_KCONTIG) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
+            int64_t gn = n0 + nn;
+            gk = k0 + kk;
+            rb[r] = (gn < d.N && gk < d.K) ? __ldg(B + gk * d.sBk + gn * d.sBn) : 0.0;
+        }
+    };
+    auto store_tiles = [&]() {
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            int e = tid + 256 * r;
+            if (A_KCONTIG) As[e & 15][e >> 4] = ra[r]; else As[e >> 6][e & 63] = ra[r];
+            if (B_KCONTIG) Bs[e & 15][e >> 4] = rb[r]; else Bs[e >> 6][e & 63] = rb[r];
+        }
+    };
+
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+    load_tiles(0);
+    for (int64_t k0 = 0; k0 < d.K; k0 += GBK) {
+        __syncthreads();
+        store_tiles();
+        __syncthreads();
+        if (k0 + GBK < d.K) load_tiles(k0 + GBK);
+#pragma unroll
+        for (int k = 0; k < GBK; k++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[k][tm + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[k][tn + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+    }
+    int64_t ro[4], co[4];
+    bool rv[4], cv[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int64_t m = m0 + tm + 16 * i;
+        rv[i] = m < d.M;
+        ro[i] = rv[i] ? grp_offset(d.cm, m) : 0;
+        int64_t n = n0 + tn + 16 * i;
+        cv[i] = n < d.N;
+        co[i] = cv[i] ? grp_offset(d.cn, n) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (!(rv[i] && cv[j])) continue;
+            double *p = C + ro[i] + co[j];
+            double val = d.alpha * acc[i][j];
+            if (d.beta != 0.0) val += d.beta * *p;
+            *p = val;
+        }
+}
+
+cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, cudaStream_t s) {
+    if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((d.M + GBM - 1) / GBM), (unsigned)((d.N + GBN - 1) / GBN));
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    // threads run fastest along the output direction with the smaller stride
+    int64_t sm = d.cm.nd ? d.cm.str[d.cm.nd - 1] : 0, sn = d.cn.nd ? d.cn.str[d.cn.nd - 1] : 0;
+    int m_fast = (d.cm.nd && (!d.cn.nd || sm <= sn)) ? 1 : 0;
+    const bool ak = d.sAk == 1 && !(d.sAm == 1 && d.K == 1);
+    const bool bk = d.sBk == 1 && !(d.sBn == 1 && d.K == 1);
+    if (ak && bk) gemm_f64_kernel<true, true><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
+    else if (ak) gemm_f64_kernel<true, false><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
+    else if (bk) gemm_f64_kernel<false, true><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
+    else gemm_f64_kernel<false, false><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- iteration kernels
+// D for a residual element stored [i..][a..] row-major (rank occupied, then
+// rank virtual indices): sum of occupied minus sum of virtual orbital energies.
+__device__ __forceinline__ double denom(int rank, int o, int v, const double *fo, const double *fv, int64_t e) {
+    double d = 0.0;
+    int64_t x = e;
+    for (int k = 0; k < rank; k++) { d -= fv[x % v]; x /= v; }
+    for (int k = 0; k < rank; k++) { d += fo[x % o]; x /= o; }
+    return d;
+}
+
+__global__ void denom_sub_kernel(int rank, int o, int v, const double *fo, const double *fv, const double *t,
+                                 double *r, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        r[e] -= denom(rank, o, v, fo, fv, e) * t[e];
+}
+
+static int64_t count_of(int rank, int o, int v) {
+    int64_t n = 1;
+    for (int k = 0; k < rank; k++) n *= (int64_t)o * v;
+    return n;
+}
+
+cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv, const double *t, double *r,
+                             cudaStream_t s) {
+    int64_t n = count_of(rank, o, v);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    denom_sub_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, n);
+    return cudaGetLastError();
+}
+
+__global__ void jacobi_kernel(int rank, int o, int v, const double *fo, const double *fv, const double *t,
+                              const double *r, double *xo, double *eo, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double q = r[e] / denom(rank, o, v, fo, fv, e);
+        eo[e] = q;
+        xo[e] = t[e] + q;
+    }
+}
+
+cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
+                          const double *r, double *xo, double *eo, cudaStream_t s) {
+    int64_t n = count_of(rank, o, v);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, n);
+    return cudaGetLastError();
+}
+
+// deterministic block reduction (fixed grid, fixed order)
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double sh[256];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) dot_partials_kernel(const double *x, const double *y, int64_t n,
+                                                           double *partials) {
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)kRedBlocks * 256)
+        s = fma(x[e], y[e], s);
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *partials, cudaStream_t s) {
+    dot_partials_kernel<<<kRedBlocks, 256, 0, s>>>(x, y, n, partials);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) energy_partials_kernel(int o, int v, const double *V, const double *t1,
+                                                              const double *t2, double *partials) {
+    const int64_t n = (int64_t)o * o * v * v;
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)kRedBlocks * 256) {
+        double w = 0.25 * t2[e];
+        if (t1) {
+            int64_t x = e;
+            int b = (int)(x % v); x /= v;
+            int a = (int)(x % v); x /= v;
+            int j = (int)(x % o); x /= o;
+            int i = (int)x;
+            w += 0.5 * t1[(int64_t)i * v + a] * t1[(int64_t)j * v + b];
+        }
+        s = fma(V[e], w, s);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+cudaError_t launch_energy_partials(int o, int v, const double *Voovv, const double *t1, const double *t2,
+                                   double *partials, cudaStream_t s) {
+    energy_partials_kernel<<<kRedBlocks, 256, 0, s>>>(o, v, Voovv, t1, t2, partials);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const double *partials, int count, double *out) {
+    for (int c = 0; c < count; c++) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < kRedBlocks; k += 256) s += partials[(int64_t)c * kRedBlocks + k];
+        s = block_sum(s);
+        if (threadIdx.x == 0) out[c] = s;
+    }
+}
+
+cudaError_t launch_reduce_partials(const double *partials, int count, double *out, cudaStream_t s) {
+    reduce_partials_kernel<<<1, 256, 0, s>>>(partials, count, out);
+    return cudaGetLastError();
+}
+
+struct Order {
+    int s[16];
+};
+
+// DIIS: the bordered system [B 1; 1^T 0][c; l] = [0; 1] with B scaled by
+// 1/max(diag B), Gaussian elimination with partial pivoting; while a pivot is
+// below 1e-14 the oldest vector is dropped and the solve repeated (down to
+// two vectors).  status[0] = number of newest vectors used (0: none usable).
+__global__ void diis_solve_kernel(const double *gram16, Order ord, int m, double *coef, int *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int used = 0;
+    for (int mm = m; mm >= 2; mm--) {
+        const int off = m - mm;     // drop the `off` oldest
+        const int N = mm + 1;
+        auto G = [&](int r, int c) { return gram16[ord.s[off + r] * 16 + ord.s[off + c]]; };
+        double Am[17][18];
+        double dmax = 0.0;
+        for (int k = 0; k < mm; k++) dmax = fmax(dmax, G(k, k));
+        if (!(dmax > 0.0)) continue;
+        for (int r = 0; r < N; r++)
+            for (int c = 0; c <= N; c++) Am[r][c] = 0.0;
+        for (int r = 0; r < mm; r++) {
+            for (int c = 0; c < mm; c++) Am[r][c] = G(r, c) / dmax;
+            Am[r][mm] = 1.0;
+            Am[mm][r] = 1.0;
+        }
+        Am[mm][N] = 1.0;
+        bool ok = true;
+        for (int c = 0; c < N && ok; c++) {
+            int piv = c;
+            for (int r = c + 1; r < N; r++)
+                if (fabs(Am[r][c]) > fabs(Am[piv][c])) piv = r;
+            if (fabs(Am[piv][c]) < 1e-14) { ok = false; break; }
+            if (piv != c)
+                for (int k = 0; k <= N; k++) { double t = Am[c][k]; Am[c][k] = Am[piv][k]; Am[piv][k] = t; }
+            for (int r = c + 1; r < N; r++) {
+                double f = Am[r][c] / Am[c][c];
+                for (int k = c; k <= N; k++) Am[r][k] -= f * Am[c][k];
+            }
+        }
+        if (!ok) continue;
+        double x[17];
+        for (int r = N - 1; r >= 0; r--) {
+            double s = Am[r][N];
+            for (int k = r + 1; k < N; k++) s -= Am[r][k] * x[k];
+            x[r] = s / Am[r][r];
+        }
+        for (int k = 0; k < mm; k++) coef[k] = x[k];
+        used = mm;
+        break;
+    }
+    status[0] = used;
+}
+
+cudaError_t launch_diis_solve(const double *gram16, const int *order_host, int m, double *coef, int *status,
+                              cudaStream_t s) {
+    Order o{};
+    for (int k = 0; k < m && k < 16; k++) o.s[k] = order_host[k];
+    diis_solve_kernel<<<1, 32, 0, s>>>(gram16, o, m, coef, status);
+    return cudaGetLastError();
+}
+
+struct PairPack {
+    int2 p[16];
+};
+
+// gram16[a_k*16 + b_k] = gram16[b_k*16 + a_k] = sum of partials row k (fixed order)
+__global__ void __launch_bounds__(256) gram_scatter_kernel(const double *partials, int count, PairPack pk,
+                                                           double *gram16) {
+    for (int c = 0; c < count; c++) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < kRedBlocks; k += 256) s += partials[(int64_t)c * kRedBlocks + k];
+        s = block_sum(s);
+        if (threadIdx.x == 0) {
+            int2 pr = pk.p[c];
+            gram16[pr.x * 16 + pr.y] = s;
+            gram16[pr.y * 16 + pr.x] = s;
+        }
+    }
+}
+
+cudaError_t launch_gram_scatter(const double *partials, int count, const int *a_host, const int *b_host,
+                                double *gram16, cudaStream_t s) {
+    PairPack pk{};
+    for (int k = 0; k < count && k < 16; k++) pk.p[k] = make_int2(a_host[k], b_host[k]);
+    gram_scatter_kernel<<<1, 256, 0, s>>>(partials, count, pk, gram16);
+    return cudaGetLastError();
+}
+
+struct PtrPack {
+    const double *p[16];
+};
+
+// x = sum_k coef[k] * xs[m - used + k] over the `used` newest vectors
+// (used read from the device; used == 0 copies the newest vector).
+__global__ void combine_kernel(PtrPack xs, const double *coef, const int *used_dev, int m, int64_t n, double *x) {
+    const int used = *used_dev;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double s;
+        if (used == 0) {
+            s = xs.p[m - 1][e];
+        } else {
+            s = 0.0;
+            for (int k = 0; k < used; k++) s += coef[k] * xs.p[m - used + k][e];
+        }
+        x[e] = s;
+    }
+}
+
+cudaError_t launch_combine(const double *const *xs_host, const double *coef, const int *used_dev, int m, int64_t n,
+                           double *x, cudaStream_t s) {
+    PtrPack pk{};
+    for (int k = 0; k < m && k < 16; k++) pk.p[k] = xs_host[k];
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    combine_kernel<<<(unsigned)blocks, 256, 0, s>>>(pk, coef, used_dev, m, n, x);
+    return cudaGetLastError();
+}
+
+}  // namespace ccb

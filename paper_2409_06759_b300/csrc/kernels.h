@@ -1,0 +1,103 @@
+// kernels.h -- host-side launchers of the ccb300 CUDA kernels and the small
+// descriptor structs they take.  Shared by the planner/executor (C++) and the
+// kernel translation units (CUDA).  No torch types anywhere.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccb {
+
+constexpr int kMaxDims = 8;     // dims of one tensor view
+constexpr int kMaxPerms = 16;   // terms of an expanded permutation operator
+
+// Mixed-radix index group: a fused matrix index decomposed into nd digits
+// (digit 0 outermost, digit nd-1 fastest); offset = sum digit_d * str[d].
+struct Grp {
+    int nd;
+    int64_t ext[6];
+    int64_t str[6];
+};
+
+// out[offset(idx)] = beta * out[...] + alpha * sum_p sign[p] * src[sum_d idx_d * sstr[p][d]]
+// over the nd-dimensional index box ext[]; the output is visited in the
+// row-major order of ext (out strides arbitrary).  Covers permutes (TTGT
+// transposes), copies, and the antisymmetrising epilogues P(..).
+struct AccumDesc {
+    int nd;
+    int nperm;
+    int64_t total;
+    int64_t ext[kMaxDims];
+    int64_t ostr[kMaxDims];
+    int64_t sstr[kMaxPerms][kMaxDims];
+    double sign[kMaxPerms];
+    double alpha, beta;
+};
+
+// C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), FP64.
+// A(m,k) = A[m*sAm + k*sAk] with sAm == 1 or sAk == 1; B(k,n) = B[k*sBk + n*sBn]
+// likewise; C addressed through two mixed-radix groups.
+struct GemmF64Desc {
+    int64_t M, N, K;
+    int64_t sAm, sAk, sBk, sBn;
+    Grp cm, cn;
+    double alpha, beta;
+};
+
+// Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes
+// bf16 planes P_p[r][k] of a padded K-major matrix [Rp][Kp]:
+//   hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); rows >= R and
+//   columns >= K are written as zeros.
+struct SplitDesc {
+    int64_t R, K, Rp, Kp;
+    Grp gr, gk;
+    int nplanes;
+};
+
+// Split-bf16 GEMM on tcgen05: D[m][n] = sum_{(p,q) in products} A_p[m][:] . B_q[n][:]
+// (fp32 in TMEM), then C(m,n) = alpha * D + beta * C(m,n) in FP64.
+struct TcGemmDesc {
+    int64_t M, N, Mp, Np, Kp;
+    int nplanes_a, nplanes_b;
+    int nprod;                 // number of (p,q) products
+    int prod_a[8], prod_b[8];  // plane indices of each product
+    Grp cm, cn;
+    double alpha, beta;
+};
+
+cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s);
+cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
+cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C,
+                            cudaStream_t s);
+cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s);
+cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C,
+                           int *err_flag, cudaStream_t s);
+
+// R -= D * T for rank 1..3 residuals: D from the orbital energies.
+cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv,
+                             const double *t, double *r, cudaStream_t s);
+// Jacobi step: e = r / D, x' = t + e (written to xo, eo).
+cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
+                          const double *r, double *xo, double *eo, cudaStream_t s);
+// partial sums for dot products: partials[b] = sum over block b of x*y (fixed grid)
+constexpr int kRedBlocks = 592;
+cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *partials,
+                                cudaStream_t s);
+// energy partials: sum_ijab V[ijab] (1/4 t2[ijab] + 1/2 t1[ia] t1[jb]); t1 may be NULL
+cudaError_t launch_energy_partials(int o, int v, const double *Voovv, const double *t1,
+                                   const double *t2, double *partials, cudaStream_t s);
+// out[k] = sum of partials[k][0..kRedBlocks) for k < count (fixed order)
+cudaError_t launch_reduce_partials(const double *partials, int count, double *out, cudaStream_t s);
+// DIIS on device.  gram16[16*16] holds <e_a|e_b> by history slot; order_host
+// lists the m stored slots oldest first.  Writes coef (for the newest
+// status[0] vectors) and status[0] = vectors used (0: no usable solve).
+cudaError_t launch_diis_solve(const double *gram16, const int *order_host, int m, double *coef, int *status,
+                              cudaStream_t s);
+// reduce `count` partial rows into gram16 at the symmetric pairs (a_k, b_k)
+cudaError_t launch_gram_scatter(const double *partials, int count, const int *a_host, const int *b_host,
+                                double *gram16, cudaStream_t s);
+// x = sum_k c_k xs[m - used + k] over n elements (used read from used_dev);
+// xs_host: host array of m device pointers, oldest first.
+cudaError_t launch_combine(const double *const *xs_host, const double *coef, const int *used_dev, int m, int64_t n,
+                           double *x, cudaStream_t s);
+
+}  // namespace ccb

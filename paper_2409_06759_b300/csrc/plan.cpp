@@ -1,0 +1,829 @@
+// plan.cpp -- parser and TTGT planner for contraction lists.
+//
+// Grammar (one statement per line, '#' comment):
+//   OUT[idx].. (=|+=|-=) [factor] [P(pq)|P(p/qr)]... A[idx].. [* B[idx]..]
+// This is the text form of the "Contraction" class of arxiv 2409.06759
+// Sec. II C (factor, permutation operators, tensors, output); as in the
+// paper's Fig. algo:remove, only binary contractions are accepted.
+#include "plan.h"
+
+#include <algorithm>
+#include <cctype>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <set>
+#include <sstream>
+
+namespace ccb {
+
+static const char *kBlockNames[6] = {"oooo", "ooov", "oovv", "ovov", "ovvv", "vvvv"};
+
+void integral_block_dims(int o, int v, int block, int64_t ext[4]) {
+    for (int d = 0; d < 4; d++) ext[d] = kBlockNames[block][d] == 'o' ? o : v;
+}
+
+namespace {
+
+constexpr int64_t kAlign = 256;
+int64_t align_up(int64_t x, int64_t a = kAlign) { return (x + a - 1) / a * a; }
+
+struct Ref {
+    std::string name;
+    std::vector<int> letters;   // letter ids in written order
+};
+
+struct Stmt {
+    int line = 0;
+    Ref out;
+    int op = 0;                 // 0 '=', +1 '+=', -1 '-='
+    double factor = 1.0;
+    std::vector<std::pair<std::vector<int>, bool>> perms;  // letters, slash form
+    std::vector<Ref> rhs;
+};
+
+struct Parser {
+    const std::string &s;
+    size_t p = 0;
+    std::vector<std::string> &tokens;   // letter id -> token
+    std::vector<char> &spaces;
+    std::string err;
+    Parser(const std::string &line, std::vector<std::string> &t, std::vector<char> &sp)
+        : s(line), tokens(t), spaces(sp) {}
+    void ws() {
+        while (p < s.size() && std::isspace((unsigned char)s[p])) p++;
+    }
+    bool eat(char c) {
+        ws();
+        if (p < s.size() && s[p] == c) { p++; return true; }
+        return false;
+    }
+    bool at_end() { ws(); return p >= s.size(); }
+    int letter_id(const std::string &tok) {
+        for (size_t k = 0; k < tokens.size(); k++)
+            if (tokens[k] == tok) return (int)k;
+        char sp = 0;
+        if (tok.size() == 1) {
+            char c = tok[0];
+            if (c >= 'a' && c <= 'h') sp = 'v';
+            else if (c >= 'i' && c <= 'n') sp = 'o';
+        } else if (tok[0] == 'p') sp = 'v';
+        else if (tok[0] == 'h') sp = 'o';
+        if (!sp) { err = "index '" + tok + "' is neither occupied (i..n, h<k>) nor virtual (a..h, p<k>)"; return -1; }
+        tokens.push_back(tok);
+        spaces.push_back(sp);
+        return (int)tokens.size() - 1;
+    }
+    // reads [a-z][0-9]* tokens until the closing bracket
+    bool letters_until(char close, std::vector<int> &out, std::vector<int> *slash_pos = nullptr) {
+        for (;;) {
+            ws();
+            if (p >= s.size()) { err = "missing closing bracket"; return false; }
+            char c = s[p];
+            if (c == close) { p++; return true; }
+            if (c == ',') { p++; continue; }
+            if (c == '/' && slash_pos) { slash_pos->push_back((int)out.size()); p++; continue; }
+            if (!(c >= 'a' && c <= 'z')) { err = std::string("unexpected character '") + c + "' in index list"; return false; }
+            std::string tok(1, c);
+            p++;
+            while (p < s.size() && std::isdigit((unsigned char)s[p])) tok += s[p++];
+            int id = letter_id(tok);
+            if (id < 0) return false;
+            out.push_back(id);
+        }
+    }
+    bool ref(Ref &r) {
+        ws();
+        size_t q = p;
+        while (p < s.size() && (std::isalnum((unsigned char)s[p]) || s[p] == '_')) p++;
+        if (p == q || std::isdigit((unsigned char)s[q])) { err = "expected a tensor name"; return false; }
+        r.name = s.substr(q, p - q);
+        bool any = false;
+        while (eat('[')) {
+            if (!letters_until(']', r.letters)) return false;
+            any = true;
+        }
+        if (!any) { err = "tensor '" + r.name + "' has no index brackets"; return false; }
+        return true;
+    }
+    bool number(double &x) {
+        ws();
+        const char *b = s.c_str() + p;
+        char *e = nullptr;
+        x = std::strtod(b, &e);
+        if (e == b) return false;
+        p += (size_t)(e - b);
+        ws();
+        if (p + 1 < s.size() && s[p] == '/' && std::isdigit((unsigned char)s[p + 1])) {
+            p++;
+            const char *b2 = s.c_str() + p;
+            double d = std::strtod(b2, &e);
+            p += (size_t)(e - b2);
+            if (d == 0.0) { err = "division by zero in factor"; return false; }
+            x /= d;
+        }
+        return true;
+    }
+};
+
+bool parse_stmt(const std::string &line, Stmt &st, std::vector<std::string> &tokens,
+                std::vector<char> &spaces, std::string &err) {
+    Parser P(line, tokens, spaces);
+    if (!P.ref(st.out)) { err = P.err; return false; }
+    P.ws();
+    if (P.s.compare(P.p, 2, "+=") == 0) { st.op = 1; P.p += 2; }
+    else if (P.s.compare(P.p, 2, "-=") == 0) { st.op = -1; P.p += 2; }
+    else if (P.eat('=')) st.op = 0;
+    else { err = "expected '=', '+=' or '-='"; return false; }
+    st.factor = 1.0;
+    P.ws();
+    // factor: a number (optionally a/b), or a bare sign
+    if (P.p < P.s.size() && (P.s[P.p] == '-' || P.s[P.p] == '+')) {
+        bool neg = P.s[P.p] == '-';
+        size_t q = P.p + 1;
+        while (q < P.s.size() && std::isspace((unsigned char)P.s[q])) q++;
+        P.p = q;
+        double x = 1.0;
+        if (q < P.s.size() && (std::isdigit((unsigned char)P.s[q]) || P.s[q] == '.')) {
+            if (!P.number(x)) { err = P.err.empty() ? "bad factor" : P.err; return false; }
+        }
+        st.factor = neg ? -x : x;
+    } else if (P.p < P.s.size() && (std::isdigit((unsigned char)P.s[P.p]) || P.s[P.p] == '.')) {
+        double x;
+        if (!P.number(x)) { err = P.err.empty() ? "bad factor" : P.err; return false; }
+        st.factor = x;
+    }
+    P.eat('*');
+    // permutation operators
+    for (;;) {
+        P.ws();
+        if (P.p + 1 < P.s.size() && P.s[P.p] == 'P' && P.s[P.p + 1] == '(') {
+            P.p += 2;
+            std::vector<int> ls, slash;
+            if (!P.letters_until(')', ls, &slash)) { err = P.err; return false; }
+            bool sl = !slash.empty();
+            if (sl && (slash.size() != 1 || slash[0] != 1 || ls.size() < 3)) {
+                err = "permutation operator must be P(pq) or P(p/qr..)";
+                return false;
+            }
+            if (!sl && ls.size() != 2) { err = "permutation operator P(pq) needs exactly two indices"; return false; }
+            st.perms.push_back({ls, sl});
+            P.eat('*');
+        } else {
+            break;
+        }
+    }
+    Ref a;
+    if (!P.ref(a)) { err = P.err; return false; }
+    st.rhs.push_back(a);
+    if (P.eat('*')) {
+        Ref b;
+        if (!P.ref(b)) { err = P.err; return false; }
+        st.rhs.push_back(b);
+    }
+    if (!P.at_end()) {
+        err = "unexpected text after the contraction (only binary contractions are accepted)";
+        return false;
+    }
+    return true;
+}
+
+struct Perm {
+    double sign;
+    std::map<int, int> sigma;   // letter -> letter (identity when absent)
+    int at(int l) const {
+        auto it = sigma.find(l);
+        return it == sigma.end() ? l : it->second;
+    }
+};
+
+// Expands a product of permutation operators into signed relabellings.  A
+// relabelling sigma acts as (sigma X)(idx) = X(idx'), idx'(l) = idx(sigma(l)).
+std::vector<Perm> expand_perms(const std::vector<std::pair<std::vector<int>, bool>> &ps) {
+    std::vector<Perm> terms(1, Perm{1.0, {}});
+    for (auto &pp : ps) {
+        std::vector<Perm> ops;
+        ops.push_back(Perm{1.0, {}});
+        const auto &ls = pp.first;
+        if (!pp.second) {
+            ops.push_back(Perm{-1.0, {{ls[0], ls[1]}, {ls[1], ls[0]}}});
+        } else {
+            for (size_t k = 1; k < ls.size(); k++) ops.push_back(Perm{-1.0, {{ls[0], ls[k]}, {ls[k], ls[0]}}});
+        }
+        std::vector<Perm> nt;
+        for (auto &t : terms)
+            for (auto &op : ops) {
+                Perm c{t.sign * op.sign, {}};
+                std::set<int> keys;
+                for (auto &kv : t.sigma) keys.insert(kv.first);
+                for (auto &kv : op.sigma) keys.insert(kv.first);
+                for (int l : keys) {
+                    int m = t.at(op.at(l));
+                    if (m != l) c.sigma[l] = m;
+                }
+                nt.push_back(c);
+            }
+        terms.swap(nt);
+    }
+    return terms;
+}
+
+struct Planner {
+    Plan &plan;
+    int o, v;
+    std::string err;
+    std::map<std::string, int> by_name;
+    std::vector<bool> initialized;
+    int64_t scratch_need = 0;       // arena bytes of the current statement
+    int64_t cache_need = 0;         // static split planes
+    int64_t interm_need = kAlign;   // [status word][intermediates...] at the start of the workspace
+    bool mixed_all = false;
+
+    explicit Planner(Plan &pl) : plan(pl), o(pl.o), v(pl.v) {}
+
+    int add_tensor(const std::string &name, TKind k, const std::vector<char> &sp, int slot) {
+        Tensor t;
+        t.name = name;
+        t.kind = k;
+        t.spaces = sp;
+        t.slot = slot;
+        int64_t e = 1;
+        t.ext.resize(sp.size());
+        t.str.resize(sp.size());
+        for (size_t d = 0; d < sp.size(); d++) t.ext[d] = sp[d] == 'o' ? o : v;
+        for (int d = (int)sp.size() - 1; d >= 0; d--) { t.str[d] = e; e *= t.ext[d]; }
+        t.elems = e;
+        if (k == TKind::INTERM) { t.ws_off = interm_need; interm_need += align_up(e * 8); }
+        plan.tensors.push_back(t);
+        initialized.push_back(k != TKind::RES && k != TKind::INTERM);
+        by_name[name] = (int)plan.tensors.size() - 1;
+        return (int)plan.tensors.size() - 1;
+    }
+
+    bool resolve(const Ref &r, bool is_out, int op, const std::vector<char> &lsp, View &vw) {
+        const std::string &nm = r.name;
+        const int rank = (int)r.letters.size();
+        std::set<int> uniq(r.letters.begin(), r.letters.end());
+        if ((int)uniq.size() != rank) { err = "repeated index in " + nm; return false; }
+        auto is_amp = [](const std::string &x) {
+            return x == "t" || x == "T" || x == "T1" || x == "T2" || x == "T3" || x == "t1" || x == "t2" || x == "t3";
+        };
+        auto is_res = [](const std::string &x) {
+            return x == "R" || x == "r" || x == "R1" || x == "R2" || x == "R3" || x == "r1" || x == "r2" || x == "r3";
+        };
+        if (is_amp(nm) || is_res(nm)) {
+            bool amp = is_amp(nm);
+            if (rank % 2 || rank < 2 || rank > 6) { err = nm + " needs 2, 4 or 6 indices"; return false; }
+            int lvl = rank / 2;
+            if (nm.size() == 2 && nm[1] - '0' != lvl) { err = nm + " has the wrong number of indices"; return false; }
+            std::vector<int> occ, vir;
+            for (int l : r.letters) (lsp[l] == 'o' ? occ : vir).push_back(l);
+            if ((int)occ.size() != lvl) { err = nm + " needs equal numbers of occupied and virtual indices"; return false; }
+            std::string key = std::string(amp ? "T" : "R") + char('0' + lvl);
+            if (amp && is_out) { err = "amplitudes are inputs and cannot be assigned"; return false; }
+            if (!amp && !is_out) { err = "residual tensors are outputs only"; return false; }
+            int id;
+            auto it = by_name.find(key);
+            if (it == by_name.end()) {
+                std::vector<char> sp(lvl, 'o');
+                sp.insert(sp.end(), lvl, 'v');
+                id = add_tensor(key, amp ? TKind::AMP : TKind::RES, sp, lvl);
+            } else {
+                id = it->second;
+            }
+            if (amp) plan.amp_used[lvl] = true; else plan.res_used[lvl] = true;
+            vw.tensor = id;
+            vw.idx = occ;
+            vw.idx.insert(vw.idx.end(), vir.begin(), vir.end());
+        } else if (nm == "V" || nm == "v") {
+            if (is_out) { err = "integrals are inputs and cannot be assigned"; return false; }
+            if (rank != 4) { err = "V needs four indices <pq||rs> = V[pq][rs]"; return false; }
+            char s[4];
+            for (int d = 0; d < 4; d++) s[d] = lsp[r.letters[d]];
+            bool found = false;
+            // <pq||rs> = -<qp||rs> = -<pq||sr> = conj(<rs||pq>): search the canonical block
+            for (int bk = 0; bk < 2 && !found; bk++)
+                for (int bs = 0; bs < 2 && !found; bs++)
+                    for (int ks = 0; ks < 2 && !found; ks++) {
+                        int pos[4] = {0, 1, 2, 3};
+                        double sg = 1.0;
+                        if (bk) { pos[0] = 2; pos[1] = 3; pos[2] = 0; pos[3] = 1; }
+                        if (bs) { std::swap(pos[0], pos[1]); sg = -sg; }
+                        if (ks) { std::swap(pos[2], pos[3]); sg = -sg; }
+                        char pat[5] = {s[pos[0]], s[pos[1]], s[pos[2]], s[pos[3]], 0};
+                        for (int b = 0; b < 6; b++)
+                            if (!std::strcmp(pat, kBlockNames[b])) {
+                                std::string key = std::string("V_") + kBlockNames[b];
+                                auto it = by_name.find(key);
+                                int id = it == by_name.end()
+                                             ? add_tensor(key, TKind::INTEGRAL, std::vector<char>(pat, pat + 4), b)
+                                             : it->second;
+                                vw.tensor = id;
+                                vw.idx.resize(4);
+                                for (int d = 0; d < 4; d++) vw.idx[d] = r.letters[pos[d]];
+                                vw.sign = sg;
+                                vw.conj = bk != 0;
+                                found = true;
+                                break;
+                            }
+                    }
+            if (!found) { err = "internal: no canonical integral block"; return false; }
+        } else {
+            std::vector<char> sp;
+            for (int l : r.letters) sp.push_back(lsp[l]);
+            auto it = by_name.find(nm);
+            int id;
+            if (it == by_name.end()) {
+                if (!is_out || op != 0) {
+                    err = "intermediate '" + nm + "' is used before a defining '=' statement";
+                    return false;
+                }
+                id = add_tensor(nm, TKind::INTERM, sp, 0);
+            } else {
+                id = it->second;
+                const Tensor &t = plan.tensors[id];
+                if (t.kind != TKind::INTERM) { err = "name '" + nm + "' is reserved"; return false; }
+                if (t.spaces != sp) { err = "index spaces of '" + nm + "' differ from its definition"; return false; }
+            }
+            vw.tensor = id;
+            vw.idx = r.letters;
+        }
+        const Tensor &t = plan.tensors[vw.tensor];
+        vw.ext = t.ext;
+        vw.str = t.str;
+        return true;
+    }
+
+    struct Fuse {
+        bool ok = true;
+        std::vector<int> order;     // letters, outermost first (extent-1 letters last)
+        int64_t stride = 0, extent = 1;
+    };
+
+    // Can the letters `grp` of view `vw` be addressed as one index with a single
+    // stride?  The only candidate order is by decreasing stride.
+    static Fuse fusable(const View &vw, const std::set<int> &grp) {
+        Fuse f;
+        std::vector<int> dims, ones;
+        for (size_t d = 0; d < vw.idx.size(); d++)
+            if (grp.count(vw.idx[d])) (vw.ext[d] > 1 ? dims : ones).push_back((int)d);
+        std::sort(dims.begin(), dims.end(), [&](int x, int y) { return vw.str[x] > vw.str[y]; });
+        for (size_t t = 0; t + 1 < dims.size(); t++)
+            if (vw.str[dims[t]] != vw.str[dims[t + 1]] * vw.ext[dims[t + 1]]) f.ok = false;
+        for (int d : dims) { f.order.push_back(vw.idx[d]); f.extent *= vw.ext[d]; }
+        for (int d : ones) f.order.push_back(vw.idx[d]);
+        f.stride = dims.empty() ? 1 : vw.str[dims.back()];
+        return f;
+    }
+
+    static bool same_order(const View &va, const std::vector<int> &a, const View &vb, const std::vector<int> &b) {
+        auto strip = [](const View &vw, const std::vector<int> &o) {
+            std::vector<int> r;
+            for (int l : o)
+                for (size_t d = 0; d < vw.idx.size(); d++)
+                    if (vw.idx[d] == l && vw.ext[d] > 1) r.push_back(l);
+            return r;
+        };
+        return strip(va, a) == strip(vb, b);
+    }
+
+    static int64_t ext_of(const View &vw, int l) {
+        for (size_t d = 0; d < vw.idx.size(); d++)
+            if (vw.idx[d] == l) return vw.ext[d];
+        return 1;
+    }
+    static int64_t str_of(const View &vw, int l) {
+        for (size_t d = 0; d < vw.idx.size(); d++)
+            if (vw.idx[d] == l) return vw.str[d];
+        return 0;
+    }
+
+    BufRef tensor_ref(int id) const {
+        const Tensor &t = plan.tensors[id];
+        BufRef r;
+        switch (t.kind) {
+            case TKind::AMP: r.where = BufRef::AMP; r.slot = t.slot; break;
+            case TKind::RES: r.where = BufRef::RES; r.slot = t.slot; break;
+            case TKind::INTEGRAL: r.where = BufRef::INTEG; r.slot = t.slot; break;
+            case TKind::INTERM: r.where = BufRef::WS; r.off = t.ws_off; break;
+        }
+        return r;
+    }
+
+    BufRef scratch(int64_t bytes) {
+        BufRef r;
+        r.where = BufRef::WS;
+        r.slot = 1;                 // arena-relative; rebased after planning
+        r.off = scratch_need;
+        scratch_need += align_up(bytes);
+        return r;
+    }
+
+    Grp make_grp(const std::vector<int> &letters, const View &ext_src, const View &str_src) {
+        Grp g{};
+        for (int l : letters) {
+            if (ext_of(ext_src, l) <= 1) continue;
+            if (g.nd >= 6) { err = "more than six indices in one matrix dimension"; return g; }
+            g.ext[g.nd] = ext_of(ext_src, l);
+            g.str[g.nd] = str_of(str_src, l);
+            g.nd++;
+        }
+        return g;
+    }
+
+    // ACCUM step: out (view over OUT letters) = beta*out + alpha*sum_p s_p src[sigma_p]
+    Step accum_step(const View &out, BufRef outref, const View &src, BufRef srcref, const std::vector<Perm> &perms,
+                    double alpha, double beta) {
+        Step st;
+        st.kind = StepKind::ACCUM;
+        st.out = outref;
+        st.a = srcref;
+        AccumDesc &d = st.acc;
+        d.nd = (int)out.idx.size();
+        d.nperm = (int)perms.size();
+        d.total = 1;
+        for (int k = 0; k < d.nd; k++) {
+            d.ext[k] = out.ext[k];
+            d.ostr[k] = out.str[k];
+            d.total *= out.ext[k];
+        }
+        for (int p = 0; p < d.nperm; p++) {
+            d.sign[p] = perms[p].sign;
+            for (int k = 0; k < d.nd; k++) {
+                // the source stride for output letter mu is that of sigma^-1(mu)
+                int mu = out.idx[k];
+                int pre = mu;
+                for (auto &kv : perms[p].sigma)
+                    if (kv.second == mu) pre = kv.first;
+                d.sstr[p][k] = str_of(src, pre);
+            }
+        }
+        d.alpha = alpha;
+        d.beta = beta;
+        st.note = "accum";
+        return st;
+    }
+
+    // contiguous buffer view with the given letter order
+    static View contiguous_view(const std::vector<int> &order, const View &ext_src1, const View *ext_src2 = nullptr) {
+        View w;
+        w.tensor = -1;
+        w.idx = order;
+        w.ext.resize(order.size());
+        w.str.resize(order.size());
+        int64_t e = 1;
+        for (int d = (int)order.size() - 1; d >= 0; d--) {
+            int64_t x = ext_of(ext_src1, order[d]);
+            if (x <= 1 && ext_src2) x = ext_of(*ext_src2, order[d]);
+            w.ext[d] = x;
+            w.str[d] = e;
+            e *= x;
+        }
+        return w;
+    }
+
+    static int64_t view_elems(const View &w) {
+        int64_t e = 1;
+        for (auto x : w.ext) e *= x;
+        return e;
+    }
+
+    bool plan_stmt(const Stmt &s, const std::vector<char> &lsp, int si) {
+        View out;
+        if (!resolve(s.out, true, s.op, lsp, out)) return false;
+        const Tensor T = plan.tensors[out.tensor];
+        if (T.kind != TKind::RES && T.kind != TKind::INTERM) { err = "output must be a residual or an intermediate"; return false; }
+        std::vector<View> in(s.rhs.size());
+        for (size_t k = 0; k < s.rhs.size(); k++)
+            if (!resolve(s.rhs[k], false, 0, lsp, in[k])) return false;
+        for (auto &w : in)
+            if (w.tensor == out.tensor) { err = "output also used as an operand"; return false; }
+        std::set<int> O(s.out.letters.begin(), s.out.letters.end());
+        for (auto &pp : s.perms) {
+            for (int l : pp.first)
+                if (!O.count(l)) { err = "permutation index not in the output"; return false; }
+            for (int l : pp.first)
+                if (lsp[l] != lsp[pp.first[0]]) { err = "permutation mixes occupied and virtual indices"; return false; }
+        }
+        std::vector<Perm> perms = expand_perms(s.perms);
+        double alpha = s.factor * (s.op == -1 ? -1.0 : 1.0);
+        for (auto &w : in) {
+            alpha *= w.sign;
+            if (w.conj && plan.dtype == 0) w.conj = false;   // real integrals: bra<->ket symmetric
+        }
+        double beta = s.op == 0 ? 0.0 : 1.0;
+        BufRef outref = tensor_ref(out.tensor);
+        if (!initialized[out.tensor] && s.op != 0) {
+            if (T.kind == TKind::INTERM) { err = "intermediate accumulated before it is defined"; return false; }
+            Step z;
+            z.kind = StepKind::ZERO;
+            z.stmt = si;
+            z.out = outref;
+            z.zero_elems = T.elems;
+            z.note = "zero " + T.name;
+            plan.steps.push_back(z);
+        }
+        initialized[out.tensor] = true;
+
+        if (in.size() == 1) {
+            std::set<int> A(s.rhs[0].letters.begin(), s.rhs[0].letters.end());
+            if (A != O) { err = "a single-tensor statement must carry exactly the output's indices"; return false; }
+            Step st = accum_step(out, outref, in[0], tensor_ref(in[0].tensor), perms, alpha, beta);
+            st.stmt = si;
+            st.note = "copy " + plan.tensors[in[0].tensor].name + " -> " + T.name;
+            plan.steps.push_back(st);
+            return true;
+        }
+
+        // binary contraction
+        std::set<int> LA(s.rhs[0].letters.begin(), s.rhs[0].letters.end());
+        std::set<int> LB(s.rhs[1].letters.begin(), s.rhs[1].letters.end());
+        std::set<int> K, FA, FB;
+        for (int l : LA) (LB.count(l) ? K : FA).insert(l);
+        for (int l : LB)
+            if (!LA.count(l)) FB.insert(l);
+        for (int l : K)
+            if (O.count(l)) { err = "an index in both operands and in the output (Hadamard product) is not supported"; return false; }
+        std::set<int> F;
+        F.insert(FA.begin(), FA.end());
+        F.insert(FB.begin(), FB.end());
+        if (F != O) { err = "output indices must be exactly the uncontracted operand indices"; return false; }
+
+        // GEMM rows (A side) get the operand whose free indices hold the
+        // output's fastest index, so epilogue stores coalesce along rows.
+        int ia = 0, ib = 1;
+        {
+            int inner = out.idx.back();
+            if (FB.count(inner)) { std::swap(ia, ib); std::swap(FA, FB); }
+        }
+        View A = in[ia], B = in[ib];
+        BufRef aref = tensor_ref(A.tensor), bref = tensor_ref(B.tensor);
+        int64_t Mx = 1, Nx = 1, Kx = 1;
+        for (int l : FA) Mx *= ext_of(A, l);
+        for (int l : FB) Nx *= ext_of(B, l);
+        for (int l : K) Kx *= ext_of(A, l);
+        const double flops = 2.0 * (double)Mx * (double)Nx * (double)Kx;
+        scratch_need = 0;
+        const bool use_mixed = plan.precision != 0 && (mixed_all || flops >= 4.0e9);
+
+        Step g;
+        g.kind = StepKind::GEMM;
+        g.stmt = si;
+        g.flops = flops;
+        g.note = plan.tensors[A.tensor].name + "*" + plan.tensors[B.tensor].name + " -> " + T.name;
+        std::vector<int> fa_order, fb_order, k_order;
+
+        if (use_mixed) {
+            // the split kernels read any strided view: no permutes on this route
+            fa_order = fusable(A, FA).order;
+            fb_order = fusable(B, FB).order;
+            k_order = fusable(A, K).order;
+            g.mixed = true;
+        } else {
+            Fuse fa = fusable(A, FA), ka = fusable(A, K), fb = fusable(B, FB), kb = fusable(B, K);
+            bool a_ok = fa.ok && ka.ok, b_ok = fb.ok && kb.ok;
+            bool match = a_ok && b_ok && same_order(A, ka.order, B, kb.order);
+            bool perm_a = false, perm_b = false;
+            std::vector<int> korder = ka.order;
+            if (!match) {
+                if (a_ok && (!b_ok || view_elems(B) <= view_elems(A))) { perm_b = true; korder = ka.order; }
+                else if (b_ok) { perm_a = true; korder = kb.order; }
+                else { perm_a = perm_b = true; korder = ka.order; }
+            }
+            auto do_perm = [&](View &X, BufRef &xref, const std::vector<int> &forder) {
+                std::vector<int> ord = forder;
+                ord.insert(ord.end(), korder.begin(), korder.end());
+                View w = contiguous_view(ord, X);
+                BufRef r = scratch(view_elems(w) * 8);
+                Step p = accum_step(w, r, X, xref, std::vector<Perm>(1, Perm{1.0, {}}), 1.0, 0.0);
+                p.stmt = si;
+                p.note = "permute " + plan.tensors[X.tensor].name;
+                plan.steps.push_back(p);
+                w.tensor = X.tensor;
+                w.sign = X.sign;
+                X = w;
+                xref = r;
+            };
+            if (perm_a) do_perm(A, aref, fa.order);
+            if (perm_b) do_perm(B, bref, fb.order);
+            Fuse fa2 = fusable(A, FA), ka2 = fusable(A, K), fb2 = fusable(B, FB), kb2 = fusable(B, K);
+            if (!(fa2.ok && ka2.ok && fb2.ok && kb2.ok && same_order(A, ka2.order, B, kb2.order))) {
+                err = "internal: operands not GEMM-ready after permutes";
+                return false;
+            }
+            fa_order = fa2.order;
+            fb_order = fb2.order;
+            k_order = ka2.order;
+            g.gemm.M = fa2.extent;
+            g.gemm.N = fb2.extent;
+            g.gemm.K = ka2.extent;
+            g.gemm.sAm = g.gemm.M == 1 ? 1 : fa2.stride;
+            g.gemm.sAk = g.gemm.K == 1 ? 1 : ka2.stride;
+            g.gemm.sBk = g.gemm.K == 1 ? 1 : kb2.stride;
+            g.gemm.sBn = g.gemm.N == 1 ? 1 : fb2.stride;
+            if (!(g.gemm.sAm == 1 || g.gemm.sAk == 1) || !(g.gemm.sBk == 1 || g.gemm.sBn == 1)) {
+                err = "internal: GEMM operand without a unit stride";
+                return false;
+            }
+        }
+
+        // output: direct (generalised strides) or scratch + antisymmetrising epilogue
+        const bool direct = perms.size() == 1 && perms[0].sigma.empty();
+        View Cv;
+        BufRef cref;
+        double galpha = alpha, gbeta = beta;
+        if (direct) {
+            Cv = out;
+            cref = outref;
+        } else {
+            // scratch [FB][FA]: the GEMM's row index (A side) is the fastest
+            std::vector<int> ord = fb_order;
+            ord.insert(ord.end(), fa_order.begin(), fa_order.end());
+            Cv = contiguous_view(ord, A, &B);
+            cref = scratch(view_elems(Cv) * 8);
+            gbeta = 0.0;
+        }
+        Grp cm = make_grp(fa_order, A, Cv), cn = make_grp(fb_order, B, Cv);
+        if (!err.empty()) return false;
+        g.out = cref;
+        g.a = aref;
+        g.b = bref;
+        if (!g.mixed) {
+            g.gemm.cm = cm;
+            g.gemm.cn = cn;
+            g.gemm.alpha = galpha;
+            g.gemm.beta = gbeta;
+        } else {
+            const int np = plan.precision == 3 ? 3 : 2;
+            TcGemmDesc &t = g.tc;
+            t.M = Mx;
+            t.N = Nx;
+            t.Mp = align_up(Mx, 128);
+            t.Np = align_up(Nx, 256);
+            t.Kp = align_up(Kx, 64);
+            t.nplanes_a = t.nplanes_b = np;
+            if (np == 2) {
+                const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+                t.nprod = 3;
+                for (int k = 0; k < 3; k++) { t.prod_a[k] = pa[k]; t.prod_b[k] = pb[k]; }
+            } else {
+                const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+                t.nprod = 6;
+                for (int k = 0; k < 6; k++) { t.prod_a[k] = pa[k]; t.prod_b[k] = pb[k]; }
+            }
+            t.cm = cm;
+            t.cn = cn;
+            t.alpha = galpha;
+            t.beta = gbeta;
+            SplitDesc &sa = g.split_a;
+            sa.R = Mx; sa.K = Kx; sa.Rp = t.Mp; sa.Kp = t.Kp; sa.nplanes = np;
+            sa.gr = make_grp(fa_order, A, A);
+            sa.gk = make_grp(k_order, A, A);
+            SplitDesc &sb = g.split_b;
+            sb.R = Nx; sb.K = Kx; sb.Rp = t.Np; sb.Kp = t.Kp; sb.nplanes = np;
+            sb.gr = make_grp(fb_order, B, B);
+            sb.gk = make_grp(k_order, B, B);
+            g.a_static = plan.tensors[A.tensor].kind == TKind::INTEGRAL;
+            g.b_static = plan.tensors[B.tensor].kind == TKind::INTEGRAL;
+            const int64_t bytes_a = t.Mp * t.Kp * 2 * np, bytes_b = t.Np * t.Kp * 2 * np;
+            if (g.a_static) { g.planes_a_off = cache_need; cache_need += align_up(bytes_a); }
+            else { g.planes_a_off = scratch(bytes_a).off; }
+            if (g.b_static) { g.planes_b_off = cache_need; cache_need += align_up(bytes_b); }
+            else { g.planes_b_off = scratch(bytes_b).off; }
+            plan.flops_mixed += flops;
+        }
+        plan.flops += flops;
+        plan.steps.push_back(g);
+        if (!direct) {
+            Step e = accum_step(out, outref, Cv, cref, perms, 1.0, beta);   // alpha went into the GEMM
+            e.stmt = si;
+            e.note = "antisymmetrise -> " + T.name;
+            plan.steps.push_back(e);
+        }
+        return true;
+    }
+};
+
+}  // namespace
+
+bool build_plan(const std::string &text, int o, int v, int dtype, int precision, Plan &plan, std::string &err) {
+    plan = Plan();
+    plan.o = o;
+    plan.v = v;
+    plan.dtype = dtype;
+    plan.precision = precision >= 100 ? precision - 100 : precision;
+    Planner P(plan);
+    P.mixed_all = precision >= 100;
+    std::istringstream in(text);
+    std::string line;
+    int lineno = 0;
+    int64_t max_scratch = 0;
+    while (std::getline(in, line)) {
+        lineno++;
+        size_t h = line.find('#');
+        if (h != std::string::npos) line = line.substr(0, h);
+        bool blank = true;
+        for (char c : line)
+            if (!std::isspace((unsigned char)c)) blank = false;
+        if (blank) continue;
+        Stmt st;
+        st.line = lineno;
+        std::vector<std::string> tokens;
+        std::vector<char> spaces;
+        std::string e;
+        if (!parse_stmt(line, st, tokens, spaces, e)) {
+            err = "line " + std::to_string(lineno) + ": " + e;
+            return false;
+        }
+        int si = (int)plan.stmt_text.size();
+        plan.stmt_text.push_back(line);
+        if (!P.plan_stmt(st, spaces, si)) {
+            err = "line " + std::to_string(lineno) + ": " + P.err;
+            return false;
+        }
+        max_scratch = std::max(max_scratch, P.scratch_need);
+    }
+    if (plan.stmt_text.empty()) { err = "empty contraction list"; return false; }
+    // workspace: [status word][intermediates][scratch arena][static plane cache]
+    plan.flags_off = 0;
+    int64_t off = P.interm_need;
+    plan.interm_bytes = off;
+    plan.scratch_off = off;
+    plan.scratch_bytes = max_scratch;
+    off += max_scratch;
+    plan.cache_off = off;
+    plan.cache_bytes = P.cache_need;
+    off += P.cache_need;
+    plan.ws_bytes = off;
+    for (auto &st : plan.steps) {
+        for (BufRef *r : {&st.out, &st.a, &st.b})
+            if (r->where == BufRef::WS && r->slot == 1) { r->off += plan.scratch_off; r->slot = 0; }
+        if (st.mixed) {
+            st.planes_a_off += st.a_static ? plan.cache_off : plan.scratch_off;
+            st.planes_b_off += st.b_static ? plan.cache_off : plan.scratch_off;
+        }
+    }
+    return true;
+}
+
+static void grp_json(std::ostringstream &os, const Grp &g) {
+    os << "{\"ext\":[";
+    for (int d = 0; d < g.nd; d++) os << (d ? "," : "") << g.ext[d];
+    os << "],\"str\":[";
+    for (int d = 0; d < g.nd; d++) os << (d ? "," : "") << g.str[d];
+    os << "]}";
+}
+
+std::string describe_plan(const Plan &plan) {
+    std::ostringstream os;
+    os.precision(17);
+    os << "{\"o\":" << plan.o << ",\"v\":" << plan.v << ",\"precision\":" << plan.precision
+       << ",\"workspace_bytes\":" << plan.ws_bytes << ",\"flops\":" << plan.flops
+       << ",\"flops_mixed\":" << plan.flops_mixed << ",\"tensors\":[";
+    for (size_t k = 0; k < plan.tensors.size(); k++) {
+        const Tensor &t = plan.tensors[k];
+        os << (k ? "," : "") << "{\"name\":\"" << t.name << "\",\"spaces\":\""
+           << std::string(t.spaces.begin(), t.spaces.end()) << "\",\"elems\":" << t.elems << "}";
+    }
+    os << "],\"steps\":[";
+    for (size_t k = 0; k < plan.steps.size(); k++) {
+        const Step &s = plan.steps[k];
+        os << (k ? "," : "") << "{\"stmt\":" << s.stmt << ",\"kind\":\""
+           << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : "gemm_f64")
+                                        : s.kind == StepKind::ACCUM ? "accum" : "zero")
+           << "\",\"note\":\"" << s.note << "\"";
+        if (s.kind == StepKind::GEMM && !s.mixed) {
+            os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
+               << ",\"sAm\":" << s.gemm.sAm << ",\"sAk\":" << s.gemm.sAk << ",\"sBk\":" << s.gemm.sBk
+               << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta << ",\"cm\":";
+            grp_json(os, s.gemm.cm);
+            os << ",\"cn\":";
+            grp_json(os, s.gemm.cn);
+        } else if (s.kind == StepKind::GEMM) {
+            os << ",\"M\":" << s.tc.M << ",\"N\":" << s.tc.N << ",\"K\":" << s.split_a.K << ",\"flops\":" << s.flops
+               << ",\"products\":" << s.tc.nprod << ",\"a_static\":" << (s.a_static ? 1 : 0)
+               << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta;
+        } else if (s.kind == StepKind::ACCUM) {
+            os << ",\"elems\":" << s.acc.total << ",\"terms\":" << s.acc.nperm << ",\"alpha\":" << s.acc.alpha
+               << ",\"beta\":" << s.acc.beta;
+        } else {
+            os << ",\"elems\":" << s.zero_elems;
+        }
+        os << "}";
+    }
+    os << "],\"statements\":[";
+    for (size_t k = 0; k < plan.stmt_text.size(); k++) {
+        std::string esc;
+        for (char c : plan.stmt_text[k]) {
+            if (c == '"' || c == '\\') esc += '\\';
+            esc += c;
+        }
+        os << (k ? "," : "") << "\"" << esc << "\"";
+    }
+    os << "]}";
+    return os.str();
+}
+
+}  // namespace ccb

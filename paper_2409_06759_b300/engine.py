@@ -1,0 +1,89 @@
+"""Device-side convenience layer over the C ABI (argument marshalling only).
+
+Allocates device buffers with torch, builds the integral blocks with the
+library's own kernels (cc_build_integrals), and wraps plans, workspaces and the
+solver.  Every arithmetic step runs in libccb300.so.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import (BLOCKS, CC_F64, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
+               cc_integral_block_elems, cc_plan_create, cc_residual, cc_solve, cc_solve_workspace_bytes,
+               load_list)
+
+
+def alloc_ws(nbytes: int, device) -> torch.Tensor:
+    """Workspace buffer (torch's caching allocator returns 512-byte aligned blocks)."""
+    t = torch.empty(max(1, (nbytes + 7) // 8), dtype=torch.float64, device=device)
+    assert t.data_ptr() % 256 == 0
+    return t
+
+
+class DeviceSystem:
+    """Orbital energies and the six integral blocks of one system, on the device."""
+
+    def __init__(self, o: int, v: int, eps_occ, eps_vir, B, device="cuda:0", blocks=BLOCKS, stream=None):
+        self.o, self.v, self.device = o, v, torch.device(device)
+        self.f_occ = torch.as_tensor(eps_occ, dtype=torch.float64).to(self.device)
+        self.f_vir = torch.as_tensor(eps_vir, dtype=torch.float64).to(self.device)
+        Bd = torch.as_tensor(B, dtype=torch.float64).to(self.device).contiguous()
+        L = Bd.shape[0]
+        elems = cc_integral_block_elems(o, v)
+        self.blocks = {k: torch.empty(elems[k], dtype=torch.float64, device=self.device) for k in blocks}
+        ws = alloc_ws(cc_build_integrals_workspace_bytes(o, v, L), self.device)
+        cc_build_integrals(o, v, L, Bd, self.blocks, ws, stream=stream)
+        torch.cuda.synchronize(self.device)
+        del ws, Bd
+
+    @classmethod
+    def from_system(cls, sysm, device="cuda:0", scale: float = 1.0, **kw):
+        return cls(sysm.o, sysm.v, sysm.eps_occ, sysm.eps_vir, sysm.B * scale, device=device, **kw)
+
+    def ints(self) -> dict:
+        d = dict(f_occ=self.f_occ, f_vir=self.f_vir)
+        d.update(self.blocks)
+        return d
+
+    def block(self, name: str) -> torch.Tensor:
+        shape = [self.o if c == "o" else self.v for c in name]
+        return self.blocks[name].view(*shape)
+
+
+class Engine:
+    """A plan plus its workspace for one system."""
+
+    def __init__(self, system: DeviceSystem, list_text: str | None = None, precision="fp64",
+                 route_all: bool = False, list_name: str | None = None):
+        if list_text is None:
+            list_text = load_list(list_name or ("ccsd" if precision == "fp64" else "ccsd_vvvv"))
+        self.sys = system
+        self.plan = cc_plan_create(list_text, system.o, system.v, CC_F64, precision, _route_all=route_all)
+        self.ws = alloc_ws(self.plan.workspace_bytes, system.device)
+
+    def residual(self, t1, t2, r1=None, r2=None, stream=None):
+        o, v, dev = self.sys.o, self.sys.v, self.sys.device
+        r1 = torch.empty(o, v, dtype=torch.float64, device=dev) if r1 is None else r1
+        r2 = torch.empty(o, o, v, v, dtype=torch.float64, device=dev) if r2 is None else r2
+        cc_residual(self.plan, self.sys.ints(), t1, t2, r1, r2, self.ws, stream=stream)
+        return r1, r2
+
+    def energy(self, t1, t2, stream=None) -> float:
+        e = torch.zeros(2, dtype=torch.float64, device=self.sys.device)
+        cc_energy(self.plan, self.sys.ints(), t1, t2, e, self.ws, stream=stream)
+        return float(e[0].item())
+
+
+class Solver:
+    """cc_solve with its own workspace (the DIIS history lives there)."""
+
+    def __init__(self, engine: Engine, diis_max: int = 8, refine: Engine | None = None):
+        self.eng, self.refine, self.diis_max = engine, refine, diis_max
+        nb = cc_solve_workspace_bytes(engine.plan, diis_max, refine.plan if refine else None)
+        self.ws = alloc_ws(nb, engine.sys.device)
+
+    def solve(self, t1, t2, max_iter=100, tol=1e-8, resume=False, switch_tol=0.0, verbose=0, stream=None):
+        return cc_solve(self.eng.plan, self.eng.sys.ints(), t1, t2, self.ws, max_iter=max_iter, tol=tol,
+                        diis_max=self.diis_max, resume=resume,
+                        refine_plan=self.refine.plan if self.refine else None, switch_tol=switch_tol,
+                        verbose=verbose, stream=stream)

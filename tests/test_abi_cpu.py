@@ -1,0 +1,110 @@
+"""C-ABI library checks that need no GPU: the .so loads, exports every symbol
+include/cc.h declares, and the parser/planner (host only) behaves."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cc():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2409_06759_b300 as cc
+    return cc
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "cc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(cc):
+    lib = ctypes.CDLL(cc.LIB_PATH)
+    names = header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(cc.EXPORTS) == names
+
+
+def test_version_and_status(cc):
+    assert "sm_103a" in cc.cc_version()
+    assert cc.cc_status_string(0) == "ok"
+    assert cc.cc_status_string(2) == "parse error"
+
+
+@pytest.mark.parametrize("name", ["ccsd", "ccsd_vvvv"])
+def test_plan_ccsd_structure(cc, name):
+    o, v = 40, 200
+    p = cc.cc_plan_create(cc.load_list(name), o, v, precision="fp64")
+    d = p.describe()
+    gemms = [s for s in d["steps"] if s["kind"].startswith("gemm")]
+    assert sum(s["flops"] for s in gemms) == pytest.approx(p.flops)
+    ladder = [s for s in gemms if s["M"] * s["N"] * s["K"] == (v * v) * (o * o) * (v * v)]
+    assert len(ladder) == 1, "one o^2 v^4 ladder GEMM"
+    # the ladder runs as a plain GEMM: no permute or epilogue in its statement
+    st = ladder[0]["stmt"]
+    assert not [s for s in d["steps"] if s["stmt"] == st and s["kind"] == "accum"]
+    assert p.flops < 1.3 * (2 * o**2 * v**4 + 6 * o**3 * v**3 + 10 * o**4 * v**2)
+
+
+def test_plan_mixed_routes_big_gemms(cc):
+    o, v = 40, 200
+    p = cc.cc_plan_create(cc.load_list("ccsd_vvvv"), o, v, precision="bf16x3")
+    d = p.describe()
+    mixed = [s for s in d["steps"] if s["kind"] == "gemm_bf16split"]
+    assert mixed and max(s["flops"] for s in mixed) == 2.0 * o**2 * v**4
+    lad = [s for s in mixed if s["flops"] == 2.0 * o**2 * v**4][0]
+    assert lad["products"] == 3
+    assert lad["a_static"] or lad["b_static"], "the <ab||ef> planes are cached"
+
+
+@pytest.mark.parametrize("text,frag", [
+    ("R2[ijab] = V[ijab] * T2[ijab] * T1[ia]", "binary"),
+    ("R2[ijab] = X[ijab]", "before a defining"),
+    ("R2[ijqb] = V[ijqb]", "neither occupied"),
+    ("R2[ijab] = V[ijab", "bracket"),
+    ("X[ijab] += T2[ijab]", "before a defining"),
+    ("R2[ijab] = T2[ijae] * V[ebcd]", "output indices"),
+    ("R2[ijab] = 0.5 P(ia) T2[ijab]", "mixes occupied"),
+    ("T2[ijab] = V[ijab]", "inputs"),
+])
+def test_parse_errors(cc, text, frag):
+    with pytest.raises(cc.CCError) as ei:
+        cc.cc_plan_create(text, 3, 4)
+    assert frag in str(ei.value)
+    assert "line 1" in str(ei.value)
+
+
+def test_paper_bracket_form_is_accepted(cc):
+    """t[ef][ij] (upper/lower, as printed in the paper) names the same tensor as T2[ijef]."""
+    a = cc.cc_plan_create("R2[ijab] = 0.5 t[ef][ij] * V[ab][ef]", 3, 5).describe()
+    b = cc.cc_plan_create("R2[ijab] = 0.5 T2[ijef] * V[abef]", 3, 5).describe()
+    ga = [s for s in a["steps"] if s["kind"] == "gemm_f64"][0]
+    gb = [s for s in b["steps"] if s["kind"] == "gemm_f64"][0]
+    for k in ("M", "N", "K", "sAm", "sAk", "sBk", "sBn", "alpha"):
+        assert ga[k] == gb[k]
+
+
+def test_integral_block_resolution_signs(cc):
+    """<mb||ej> comes from the ovov block with a minus sign (ket swap)."""
+    d = cc.cc_plan_create("X[mbej] = V[mbej]", 3, 5).describe()
+    acc = [s for s in d["steps"] if s["kind"] == "accum"][0]
+    assert acc["alpha"] == -1.0
+    assert {t["name"] for t in d["tensors"]} >= {"V_ovov"}
+
+
+def test_integral_block_elems(cc):
+    e = cc.cc_integral_block_elems(3, 5)
+    assert e == dict(oooo=81, ooov=135, oovv=225, ovov=225, ovvv=375, vvvv=625)
+
+
+def test_workspace_grows_with_size(cc):
+    small = cc.cc_plan_create(cc.load_list("ccsd"), 4, 8).workspace_bytes
+    big = cc.cc_plan_create(cc.load_list("ccsd"), 8, 16).workspace_bytes
+    assert 0 < small < big
