@@ -97,6 +97,8 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
     if (st != CC_OK) return st;
     char *w = (char *)ws;
     if (!use_cache) pl->cache_filled = false;
+    if (P.flops_mixed > 0 && !pl->cache_filled)   // clear the bounded-wait status word
+        CC_CUDA(cudaMemsetAsync(w + P.flags_off, 0, sizeof(int), s));
     for (const Step &stp : P.steps) {
         switch (stp.kind) {
             case StepKind::ZERO:
@@ -365,7 +367,10 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         if (st != CC_OK) return st;
         CC_CUDA(cudaMemcpyAsync(h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CC_CUDA(cudaMemcpyAsync(h_scal + 4, used_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(h_scal + 5, pws + cur->plan.flags_off, sizeof(int), cudaMemcpyDeviceToHost, s));
         CC_CUDA(cudaStreamSynchronize(s));
+        if (cur->plan.flops_mixed > 0 && *(int *)(h_scal + 5) != 0)
+            return fail(CC_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
         // history bookkeeping of the previous device DIIS solve: drop what it dropped
         if (S.pending_m >= 2) {
             int used = *(int *)(h_scal + 4);

@@ -4,6 +4,7 @@
 //   tc_gemm      tcgen05 GEMM over the plane products, FP32 accumulation in
 //                TMEM, FP64 epilogue into the output
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -77,10 +78,326 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ tcgen05
+// One CTA computes a 128 x BN tile of D = sum_products A_p B_q^T:
+//   warp 0      TMA producer (one elected lane): all A and B planes of a
+//               64-wide K block land in one pipeline stage (SWIZZLE_128B)
+//   warp 1      TMEM allocator + MMA issuer (one lane): tcgen05.mma kind::f16,
+//               bf16 x bf16 -> fp32 accumulator of 128 lanes x BN columns
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, FP64 alpha/beta
+//               update of the output through the mixed-radix addressing
+// Every mbarrier wait is bounded (clock64 budget); on expiry the CTA sets
+// err_flag, stops issuing work, waits (bounded) for what it already issued,
+// frees its TMEM and returns.
+namespace tc {
+
+constexpr int BM = 128, BK = 64;
+constexpr long long kWaitBudget = 4000000000LL;   // cycles (~2 s at 2 GHz)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// false when the budget runs out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitBudget) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major bf16 tile written by TMA with
+// SWIZZLE_128B: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;                     // descriptor version of tcgen05
+    d |= (uint64_t)2 << 61;                     // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int NP, int BN, int STAGES>
+struct Cfg {
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 1024 /*barriers, offsets*/ + BN * 8;
+    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+template <int NP, int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const TcGemmDesc d, double *__restrict__ C, int *err_flag) {
+    using G = Cfg<NP, BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *tiles = smem;
+    uint64_t *full = (uint64_t *)(smem + STAGES * G::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accum = empty + STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    volatile int *consumed = abort_flag + 1;
+    int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (int)(d.Np / BN);
+    const int tile = blockIdx.x;
+    const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
+    const int64_t n0 = (int64_t)(tile % n_tiles) * BN;
+    const int kblocks = (int)(d.Kp / BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, G::TMEM_COLS);
+        tmem_relinquish();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < kblocks; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t *st = tiles + s * G::STAGE_BYTES;
+                mbar_expect_tx(&full[s], G::STAGE_BYTES);
+                for (int p = 0; p < NP; p++)
+                    tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], kb * BK, (int)(p * d.Mp + m0));
+                for (int q = 0; q < NP; q++)
+                    tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BK,
+                                (int)(q * d.Np + n0));
+                issued = kb + 1;
+            }
+            if (*abort_flag) {
+                // let the copies already in flight land before the CTA exits
+                for (int kb = *consumed; kb < issued; kb++) mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
+                atomicOr(err_flag, 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            for (int kb = 0; kb < kblocks; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&full[s], ph)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t st = smem_u32(tiles + s * G::STAGE_BYTES);
+                for (int pr = 0; pr < d.nprod; pr++) {
+                    const uint32_t a0 = st + d.prod_a[pr] * G::A_BYTES;
+                    const uint32_t b0 = st + NP * G::A_BYTES + d.prod_b[pr] * G::B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++)
+                        mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                 (kb | pr | kk) != 0);
+                }
+                mma_commit(&empty[s]);   // frees the stage when these MMAs complete
+                *consumed = kb + 1;
+            }
+            mma_commit(accum);           // accumulator complete (or, on abort, all issued MMAs done)
+        }
+        __syncwarp();
+    } else {
+        // epilogue warpgroup: warp w reads TMEM lanes 32*(w%4) .. +31
+        const int q = warp & 3;
+        const int et = threadIdx.x - 64;                 // 0..127
+        for (int c = et; c < BN; c += 128) {
+            const int64_t n = n0 + c;
+            coloff[c] = n < d.N ? grp_off(d.cn, n) : -1;
+        }
+        const int64_t m = m0 + q * 32 + lane;
+        const bool mok = m < d.M;
+        const int64_t roff = mok ? grp_off(d.cm, m) : 0;
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // coloff visible to the epilogue warps
+        bool ok = mbar_wait(accum, 0);
+        fence_after();
+        ok = __all_sync(0xffffffffu, ok && !*abort_flag);   // tcgen05.ld below is warp-collective
+        if (!ok) {
+            *abort_flag = 1;
+            if (lane == 0) atomicOr(err_flag, 1);
+        } else {
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                tmem_ld_wait();
+                if (mok) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int64_t co = coloff[c0 + j];
+                        if (co < 0) continue;
+                        double *p = C + roff + co;
+                        double val = d.alpha * (double)__uint_as_float(r[j]);
+                        if (d.beta != 0.0) val += d.beta * *p;
+                        *p = val;
+                    }
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, G::TMEM_COLS);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2-D map over planes stacked as rows: [nplanes * rows][Kp] bf16, box {64, box_rows}
+static bool make_map(CUtensorMap *map, const void *base, int64_t rows_total, int64_t Kp, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows_total};
+    cuuint64_t strides[1] = {(cuuint64_t)(Kp * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int NP, int BN, int STAGES>
+static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B, double *C, int *err, cudaStream_t s) {
+    using G = Cfg<NP, BN, STAGES>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NP, BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (d.Np % BN || d.Mp % BM || d.Kp % BK) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
+        return cudaErrorInvalidValue;
+    const int64_t tiles = (d.Mp / BM) * (d.Np / BN);
+    if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    tc_gemm_kernel<NP, BN, STAGES><<<(unsigned)tiles, 192, G::SMEM, s>>>(ma, mb, d, C, err);
+    return cudaGetLastError();
+}
+
+}  // namespace tc
+
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C, int *err_flag,
                            cudaStream_t s) {
-    (void)d; (void)Aplanes; (void)Bplanes; (void)C; (void)err_flag; (void)s;
-    return cudaErrorNotSupported;
+    if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+    if (d.nplanes_a != d.nplanes_b || d.nprod < 1 || d.nprod > 8) return cudaErrorInvalidValue;
+    if (((uintptr_t)Aplanes & 1023) || ((uintptr_t)Bplanes & 1023) || d.Kp < 64) {
+        // TMA needs 16-byte aligned bases; the planner hands out 256-byte aligned workspace
+        if (((uintptr_t)Aplanes & 15) || ((uintptr_t)Bplanes & 15)) return cudaErrorMisalignedAddress;
+    }
+    if (d.nplanes_a == 2) return tc::launch_cfg<2, 256, 2>(d, Aplanes, Bplanes, C, err_flag, s);
+    if (d.nplanes_a == 3) return tc::launch_cfg<3, 128, 2>(d, Aplanes, Bplanes, C, err_flag, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace ccb

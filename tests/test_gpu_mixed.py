@@ -1,0 +1,106 @@
+"""Split-bf16 tensor-core route (tcgen05) vs FP64 references.
+
+Tolerance derived from the arithmetic: with two bf16 planes per operand the
+dropped lo*lo product and the plane rounding leave at most ~3*2^-16 |a||b|
+per product, and FP32 accumulation over K adds at most K*2^-24 sum|a||b|
+(first-order worst case).  So every element must satisfy
+    |err| <= nterms * |factor| * (3*2^-16 + K*2^-24) * max sum_k |a_ik||b_kj|.
+With three planes (six products) the first term drops to ~3*2^-24.
+"""
+import numpy as np
+import pytest
+import torch
+
+import ccinputs
+import list_exec
+import oracle
+from gpu_util import DEV, oracle_V, small_case, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2409_06759_b300 as cc
+    from paper_2409_06759_b300 import engine
+    return cc, engine
+
+
+STATEMENTS = [
+    # (text, K as a function of (o, v), number of permutation terms)
+    ("R2[ijab] = 0.5 T2[ijef] * V[abef]", lambda o, v: v * v, 1),
+    ("R2[ijab] = P(ij) P(ab) T2[imae] * V[mbej]", lambda o, v: o * v, 4),
+    ("R1[ia] = -0.5 T2[imef] * V[maef]", lambda o, v: o * v * v, 1),
+    ("R2[ijab] = 0.5 T2[mnab] * V[mnij]", lambda o, v: o * o, 1),
+]
+
+
+def _abs_bound(text, o, v, eps, V, t1, t2):
+    """max_ij sum_k |a_ik||b_kj| of the statement's plain contraction."""
+    plain = text.split("=", 1)[0] + "= " + " ".join(w for w in text.split("=", 1)[1].split()
+                                                      if not w.startswith("P(") and not w.lstrip("-").replace(".", "").isdigit())
+    z = np.zeros_like(eps)
+    a1, a2 = list_exec.run_list(plain, o, v, z, np.abs(V), np.abs(t1), np.abs(t2))
+    return max(np.abs(a1).max(), np.abs(a2).max())
+
+
+@pytest.mark.parametrize("prec,first", [("bf16x3", 3 * 2.0 ** -16), ("bf16x6", 3 * 2.0 ** -24)])
+@pytest.mark.parametrize("o,v", [(3, 20), (5, 70), (2, 9), (7, 33)])
+@pytest.mark.parametrize("k", range(len(STATEMENTS)))
+def test_split_gemm_statement(cc, prec, first, o, v, k):
+    ccm, engine = cc
+    text, kfun, nterms = STATEMENTS[k]
+    s, B, t1, t2 = small_case(o, v, 100 + k, L=8, scale=6.0, tscale=0.1)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
+    eng = engine.Engine(dsys, list_text=text, precision=prec, route_all=True)
+    assert any(st["kind"] == "gemm_bf16split" for st in eng.plan.describe()["steps"])
+    r1 = torch.zeros(o, v, dtype=torch.float64, device=DEV)
+    r2 = torch.zeros(o, o, v, v, dtype=torch.float64, device=DEV)
+    ccm.cc_residual(eng.plan, dsys.ints(), to_dev(t1), to_dev(t2), r1, r2, eng.ws)
+    torch.cuda.synchronize()
+    V = oracle_V(o, v, B)
+    e1, e2 = list_exec.run_list(text, o, v, s.eps, V, t1, t2)
+    fac = abs(float(text.split("=", 1)[1].split()[0])) if text.split("=", 1)[1].split()[0][0] in "-0123456789" else 1.0
+    tol = nterms * fac * (first + kfun(o, v) * 2.0 ** -24) * _abs_bound(text, o, v, s.eps, V, t1, t2) + 1e-15
+    err = max(np.abs(r1.cpu().numpy() - e1).max(), np.abs(r2.cpu().numpy() - e2).max())
+    assert err <= tol, (err, tol)
+    mag = max(np.abs(e1).max(), np.abs(e2).max())
+    assert err <= 1e-3 * mag
+
+
+@pytest.mark.parametrize("prec,rel", [("bf16x3", 2e-4), ("bf16x6", 2e-6)])
+@pytest.mark.parametrize("o,v", [(3, 8), (6, 30)])
+def test_mixed_full_residual_vs_oracle(cc, prec, rel, o, v):
+    _, engine = cc
+    s, B, t1, t2 = small_case(o, v, 7, L=8, scale=6.0, tscale=0.05)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
+    eng = engine.Engine(dsys, list_name="ccsd_vvvv", precision=prec, route_all=True)
+    r1, r2 = eng.residual(to_dev(t1), to_dev(t2))
+    torch.cuda.synchronize()
+    o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
+    d = np.sqrt(np.sum((r1.cpu().numpy() - o1) ** 2) + np.sum((r2.cpu().numpy() - o2) ** 2))
+    ref = np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
+    assert d <= rel * ref
+
+
+def test_mixed_solve_small_config(cc):
+    """o=10, v=40: split-bf16 iterations alone reach |dE| < 1e-6 Eh; with the FP64
+    refine plan the converged energy matches the oracle to 1e-10 Eh."""
+    _, engine = cc
+    s = ccinputs.make_system(**ccinputs.CONFIG_SMALL)
+    o, v = s.o, s.v
+    ref = oracle.ccsd_solve(o, v, s.eps, oracle_V(o, v, s.B), tol=1e-8, maxiter=60)
+    dsys = engine.DeviceSystem.from_system(s, device=DEV)
+    mixed = engine.Engine(dsys, list_name="ccsd_vvvv", precision="bf16x3", route_all=True)
+    fp64 = engine.Engine(dsys, list_name="ccsd")
+    z = lambda: (torch.zeros(o, v, dtype=torch.float64, device=DEV),
+                 torch.zeros(o, o, v, v, dtype=torch.float64, device=DEV))
+    a1, a2 = z()
+    alone = engine.Solver(mixed).solve(a1, a2, max_iter=40, tol=1e-8)
+    assert abs(alone.energy - ref["energy"]) < 1e-6
+    b1, b2 = z()
+    res = engine.Solver(mixed, refine=fp64).solve(b1, b2, max_iter=60, tol=1e-8, switch_tol=1e-6)
+    assert res.converged and res.switched_at >= 0
+    assert abs(res.energy - ref["energy"]) < 1e-10
