@@ -804,7 +804,9 @@ std::string describe_plan(const Plan &plan) {
         } else if (s.kind == StepKind::GEMM) {
             os << ",\"M\":" << s.tc.M << ",\"N\":" << s.tc.N << ",\"K\":" << s.split_a.K << ",\"flops\":" << s.flops
                << ",\"products\":" << s.tc.nprod << ",\"a_static\":" << (s.a_static ? 1 : 0)
-               << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta;
+               << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta
+               << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp
+               << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off;
         } else if (s.kind == StepKind::ACCUM) {
             os << ",\"elems\":" << s.acc.total << ",\"terms\":" << s.acc.nperm << ",\"alpha\":" << s.acc.alpha
                << ",\"beta\":" << s.acc.beta;

@@ -121,9 +121,10 @@ def run_list(text: str, o: int, v: int, eps, V, t1, t2):
             tgt[oname] = tgt.get(oname, np.zeros_like(val)) + val
         else:
             tgt[oname] = tgt.get(oname, np.zeros_like(val)) - val
-    r1 = out.get("R1", np.zeros((o, v)))
-    r2 = out.get("R2", np.zeros((o, o, v, v)))
+    # the engine adds -D*t to the residuals the list writes (and only to those)
     eo, ev = eps[:o], eps[o:]
     d1 = eo[:, None] - ev[None, :]
     d2 = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
-    return r1 - d1 * t1, r2 - d2 * t2
+    r1 = out["R1"] - d1 * t1 if "R1" in out else np.zeros((o, v))
+    r2 = out["R2"] - d2 * t2 if "R2" in out else np.zeros((o, o, v, v))
+    return r1, r2
