@@ -10,6 +10,10 @@ Parity pins (all in ``tests/test_oracle_pins.py``):
 * converged CCSD energy vs FCI for two electrons;
 * first-iteration energy vs the MP2 closed form computed in determinant space;
 * antisymmetry of the residual; lambda-scaling of the energy.
+
+``ccsd_r2_sample`` evaluates selected residual elements of large systems from
+B directly (same equations); it is pinned against the brute force and the
+full residual at small sizes.
 """
 from __future__ import annotations
 
@@ -46,6 +50,8 @@ def lib():
         L.orc_ccsd_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double,
                                      ctypes.c_int, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int)]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_ccsd_r2_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), dp]
         _lib = L
     return _lib
 
@@ -77,6 +83,22 @@ def ccsd_residual(o, v, eps, V, t1, t2):
     if lib().orc_ccsd_residual(o, v, _p(eps), _p(V), _p(t1), _p(t2), _p(r1), _p(r2)) != 0:
         raise MemoryError("oracle residual failed")
     return r1, r2
+
+
+def ccsd_r2_sample(o, v, B, eps, t1, t2, idx):
+    """R2[i,j,a,b] for each row (i, j, a, b) of idx, integrals formed from B on
+    demand (large systems)."""
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    t1 = np.ascontiguousarray(t1, dtype=np.float64)
+    t2 = np.ascontiguousarray(t2, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 4)
+    out = np.empty(idx.shape[0])
+    rc = lib().orc_ccsd_r2_sample(o, v, B.shape[0], _p(B), _p(eps), _p(t1), _p(t2), idx.shape[0],
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle sampled residual failed")
+    return out
 
 
 def ccsd_energy(o, v, V, t1, t2) -> float:

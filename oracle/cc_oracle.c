@@ -463,3 +463,172 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* --------------------------------------------------------- sampled R2 elements
+ *
+ * Selected elements R_ij^ab of the same CCSD residual (same equations as
+ * orc_ccsd_residual), for systems whose n^4 integral tensor does not fit:
+ * integrals are formed from B on demand, <pq||rs> = sum_L B_pr B_qs - B_ps B_qr.
+ * Built once: the oovv, ooov and ovvv blocks, tau, tau~ and the one-particle
+ * intermediates.  Per sample: the W_mnij(.,.,i,j), W_abef(a,b,.,.) and
+ * W_mbej(.,d,.,q) slices that element needs.  OpenMP over samples.
+ */
+typedef struct {
+    int o, v, n, L;
+    const double *Bt;                 /* [p][r][L] */
+    double *oovv, *ooov, *ovvv;       /* <mn||ef>, <mn||ie>, <ma||ef> */
+} vsrc;
+
+static double vint(const vsrc *S, int p, int q, int r, int s)
+{
+    const double *a = S->Bt + ((ll)p * S->n + r) * S->L, *b = S->Bt + ((ll)q * S->n + s) * S->L;
+    const double *c = S->Bt + ((ll)p * S->n + s) * S->L, *d = S->Bt + ((ll)q * S->n + r) * S->L;
+    double x = 0.0;
+    for (int l = 0; l < S->L; l++) x += a[l] * b[l] - c[l] * d[l];
+    return x;
+}
+
+#define OOVV(m, nn, e, f) S.oovv[(((ll)(m) * o + (nn)) * v + (e)) * v + (f)]
+#define OOOV(m, nn, i, e) S.ooov[(((ll)(m) * o + (nn)) * o + (i)) * v + (e)]
+#define OVVV(m, a, e, f) S.ovvv[(((ll)(m) * v + (a)) * v + (e)) * v + (f)]
+
+/* X_pqcd = sum_me ( t_pm^ce W_mdeq - t_p^e t_m^c <md||eq> ) for the ring term */
+static double ring_x(const vsrc *Sp, const double *t1, const double *t2, int p, int q, int c, int dd)
+{
+    const vsrc S = *Sp;
+    const int o = S.o, v = S.v;
+    double x = 0.0;
+    for (int m = 0; m < o; m++)
+        for (int e = 0; e < v; e++) {
+            /* W_mbej with b = dd, j = q */
+            double w = vint(&S, m, o + dd, o + e, q);
+            for (int f = 0; f < v; f++) w += T1(q, f) * OVVV(m, dd, e, f);
+            for (int nn = 0; nn < o; nn++) w += T1(nn, dd) * OOOV(m, nn, q, e);   /* -t_n^b <mn||ej> */
+            for (int nn = 0; nn < o; nn++)
+                for (int f = 0; f < v; f++)
+                    w -= (0.5 * T2(q, nn, f, dd) + T1(q, f) * T1(nn, dd)) * OOVV(m, nn, e, f);
+            x += T2(p, m, c, e) * w - T1(p, e) * T1(m, c) * vint(&S, m, o + dd, o + e, q);
+        }
+    return x;
+}
+
+int orc_ccsd_r2_sample(int o, int v, int L, const double *B, const double *eps, const double *t1,
+                       const double *t2, int ns, const int *idx, double *out)
+{
+    const ll n = o + v;
+    vsrc S;
+    S.o = o; S.v = v; S.n = (int)n; S.L = L;
+    double *Bt = malloc(sizeof(double) * n * n * L);
+    S.oovv = malloc(sizeof(double) * (ll)o * o * v * v);
+    S.ooov = malloc(sizeof(double) * (ll)o * o * o * v);
+    S.ovvv = malloc(sizeof(double) * (ll)o * v * v * v);
+    double *tau = malloc(sizeof(double) * (ll)o * o * v * v), *taut = malloc(sizeof(double) * (ll)o * o * v * v);
+    double *Fae = malloc(sizeof(double) * v * v), *Fmi = malloc(sizeof(double) * o * o);
+    double *Fme = malloc(sizeof(double) * o * v), *Fbe2 = malloc(sizeof(double) * v * v);
+    double *Fmj2 = malloc(sizeof(double) * o * o);
+    if (!Bt || !S.oovv || !S.ooov || !S.ovvv || !tau || !taut || !Fae || !Fmi || !Fme || !Fbe2 || !Fmj2) return 1;
+#pragma omp parallel for
+    for (ll pr = 0; pr < n * n; pr++)
+        for (int l = 0; l < L; l++) Bt[pr * L + l] = B[(ll)l * n * n + pr];
+    S.Bt = Bt;
+#pragma omp parallel for collapse(2)
+    for (int m = 0; m < o; m++)
+        for (int nn = 0; nn < o; nn++) {
+            for (int e = 0; e < v; e++)
+                for (int f = 0; f < v; f++) OOVV(m, nn, e, f) = vint(&S, m, nn, o + e, o + f);
+            for (int i = 0; i < o; i++)
+                for (int e = 0; e < v; e++) OOOV(m, nn, i, e) = vint(&S, m, nn, i, o + e);
+        }
+#pragma omp parallel for collapse(2)
+    for (int m = 0; m < o; m++)
+        for (int a = 0; a < v; a++)
+            for (int e = 0; e < v; e++)
+                for (int f = 0; f < v; f++) OVVV(m, a, e, f) = vint(&S, m, o + a, o + e, o + f);
+    for (int i = 0; i < o; i++)
+        for (int j = 0; j < o; j++)
+            for (int a = 0; a < v; a++)
+                for (int b = 0; b < v; b++) {
+                    double p = T1(i, a) * T1(j, b) - T1(i, b) * T1(j, a);
+                    O4(tau, i, j, a, b) = T2(i, j, a, b) + p;
+                    O4(taut, i, j, a, b) = T2(i, j, a, b) + 0.5 * p;
+                }
+#pragma omp parallel for
+    for (int a = 0; a < v; a++)
+        for (int e = 0; e < v; e++) {
+            double s = 0.0;
+            for (int m = 0; m < o; m++)
+                for (int f = 0; f < v; f++) s += T1(m, f) * OVVV(m, a, f, e);
+            for (int m = 0; m < o; m++)
+                for (int nn = 0; nn < o; nn++)
+                    for (int f = 0; f < v; f++) s -= 0.5 * O4(taut, m, nn, a, f) * OOVV(m, nn, e, f);
+            Fae[a * v + e] = s;
+        }
+    for (int m = 0; m < o; m++)
+        for (int i = 0; i < o; i++) {
+            double s = 0.0;
+            for (int e = 0; e < v; e++)
+                for (int nn = 0; nn < o; nn++) s += T1(nn, e) * OOOV(m, nn, i, e);
+            for (int nn = 0; nn < o; nn++)
+                for (int e = 0; e < v; e++)
+                    for (int f = 0; f < v; f++) s += 0.5 * O4(taut, i, nn, e, f) * OOVV(m, nn, e, f);
+            Fmi[m * o + i] = s;
+        }
+    for (int m = 0; m < o; m++)
+        for (int e = 0; e < v; e++) {
+            double s = 0.0;
+            for (int nn = 0; nn < o; nn++)
+                for (int f = 0; f < v; f++) s += T1(nn, f) * OOVV(m, nn, e, f);
+            Fme[m * v + e] = s;
+        }
+    for (int b = 0; b < v; b++)
+        for (int e = 0; e < v; e++) {
+            double s = Fae[b * v + e];
+            for (int m = 0; m < o; m++) s -= 0.5 * T1(m, b) * Fme[m * v + e];
+            Fbe2[b * v + e] = s;
+        }
+    for (int m = 0; m < o; m++)
+        for (int j = 0; j < o; j++) {
+            double s = Fmi[m * o + j];
+            for (int e = 0; e < v; e++) s += 0.5 * T1(j, e) * Fme[m * v + e];
+            Fmj2[m * o + j] = s;
+        }
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < ns; k++) {
+        const int i = idx[4 * k], j = idx[4 * k + 1], a = idx[4 * k + 2], b = idx[4 * k + 3];
+        double r = OOVV(i, j, a, b) - (eps[i] + eps[j] - eps[o + a] - eps[o + b]) * T2(i, j, a, b);
+        /* P(ab) sum_e t_ij^ae Fbe2_be  and  -P(ij) sum_m t_im^ab Fmj2_mj */
+        for (int e = 0; e < v; e++) r += T2(i, j, a, e) * Fbe2[b * v + e] - T2(i, j, b, e) * Fbe2[a * v + e];
+        for (int m = 0; m < o; m++) r -= T2(i, m, a, b) * Fmj2[m * o + j] - T2(j, m, a, b) * Fmj2[m * o + i];
+        /* 1/2 sum_mn tau_mn^ab W_mnij */
+        for (int m = 0; m < o; m++)
+            for (int nn = 0; nn < o; nn++) {
+                double w = vint(&S, m, nn, i, j);
+                for (int e = 0; e < v; e++) w += T1(j, e) * OOOV(m, nn, i, e) - T1(i, e) * OOOV(m, nn, j, e);
+                for (int e = 0; e < v; e++)
+                    for (int f = 0; f < v; f++) w += 0.25 * O4(tau, i, j, e, f) * OOVV(m, nn, e, f);
+                r += 0.5 * O4(tau, m, nn, a, b) * w;
+            }
+        /* 1/2 sum_ef tau_ij^ef W_abef, <am||ef> = -<ma||ef> */
+        for (int e = 0; e < v; e++)
+            for (int f = 0; f < v; f++) {
+                double w = vint(&S, o + a, o + b, o + e, o + f);
+                for (int m = 0; m < o; m++) w -= -T1(m, b) * OVVV(m, a, e, f) + T1(m, a) * OVVV(m, b, e, f);
+                for (int m = 0; m < o; m++)
+                    for (int nn = 0; nn < o; nn++) w += 0.25 * O4(tau, m, nn, a, b) * OOVV(m, nn, e, f);
+                r += 0.5 * O4(tau, i, j, e, f) * w;
+            }
+        /* P(ij) P(ab) X */
+        r += ring_x(&S, t1, t2, i, j, a, b) - ring_x(&S, t1, t2, j, i, a, b)
+           - ring_x(&S, t1, t2, i, j, b, a) + ring_x(&S, t1, t2, j, i, b, a);
+        /* P(ij) sum_e t_i^e <ab||ej>  and  -P(ab) sum_m t_m^a <mb||ij> */
+        for (int e = 0; e < v; e++)
+            r += T1(i, e) * vint(&S, o + a, o + b, o + e, j) - T1(j, e) * vint(&S, o + a, o + b, o + e, i);
+        for (int m = 0; m < o; m++)
+            r -= T1(m, a) * vint(&S, m, o + b, i, j) - T1(m, b) * vint(&S, m, o + a, i, j);
+        out[k] = r;
+    }
+    free(Bt); free(S.oovv); free(S.ooov); free(S.ovvv); free(tau); free(taut);
+    free(Fae); free(Fmi); free(Fme); free(Fbe2); free(Fmj2);
+    return 0;
+}

@@ -107,3 +107,18 @@ def test_energy_lambda_scaling_leading_order_is_mp2():
     A = np.stack([lam ** 2, lam ** 3, lam ** 4], 1)
     coef = np.linalg.solve(A, np.array(es))
     assert abs(coef[0] - e2) < 1e-6 * abs(e2) + 1e-12
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 51), (3, 5, 52), (4, 4, 53)])
+def test_sampled_elements_match_brute_force_and_full_residual(o, v, seed):
+    s, B = _system(o, v, seed)
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=seed, scale1=0.1, scale2=0.1)
+    rng = np.random.default_rng(seed)
+    idx = np.stack([rng.integers(0, o, 12), rng.integers(0, o, 12), rng.integers(0, v, 12),
+                    rng.integers(0, v, 12)], 1)
+    got = oracle.ccsd_r2_sample(o, v, B, s.eps, t1, t2, idx)
+    _, _, r2_b = detspace.brute_residual(o, v, s.eps, detspace.antisym_from_B(B), t1, t2)
+    _, r2 = oracle.ccsd_residual(o, v, s.eps, oracle.antisym_integrals(o, v, B), t1, t2)
+    want = r2_b[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]
+    assert np.abs(got - want).max() < 1e-12 * max(1.0, np.abs(r2_b).max())
+    assert np.abs(got - r2[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]).max() < 1e-13
