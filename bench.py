@@ -1,0 +1,352 @@
+"""Benchmark: CC residual TFLOP/s and s/iter on one B300, split-bf16 vs FP64.
+
+Workload: spin-orbital CCSD, o=40 occupied, v=200 virtual, L=120, seed 0,
+FP64 real, synthetic integrals (ccinputs).  One step = one iteration of
+cc_solve: the full residual (every statement of the contraction list), the
+energy, |R|, the Jacobi update and the DIIS extrapolation.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the residual of
+one system does not shard without an exchange; no collective is used on the
+data path); value = all ranks' flops / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CC residual TFLOP/s and s/iter on 1 B300, mixed vs FP64 at |ΔE|<1e-6 Eh"
+WORKLOAD = "spin-orbital CCSD o=40 v=200 L=120 seed=0, FP64 real, synthetic integrals"
+SMALL = "spin-orbital CCSD o=10 v=40 L=120 seed=0, FP64 real, synthetic integrals"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        load = [x for x, p in zip(sm, pw) if p > 300] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if __import__("torch").cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def fp64_peak_live(torch):
+    """cuBLAS DGEMM 4096^3, best of 3 (the FP64 roofline denominator)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2 * n ** 3 / best / 1e12
+
+
+def cpu_baseline(o, v, nsamp, flops_per_residual, seed=0):
+    """The FP64 oracle on the host cores: nsamp sampled R2 elements of the same
+    workload (integral blocks and one-particle intermediates built from B first),
+    converted to the metric's unit as the residual share those elements stand for."""
+    import numpy as np
+
+    import ccinputs
+    import oracle
+    s = ccinputs.make_system(o, v, L=120 if o > 10 else 120, seed=seed)
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=seed, scale1=0.01, scale2=0.01)
+    rng = np.random.default_rng(1)
+    idx = np.stack([rng.integers(0, o, nsamp), rng.integers(0, o, nsamp), rng.integers(0, v, nsamp),
+                    rng.integers(0, v, nsamp)], 1)
+    t0 = time.perf_counter()
+    oracle.ccsd_r2_sample(o, v, s.B, s.eps, t1, t2, idx)
+    dt = time.perf_counter() - t0
+    share = nsamp / float(o * o * v * v)
+    return {"value": flops_per_residual * share / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{nsamp} R2 elements of the o={o} v={v} residual by the explicit-loop FP64 oracle "
+                      f"(oovv/ooov/ovvv blocks and one-particle intermediates built from B first); value = "
+                      f"residual flops x {nsamp}/(o^2 v^2) / time"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    o, v = (10, 40) if args.small else (40, 200)
+    import paper_2409_06759_b300 as cc
+    flops = cc.cc_plan_create(cc.load_list("ccsd"), o, v).flops
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(o, v, args.ref_samples, flops)
+        if k >= args.warmup:
+            vals.append(r)
+    secs = sum(r["seconds"] for r in vals)
+    value = flops * args.ref_samples / float(o * o * v * v) * len(vals) / secs / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / len(vals) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": SMALL if args.small else WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6"])
+    ap.add_argument("--small", action="store_true", help="o=10 v=40 instead of o=40 v=200")
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--ref-samples", type=int, default=2)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    import ccinputs
+    import paper_2409_06759_b300 as cc
+    from paper_2409_06759_b300.engine import DeviceSystem, Engine, Solver
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = dict(ccinputs.CONFIG_SMALL if args.small else ccinputs.CONFIG_LADDER)
+    o, v = cfg["o"], cfg["v"]
+    pk, pk_kind = peaks()
+
+    # the oracle's host leg runs before any GPU work (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        flops_fp64 = cc.cc_plan_create(cc.load_list("ccsd"), o, v).flops
+        cpu = cpu_baseline(o, v, 4, flops_fp64)
+
+    sysm = ccinputs.make_system(**cfg)
+    t0 = time.perf_counter()
+    dsys = DeviceSystem.from_system(sysm, device=dev)
+    t_int = time.perf_counter() - t0
+    mixed = Engine(dsys, list_name="ccsd_vvvv", precision=args.precision)
+    fp64 = Engine(dsys, list_name="ccsd")
+    stream = torch.cuda.current_stream(dev)
+    z = lambda: (torch.zeros(o, v, dtype=torch.float64, device=dev),
+                 torch.zeros(o, o, v, v, dtype=torch.float64, device=dev))
+
+    # ---- device-timed steps on the split-bf16 plan
+    t1, t2 = z()
+    sol = Solver(mixed)
+    sol.solve(t1, t2, max_iter=args.warmup, tol=0.0, stream=stream)
+    cc.cc_plan_profile_enable(mixed.plan, True)
+    n0 = cc.cc_plan_launch_count(mixed.plan)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sol.solve(t1, t2, max_iter=args.steps, tol=0.0, resume=True, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = cc.cc_plan_launch_count(mixed.plan) - n0
+    dt = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    ms_step, ms_kernel, calls = cc.cc_plan_profile_read(mixed.plan)
+    cc.cc_plan_profile_enable(mixed.plan, False)
+    desc = mixed.plan.describe()
+    flops = mixed.plan.flops
+    s_iter = dt / args.steps
+    value = world * flops * args.steps / dt / 1e12
+
+    # roofline of the dominant kernel (largest accumulated kernel time)
+    k_dom = max(range(len(ms_kernel)), key=lambda k: ms_kernel[k])
+    st = desc["steps"][k_dom]
+    t_kernel = ms_kernel[k_dom] / calls / 1e3
+    if st["kind"] == "gemm_bf16split":
+        tflop = st["flops"] * st["products"]
+        achieved = tflop / t_kernel / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "tc_gemm_kernel (" + st["note"] + ")",
+                "fp64_equiv_tflops": st["flops"] / t_kernel / 1e12, "ms_per_launch": t_kernel * 1e3,
+                "peak_kind": f"{pk_kind} bf16 sustained (tensor-pipe flops = {st['products']} products x 2MNK)"}
+    else:
+        roof = {"bound": "fp64", "achieved": st.get("flops", 0) / t_kernel / 1e12, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "kernel": st["note"]}
+
+    # ---- end to end through the C ABI with host buffers
+    h1 = torch.empty(o, v, dtype=torch.float64).pin_memory()
+    h2 = torch.empty(o, o, v, v, dtype=torch.float64).pin_memory()
+    h1.copy_(t1.cpu())
+    h2.copy_(t2.cpu())
+    e2e_steps = max(2, min(args.steps, 4))
+    torch.cuda.synchronize()
+    barrier(world)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        t1.copy_(h1, non_blocking=True)
+        t2.copy_(h2, non_blocking=True)
+        sol.solve(t1, t2, max_iter=1, tol=0.0, resume=True, stream=stream)
+        h1.copy_(t1, non_blocking=True)
+        h2.copy_(t2, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    dt_e2e = max_over_ranks(f0.elapsed_time(f1) / 1e3, world)
+    nbytes = (h1.numel() + h2.numel()) * 8
+    e2e = {"value": world * flops * e2e_steps / dt_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "s_per_iter": dt_e2e / e2e_steps}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": s_iter * 1e3, "s_per_iter": s_iter, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}: bf16 tensor-core products, fp32 "
+            "accumulation, fp64 outputs/energy/DIIS", "data": "synthetic",
+            "config": {"workload": SMALL if args.small else WORKLOAD, "precision": args.precision,
+                       "list": "ccsd_vvvv", "flops_per_iter": flops, "replicas": world,
+                       "l2": "inputs larger than L2 (<ab||ef> split planes 6.4 GB, T2 512 MB)",
+                       "integral_build_s": t_int},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+    if cpu is not None:
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    # ---- time to solution: split-bf16 + FP64 refinement vs FP64 alone (|R| < 1e-8)
+    if not args.no_tts:
+        fpk = fp64_peak_live(torch)
+        a1, a2 = z()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        mix_sol = Solver(mixed, refine=fp64)
+        g0.record(stream)
+        rm = mix_sol.solve(a1, a2, max_iter=60, tol=1e-8, switch_tol=1e-6, stream=stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tts_mixed = g0.elapsed_time(g1) / 1e3
+        b1, b2 = z()
+        cc.cc_plan_profile_enable(fp64.plan, True)
+        h0, hh1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        rf = Solver(fp64).solve(b1, b2, max_iter=60, tol=1e-8, stream=stream)
+        hh1.record(stream)
+        torch.cuda.synchronize()
+        tts_fp64 = h0.elapsed_time(hh1) / 1e3
+        fms, fker, fcalls = cc.cc_plan_profile_read(fp64.plan)
+        cc.cc_plan_profile_enable(fp64.plan, False)
+        fdesc = fp64.plan.describe()
+        kf = max(range(len(fker)), key=lambda k: fker[k])
+        fst = fdesc["steps"][kf]
+        tk = fker[kf] / fcalls / 1e3
+        line["fp64"] = {"value": fp64.plan.flops * rf.iterations / tts_fp64 / 1e12, "unit": "TFLOP/s",
+                        "s_per_iter": tts_fp64 / rf.iterations, "iterations": rf.iterations,
+                        "time_to_solution_s": tts_fp64, "energy": rf.energy, "converged": rf.converged,
+                        "roofline": {"bound": "fp64", "kernel": "gemm_f64_kernel (" + fst["note"] + ")",
+                                     "achieved": fst["flops"] / tk / 1e12, "peak": fpk, "unit": "TFLOP/s",
+                                     "frac": fst["flops"] / tk / 1e12 / fpk,
+                                     "peak_kind": "measured live: cuBLAS DGEMM 4096^3 best of 3"}}
+        line["tts"] = {"mixed_refined_s": tts_mixed, "fp64_s": tts_fp64, "speedup": tts_fp64 / tts_mixed,
+                       "mixed_iterations": rm.iterations, "switched_at": rm.switched_at,
+                       "energy_mixed_refined": rm.energy, "energy_fp64": rf.energy,
+                       "delta_E": abs(rm.energy - rf.energy),
+                       "delta_E_mixed_phase": (abs(rm.energies[rm.switched_at] - rf.energy)
+                                               if rm.switched_at is not None and rm.switched_at >= 0 else None),
+                       "converged": rm.converged and rf.converged}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,24 @@ CC_API cc_status cc_plan_flops(cc_plan plan, double *flops);
 
 CC_API cc_status cc_plan_destroy(cc_plan plan);
 
+/* Per-step timing with CUDA events recorded on each call's stream (off by
+ * default).  enable = 1 creates the events (a host call: make it before any
+ * timed region) and clears the totals; 0 stops recording.  When a refine plan
+ * runs inside cc_solve, its own profile records its steps. */
+CC_API cc_status cc_plan_profile_enable(cc_plan plan, int enable);
+
+/* Accumulated device milliseconds per plan step (the order of
+ * cc_plan_describe's steps) over `calls` residual evaluations since enabling.
+ * ms_kernel[k] is the GEMM kernel alone (the split kernels of a split-bf16
+ * step excluded), or the whole step for permutes and epilogues.  Waits for the
+ * events of the last evaluation.  Arrays may be NULL; cap bounds the writes. */
+CC_API cc_status cc_plan_profile_read(cc_plan plan, double *ms_step, double *ms_kernel, int cap, int *nsteps,
+                                      int *calls);
+
+/* Number of kernels launched so far by calls on this plan (residual steps,
+ * operand splits, epilogues, and in cc_solve the iteration kernels). */
+CC_API cc_status cc_plan_launch_count(cc_plan plan, long long *count);
+
 /* cc_residual -- evaluate R1, R2 (, R3) for the given amplitudes.
  *   ints, amps: inputs (device, unchanged).  res: outputs (device), fully
  *   overwritten.  ws: device workspace of at least cc_plan_workspace_bytes.

@@ -29,6 +29,7 @@ STATUS = ["CC_OK", "CC_ERR_INVALID_ARG", "CC_ERR_PARSE", "CC_ERR_SHAPE", "CC_ERR
 
 # every function include/cc.h declares
 EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_plan_flops", "cc_plan_destroy",
+           "cc_plan_profile_enable", "cc_plan_profile_read", "cc_plan_launch_count",
            "cc_residual", "cc_energy", "cc_solve_workspace_bytes", "cc_solve", "cc_integral_block_elems",
            "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_status_string", "cc_last_error",
            "cc_version"]
@@ -76,6 +77,9 @@ _sig = {
     "cc_plan_describe": (c_int, [c_void_p, ctypes.c_char_p, c_size_t, _P(c_size_t)]),
     "cc_plan_flops": (c_int, [c_void_p, _P(c_double)]),
     "cc_plan_destroy": (c_int, [c_void_p]),
+    "cc_plan_profile_enable": (c_int, [c_void_p, c_int]),
+    "cc_plan_profile_read": (c_int, [c_void_p, _P(c_double), _P(c_double), c_int, _P(c_int), _P(c_int)]),
+    "cc_plan_launch_count": (c_int, [c_void_p, _P(ctypes.c_longlong)]),
     "cc_residual": (c_int, [c_void_p, _P(cc_integrals), _P(cc_amps), _P(cc_resid), c_void_p, c_size_t, c_void_p]),
     "cc_energy": (c_int, [c_void_p, _P(cc_integrals), _P(cc_amps), c_void_p, c_void_p, c_size_t, c_void_p]),
     "cc_solve_workspace_bytes": (c_int, [c_void_p, _P(cc_solve_opts), _P(c_size_t)]),
@@ -199,6 +203,27 @@ def cc_plan_describe(plan: Plan) -> dict:
     buf = ctypes.create_string_buffer(need.value)
     _check(_lib.cc_plan_describe(plan.handle, buf, need.value, ctypes.byref(need)), "cc_plan_describe")
     return json.loads(buf.value.decode())
+
+
+def cc_plan_profile_enable(plan: Plan, enable: bool = True):
+    _check(_lib.cc_plan_profile_enable(plan.handle, int(enable)), "cc_plan_profile_enable")
+
+
+def cc_plan_profile_read(plan: Plan):
+    """(ms_step[], ms_kernel[], calls) accumulated since enabling."""
+    n, calls = c_int(), c_int()
+    _check(_lib.cc_plan_profile_read(plan.handle, None, None, 0, ctypes.byref(n), ctypes.byref(calls)),
+           "cc_plan_profile_read")
+    a, b = (c_double * max(n.value, 1))(), (c_double * max(n.value, 1))()
+    _check(_lib.cc_plan_profile_read(plan.handle, a, b, n.value, ctypes.byref(n), ctypes.byref(calls)),
+           "cc_plan_profile_read")
+    return list(a[:n.value]), list(b[:n.value]), calls.value
+
+
+def cc_plan_launch_count(plan: Plan) -> int:
+    c = ctypes.c_longlong()
+    _check(_lib.cc_plan_launch_count(plan.handle, ctypes.byref(c)), "cc_plan_launch_count")
+    return c.value
 
 
 def integrals_struct(ints: dict) -> cc_integrals:

@@ -43,10 +43,21 @@ struct SolverState {
 
 }  // namespace
 
+// Per-step CUDA-event timing (cc_plan_profile_enable).
+struct Profile {
+    bool on = false;
+    bool pending = false;           // events of the last run not yet harvested
+    std::vector<cudaEvent_t> ev;    // 3 per step: start, after the operand splits, end
+    std::vector<double> ms_step, ms_gemm;
+    int calls = 0;
+};
+
 struct cc_plan_s {
     Plan plan;
     bool cache_filled = false;  // static split planes valid (inside one cc_solve call)
     SolverState solver;
+    Profile prof;
+    long long launches = 0;     // kernels launched by calls on this plan
 };
 
 namespace {
@@ -90,45 +101,87 @@ cc_status check_inputs(const Plan &P, const cc_integrals *I, const cc_amps *A, c
     return CC_OK;
 }
 
+cc_status harvest_profile(cc_plan_s *pl) {
+    Profile &pf = pl->prof;
+    if (!pf.pending) return CC_OK;
+    CC_CUDA(cudaEventSynchronize(pf.ev.back()));
+    for (size_t k = 0; k < pl->plan.steps.size(); k++) {
+        float a = 0.f, b = 0.f;
+        CC_CUDA(cudaEventElapsedTime(&a, pf.ev[3 * k], pf.ev[3 * k + 2]));
+        CC_CUDA(cudaEventElapsedTime(&b, pf.ev[3 * k + 1], pf.ev[3 * k + 2]));
+        pf.ms_step[k] += a;
+        pf.ms_gemm[k] += b;
+    }
+    pf.calls++;
+    pf.pending = false;
+    return CC_OK;
+}
+
 cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, const cc_resid *R, void *ws,
                        size_t wsb, cudaStream_t s, bool use_cache) {
     const Plan &P = pl->plan;
     cc_status st = check_inputs(P, I, A, R, ws, wsb);
     if (st != CC_OK) return st;
     char *w = (char *)ws;
+    Profile &pf = pl->prof;
+    if (pf.on) {
+        st = harvest_profile(pl);
+        if (st != CC_OK) return st;
+    }
+    size_t si = 0;
     if (!use_cache) pl->cache_filled = false;
     if (P.flops_mixed > 0 && !pl->cache_filled)   // clear the bounded-wait status word
         CC_CUDA(cudaMemsetAsync(w + P.flags_off, 0, sizeof(int), s));
     for (const Step &stp : P.steps) {
+        if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si], s));
         switch (stp.kind) {
             case StepKind::ZERO:
                 CC_CUDA(launch_zero(resolve(stp.out, I, A, R, w), stp.zero_elems, s));
+                pl->launches++;
                 break;
             case StepKind::ACCUM:
                 CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s));
+                pl->launches++;
                 break;
             case StepKind::GEMM:
                 if (!stp.mixed) {
+                    if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
                     CC_CUDA(launch_gemm_f64(stp.gemm, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
                                             resolve(stp.out, I, A, R, w), s));
+                    pl->launches++;
                 } else {
                     void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
-                    if (!(stp.a_static && pl->cache_filled))
+                    if (!(stp.a_static && pl->cache_filled)) {
                         CC_CUDA(launch_split_bf16(stp.split_a, resolve(stp.a, I, A, R, w), pa, s));
-                    if (!(stp.b_static && pl->cache_filled))
+                        pl->launches++;
+                    }
+                    if (!(stp.b_static && pl->cache_filled)) {
                         CC_CUDA(launch_split_bf16(stp.split_b, resolve(stp.b, I, A, R, w), pb, s));
+                        pl->launches++;
+                    }
+                    if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
                     CC_CUDA(launch_tc_gemm(stp.tc, pa, pb, resolve(stp.out, I, A, R, w), (int *)(w + P.flags_off), s));
+                    pl->launches++;
                 }
                 break;
         }
+        if (pf.on) {
+            if (stp.kind != StepKind::GEMM) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
+            CC_CUDA(cudaEventRecord(pf.ev[3 * si + 2], s));
+        }
+        si++;
     }
+    if (pf.on) pf.pending = true;
     if (use_cache) pl->cache_filled = true;
     // R -= D * t for every residual the list writes
     for (int l = 1; l <= 3; l++) {
         if (!P.res_used[l]) continue;
         const double *t = (const double *)(l == 1 ? A->t1 : l == 2 ? A->t2 : A->t3);
         double *r = (double *)(l == 1 ? R->r1 : l == 2 ? R->r2 : R->r3);
-        if (t) CC_CUDA(launch_denom_sub(l, P.o, P.v, I->f_occ, I->f_vir, t, r, s));
+        if (t) {
+            CC_CUDA(launch_denom_sub(l, P.o, P.v, I->f_occ, I->f_vir, t, r, s));
+            pl->launches++;
+        }
     }
     return CC_OK;
 }
@@ -265,7 +318,53 @@ cc_status cc_plan_flops(cc_plan plan, double *flops) {
 }
 
 cc_status cc_plan_destroy(cc_plan plan) {
+    if (!plan) return CC_OK;
+    for (cudaEvent_t e : plan->prof.ev) cudaEventDestroy(e);
     delete plan;
+    return CC_OK;
+}
+
+cc_status cc_plan_profile_enable(cc_plan plan, int enable) {
+    if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
+    Profile &pf = plan->prof;
+    if (enable) {
+        const size_t need = 3 * plan->plan.steps.size();
+        while (pf.ev.size() < need) {
+            cudaEvent_t e;
+            CC_CUDA(cudaEventCreate(&e));
+            pf.ev.push_back(e);
+        }
+        pf.ms_step.assign(plan->plan.steps.size(), 0.0);
+        pf.ms_gemm.assign(plan->plan.steps.size(), 0.0);
+        pf.calls = 0;
+        pf.pending = false;
+        pf.on = true;
+    } else {
+        cc_status st = harvest_profile(plan);
+        pf.on = false;
+        if (st != CC_OK) return st;
+    }
+    return CC_OK;
+}
+
+cc_status cc_plan_profile_read(cc_plan plan, double *ms_step, double *ms_kernel, int cap, int *nsteps, int *calls) {
+    if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
+    cc_status st = harvest_profile(plan);
+    if (st != CC_OK) return st;
+    const Profile &pf = plan->prof;
+    const int n = (int)pf.ms_step.size();
+    if (nsteps) *nsteps = (int)plan->plan.steps.size();
+    if (calls) *calls = pf.calls;
+    for (int k = 0; k < n && k < cap; k++) {
+        if (ms_step) ms_step[k] = pf.ms_step[k];
+        if (ms_kernel) ms_kernel[k] = pf.ms_gemm[k];
+    }
+    return CC_OK;
+}
+
+cc_status cc_plan_launch_count(cc_plan plan, long long *count) {
+    if (!plan || !count) return fail(CC_ERR_INVALID_ARG, "NULL argument");
+    *count = plan->launches;
     return CC_OK;
 }
 
@@ -365,6 +464,7 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         if (st != CC_OK) return st;
         st = reduce_energy_norm(P, ints, amps, r, L.n, partials, scal, s);
         if (st != CC_OK) return st;
+        plan->launches += 2 + (r[1] != nullptr) + (r[2] != nullptr) + (r[3] != nullptr);
         CC_CUDA(cudaMemcpyAsync(h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CC_CUDA(cudaMemcpyAsync(h_scal + 4, used_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
         CC_CUDA(cudaMemcpyAsync(h_scal + 5, pws + cur->plan.flags_off, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -425,6 +525,7 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         for (int l = 1; l <= 3; l++) {
             if (!r[l]) continue;
             CC_CUDA(launch_jacobi(l, o_, v_, ints->f_occ, ints->f_vir, t[l], r[l], xs + off, es + off, s));
+            plan->launches++;
             off += L.n[l];
         }
         if (o.diis_max > 0) {
@@ -437,15 +538,18 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
                 b_[q] = sq;
             }
             CC_CUDA(launch_gram_scatter(partials, S.nstored, a_, b_, gram, s));
+            plan->launches += S.nstored + 1;
         }
         if (S.nstored >= 2) {
             CC_CUDA(launch_diis_solve(gram, S.order, S.nstored, coef, used_dev, s));
+            plan->launches++;
             int64_t off2 = 0;
             for (int l = 1; l <= 3; l++) {
                 if (!r[l]) continue;
                 const double *xq[16];
                 for (int q = 0; q < S.nstored; q++) xq[q] = hx + (int64_t)S.order[q] * L.nx + off2;
                 CC_CUDA(launch_combine(xq, coef, used_dev, S.nstored, L.n[l], t[l], s));
+                plan->launches++;
                 off2 += L.n[l];
             }
             S.pending_m = S.nstored;
