@@ -207,9 +207,13 @@ CC_API cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opt
  *   amps: in = start (zeros give MP2 at k = 1); out = the converged x_k, or,
  *   when max_iter ends the call, the next iterate x_{k+1} (resume = 1 continues
  *   from it with the DIIS history kept in ws).
- * With refine_plan, iterations run on `plan` until |R| < max(switch_tol, tol)
- * or |R| stops improving for three iterations, then on refine_plan (DIIS
- * restarted) until convergence.
+ * With refine_plan (an FP64 plan of the same system), iterations run on `plan`
+ * until |R| < max(switch_tol, tol) or |R| stops improving for two iterations;
+ * then the DIIS history restarts and the iteration turns defect-corrected: an
+ * outer step evaluates R64(x) with refine_plan (convergence is judged on this
+ * FP64 residual only) and Rp(x) with plan, keeping delta = R64 - Rp; up to four
+ * inner steps use Rp(x) + delta, and a new outer step starts once the
+ * corrected |R| drops below 0.02 |R64|.
  * Returns CC_OK when converged, CC_ERR_NOT_CONVERGED when max_iter is reached
  * or |R| stops being finite or grows 1e3 times above its best value. */
 CC_API cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const cc_solve_opts *opts,

@@ -37,9 +37,19 @@ struct SolverState {
     int pending_m = 0;          // m passed to the last device DIIS solve (0 = none)
     int iter = 0;
     double best = INFINITY;
-    int phase = 0;              // 0: plan, 1: refine plan
+    int phase = 0;              // 0: plan, 1: defect-corrected with the refine plan
     int stall = 0;
+    int inner = 0;              // phase 1: corrected iterations since the last FP64 evaluation
+    double rn64 = INFINITY;     // phase 1: |R| of the last FP64 evaluation
 };
+
+// Phase 1 of cc_solve with a refine plan: every outer step evaluates the FP64
+// residual R64(x) (convergence is judged on it alone) and the plan's residual
+// Rp(x) at the same point, keeps delta = R64 - Rp, and the following inner
+// iterations use Rp(x) + delta.  A new outer step starts after kInnerMax inner
+// iterations or once the corrected |R| falls below kInnerDrop * |R64|.
+constexpr int kInnerMax = 4;
+constexpr double kInnerDrop = 0.02;
 
 }  // namespace
 
@@ -147,8 +157,8 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
                 if (!stp.mixed) {
                     if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
                     CC_CUDA(launch_gemm_f64(stp.gemm, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
-                                            resolve(stp.out, I, A, R, w), s));
-                    pl->launches++;
+                                            resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w), s));
+                    pl->launches += stp.gemm.splitk > 1 ? 2 : 1;
                 } else {
                     void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
                     if (!(stp.a_static && pl->cache_filled)) {
@@ -160,8 +170,9 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
                         pl->launches++;
                     }
                     if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
-                    CC_CUDA(launch_tc_gemm(stp.tc, pa, pb, resolve(stp.out, I, A, R, w), (int *)(w + P.flags_off), s));
-                    pl->launches++;
+                    CC_CUDA(launch_tc_gemm(stp.tc, pa, pb, resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w),
+                                           (int *)(w + P.flags_off), s));
+                    pl->launches += stp.tc.splitk > 1 ? 2 : 1;
                 }
                 break;
         }
@@ -201,7 +212,7 @@ struct SolverLayout {
     int64_t nx = 0;                 // elements of x = concatenation of the ranks in use
     int64_t r_off[4] = {0, 0, 0, 0};
     int64_t hist_x = 0, hist_e = 0; // diis_max vectors of nx each
-    int64_t gram = 0, coef = 0, used = 0, scal = 0, partials = 0;
+    int64_t gram = 0, coef = 0, used = 0, scal = 0, partials = 0, delta = 0;
     int64_t bytes = 0;
     int diis = 0;
 };
@@ -221,6 +232,8 @@ SolverLayout solver_layout(const Plan &P, int diis_max) {
     off += al((int64_t)L.diis * L.nx * 8);
     L.hist_e = off;
     off += al((int64_t)L.diis * L.nx * 8);
+    L.delta = off;
+    off += al(L.nx * 8);
     L.gram = off; off += al(256 * 8);
     L.coef = off; off += al(16 * 8);
     L.used = off; off += al(16);
@@ -458,18 +471,39 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     cc_status result = CC_ERR_NOT_CONVERGED;
     double last_e = NAN, last_rn = NAN;
     int k = 0;
+    double *dl = (double *)(sreg + L.delta);
+    double *dlr[4] = {nullptr, nullptr, nullptr, nullptr};
+    {
+        int64_t off = 0;
+        for (int l = 1; l <= 3; l++)
+            if (r[l]) { dlr[l] = dl + off; off += L.n[l]; }
+    }
+    cc_resid Rd{dlr[1], dlr[2], dlr[3]};
     for (k = 0; k < o.max_iter; k++) {
-        cc_plan_s *cur = (S.phase == 1 && refine) ? refine : plan;
+        const bool corrected = S.phase == 1 && refine != nullptr;
+        const bool outer = corrected && S.inner == 0;
+        cc_plan_s *cur = (corrected && outer) ? refine : plan;
         st = run_residual(cur, ints, amps, &R, pws, (size_t)pw, s, true);
         if (st != CC_OK) return st;
+        if (corrected) {
+            // delta = R64 - Rp at this point (outer), or R = Rp + delta (inner)
+            st = run_residual(plan, ints, amps, outer ? &Rd : &R, pws, (size_t)pw, s, true);
+            if (st != CC_OK) return st;
+            for (int l = 1; l <= 3; l++) {
+                if (!r[l]) continue;
+                if (outer) CC_CUDA(launch_axpby(L.n[l], 1.0, r[l], -1.0, dlr[l], s));
+                else CC_CUDA(launch_axpby(L.n[l], 1.0, dlr[l], 1.0, r[l], s));
+                plan->launches++;
+            }
+        }
         st = reduce_energy_norm(P, ints, amps, r, L.n, partials, scal, s);
         if (st != CC_OK) return st;
         plan->launches += 2 + (r[1] != nullptr) + (r[2] != nullptr) + (r[3] != nullptr);
         CC_CUDA(cudaMemcpyAsync(h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CC_CUDA(cudaMemcpyAsync(h_scal + 4, used_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CC_CUDA(cudaMemcpyAsync(h_scal + 5, pws + cur->plan.flags_off, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(h_scal + 5, pws + plan->plan.flags_off, sizeof(int), cudaMemcpyDeviceToHost, s));
         CC_CUDA(cudaStreamSynchronize(s));
-        if (cur->plan.flops_mixed > 0 && *(int *)(h_scal + 5) != 0)
+        if (plan->plan.flops_mixed > 0 && *(int *)(h_scal + 5) != 0)
             return fail(CC_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
         // history bookkeeping of the previous device DIIS solve: drop what it dropped
         if (S.pending_m >= 2) {
@@ -489,7 +523,9 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         last_rn = rn;
         if (report && report->energies) report->energies[k] = e;
         if (report && report->rnorms) report->rnorms[k] = rn;
-        if (o.verbose) std::fprintf(stderr, "cc_solve iter %d phase %d E %.14f |R| %.3e\n", S.iter, S.phase, e, rn);
+        if (o.verbose)
+            std::fprintf(stderr, "cc_solve iter %d phase %d%s E %.14f |R| %.3e\n", S.iter, S.phase,
+                         corrected ? (outer ? " fp64" : " corrected") : "", e, rn);
         S.iter++;
         if (!std::isfinite(rn) || rn > 1e3 * S.best) {
             g_err = "divergence: |R| not finite or 1e3 above its best value";
@@ -497,16 +533,27 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
             break;
         }
         if (rn < S.best) { S.best = rn; S.stall = 0; } else S.stall++;
-        if (refine && S.phase == 0 && (rn < std::max(o.switch_tol, o.tol) || S.stall >= 3)) {
-            // switch to the refine plan and re-evaluate at the same amplitudes
+        if (refine && S.phase == 0 && (rn < std::max(o.switch_tol, o.tol) || S.stall >= 2)) {
+            // switch: the next iteration is an FP64 evaluation at the same amplitudes
             S.phase = 1;
+            S.inner = 0;
             S.nstored = 0;
             S.best = INFINITY;
             S.stall = 0;
             if (report) report->switched_at = k;
             continue;
         }
-        if (o.tol > 0 && rn < o.tol) { result = CC_OK; k++; break; }
+        if (corrected) {
+            if (outer) {
+                S.rn64 = rn;
+                if (o.tol > 0 && rn < o.tol) { result = CC_OK; k++; break; }
+                S.inner = 1;
+            } else {
+                S.inner++;
+                if (S.inner > kInnerMax || rn < kInnerDrop * S.rn64) S.inner = 0;
+            }
+        }
+        if (!corrected && o.tol > 0 && rn < o.tol) { result = CC_OK; k++; break; }
         // Jacobi step into a history slot
         int slot = 0;
         if (o.diis_max > 0 && S.nstored == o.diis_max) {
@@ -643,7 +690,8 @@ cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B,
             g.cn.nd = 2; g.cn.ext[0] = e[1]; g.cn.ext[1] = e[si]; g.cn.str[0] = str[1]; g.cn.str[1] = str[si];
             g.alpha = term == 0 ? 1.0 : -1.0;
             g.beta = term == 0 ? 0.0 : 1.0;
-            CC_CUDA(launch_gemm_f64(g, sub[sp[0]][sp[ri]], sub[sp[1]][sp[si]], (double *)blocks[b], s));
+            g.splitk = 1;
+            CC_CUDA(launch_gemm_f64(g, sub[sp[0]][sp[ri]], sub[sp[1]][sp[si]], (double *)blocks[b], nullptr, s));
         }
     }
     return CC_OK;

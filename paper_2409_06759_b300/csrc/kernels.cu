@@ -100,7 +100,7 @@ __device__ __forceinline__ int64_t grp_offset(const Grp &g, int64_t x) {
 template <bool A_KCONTIG, bool B_KCONTIG>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, const double *__restrict__ A,
                                                        const double *__restrict__ B, double *__restrict__ C,
-                                                       int thread_m_fast) {
+                                                       double *__restrict__ partials, int thread_m_fast, int64_t kchunk) {
     __shared__ double As[GBK][GBM + GPAD];
     __shared__ double Bs[GBK][GBN + GPAD];
     const int tid = threadIdx.x;
@@ -110,19 +110,19 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
     const int tn = thread_m_fast ? (tid >> 4) : (tid & 15);
 
     double ra[4], rb[4];
-    auto load_tiles = [&](int64_t k0) {
+    auto load_tiles = [&](int64_t k0, int64_t klim) {
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             int e = tid + 256 * r;
             int mm, kk;
             if (A_KCONTIG) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
             int64_t gm = m0 + mm, gk = k0 + kk;
-            ra[r] = (gm < d.M && gk < d.K) ? __ldg(A + gm * d.sAm + gk * d.sAk) : 0.0;
+            ra[r] = (gm < d.M && gk < klim) ? __ldg(A + gm * d.sAm + gk * d.sAk) : 0.0;
             int nn;
             if (B_KCONTIG) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
             int64_t gn = n0 + nn;
             gk = k0 + kk;
-            rb[r] = (gn < d.N && gk < d.K) ? __ldg(B + gk * d.sBk + gn * d.sBn) : 0.0;
+            rb[r] = (gn < d.N && gk < klim) ? __ldg(B + gk * d.sBk + gn * d.sBn) : 0.0;
         }
     };
     auto store_tiles = [&]() {
@@ -140,12 +140,15 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
 
-    load_tiles(0);
-    for (int64_t k0 = 0; k0 < d.K; k0 += GBK) {
+    // K slice of this CTA (the whole K unless split)
+    const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+    const int64_t kend = kbeg + kchunk < d.K ? kbeg + kchunk : d.K;
+    load_tiles(kbeg, kend);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
         __syncthreads();
         store_tiles();
         __syncthreads();
-        if (k0 + GBK < d.K) load_tiles(k0 + GBK);
+        if (k0 + GBK < kend) load_tiles(k0 + GBK, kend);
 #pragma unroll
         for (int k = 0; k < GBK; k++) {
             double a[4], b[4];
@@ -158,6 +161,18 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
 #pragma unroll
                 for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
+    }
+    if (gridDim.z > 1) {
+        // split K: raw partial sums, [z][n][m]
+        double *P = partials + (int64_t)blockIdx.z * d.M * d.N;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int64_t m = m0 + tm + 16 * i, n = n0 + tn + 16 * j;
+                if (m < d.M && n < d.N) P[n * d.M + m] = acc[i][j];
+            }
+        return;
     }
     int64_t ro[4], co[4];
     bool rv[4], cv[4];
@@ -182,19 +197,147 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         }
 }
 
-cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, cudaStream_t s) {
+// ------------------------------------------------------------------ gemv
+// y(r) = alpha * sum_k X(r,k) x(k) + beta * y(r): the GEMM shapes with one
+// output dimension of extent 1 are memory-bound matrix-vector products.
+// X(r,k) = X[r*sr + k*sk]; x(k) = x[k*incx]; y addressed through a group.
+// K-contiguous X (sk == 1): one warp per row; otherwise one thread per row.
+__global__ void __launch_bounds__(256) gemv_rowwarp_kernel(int64_t R, int64_t K, const double *__restrict__ X,
+                                                           int64_t sr, const double *__restrict__ x, int64_t incx,
+                                                           const Grp gy, double alpha, double beta,
+                                                           double *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    for (int64_t r = w0; r < R; r += (int64_t)gridDim.x * 8) {
+        const double *row = X + r * sr;
+        double s0 = 0.0, s1 = 0.0;
+        int64_t k = lane;
+        for (; k + 32 < K; k += 64) {
+            s0 = fma(__ldg(row + k), __ldg(x + k * incx), s0);
+            s1 = fma(__ldg(row + k + 32), __ldg(x + (k + 32) * incx), s1);
+        }
+        if (k < K) s0 = fma(__ldg(row + k), __ldg(x + k * incx), s0);
+        double s = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            double *p = y + grp_offset(gy, r);
+            double val = alpha * s;
+            if (beta != 0.0) val += beta * *p;
+            *p = val;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) gemv_rowthread_kernel(int64_t R, int64_t K, const double *__restrict__ X,
+                                                             int64_t sk, const double *__restrict__ x, int64_t incx,
+                                                             const Grp gy, double alpha, double beta,
+                                                             double *__restrict__ y) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int64_t k = 0;
+        for (; k + 3 < K; k += 4) {
+            s0 = fma(__ldg(X + r + k * sk), __ldg(x + k * incx), s0);
+            s1 = fma(__ldg(X + r + (k + 1) * sk), __ldg(x + (k + 1) * incx), s1);
+            s2 = fma(__ldg(X + r + (k + 2) * sk), __ldg(x + (k + 2) * incx), s2);
+            s3 = fma(__ldg(X + r + (k + 3) * sk), __ldg(x + (k + 3) * incx), s3);
+        }
+        for (; k < K; k++) s0 = fma(__ldg(X + r + k * sk), __ldg(x + k * incx), s0);
+        double *p = y + grp_offset(gy, r);
+        double val = alpha * ((s0 + s1) + (s2 + s3));
+        if (beta != 0.0) val += beta * *p;
+        *p = val;
+    }
+}
+
+static cudaError_t launch_gemv(int64_t R, int64_t K, const double *X, int64_t sr, int64_t sk, const double *x,
+                               int64_t incx, const Grp &gy, double alpha, double beta, double *y, cudaStream_t s) {
+    if (sk == 1 || K == 1) {
+        int64_t blocks = (R + 7) / 8;
+        if (blocks > 148 * 16) blocks = 148 * 16;
+        gemv_rowwarp_kernel<<<(unsigned)blocks, 256, 0, s>>>(R, K, X, K == 1 ? sr : sr, x, incx, gy, alpha, beta, y);
+    } else {
+        int64_t blocks = (R + 255) / 256;
+        if (blocks > 148 * 16) blocks = 148 * 16;
+        gemv_rowthread_kernel<<<(unsigned)blocks, 256, 0, s>>>(R, K, X, sk, x, incx, gy, alpha, beta, y);
+    }
+    return cudaGetLastError();
+}
+
+// C(m,n) = alpha * a(m) b(n) + beta * C(m,n): the K = 1 (outer product) shape,
+// memory-bound; threads run along the output direction with the smaller stride.
+__global__ void __launch_bounds__(256) outer_kernel(int64_t M, int64_t N, const double *__restrict__ a, int64_t sa,
+                                                    const double *__restrict__ b, int64_t sb, const Grp cm,
+                                                    const Grp cn, double alpha, double beta, double *__restrict__ C,
+                                                    int m_fast) {
+    const int64_t MN = M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m, n;
+        if (m_fast) { n = e / M; m = e - n * M; } else { m = e / N; n = e - m * N; }
+        double *p = C + grp_offset(cm, m) + grp_offset(cn, n);
+        double val = alpha * __ldg(a + m * sa) * __ldg(b + n * sb);
+        if (beta != 0.0) val += beta * *p;
+        *p = val;
+    }
+}
+
+cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, double *partials,
+                            cudaStream_t s) {
     if (d.M <= 0 || d.N <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((d.M + GBM - 1) / GBM), (unsigned)((d.N + GBN - 1) / GBN));
-    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    if (d.K == 1 && d.M > 1 && d.N > 1) {
+        int64_t sm = d.cm.nd ? d.cm.str[d.cm.nd - 1] : 0, sn = d.cn.nd ? d.cn.str[d.cn.nd - 1] : 0;
+        int64_t blocks = (d.M * d.N + 255) / 256;
+        if (blocks > 148 * 16) blocks = 148 * 16;
+        outer_kernel<<<(unsigned)blocks, 256, 0, s>>>(d.M, d.N, A, d.sAm, B, d.sBn, d.cm, d.cn, d.alpha, d.beta, C,
+                                                      sm <= sn ? 1 : 0);
+        return cudaGetLastError();
+    }
+    // matrix-vector shapes: rows m of A against the single column of B, or
+    // rows n of B^T against the single row of A
+    if (d.N == 1 && d.M > 1 && (d.sAk == 1 || d.sAm == 1))
+        return launch_gemv(d.M, d.K, A, d.sAm, d.sAk, B, d.sBk, d.cm, d.alpha, d.beta, C, s);
+    if (d.M == 1 && d.N > 1 && (d.sBk == 1 || d.sBn == 1))
+        return launch_gemv(d.N, d.K, B, d.sBn, d.sBk, A, d.sAk, d.cn, d.alpha, d.beta, C, s);
+    const int sk = d.splitk > 1 ? d.splitk : 1;
+    const int64_t kchunk = sk > 1 ? ((d.K + sk - 1) / sk + GBK - 1) / GBK * GBK : (d.K > 0 ? d.K : 1);
+    const int zs = (int)((d.K + kchunk - 1) / kchunk);
+    dim3 grid((unsigned)((d.M + GBM - 1) / GBM), (unsigned)((d.N + GBN - 1) / GBN), (unsigned)zs);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    if (zs > 1 && !partials) return cudaErrorInvalidValue;
     // threads run fastest along the output direction with the smaller stride
     int64_t sm = d.cm.nd ? d.cm.str[d.cm.nd - 1] : 0, sn = d.cn.nd ? d.cn.str[d.cn.nd - 1] : 0;
     int m_fast = (d.cm.nd && (!d.cn.nd || sm <= sn)) ? 1 : 0;
     const bool ak = d.sAk == 1 && !(d.sAm == 1 && d.K == 1);
     const bool bk = d.sBk == 1 && !(d.sBn == 1 && d.K == 1);
-    if (ak && bk) gemm_f64_kernel<true, true><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
-    else if (ak) gemm_f64_kernel<true, false><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
-    else if (bk) gemm_f64_kernel<false, true><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
-    else gemm_f64_kernel<false, false><<<grid, 256, 0, s>>>(d, A, B, C, m_fast);
+    if (zs > 1) m_fast = 1;
+    if (ak && bk) gemm_f64_kernel<true, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else if (ak) gemm_f64_kernel<true, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else if (bk) gemm_f64_kernel<false, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else gemm_f64_kernel<false, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || zs == 1) return e;
+    return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
+}
+
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t M, int64_t N, int nz, const double *__restrict__ P,
+                                                            const Grp cm, const Grp cn, double alpha, double beta,
+                                                            double *__restrict__ C) {
+    const int64_t MN = M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int z = 0; z < nz; z++) acc += P[z * MN + e];
+        const int64_t n = e / M, m = e - n * M;
+        double *p = C + grp_offset(cm, m) + grp_offset(cn, n);
+        double val = alpha * acc;
+        if (beta != 0.0) val += beta * *p;
+        *p = val;
+    }
+}
+
+cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
+                                 double alpha, double beta, double *C, cudaStream_t s) {
+    int64_t blocks = (M * N + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(M, N, splitk, partials, cm, cn, alpha, beta, C);
     return cudaGetLastError();
 }
 
@@ -245,6 +388,19 @@ cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double
     int64_t blocks = (n + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
     jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, n);
+    return cudaGetLastError();
+}
+
+__global__ void axpby_kernel(int64_t n, double a, const double *__restrict__ x, double b, double *__restrict__ y) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = a * x[e] + b * y[e];
+}
+
+cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    axpby_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, a, x, b, y);
     return cudaGetLastError();
 }
 

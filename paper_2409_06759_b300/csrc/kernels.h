@@ -36,11 +36,14 @@ struct AccumDesc {
 // C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), FP64.
 // A(m,k) = A[m*sAm + k*sAk] with sAm == 1 or sAk == 1; B(k,n) = B[k*sBk + n*sBn]
 // likewise; C addressed through two mixed-radix groups.
+// splitk > 1: grid z = splitk slices of K; each writes its raw partial sum to
+// partials[z][n][m] (m fastest) and launch_splitk_reduce applies alpha/beta.
 struct GemmF64Desc {
     int64_t M, N, K;
     int64_t sAm, sAk, sBk, sBn;
     Grp cm, cn;
     double alpha, beta;
+    int splitk;
 };
 
 // Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes
@@ -55,6 +58,8 @@ struct SplitDesc {
 
 // Split-bf16 GEMM on tcgen05: D[m][n] = sum_{(p,q) in products} A_p[m][:] . B_q[n][:]
 // (fp32 in TMEM), then C(m,n) = alpha * D + beta * C(m,n) in FP64.
+// bn: N tile (64, 128 or 256); splitk > 1: each CTA covers one slice of the
+// K blocks and stores its raw fp32 tile (as double) to partials[z][n][m].
 struct TcGemmDesc {
     int64_t M, N, Mp, Np, Kp;
     int nplanes_a, nplanes_b;
@@ -62,15 +67,20 @@ struct TcGemmDesc {
     int prod_a[8], prod_b[8];  // plane indices of each product
     Grp cm, cn;
     double alpha, beta;
+    int bn;
+    int splitk;
 };
 
 cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s);
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
-cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C,
+cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, double *partials,
                             cudaStream_t s);
+// C(m,n) = alpha * sum_z partials[z][n][m] + beta * C(m,n) (fixed summation order)
+cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
+                                 double alpha, double beta, double *C, cudaStream_t s);
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s);
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C,
-                           int *err_flag, cudaStream_t s);
+                           double *partials, int *err_flag, cudaStream_t s);
 
 // R -= D * T for rank 1..3 residuals: D from the orbital energies.
 cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv,
@@ -78,6 +88,8 @@ cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const dou
 // Jacobi step: e = r / D, x' = t + e (written to xo, eo).
 cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
                           const double *r, double *xo, double *eo, cudaStream_t s);
+// y = a*x + b*y over n elements
+cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s);
 // partial sums for dot products: partials[b] = sum over block b of x*y (fixed grid)
 constexpr int kRedBlocks = 592;
 cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *partials,

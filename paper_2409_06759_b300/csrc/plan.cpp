@@ -627,6 +627,18 @@ struct Planner {
                 err = "internal: GEMM operand without a unit stride";
                 return false;
             }
+            // split K when the output has too few 64x64 tiles to fill the SMs
+            const int64_t tiles = ((g.gemm.M + 63) / 64) * ((g.gemm.N + 63) / 64);
+            g.gemm.splitk = 1;
+            if (tiles < 296 && g.gemm.K >= 512 && g.gemm.M > 1 && g.gemm.N > 1) {
+                int64_t sk = (592 + tiles - 1) / tiles;
+                sk = std::min<int64_t>(sk, g.gemm.K / 128);
+                sk = std::min<int64_t>(sk, 256);
+                if (sk > 1) {
+                    g.gemm.splitk = (int)sk;
+                    g.partials = scratch(sk * g.gemm.M * g.gemm.N * 8);
+                }
+            }
         }
 
         // output: direct (generalised strides) or scratch + antisymmetrising epilogue
@@ -660,9 +672,20 @@ struct Planner {
             TcGemmDesc &t = g.tc;
             t.M = Mx;
             t.N = Nx;
+            t.bn = Nx <= 64 ? 64 : (Nx <= 128 || np == 3) ? 128 : 256;
             t.Mp = align_up(Mx, 128);
-            t.Np = align_up(Nx, 256);
+            t.Np = align_up(Nx, t.bn);
             t.Kp = align_up(Kx, 64);
+            // split K when the output tiles cannot fill the 148 SMs
+            const int64_t tiles = (t.Mp / 128) * (t.Np / t.bn), kblocks = t.Kp / 64;
+            t.splitk = 1;
+            if (tiles < 148 && kblocks >= 8) {
+                int64_t sk = std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
+                if (sk > 1) {
+                    t.splitk = (int)sk;
+                    g.partials = scratch(sk * Mx * Nx * 8);
+                }
+            }
             t.nplanes_a = t.nplanes_b = np;
             if (np == 2) {
                 const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
@@ -758,7 +781,7 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     off += P.cache_need;
     plan.ws_bytes = off;
     for (auto &st : plan.steps) {
-        for (BufRef *r : {&st.out, &st.a, &st.b})
+        for (BufRef *r : {&st.out, &st.a, &st.b, &st.partials})
             if (r->where == BufRef::WS && r->slot == 1) { r->off += plan.scratch_off; r->slot = 0; }
         if (st.mixed) {
             st.planes_a_off += st.a_static ? plan.cache_off : plan.scratch_off;
@@ -796,6 +819,7 @@ std::string describe_plan(const Plan &plan) {
            << "\",\"note\":\"" << s.note << "\"";
         if (s.kind == StepKind::GEMM && !s.mixed) {
             os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
+               << ",\"splitk\":" << s.gemm.splitk
                << ",\"sAm\":" << s.gemm.sAm << ",\"sAk\":" << s.gemm.sAk << ",\"sBk\":" << s.gemm.sBk
                << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta << ",\"cm\":";
             grp_json(os, s.gemm.cm);
@@ -805,7 +829,8 @@ std::string describe_plan(const Plan &plan) {
             os << ",\"M\":" << s.tc.M << ",\"N\":" << s.tc.N << ",\"K\":" << s.split_a.K << ",\"flops\":" << s.flops
                << ",\"products\":" << s.tc.nprod << ",\"a_static\":" << (s.a_static ? 1 : 0)
                << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta
-               << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp
+               << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp << ",\"bn\":" << s.tc.bn
+               << ",\"splitk\":" << s.tc.splitk
                << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off;
         } else if (s.kind == StepKind::ACCUM) {
             os << ",\"elems\":" << s.acc.total << ",\"terms\":" << s.acc.nperm << ",\"alpha\":" << s.acc.alpha

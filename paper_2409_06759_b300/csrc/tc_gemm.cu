@@ -23,58 +23,62 @@ __device__ __forceinline__ int64_t grp_off(const Grp &g, int64_t x) {
     return off;
 }
 
-// One block per row (grid-stride over rows), each thread 4 consecutive columns.
+// One warp per row (grid-stride over rows); lane l converts columns
+// [8l, 8l+8) of each 256-column chunk and stores 16 bytes per plane.  When the
+// K group's innermost index has unit stride and every other stride keeps
+// 16-byte alignment, the eight sources are read as four double2 loads.
+__device__ __forceinline__ void split3(double x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
+    h = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(h);
+    m = __double2bfloat16(r1);
+    l = __double2bfloat16(r1 - (double)__bfloat162float(m));
+}
+
 __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, const double *__restrict__ x,
-                                                         __nv_bfloat16 *__restrict__ planes) {
+                                                         __nv_bfloat16 *__restrict__ planes, int vec) {
     const int64_t plane_elems = d.Rp * d.Kp;
-    for (int64_t r = blockIdx.x; r < d.Rp; r += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); r < d.Rp; r += nwarps) {
         const bool row_ok = r < d.R;
         const int64_t roff = row_ok ? grp_off(d.gr, r) : 0;
-        for (int64_t k0 = (int64_t)threadIdx.x * 4; k0 < d.Kp; k0 += 1024) {
-            // digits of k0 in the K group, advanced as an odometer
-            int dig[6];
-            int64_t coff = 0;
-            {
-                int64_t t = k0 < d.K ? k0 : 0;
-                for (int q = d.gk.nd - 1; q >= 0; q--) {
-                    dig[q] = (int)(t % d.gk.ext[q]);
-                    t /= d.gk.ext[q];
-                    coff += dig[q] * d.gk.str[q];
-                }
-            }
-            __align__(8) __nv_bfloat16 h[4], m[4], l[4];
+        for (int64_t k0 = (int64_t)lane * 8; k0 < d.Kp; k0 += 256) {
+            __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+            if (row_ok && vec && k0 + 7 < d.K) {
+                const double2 *src = reinterpret_cast<const double2 *>(x + roff + grp_off(d.gk, k0));
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int64_t k = k0 + j;
-                double val = 0.0;
-                if (row_ok && k < d.K) {
-                    val = __ldg(x + roff + coff);
-                    for (int q = d.gk.nd - 1; q >= 0; q--) {
-                        coff += d.gk.str[q];
-                        if (++dig[q] < d.gk.ext[q]) break;
-                        coff -= dig[q] * d.gk.str[q];
-                        dig[q] = 0;
-                    }
+                for (int j = 0; j < 4; j++) {
+                    const double2 v2 = __ldg(src + j);
+                    split3(v2.x, h[2 * j], m[2 * j], l[2 * j]);
+                    split3(v2.y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
                 }
-                h[j] = __double2bfloat16(val);
-                double r1 = val - (double)__bfloat162float(h[j]);
-                m[j] = __double2bfloat16(r1);
-                double r2 = r1 - (double)__bfloat162float(m[j]);
-                l[j] = __double2bfloat16(r2);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int64_t k = k0 + j;
+                    const double val = (row_ok && k < d.K) ? __ldg(x + roff + grp_off(d.gk, k)) : 0.0;
+                    split3(val, h[j], m[j], l[j]);
+                }
             }
-            // Kp is a multiple of 64, so the 4 columns are always in range
             __nv_bfloat16 *p0 = planes + r * d.Kp + k0;
-            *reinterpret_cast<uint2 *>(p0) = *reinterpret_cast<uint2 *>(h);
-            *reinterpret_cast<uint2 *>(p0 + plane_elems) = *reinterpret_cast<uint2 *>(m);
-            if (d.nplanes == 3) *reinterpret_cast<uint2 *>(p0 + 2 * plane_elems) = *reinterpret_cast<uint2 *>(l);
+            *reinterpret_cast<uint4 *>(p0) = *reinterpret_cast<const uint4 *>(h);
+            *reinterpret_cast<uint4 *>(p0 + plane_elems) = *reinterpret_cast<const uint4 *>(m);
+            if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = *reinterpret_cast<const uint4 *>(l);
         }
     }
 }
 
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s) {
     if (d.Kp % 64 || d.Rp <= 0 || d.nplanes < 2 || d.nplanes > 3) return cudaErrorInvalidValue;
-    int64_t blocks = d.Rp < 148 * 32 ? d.Rp : 148 * 32;
-    split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes);
+    // vector path: innermost K digit contiguous with an extent that keeps 8-runs
+    // inside it, every other stride even (16-byte aligned double2), base aligned
+    int vec = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == 1 && d.gk.ext[d.gk.nd - 1] % 8 == 0 &&
+              ((uintptr_t)x & 15) == 0;
+    for (int q = 0; q + 1 < d.gk.nd; q++) vec &= (d.gk.str[q] % 2) == 0;
+    for (int q = 0; q < d.gr.nd; q++) vec &= (d.gr.str[q] % 2) == 0;
+    int64_t blocks = (d.Rp + 7) / 8;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes, vec);
     return cudaGetLastError();
 }
 
@@ -199,7 +203,8 @@ struct Cfg {
 template <int NP, int BN, int STAGES>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   const TcGemmDesc d, double *__restrict__ C, int *err_flag) {
+                   const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials, int kb_per_split,
+                   int *err_flag) {
     using G = Cfg<NP, BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -217,7 +222,11 @@ __global__ void __launch_bounds__(192, 1)
     const int tile = blockIdx.x;
     const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
     const int64_t n0 = (int64_t)(tile % n_tiles) * BN;
-    const int kblocks = (int)(d.Kp / BK);
+    // K blocks of this CTA: all of them, or one slice when K is split
+    const int kb_total = (int)(d.Kp / BK);
+    const int kb0 = (int)blockIdx.y * kb_per_split;
+    const int kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    const int kblocks = kb1 - kb0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -251,14 +260,14 @@ __global__ void __launch_bounds__(192, 1)
                 uint8_t *st = tiles + s * G::STAGE_BYTES;
                 mbar_expect_tx(&full[s], G::STAGE_BYTES);
                 for (int p = 0; p < NP; p++)
-                    tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], kb * BK, (int)(p * d.Mp + m0));
+                    tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)(p * d.Mp + m0));
                 for (int q = 0; q < NP; q++)
-                    tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BK,
+                    tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK,
                                 (int)(q * d.Np + n0));
                 issued = kb + 1;
             }
             if (*abort_flag) {
-                // let the copies already in flight land before the CTA exits
+                // let the copies already in flight land before the CTA exits (kb counts from this slice's start)
                 for (int kb = *consumed; kb < issued; kb++) mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
                 atomicOr(err_flag, 1);
             }
@@ -307,6 +316,22 @@ __global__ void __launch_bounds__(192, 1)
         if (!ok) {
             *abort_flag = 1;
             if (lane == 0) atomicOr(err_flag, 1);
+        } else if (gridDim.y > 1) {
+            // split K: raw partial tile, partials[z][n][m] (rows coalesce across the warp)
+            double *P = partials + (int64_t)blockIdx.y * d.M * d.N;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                tmem_ld_wait();
+                if (mok) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int64_t n = n0 + c0 + j;
+                        if (n < d.N) P[n * d.M + m] = (double)__uint_as_float(r[j]);
+                    }
+                }
+            }
         } else {
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -366,7 +391,8 @@ static bool make_map(CUtensorMap *map, const void *base, int64_t rows_total, int
 }
 
 template <int NP, int BN, int STAGES>
-static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B, double *C, int *err, cudaStream_t s) {
+static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials, int *err,
+                              cudaStream_t s) {
     using G = Cfg<NP, BN, STAGES>;
     static bool attr = false;
     if (!attr) {
@@ -381,22 +407,37 @@ static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B,
         return cudaErrorInvalidValue;
     const int64_t tiles = (d.Mp / BM) * (d.Np / BN);
     if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    tc_gemm_kernel<NP, BN, STAGES><<<(unsigned)tiles, 192, G::SMEM, s>>>(ma, mb, d, C, err);
-    return cudaGetLastError();
+    const int kb_total = (int)(d.Kp / BK);
+    const int sk = d.splitk > 1 ? d.splitk : 1;
+    const int per = (kb_total + sk - 1) / sk;
+    const int zs = (kb_total + per - 1) / per;
+    if (zs > 1 && !partials) return cudaErrorInvalidValue;
+    if (zs > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)tiles, (unsigned)zs);
+    tc_gemm_kernel<NP, BN, STAGES><<<grid, 192, G::SMEM, s>>>(ma, mb, d, C, partials, per, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || zs == 1) return e;
+    return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
 }  // namespace tc
 
-cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C, int *err_flag,
-                           cudaStream_t s) {
+cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C, double *partials,
+                           int *err_flag, cudaStream_t s) {
     if (d.M <= 0 || d.N <= 0) return cudaSuccess;
     if (d.nplanes_a != d.nplanes_b || d.nprod < 1 || d.nprod > 8) return cudaErrorInvalidValue;
     if (((uintptr_t)Aplanes & 1023) || ((uintptr_t)Bplanes & 1023) || d.Kp < 64) {
         // TMA needs 16-byte aligned bases; the planner hands out 256-byte aligned workspace
         if (((uintptr_t)Aplanes & 15) || ((uintptr_t)Bplanes & 15)) return cudaErrorMisalignedAddress;
     }
-    if (d.nplanes_a == 2) return tc::launch_cfg<2, 256, 2>(d, Aplanes, Bplanes, C, err_flag, s);
-    if (d.nplanes_a == 3) return tc::launch_cfg<3, 128, 2>(d, Aplanes, Bplanes, C, err_flag, s);
+    if (d.nplanes_a == 2) {
+        if (d.bn == 256) return tc::launch_cfg<2, 256, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        if (d.bn == 128) return tc::launch_cfg<2, 128, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        if (d.bn == 64) return tc::launch_cfg<2, 64, 4>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+    } else if (d.nplanes_a == 3) {
+        if (d.bn == 128) return tc::launch_cfg<3, 128, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        if (d.bn == 64) return tc::launch_cfg<3, 64, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+    }
     return cudaErrorInvalidValue;
 }
 
