@@ -340,7 +340,9 @@ def main():
                        "delta_E": abs(rm.energy - rf.energy),
                        "delta_E_mixed_phase": (abs(rm.energies[rm.switched_at] - rf.energy)
                                                if rm.switched_at is not None and rm.switched_at >= 0 else None),
-                       "converged": rm.converged and rf.converged}
+                       "converged": rm.converged and rf.converged,
+                       "rnorms_mixed_refined": [float(f"{x:.3e}") for x in rm.rnorms],
+                       "rnorms_fp64": [float(f"{x:.3e}") for x in rf.rnorms]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

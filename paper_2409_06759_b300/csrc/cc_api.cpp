@@ -406,9 +406,11 @@ cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opts, size
     if (!plan || !bytes) return fail(CC_ERR_INVALID_ARG, "NULL argument");
     int diis = opts ? opts->diis_max : 8;
     if (diis < 0 || diis > 16) return fail(CC_ERR_INVALID_ARG, "diis_max must be in [0, 16]");
-    int64_t pw = plan->plan.ws_bytes;
-    if (opts && opts->refine_plan) pw = std::max(pw, opts->refine_plan->plan.ws_bytes);
-    *bytes = (size_t)(al(pw) + solver_layout(plan->plan, diis).bytes);
+    // the refine plan gets a region of its own: the plan's cached split planes
+    // must survive the FP64 evaluations of the corrected phase
+    int64_t pw = al(plan->plan.ws_bytes);
+    if (opts && opts->refine_plan) pw += al(opts->refine_plan->plan.ws_bytes);
+    *bytes = (size_t)(pw + solver_layout(plan->plan, diis).bytes);
     return CC_OK;
 }
 
@@ -438,10 +440,11 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     if (ws_bytes < need || !ws || !aligned256(ws))
         return fail(CC_ERR_WORKSPACE, "solve workspace too small: need " + std::to_string(need));
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t pw = P.ws_bytes;
-    if (refine) pw = std::max(pw, refine->plan.ws_bytes);
+    const int64_t pw = al(P.ws_bytes);
+    const int64_t rw = refine ? al(refine->plan.ws_bytes) : 0;
     char *pws = (char *)ws;
-    char *sreg = (char *)ws + al(pw);
+    char *rws = (char *)ws + pw;
+    char *sreg = (char *)ws + pw + rw;
     SolverLayout L = solver_layout(P, o.diis_max);
     const int o_ = P.o, v_ = P.v;
     double *r[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -482,13 +485,15 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     for (k = 0; k < o.max_iter; k++) {
         const bool corrected = S.phase == 1 && refine != nullptr;
         const bool outer = corrected && S.inner == 0;
-        cc_plan_s *cur = (corrected && outer) ? refine : plan;
-        st = run_residual(cur, ints, amps, &R, pws, (size_t)pw, s, true);
+        if (corrected && outer) {
+            st = run_residual(refine, ints, amps, &R, rws, (size_t)rw, s, true);
+            if (st != CC_OK) return st;
+        }
+        // the plan's residual: R itself, or (outer) Rp into the delta buffer
+        st = run_residual(plan, ints, amps, (corrected && outer) ? &Rd : &R, pws, (size_t)pw, s, true);
         if (st != CC_OK) return st;
         if (corrected) {
-            // delta = R64 - Rp at this point (outer), or R = Rp + delta (inner)
-            st = run_residual(plan, ints, amps, outer ? &Rd : &R, pws, (size_t)pw, s, true);
-            if (st != CC_OK) return st;
+            // delta = R64 - Rp (outer), or R = Rp + delta (inner)
             for (int l = 1; l <= 3; l++) {
                 if (!r[l]) continue;
                 if (outer) CC_CUDA(launch_axpby(L.n[l], 1.0, r[l], -1.0, dlr[l], s));

@@ -23,15 +23,20 @@ __device__ __forceinline__ int64_t grp_off(const Grp &g, int64_t x) {
     return off;
 }
 
-// One warp per row (grid-stride over rows); lane l converts columns
+// Warps take (row, 1024-column span) items; lane l converts columns
 // [8l, 8l+8) of each 256-column chunk and stores 16 bytes per plane.  When the
 // K group's innermost index has unit stride and every other stride keeps
 // 16-byte alignment, the eight sources are read as four double2 loads.
+// The split runs in FP32 after one rounding of x to FP32 (24 significant
+// bits, as many as three bf16 planes hold): the remainders x_f - hi and
+// r - mid are exact in FP32, and the FP64 pipe of sm_103a -- a few
+// operations per clock per SM -- is used only for that one conversion.
 __device__ __forceinline__ void split3(double x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
-    h = __double2bfloat16(x);
-    const double r1 = x - (double)__bfloat162float(h);
-    m = __double2bfloat16(r1);
-    l = __double2bfloat16(r1 - (double)__bfloat162float(m));
+    const float xf = __double2float_rn(x);
+    h = __float2bfloat16_rn(xf);
+    const float r1 = xf - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
 __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, const double *__restrict__ x,
@@ -39,10 +44,15 @@ __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, cons
     const int64_t plane_elems = d.Rp * d.Kp;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * 8;
-    for (int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); r < d.Rp; r += nwarps) {
+    // work items: (row, 1024-column span); a warp takes one item at a time
+    const int64_t spans = (d.Kp + 1023) / 1024;
+    for (int64_t it = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < d.Rp * spans; it += nwarps) {
+        const int64_t r = it / spans;
+        const int64_t kspan = (it - r * spans) * 1024;
+        const int64_t kend = kspan + 1024 < d.Kp ? kspan + 1024 : d.Kp;
         const bool row_ok = r < d.R;
         const int64_t roff = row_ok ? grp_off(d.gr, r) : 0;
-        for (int64_t k0 = (int64_t)lane * 8; k0 < d.Kp; k0 += 256) {
+        for (int64_t k0 = kspan + (int64_t)lane * 8; k0 < kend; k0 += 256) {
             __align__(16) __nv_bfloat16 h[8], m[8], l[8];
             if (row_ok && vec && k0 + 7 < d.K) {
                 const double2 *src = reinterpret_cast<const double2 *>(x + roff + grp_off(d.gk, k0));
@@ -76,7 +86,8 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
               ((uintptr_t)x & 15) == 0;
     for (int q = 0; q + 1 < d.gk.nd; q++) vec &= (d.gk.str[q] % 2) == 0;
     for (int q = 0; q < d.gr.nd; q++) vec &= (d.gr.str[q] % 2) == 0;
-    int64_t blocks = (d.Rp + 7) / 8;
+    const int64_t items = d.Rp * ((d.Kp + 1023) / 1024);
+    int64_t blocks = (items + 7) / 8;
     if (blocks > 148 * 16) blocks = 148 * 16;
     split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes, vec);
     return cudaGetLastError();
