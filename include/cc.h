@@ -231,6 +231,25 @@ CC_API cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const v
                                     void *oovv, void *ovov, void *ovvv, void *vvvv, void *ws, size_t ws_bytes,
                                     void *stream);
 
+/* cc_energy_noalloc -- the same energy as cc_energy, for callers that cannot
+ * allocate device memory: code running under a host application that owns the
+ * device heap, or in a region where a cudaMalloc would be refused or would
+ * synchronise the device.  The paper has no counterpart; it is a convenience
+ * of this library.  The block partial sums live in a fixed device array of
+ * the library (32 KiB, 4096 partials of 16384 elements each), held on every
+ * GPU that loads the library until the process exits; nothing is allocated
+ * and no workspace is taken.
+ *   o, v: extents; o^2 v^2 must not exceed 67,108,864, otherwise the call
+ *   returns CC_ERR_INVALID_ARG before touching any pointer.
+ *   ints->oovv, amps->t2 (and amps->t1, may be NULL): device inputs.
+ *   e_dev: device double[2] receiving (E, 0).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's partials: calls that
+ * overlap on the GPU (different streams or threads, same device) race. */
+CC_API cc_status cc_energy_noalloc(int o, int v, const cc_integrals *ints, const cc_amps *amps, double *e_dev,
+                                   void *stream);
+
 CC_API const char *cc_status_string(cc_status s);
 CC_API const char *cc_last_error(void);
 

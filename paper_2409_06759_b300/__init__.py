@@ -31,8 +31,8 @@ STATUS = ["CC_OK", "CC_ERR_INVALID_ARG", "CC_ERR_PARSE", "CC_ERR_SHAPE", "CC_ERR
 EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_plan_flops", "cc_plan_destroy",
            "cc_plan_profile_enable", "cc_plan_profile_read", "cc_plan_launch_count",
            "cc_residual", "cc_energy", "cc_solve_workspace_bytes", "cc_solve", "cc_integral_block_elems",
-           "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_status_string", "cc_last_error",
-           "cc_version"]
+           "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_status_string",
+           "cc_last_error", "cc_version"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libccb300.so is not built ({LIB_PATH}); run paper_2409_06759_b300/build.py "
@@ -89,6 +89,7 @@ _sig = {
     "cc_build_integrals_workspace_bytes": (c_int, [c_int, c_int, c_int, c_int, _P(c_size_t)]),
     "cc_build_integrals": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "cc_energy_noalloc": (c_int, [c_int, c_int, _P(cc_integrals), _P(cc_amps), c_void_p, c_void_p]),
     "cc_status_string": (ctypes.c_char_p, [c_int]),
     "cc_last_error": (ctypes.c_char_p, []),
     "cc_version": (ctypes.c_char_p, []),
@@ -244,6 +245,14 @@ def cc_energy(plan: Plan, ints: dict, t1, t2, e_dev, ws, stream=None):
     A = cc_amps(_ptr(t1), _ptr(t2), None)
     _check(_lib.cc_energy(plan.handle, ctypes.byref(I), ctypes.byref(A), _ptr(e_dev), _ptr(ws), _nbytes(ws),
                           _stream(stream)), "cc_energy")
+
+
+def cc_energy_noalloc(o: int, v: int, ints: dict, t1, t2, e_dev, stream=None):
+    """cc_energy without a workspace, for callers that cannot allocate (see include/cc.h)."""
+    I = integrals_struct(ints)
+    A = cc_amps(_ptr(t1), _ptr(t2), None)
+    _check(_lib.cc_energy_noalloc(o, v, ctypes.byref(I), ctypes.byref(A), _ptr(e_dev), _stream(stream)),
+           "cc_energy_noalloc")
 
 
 @dataclass

@@ -13,7 +13,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
-SOURCES = ["kernels.cu", "tc_gemm.cu", "plan.cpp", "cc_api.cpp"]
+SOURCES = ["kernels.cu", "tc_gemm.cu", "no_alloc.cu", "plan.cpp", "cc_api.cpp"]
 
 
 def _mtime(p: str) -> float:

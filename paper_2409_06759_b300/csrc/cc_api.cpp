@@ -53,6 +53,8 @@ constexpr double kInnerDrop = 0.02;
 
 }  // namespace
 
+void ccb_set_last_error(const std::string &msg) { g_err = msg; }
+
 // Per-step CUDA-event timing (cc_plan_profile_enable).
 struct Profile {
     bool on = false;
