@@ -259,8 +259,14 @@ def main():
         tflop = st["flops"] * st["products"]
         achieved = tflop / t_kernel / 1e12
         peak = pk["bf16_tflops_sustained"]
+        # DRAM bytes of one launch, from the ncu capture of this kernel at o=20 v=100 scaled by the operand
+        # bytes (profiles/tc_gemm_ladder_o20_v100.md): valid for the ladder statement of this kernel version
+        traffic = None
+        if st["M"] == v * v and st["N"] == o * o and st["K"] == v * v and st.get("bn") == 256:
+            traffic = 1.07 * (st["Mp"] * st["Kp"] * 4 + st["Np"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tc_gemm_kernel (" + st["note"] + ")",
+                "traffic": traffic, "traffic_unit": "bytes per launch",
+                "kernel": "tc_gemm_kernel (" + st["note"] + ")",
                 "fp64_equiv_tflops": st["flops"] / t_kernel / 1e12, "ms_per_launch": t_kernel * 1e3,
                 "peak_kind": f"{pk_kind} bf16 sustained (tensor-pipe flops = {st['products']} products x 2MNK)"}
     else:
