@@ -371,6 +371,210 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+// ---- chunked-accumulation variant (the accurate split route, three planes)
+// TMEM holds two 128 x BN fp32 accumulators.  The MMA issuer alternates
+// between them every CH K blocks; eight epilogue warps drain the finished one
+// into float-float (hi, lo) registers with an exact two-sum, so fp32 rounding
+// only ever acts on CH*64-long partial sums.  Warp w (2..9) owns TMEM lanes
+// 32*(w%4).. and the column half (w-2)/4 of the tile.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <int NP, int BN, int STAGES, int CH>
+__global__ void __launch_bounds__(320, 1)
+    tc_gemm_chunked_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                           const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials, int kb_per_split,
+                           int *err_flag) {
+    using G = Cfg<NP, BN, STAGES>;
+    constexpr int HALF = BN / 2;                 // columns per epilogue warp
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *tiles = smem;
+    uint64_t *full = (uint64_t *)(smem + STAGES * G::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;             // [2] accumulator b complete
+    uint64_t *acce = accf + 2;                   // [2] accumulator b drained
+    uint32_t *tmem_slot = (uint32_t *)(acce + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    volatile int *consumed = abort_flag + 1;
+    int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (int)(d.Np / BN);
+    const int tile = blockIdx.x;
+    const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
+    const int64_t n0 = (int64_t)(tile % n_tiles) * BN;
+    const int kb_total = (int)(d.Kp / BK);
+    const int kb0 = (int)blockIdx.y * kb_per_split;
+    const int kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    const int kblocks = kb1 - kb0;
+    const int nch = (kblocks + CH - 1) / CH;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 8);              // one arrival per epilogue warp
+        }
+        *abort_flag = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 2 * BN);
+        tmem_relinquish();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < kblocks; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t *st = tiles + s * G::STAGE_BYTES;
+                mbar_expect_tx(&full[s], G::STAGE_BYTES);
+                for (int p = 0; p < NP; p++)
+                    tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)(p * d.Mp + m0));
+                for (int q = 0; q < NP; q++)
+                    tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK,
+                                (int)(q * d.Np + n0));
+                issued = kb + 1;
+            }
+            if (*abort_flag) {
+                for (int kb = *consumed; kb < issued; kb++) mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
+                atomicOr(err_flag, 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int committed = -1;              // last chunk whose accumulator was committed
+            for (int kb = 0; kb < kblocks; kb++) {
+                const int c = kb / CH, b = c & 1;
+                const bool first = (kb % CH) == 0;
+                if (first && c >= 2) {
+                    // the epilogue must have drained this buffer's previous chunk
+                    if (*abort_flag || !mbar_wait(&acce[b], (uint32_t)((c >> 1) - 1) & 1u)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    fence_after();
+                }
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&full[s], ph)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t st = smem_u32(tiles + s * G::STAGE_BYTES);
+                const uint32_t dt = tmem + (uint32_t)(b * BN);
+                for (int pr = 0; pr < d.nprod; pr++) {
+                    const uint32_t a0 = st + d.prod_a[pr] * G::A_BYTES;
+                    const uint32_t b0 = st + NP * G::A_BYTES + d.prod_b[pr] * G::B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++)
+                        mma_bf16(dt, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                 !(first && pr == 0 && kk == 0));
+                }
+                mma_commit(&empty[s]);
+                *consumed = kb + 1;
+                if ((kb % CH) == CH - 1 || kb == kblocks - 1) {
+                    mma_commit(&accf[b]);
+                    committed = c;
+                }
+            }
+            // on abort, still complete the pending chunks' barriers so the epilogue can finish
+            for (int c = committed + 1; c < nch; c++) mma_commit(&accf[c & 1]);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;              // column half
+        const int et = threadIdx.x - 64;            // 0..255
+        for (int c = et; c < BN; c += 256) {
+            const int64_t n = n0 + c;
+            coloff[c] = n < d.N ? grp_off(d.cn, n) : -1;
+        }
+        const int64_t m = m0 + q * 32 + lane;
+        const bool mok = m < d.M;
+        const int64_t roff = mok ? grp_off(d.cm, m) : 0;
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        float hi[HALF], lo[HALF];
+#pragma unroll
+        for (int j = 0; j < HALF; j++) { hi[j] = 0.f; lo[j] = 0.f; }
+        bool good = true;
+        for (int c = 0; c < nch; c++) {
+            const int b = c & 1;
+            bool ok = mbar_wait(&accf[b], (uint32_t)(c >> 1) & 1u);
+            fence_after();
+            ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+            if (!ok) {
+                good = false;
+                *abort_flag = 1;
+                if (lane == 0) atomicOr(err_flag, 1);
+                break;
+            }
+#pragma unroll
+            for (int c0 = 0; c0 < HALF; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + h * HALF + c0), r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    float s2, e2;
+                    two_sum(hi[c0 + j], __uint_as_float(r[j]), s2, e2);
+                    hi[c0 + j] = s2;
+                    lo[c0 + j] += e2;
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+        }
+        if (good && mok) {
+            if (gridDim.y > 1) {
+                double *P = partials + (int64_t)blockIdx.y * d.M * d.N;
+#pragma unroll
+                for (int j = 0; j < HALF; j++) {
+                    const int64_t n = n0 + h * HALF + j;
+                    if (n < d.N) P[n * d.M + m] = (double)hi[j] + (double)lo[j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < HALF; j++) {
+                    const int64_t co = coloff[h * HALF + j];
+                    if (co < 0) continue;
+                    double *p = C + roff + co;
+                    double val = d.alpha * ((double)hi[j] + (double)lo[j]);
+                    if (d.beta != 0.0) val += d.beta * *p;
+                    *p = val;
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -431,6 +635,36 @@ static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B,
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
+template <int NP, int BN, int STAGES, int CH>
+static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials,
+                                  int *err, cudaStream_t s) {
+    using G = Cfg<NP, BN, STAGES>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_chunked_kernel<NP, BN, STAGES, CH>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (d.Np % BN || d.Mp % BM || d.Kp % BK) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
+        return cudaErrorInvalidValue;
+    const int64_t tiles = (d.Mp / BM) * (d.Np / BN);
+    if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const int kb_total = (int)(d.Kp / BK);
+    const int sk = d.splitk > 1 ? d.splitk : 1;
+    const int per = (kb_total + sk - 1) / sk;
+    const int zs = (kb_total + per - 1) / per;
+    if (zs > 1 && !partials) return cudaErrorInvalidValue;
+    if (zs > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)tiles, (unsigned)zs);
+    tc_gemm_chunked_kernel<NP, BN, STAGES, CH><<<grid, 320, G::SMEM, s>>>(ma, mb, d, C, partials, per, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || zs == 1) return e;
+    return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
+}
+
 }  // namespace tc
 
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C, double *partials,
@@ -446,8 +680,9 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void 
         if (d.bn == 128) return tc::launch_cfg<2, 128, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
         if (d.bn == 64) return tc::launch_cfg<2, 64, 4>(d, Aplanes, Bplanes, C, partials, err_flag, s);
     } else if (d.nplanes_a == 3) {
-        if (d.bn == 128) return tc::launch_cfg<3, 128, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
-        if (d.bn == 64) return tc::launch_cfg<3, 64, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        // three planes: the accurate route, chunked float-float accumulation
+        if (d.bn == 128) return tc::launch_chunked<3, 128, 2, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        if (d.bn == 64) return tc::launch_chunked<3, 64, 3, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
     }
     return cudaErrorInvalidValue;
 }
