@@ -142,7 +142,7 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
     }
     size_t si = 0;
     if (!use_cache) pl->cache_filled = false;
-    if (P.flops_mixed > 0 && !pl->cache_filled)   // clear the bounded-wait status word
+    if (P.flops_mixed > 0 && !pl->cache_filled)   // clear the bounded-wait status word (once per solve)
         CC_CUDA(cudaMemsetAsync(w + P.flags_off, 0, sizeof(int), s));
     for (const Step &stp : P.steps) {
         if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si], s));
@@ -152,8 +152,10 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
                 pl->launches++;
                 break;
             case StepKind::ACCUM:
-                CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s));
-                pl->launches++;
+                if (!(stp.static_src && pl->cache_filled)) {
+                    CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s));
+                    pl->launches++;
+                }
                 break;
             case StepKind::GEMM:
                 if (!stp.mixed) {

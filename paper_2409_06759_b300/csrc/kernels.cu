@@ -44,20 +44,114 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const dou
             double val = d.alpha * acc;
             if (d.beta != 0.0) val += d.beta * out[oo];
             out[oo] = val;
-            // advance by 32 elements
+            // advance by 32 elements (compare-and-subtract carries)
             e += 32;
             int carry = 32;
             for (int k = d.nd - 1; k >= 0 && carry; k--) {
-                int64_t t = dig[k] + carry;
-                dig[k] = (int)(t % d.ext[k]);
-                carry = (int)(t / d.ext[k]);
+                int t = dig[k] + carry;
+                carry = 0;
+                const int ex = (int)d.ext[k];
+                while (t >= ex) { t -= ex; carry++; }
+                dig[k] = t;
             }
         }
     }
 }
 
+// Tiled variant: 32 x 32 tiles over two output dims, d0 = the innermost output
+// dim and d1 = a dim that carries some term's unit source stride; every other
+// dim is a batch index of the block.  Each term reads its source tile either
+// directly (lanes along d0) or through shared memory (lanes along d1, then
+// transposed), so reads and writes stay coalesced for the P(..) gathers.
+__global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, const double *__restrict__ src,
+                                                          double *__restrict__ out, int d0, int d1, unsigned tmask,
+                                                          int64_t tiles0, int64_t tiles1) {
+    __shared__ double sm[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
+    int64_t bid = blockIdx.x;
+    const int64_t t0 = bid % tiles0; bid /= tiles0;
+    const int64_t t1 = bid % tiles1; bid /= tiles1;
+    // batch digits (all dims except d0, d1), row-major over the remaining dims
+    int64_t obase = 0, sbase[kMaxPerms];
+    for (int p = 0; p < d.nperm; p++) sbase[p] = 0;
+    for (int k = d.nd - 1; k >= 0; k--) {
+        if (k == d0 || k == d1) continue;
+        const int64_t dig = bid % d.ext[k];
+        bid /= d.ext[k];
+        obase += dig * d.ostr[k];
+        for (int p = 0; p < d.nperm; p++) sbase[p] += dig * d.sstr[p][k];
+    }
+    const int64_t i0b = t0 * 32, i1b = t1 * 32;
+    const int64_t E0 = d.ext[d0], E1 = d.ext[d1];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int p = 0; p < d.nperm; p++) {
+        const int64_t s0 = d.sstr[p][d0], s1 = d.sstr[p][d1];
+        const int64_t base = sbase[p] + i0b * s0 + i1b * s1;
+        if (!((tmask >> p) & 1u)) {
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int64_t i1 = ty + 8 * r;
+                if (i0b + tx < E0 && i1b + i1 < E1) acc[r] += d.sign[p] * __ldg(src + base + tx * s0 + i1 * s1);
+            }
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int64_t i0 = ty + 8 * r;
+                sm[tx][i0] = (i1b + tx < E1 && i0b + i0 < E0) ? __ldg(src + base + tx * s1 + i0 * s0) : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[r] += d.sign[p] * sm[ty + 8 * r][tx];
+        }
+    }
+    const int64_t os0 = d.ostr[d0], os1 = d.ostr[d1];
+    double old[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int64_t i1 = ty + 8 * r;
+        const bool ok = i0b + tx < E0 && i1b + i1 < E1;
+        old[r] = (d.beta != 0.0 && ok) ? out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int64_t i1 = ty + 8 * r;
+        if (i0b + tx < E0 && i1b + i1 < E1)
+            out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = d.alpha * acc[r] + d.beta * old[r];
+    }
+}
+
 cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s) {
     if (d.total <= 0) return cudaSuccess;
+    // tiled path: the output's innermost dim and a partner dim both of extent >= 16
+    if (d.nd >= 2 && d.ext[d.nd - 1] >= 16) {
+        const int d0 = d.nd - 1;
+        int d1 = -1;
+        unsigned tmask = 0;
+        // partner: the dim holding a term's smallest source stride, when that is not d0
+        for (int p = 0; p < d.nperm; p++) {
+            int kmin = 0;
+            for (int k = 1; k < d.nd; k++)
+                if (d.ext[k] > 1 && (d.ext[kmin] <= 1 || d.sstr[p][k] < d.sstr[p][kmin])) kmin = k;
+            if (kmin != d0 && d.sstr[p][kmin] < d.sstr[p][d0]) {
+                if (d1 < 0) d1 = kmin;
+                if (kmin == d1) tmask |= 1u << p;
+            }
+        }
+        if (d1 < 0) {
+            // no transposed term: pair d0 with the largest remaining dim
+            for (int k = 0; k < d.nd - 1; k++)
+                if (d1 < 0 || d.ext[k] > d.ext[d1]) d1 = k;
+        }
+        if (d.ext[d1] >= 16) {
+            const int64_t tiles0 = (d.ext[d0] + 31) / 32, tiles1 = (d.ext[d1] + 31) / 32;
+            const int64_t blocks = tiles0 * tiles1 * (d.total / (d.ext[d0] * d.ext[d1]));
+            if (blocks <= 0x7fffffffLL) {
+                accum_tiled_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, src, out, d0, d1, tmask, tiles0, tiles1);
+                return cudaGetLastError();
+            }
+        }
+    }
     int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
     int64_t blocks = (runs + 7) / 8;
     if (blocks > 148 * 16) blocks = 148 * 16;
@@ -185,16 +279,16 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         cv[i] = n < d.N;
         co[i] = cv[i] ? grp_offset(d.cn, n) : 0;
     }
+    double old[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (!(rv[i] && cv[j])) continue;
-            double *p = C + ro[i] + co[j];
-            double val = d.alpha * acc[i][j];
-            if (d.beta != 0.0) val += d.beta * *p;
-            *p = val;
-        }
+        for (int j = 0; j < 4; j++) old[i][j] = (d.beta != 0.0 && rv[i] && cv[j]) ? C[ro[i] + co[j]] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (rv[i] && cv[j]) C[ro[i] + co[j]] = d.alpha * acc[i][j] + d.beta * old[i][j];
 }
 
 // ------------------------------------------------------------------ gemv
@@ -342,52 +436,69 @@ cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double 
 }
 
 // ------------------------------------------------------- iteration kernels
-// D for a residual element stored [i..][a..] row-major (rank occupied, then
-// rank virtual indices): sum of occupied minus sum of virtual orbital energies.
-__device__ __forceinline__ double denom(int rank, int o, int v, const double *fo, const double *fv, int64_t e) {
-    double d = 0.0;
-    int64_t x = e;
-    for (int k = 0; k < rank; k++) { d -= fv[x % v]; x /= v; }
-    for (int k = 0; k < rank; k++) { d += fo[x % o]; x /= o; }
-    return d;
+// Residual arrays are [occupied tuple][virtual tuple] row-major with
+// nvt = v^rank virtual tuples per occupied tuple.  One block row per occupied
+// tuple: its orbital-energy sum is formed once; the virtual tuple's is formed
+// from 32-bit digits.  D = sum f_occ - sum f_vir.
+__device__ __forceinline__ double occ_sum(int rank, int o, const double *fo, int64_t row) {
+    double s = 0.0;
+    for (int k = 0; k < rank; k++) { s += fo[row % o]; row /= o; }
+    return s;
+}
+__device__ __forceinline__ double vir_sum(int rank, int v, const double *fv, uint32_t col) {
+    double s = 0.0;
+    for (int k = 0; k < rank; k++) { s += fv[col % (uint32_t)v]; col /= (uint32_t)v; }
+    return s;
 }
 
-__global__ void denom_sub_kernel(int rank, int o, int v, const double *fo, const double *fv, const double *t,
-                                 double *r, int64_t n) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        r[e] -= denom(rank, o, v, fo, fv, e) * t[e];
+__global__ void __launch_bounds__(256) denom_sub_kernel(int rank, int o, int v, const double *fo, const double *fv,
+                                                        const double *t, double *r, int64_t rows, uint32_t nvt) {
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const double so = occ_sum(rank, o, fo, row);
+        const int64_t base = row * nvt;
+        for (uint32_t c = threadIdx.x; c < nvt; c += blockDim.x)
+            r[base + c] -= (so - vir_sum(rank, v, fv, c)) * t[base + c];
+    }
 }
 
-static int64_t count_of(int rank, int o, int v) {
-    int64_t n = 1;
-    for (int k = 0; k < rank; k++) n *= (int64_t)o * v;
-    return n;
+static void rows_cols(int rank, int o, int v, int64_t &rows, uint32_t &nvt) {
+    rows = 1;
+    int64_t c = 1;
+    for (int k = 0; k < rank; k++) { rows *= o; c *= v; }
+    nvt = (uint32_t)c;
 }
 
 cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv, const double *t, double *r,
                              cudaStream_t s) {
-    int64_t n = count_of(rank, o, v);
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 148 * 8) blocks = 148 * 8;
-    denom_sub_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, n);
+    int64_t rows;
+    uint32_t nvt;
+    rows_cols(rank, o, v, rows, nvt);
+    int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
+    denom_sub_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, rows, nvt);
     return cudaGetLastError();
 }
 
-__global__ void jacobi_kernel(int rank, int o, int v, const double *fo, const double *fv, const double *t,
-                              const double *r, double *xo, double *eo, int64_t n) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        double q = r[e] / denom(rank, o, v, fo, fv, e);
-        eo[e] = q;
-        xo[e] = t[e] + q;
+__global__ void __launch_bounds__(256) jacobi_kernel(int rank, int o, int v, const double *fo, const double *fv,
+                                                     const double *t, const double *r, double *xo, double *eo,
+                                                     int64_t rows, uint32_t nvt) {
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const double so = occ_sum(rank, o, fo, row);
+        const int64_t base = row * nvt;
+        for (uint32_t c = threadIdx.x; c < nvt; c += blockDim.x) {
+            const double q = r[base + c] / (so - vir_sum(rank, v, fv, c));
+            eo[base + c] = q;
+            xo[base + c] = t[base + c] + q;
+        }
     }
 }
 
 cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
                           const double *r, double *xo, double *eo, cudaStream_t s) {
-    int64_t n = count_of(rank, o, v);
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 148 * 8) blocks = 148 * 8;
-    jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, n);
+    int64_t rows;
+    uint32_t nvt;
+    rows_cols(rank, o, v, rows, nvt);
+    int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
+    jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, rows, nvt);
     return cudaGetLastError();
 }
 

@@ -576,10 +576,18 @@ struct Planner {
         std::vector<int> fa_order, fb_order, k_order;
 
         if (use_mixed) {
-            // the split kernels read any strided view: no permutes on this route
-            fa_order = fusable(A, FA).order;
-            fb_order = fusable(B, FB).order;
-            k_order = fusable(A, K).order;
+            // The split kernels read any strided view: no permutes on this route,
+            // and the row/column orders are free.  Rows and columns follow the
+            // output's stride order (consecutive rows -> the output's fastest
+            // index, so epilogue stores coalesce); K follows the larger operand.
+            if (perms.size() == 1 && perms[0].sigma.empty()) {
+                fa_order = fusable(out, FA).order;
+                fb_order = fusable(out, FB).order;
+            } else {
+                fa_order = fusable(A, FA).order;
+                fb_order = fusable(B, FB).order;
+            }
+            k_order = view_elems(A) >= view_elems(B) ? fusable(A, K).order : fusable(B, K).order;
             g.mixed = true;
         } else {
             Fuse fa = fusable(A, FA), ka = fusable(A, K), fb = fusable(B, FB), kb = fusable(B, K);
@@ -596,10 +604,23 @@ struct Planner {
                 std::vector<int> ord = forder;
                 ord.insert(ord.end(), korder.begin(), korder.end());
                 View w = contiguous_view(ord, X);
-                BufRef r = scratch(view_elems(w) * 8);
+                // an integral block's permuted copy is static: it lives in the cache region
+                // and is rebuilt only when the cache is invalid (every cc_residual call,
+                // once per cc_solve)
+                const bool stat = plan.tensors[X.tensor].kind == TKind::INTEGRAL;
+                BufRef r;
+                if (stat) {
+                    r.where = BufRef::WS;
+                    r.slot = 2;                 // cache-relative, rebased after planning
+                    r.off = cache_need;
+                    cache_need += align_up(view_elems(w) * 8);
+                } else {
+                    r = scratch(view_elems(w) * 8);
+                }
                 Step p = accum_step(w, r, X, xref, std::vector<Perm>(1, Perm{1.0, {}}), 1.0, 0.0);
+                p.static_src = stat;
                 p.stmt = si;
-                p.note = "permute " + plan.tensors[X.tensor].name;
+                p.note = std::string(stat ? "permute (cached) " : "permute ") + plan.tensors[X.tensor].name;
                 plan.steps.push_back(p);
                 w.tensor = X.tensor;
                 w.sign = X.sign;
@@ -781,8 +802,10 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     off += P.cache_need;
     plan.ws_bytes = off;
     for (auto &st : plan.steps) {
-        for (BufRef *r : {&st.out, &st.a, &st.b, &st.partials})
+        for (BufRef *r : {&st.out, &st.a, &st.b, &st.partials}) {
             if (r->where == BufRef::WS && r->slot == 1) { r->off += plan.scratch_off; r->slot = 0; }
+            if (r->where == BufRef::WS && r->slot == 2) { r->off += plan.cache_off; r->slot = 0; }
+        }
         if (st.mixed) {
             st.planes_a_off += st.a_static ? plan.cache_off : plan.scratch_off;
             st.planes_b_off += st.b_static ? plan.cache_off : plan.scratch_off;

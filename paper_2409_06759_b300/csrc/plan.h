@@ -60,6 +60,7 @@ struct Step {
     int64_t planes_a_off = 0, planes_b_off = 0;  // workspace byte offsets of the planes
     BufRef partials;                             // split-K partial sums (when splitk > 1)
     bool a_static = false, b_static = false;     // operand is an integral block (cacheable)
+    bool static_src = false;                     // ACCUM permute of an integral block into the cache
     double flops = 0.0;
     std::string note;
 };

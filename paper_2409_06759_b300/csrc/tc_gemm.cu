@@ -78,8 +78,53 @@ __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, cons
     }
 }
 
+// Transposed variant for sources whose unit stride lies in the row group:
+// a 32-row x 64-column tile is read with lanes along rows (coalesced), staged
+// in shared memory, and written K-major (16 bytes per lane per plane).
+__global__ void __launch_bounds__(256) split_bf16_rows_kernel(const SplitDesc d, const double *__restrict__ x,
+                                                              __nv_bfloat16 *__restrict__ planes) {
+    __shared__ double tile[64][33];
+    const int64_t plane_elems = d.Rp * d.Kp;
+    const int64_t rtiles = (d.Rp + 31) / 32, ktiles = d.Kp / 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int64_t t = blockIdx.x; t < rtiles * ktiles; t += gridDim.x) {
+        const int64_t r0 = (t % rtiles) * 32, k0 = (t / rtiles) * 64;
+        const int64_t r = r0 + tx;
+        const bool rok = r < d.R;
+        const int64_t roff = rok ? grp_off(d.gr, r) : 0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int64_t k = k0 + ty + 8 * j;
+            tile[ty + 8 * j][tx] = (rok && k < d.K) ? __ldg(x + roff + grp_off(d.gk, k)) : 0.0;
+        }
+        __syncthreads();
+        // 32 rows x 64 columns = 256 runs of 8 columns: one per thread
+        const int rr = threadIdx.x >> 3, kk = (threadIdx.x & 7) * 8;
+        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) split3(tile[kk + j][rr], h[j], m[j], l[j]);
+        const int64_t row = r0 + rr;
+        if (row < d.Rp) {
+            __nv_bfloat16 *p0 = planes + row * d.Kp + k0 + kk;
+            *reinterpret_cast<uint4 *>(p0) = *reinterpret_cast<const uint4 *>(h);
+            *reinterpret_cast<uint4 *>(p0 + plane_elems) = *reinterpret_cast<const uint4 *>(m);
+            if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = *reinterpret_cast<const uint4 *>(l);
+        }
+    }
+}
+
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s) {
     if (d.Kp % 64 || d.Rp <= 0 || d.nplanes < 2 || d.nplanes > 3) return cudaErrorInvalidValue;
+    // source unit stride inside the row group and not in K: transposed tiles
+    const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == 1;
+    const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == 1;
+    if (r_unit && !k_unit) {
+        const int64_t tiles = ((d.Rp + 31) / 32) * (d.Kp / 64);
+        int64_t blocks = tiles < 148 * 16 ? tiles : 148 * 16;
+        split_bf16_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes);
+        return cudaGetLastError();
+    }
     // vector path: innermost K digit contiguous with an extent that keeps 8-runs
     // inside it, every other stride even (16-byte aligned double2), base aligned
     int vec = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == 1 && d.gk.ext[d.gk.nd - 1] % 8 == 0 &&
@@ -350,14 +395,17 @@ __global__ void __launch_bounds__(192, 1)
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
                 tmem_ld_wait();
                 if (mok) {
+                    // loads of the 32 outputs are issued together, then the stores
+                    double old[32];
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int64_t co = coloff[c0 + j];
-                        if (co < 0) continue;
-                        double *p = C + roff + co;
-                        double val = d.alpha * (double)__uint_as_float(r[j]);
-                        if (d.beta != 0.0) val += d.beta * *p;
-                        *p = val;
+                        old[j] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int64_t co = coloff[c0 + j];
+                        if (co >= 0) C[roff + co] = d.alpha * (double)__uint_as_float(r[j]) + d.beta * old[j];
                     }
                 }
             }
@@ -556,13 +604,19 @@ __global__ void __launch_bounds__(320, 1)
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < HALF; j++) {
-                    const int64_t co = coloff[h * HALF + j];
-                    if (co < 0) continue;
-                    double *p = C + roff + co;
-                    double val = d.alpha * ((double)hi[j] + (double)lo[j]);
-                    if (d.beta != 0.0) val += d.beta * *p;
-                    *p = val;
+                for (int j0 = 0; j0 < HALF; j0 += 16) {
+                    double old[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int64_t co = coloff[h * HALF + j0 + j];
+                        old[j] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int64_t co = coloff[h * HALF + j0 + j];
+                        if (co >= 0)
+                            C[roff + co] = d.alpha * ((double)hi[j0 + j] + (double)lo[j0 + j]) + d.beta * old[j];
+                    }
                 }
             }
         }
