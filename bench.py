@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 METRIC = "CC residual TFLOP/s and s/iter on 1 B300, mixed vs FP64 at |ΔE|<1e-6 Eh"
 WORKLOAD = "spin-orbital CCSD o=40 v=200 L=120 seed=0, FP64 real, synthetic integrals"
 SMALL = "spin-orbital CCSD o=10 v=40 L=120 seed=0, FP64 real, synthetic integrals"
+# DRAM bytes / operand-plane bytes of the ladder kernel, from its ncu capture (None until re-captured
+# after a kernel change)
+TRAFFIC_RATIO = None
 
 
 def peaks():
@@ -260,11 +263,11 @@ def main():
         achieved = tflop / t_kernel / 1e12
         # the kernel runs ~10 ms inside a ~50 ms step: the burst figure is the denominator
         peak = pk["bf16_tflops"]
-        # DRAM bytes of one launch, from the ncu capture of this kernel at o=20 v=100 scaled by the operand
-        # bytes (profiles/tc_gemm_ladder_o20_v100.md): valid for the ladder statement of this kernel version
+        # DRAM bytes of one launch, from the ncu capture of this kernel version at o=20 v=100, scaled by
+        # the operand bytes that dominate it (profiles/tc_gemm_ladder_o20_v100.md); None until captured
         traffic = None
-        if st["M"] == v * v and st["N"] == o * o and st["K"] == v * v and st.get("bn") == 256:
-            traffic = 1.07 * (st["Mp"] * st["Kp"] * 4 + st["Np"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
+        if TRAFFIC_RATIO is not None and st["M"] == v * v and st["N"] == o * o and st["K"] == v * v:
+            traffic = TRAFFIC_RATIO * (st["Mp"] * st["Kp"] * 4 + st["Np"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": "tc_gemm_kernel (" + st["note"] + ")",

@@ -153,7 +153,8 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
                 break;
             case StepKind::ACCUM:
                 if (!(stp.static_src && pl->cache_filled)) {
-                    CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s));
+                    CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s,
+                                         stp.acc.two_src ? resolve(stp.b, I, A, R, w) : nullptr));
                     pl->launches++;
                 }
                 break;
@@ -165,11 +166,11 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
                     pl->launches += stp.gemm.splitk > 1 ? 2 : 1;
                 } else {
                     void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
-                    if (!(stp.a_static && pl->cache_filled)) {
+                    if (!(stp.a_static && pl->cache_filled) && !stp.skip_a) {
                         CC_CUDA(launch_split_bf16(stp.split_a, resolve(stp.a, I, A, R, w), pa, s));
                         pl->launches++;
                     }
-                    if (!(stp.b_static && pl->cache_filled)) {
+                    if (!(stp.b_static && pl->cache_filled) && !stp.skip_b) {
                         CC_CUDA(launch_split_bf16(stp.split_b, resolve(stp.b, I, A, R, w), pb, s));
                         pl->launches++;
                     }

@@ -16,7 +16,7 @@ namespace ccb {
 constexpr int kAccChunk = 8;
 
 __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const double *__restrict__ src,
-                                                    double *__restrict__ out) {
+                                                    double *__restrict__ out, const double *__restrict__ src2) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -39,7 +39,13 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const dou
             for (int p = 0; p < d.nperm; p++) {
                 int64_t so = 0;
                 for (int k = 0; k < d.nd; k++) so += dig[k] * d.sstr[p][k];
-                acc += d.sign[p] * __ldg(src + so);
+                double x = __ldg(src + so);
+                if (d.two_src) {
+                    int64_t so2 = 0;
+                    for (int k = 0; k < d.nd; k++) so2 += dig[k] * d.sstr2[p][k];
+                    x *= __ldg(src2 + so2);
+                }
+                acc += d.sign[p] * x;
             }
             double val = d.alpha * acc;
             if (d.beta != 0.0) val += d.beta * out[oo];
@@ -121,10 +127,10 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
     }
 }
 
-cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s) {
+cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s, const double *src2) {
     if (d.total <= 0) return cudaSuccess;
     // tiled path: the output's innermost dim and a partner dim both of extent >= 16
-    if (d.nd >= 2 && d.ext[d.nd - 1] >= 16) {
+    if (!d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 16) {
         const int d0 = d.nd - 1;
         int d1 = -1;
         unsigned tmask = 0;
@@ -155,7 +161,7 @@ cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cud
     int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
     int64_t blocks = (runs + 7) / 8;
     if (blocks > 148 * 16) blocks = 148 * 16;
-    accum_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, src, out);
+    accum_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, src, out, src2);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,8 @@ struct Grp {
 // over the nd-dimensional index box ext[]; the output is visited in the
 // row-major order of ext (out strides arbitrary).  Covers permutes (TTGT
 // transposes), copies, and the antisymmetrising epilogues P(..).
+// two_src: each term is the product src[sstr . idx] * src2[sstr2 . idx] (an
+// outer product with permutation operators, formed directly in the output).
 struct AccumDesc {
     int nd;
     int nperm;
@@ -31,6 +33,8 @@ struct AccumDesc {
     int64_t sstr[kMaxPerms][kMaxDims];
     double sign[kMaxPerms];
     double alpha, beta;
+    int two_src;
+    int64_t sstr2[kMaxPerms][kMaxDims];
 };
 
 // C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), FP64.
@@ -71,7 +75,8 @@ struct TcGemmDesc {
     int splitk;
 };
 
-cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s);
+cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s,
+                         const double *src2 = nullptr);
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
 cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, double *partials,
                             cudaStream_t s);

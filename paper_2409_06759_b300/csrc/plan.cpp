@@ -239,7 +239,39 @@ struct Planner {
     int64_t scratch_need = 0;       // arena bytes of the current statement
     int64_t cache_need = 0;         // static split planes
     int64_t interm_need = kAlign;   // [status word][intermediates...] at the start of the workspace
+    int64_t splits_need = 0;        // planes of non-static split operands, kept for reuse within a residual
     bool mixed_all = false;
+    std::vector<int> version;       // per tensor: number of statements that wrote it so far
+
+    // one split of a tensor version into planes, reusable by later steps
+    struct SplitRec {
+        int tensor, version, np;
+        SplitDesc d;
+        int64_t off;
+    };
+    std::vector<SplitRec> splits;
+
+    static bool same_grp(const Grp &a, const Grp &b) {
+        if (a.nd != b.nd) return false;
+        for (int k = 0; k < a.nd; k++)
+            if (a.ext[k] != b.ext[k] || a.str[k] != b.str[k]) return false;
+        return true;
+    }
+    // offset of the planes (split-region relative) and whether they already exist
+    int64_t split_slot(int tensor, const SplitDesc &d, bool &exists) {
+        const int ver = version[tensor];
+        for (auto &r : splits)
+            if (r.tensor == tensor && r.version == ver && r.np == d.nplanes && r.d.R == d.R && r.d.K == d.K &&
+                r.d.Rp == d.Rp && r.d.Kp == d.Kp && same_grp(r.d.gr, d.gr) && same_grp(r.d.gk, d.gk)) {
+                exists = true;
+                return r.off;
+            }
+        exists = false;
+        SplitRec r{tensor, ver, d.nplanes, d, splits_need};
+        splits_need += align_up(d.Rp * d.Kp * 2 * d.nplanes);
+        splits.push_back(r);
+        return r.off;
+    }
 
     explicit Planner(Plan &pl) : plan(pl), o(pl.o), v(pl.v) {}
 
@@ -257,6 +289,7 @@ struct Planner {
         t.elems = e;
         if (k == TKind::INTERM) { t.ws_off = interm_need; interm_need += align_up(e * 8); }
         plan.tensors.push_back(t);
+        version.push_back(0);
         initialized.push_back(k != TKind::RES && k != TKind::INTERM);
         by_name[name] = (int)plan.tensors.size() - 1;
         return (int)plan.tensors.size() - 1;
@@ -490,9 +523,12 @@ struct Planner {
         return e;
     }
 
+    int last_out = 0;
+
     bool plan_stmt(const Stmt &s, const std::vector<char> &lsp, int si) {
         View out;
         if (!resolve(s.out, true, s.op, lsp, out)) return false;
+        last_out = out.tensor;
         const Tensor T = plan.tensors[out.tensor];
         if (T.kind != TKind::RES && T.kind != TKind::INTERM) { err = "output must be a residual or an intermediate"; return false; }
         std::vector<View> in(s.rhs.size());
@@ -551,6 +587,26 @@ struct Planner {
         F.insert(FB.begin(), FB.end());
         if (F != O) { err = "output indices must be exactly the uncontracted operand indices"; return false; }
 
+        if (K.empty()) {
+            // outer product: each output element is formed directly as a sum of
+            // signed products (no GEMM, no scratch, no separate antisymmetrisation)
+            Step st = accum_step(out, outref, in[0], tensor_ref(in[0].tensor), perms, alpha, beta);
+            st.acc.two_src = 1;
+            for (int p = 0; p < st.acc.nperm; p++)
+                for (int k = 0; k < st.acc.nd; k++) {
+                    int mu = out.idx[k], pre = mu;
+                    for (auto &kv : perms[p].sigma)
+                        if (kv.second == mu) pre = kv.first;
+                    st.acc.sstr[p][k] = str_of(in[0], pre);
+                    st.acc.sstr2[p][k] = str_of(in[1], pre);
+                }
+            st.b = tensor_ref(in[1].tensor);
+            st.stmt = si;
+            st.note = "outer " + plan.tensors[in[0].tensor].name + "*" + plan.tensors[in[1].tensor].name + " -> " + T.name;
+            plan.steps.push_back(st);
+            return true;
+        }
+
         // GEMM rows (A side) get the operand whose free indices hold the
         // output's fastest index, so epilogue stores coalesce along rows.
         int ia = 0, ib = 1;
@@ -566,7 +622,10 @@ struct Planner {
         for (int l : K) Kx *= ext_of(A, l);
         const double flops = 2.0 * (double)Mx * (double)Nx * (double)Kx;
         scratch_need = 0;
-        const bool use_mixed = plan.precision != 0 && (mixed_all || flops >= 4.0e9);
+        // split-bf16 route: contractions of >= 2e8 flops that are real GEMMs
+        // (matrix-vector shapes stay on the memory-bound FP64 kernels)
+        const bool use_mixed = plan.precision != 0 &&
+                               (mixed_all || (flops >= 2.0e8 && Mx > 1 && Nx > 1 && Kx > 1));
 
         Step g;
         g.kind = StepKind::GEMM;
@@ -732,10 +791,12 @@ struct Planner {
             g.a_static = plan.tensors[A.tensor].kind == TKind::INTEGRAL;
             g.b_static = plan.tensors[B.tensor].kind == TKind::INTEGRAL;
             const int64_t bytes_a = t.Mp * t.Kp * 2 * np, bytes_b = t.Np * t.Kp * 2 * np;
+            // static planes live in the cache; other planes in the split region, shared by
+            // every later step that splits the same version of the same view
             if (g.a_static) { g.planes_a_off = cache_need; cache_need += align_up(bytes_a); }
-            else { g.planes_a_off = scratch(bytes_a).off; }
+            else { g.planes_a_off = split_slot(A.tensor, sa, g.skip_a); }
             if (g.b_static) { g.planes_b_off = cache_need; cache_need += align_up(bytes_b); }
-            else { g.planes_b_off = scratch(bytes_b).off; }
+            else { g.planes_b_off = split_slot(B.tensor, sb, g.skip_b); }
             plan.flops_mixed += flops;
         }
         plan.flops += flops;
@@ -787,6 +848,7 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
             err = "line " + std::to_string(lineno) + ": " + P.err;
             return false;
         }
+        P.version[P.last_out]++;   // the statement's output has a new version
         max_scratch = std::max(max_scratch, P.scratch_need);
     }
     if (plan.stmt_text.empty()) { err = "empty contraction list"; return false; }
@@ -797,6 +859,9 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     plan.scratch_off = off;
     plan.scratch_bytes = max_scratch;
     off += max_scratch;
+    plan.splits_off = off;
+    plan.splits_bytes = P.splits_need;
+    off += P.splits_need;
     plan.cache_off = off;
     plan.cache_bytes = P.cache_need;
     off += P.cache_need;
@@ -807,8 +872,8 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
             if (r->where == BufRef::WS && r->slot == 2) { r->off += plan.cache_off; r->slot = 0; }
         }
         if (st.mixed) {
-            st.planes_a_off += st.a_static ? plan.cache_off : plan.scratch_off;
-            st.planes_b_off += st.b_static ? plan.cache_off : plan.scratch_off;
+            st.planes_a_off += st.a_static ? plan.cache_off : plan.splits_off;
+            st.planes_b_off += st.b_static ? plan.cache_off : plan.splits_off;
         }
     }
     return true;
@@ -854,7 +919,8 @@ std::string describe_plan(const Plan &plan) {
                << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta
                << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp << ",\"bn\":" << s.tc.bn
                << ",\"splitk\":" << s.tc.splitk
-               << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off;
+               << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off
+               << ",\"reuse_a\":" << (s.skip_a ? 1 : 0) << ",\"reuse_b\":" << (s.skip_b ? 1 : 0);
         } else if (s.kind == StepKind::ACCUM) {
             os << ",\"elems\":" << s.acc.total << ",\"terms\":" << s.acc.nperm << ",\"alpha\":" << s.acc.alpha
                << ",\"beta\":" << s.acc.beta;

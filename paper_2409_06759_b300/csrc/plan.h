@@ -61,6 +61,7 @@ struct Step {
     BufRef partials;                             // split-K partial sums (when splitk > 1)
     bool a_static = false, b_static = false;     // operand is an integral block (cacheable)
     bool static_src = false;                     // ACCUM permute of an integral block into the cache
+    bool skip_a = false, skip_b = false;         // planes already split by an earlier step (same source version)
     double flops = 0.0;
     std::string note;
 };
@@ -78,6 +79,7 @@ struct Plan {
     int64_t interm_bytes = 0;
     int64_t scratch_off = 0, scratch_bytes = 0;
     int64_t cache_off = 0, cache_bytes = 0;   // static split planes
+    int64_t splits_off = 0, splits_bytes = 0; // per-iteration split planes shared between steps
     double flops = 0.0;
     double flops_mixed = 0.0;   // flops of steps on the split-bf16 route (fp64-equivalent)
     int verbose = 0;

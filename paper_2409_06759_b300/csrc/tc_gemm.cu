@@ -419,6 +419,211 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+// ---- persistent variant (two planes): one CTA per SM walks the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... of the (tile, K-slice) space.
+// The producer streams K blocks of consecutive tiles through the stage ring
+// without a break; the MMA issuer alternates between two TMEM accumulators so
+// the epilogue of one tile overlaps the main loop of the next.
+template <int NP, int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                              const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials,
+                              int kb_per_split, int nslices, int64_t ntiles, int *err_flag) {
+    using G = Cfg<NP, BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *tiles = smem;
+    uint64_t *full = (uint64_t *)(smem + STAGES * G::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;             // [2]
+    uint64_t *acce = accf + 2;                   // [2]
+    uint32_t *tmem_slot = (uint32_t *)(acce + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    volatile int *epi_abort = abort_flag + 1;    // written by epilogue warps only (uniform decision)
+    int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);   // [BN]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (int)(d.Np / BN);
+    const int kb_total = (int)(d.Kp / BK);
+    const int64_t total = ntiles * nslices;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);              // one arrival per epilogue warp
+        }
+        *abort_flag = 0;
+        *epi_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 2 * BN);
+        tmem_relinquish();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto tile_coords = [&](int64_t t, int64_t &m0, int64_t &n0, int &kb0, int &kb1) {
+        const int64_t tile = t % ntiles;
+        const int z = (int)(t / ntiles);
+        m0 = (tile / n_tiles) * BM;
+        n0 = (tile % n_tiles) * BN;
+        kb0 = z * kb_per_split;
+        kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t g = 0;                       // K blocks issued by this CTA so far
+            bool stop = false;
+            for (int64_t t = blockIdx.x; t < total && !stop; t += gridDim.x) {
+                int64_t m0, n0;
+                int kb0, kb1;
+                tile_coords(t, m0, n0, kb0, kb1);
+                for (int kb = kb0; kb < kb1; kb++, g++) {
+                    const int s = (int)(g % STAGES);
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    uint8_t *st = tiles + s * G::STAGE_BYTES;
+                    mbar_expect_tx(&full[s], G::STAGE_BYTES);
+                    for (int p = 0; p < NP; p++)
+                        tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], kb * BK, (int)(p * d.Mp + m0));
+                    for (int q = 0; q < NP; q++)
+                        tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BK,
+                                    (int)(q * d.Np + n0));
+                }
+            }
+            if (stop) {
+                // let the last STAGES issued copies land before the CTA can exit
+                for (int64_t k = (g > STAGES ? g - STAGES : 0); k < g; k++)
+                    mbar_wait(&full[k % STAGES], (uint32_t)(k / STAGES) & 1u);
+                atomicOr(err_flag, 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int64_t g = 0;
+            int j = 0;                           // local tile counter
+            for (int64_t t = blockIdx.x; t < total; t += gridDim.x, j++) {
+                if (*abort_flag) break;
+                int64_t m0, n0;
+                int kb0, kb1;
+                tile_coords(t, m0, n0, kb0, kb1);
+                const int b = j & 1;
+                if (j >= 2) {
+                    if (!mbar_wait(&acce[b], (uint32_t)((j >> 1) - 1) & 1u)) {
+                        *abort_flag = 1;
+                        atomicOr(err_flag, 1);
+                    }
+                    fence_after();
+                }
+                const uint32_t dt = tmem + (uint32_t)(b * BN);
+                for (int kb = kb0; kb < kb1 && !*abort_flag; kb++, g++) {
+                    const int s = (int)(g % STAGES);
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (!mbar_wait(&full[s], ph)) {
+                        *abort_flag = 1;
+                        atomicOr(err_flag, 1);
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t st = smem_u32(tiles + s * G::STAGE_BYTES);
+                    for (int pr = 0; pr < d.nprod; pr++) {
+                        const uint32_t a0 = st + d.prod_a[pr] * G::A_BYTES;
+                        const uint32_t b0 = st + NP * G::A_BYTES + d.prod_b[pr] * G::B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; kk++)
+                            mma_bf16(dt, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                     ((kb - kb0) | pr | kk) != 0);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&accf[b]);            // tile j's accumulator (complete, or abandoned on abort)
+            }
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const int et = threadIdx.x - 64;         // 0..127
+        int j = 0;
+        for (int64_t t = blockIdx.x; t < total; t += gridDim.x, j++) {
+            int64_t m0, n0;
+            int kb0, kb1;
+            tile_coords(t, m0, n0, kb0, kb1);
+            const int b = j & 1;
+            const bool split = nslices > 1;
+            asm volatile("bar.sync 1, 128;" ::: "memory");   // previous tile's coloff reads are done
+            for (int c = et; c < BN; c += 128) {
+                const int64_t n = n0 + c;
+                coloff[c] = n < d.N ? (split ? n : grp_off(d.cn, n)) : -1;
+            }
+            const int64_t m = m0 + q * 32 + lane;
+            const bool mok = m < d.M;
+            const int64_t roff = mok ? (split ? 0 : grp_off(d.cm, m)) : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            bool ok = mbar_wait(&accf[b], (uint32_t)(j >> 1) & 1u);
+            fence_after();
+            ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+            if (!ok) *epi_abort = 1;
+            // all four epilogue warps take the same decision (only they write epi_abort)
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (*epi_abort) {
+                *abort_flag = 1;
+                if (lane == 0) atomicOr(err_flag, 1);
+                break;
+            }
+            double *P = split ? partials + (t / ntiles) * d.M * d.N : nullptr;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), r);
+                tmem_ld_wait();
+                if (mok) {
+                    if (split) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj++) {
+                            const int64_t n = coloff[c0 + jj];
+                            if (n >= 0) P[n * d.M + m] = (double)__uint_as_float(r[jj]);
+                        }
+                    } else {
+                        double old[32];
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj++) {
+                            const int64_t co = coloff[c0 + jj];
+                            old[jj] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj++) {
+                            const int64_t co = coloff[c0 + jj];
+                            if (co >= 0) C[roff + co] = d.alpha * (double)__uint_as_float(r[jj]) + d.beta * old[jj];
+                        }
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
 // ---- chunked-accumulation variant (the accurate split route, three planes)
 // TMEM holds two 128 x BN fp32 accumulators.  The MMA issuer alternates
 // between them every CH K blocks; eight epilogue warps drain the finished one
@@ -689,6 +894,35 @@ static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B,
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
+template <int NP, int BN, int STAGES>
+static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials,
+                                     int *err, cudaStream_t s) {
+    using G = Cfg<NP, BN, STAGES>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_persistent_kernel<NP, BN, STAGES>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (d.Np % BN || d.Mp % BM || d.Kp % BK) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
+        return cudaErrorInvalidValue;
+    const int64_t ntiles = (d.Mp / BM) * (d.Np / BN);
+    const int kb_total = (int)(d.Kp / BK);
+    const int sk = d.splitk > 1 ? d.splitk : 1;
+    const int per = (kb_total + sk - 1) / sk;
+    const int zs = (kb_total + per - 1) / per;
+    if (zs > 1 && !partials) return cudaErrorInvalidValue;
+    const int64_t total = ntiles * zs;
+    const int grid = (int)(total < 148 ? total : 148);
+    tc_gemm_persistent_kernel<NP, BN, STAGES><<<grid, 192, G::SMEM, s>>>(ma, mb, d, C, partials, per, zs, ntiles, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || zs == 1) return e;
+    return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
+}
+
 template <int NP, int BN, int STAGES, int CH>
 static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials,
                                   int *err, cudaStream_t s) {
@@ -730,9 +964,9 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void 
         if (((uintptr_t)Aplanes & 15) || ((uintptr_t)Bplanes & 15)) return cudaErrorMisalignedAddress;
     }
     if (d.nplanes_a == 2) {
-        if (d.bn == 256) return tc::launch_cfg<2, 256, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
-        if (d.bn == 128) return tc::launch_cfg<2, 128, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
-        if (d.bn == 64) return tc::launch_cfg<2, 64, 4>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        if (d.bn == 256) return tc::launch_persistent<2, 256, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        if (d.bn == 128) return tc::launch_persistent<2, 128, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+        if (d.bn == 64) return tc::launch_persistent<2, 64, 4>(d, Aplanes, Bplanes, C, partials, err_flag, s);
     } else if (d.nplanes_a == 3) {
         // three planes: the accurate route, chunked float-float accumulation
         if (d.bn == 128) return tc::launch_chunked<3, 128, 2, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
