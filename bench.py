@@ -30,7 +30,7 @@ WORKLOAD = "spin-orbital CCSD o=40 v=200 L=120 seed=0, FP64 real, synthetic inte
 SMALL = "spin-orbital CCSD o=10 v=40 L=120 seed=0, FP64 real, synthetic integrals"
 # DRAM bytes / operand-plane bytes of the ladder kernel, from its ncu capture (None until re-captured
 # after a kernel change)
-TRAFFIC_RATIO = None
+TRAFFIC_RATIO = 1.066
 
 
 def peaks():
