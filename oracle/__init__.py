@@ -29,10 +29,22 @@ _LIB = os.path.join(_HERE, "libccoracle.so")
 _lib = None
 
 
+class _Complex(ctypes.Structure):
+    """C99 double complex returned by value (two doubles)."""
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
 def build(force: bool = False) -> str:
-    """Compile cc_oracle.c into libccoracle.so (gcc -O2 -fopenmp)."""
+    """Compile cc_oracle.c twice (real orc_*, complex orz_*) into libccoracle.so."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            objs = []
+            for tag, flags in (("real", []), ("cplx", ["-DCC_COMPLEX"])):
+                obj = os.path.join(td, tag + ".o")
+                subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", *flags, "-c", _SRC, "-o", obj])
+                objs.append(obj)
+            subprocess.check_call(["gcc", "-shared", "-fopenmp", "-o", _LIB, *objs, "-lm"])
     return _LIB
 
 
@@ -52,6 +64,15 @@ def lib():
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_ccsd_r2_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), dp]
+        vp = ctypes.c_void_p
+        L.orz_antisym_integrals.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.orz_ccsd_residual.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, vp, vp, vp, vp]
+        L.orz_ccsd_energy.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        L.orz_ccsd_energy.restype = _Complex
+        L.orz_ccsd_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, vp, vp, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, vp, dp, ctypes.POINTER(ctypes.c_int)]
+        L.orz_ccsd_r2_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp, vp, vp, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), vp]
         _lib = L
     return _lib
 
@@ -61,14 +82,29 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _z(a: np.ndarray):
+    assert a.dtype == np.complex128 and a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _cplx(*arrays) -> bool:
+    return any(np.iscomplexobj(a) for a in arrays if a is not None)
+
+
 def num_threads() -> int:
     return lib().orc_num_threads()
 
 
 def antisym_integrals(o: int, v: int, B: np.ndarray) -> np.ndarray:
-    """Full <pq||rs> tensor [n][n][n][n] from B[L][n][n] (Eq. ham2q)."""
-    B = np.ascontiguousarray(B, dtype=np.float64)
+    """Full <pq||rs> tensor [n][n][n][n] from B[L][n][n] (Eq. ham2q); complex B gives complex V."""
     n = o + v
+    if np.iscomplexobj(B):
+        B = np.ascontiguousarray(B, dtype=np.complex128)
+        V = np.empty((n, n, n, n), dtype=np.complex128)
+        if lib().orz_antisym_integrals(o, v, B.shape[0], _z(B), _z(V)) != 0:
+            raise MemoryError("oracle integral build failed")
+        return V
+    B = np.ascontiguousarray(B, dtype=np.float64)
     V = np.empty((n, n, n, n))
     if lib().orc_antisym_integrals(o, v, B.shape[0], _p(B), _p(V)) != 0:
         raise MemoryError("oracle integral build failed")
@@ -76,6 +112,15 @@ def antisym_integrals(o: int, v: int, B: np.ndarray) -> np.ndarray:
 
 
 def ccsd_residual(o, v, eps, V, t1, t2):
+    if _cplx(V, t1, t2):
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        V = np.ascontiguousarray(V, dtype=np.complex128)
+        t1 = np.ascontiguousarray(t1, dtype=np.complex128)
+        t2 = np.ascontiguousarray(t2, dtype=np.complex128)
+        r1 = np.empty((o, v), dtype=np.complex128); r2 = np.empty((o, o, v, v), dtype=np.complex128)
+        if lib().orz_ccsd_residual(o, v, _p(eps), _z(V), _z(t1), _z(t2), _z(r1), _z(r2)) != 0:
+            raise MemoryError("oracle residual failed")
+        return r1, r2
     eps = np.ascontiguousarray(eps, dtype=np.float64)
     t1 = np.ascontiguousarray(t1, dtype=np.float64)
     t2 = np.ascontiguousarray(t2, dtype=np.float64)
@@ -88,6 +133,18 @@ def ccsd_residual(o, v, eps, V, t1, t2):
 def ccsd_r2_sample(o, v, B, eps, t1, t2, idx):
     """R2[i,j,a,b] for each row (i, j, a, b) of idx, integrals formed from B on
     demand (large systems)."""
+    if _cplx(B, t1, t2):
+        B = np.ascontiguousarray(B, dtype=np.complex128)
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        t1 = np.ascontiguousarray(t1, dtype=np.complex128)
+        t2 = np.ascontiguousarray(t2, dtype=np.complex128)
+        idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 4)
+        out = np.empty(idx.shape[0], dtype=np.complex128)
+        rc = lib().orz_ccsd_r2_sample(o, v, B.shape[0], _z(B), _p(eps), _z(t1), _z(t2), idx.shape[0],
+                                      idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _z(out))
+        if rc != 0:
+            raise MemoryError("oracle sampled residual failed")
+        return out
     B = np.ascontiguousarray(B, dtype=np.float64)
     eps = np.ascontiguousarray(eps, dtype=np.float64)
     t1 = np.ascontiguousarray(t1, dtype=np.float64)
@@ -101,7 +158,13 @@ def ccsd_r2_sample(o, v, B, eps, t1, t2, idx):
     return out
 
 
-def ccsd_energy(o, v, V, t1, t2) -> float:
+def ccsd_energy(o, v, V, t1, t2):
+    if _cplx(V, t1, t2):
+        V = np.ascontiguousarray(V, dtype=np.complex128)
+        t1 = np.ascontiguousarray(t1, dtype=np.complex128)
+        t2 = np.ascontiguousarray(t2, dtype=np.complex128)
+        e = lib().orz_ccsd_energy(o, v, _z(V), _z(t1), _z(t2))
+        return complex(e.re, e.im)
     t1 = np.ascontiguousarray(t1, dtype=np.float64)
     t2 = np.ascontiguousarray(t2, dtype=np.float64)
     return lib().orc_ccsd_energy(o, v, _p(V), _p(t1), _p(t2))
@@ -118,6 +181,16 @@ def diis_coeffs(Bmat: np.ndarray):
 def ccsd_solve(o, v, eps, V, t1=None, t2=None, tol=1e-8, maxiter=100, diis_max=8):
     """Jacobi + DIIS from (t1, t2) (zeros by default).  Returns a dict."""
     eps = np.ascontiguousarray(eps, dtype=np.float64)
+    if _cplx(V, t1, t2):
+        V = np.ascontiguousarray(V, dtype=np.complex128)
+        t1 = np.zeros((o, v), complex) if t1 is None else np.array(t1, dtype=np.complex128, order="C")
+        t2 = np.zeros((o, o, v, v), complex) if t2 is None else np.array(t2, dtype=np.complex128, order="C")
+        en = np.zeros(maxiter, dtype=np.complex128); rn = np.zeros(maxiter); it = ctypes.c_int(0)
+        st = lib().orz_ccsd_solve(o, v, _p(eps), _z(V), _z(t1), _z(t2), tol, maxiter, diis_max, _z(en), _p(rn),
+                                  ctypes.byref(it))
+        k = it.value
+        return dict(status=st, iters=k, energies=en[:k], rnorms=rn[:k], t1=t1, t2=t2,
+                    energy=en[k - 1] if k else complex("nan"))
     t1 = np.zeros((o, v)) if t1 is None else np.array(t1, dtype=np.float64, order="C")
     t2 = np.zeros((o, o, v, v)) if t2 is None else np.array(t2, dtype=np.float64, order="C")
     en = np.zeros(maxiter); rn = np.zeros(maxiter); it = ctypes.c_int(0)

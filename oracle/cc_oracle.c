@@ -33,18 +33,35 @@
 
 typedef long long ll;
 
+/* The same source is compiled twice: real (orc_*) and, with CC_COMPLEX,
+ * complex double (orz_*) for complex Hermitian integrals (relativistic
+ * spinors).  The CC equations are polynomial in t and <pq||rs> with no
+ * conjugation, so only the scalar type changes; norms and DIIS overlaps use
+ * Re<x|y>, orbital energies and denominators stay real. */
+#ifdef CC_COMPLEX
+typedef double complex sc;
+#define FN(name) orz_##name
+#define ABS2(x) (creal(x) * creal(x) + cimag(x) * cimag(x))
+#define RDOT(a, b) (creal(a) * creal(b) + cimag(a) * cimag(b))
+#else
+typedef double sc;
+#define FN(name) orc_##name
+#define ABS2(x) ((x) * (x))
+#define RDOT(a, b) ((a) * (b))
+#endif
+
 /* ---------------------------------------------------------------- integrals */
 
 /* <pq||rs> = (pr|qs) - (ps|qr),  (pq|rs) = sum_L B[L][p][q] B[L][r][s]. */
-int orc_antisym_integrals(int o, int v, int L, const double *B, double *V)
+int FN(antisym_integrals)(int o, int v, int L, const sc *B, sc *V)
 {
     const ll n = o + v;
-    double *chem = (double *)malloc(sizeof(double) * n * n * n * n);
+    sc *chem = (sc *)malloc(sizeof(sc) * n * n * n * n);
     if (!chem) return 1;
 #pragma omp parallel for schedule(static)
     for (ll pq = 0; pq < n * n; pq++) {
         for (ll rs = 0; rs < n * n; rs++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (ll l = 0; l < L; l++) s += B[l * n * n + pq] * B[l * n * n + rs];
             chem[pq * n * n + rs] = s;
         }
@@ -54,8 +71,8 @@ int orc_antisym_integrals(int o, int v, int L, const double *B, double *V)
         for (ll q = 0; q < n; q++)
             for (ll r = 0; r < n; r++)
                 for (ll s = 0; s < n; s++) {
-                    double prqs = chem[((p * n + r) * n + q) * n + s];
-                    double psqr = chem[((p * n + s) * n + q) * n + r];
+                    sc prqs = chem[((p * n + r) * n + q) * n + s];
+                    sc psqr = chem[((p * n + s) * n + q) * n + r];
                     V[((p * n + q) * n + r) * n + s] = prqs - psqr;
                 }
     free(chem);
@@ -71,22 +88,22 @@ int orc_antisym_integrals(int o, int v, int L, const double *B, double *V)
 
 /* Residual R = <Phi_l|Hbar|Phi_0> for l = singles, doubles.  eps[n] holds the
  * diagonal Fock matrix (occupied first).  Returns 0 on success. */
-int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
-                      const double *t1, const double *t2, double *r1, double *r2)
+int FN(ccsd_residual)(int o, int v, const double *eps, const sc *V,
+                      const sc *t1, const sc *t2, sc *r1, sc *r2)
 {
     const ll n = o + v;
     const ll ov2 = (ll)o * o * v * v;
-    double *tau = malloc(sizeof(double) * ov2);
-    double *taut = malloc(sizeof(double) * ov2);
-    double *Fae = malloc(sizeof(double) * v * v);
-    double *Fmi = malloc(sizeof(double) * o * o);
-    double *Fme = malloc(sizeof(double) * o * v);
-    double *Fbe2 = malloc(sizeof(double) * v * v);   /* F_be - 1/2 sum_m t_m^b F_me */
-    double *Fmj2 = malloc(sizeof(double) * o * o);   /* F_mj + 1/2 sum_e t_j^e F_me */
-    double *Wmnij = malloc(sizeof(double) * o * o * o * o);
-    double *Wabef = malloc(sizeof(double) * (ll)v * v * v * v);
-    double *Wmbej = malloc(sizeof(double) * (ll)o * v * v * o);
-    double *X = malloc(sizeof(double) * ov2);
+    sc *tau = malloc(sizeof(sc) * ov2);
+    sc *taut = malloc(sizeof(sc) * ov2);
+    sc *Fae = malloc(sizeof(sc) * v * v);
+    sc *Fmi = malloc(sizeof(sc) * o * o);
+    sc *Fme = malloc(sizeof(sc) * o * v);
+    sc *Fbe2 = malloc(sizeof(sc) * v * v);   /* F_be - 1/2 sum_m t_m^b F_me */
+    sc *Fmj2 = malloc(sizeof(sc) * o * o);   /* F_mj + 1/2 sum_e t_j^e F_me */
+    sc *Wmnij = malloc(sizeof(sc) * o * o * o * o);
+    sc *Wabef = malloc(sizeof(sc) * (ll)v * v * v * v);
+    sc *Wmbej = malloc(sizeof(sc) * (ll)o * v * v * o);
+    sc *X = malloc(sizeof(sc) * ov2);
     if (!tau || !taut || !Fae || !Fmi || !Fme || !Fbe2 || !Fmj2 || !Wmnij || !Wabef || !Wmbej || !X)
         return 1;
 
@@ -95,7 +112,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double p = T1(i, a) * T1(j, b) - T1(i, b) * T1(j, a);
+                    sc p = T1(i, a) * T1(j, b) - T1(i, b) * T1(j, a);
                     O4(tau, i, j, a, b) = T2(i, j, a, b) + p;
                     O4(taut, i, j, a, b) = T2(i, j, a, b) + 0.5 * p;
                 }
@@ -104,7 +121,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
 #pragma omp parallel for
     for (int a = 0; a < v; a++)
         for (int e = 0; e < v; e++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (int m = 0; m < o; m++)
                 for (int f = 0; f < v; f++) s += T1(m, f) * VV(m, o + a, o + f, o + e);
             for (int m = 0; m < o; m++)
@@ -115,7 +132,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
     /* F_mi = sum_en t_n^e <mn||ie> + 1/2 sum_nef tau~_in^ef <mn||ef> */
     for (int m = 0; m < o; m++)
         for (int i = 0; i < o; i++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (int e = 0; e < v; e++)
                 for (int nn = 0; nn < o; nn++) s += T1(nn, e) * VV(m, nn, i, o + e);
             for (int nn = 0; nn < o; nn++)
@@ -126,20 +143,20 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
     /* F_me = sum_nf t_n^f <mn||ef> */
     for (int m = 0; m < o; m++)
         for (int e = 0; e < v; e++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (int nn = 0; nn < o; nn++)
                 for (int f = 0; f < v; f++) s += T1(nn, f) * VV(m, nn, o + e, o + f);
             Fme[m * v + e] = s;
         }
     for (int b = 0; b < v; b++)
         for (int e = 0; e < v; e++) {
-            double s = Fae[b * v + e];
+            sc s = Fae[b * v + e];
             for (int m = 0; m < o; m++) s -= 0.5 * T1(m, b) * Fme[m * v + e];
             Fbe2[b * v + e] = s;
         }
     for (int m = 0; m < o; m++)
         for (int j = 0; j < o; j++) {
-            double s = Fmi[m * o + j];
+            sc s = Fmi[m * o + j];
             for (int e = 0; e < v; e++) s += 0.5 * T1(j, e) * Fme[m * v + e];
             Fmj2[m * o + j] = s;
         }
@@ -149,7 +166,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int nn = 0; nn < o; nn++)
             for (int i = 0; i < o; i++)
                 for (int j = 0; j < o; j++) {
-                    double s = VV(m, nn, i, j);
+                    sc s = VV(m, nn, i, j);
                     for (int e = 0; e < v; e++)
                         s += T1(j, e) * VV(m, nn, i, o + e) - T1(i, e) * VV(m, nn, j, o + e);
                     for (int e = 0; e < v; e++)
@@ -163,7 +180,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int b = 0; b < v; b++)
             for (int e = 0; e < v; e++)
                 for (int f = 0; f < v; f++) {
-                    double s = VV(o + a, o + b, o + e, o + f);
+                    sc s = VV(o + a, o + b, o + e, o + f);
                     for (int m = 0; m < o; m++)
                         s -= T1(m, b) * VV(o + a, m, o + e, o + f) - T1(m, a) * VV(o + b, m, o + e, o + f);
                     for (int m = 0; m < o; m++)
@@ -178,7 +195,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int b = 0; b < v; b++)
             for (int e = 0; e < v; e++)
                 for (int j = 0; j < o; j++) {
-                    double s = VV(m, o + b, o + e, j);
+                    sc s = VV(m, o + b, o + e, j);
                     for (int f = 0; f < v; f++) s += T1(j, f) * VV(m, o + b, o + e, o + f);
                     for (int nn = 0; nn < o; nn++) s -= T1(nn, b) * VV(m, nn, o + e, j);
                     for (int nn = 0; nn < o; nn++)
@@ -190,7 +207,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
     /* ---- T1 residual */
     for (int i = 0; i < o; i++)
         for (int a = 0; a < v; a++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (int e = 0; e < v; e++) s += T1(i, e) * Fae[a * v + e];
             for (int m = 0; m < o; m++) s -= T1(m, a) * Fmi[m * o + i];
             for (int m = 0; m < o; m++)
@@ -207,12 +224,14 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
             r1[(ll)i * v + a] = s;
         }
 
-    /* ---- T2 residual: start from <ij||ab> - D t2 */
+    /* ---- T2 residual: start from <ab||ij> - D t2 (the doubles projection of
+     * H|Phi_0> creates a, b and annihilates i, j; equal to <ij||ab> only for
+     * real orbitals) */
     for (int i = 0; i < o; i++)
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++)
-                    O4(r2, i, j, a, b) = VV(i, j, o + a, o + b)
+                    O4(r2, i, j, a, b) = VV(o + a, o + b, i, j)
                         - (eps[i] + eps[j] - eps[o + a] - eps[o + b]) * T2(i, j, a, b);
 
     /* + P(ab) sum_e t_ij^ae (F_be - 1/2 sum_m t_m^b F_me) */
@@ -220,7 +239,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double s = 0.0;
+                    sc s = 0.0;
                     for (int e = 0; e < v; e++) s += T2(i, j, a, e) * Fbe2[b * v + e];
                     O4(X, i, j, a, b) = s;
                 }
@@ -234,7 +253,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double s = 0.0;
+                    sc s = 0.0;
                     for (int m = 0; m < o; m++) s += T2(i, m, a, b) * Fmj2[m * o + j];
                     O4(X, i, j, a, b) = s;
                 }
@@ -249,7 +268,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double s = 0.0;
+                    sc s = 0.0;
                     for (int m = 0; m < o; m++)
                         for (int nn = 0; nn < o; nn++)
                             s += 0.5 * O4(tau, m, nn, a, b) * Wmnij[((m * o + nn) * o + i) * o + j];
@@ -265,7 +284,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double s = 0.0;
+                    sc s = 0.0;
                     for (int m = 0; m < o; m++)
                         for (int e = 0; e < v; e++)
                             s += T2(i, m, a, e) * Wmbej[(((ll)m * v + b) * v + e) * o + j]
@@ -284,7 +303,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double s = 0.0;
+                    sc s = 0.0;
                     for (int e = 0; e < v; e++) s += T1(i, e) * VV(o + a, o + b, o + e, j);
                     O4(X, i, j, a, b) = s;
                 }
@@ -298,7 +317,7 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double s = 0.0;
+                    sc s = 0.0;
                     for (int m = 0; m < o; m++) s += T1(m, a) * VV(m, o + b, i, j);
                     O4(X, i, j, a, b) = s;
                 }
@@ -313,10 +332,10 @@ int orc_ccsd_residual(int o, int v, const double *eps, const double *V,
 }
 
 /* E_CC - E_ref = sum f_ia t_i^a + 1/4 sum <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b  (f_ia = 0) */
-double orc_ccsd_energy(int o, int v, const double *V, const double *t1, const double *t2)
+sc FN(ccsd_energy)(int o, int v, const sc *V, const sc *t1, const sc *t2)
 {
     const ll n = o + v;
-    double e = 0.0;
+    sc e = 0.0;
     for (int i = 0; i < o; i++)
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
@@ -330,6 +349,7 @@ double orc_ccsd_energy(int o, int v, const double *V, const double *t1, const do
 /* Solve [B 1; 1^T 0][c; lambda] = [0; 1] (size m+1) by Gaussian elimination with
  * partial pivoting.  B is first scaled by 1/max(diag B).  Returns 0, or 1 if a
  * pivot falls below 1e-14 in magnitude (caller drops the oldest vector). */
+#ifndef CC_COMPLEX
 int orc_diis_coeffs(int m, const double *Bmat, double *c)
 {
     int N = m + 1;
@@ -366,6 +386,10 @@ int orc_diis_coeffs(int m, const double *Bmat, double *c)
     return 0;
 }
 
+#else
+int orc_diis_coeffs(int m, const double *Bmat, double *c);
+#endif
+
 /* Jacobi + DIIS on x = (t1, t2).  Iteration k: R_k = R(x_k), E_k = E(x_k),
  * |R_k| = Frobenius norm over the full t1 and t2 residual arrays.  Stop when
  * |R_k| < tol.  Otherwise x'_{k+1} = x_k + R_k/D, e_k = R_k/D; keep the last
@@ -374,15 +398,15 @@ int orc_diis_coeffs(int m, const double *Bmat, double *c)
  * x_{k+1} = x'_{k+1}.  t1/t2 hold the start on entry and the last x_k on exit.
  * energies/rnorms receive E_k and |R_k| (maxiter entries).  Returns 0 when
  * converged, 2 when maxiter is reached, 3 on a non-finite or exploding norm. */
-int orc_ccsd_solve(int o, int v, const double *eps, const double *V, double *t1, double *t2,
-                   double tol, int maxiter, int diis_max, double *energies, double *rnorms, int *iters)
+int FN(ccsd_solve)(int o, int v, const double *eps, const sc *V, sc *t1, sc *t2,
+                   double tol, int maxiter, int diis_max, sc *energies, double *rnorms, int *iters)
 {
     const ll n1 = (ll)o * v, n2 = (ll)o * o * v * v, nx = n1 + n2;
     if (diis_max > 16) diis_max = 16;
-    double *r1 = malloc(sizeof(double) * n1), *r2 = malloc(sizeof(double) * n2);
+    sc *r1 = malloc(sizeof(sc) * n1), *r2 = malloc(sizeof(sc) * n2);
     double *D = malloc(sizeof(double) * nx);
-    double *hx = malloc(sizeof(double) * nx * (diis_max > 0 ? diis_max : 1));
-    double *he = malloc(sizeof(double) * nx * (diis_max > 0 ? diis_max : 1));
+    sc *hx = malloc(sizeof(sc) * nx * (diis_max > 0 ? diis_max : 1));
+    sc *he = malloc(sizeof(sc) * nx * (diis_max > 0 ? diis_max : 1));
     if (!r1 || !r2 || !D || !hx || !he) return 1;
     for (int i = 0; i < o; i++)
         for (int a = 0; a < v; a++) D[(ll)i * v + a] = eps[i] - eps[o + a];
@@ -395,11 +419,11 @@ int orc_ccsd_solve(int o, int v, const double *eps, const double *V, double *t1,
     double best = INFINITY;
     int k;
     for (k = 0; k < maxiter; k++) {
-        orc_ccsd_residual(o, v, eps, V, t1, t2, r1, r2);
-        double e = orc_ccsd_energy(o, v, V, t1, t2);
+        FN(ccsd_residual)(o, v, eps, V, t1, t2, r1, r2);
+        sc e = FN(ccsd_energy)(o, v, V, t1, t2);
         double s = 0.0;
-        for (ll q = 0; q < n1; q++) s += r1[q] * r1[q];
-        for (ll q = 0; q < n2; q++) s += r2[q] * r2[q];
+        for (ll q = 0; q < n1; q++) s += ABS2(r1[q]);
+        for (ll q = 0; q < n2; q++) s += ABS2(r2[q]);
         double rn = sqrt(s);
         energies[k] = e;
         rnorms[k] = rn;
@@ -408,12 +432,12 @@ int orc_ccsd_solve(int o, int v, const double *eps, const double *V, double *t1,
         if (rn < tol) { status = 0; k++; break; }
         /* push (x', e) as the newest entry; drop the oldest when full */
         if (diis_max > 0 && nstored == diis_max) {
-            memmove(hx, hx + nx, sizeof(double) * nx * (diis_max - 1));
-            memmove(he, he + nx, sizeof(double) * nx * (diis_max - 1));
+            memmove(hx, hx + nx, sizeof(sc) * nx * (diis_max - 1));
+            memmove(he, he + nx, sizeof(sc) * nx * (diis_max - 1));
             nstored--;
         }
-        double *xn = hx + nx * (diis_max > 0 ? nstored : 0);
-        double *en = he + nx * (diis_max > 0 ? nstored : 0);
+        sc *xn = hx + nx * (diis_max > 0 ? nstored : 0);
+        sc *en = he + nx * (diis_max > 0 ? nstored : 0);
         for (ll q = 0; q < n1; q++) { en[q] = r1[q] / D[q]; xn[q] = t1[q] + en[q]; }
         for (ll q = 0; q < n2; q++) { en[n1 + q] = r2[q] / D[n1 + q]; xn[n1 + q] = t2[q] + en[n1 + q]; }
         if (diis_max > 0) nstored++;
@@ -425,29 +449,29 @@ int orc_ccsd_solve(int o, int v, const double *eps, const double *V, double *t1,
                 for (int a = 0; a < m; a++)
                     for (int b = 0; b < m; b++) {
                         double d = 0.0;
-                        for (ll q = 0; q < nx; q++) d += he[nx * a + q] * he[nx * b + q];
+                        for (ll q = 0; q < nx; q++) d += RDOT(he[nx * a + q], he[nx * b + q]);
                         Bm[a * m + b] = d;
                     }
                 ok = (orc_diis_coeffs(m, Bm, c) == 0);
                 if (ok || m <= 2) break;
-                memmove(hx, hx + nx, sizeof(double) * nx * (m - 1));
-                memmove(he, he + nx, sizeof(double) * nx * (m - 1));
+                memmove(hx, hx + nx, sizeof(sc) * nx * (m - 1));
+                memmove(he, he + nx, sizeof(sc) * nx * (m - 1));
                 nstored--;
             }
             if (ok) {
                 for (ll q = 0; q < nx; q++) {
-                    double s2 = 0.0;
+                    sc s2 = 0.0;
                     for (int a = 0; a < nstored; a++) s2 += c[a] * hx[nx * a + q];
                     if (q < n1) t1[q] = s2; else t2[q - n1] = s2;
                 }
             } else {
-                const double *xl = hx + nx * (nstored - 1);
-                memcpy(t1, xl, sizeof(double) * n1);
-                memcpy(t2, xl + n1, sizeof(double) * n2);
+                const sc *xl = hx + nx * (nstored - 1);
+                memcpy(t1, xl, sizeof(sc) * n1);
+                memcpy(t2, xl + n1, sizeof(sc) * n2);
             }
         } else {
-            memcpy(t1, xn, sizeof(double) * n1);
-            memcpy(t2, xn + n1, sizeof(double) * n2);
+            memcpy(t1, xn, sizeof(sc) * n1);
+            memcpy(t2, xn + n1, sizeof(sc) * n2);
         }
     }
     *iters = k;
@@ -455,6 +479,7 @@ int orc_ccsd_solve(int o, int v, const double *eps, const double *V, double *t1,
     return status;
 }
 
+#ifndef CC_COMPLEX
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
@@ -463,6 +488,7 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+#endif
 
 /* --------------------------------------------------------- sampled R2 elements
  *
@@ -475,15 +501,15 @@ int orc_num_threads(void)
  */
 typedef struct {
     int o, v, n, L;
-    const double *Bt;                 /* [p][r][L] */
-    double *oovv, *ooov, *ovvv;       /* <mn||ef>, <mn||ie>, <ma||ef> */
+    const sc *Bt;                     /* [p][r][L] */
+    sc *oovv, *ooov, *ovvv;           /* <mn||ef>, <mn||ie>, <ma||ef> */
 } vsrc;
 
-static double vint(const vsrc *S, int p, int q, int r, int s)
+static sc vint(const vsrc *S, int p, int q, int r, int s)
 {
-    const double *a = S->Bt + ((ll)p * S->n + r) * S->L, *b = S->Bt + ((ll)q * S->n + s) * S->L;
-    const double *c = S->Bt + ((ll)p * S->n + s) * S->L, *d = S->Bt + ((ll)q * S->n + r) * S->L;
-    double x = 0.0;
+    const sc *a = S->Bt + ((ll)p * S->n + r) * S->L, *b = S->Bt + ((ll)q * S->n + s) * S->L;
+    const sc *c = S->Bt + ((ll)p * S->n + s) * S->L, *d = S->Bt + ((ll)q * S->n + r) * S->L;
+    sc x = 0.0;
     for (int l = 0; l < S->L; l++) x += a[l] * b[l] - c[l] * d[l];
     return x;
 }
@@ -493,15 +519,15 @@ static double vint(const vsrc *S, int p, int q, int r, int s)
 #define OVVV(m, a, e, f) S.ovvv[(((ll)(m) * v + (a)) * v + (e)) * v + (f)]
 
 /* X_pqcd = sum_me ( t_pm^ce W_mdeq - t_p^e t_m^c <md||eq> ) for the ring term */
-static double ring_x(const vsrc *Sp, const double *t1, const double *t2, int p, int q, int c, int dd)
+static sc ring_x(const vsrc *Sp, const sc *t1, const sc *t2, int p, int q, int c, int dd)
 {
     const vsrc S = *Sp;
     const int o = S.o, v = S.v;
-    double x = 0.0;
+    sc x = 0.0;
     for (int m = 0; m < o; m++)
         for (int e = 0; e < v; e++) {
             /* W_mbej with b = dd, j = q */
-            double w = vint(&S, m, o + dd, o + e, q);
+            sc w = vint(&S, m, o + dd, o + e, q);
             for (int f = 0; f < v; f++) w += T1(q, f) * OVVV(m, dd, e, f);
             for (int nn = 0; nn < o; nn++) w += T1(nn, dd) * OOOV(m, nn, q, e);   /* -t_n^b <mn||ej> */
             for (int nn = 0; nn < o; nn++)
@@ -512,20 +538,20 @@ static double ring_x(const vsrc *Sp, const double *t1, const double *t2, int p, 
     return x;
 }
 
-int orc_ccsd_r2_sample(int o, int v, int L, const double *B, const double *eps, const double *t1,
-                       const double *t2, int ns, const int *idx, double *out)
+int FN(ccsd_r2_sample)(int o, int v, int L, const sc *B, const double *eps, const sc *t1,
+                       const sc *t2, int ns, const int *idx, sc *out)
 {
     const ll n = o + v;
     vsrc S;
     S.o = o; S.v = v; S.n = (int)n; S.L = L;
-    double *Bt = malloc(sizeof(double) * n * n * L);
-    S.oovv = malloc(sizeof(double) * (ll)o * o * v * v);
-    S.ooov = malloc(sizeof(double) * (ll)o * o * o * v);
-    S.ovvv = malloc(sizeof(double) * (ll)o * v * v * v);
-    double *tau = malloc(sizeof(double) * (ll)o * o * v * v), *taut = malloc(sizeof(double) * (ll)o * o * v * v);
-    double *Fae = malloc(sizeof(double) * v * v), *Fmi = malloc(sizeof(double) * o * o);
-    double *Fme = malloc(sizeof(double) * o * v), *Fbe2 = malloc(sizeof(double) * v * v);
-    double *Fmj2 = malloc(sizeof(double) * o * o);
+    sc *Bt = malloc(sizeof(sc) * n * n * L);
+    S.oovv = malloc(sizeof(sc) * (ll)o * o * v * v);
+    S.ooov = malloc(sizeof(sc) * (ll)o * o * o * v);
+    S.ovvv = malloc(sizeof(sc) * (ll)o * v * v * v);
+    sc *tau = malloc(sizeof(sc) * (ll)o * o * v * v), *taut = malloc(sizeof(sc) * (ll)o * o * v * v);
+    sc *Fae = malloc(sizeof(sc) * v * v), *Fmi = malloc(sizeof(sc) * o * o);
+    sc *Fme = malloc(sizeof(sc) * o * v), *Fbe2 = malloc(sizeof(sc) * v * v);
+    sc *Fmj2 = malloc(sizeof(sc) * o * o);
     if (!Bt || !S.oovv || !S.ooov || !S.ovvv || !tau || !taut || !Fae || !Fmi || !Fme || !Fbe2 || !Fmj2) return 1;
 #pragma omp parallel for
     for (ll pr = 0; pr < n * n; pr++)
@@ -548,14 +574,14 @@ int orc_ccsd_r2_sample(int o, int v, int L, const double *B, const double *eps, 
         for (int j = 0; j < o; j++)
             for (int a = 0; a < v; a++)
                 for (int b = 0; b < v; b++) {
-                    double p = T1(i, a) * T1(j, b) - T1(i, b) * T1(j, a);
+                    sc p = T1(i, a) * T1(j, b) - T1(i, b) * T1(j, a);
                     O4(tau, i, j, a, b) = T2(i, j, a, b) + p;
                     O4(taut, i, j, a, b) = T2(i, j, a, b) + 0.5 * p;
                 }
 #pragma omp parallel for
     for (int a = 0; a < v; a++)
         for (int e = 0; e < v; e++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (int m = 0; m < o; m++)
                 for (int f = 0; f < v; f++) s += T1(m, f) * OVVV(m, a, f, e);
             for (int m = 0; m < o; m++)
@@ -565,7 +591,7 @@ int orc_ccsd_r2_sample(int o, int v, int L, const double *B, const double *eps, 
         }
     for (int m = 0; m < o; m++)
         for (int i = 0; i < o; i++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (int e = 0; e < v; e++)
                 for (int nn = 0; nn < o; nn++) s += T1(nn, e) * OOOV(m, nn, i, e);
             for (int nn = 0; nn < o; nn++)
@@ -575,20 +601,20 @@ int orc_ccsd_r2_sample(int o, int v, int L, const double *B, const double *eps, 
         }
     for (int m = 0; m < o; m++)
         for (int e = 0; e < v; e++) {
-            double s = 0.0;
+            sc s = 0.0;
             for (int nn = 0; nn < o; nn++)
                 for (int f = 0; f < v; f++) s += T1(nn, f) * OOVV(m, nn, e, f);
             Fme[m * v + e] = s;
         }
     for (int b = 0; b < v; b++)
         for (int e = 0; e < v; e++) {
-            double s = Fae[b * v + e];
+            sc s = Fae[b * v + e];
             for (int m = 0; m < o; m++) s -= 0.5 * T1(m, b) * Fme[m * v + e];
             Fbe2[b * v + e] = s;
         }
     for (int m = 0; m < o; m++)
         for (int j = 0; j < o; j++) {
-            double s = Fmi[m * o + j];
+            sc s = Fmi[m * o + j];
             for (int e = 0; e < v; e++) s += 0.5 * T1(j, e) * Fme[m * v + e];
             Fmj2[m * o + j] = s;
         }
@@ -596,14 +622,14 @@ int orc_ccsd_r2_sample(int o, int v, int L, const double *B, const double *eps, 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < ns; k++) {
         const int i = idx[4 * k], j = idx[4 * k + 1], a = idx[4 * k + 2], b = idx[4 * k + 3];
-        double r = OOVV(i, j, a, b) - (eps[i] + eps[j] - eps[o + a] - eps[o + b]) * T2(i, j, a, b);
+        sc r = vint(&S, o + a, o + b, i, j) - (eps[i] + eps[j] - eps[o + a] - eps[o + b]) * T2(i, j, a, b);
         /* P(ab) sum_e t_ij^ae Fbe2_be  and  -P(ij) sum_m t_im^ab Fmj2_mj */
         for (int e = 0; e < v; e++) r += T2(i, j, a, e) * Fbe2[b * v + e] - T2(i, j, b, e) * Fbe2[a * v + e];
         for (int m = 0; m < o; m++) r -= T2(i, m, a, b) * Fmj2[m * o + j] - T2(j, m, a, b) * Fmj2[m * o + i];
         /* 1/2 sum_mn tau_mn^ab W_mnij */
         for (int m = 0; m < o; m++)
             for (int nn = 0; nn < o; nn++) {
-                double w = vint(&S, m, nn, i, j);
+                sc w = vint(&S, m, nn, i, j);
                 for (int e = 0; e < v; e++) w += T1(j, e) * OOOV(m, nn, i, e) - T1(i, e) * OOOV(m, nn, j, e);
                 for (int e = 0; e < v; e++)
                     for (int f = 0; f < v; f++) w += 0.25 * O4(tau, i, j, e, f) * OOVV(m, nn, e, f);
@@ -612,7 +638,7 @@ int orc_ccsd_r2_sample(int o, int v, int L, const double *B, const double *eps, 
         /* 1/2 sum_ef tau_ij^ef W_abef, <am||ef> = -<ma||ef> */
         for (int e = 0; e < v; e++)
             for (int f = 0; f < v; f++) {
-                double w = vint(&S, o + a, o + b, o + e, o + f);
+                sc w = vint(&S, o + a, o + b, o + e, o + f);
                 for (int m = 0; m < o; m++) w -= -T1(m, b) * OVVV(m, a, e, f) + T1(m, a) * OVVV(m, b, e, f);
                 for (int m = 0; m < o; m++)
                     for (int nn = 0; nn < o; nn++) w += 0.25 * O4(tau, m, nn, a, b) * OOVV(m, nn, e, f);

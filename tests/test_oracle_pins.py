@@ -122,3 +122,57 @@ def test_sampled_elements_match_brute_force_and_full_residual(o, v, seed):
     want = r2_b[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]
     assert np.abs(got - want).max() < 1e-12 * max(1.0, np.abs(r2_b).max())
     assert np.abs(got - r2[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]).max() < 1e-13
+
+
+# ----------------------------------------------------------------- complex128
+def _csystem(o, v, seed, scale=6.0):
+    s = ccinputs.make_system(o, v, L=6, seed=seed, complex_=True)
+    return s, s.B * scale
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 71), (3, 4, 72), (3, 5, 73)])
+def test_complex_residual_matches_determinant_brute_force(o, v, seed):
+    s, B = _csystem(o, v, seed)
+    V = oracle.antisym_integrals(o, v, B)
+    assert np.abs(V - detspace.antisym_from_B(B)).max() < 1e-14
+    # Hermitian antisymmetrised integrals
+    assert np.abs(V - V.transpose(2, 3, 0, 1).conj()).max() < 1e-14
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=seed, scale1=0.1, scale2=0.1, complex_=True)
+    e_b, r1_b, r2_b = detspace.brute_residual(o, v, s.eps, V, t1, t2)
+    r1, r2 = oracle.ccsd_residual(o, v, s.eps, V, t1, t2)
+    e = oracle.ccsd_energy(o, v, V, t1, t2)
+    scale = max(np.abs(r2_b).max(), np.abs(r1_b).max())
+    assert np.abs(r1 - r1_b).max() < 1e-12 * scale
+    assert np.abs(r2 - r2_b).max() < 1e-12 * scale
+    assert abs(e - e_b) < 1e-13
+
+
+def test_complex_ccsd_equals_fci_for_two_electrons():
+    o, v = 2, 5
+    s, B = _csystem(o, v, 74)
+    V = oracle.antisym_integrals(o, v, B)
+    res = oracle.ccsd_solve(o, v, s.eps, V, tol=1e-12, maxiter=200)
+    assert res["status"] == 0
+    assert abs(res["energy"] - detspace.fci_correlation(o, v, s.eps, V)) < 1e-12
+
+
+def test_complex_path_with_real_B_equals_real_path():
+    o, v = 3, 4
+    s, B = _system(o, v, 75)
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=75, scale1=0.1, scale2=0.1)
+    Vr = oracle.antisym_integrals(o, v, B)
+    Vc = oracle.antisym_integrals(o, v, B.astype(np.complex128))
+    r1, r2 = oracle.ccsd_residual(o, v, s.eps, Vr, t1, t2)
+    z1, z2 = oracle.ccsd_residual(o, v, s.eps, Vc, t1.astype(complex), t2.astype(complex))
+    assert np.abs(z2.imag).max() == 0.0 and np.abs(z2.real - r2).max() < 1e-15
+    assert np.abs(z1.real - r1).max() < 1e-15
+
+
+def test_complex_sampled_elements_match_full_residual():
+    o, v = 3, 5
+    s, B = _csystem(o, v, 76)
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=76, scale1=0.1, scale2=0.1, complex_=True)
+    idx = np.array([[0, 1, 0, 1], [2, 0, 4, 3], [1, 2, 3, 0]])
+    got = oracle.ccsd_r2_sample(o, v, B, s.eps, t1, t2, idx)
+    _, r2 = oracle.ccsd_residual(o, v, s.eps, oracle.antisym_integrals(o, v, B), t1, t2)
+    assert np.abs(got - r2[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]).max() < 1e-13
