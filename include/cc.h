@@ -26,8 +26,11 @@
  *   * Errors: every call returns a cc_status and never aborts.  On error the
  *     outputs are unspecified, the inputs are untouched, and cc_last_error()
  *     returns a message (thread-local, valid until the next call).
- *   * dtype CC_F64: double.  CC_C128: interleaved complex double (re, im);
- *     orbital energies stay real.  This build implements CC_F64.
+ *   * dtype CC_F64: double.  CC_C128: interleaved complex double (re, im)
+ *     for every tensor (integral blocks, amplitudes, residuals); orbital
+ *     energies stay real.  Complex integrals are Hermitian,
+ *     <pq||rs> = conj(<rs||pq>); a list names each integral in the
+ *     orientation the projection fixes (the doubles driver is <ab||ij>).
  */
 #ifndef CCB300_CC_H
 #define CCB300_CC_H
@@ -167,8 +170,8 @@ CC_API cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_am
                              void *ws, size_t ws_bytes, void *stream);
 
 /* cc_energy -- E_CC - E_ref = 1/4 sum <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b
- * (f_ia = 0).  e_dev: device double[2] receiving (Re E, Im E).  Uses the first
- * 8 KiB of ws as scratch. */
+ * (f_ia = 0).  e_dev: device double[2] receiving (Re E, Im E) (Im E = 0 for
+ * CC_F64).  Uses the first 10 KiB of ws as scratch. */
 CC_API cc_status cc_energy(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, double *e_dev,
                            void *ws, size_t ws_bytes, void *stream);
 
@@ -187,10 +190,12 @@ typedef struct {
     int iterations;           /* iterations done by this call */
     int converged;            /* 1 when |R| < tol */
     int switched_at;          /* iteration index of the switch to refine_plan, -1 if none */
-    double energy;            /* E(x_k) of the last evaluated iterate */
+    double energy;            /* Re E(x_k) of the last evaluated iterate */
     double rnorm;             /* |R(x_k)|_2 of the last evaluated iterate */
     double *energies;         /* optional host array [max_iter] (NULL = skip) */
     double *rnorms;           /* optional host array [max_iter] (NULL = skip) */
+    double energy_im;         /* Im E(x_k) (0 for CC_F64) */
+    double *energies_im;      /* optional host array [max_iter] of Im E (NULL = skip) */
 } cc_solve_report;
 
 /* Workspace of cc_solve: cc_plan_workspace_bytes plus the DIIS history and
@@ -202,8 +207,9 @@ CC_API cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opt
  * residual arrays) and stops when |R_k| < tol; otherwise x'_{k+1} = x_k + R_k/D,
  * e_k = R_k/D, the last diis_max pairs (x', e) are kept and, once two are
  * stored, x_{k+1} = sum_l c_l x'_l with [B 1; 1^T 0][c; lambda] = [0; 1],
- * B_kl = <e_k|e_l>, solved in FP64 on the device (B scaled by 1/max diag,
- * partial pivoting, the oldest vector dropped while a pivot is below 1e-14).
+ * B_kl = Re<e_k|e_l> (complex vectors as real ones of twice the length),
+ * solved in FP64 on the device (B scaled by 1/max diag, partial pivoting, the
+ * oldest vector dropped while a pivot is below 1e-14).
  *   amps: in = start (zeros give MP2 at k = 1); out = the converged x_k, or,
  *   when max_iter ends the call, the next iterate x_{k+1} (resume = 1 continues
  *   from it with the DIIS history kept in ws).
@@ -221,7 +227,9 @@ CC_API cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps,
 
 /* Integral construction (setup step):  (pq|rs) = sum_L B[L][p][q] B[L][r][s]
  * and <pq||rs> = (pr|qs) - (ps|qr) for the six canonical blocks (Eq. ham2q).
- *   B: device [L][n][n] (n = o + v, occupied first), double.
+ *   B: device [L][n][n] (n = o + v, occupied first), double or complex
+ *   double (dtype); complex B gives <pq||rs> = sum_L B_pr B_qs - B_ps B_qr
+ *   with no conjugation (B[L][q][p] = conj(B[L][p][q]) makes them Hermitian).
  *   blocks: device outputs (NULL skips a block), sizes from
  *   cc_integral_block_elems (elements).
  *   ws: device workspace of cc_build_integrals_workspace_bytes. */

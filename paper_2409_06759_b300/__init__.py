@@ -67,7 +67,8 @@ class cc_solve_opts(ctypes.Structure):
 
 class cc_solve_report(ctypes.Structure):
     _fields_ = [("iterations", c_int), ("converged", c_int), ("switched_at", c_int), ("energy", c_double),
-                ("rnorm", c_double), ("energies", ctypes.POINTER(c_double)), ("rnorms", ctypes.POINTER(c_double))]
+                ("rnorm", c_double), ("energies", ctypes.POINTER(c_double)), ("rnorms", ctypes.POINTER(c_double)),
+                ("energy_im", c_double), ("energies_im", ctypes.POINTER(c_double))]
 
 
 _P = ctypes.POINTER
@@ -147,8 +148,9 @@ def cc_last_error() -> str:
 class Plan:
     """Owns a cc_plan handle (a host object)."""
 
-    def __init__(self, handle: int, o: int, v: int, precision: int, text: str):
+    def __init__(self, handle: int, o: int, v: int, precision: int, text: str, dtype: int = 0):
         self.handle, self.o, self.v, self.precision, self.text = handle, o, v, precision, text
+        self.dtype = dtype
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -183,7 +185,7 @@ def cc_plan_create(text: str, o: int, v: int, dtype: int = CC_F64, precision=CC_
     opts = cc_plan_opts(ctypes.sizeof(cc_plan_opts), verbose, 0)
     _check(_lib.cc_plan_create(text.encode(), o, v, dtype, prec, ctypes.byref(opts), ctypes.byref(h)),
            "cc_plan_create")
-    return Plan(h.value, o, v, precision, text)
+    return Plan(h.value, o, v, precision, text, dtype)
 
 
 def cc_plan_workspace_bytes(plan: Plan) -> int:
@@ -261,7 +263,7 @@ class SolveResult:
     iterations: int
     converged: bool
     switched_at: int
-    energy: float
+    energy: float             # complex for CC_C128 plans
     rnorm: float
     energies: list
     rnorms: list
@@ -286,12 +288,17 @@ def cc_solve(plan: Plan, ints: dict, t1, t2, ws, max_iter: int = 100, tol: float
     A = cc_amps(_ptr(t1), _ptr(t2), _ptr(t3))
     o = _solve_opts(max_iter, tol, diis_max, int(resume), refine_plan, switch_tol, verbose)
     en = (c_double * max(max_iter, 1))()
+    ei = (c_double * max(max_iter, 1))()
     rn = (c_double * max(max_iter, 1))()
-    rep = cc_solve_report(0, 0, -1, 0.0, 0.0, ctypes.cast(en, _P(c_double)), ctypes.cast(rn, _P(c_double)))
+    rep = cc_solve_report(0, 0, -1, 0.0, 0.0, ctypes.cast(en, _P(c_double)), ctypes.cast(rn, _P(c_double)), 0.0,
+                          ctypes.cast(ei, _P(c_double)))
     st = _lib.cc_solve(plan.handle, ctypes.byref(I), ctypes.byref(A), ctypes.byref(o), ctypes.byref(rep), _ptr(ws),
                        _nbytes(ws), _stream(stream))
     _check(st, "cc_solve", ok=(0, 7))
     k = rep.iterations
+    if plan.dtype == CC_C128:
+        return SolveResult(st, k, bool(rep.converged), rep.switched_at, complex(rep.energy, rep.energy_im), rep.rnorm,
+                           [complex(a, b) for a, b in zip(en[:k], ei[:k])], list(rn[:k]))
     return SolveResult(st, k, bool(rep.converged), rep.switched_at, rep.energy, rep.rnorm, list(en[:k]),
                        list(rn[:k]))
 

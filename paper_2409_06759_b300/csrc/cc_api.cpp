@@ -195,7 +195,7 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
         const double *t = (const double *)(l == 1 ? A->t1 : l == 2 ? A->t2 : A->t3);
         double *r = (double *)(l == 1 ? R->r1 : l == 2 ? R->r2 : R->r3);
         if (t) {
-            CC_CUDA(launch_denom_sub(l, P.o, P.v, I->f_occ, I->f_vir, t, r, s));
+            CC_CUDA(launch_denom_sub(l, P.o, P.v, I->f_occ, I->f_vir, t, r, P.dtype == CC_C128, s));
             pl->launches++;
         }
     }
@@ -211,9 +211,10 @@ int64_t amp_count(int rank, int o, int v) {
 constexpr int64_t kAlign = 256;
 int64_t al(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// solver region layout (bytes, relative to its start)
+// solver region layout (bytes, relative to its start).  Counts are in
+// doubles: a complex amplitude is two, and the DIIS overlaps are Re<x|y>.
 struct SolverLayout {
-    int64_t n[4] = {0, 0, 0, 0};    // elements per rank (1..3)
+    int64_t n[4] = {0, 0, 0, 0};    // doubles per rank (1..3)
     int64_t nx = 0;                 // elements of x = concatenation of the ranks in use
     int64_t r_off[4] = {0, 0, 0, 0};
     int64_t hist_x = 0, hist_e = 0; // diis_max vectors of nx each
@@ -227,7 +228,7 @@ SolverLayout solver_layout(const Plan &P, int diis_max) {
     int64_t off = 0;
     for (int l = 1; l <= 3; l++) {
         if (!P.res_used[l]) continue;
-        L.n[l] = amp_count(l, P.o, P.v);
+        L.n[l] = amp_count(l, P.o, P.v) * (P.dtype == CC_C128 ? 2 : 1);
         L.nx += L.n[l];
         L.r_off[l] = off;
         off += al(L.n[l] * 8);
@@ -248,12 +249,14 @@ SolverLayout solver_layout(const Plan &P, int diis_max) {
     return L;
 }
 
-// scal[0] = E, scal[1..] = |R_l|^2 for the residual ranks in use
+// scal[0] = Re E, scal[1] = Im E, scal[2..] = |R_l|^2 for the residual ranks in use
 cc_status reduce_energy_norm(const Plan &P, const cc_integrals *I, const cc_amps *A, double *const r[4],
                              const int64_t n[4], double *partials, double *scal, cudaStream_t s) {
+    const int cplx = P.dtype == CC_C128;
     CC_CUDA(launch_energy_partials(P.o, P.v, (const double *)I->oovv, (const double *)A->t1, (const double *)A->t2,
-                                   partials, s));
-    int cnt = 1;
+                                   partials, cplx, s));
+    if (!cplx) CC_CUDA(cudaMemsetAsync(partials + kRedBlocks, 0, kRedBlocks * sizeof(double), s));
+    int cnt = 2;
     for (int l = 1; l <= 3; l++) {
         if (!r[l]) continue;
         CC_CUDA(launch_dot_partials(r[l], r[l], n[l], partials + (int64_t)cnt * kRedBlocks, s));
@@ -291,7 +294,7 @@ cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_prec
                          const cc_plan_opts *opts, cc_plan *out) {
     if (!text || !out) return fail(CC_ERR_INVALID_ARG, "NULL text or output handle");
     if (o < 1 || v < 1) return fail(CC_ERR_INVALID_ARG, "o and v must be >= 1");
-    if (dtype != CC_F64) return fail(CC_ERR_UNSUPPORTED, "only CC_F64 is implemented in this build");
+    if (dtype != CC_F64 && dtype != CC_C128) return fail(CC_ERR_INVALID_ARG, "unknown dtype");
     const int prec = (int)precision;
     const int base = prec >= 100 ? prec - 100 : prec;
     if (base != CC_PREC_FP64 && base != CC_PREC_BF16X3 && base != CC_PREC_BF16X6)
@@ -396,14 +399,15 @@ cc_status cc_energy(cc_plan plan, const cc_integrals *ints, const cc_amps *amps,
                     size_t ws_bytes, void *stream) {
     if (!plan || !ints || !amps || !e_dev) return fail(CC_ERR_INVALID_ARG, "NULL argument");
     if (!ints->oovv || !amps->t2) return fail(CC_ERR_INVALID_ARG, "energy needs the oovv block and t2");
-    if (!ws || ws_bytes < (size_t)kRedBlocks * 8 || !aligned256(ws))
-        return fail(CC_ERR_WORKSPACE, "energy needs 8 KiB of 256-byte aligned workspace");
+    if (!ws || ws_bytes < (size_t)2 * kRedBlocks * 8 || !aligned256(ws))
+        return fail(CC_ERR_WORKSPACE, "energy needs 10 KiB of 256-byte aligned workspace");
     cudaStream_t s = (cudaStream_t)stream;
     double *partials = (double *)ws;
+    const int cplx = plan->plan.dtype == CC_C128;
     CC_CUDA(launch_energy_partials(plan->plan.o, plan->plan.v, (const double *)ints->oovv, (const double *)amps->t1,
-                                   (const double *)amps->t2, partials, s));
-    CC_CUDA(launch_reduce_partials(partials, 1, e_dev, s));
-    CC_CUDA(cudaMemsetAsync(e_dev + 1, 0, sizeof(double), s));
+                                   (const double *)amps->t2, partials, cplx, s));
+    CC_CUDA(launch_reduce_partials(partials, cplx ? 2 : 1, e_dev, s));
+    if (!cplx) CC_CUDA(cudaMemsetAsync(e_dev + 1, 0, sizeof(double), s));
     return CC_OK;
 }
 
@@ -430,8 +434,9 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     if (opts) o = *opts;
     if (o.max_iter < 0 || o.diis_max < 0 || o.diis_max > 16) return fail(CC_ERR_INVALID_ARG, "bad solve options");
     cc_plan refine = o.refine_plan;
-    if (refine && (refine->plan.o != plan->plan.o || refine->plan.v != plan->plan.v))
-        return fail(CC_ERR_INVALID_ARG, "refine plan has different o/v");
+    if (refine && (refine->plan.o != plan->plan.o || refine->plan.v != plan->plan.v ||
+                   refine->plan.dtype != plan->plan.dtype))
+        return fail(CC_ERR_INVALID_ARG, "refine plan has different o/v or dtype");
     const Plan &P = plan->plan;
     if (!P.res_used[2]) return fail(CC_ERR_INVALID_ARG, "cc_solve needs a list that writes R2");
     if (refine) {
@@ -471,13 +476,14 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     }
     // pinned host staging for the per-iteration scalars (one per thread)
     static thread_local double *h_scal = nullptr;
-    if (!h_scal) CC_CUDA(cudaMallocHost(&h_scal, 64));
+    if (!h_scal) CC_CUDA(cudaMallocHost(&h_scal, 128));
     if (report) { report->iterations = 0; report->converged = 0; report->switched_at = -1; }
+    const int cplx = P.dtype == CC_C128;
     plan->cache_filled = false;
     if (refine) refine->cache_filled = false;
     g_err.clear();
     cc_status result = CC_ERR_NOT_CONVERGED;
-    double last_e = NAN, last_rn = NAN;
+    double last_e = NAN, last_ei = NAN, last_rn = NAN;
     int k = 0;
     double *dl = (double *)(sreg + L.delta);
     double *dlr[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -509,15 +515,15 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         st = reduce_energy_norm(P, ints, amps, r, L.n, partials, scal, s);
         if (st != CC_OK) return st;
         plan->launches += 2 + (r[1] != nullptr) + (r[2] != nullptr) + (r[3] != nullptr);
-        CC_CUDA(cudaMemcpyAsync(h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CC_CUDA(cudaMemcpyAsync(h_scal + 4, used_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CC_CUDA(cudaMemcpyAsync(h_scal + 5, pws + plan->plan.flags_off, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(h_scal, scal, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(h_scal + 6, used_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(h_scal + 7, pws + plan->plan.flags_off, sizeof(int), cudaMemcpyDeviceToHost, s));
         CC_CUDA(cudaStreamSynchronize(s));
-        if (plan->plan.flops_mixed > 0 && *(int *)(h_scal + 5) != 0)
+        if (plan->plan.flops_mixed > 0 && *(int *)(h_scal + 7) != 0)
             return fail(CC_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
         // history bookkeeping of the previous device DIIS solve: drop what it dropped
         if (S.pending_m >= 2) {
-            int used = *(int *)(h_scal + 4);
+            int used = *(int *)(h_scal + 6);
             int keep = used == 0 ? 2 : used;
             while (S.nstored > keep) {
                 for (int q = 0; q + 1 < S.nstored; q++) S.order[q] = S.order[q + 1];
@@ -526,12 +532,14 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
             S.pending_m = 0;
         }
         double rr = 0.0;
-        for (int l = 1, c = 1; l <= 3; l++)
+        for (int l = 1, c = 2; l <= 3; l++)
             if (r[l]) rr += h_scal[c++];
         const double e = h_scal[0], rn = std::sqrt(rr);
         last_e = e;
+        last_ei = h_scal[1];
         last_rn = rn;
         if (report && report->energies) report->energies[k] = e;
+        if (report && report->energies_im) report->energies_im[k] = h_scal[1];
         if (report && report->rnorms) report->rnorms[k] = rn;
         if (o.verbose)
             std::fprintf(stderr, "cc_solve iter %d phase %d%s E %.14f |R| %.3e\n", S.iter, S.phase,
@@ -581,7 +589,7 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         int64_t off = 0;
         for (int l = 1; l <= 3; l++) {
             if (!r[l]) continue;
-            CC_CUDA(launch_jacobi(l, o_, v_, ints->f_occ, ints->f_vir, t[l], r[l], xs + off, es + off, s));
+            CC_CUDA(launch_jacobi(l, o_, v_, ints->f_occ, ints->f_vir, t[l], r[l], xs + off, es + off, cplx, s));
             plan->launches++;
             off += L.n[l];
         }
@@ -623,6 +631,7 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         report->iterations = k;
         report->converged = result == CC_OK;
         report->energy = last_e;
+        report->energy_im = last_ei;
         report->rnorm = last_rn;
     }
     if (result != CC_OK && g_err.empty()) g_err = "maximum iterations reached";
@@ -641,15 +650,14 @@ cc_status cc_integral_block_elems(int o, int v, size_t elems[6]) {
 
 cc_status cc_build_integrals_workspace_bytes(int o, int v, int L, cc_dtype dtype, size_t *bytes) {
     if (o < 1 || v < 1 || L < 1 || !bytes) return fail(CC_ERR_INVALID_ARG, "bad arguments");
-    if (dtype != CC_F64) return fail(CC_ERR_UNSUPPORTED, "only CC_F64 is implemented in this build");
-    const int64_t n = o + v;
-    *bytes = (size_t)(al((int64_t)L * n * n * 8) + 4 * kAlign);
+    if (dtype != CC_F64 && dtype != CC_C128) return fail(CC_ERR_INVALID_ARG, "unknown dtype");
+    const int64_t n = o + v, esz = dtype == CC_C128 ? 16 : 8;
+    *bytes = (size_t)(al((int64_t)L * n * n * esz) + 4 * kAlign);
     return CC_OK;
 }
 
 cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B, void *oooo, void *ooov, void *oovv,
                              void *ovov, void *ovvv, void *vvvv, void *ws, size_t ws_bytes, void *stream) {
-    if (dtype != CC_F64) return fail(CC_ERR_UNSUPPORTED, "only CC_F64 is implemented in this build");
     size_t need = 0;
     cc_status st = cc_build_integrals_workspace_bytes(o, v, L, dtype, &need);
     if (st != CC_OK) return st;
@@ -658,13 +666,15 @@ cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B,
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = o + v;
     const int64_t ext[2] = {o, v}, base[2] = {0, o};
+    const int cplx = dtype == CC_C128;
+    const int64_t esz = cplx ? 16 : 8, ew = cplx ? 2 : 1;   // bytes and doubles per element
     // sub-blocks Bsub[x][y] = B[L][x-range][y-range], contiguous [L][X][Y]
     double *sub[2][2];
     int64_t off = 0;
     for (int x = 0; x < 2; x++)
         for (int y = 0; y < 2; y++) {
             sub[x][y] = (double *)((char *)ws + off);
-            off += (int64_t)L * ext[x] * ext[y] * 8;
+            off += (int64_t)L * ext[x] * ext[y] * esz;
             AccumDesc d{};
             d.nd = 3;
             d.nperm = 1;
@@ -675,7 +685,8 @@ cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B,
             d.sign[0] = 1.0;
             d.alpha = 1.0;
             d.beta = 0.0;
-            CC_CUDA(launch_accum(d, (const double *)B + base[x] * n + base[y], sub[x][y], s));
+            d.cplx = cplx;
+            CC_CUDA(launch_accum(d, (const double *)B + (base[x] * n + base[y]) * ew, sub[x][y], s));
         }
     static const char *nm[6] = {"oooo", "ooov", "oovv", "ovov", "ovvv", "vvvv"};
     for (int b = 0; b < 6; b++) {
@@ -701,6 +712,7 @@ cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B,
             g.alpha = term == 0 ? 1.0 : -1.0;
             g.beta = term == 0 ? 0.0 : 1.0;
             g.splitk = 1;
+            g.cplx = cplx;
             CC_CUDA(launch_gemm_f64(g, sub[sp[0]][sp[ri]], sub[sp[1]][sp[si]], (double *)blocks[b], nullptr, s));
         }
     }

@@ -9,14 +9,46 @@
 
 namespace ccb {
 
+// ------------------------------------------------------------------ scalars
+// The kernels below are written once over the element type T: double, or
+// double2 holding an interleaved complex double (re, im).
+__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ double cj(double x, int) { return x; }
+__device__ __forceinline__ double2 cj(double2 x, int c) { return c ? make_double2(x.x, -x.y) : x; }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 mul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + s * x, s real
+__device__ __forceinline__ double axpy(double s, double x, double acc) { return fma(s, x, acc); }
+__device__ __forceinline__ double2 axpy(double s, double2 x, double2 acc) {
+    return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
+}
+__device__ __forceinline__ double scal(double s, double x) { return s * x; }
+__device__ __forceinline__ double2 scal(double s, double2 x) { return make_double2(s * x.x, s * x.y); }
+template <typename T> __device__ __forceinline__ T zero();
+template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ double2 zero<double2>() { return make_double2(0.0, 0.0); }
+// acc + a * b over complex (or real) numbers
+__device__ __forceinline__ double cfma(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+
 // ------------------------------------------------------------------ accum
 // Each warp owns a contiguous run of 32*kAccChunk output elements; lane l
 // visits run_start + l + 32*j, so stores to a contiguous output coalesce.
 // The multi-index is decomposed once per run and advanced as an odometer.
 constexpr int kAccChunk = 8;
 
-__global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const double *__restrict__ src,
-                                                    double *__restrict__ out, const double *__restrict__ src2) {
+template <typename T>
+__global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *__restrict__ src,
+                                                    T *__restrict__ out, const T *__restrict__ src2) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -35,20 +67,20 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const dou
         for (int j = 0; j < kAccChunk && e < d.total; j++) {
             int64_t oo = 0;
             for (int k = 0; k < d.nd; k++) oo += dig[k] * d.ostr[k];
-            double acc = 0.0;
+            T acc = zero<T>();
             for (int p = 0; p < d.nperm; p++) {
                 int64_t so = 0;
                 for (int k = 0; k < d.nd; k++) so += dig[k] * d.sstr[p][k];
-                double x = __ldg(src + so);
+                T x = cj(ld(src + so), d.conj_a);
                 if (d.two_src) {
                     int64_t so2 = 0;
                     for (int k = 0; k < d.nd; k++) so2 += dig[k] * d.sstr2[p][k];
-                    x *= __ldg(src2 + so2);
+                    x = mul(x, cj(ld(src2 + so2), d.conj_b));
                 }
-                acc += d.sign[p] * x;
+                acc = axpy(d.sign[p], x, acc);
             }
-            double val = d.alpha * acc;
-            if (d.beta != 0.0) val += d.beta * out[oo];
+            T val = scal(d.alpha, acc);
+            if (d.beta != 0.0) val = axpy(d.beta, out[oo], val);
             out[oo] = val;
             // advance by 32 elements (compare-and-subtract carries)
             e += 32;
@@ -69,10 +101,11 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const dou
 // dim is a batch index of the block.  Each term reads its source tile either
 // directly (lanes along d0) or through shared memory (lanes along d1, then
 // transposed), so reads and writes stay coalesced for the P(..) gathers.
-__global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, const double *__restrict__ src,
-                                                          double *__restrict__ out, int d0, int d1, unsigned tmask,
+template <typename T>
+__global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, const T *__restrict__ src,
+                                                          T *__restrict__ out, int d0, int d1, unsigned tmask,
                                                           int64_t tiles0, int64_t tiles1) {
-    __shared__ double sm[32][33];
+    __shared__ T sm[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
     int64_t bid = blockIdx.x;
     const int64_t t0 = bid % tiles0; bid /= tiles0;
@@ -89,7 +122,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
     }
     const int64_t i0b = t0 * 32, i1b = t1 * 32;
     const int64_t E0 = d.ext[d0], E1 = d.ext[d1];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T acc[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
     for (int p = 0; p < d.nperm; p++) {
         const int64_t s0 = d.sstr[p][d0], s1 = d.sstr[p][d1];
         const int64_t base = sbase[p] + i0b * s0 + i1b * s1;
@@ -97,38 +130,39 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
 #pragma unroll
             for (int r = 0; r < 4; r++) {
                 const int64_t i1 = ty + 8 * r;
-                if (i0b + tx < E0 && i1b + i1 < E1) acc[r] += d.sign[p] * __ldg(src + base + tx * s0 + i1 * s1);
+                if (i0b + tx < E0 && i1b + i1 < E1)
+                    acc[r] = axpy(d.sign[p], cj(ld(src + base + tx * s0 + i1 * s1), d.conj_a), acc[r]);
             }
         } else {
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < 4; r++) {
                 const int64_t i0 = ty + 8 * r;
-                sm[tx][i0] = (i1b + tx < E1 && i0b + i0 < E0) ? __ldg(src + base + tx * s1 + i0 * s0) : 0.0;
+                sm[tx][i0] = (i1b + tx < E1 && i0b + i0 < E0) ? ld(src + base + tx * s1 + i0 * s0) : zero<T>();
             }
             __syncthreads();
 #pragma unroll
-            for (int r = 0; r < 4; r++) acc[r] += d.sign[p] * sm[ty + 8 * r][tx];
+            for (int r = 0; r < 4; r++) acc[r] = axpy(d.sign[p], cj(sm[ty + 8 * r][tx], d.conj_a), acc[r]);
         }
     }
     const int64_t os0 = d.ostr[d0], os1 = d.ostr[d1];
-    double old[4];
+    T old[4];
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         const int64_t i1 = ty + 8 * r;
         const bool ok = i0b + tx < E0 && i1b + i1 < E1;
-        old[r] = (d.beta != 0.0 && ok) ? out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] : 0.0;
+        old[r] = (d.beta != 0.0 && ok) ? out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] : zero<T>();
     }
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         const int64_t i1 = ty + 8 * r;
         if (i0b + tx < E0 && i1b + i1 < E1)
-            out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = d.alpha * acc[r] + d.beta * old[r];
+            out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = axpy(d.beta, old[r], scal(d.alpha, acc[r]));
     }
 }
 
-cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s, const double *src2) {
-    if (d.total <= 0) return cudaSuccess;
+template <typename T>
+static cudaError_t accum_t(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
     // tiled path: the output's innermost dim and a partner dim both of extent >= 16
     if (!d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 16) {
         const int d0 = d.nd - 1;
@@ -153,7 +187,7 @@ cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cud
             const int64_t tiles0 = (d.ext[d0] + 31) / 32, tiles1 = (d.ext[d1] + 31) / 32;
             const int64_t blocks = tiles0 * tiles1 * (d.total / (d.ext[d0] * d.ext[d1]));
             if (blocks <= 0x7fffffffLL) {
-                accum_tiled_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, src, out, d0, d1, tmask, tiles0, tiles1);
+                accum_tiled_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, src, out, d0, d1, tmask, tiles0, tiles1);
                 return cudaGetLastError();
             }
         }
@@ -161,8 +195,16 @@ cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cud
     int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
     int64_t blocks = (runs + 7) / 8;
     if (blocks > 148 * 16) blocks = 148 * 16;
-    accum_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, src, out, src2);
+    accum_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, src, out, src2);
     return cudaGetLastError();
+}
+
+cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s, const double *src2) {
+    if (d.total <= 0) return cudaSuccess;
+    if (d.cplx)
+        return accum_t<double2>(d, reinterpret_cast<const double2 *>(src), reinterpret_cast<double2 *>(out), s,
+                                reinterpret_cast<const double2 *>(src2));
+    return accum_t<double>(d, src, out, s, src2);
 }
 
 __global__ void zero_kernel(double *p, int64_t n) {
@@ -197,19 +239,19 @@ __device__ __forceinline__ int64_t grp_offset(const Grp &g, int64_t x) {
     return off;
 }
 
-template <bool A_KCONTIG, bool B_KCONTIG>
-__global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, const double *__restrict__ A,
-                                                       const double *__restrict__ B, double *__restrict__ C,
-                                                       double *__restrict__ partials, int thread_m_fast, int64_t kchunk) {
-    __shared__ double As[GBK][GBM + GPAD];
-    __shared__ double Bs[GBK][GBN + GPAD];
+template <typename T, bool A_KCONTIG, bool B_KCONTIG>
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, const T *__restrict__ A,
+                                                       const T *__restrict__ B, T *__restrict__ C,
+                                                       T *__restrict__ partials, int thread_m_fast, int64_t kchunk) {
+    __shared__ T As[GBK][GBM + GPAD];
+    __shared__ T Bs[GBK][GBN + GPAD];
     const int tid = threadIdx.x;
     const int64_t m0 = (int64_t)blockIdx.x * GBM;
     const int64_t n0 = (int64_t)blockIdx.y * GBN;
     const int tm = thread_m_fast ? (tid & 15) : (tid >> 4);
     const int tn = thread_m_fast ? (tid >> 4) : (tid & 15);
 
-    double ra[4], rb[4];
+    T ra[4], rb[4];
     auto load_tiles = [&](int64_t k0, int64_t klim) {
 #pragma unroll
         for (int r = 0; r < 4; r++) {
@@ -217,12 +259,12 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
             int mm, kk;
             if (A_KCONTIG) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
             int64_t gm = m0 + mm, gk = k0 + kk;
-            ra[r] = (gm < d.M && gk < klim) ? __ldg(A + gm * d.sAm + gk * d.sAk) : 0.0;
+            ra[r] = (gm < d.M && gk < klim) ? cj(ld(A + gm * d.sAm + gk * d.sAk), d.conj_a) : zero<T>();
             int nn;
             if (B_KCONTIG) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
             int64_t gn = n0 + nn;
             gk = k0 + kk;
-            rb[r] = (gn < d.N && gk < klim) ? __ldg(B + gk * d.sBk + gn * d.sBn) : 0.0;
+            rb[r] = (gn < d.N && gk < klim) ? cj(ld(B + gk * d.sBk + gn * d.sBn), d.conj_b) : zero<T>();
         }
     };
     auto store_tiles = [&]() {
@@ -234,11 +276,11 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         }
     };
 
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; j++) acc[i][j] = zero<T>();
 
     // K slice of this CTA (the whole K unless split)
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
@@ -251,7 +293,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         if (k0 + GBK < kend) load_tiles(k0 + GBK, kend);
 #pragma unroll
         for (int k = 0; k < GBK; k++) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; i++) a[i] = As[k][tm + 16 * i];
 #pragma unroll
@@ -259,12 +301,12 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; j++) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
         }
     }
     if (gridDim.z > 1) {
         // split K: raw partial sums, [z][n][m]
-        double *P = partials + (int64_t)blockIdx.z * d.M * d.N;
+        T *P = partials + (int64_t)blockIdx.z * d.M * d.N;
 #pragma unroll
         for (int i = 0; i < 4; i++)
 #pragma unroll
@@ -285,118 +327,159 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         cv[i] = n < d.N;
         co[i] = cv[i] ? grp_offset(d.cn, n) : 0;
     }
-    double old[4][4];
+    T old[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) old[i][j] = (d.beta != 0.0 && rv[i] && cv[j]) ? C[ro[i] + co[j]] : 0.0;
+        for (int j = 0; j < 4; j++) old[i][j] = (d.beta != 0.0 && rv[i] && cv[j]) ? C[ro[i] + co[j]] : zero<T>();
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            if (rv[i] && cv[j]) C[ro[i] + co[j]] = d.alpha * acc[i][j] + d.beta * old[i][j];
+            if (rv[i] && cv[j]) C[ro[i] + co[j]] = axpy(d.beta, old[i][j], scal(d.alpha, acc[i][j]));
 }
 
 // ------------------------------------------------------------------ gemv
 // y(r) = alpha * sum_k X(r,k) x(k) + beta * y(r): the GEMM shapes with one
 // output dimension of extent 1 are memory-bound matrix-vector products.
-// X(r,k) = X[r*sr + k*sk]; x(k) = x[k*incx]; y addressed through a group.
-// K-contiguous X (sk == 1): one warp per row; otherwise one thread per row.
-__global__ void __launch_bounds__(256) gemv_rowwarp_kernel(int64_t R, int64_t K, const double *__restrict__ X,
-                                                           int64_t sr, const double *__restrict__ x, int64_t incx,
-                                                           const Grp gy, double alpha, double beta,
-                                                           double *__restrict__ y) {
+// X(r,k) = X[r*sr + k*sk]; x(k) = x[k*incx]; y addressed through a group;
+// cX / cx conjugate X / x.  K-contiguous X (sk == 1): one warp per row;
+// otherwise one thread per row.
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double2 shfl_xor(double2 v, int o) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_rowwarp_kernel(int64_t R, int64_t K, const T *__restrict__ X, int64_t sr,
+                                                           const T *__restrict__ x, int64_t incx, const Grp gy,
+                                                           double alpha, double beta, T *__restrict__ y, int cX,
+                                                           int cx) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     for (int64_t r = w0; r < R; r += (int64_t)gridDim.x * 8) {
-        const double *row = X + r * sr;
-        double s0 = 0.0, s1 = 0.0;
+        const T *row = X + r * sr;
+        T s0 = zero<T>(), s1 = zero<T>();
         int64_t k = lane;
         for (; k + 32 < K; k += 64) {
-            s0 = fma(__ldg(row + k), __ldg(x + k * incx), s0);
-            s1 = fma(__ldg(row + k + 32), __ldg(x + (k + 32) * incx), s1);
+            s0 = cfma(cj(ld(row + k), cX), cj(ld(x + k * incx), cx), s0);
+            s1 = cfma(cj(ld(row + k + 32), cX), cj(ld(x + (k + 32) * incx), cx), s1);
         }
-        if (k < K) s0 = fma(__ldg(row + k), __ldg(x + k * incx), s0);
-        double s = s0 + s1;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (k < K) s0 = cfma(cj(ld(row + k), cX), cj(ld(x + k * incx), cx), s0);
+        T s = add(s0, s1);
+        for (int o = 16; o > 0; o >>= 1) s = add(s, shfl_xor(s, o));
         if (lane == 0) {
-            double *p = y + grp_offset(gy, r);
-            double val = alpha * s;
-            if (beta != 0.0) val += beta * *p;
+            T *p = y + grp_offset(gy, r);
+            T val = scal(alpha, s);
+            if (beta != 0.0) val = axpy(beta, *p, val);
             *p = val;
         }
     }
 }
 
-__global__ void __launch_bounds__(256) gemv_rowthread_kernel(int64_t R, int64_t K, const double *__restrict__ X,
-                                                             int64_t sk, const double *__restrict__ x, int64_t incx,
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_rowthread_kernel(int64_t R, int64_t K, const T *__restrict__ X,
+                                                             int64_t sk, const T *__restrict__ x, int64_t incx,
                                                              const Grp gy, double alpha, double beta,
-                                                             double *__restrict__ y) {
+                                                             T *__restrict__ y, int cX, int cx) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        T s0 = zero<T>(), s1 = zero<T>(), s2 = zero<T>(), s3 = zero<T>();
         int64_t k = 0;
         for (; k + 3 < K; k += 4) {
-            s0 = fma(__ldg(X + r + k * sk), __ldg(x + k * incx), s0);
-            s1 = fma(__ldg(X + r + (k + 1) * sk), __ldg(x + (k + 1) * incx), s1);
-            s2 = fma(__ldg(X + r + (k + 2) * sk), __ldg(x + (k + 2) * incx), s2);
-            s3 = fma(__ldg(X + r + (k + 3) * sk), __ldg(x + (k + 3) * incx), s3);
+            s0 = cfma(cj(ld(X + r + k * sk), cX), cj(ld(x + k * incx), cx), s0);
+            s1 = cfma(cj(ld(X + r + (k + 1) * sk), cX), cj(ld(x + (k + 1) * incx), cx), s1);
+            s2 = cfma(cj(ld(X + r + (k + 2) * sk), cX), cj(ld(x + (k + 2) * incx), cx), s2);
+            s3 = cfma(cj(ld(X + r + (k + 3) * sk), cX), cj(ld(x + (k + 3) * incx), cx), s3);
         }
-        for (; k < K; k++) s0 = fma(__ldg(X + r + k * sk), __ldg(x + k * incx), s0);
-        double *p = y + grp_offset(gy, r);
-        double val = alpha * ((s0 + s1) + (s2 + s3));
-        if (beta != 0.0) val += beta * *p;
+        for (; k < K; k++) s0 = cfma(cj(ld(X + r + k * sk), cX), cj(ld(x + k * incx), cx), s0);
+        T *p = y + grp_offset(gy, r);
+        T val = scal(alpha, add(add(s0, s1), add(s2, s3)));
+        if (beta != 0.0) val = axpy(beta, *p, val);
         *p = val;
     }
 }
 
-static cudaError_t launch_gemv(int64_t R, int64_t K, const double *X, int64_t sr, int64_t sk, const double *x,
-                               int64_t incx, const Grp &gy, double alpha, double beta, double *y, cudaStream_t s) {
+template <typename T>
+static cudaError_t launch_gemv(int64_t R, int64_t K, const T *X, int64_t sr, int64_t sk, const T *x, int64_t incx,
+                               const Grp &gy, double alpha, double beta, T *y, int cX, int cx, cudaStream_t s) {
     if (sk == 1 || K == 1) {
         int64_t blocks = (R + 7) / 8;
         if (blocks > 148 * 16) blocks = 148 * 16;
-        gemv_rowwarp_kernel<<<(unsigned)blocks, 256, 0, s>>>(R, K, X, K == 1 ? sr : sr, x, incx, gy, alpha, beta, y);
+        gemv_rowwarp_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(R, K, X, sr, x, incx, gy, alpha, beta, y, cX, cx);
     } else {
         int64_t blocks = (R + 255) / 256;
         if (blocks > 148 * 16) blocks = 148 * 16;
-        gemv_rowthread_kernel<<<(unsigned)blocks, 256, 0, s>>>(R, K, X, sk, x, incx, gy, alpha, beta, y);
+        gemv_rowthread_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(R, K, X, sk, x, incx, gy, alpha, beta, y, cX, cx);
     }
     return cudaGetLastError();
 }
 
 // C(m,n) = alpha * a(m) b(n) + beta * C(m,n): the K = 1 (outer product) shape,
 // memory-bound; threads run along the output direction with the smaller stride.
-__global__ void __launch_bounds__(256) outer_kernel(int64_t M, int64_t N, const double *__restrict__ a, int64_t sa,
-                                                    const double *__restrict__ b, int64_t sb, const Grp cm,
-                                                    const Grp cn, double alpha, double beta, double *__restrict__ C,
-                                                    int m_fast) {
+template <typename T>
+__global__ void __launch_bounds__(256) outer_kernel(int64_t M, int64_t N, const T *__restrict__ a, int64_t sa,
+                                                    const T *__restrict__ b, int64_t sb, const Grp cm, const Grp cn,
+                                                    double alpha, double beta, T *__restrict__ C, int m_fast, int ca,
+                                                    int cb) {
     const int64_t MN = M * N;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t m, n;
         if (m_fast) { n = e / M; m = e - n * M; } else { m = e / N; n = e - m * N; }
-        double *p = C + grp_offset(cm, m) + grp_offset(cn, n);
-        double val = alpha * __ldg(a + m * sa) * __ldg(b + n * sb);
-        if (beta != 0.0) val += beta * *p;
+        T *p = C + grp_offset(cm, m) + grp_offset(cn, n);
+        T val = scal(alpha, mul(cj(ld(a + m * sa), ca), cj(ld(b + n * sb), cb)));
+        if (beta != 0.0) val = axpy(beta, *p, val);
         *p = val;
     }
 }
 
-cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, double *partials,
-                            cudaStream_t s) {
-    if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+template <typename T>
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t M, int64_t N, int nz, const T *__restrict__ P,
+                                                            const Grp cm, const Grp cn, double alpha, double beta,
+                                                            T *__restrict__ C) {
+    const int64_t MN = M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+        T acc = zero<T>();
+        for (int z = 0; z < nz; z++) acc = add(acc, P[z * MN + e]);
+        const int64_t n = e / M, m = e - n * M;
+        T *p = C + grp_offset(cm, m) + grp_offset(cn, n);
+        T val = scal(alpha, acc);
+        if (beta != 0.0) val = axpy(beta, *p, val);
+        *p = val;
+    }
+}
+
+template <typename T>
+static cudaError_t splitk_reduce_t(int64_t M, int64_t N, int splitk, const T *partials, const Grp &cm, const Grp &cn,
+                                   double alpha, double beta, T *C, cudaStream_t s) {
+    int64_t blocks = (M * N + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    splitk_reduce_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(M, N, splitk, partials, cm, cn, alpha, beta, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
+                                 double alpha, double beta, double *C, cudaStream_t s) {
+    return splitk_reduce_t<double>(M, N, splitk, partials, cm, cn, alpha, beta, C, s);
+}
+
+template <typename T>
+static cudaError_t gemm_t(const GemmF64Desc &d, const T *A, const T *B, T *C, T *partials, cudaStream_t s) {
     if (d.K == 1 && d.M > 1 && d.N > 1) {
         int64_t sm = d.cm.nd ? d.cm.str[d.cm.nd - 1] : 0, sn = d.cn.nd ? d.cn.str[d.cn.nd - 1] : 0;
         int64_t blocks = (d.M * d.N + 255) / 256;
         if (blocks > 148 * 16) blocks = 148 * 16;
-        outer_kernel<<<(unsigned)blocks, 256, 0, s>>>(d.M, d.N, A, d.sAm, B, d.sBn, d.cm, d.cn, d.alpha, d.beta, C,
-                                                      sm <= sn ? 1 : 0);
+        outer_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d.M, d.N, A, d.sAm, B, d.sBn, d.cm, d.cn, d.alpha, d.beta, C,
+                                                         sm <= sn ? 1 : 0, d.conj_a, d.conj_b);
         return cudaGetLastError();
     }
     // matrix-vector shapes: rows m of A against the single column of B, or
     // rows n of B^T against the single row of A
     if (d.N == 1 && d.M > 1 && (d.sAk == 1 || d.sAm == 1))
-        return launch_gemv(d.M, d.K, A, d.sAm, d.sAk, B, d.sBk, d.cm, d.alpha, d.beta, C, s);
+        return launch_gemv<T>(d.M, d.K, A, d.sAm, d.sAk, B, d.sBk, d.cm, d.alpha, d.beta, C, d.conj_a, d.conj_b, s);
     if (d.M == 1 && d.N > 1 && (d.sBk == 1 || d.sBn == 1))
-        return launch_gemv(d.N, d.K, B, d.sBn, d.sBk, A, d.sAk, d.cn, d.alpha, d.beta, C, s);
+        return launch_gemv<T>(d.N, d.K, B, d.sBn, d.sBk, A, d.sAk, d.cn, d.alpha, d.beta, C, d.conj_b, d.conj_a, s);
     const int sk = d.splitk > 1 ? d.splitk : 1;
     const int64_t kchunk = sk > 1 ? ((d.K + sk - 1) / sk + GBK - 1) / GBK * GBK : (d.K > 0 ? d.K : 1);
     const int zs = (int)((d.K + kchunk - 1) / kchunk);
@@ -409,36 +492,22 @@ cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double 
     const bool ak = d.sAk == 1 && !(d.sAm == 1 && d.K == 1);
     const bool bk = d.sBk == 1 && !(d.sBn == 1 && d.K == 1);
     if (zs > 1) m_fast = 1;
-    if (ak && bk) gemm_f64_kernel<true, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
-    else if (ak) gemm_f64_kernel<true, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
-    else if (bk) gemm_f64_kernel<false, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
-    else gemm_f64_kernel<false, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    if (ak && bk) gemm_f64_kernel<T, true, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else if (ak) gemm_f64_kernel<T, true, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else if (bk) gemm_f64_kernel<T, false, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else gemm_f64_kernel<T, false, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || zs == 1) return e;
-    return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
+    return splitk_reduce_t<T>(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
-__global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t M, int64_t N, int nz, const double *__restrict__ P,
-                                                            const Grp cm, const Grp cn, double alpha, double beta,
-                                                            double *__restrict__ C) {
-    const int64_t MN = M * N;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int z = 0; z < nz; z++) acc += P[z * MN + e];
-        const int64_t n = e / M, m = e - n * M;
-        double *p = C + grp_offset(cm, m) + grp_offset(cn, n);
-        double val = alpha * acc;
-        if (beta != 0.0) val += beta * *p;
-        *p = val;
-    }
-}
-
-cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
-                                 double alpha, double beta, double *C, cudaStream_t s) {
-    int64_t blocks = (M * N + 255) / 256;
-    if (blocks > 148 * 8) blocks = 148 * 8;
-    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(M, N, splitk, partials, cm, cn, alpha, beta, C);
-    return cudaGetLastError();
+cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, double *partials,
+                            cudaStream_t s) {
+    if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+    if (d.cplx)
+        return gemm_t<double2>(d, reinterpret_cast<const double2 *>(A), reinterpret_cast<const double2 *>(B),
+                               reinterpret_cast<double2 *>(C), reinterpret_cast<double2 *>(partials), s);
+    return gemm_t<double>(d, A, B, C, partials, s);
 }
 
 // ------------------------------------------------------- iteration kernels
@@ -457,13 +526,17 @@ __device__ __forceinline__ double vir_sum(int rank, int v, const double *fv, uin
     return s;
 }
 
+// cplx: the arrays are interleaved complex; column c of a row is component
+// c & 1 of virtual tuple c >> 1 (D is real).
 __global__ void __launch_bounds__(256) denom_sub_kernel(int rank, int o, int v, const double *fo, const double *fv,
-                                                        const double *t, double *r, int64_t rows, uint32_t nvt) {
+                                                        const double *t, double *r, int64_t rows, uint32_t nvt,
+                                                        int cplx) {
+    const uint32_t ncol = nvt << cplx;
     for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
         const double so = occ_sum(rank, o, fo, row);
-        const int64_t base = row * nvt;
-        for (uint32_t c = threadIdx.x; c < nvt; c += blockDim.x)
-            r[base + c] -= (so - vir_sum(rank, v, fv, c)) * t[base + c];
+        const int64_t base = row * ncol;
+        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x)
+            r[base + c] -= (so - vir_sum(rank, v, fv, c >> cplx)) * t[base + c];
     }
 }
 
@@ -475,23 +548,24 @@ static void rows_cols(int rank, int o, int v, int64_t &rows, uint32_t &nvt) {
 }
 
 cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv, const double *t, double *r,
-                             cudaStream_t s) {
+                             int cplx, cudaStream_t s) {
     int64_t rows;
     uint32_t nvt;
     rows_cols(rank, o, v, rows, nvt);
     int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
-    denom_sub_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, rows, nvt);
+    denom_sub_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, rows, nvt, cplx ? 1 : 0);
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) jacobi_kernel(int rank, int o, int v, const double *fo, const double *fv,
                                                      const double *t, const double *r, double *xo, double *eo,
-                                                     int64_t rows, uint32_t nvt) {
+                                                     int64_t rows, uint32_t nvt, int cplx) {
+    const uint32_t ncol = nvt << cplx;
     for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
         const double so = occ_sum(rank, o, fo, row);
-        const int64_t base = row * nvt;
-        for (uint32_t c = threadIdx.x; c < nvt; c += blockDim.x) {
-            const double q = r[base + c] / (so - vir_sum(rank, v, fv, c));
+        const int64_t base = row * ncol;
+        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+            const double q = r[base + c] / (so - vir_sum(rank, v, fv, c >> cplx));
             eo[base + c] = q;
             xo[base + c] = t[base + c] + q;
         }
@@ -499,12 +573,12 @@ __global__ void __launch_bounds__(256) jacobi_kernel(int rank, int o, int v, con
 }
 
 cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
-                          const double *r, double *xo, double *eo, cudaStream_t s) {
+                          const double *r, double *xo, double *eo, int cplx, cudaStream_t s) {
     int64_t rows;
     uint32_t nvt;
     rows_cols(rank, o, v, rows, nvt);
     int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
-    jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, rows, nvt);
+    jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, rows, nvt, cplx ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -549,29 +623,43 @@ cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, dou
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) energy_partials_kernel(int o, int v, const double *V, const double *t1,
-                                                              const double *t2, double *partials) {
+template <typename T>
+__global__ void __launch_bounds__(256) energy_partials_kernel(int o, int v, const T *V, const T *t1, const T *t2,
+                                                              double *partials) {
     const int64_t n = (int64_t)o * o * v * v;
-    double s = 0.0;
+    T s = zero<T>();
     for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)kRedBlocks * 256) {
-        double w = 0.25 * t2[e];
+        T w = scal(0.25, t2[e]);
         if (t1) {
             int64_t x = e;
             int b = (int)(x % v); x /= v;
             int a = (int)(x % v); x /= v;
             int j = (int)(x % o); x /= o;
             int i = (int)x;
-            w += 0.5 * t1[(int64_t)i * v + a] * t1[(int64_t)j * v + b];
+            w = axpy(0.5, mul(t1[(int64_t)i * v + a], t1[(int64_t)j * v + b]), w);
         }
-        s = fma(V[e], w, s);
+        s = cfma(V[e], w, s);
     }
-    s = block_sum(s);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        const double r = block_sum(s);
+        if (threadIdx.x == 0) partials[blockIdx.x] = r;
+    } else {
+        const double re = block_sum(s.x), im = block_sum(s.y);
+        if (threadIdx.x == 0) {
+            partials[blockIdx.x] = re;
+            partials[kRedBlocks + blockIdx.x] = im;
+        }
+    }
 }
 
 cudaError_t launch_energy_partials(int o, int v, const double *Voovv, const double *t1, const double *t2,
-                                   double *partials, cudaStream_t s) {
-    energy_partials_kernel<<<kRedBlocks, 256, 0, s>>>(o, v, Voovv, t1, t2, partials);
+                                   double *partials, int cplx, cudaStream_t s) {
+    if (cplx)
+        energy_partials_kernel<double2><<<kRedBlocks, 256, 0, s>>>(
+            o, v, reinterpret_cast<const double2 *>(Voovv), reinterpret_cast<const double2 *>(t1),
+            reinterpret_cast<const double2 *>(t2), partials);
+    else
+        energy_partials_kernel<double><<<kRedBlocks, 256, 0, s>>>(o, v, Voovv, t1, t2, partials);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,8 @@ struct Grp {
 // transposes), copies, and the antisymmetrising epilogues P(..).
 // two_src: each term is the product src[sstr . idx] * src2[sstr2 . idx] (an
 // outer product with permutation operators, formed directly in the output).
+// cplx: elements are interleaved complex doubles (strides count complex
+// elements); conj_a / conj_b conjugate src / src2 as they are read.
 struct AccumDesc {
     int nd;
     int nperm;
@@ -35,6 +37,7 @@ struct AccumDesc {
     double alpha, beta;
     int two_src;
     int64_t sstr2[kMaxPerms][kMaxDims];
+    int cplx, conj_a, conj_b;
 };
 
 // C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), FP64.
@@ -42,22 +45,34 @@ struct AccumDesc {
 // likewise; C addressed through two mixed-radix groups.
 // splitk > 1: grid z = splitk slices of K; each writes its raw partial sum to
 // partials[z][n][m] (m fastest) and launch_splitk_reduce applies alpha/beta.
+// cplx: complex double operands and output (strides in complex elements, four
+// real FMAs per complex product); conj_a / conj_b conjugate A / B.
 struct GemmF64Desc {
     int64_t M, N, K;
     int64_t sAm, sAk, sBk, sBn;
     Grp cm, cn;
     double alpha, beta;
     int splitk;
+    int cplx, conj_a, conj_b;
 };
 
 // Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes
 // bf16 planes P_p[r][k] of a padded K-major matrix [Rp][Kp]:
 //   hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); rows >= R and
 //   columns >= K are written as zeros.
+// Complex sources (gr, gk give complex-element offsets in doubles) enter the
+// real GEMM that carries a complex product C = A B (4M, one GEMM):
+//   cplx 1, stacked:  X(r, 2k + c) = component c of X(r, k)
+//                     (conj: the c = 1 column negated)
+//   cplx 2, embedded: X(2r + cr, 2k + ck) = s * component (cr ^ ck) of X(r, k),
+//                     s = -1 for (cr, ck) = (0, 1) (conj: also for cr ^ ck = 1)
+// so that [C_re; C_im] = embedded(A) stacked(B) and likewise with the roles of
+// the operands swapped.  R and K count the real rows and columns.
 struct SplitDesc {
     int64_t R, K, Rp, Kp;
     Grp gr, gk;
     int nplanes;
+    int cplx, conj;
 };
 
 // Split-bf16 GEMM on tcgen05: D[m][n] = sum_{(p,q) in products} A_p[m][:] . B_q[n][:]
@@ -87,21 +102,23 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C,
                            double *partials, int *err_flag, cudaStream_t s);
 
-// R -= D * T for rank 1..3 residuals: D from the orbital energies.
+// R -= D * T for rank 1..3 residuals: D from the orbital energies (real);
+// cplx: t and r are interleaved complex.
 cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv,
-                             const double *t, double *r, cudaStream_t s);
+                             const double *t, double *r, int cplx, cudaStream_t s);
 // Jacobi step: e = r / D, x' = t + e (written to xo, eo).
 cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
-                          const double *r, double *xo, double *eo, cudaStream_t s);
+                          const double *r, double *xo, double *eo, int cplx, cudaStream_t s);
 // y = a*x + b*y over n elements
 cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s);
 // partial sums for dot products: partials[b] = sum over block b of x*y (fixed grid)
 constexpr int kRedBlocks = 592;
 cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *partials,
                                 cudaStream_t s);
-// energy partials: sum_ijab V[ijab] (1/4 t2[ijab] + 1/2 t1[ia] t1[jb]); t1 may be NULL
+// energy partials: sum_ijab V[ijab] (1/4 t2[ijab] + 1/2 t1[ia] t1[jb]); t1 may be NULL.
+// cplx: complex inputs; two partial rows (real part, then imaginary part).
 cudaError_t launch_energy_partials(int o, int v, const double *Voovv, const double *t1,
-                                   const double *t2, double *partials, cudaStream_t s);
+                                   const double *t2, double *partials, int cplx, cudaStream_t s);
 // out[k] = sum of partials[k][0..kRedBlocks) for k < count (fixed order)
 cudaError_t launch_reduce_partials(const double *partials, int count, double *out, cudaStream_t s);
 // DIIS on device.  gram16[16*16] holds <e_a|e_b> by history slot; order_host

@@ -262,6 +262,7 @@ struct Planner {
         const int ver = version[tensor];
         for (auto &r : splits)
             if (r.tensor == tensor && r.version == ver && r.np == d.nplanes && r.d.R == d.R && r.d.K == d.K &&
+                r.d.cplx == d.cplx && r.d.conj == d.conj &&
                 r.d.Rp == d.Rp && r.d.Kp == d.Kp && same_grp(r.d.gr, d.gr) && same_grp(r.d.gk, d.gk)) {
                 exists = true;
                 return r.off;
@@ -273,7 +274,23 @@ struct Planner {
         return r.off;
     }
 
-    explicit Planner(Plan &pl) : plan(pl), o(pl.o), v(pl.v) {}
+    explicit Planner(Plan &pl) : plan(pl), o(pl.o), v(pl.v), cplx(pl.dtype == 1), esz(pl.dtype == 1 ? 16 : 8) {}
+    const bool cplx;            // complex double elements (interleaved re, im)
+    const int64_t esz;          // bytes per element
+
+    // complex-element strides -> double strides
+    static Grp dbl(Grp g) {
+        for (int k = 0; k < g.nd; k++) g.str[k] *= 2;
+        return g;
+    }
+    // appends the re/im component as the fastest digit of a double-addressed group
+    bool add_component(Grp &g) {
+        if (g.nd >= 6) { err = "more than five indices in one matrix dimension of a complex contraction"; return false; }
+        g.ext[g.nd] = 2;
+        g.str[g.nd] = 1;
+        g.nd++;
+        return true;
+    }
 
     int add_tensor(const std::string &name, TKind k, const std::vector<char> &sp, int slot) {
         Tensor t;
@@ -287,7 +304,7 @@ struct Planner {
         for (size_t d = 0; d < sp.size(); d++) t.ext[d] = sp[d] == 'o' ? o : v;
         for (int d = (int)sp.size() - 1; d >= 0; d--) { t.str[d] = e; e *= t.ext[d]; }
         t.elems = e;
-        if (k == TKind::INTERM) { t.ws_off = interm_need; interm_need += align_up(e * 8); }
+        if (k == TKind::INTERM) { t.ws_off = interm_need; interm_need += align_up(e * esz); }
         plan.tensors.push_back(t);
         version.push_back(0);
         initialized.push_back(k != TKind::RES && k != TKind::INTERM);
@@ -495,6 +512,8 @@ struct Planner {
         }
         d.alpha = alpha;
         d.beta = beta;
+        d.cplx = cplx ? 1 : 0;
+        d.conj_a = cplx && src.conj ? 1 : 0;
         st.note = "accum";
         return st;
     }
@@ -557,7 +576,7 @@ struct Planner {
             z.kind = StepKind::ZERO;
             z.stmt = si;
             z.out = outref;
-            z.zero_elems = T.elems;
+            z.zero_elems = T.elems * (cplx ? 2 : 1);   // doubles
             z.note = "zero " + T.name;
             plan.steps.push_back(z);
         }
@@ -601,6 +620,7 @@ struct Planner {
                     st.acc.sstr2[p][k] = str_of(in[1], pre);
                 }
             st.b = tensor_ref(in[1].tensor);
+            st.acc.conj_b = cplx && in[1].conj ? 1 : 0;
             st.stmt = si;
             st.note = "outer " + plan.tensors[in[0].tensor].name + "*" + plan.tensors[in[1].tensor].name + " -> " + T.name;
             plan.steps.push_back(st);
@@ -620,7 +640,8 @@ struct Planner {
         for (int l : FA) Mx *= ext_of(A, l);
         for (int l : FB) Nx *= ext_of(B, l);
         for (int l : K) Kx *= ext_of(A, l);
-        const double flops = 2.0 * (double)Mx * (double)Nx * (double)Kx;
+        // real flops: a complex multiply-add is four real ones
+        const double flops = (cplx ? 8.0 : 2.0) * (double)Mx * (double)Nx * (double)Kx;
         scratch_need = 0;
         // split-bf16 route: contractions of >= 2e8 flops that are real GEMMs
         // (matrix-vector shapes stay on the memory-bound FP64 kernels)
@@ -672,9 +693,9 @@ struct Planner {
                     r.where = BufRef::WS;
                     r.slot = 2;                 // cache-relative, rebased after planning
                     r.off = cache_need;
-                    cache_need += align_up(view_elems(w) * 8);
+                    cache_need += align_up(view_elems(w) * esz);
                 } else {
-                    r = scratch(view_elems(w) * 8);
+                    r = scratch(view_elems(w) * esz);
                 }
                 Step p = accum_step(w, r, X, xref, std::vector<Perm>(1, Perm{1.0, {}}), 1.0, 0.0);
                 p.static_src = stat;
@@ -683,6 +704,7 @@ struct Planner {
                 plan.steps.push_back(p);
                 w.tensor = X.tensor;
                 w.sign = X.sign;
+                w.conj = false;             // applied by the permute
                 X = w;
                 xref = r;
             };
@@ -716,7 +738,7 @@ struct Planner {
                 sk = std::min<int64_t>(sk, 256);
                 if (sk > 1) {
                     g.gemm.splitk = (int)sk;
-                    g.partials = scratch(sk * g.gemm.M * g.gemm.N * 8);
+                    g.partials = scratch(sk * g.gemm.M * g.gemm.N * esz);
                 }
             }
         }
@@ -734,7 +756,7 @@ struct Planner {
             std::vector<int> ord = fb_order;
             ord.insert(ord.end(), fa_order.begin(), fa_order.end());
             Cv = contiguous_view(ord, A, &B);
-            cref = scratch(view_elems(Cv) * 8);
+            cref = scratch(view_elems(Cv) * esz);
             gbeta = 0.0;
         }
         Grp cm = make_grp(fa_order, A, Cv), cn = make_grp(fb_order, B, Cv);
@@ -747,15 +769,30 @@ struct Planner {
             g.gemm.cn = cn;
             g.gemm.alpha = galpha;
             g.gemm.beta = gbeta;
+            g.gemm.cplx = cplx ? 1 : 0;
+            g.gemm.conj_a = cplx && A.conj ? 1 : 0;
+            g.gemm.conj_b = cplx && B.conj ? 1 : 0;
         } else {
             const int np = plan.precision == 3 ? 3 : 2;
+            // complex: one real GEMM of doubled K carries C = A B (4M); the
+            // smaller operand is embedded (rows and K doubled), the other
+            // stacked (K doubled), and the output gains a re/im digit on the
+            // embedded side
+            const bool emb_a = cplx && view_elems(A) <= view_elems(B);
+            const int64_t Mr = cplx && emb_a ? 2 * Mx : Mx, Nr = cplx && !emb_a ? 2 * Nx : Nx;
+            const int64_t Kr = cplx ? 2 * Kx : Kx;
+            if (cplx) {
+                cm = dbl(cm);
+                cn = dbl(cn);
+                if (!add_component(emb_a ? cm : cn)) return false;
+            }
             TcGemmDesc &t = g.tc;
-            t.M = Mx;
-            t.N = Nx;
-            t.bn = Nx <= 64 ? 64 : (Nx <= 128 || np == 3) ? 128 : 256;
-            t.Mp = align_up(Mx, 128);
-            t.Np = align_up(Nx, t.bn);
-            t.Kp = align_up(Kx, 64);
+            t.M = Mr;
+            t.N = Nr;
+            t.bn = Nr <= 64 ? 64 : (Nr <= 128 || np == 3) ? 128 : 256;
+            t.Mp = align_up(Mr, 128);
+            t.Np = align_up(Nr, t.bn);
+            t.Kp = align_up(Kr, 64);
             // split K when the output tiles cannot fill the 148 SMs
             const int64_t tiles = (t.Mp / 128) * (t.Np / t.bn), kblocks = t.Kp / 64;
             t.splitk = 1;
@@ -763,7 +800,7 @@ struct Planner {
                 int64_t sk = std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
                 if (sk > 1) {
                     t.splitk = (int)sk;
-                    g.partials = scratch(sk * Mx * Nx * 8);
+                    g.partials = scratch(sk * Mr * Nr * 8);
                 }
             }
             t.nplanes_a = t.nplanes_b = np;
@@ -781,13 +818,21 @@ struct Planner {
             t.alpha = galpha;
             t.beta = gbeta;
             SplitDesc &sa = g.split_a;
-            sa.R = Mx; sa.K = Kx; sa.Rp = t.Mp; sa.Kp = t.Kp; sa.nplanes = np;
+            sa.R = Mr; sa.K = Kr; sa.Rp = t.Mp; sa.Kp = t.Kp; sa.nplanes = np;
             sa.gr = make_grp(fa_order, A, A);
             sa.gk = make_grp(k_order, A, A);
             SplitDesc &sb = g.split_b;
-            sb.R = Nx; sb.K = Kx; sb.Rp = t.Np; sb.Kp = t.Kp; sb.nplanes = np;
+            sb.R = Nr; sb.K = Kr; sb.Rp = t.Np; sb.Kp = t.Kp; sb.nplanes = np;
             sb.gr = make_grp(fb_order, B, B);
             sb.gk = make_grp(k_order, B, B);
+            if (cplx) {
+                sa.gr = dbl(sa.gr); sa.gk = dbl(sa.gk);
+                sb.gr = dbl(sb.gr); sb.gk = dbl(sb.gk);
+                sa.cplx = emb_a ? 2 : 1;
+                sb.cplx = emb_a ? 1 : 2;
+                sa.conj = A.conj ? 1 : 0;
+                sb.conj = B.conj ? 1 : 0;
+            }
             g.a_static = plan.tensors[A.tensor].kind == TKind::INTEGRAL;
             g.b_static = plan.tensors[B.tensor].kind == TKind::INTEGRAL;
             const int64_t bytes_a = t.Mp * t.Kp * 2 * np, bytes_b = t.Np * t.Kp * 2 * np;
@@ -890,7 +935,7 @@ static void grp_json(std::ostringstream &os, const Grp &g) {
 std::string describe_plan(const Plan &plan) {
     std::ostringstream os;
     os.precision(17);
-    os << "{\"o\":" << plan.o << ",\"v\":" << plan.v << ",\"precision\":" << plan.precision
+    os << "{\"o\":" << plan.o << ",\"v\":" << plan.v << ",\"dtype\":" << plan.dtype << ",\"precision\":" << plan.precision
        << ",\"workspace_bytes\":" << plan.ws_bytes << ",\"flops\":" << plan.flops
        << ",\"flops_mixed\":" << plan.flops_mixed << ",\"tensors\":[";
     for (size_t k = 0; k < plan.tensors.size(); k++) {
@@ -909,7 +954,8 @@ std::string describe_plan(const Plan &plan) {
             os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
                << ",\"splitk\":" << s.gemm.splitk
                << ",\"sAm\":" << s.gemm.sAm << ",\"sAk\":" << s.gemm.sAk << ",\"sBk\":" << s.gemm.sBk
-               << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta << ",\"cm\":";
+               << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta
+               << ",\"conj_a\":" << s.gemm.conj_a << ",\"conj_b\":" << s.gemm.conj_b << ",\"cm\":";
             grp_json(os, s.gemm.cm);
             os << ",\"cn\":";
             grp_json(os, s.gemm.cn);
@@ -920,10 +966,12 @@ std::string describe_plan(const Plan &plan) {
                << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp << ",\"bn\":" << s.tc.bn
                << ",\"splitk\":" << s.tc.splitk
                << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off
-               << ",\"reuse_a\":" << (s.skip_a ? 1 : 0) << ",\"reuse_b\":" << (s.skip_b ? 1 : 0);
+               << ",\"reuse_a\":" << (s.skip_a ? 1 : 0) << ",\"reuse_b\":" << (s.skip_b ? 1 : 0)
+               << ",\"cplx_a\":" << s.split_a.cplx << ",\"cplx_b\":" << s.split_b.cplx
+               << ",\"conj_a\":" << s.split_a.conj << ",\"conj_b\":" << s.split_b.conj;
         } else if (s.kind == StepKind::ACCUM) {
             os << ",\"elems\":" << s.acc.total << ",\"terms\":" << s.acc.nperm << ",\"alpha\":" << s.acc.alpha
-               << ",\"beta\":" << s.acc.beta;
+               << ",\"beta\":" << s.acc.beta << ",\"conj_a\":" << s.acc.conj_a << ",\"conj_b\":" << s.acc.conj_b;
         } else {
             os << ",\"elems\":" << s.zero_elems;
         }

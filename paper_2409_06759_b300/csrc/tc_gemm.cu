@@ -39,6 +39,25 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16 &h, __nv_bfloat16
     l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
+// Source element X(r, k) of a split, real or complex (see SplitDesc):
+// roff = row_offset(d, r) of a valid row.
+__device__ __forceinline__ int64_t row_offset(const SplitDesc &d, int64_t r) {
+    return grp_off(d.gr, d.cplx == 2 ? (r >> 1) : r);
+}
+__device__ __forceinline__ double src_at(const SplitDesc &d, const double *__restrict__ x, int64_t r, int64_t roff,
+                                         int64_t k) {
+    if (d.cplx == 0) return __ldg(x + roff + grp_off(d.gk, k));
+    const int kc = (int)(k & 1);
+    if (d.cplx == 1) {
+        const double val = __ldg(x + roff + grp_off(d.gk, k >> 1) + kc);
+        return (d.conj && kc) ? -val : val;
+    }
+    const int rc = (int)(r & 1), comp = rc ^ kc;
+    const double val = __ldg(x + roff + grp_off(d.gk, k >> 1) + comp);
+    const bool neg = (rc == 0 && kc == 1) != (d.conj && comp == 1);
+    return neg ? -val : val;
+}
+
 __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, const double *__restrict__ x,
                                                          __nv_bfloat16 *__restrict__ planes, int vec) {
     const int64_t plane_elems = d.Rp * d.Kp;
@@ -51,22 +70,26 @@ __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, cons
         const int64_t kspan = (it - r * spans) * 1024;
         const int64_t kend = kspan + 1024 < d.Kp ? kspan + 1024 : d.Kp;
         const bool row_ok = r < d.R;
-        const int64_t roff = row_ok ? grp_off(d.gr, r) : 0;
+        const int64_t roff = row_ok ? row_offset(d, r) : 0;
         for (int64_t k0 = kspan + (int64_t)lane * 8; k0 < kend; k0 += 256) {
             __align__(16) __nv_bfloat16 h[8], m[8], l[8];
             if (row_ok && vec && k0 + 7 < d.K) {
-                const double2 *src = reinterpret_cast<const double2 *>(x + roff + grp_off(d.gk, k0));
+                // real: eight consecutive doubles; stacked complex: four
+                // consecutive complex elements (re, im pairs)
+                const double2 *src = reinterpret_cast<const double2 *>(
+                    x + roff + (d.cplx ? grp_off(d.gk, k0 >> 1) : grp_off(d.gk, k0)));
+                const double sy = (d.cplx && d.conj) ? -1.0 : 1.0;
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const double2 v2 = __ldg(src + j);
                     split3(v2.x, h[2 * j], m[2 * j], l[2 * j]);
-                    split3(v2.y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
+                    split3(d.cplx ? sy * v2.y : v2.y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
                     const int64_t k = k0 + j;
-                    const double val = (row_ok && k < d.K) ? __ldg(x + roff + grp_off(d.gk, k)) : 0.0;
+                    const double val = (row_ok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
                     split3(val, h[j], m[j], l[j]);
                 }
             }
@@ -91,12 +114,12 @@ __global__ void __launch_bounds__(256) split_bf16_rows_kernel(const SplitDesc d,
         const int64_t r0 = (t % rtiles) * 32, k0 = (t / rtiles) * 64;
         const int64_t r = r0 + tx;
         const bool rok = r < d.R;
-        const int64_t roff = rok ? grp_off(d.gr, r) : 0;
+        const int64_t roff = rok ? row_offset(d, r) : 0;
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const int64_t k = k0 + ty + 8 * j;
-            tile[ty + 8 * j][tx] = (rok && k < d.K) ? __ldg(x + roff + grp_off(d.gk, k)) : 0.0;
+            tile[ty + 8 * j][tx] = (rok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
         }
         __syncthreads();
         // 32 rows x 64 columns = 256 runs of 8 columns: one per thread
@@ -115,20 +138,25 @@ __global__ void __launch_bounds__(256) split_bf16_rows_kernel(const SplitDesc d,
 }
 
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s) {
-    if (d.Kp % 64 || d.Rp <= 0 || d.nplanes < 2 || d.nplanes > 3) return cudaErrorInvalidValue;
+    if (d.Kp % 64 || d.Rp <= 0 || d.nplanes < 2 || d.nplanes > 3 || d.cplx < 0 || d.cplx > 2)
+        return cudaErrorInvalidValue;
+    if (d.cplx && (d.K % 2 || (d.cplx == 2 && d.R % 2))) return cudaErrorInvalidValue;
     // source unit stride inside the row group and not in K: transposed tiles
-    const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == 1;
-    const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == 1;
+    // (for complex sources the unit is one complex element, two doubles)
+    const int64_t unit = d.cplx ? 2 : 1;
+    const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit;
+    const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == unit;
     if (r_unit && !k_unit) {
         const int64_t tiles = ((d.Rp + 31) / 32) * (d.Kp / 64);
         int64_t blocks = tiles < 148 * 16 ? tiles : 148 * 16;
         split_bf16_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes);
         return cudaGetLastError();
     }
-    // vector path: innermost K digit contiguous with an extent that keeps 8-runs
-    // inside it, every other stride even (16-byte aligned double2), base aligned
-    int vec = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == 1 && d.gk.ext[d.gk.nd - 1] % 8 == 0 &&
-              ((uintptr_t)x & 15) == 0;
+    // vector path: innermost K digit contiguous with an extent that keeps the
+    // 8-column runs inside it (4 complex elements when stacked), every other
+    // stride even (16-byte aligned double2), base aligned; not for embedded
+    int vec = d.cplx != 2 && d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit &&
+              d.gk.ext[d.gk.nd - 1] % (d.cplx ? 4 : 8) == 0 && ((uintptr_t)x & 15) == 0;
     for (int q = 0; q + 1 < d.gk.nd; q++) vec &= (d.gk.str[q] % 2) == 0;
     for (int q = 0; q < d.gr.nd; q++) vec &= (d.gr.str[q] % 2) == 0;
     const int64_t items = d.Rp * ((d.Kp + 1023) / 1024);

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import torch
 
-from . import (BLOCKS, CC_F64, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
+from . import (BLOCKS, CC_C128, CC_F64, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
                cc_integral_block_elems, cc_plan_create, cc_residual, cc_solve, cc_solve_workspace_bytes,
                load_list)
 
@@ -21,18 +21,22 @@ def alloc_ws(nbytes: int, device) -> torch.Tensor:
 
 
 class DeviceSystem:
-    """Orbital energies and the six integral blocks of one system, on the device."""
+    """Orbital energies and the six integral blocks of one system, on the device.
+    A complex factor B (complex spin orbitals) gives complex128 blocks."""
 
     def __init__(self, o: int, v: int, eps_occ, eps_vir, B, device="cuda:0", blocks=BLOCKS, stream=None):
         self.o, self.v, self.device = o, v, torch.device(device)
         self.f_occ = torch.as_tensor(eps_occ, dtype=torch.float64).to(self.device)
         self.f_vir = torch.as_tensor(eps_vir, dtype=torch.float64).to(self.device)
-        Bd = torch.as_tensor(B, dtype=torch.float64).to(self.device).contiguous()
+        Bt = torch.as_tensor(B)
+        self.dtype = CC_C128 if Bt.is_complex() else CC_F64
+        self.tdtype = torch.complex128 if self.dtype == CC_C128 else torch.float64
+        Bd = Bt.to(self.tdtype).to(self.device).contiguous()
         L = Bd.shape[0]
         elems = cc_integral_block_elems(o, v)
-        self.blocks = {k: torch.empty(elems[k], dtype=torch.float64, device=self.device) for k in blocks}
-        ws = alloc_ws(cc_build_integrals_workspace_bytes(o, v, L), self.device)
-        cc_build_integrals(o, v, L, Bd, self.blocks, ws, stream=stream)
+        self.blocks = {k: torch.empty(elems[k], dtype=self.tdtype, device=self.device) for k in blocks}
+        ws = alloc_ws(cc_build_integrals_workspace_bytes(o, v, L, self.dtype), self.device)
+        cc_build_integrals(o, v, L, Bd, self.blocks, ws, dtype=self.dtype, stream=stream)
         torch.cuda.synchronize(self.device)
         del ws, Bd
 
@@ -58,19 +62,24 @@ class Engine:
         if list_text is None:
             list_text = load_list(list_name or ("ccsd" if precision == "fp64" else "ccsd_vvvv"))
         self.sys = system
-        self.plan = cc_plan_create(list_text, system.o, system.v, CC_F64, precision, _route_all=route_all)
-        self.ws = alloc_ws(self.plan.workspace_bytes, system.device)
+        self.plan = cc_plan_create(list_text, system.o, system.v, system.dtype, precision, _route_all=route_all)
+        # (at least 16 KiB: cc_energy takes its scratch from the same buffer)
+        self.ws = alloc_ws(max(self.plan.workspace_bytes, 16384), system.device)
 
     def residual(self, t1, t2, r1=None, r2=None, stream=None):
         o, v, dev = self.sys.o, self.sys.v, self.sys.device
-        r1 = torch.empty(o, v, dtype=torch.float64, device=dev) if r1 is None else r1
-        r2 = torch.empty(o, o, v, v, dtype=torch.float64, device=dev) if r2 is None else r2
+        dt = self.sys.tdtype
+        r1 = torch.empty(o, v, dtype=dt, device=dev) if r1 is None else r1
+        r2 = torch.empty(o, o, v, v, dtype=dt, device=dev) if r2 is None else r2
         cc_residual(self.plan, self.sys.ints(), t1, t2, r1, r2, self.ws, stream=stream)
         return r1, r2
 
-    def energy(self, t1, t2, stream=None) -> float:
+    def energy(self, t1, t2, stream=None):
+        """float, or complex for a complex system."""
         e = torch.zeros(2, dtype=torch.float64, device=self.sys.device)
         cc_energy(self.plan, self.sys.ints(), t1, t2, e, self.ws, stream=stream)
+        if self.sys.dtype == CC_C128:
+            return complex(e[0].item(), e[1].item())
         return float(e[0].item())
 
 

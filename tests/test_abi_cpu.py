@@ -108,3 +108,36 @@ def test_workspace_grows_with_size(cc):
     small = cc.cc_plan_create(cc.load_list("ccsd"), 4, 8).workspace_bytes
     big = cc.cc_plan_create(cc.load_list("ccsd"), 8, 16).workspace_bytes
     assert 0 < small < big
+
+
+def test_complex_plan_structure(cc):
+    """Complex plans: the same steps as the real plan with four times the real
+    flops; integral references whose bra and ket are swapped against the
+    stored block are read conjugated."""
+    o, v = 6, 20
+    for name in ("ccsd", "ccsd_vvvv"):
+        r = cc.cc_plan_create(cc.load_list(name), o, v, dtype=cc.CC_F64)
+        z = cc.cc_plan_create(cc.load_list(name), o, v, dtype=cc.CC_C128)
+        assert z.describe()["dtype"] == 1
+        assert z.flops == pytest.approx(4 * r.flops)
+        assert z.workspace_bytes > 1.8 * r.workspace_bytes
+    drv = cc.cc_plan_create("R2[ijab] = V[abij]", 3, 5, dtype=cc.CC_C128).describe()
+    assert [s["conj_a"] for s in drv["steps"] if s["kind"] == "accum"] == [1]
+    drv = cc.cc_plan_create("R2[ijab] = V[ijab]", 3, 5, dtype=cc.CC_C128).describe()
+    assert [s["conj_a"] for s in drv["steps"] if s["kind"] == "accum"] == [0]
+    # real lists never conjugate
+    drv = cc.cc_plan_create("R2[ijab] = V[abij]", 3, 5).describe()
+    assert [s["conj_a"] for s in drv["steps"] if s["kind"] == "accum"] == [0]
+
+
+def test_complex_split_route_doubles_k(cc):
+    """On the split route a complex contraction is one real GEMM of doubled K,
+    with the smaller operand embedded (its rows doubled) and the larger stacked."""
+    o, v = 8, 40
+    p = cc.cc_plan_create("R2[ijab] = 0.5 T2[ijef] * V[abef]", o, v, dtype=cc.CC_C128, precision="bf16x3")
+    g = [s for s in p.describe()["steps"] if s["kind"] == "gemm_bf16split"][0]
+    assert g["K"] == 2 * v * v
+    assert {g["M"], g["N"]} == {v * v, 2 * o * o}
+    assert g["flops"] == 8.0 * o * o * v ** 4
+    small = "a" if g["M"] == 2 * o * o else "b"
+    assert g["cplx_" + small] == 2 and g["cplx_" + ("b" if small == "a" else "a")] == 1
