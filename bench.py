@@ -6,6 +6,11 @@ cc_solve: the full residual (every statement of the contraction list), the
 energy, |R|, the Jacobi update and the DIIS extrapolation.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+                  [--dtype f64|c128]
+
+--dtype c128 runs the same workload with complex spin orbitals (complex
+Hermitian integrals, complex amplitudes; every complex product is four real
+ones, counted as such in the flops).
 
 Under torchrun (N > 1) every rank runs an independent replica (the residual of
 one system does not shard without an exchange; no collective is used on the
@@ -28,6 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "CC residual TFLOP/s and s/iter on 1 B300, mixed vs FP64 at |ΔE|<1e-6 Eh"
 WORKLOAD = "spin-orbital CCSD o=40 v=200 L=120 seed=0, FP64 real, synthetic integrals"
 SMALL = "spin-orbital CCSD o=10 v=40 L=120 seed=0, FP64 real, synthetic integrals"
+WORKLOAD_C = "spin-orbital CCSD o=40 v=200 L=120 seed=0, complex128 (complex spin orbitals), synthetic integrals"
+SMALL_C = "spin-orbital CCSD o=10 v=40 L=120 seed=0, complex128 (complex spin orbitals), synthetic integrals"
+
+
+def jsonable(e):
+    """A (possibly complex) energy as JSON: a number, or [re, im]."""
+    return [e.real, e.imag] if isinstance(e, complex) else e
+
+
+def workload_name(args):
+    if args.dtype == "c128":
+        return SMALL_C if args.small else WORKLOAD_C
+    return SMALL if args.small else WORKLOAD
 # DRAM bytes / operand-plane bytes of the ladder kernel, from its ncu capture (None until re-captured
 # after a kernel change)
 TRAFFIC_RATIO = 1.066
@@ -139,7 +157,7 @@ def fp64_peak_live(torch):
     return 2 * n ** 3 / best / 1e12
 
 
-def cpu_baseline(o, v, nsamp, flops_per_residual, seed=0):
+def cpu_baseline(o, v, nsamp, flops_per_residual, seed=0, complex_=False):
     """The FP64 oracle on the host cores: nsamp sampled R2 elements of the same
     workload (integral blocks and one-particle intermediates built from B first),
     converted to the metric's unit as the residual share those elements stand for."""
@@ -147,8 +165,8 @@ def cpu_baseline(o, v, nsamp, flops_per_residual, seed=0):
 
     import ccinputs
     import oracle
-    s = ccinputs.make_system(o, v, L=120 if o > 10 else 120, seed=seed)
-    t1, t2 = ccinputs.random_amplitudes(o, v, seed=seed, scale1=0.01, scale2=0.01)
+    s = ccinputs.make_system(o, v, L=120, seed=seed, complex_=complex_)
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=seed, scale1=0.01, scale2=0.01, complex_=complex_)
     rng = np.random.default_rng(1)
     idx = np.stack([rng.integers(0, o, nsamp), rng.integers(0, o, nsamp), rng.integers(0, v, nsamp),
                     rng.integers(0, v, nsamp)], 1)
@@ -158,7 +176,8 @@ def cpu_baseline(o, v, nsamp, flops_per_residual, seed=0):
     share = nsamp / float(o * o * v * v)
     return {"value": flops_per_residual * share / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": dt,
-            "sample": f"{nsamp} R2 elements of the o={o} v={v} residual by the explicit-loop FP64 oracle "
+            "sample": f"{nsamp} R2 elements of the o={o} v={v} {'complex ' if complex_ else ''}residual by the "
+                      f"explicit-loop FP64 oracle "
                       f"(oovv/ooov/ovvv blocks and one-particle intermediates built from B first); value = "
                       f"residual flops x {nsamp}/(o^2 v^2) / time"}
 
@@ -168,18 +187,19 @@ def run_reference(args, world, rank):
         return
     o, v = (10, 40) if args.small else (40, 200)
     import paper_2409_06759_b300 as cc
-    flops = cc.cc_plan_create(cc.load_list("ccsd"), o, v).flops
+    cplx = args.dtype == "c128"
+    flops = cc.cc_plan_create(cc.load_list("ccsd"), o, v, dtype=cc.CC_C128 if cplx else cc.CC_F64).flops
     vals = []
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(o, v, args.ref_samples, flops)
+        r = cpu_baseline(o, v, args.ref_samples, flops, complex_=cplx)
         if k >= args.warmup:
             vals.append(r)
     secs = sum(r["seconds"] for r in vals)
     value = flops * args.ref_samples / float(o * o * v * v) * len(vals) / secs / 1e12
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / len(vals) * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": SMALL if args.small else WORKLOAD},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx else "f64",
+            "data": "synthetic", "config": {"workload": workload_name(args)},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -197,6 +217,7 @@ def main():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ref-samples", type=int, default=2)
+    ap.add_argument("--dtype", default="f64", choices=["f64", "c128"])
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -213,23 +234,27 @@ def main():
     dev = torch.device("cuda", local)
     cfg = dict(ccinputs.CONFIG_SMALL if args.small else ccinputs.CONFIG_LADDER)
     o, v = cfg["o"], cfg["v"]
+    cplx = args.dtype == "c128"
+    cdt = cc.CC_C128 if cplx else cc.CC_F64
+    tdt = torch.complex128 if cplx else torch.float64
+    esz = 16 if cplx else 8
     pk, pk_kind = peaks()
 
     # the oracle's host leg runs before any GPU work (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        flops_fp64 = cc.cc_plan_create(cc.load_list("ccsd"), o, v).flops
-        cpu = cpu_baseline(o, v, 4, flops_fp64)
+        flops_fp64 = cc.cc_plan_create(cc.load_list("ccsd"), o, v, dtype=cdt).flops
+        cpu = cpu_baseline(o, v, 4 if not cplx else 2, flops_fp64, complex_=cplx)
 
-    sysm = ccinputs.make_system(**cfg)
+    sysm = ccinputs.make_system(**cfg, complex_=cplx)
     t0 = time.perf_counter()
     dsys = DeviceSystem.from_system(sysm, device=dev)
     t_int = time.perf_counter() - t0
     mixed = Engine(dsys, list_name="ccsd_vvvv", precision=args.precision)
     fp64 = Engine(dsys, list_name="ccsd")
     stream = torch.cuda.current_stream(dev)
-    z = lambda: (torch.zeros(o, v, dtype=torch.float64, device=dev),
-                 torch.zeros(o, o, v, v, dtype=torch.float64, device=dev))
+    z = lambda: (torch.zeros(o, v, dtype=tdt, device=dev),
+                 torch.zeros(o, o, v, v, dtype=tdt, device=dev))
 
     # ---- device-timed steps on the split-bf16 plan
     t1, t2 = z()
@@ -261,19 +286,22 @@ def main():
     st = desc["steps"][k_dom]
     t_kernel = ms_kernel[k_dom] / calls / 1e3
     if st["kind"] == "gemm_bf16split":
-        tflop = st["flops"] * st["products"]
+        # tensor-pipe flops: products x 2 M N K of the real GEMM the kernel runs (for a
+        # complex contraction that GEMM carries the four real products of each complex one)
+        tflop = st["products"] * 2.0 * st["M"] * st["N"] * st["K"]
         achieved = tflop / t_kernel / 1e12
         # the kernel runs ~10 ms inside a ~50 ms step: the burst figure is the denominator
         peak = pk["bf16_tflops"]
         # DRAM bytes of one launch, from the ncu capture of this kernel version at o=20 v=100, scaled by
         # the operand bytes that dominate it (profiles/tc_gemm_ladder_o20_v100.md); None until captured
         traffic = None
-        if TRAFFIC_RATIO is not None and st["M"] == v * v and st["N"] == o * o and st["K"] == v * v:
+        if not cplx and TRAFFIC_RATIO is not None and st["M"] == v * v and st["N"] == o * o and st["K"] == v * v:
             traffic = TRAFFIC_RATIO * (st["Mp"] * st["Kp"] * 4 + st["Np"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": "tc_gemm_kernel (" + st["note"] + ")",
                 "fp64_equiv_tflops": st["flops"] / t_kernel / 1e12, "ms_per_launch": t_kernel * 1e3,
+                "gemm_shape": [st["M"], st["N"], st["K"]],
                 "frac_of_sustained": achieved / pk["bf16_tflops_sustained"],
                 "peak_kind": f"{pk_kind} bf16 burst (tensor-pipe flops = {st['products']} products x 2MNK)"}
     else:
@@ -281,8 +309,8 @@ def main():
                 "frac": None, "traffic": None, "kernel": st["note"]}
 
     # ---- end to end through the C ABI with host buffers
-    h1 = torch.empty(o, v, dtype=torch.float64).pin_memory()
-    h2 = torch.empty(o, o, v, v, dtype=torch.float64).pin_memory()
+    h1 = torch.empty(o, v, dtype=tdt).pin_memory()
+    h2 = torch.empty(o, o, v, v, dtype=tdt).pin_memory()
     h1.copy_(t1.cpu())
     h2.copy_(t2.cpu())
     e2e_steps = max(2, min(args.steps, 4))
@@ -299,17 +327,18 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize()
     dt_e2e = max_over_ranks(f0.elapsed_time(f1) / 1e3, world)
-    nbytes = (h1.numel() + h2.numel()) * 8
+    nbytes = (h1.numel() + h2.numel()) * esz
     e2e = {"value": world * flops * e2e_steps / dt_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "s_per_iter": dt_e2e / e2e_steps}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": s_iter * 1e3, "s_per_iter": s_iter, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}: bf16 tensor-core products, fp32 "
-            "accumulation, fp64 outputs/energy/DIIS", "data": "synthetic",
-            "config": {"workload": SMALL if args.small else WORKLOAD, "precision": args.precision,
+            "accumulation, fp64 outputs/energy/DIIS" + (" (complex128 tensors)" if cplx else ""), "data": "synthetic",
+            "config": {"workload": workload_name(args), "precision": args.precision,
                        "list": "ccsd_vvvv", "flops_per_iter": flops, "replicas": world,
-                       "l2": "inputs larger than L2 (<ab||ef> split planes 6.4 GB, T2 512 MB)",
+                       "l2": "inputs larger than L2 (<ab||ef> split planes %.1f GB, T2 %d MB)"
+                             % (6.4 * (2 if cplx else 1), 512 * (2 if cplx else 1)),
                        "integral_build_s": t_int},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
     if cpu is not None:
@@ -318,6 +347,9 @@ def main():
     # ---- time to solution (|R| < 1e-8): FP64 alone; the accurate split route (bf16x6, chunked
     #      accumulation) alone; the same with FP64 defect-corrected refinement (converged on the FP64 residual)
     if not args.no_tts:
+        # each solve holds its plans' workspaces and its DIIS history: free the timed solver's first
+        del sol, t1, t2
+        torch.cuda.empty_cache()
         fpk = fp64_peak_live(torch)
         acc = Engine(dsys, list_name="ccsd_vvvv", precision="bf16x6")
 
@@ -330,6 +362,8 @@ def main():
             r = sol_.solve(a1, a2, max_iter=60, tol=1e-8, stream=stream, **kw)
             g1.record(stream)
             torch.cuda.synchronize()
+            del sol_, a1, a2
+            torch.cuda.empty_cache()
             return r, g0.elapsed_time(g1) / 1e3
 
         cc.cc_plan_profile_enable(fp64.plan, True)
@@ -344,7 +378,7 @@ def main():
         tk = fker[kf] / fcalls / 1e3
         line["fp64"] = {"value": fp64.plan.flops * rf.iterations / tts_fp64 / 1e12, "unit": "TFLOP/s",
                         "s_per_iter": tts_fp64 / rf.iterations, "iterations": rf.iterations,
-                        "time_to_solution_s": tts_fp64, "energy": rf.energy, "converged": rf.converged,
+                        "time_to_solution_s": tts_fp64, "energy": jsonable(rf.energy), "converged": rf.converged,
                         "roofline": {"bound": "fp64", "kernel": "gemm_f64_kernel (" + fst["note"] + ")",
                                      "achieved": fst["flops"] / tk / 1e12, "peak": fpk, "unit": "TFLOP/s",
                                      "frac": fst["flops"] / tk / 1e12 / fpk,
@@ -357,7 +391,7 @@ def main():
                        "switched_at": rm.switched_at, "delta_E": abs(rm.energy - rf.energy),
                        "speedup": tts_fp64 / tts_mixed, "converged": rm.converged and rf.converged,
                        "mixed_precision": "bf16x6 (three planes, chunked float-float accumulation)",
-                       "energy_fp64": rf.energy, "energy_mixed_refined": rm.energy,
+                       "energy_fp64": jsonable(rf.energy), "energy_mixed_refined": jsonable(rm.energy),
                        "rnorms_mixed_refined": [float(f"{x:.3e}") for x in rm.rnorms],
                        "rnorms_fp64": [float(f"{x:.3e}") for x in rf.rnorms]}
     if rank == 0:

@@ -936,7 +936,9 @@ std::string describe_plan(const Plan &plan) {
     std::ostringstream os;
     os.precision(17);
     os << "{\"o\":" << plan.o << ",\"v\":" << plan.v << ",\"dtype\":" << plan.dtype << ",\"precision\":" << plan.precision
-       << ",\"workspace_bytes\":" << plan.ws_bytes << ",\"flops\":" << plan.flops
+       << ",\"workspace_bytes\":" << plan.ws_bytes << ",\"interm_bytes\":" << plan.interm_bytes
+       << ",\"scratch_bytes\":" << plan.scratch_bytes << ",\"splits_bytes\":" << plan.splits_bytes
+       << ",\"cache_bytes\":" << plan.cache_bytes << ",\"flops\":" << plan.flops
        << ",\"flops_mixed\":" << plan.flops_mixed << ",\"tensors\":[";
     for (size_t k = 0; k < plan.tensors.size(); k++) {
         const Tensor &t = plan.tensors[k];

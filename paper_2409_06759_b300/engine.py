@@ -63,8 +63,20 @@ class Engine:
             list_text = load_list(list_name or ("ccsd" if precision == "fp64" else "ccsd_vvvv"))
         self.sys = system
         self.plan = cc_plan_create(list_text, system.o, system.v, system.dtype, precision, _route_all=route_all)
-        # (at least 16 KiB: cc_energy takes its scratch from the same buffer)
-        self.ws = alloc_ws(max(self.plan.workspace_bytes, 16384), system.device)
+        self._ws = None
+
+    @property
+    def ws(self):
+        """The plan's workspace, allocated on first use (a Solver brings its own,
+        so an engine used only through a Solver never holds a second copy).  At
+        least 16 KiB: cc_energy takes its scratch from the same buffer."""
+        if self._ws is None:
+            self._ws = alloc_ws(max(self.plan.workspace_bytes, 16384), self.sys.device)
+        return self._ws
+
+    def release(self):
+        """Drops the workspace (allocated again on the next residual or energy)."""
+        self._ws = None
 
     def residual(self, t1, t2, r1=None, r2=None, stream=None):
         o, v, dev = self.sys.o, self.sys.v, self.sys.device
