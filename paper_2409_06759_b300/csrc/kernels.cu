@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
 // transposed), so reads and writes stay coalesced for the P(..) gathers.
 template <typename T>
 __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, const T *__restrict__ src,
-                                                          T *__restrict__ out, int d0, int d1, unsigned tmask,
+                                                          T *__restrict__ out, int d0, int d1, uint64_t tmask,
                                                           int64_t tiles0, int64_t tiles1) {
     __shared__ T sm[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
     for (int p = 0; p < d.nperm; p++) {
         const int64_t s0 = d.sstr[p][d0], s1 = d.sstr[p][d1];
         const int64_t base = sbase[p] + i0b * s0 + i1b * s1;
-        if (!((tmask >> p) & 1u)) {
+        if (!((tmask >> p) & 1ull)) {
 #pragma unroll
             for (int r = 0; r < 4; r++) {
                 const int64_t i1 = ty + 8 * r;
@@ -167,7 +167,7 @@ static cudaError_t accum_t(const AccumDesc &d, const T *src, T *out, cudaStream_
     if (!d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 16) {
         const int d0 = d.nd - 1;
         int d1 = -1;
-        unsigned tmask = 0;
+        uint64_t tmask = 0;
         // partner: the dim holding a term's smallest source stride, when that is not d0
         for (int p = 0; p < d.nperm; p++) {
             int kmin = 0;
@@ -175,7 +175,7 @@ static cudaError_t accum_t(const AccumDesc &d, const T *src, T *out, cudaStream_
                 if (d.ext[k] > 1 && (d.ext[kmin] <= 1 || d.sstr[p][k] < d.sstr[p][kmin])) kmin = k;
             if (kmin != d0 && d.sstr[p][kmin] < d.sstr[p][d0]) {
                 if (d1 < 0) d1 = kmin;
-                if (kmin == d1) tmask |= 1u << p;
+                if (kmin == d1) tmask |= 1ull << p;
             }
         }
         if (d1 < 0) {

@@ -8,7 +8,7 @@
 namespace ccb {
 
 constexpr int kMaxDims = 8;     // dims of one tensor view
-constexpr int kMaxPerms = 16;   // terms of an expanded permutation operator
+constexpr int kMaxPerms = 36;   // terms of an expanded permutation operator (3! x 3! for triples)
 
 // Mixed-radix index group: a fused matrix index decomposed into nd digits
 // (digit 0 outermost, digit nd-1 fastest); offset = sum digit_d * str[d].

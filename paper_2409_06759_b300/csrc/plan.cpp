@@ -490,6 +490,11 @@ struct Planner {
         st.kind = StepKind::ACCUM;
         st.out = outref;
         st.a = srcref;
+        if ((int)perms.size() > kMaxPerms || (int)out.idx.size() > kMaxDims) {
+            err = "more than " + std::to_string(kMaxPerms) + " permutation terms or " + std::to_string(kMaxDims) +
+                  " indices in one statement";
+            return st;
+        }
         AccumDesc &d = st.acc;
         d.nd = (int)out.idx.size();
         d.nperm = (int)perms.size();
@@ -586,6 +591,7 @@ struct Planner {
             std::set<int> A(s.rhs[0].letters.begin(), s.rhs[0].letters.end());
             if (A != O) { err = "a single-tensor statement must carry exactly the output's indices"; return false; }
             Step st = accum_step(out, outref, in[0], tensor_ref(in[0].tensor), perms, alpha, beta);
+            if (!err.empty()) return false;
             st.stmt = si;
             st.note = "copy " + plan.tensors[in[0].tensor].name + " -> " + T.name;
             plan.steps.push_back(st);
@@ -610,6 +616,7 @@ struct Planner {
             // outer product: each output element is formed directly as a sum of
             // signed products (no GEMM, no scratch, no separate antisymmetrisation)
             Step st = accum_step(out, outref, in[0], tensor_ref(in[0].tensor), perms, alpha, beta);
+            if (!err.empty()) return false;
             st.acc.two_src = 1;
             for (int p = 0; p < st.acc.nperm; p++)
                 for (int k = 0; k < st.acc.nd; k++) {
@@ -698,6 +705,7 @@ struct Planner {
                     r = scratch(view_elems(w) * esz);
                 }
                 Step p = accum_step(w, r, X, xref, std::vector<Perm>(1, Perm{1.0, {}}), 1.0, 0.0);
+                if (!err.empty()) return;
                 p.static_src = stat;
                 p.stmt = si;
                 p.note = std::string(stat ? "permute (cached) " : "permute ") + plan.tensors[X.tensor].name;
@@ -710,6 +718,7 @@ struct Planner {
             };
             if (perm_a) do_perm(A, aref, fa.order);
             if (perm_b) do_perm(B, bref, fb.order);
+            if (!err.empty()) return false;
             Fuse fa2 = fusable(A, FA), ka2 = fusable(A, K), fb2 = fusable(B, FB), kb2 = fusable(B, K);
             if (!(fa2.ok && ka2.ok && fb2.ok && kb2.ok && same_order(A, ka2.order, B, kb2.order))) {
                 err = "internal: operands not GEMM-ready after permutes";
@@ -848,6 +857,7 @@ struct Planner {
         plan.steps.push_back(g);
         if (!direct) {
             Step e = accum_step(out, outref, Cv, cref, perms, 1.0, beta);   // alpha went into the GEMM
+            if (!err.empty()) return false;
             e.stmt = si;
             e.note = "antisymmetrise -> " + T.name;
             plan.steps.push_back(e);

@@ -63,8 +63,9 @@ def _relabel(x, labels, mp):
     return np.transpose(x, np.argsort(a))
 
 
-def run_list(text: str, o: int, v: int, eps, V, t1, t2):
-    """Returns (R1, R2) including the -D*t terms, like the engine."""
+def run_list(text: str, o: int, v: int, eps, V, t1, t2, t3=None):
+    """Returns (R1, R2) -- or (R1, R2, R3) when t3 is given -- including the
+    -D*t terms, like the engine."""
     n = o + v
     sl = {"o": slice(0, o), "v": slice(o, n)}
     env, out = {}, {}
@@ -73,8 +74,8 @@ def run_list(text: str, o: int, v: int, eps, V, t1, t2):
         return [l for l in letters if _space(l) == "o"] + [l for l in letters if _space(l) == "v"]
 
     def get(name, letters):
-        if name in ("T1", "T2", "t", "T"):
-            return (t1 if len(letters) == 2 else t2), amp_order(letters)
+        if name in ("T1", "T2", "T3", "t", "T"):
+            return {2: t1, 4: t2, 6: t3}[len(letters)], amp_order(letters)
         if name == "V":
             sp = [_space(l) for l in letters]
             return V[sl[sp[0]], sl[sp[1]], sl[sp[2]], sl[sp[3]]], list(letters)
@@ -88,10 +89,12 @@ def run_list(text: str, o: int, v: int, eps, V, t1, t2):
         oname, obr, op, rest = m.groups()
         olet = _letters(obr)
         fac = 1.0
-        mf = re.match(r"\s*([+-]?\s*(?:\d+\.?\d*|\.\d+)(?:[eE][+-]?\d+)?)\s*(.*)$", rest)
+        mf = re.match(r"\s*([+-]?\s*(?:\d+\.?\d*|\.\d+)(?:[eE][+-]?\d+)?)(?:\s*/\s*(\d+))?\s*(.*)$", rest)
         if mf:
             fac = float(mf.group(1).replace(" ", ""))
-            rest = mf.group(2)
+            if mf.group(2):
+                fac /= float(mf.group(2))
+            rest = mf.group(3)
         elif rest.strip().startswith("-"):
             fac = -1.0
             rest = rest.strip()[1:]
@@ -127,4 +130,10 @@ def run_list(text: str, o: int, v: int, eps, V, t1, t2):
     d2 = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
     r1 = out["R1"] - d1 * t1 if "R1" in out else np.zeros((o, v))
     r2 = out["R2"] - d2 * t2 if "R2" in out else np.zeros((o, o, v, v))
-    return r1, r2
+    if t3 is None:
+        return r1, r2
+    d3 = (eo[:, None, None, None, None, None] + eo[None, :, None, None, None, None]
+          + eo[None, None, :, None, None, None] - ev[None, None, None, :, None, None]
+          - ev[None, None, None, None, :, None] - ev[None, None, None, None, None, :])
+    r3 = out["R3"] - d3 * t3 if "R3" in out else np.zeros((o, o, o, v, v, v))
+    return r1, r2, r3
