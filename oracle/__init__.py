@@ -1,8 +1,11 @@
-"""FP64 CPU oracle for the spin-orbital CCSD residual (test infrastructure).
+"""FP64 CPU oracle for the spin-orbital CC residual (test infrastructure).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
-may import this package.  It wraps ``cc_oracle.c`` (plain C, explicit loops,
-OpenMP over outer loops) through ctypes and shares no code with the CUDA path.
+may import this package.  It wraps ``cc_oracle.c`` (the CCSD equations, plain
+C, explicit loops, OpenMP over outer loops) and ``cc_definition.c`` (residual
+elements of any rank up to triples straight from <Phi_l| exp(-T) H_N exp(T)
+|Phi_0>, no CC equations) through ctypes, both compiled for double and complex
+double, and shares no code with the CUDA path or the list derivation.
 
 Parity pins (all in ``tests/test_oracle_pins.py``):
 * residual elements vs a determinant-space brute force of
@@ -25,6 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cc_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "cc_definition.c")]
 _LIB = os.path.join(_HERE, "libccoracle.so")
 _lib = None
 
@@ -36,14 +40,15 @@ class _Complex(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile cc_oracle.c twice (real orc_*, complex orz_*) into libccoracle.so."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(x) for x in _SRCS):
         import tempfile
         with tempfile.TemporaryDirectory() as td:
             objs = []
-            for tag, flags in (("real", []), ("cplx", ["-DCC_COMPLEX"])):
-                obj = os.path.join(td, tag + ".o")
-                subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", *flags, "-c", _SRC, "-o", obj])
-                objs.append(obj)
+            for src in _SRCS:
+                for tag, flags in (("real", []), ("cplx", ["-DCC_COMPLEX"])):
+                    obj = os.path.join(td, os.path.basename(src) + "." + tag + ".o")
+                    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", *flags, "-c", src, "-o", obj])
+                    objs.append(obj)
             subprocess.check_call(["gcc", "-shared", "-fopenmp", "-o", _LIB, *objs, "-lm"])
     return _LIB
 
@@ -71,6 +76,9 @@ def lib():
         L.orz_ccsd_energy.restype = _Complex
         L.orz_ccsd_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, vp, vp, ctypes.c_double,
                                      ctypes.c_int, ctypes.c_int, vp, dp, ctypes.POINTER(ctypes.c_int)]
+        for nm in ("orc_cc_definition_elements", "orz_cc_definition_elements"):
+            getattr(L, nm).argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp, vp, vp, vp, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
         L.orz_ccsd_r2_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp, vp, vp, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), vp]
         _lib = L
@@ -199,3 +207,27 @@ def ccsd_solve(o, v, eps, V, t1=None, t2=None, tol=1e-8, maxiter=100, diis_max=8
     k = it.value
     return dict(status=st, iters=k, energies=en[:k], rnorms=rn[:k], t1=t1, t2=t2,
                 energy=en[k - 1] if k else float("nan"))
+
+
+def cc_definition_elements(o, v, B, eps, t1, t2=None, t3=None, rank=2, idx=None):
+    """Residual elements of the given rank (1..3) at the index tuples idx
+    [ns][2*rank] = (i.., a..), or the energy E - E_ref (rank 0), from
+    <Phi_l| exp(-T) H_N exp(T) |Phi_0> directly (cc_definition.c).  T holds the
+    ranks whose amplitudes are given (t2 / t3 None: absent)."""
+    cplx = _cplx(B, t1, t2, t3)
+    dt = np.complex128 if cplx else np.float64
+    B = np.ascontiguousarray(B, dtype=dt)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    ts = [None if t is None else np.ascontiguousarray(t, dtype=dt) for t in (t1, t2, t3)]
+    if rank == 0:
+        idx = np.zeros((1, 0), dtype=np.int32)
+    idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 2 * rank) if rank else idx
+    ns = idx.shape[0]
+    out = np.zeros(max(ns, 1), dtype=dt)
+    vp = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+    fn = lib().orz_cc_definition_elements if cplx else lib().orc_cc_definition_elements
+    rc = fn(o, v, B.shape[0], vp(B), _p(eps), vp(ts[0]), vp(ts[1]), vp(ts[2]), rank, ns,
+            idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), vp(out))
+    if rc != 0:
+        raise MemoryError("definition oracle failed (%d)" % rc)
+    return out[0] if rank == 0 else out

@@ -176,3 +176,50 @@ def test_complex_sampled_elements_match_full_residual():
     got = oracle.ccsd_r2_sample(o, v, B, s.eps, t1, t2, idx)
     _, r2 = oracle.ccsd_residual(o, v, s.eps, oracle.antisym_integrals(o, v, B), t1, t2)
     assert np.abs(got - r2[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]).max() < 1e-13
+
+
+# ------------------------------------------- definition oracle (any rank <= 3)
+def _all_idx(o, v, rank):
+    import itertools
+    return np.array([list(i) + list(a) for i in itertools.product(range(o), repeat=rank)
+                     for a in itertools.product(range(v), repeat=rank)])
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("o,v,seed,triples", [(2, 3, 81, False), (3, 4, 82, False), (3, 4, 83, True),
+                                              (3, 5, 84, True)])
+def test_definition_oracle_matches_brute_force(cplx, o, v, seed, triples):
+    """cc_definition.c (CI coefficients of exp(T) Phi_0, Slater-Condon, the
+    exp(-T) row) against the full-matrix determinant brute force: every
+    element of R1, R2 (and R3) and the energy, CCSD and CCSDT."""
+    s = ccinputs.make_system(o, v, L=5, seed=seed, complex_=cplx)
+    B = s.B * 6.0
+    V = oracle.antisym_integrals(o, v, B)
+    amps = ccinputs.random_amplitudes(o, v, seed=seed, scale1=0.1, scale2=0.1, triples=triples, complex_=cplx)
+    t1, t2, t3 = amps[0], amps[1], (amps[2] if triples else None)
+    ref = detspace.brute_residual(o, v, s.eps, V, t1, t2, t3)
+    e = oracle.cc_definition_elements(o, v, B, s.eps, t1, t2, t3, rank=0)
+    assert abs(e - ref[0]) < 1e-13
+    for rank in ((1, 2, 3) if triples else (1, 2)):
+        idx = _all_idx(o, v, rank)
+        got = oracle.cc_definition_elements(o, v, B, s.eps, t1, t2, t3, rank=rank, idx=idx)
+        want = np.array([ref[rank][tuple(r)] for r in idx])
+        assert np.abs(got - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_definition_oracle_agrees_with_the_ccsd_equations(cplx):
+    """Two independent oracles, one from the CCSD equations and one from the
+    definition, on sampled elements of a system too large for the brute force."""
+    o, v = 5, 12
+    s = ccinputs.make_system(o, v, L=8, seed=85, complex_=cplx)
+    B = s.B * 6.0
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=85, scale1=0.1, scale2=0.1, complex_=cplx)
+    r1, r2 = oracle.ccsd_residual(o, v, s.eps, oracle.antisym_integrals(o, v, B), t1, t2)
+    rng = np.random.default_rng(3)
+    idx2 = np.stack([rng.integers(0, o, 6), rng.integers(0, o, 6), rng.integers(0, v, 6), rng.integers(0, v, 6)], 1)
+    got2 = oracle.cc_definition_elements(o, v, B, s.eps, t1, t2, None, rank=2, idx=idx2)
+    assert np.abs(got2 - r2[tuple(idx2.T)]).max() < 1e-12
+    idx1 = np.stack([rng.integers(0, o, 4), rng.integers(0, v, 4)], 1)
+    got1 = oracle.cc_definition_elements(o, v, B, s.eps, t1, t2, None, rank=1, idx=idx1)
+    assert np.abs(got1 - r1[tuple(idx1.T)]).max() < 1e-12
