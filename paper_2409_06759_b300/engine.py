@@ -61,6 +61,7 @@ class Engine:
                  route_all: bool = False, list_name: str | None = None):
         if list_text is None:
             list_text = load_list(list_name or ("ccsd" if precision == "fp64" else "ccsd_vvvv"))
+        self.triples = "T3[" in list_text
         self.sys = system
         self.plan = cc_plan_create(list_text, system.o, system.v, system.dtype, precision, _route_all=route_all)
         self._ws = None
@@ -78,13 +79,16 @@ class Engine:
         """Drops the workspace (allocated again on the next residual or energy)."""
         self._ws = None
 
-    def residual(self, t1, t2, r1=None, r2=None, stream=None):
+    def residual(self, t1, t2, r1=None, r2=None, stream=None, t3=None, r3=None):
+        """(R1, R2), or (R1, R2, R3) when t3 is given (a list with triples)."""
         o, v, dev = self.sys.o, self.sys.v, self.sys.device
         dt = self.sys.tdtype
         r1 = torch.empty(o, v, dtype=dt, device=dev) if r1 is None else r1
         r2 = torch.empty(o, o, v, v, dtype=dt, device=dev) if r2 is None else r2
-        cc_residual(self.plan, self.sys.ints(), t1, t2, r1, r2, self.ws, stream=stream)
-        return r1, r2
+        if t3 is not None and r3 is None:
+            r3 = torch.empty(o, o, o, v, v, v, dtype=dt, device=dev)
+        cc_residual(self.plan, self.sys.ints(), t1, t2, r1, r2, self.ws, stream=stream, t3=t3, r3=r3)
+        return (r1, r2) if t3 is None else (r1, r2, r3)
 
     def energy(self, t1, t2, stream=None):
         """float, or complex for a complex system."""
@@ -103,8 +107,8 @@ class Solver:
         nb = cc_solve_workspace_bytes(engine.plan, diis_max, refine.plan if refine else None)
         self.ws = alloc_ws(nb, engine.sys.device)
 
-    def solve(self, t1, t2, max_iter=100, tol=1e-8, resume=False, switch_tol=0.0, verbose=0, stream=None):
+    def solve(self, t1, t2, max_iter=100, tol=1e-8, resume=False, switch_tol=0.0, verbose=0, stream=None, t3=None):
         return cc_solve(self.eng.plan, self.eng.sys.ints(), t1, t2, self.ws, max_iter=max_iter, tol=tol,
                         diis_max=self.diis_max, resume=resume,
                         refine_plan=self.refine.plan if self.refine else None, switch_tol=switch_tol,
-                        verbose=verbose, stream=stream)
+                        verbose=verbose, stream=stream, t3=t3)
