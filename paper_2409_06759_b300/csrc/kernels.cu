@@ -30,6 +30,16 @@ __device__ __forceinline__ double2 scal(double s, double2 x) { return make_doubl
 template <typename T> __device__ __forceinline__ T zero();
 template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
 template <> __device__ __forceinline__ double2 zero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
+// element type T -> compute type CT (FP64 data multiplied in FP32: one rounding) and back
+template <typename CT> __device__ __forceinline__ CT down(double x);
+template <> __device__ __forceinline__ double down<double>(double x) { return x; }
+template <> __device__ __forceinline__ float down<float>(double x) { return __double2float_rn(x); }
+template <typename CT> __device__ __forceinline__ CT down(double2 x) { return x; }
+__device__ __forceinline__ double up(double x) { return x; }
+__device__ __forceinline__ double up(float x) { return (double)x; }
+__device__ __forceinline__ double2 up(double2 x) { return x; }
+__device__ __forceinline__ float cfma(float a, float b, float acc) { return fmaf(a, b, acc); }
 // acc + a * b over complex (or real) numbers
 __device__ __forceinline__ double cfma(double a, double b, double acc) { return fma(a, b, acc); }
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
@@ -239,19 +249,20 @@ __device__ __forceinline__ int64_t grp_offset(const Grp &g, int64_t x) {
     return off;
 }
 
-template <typename T, bool A_KCONTIG, bool B_KCONTIG>
+// CT: compute type (T, or float for FP64 data multiplied in FP32)
+template <typename T, typename CT, bool A_KCONTIG, bool B_KCONTIG>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, const T *__restrict__ A,
                                                        const T *__restrict__ B, T *__restrict__ C,
                                                        T *__restrict__ partials, int thread_m_fast, int64_t kchunk) {
-    __shared__ T As[GBK][GBM + GPAD];
-    __shared__ T Bs[GBK][GBN + GPAD];
+    __shared__ CT As[GBK][GBM + GPAD];
+    __shared__ CT Bs[GBK][GBN + GPAD];
     const int tid = threadIdx.x;
     const int64_t m0 = (int64_t)blockIdx.x * GBM;
     const int64_t n0 = (int64_t)blockIdx.y * GBN;
     const int tm = thread_m_fast ? (tid & 15) : (tid >> 4);
     const int tn = thread_m_fast ? (tid >> 4) : (tid & 15);
 
-    T ra[4], rb[4];
+    CT ra[4], rb[4];
     auto load_tiles = [&](int64_t k0, int64_t klim) {
 #pragma unroll
         for (int r = 0; r < 4; r++) {
@@ -259,12 +270,12 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
             int mm, kk;
             if (A_KCONTIG) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
             int64_t gm = m0 + mm, gk = k0 + kk;
-            ra[r] = (gm < d.M && gk < klim) ? cj(ld(A + gm * d.sAm + gk * d.sAk), d.conj_a) : zero<T>();
+            ra[r] = (gm < d.M && gk < klim) ? down<CT>(cj(ld(A + gm * d.sAm + gk * d.sAk), d.conj_a)) : zero<CT>();
             int nn;
             if (B_KCONTIG) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
             int64_t gn = n0 + nn;
             gk = k0 + kk;
-            rb[r] = (gn < d.N && gk < klim) ? cj(ld(B + gk * d.sBk + gn * d.sBn), d.conj_b) : zero<T>();
+            rb[r] = (gn < d.N && gk < klim) ? down<CT>(cj(ld(B + gk * d.sBk + gn * d.sBn), d.conj_b)) : zero<CT>();
         }
     };
     auto store_tiles = [&]() {
@@ -276,11 +287,11 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         }
     };
 
-    T acc[4][4];
+    CT acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = zero<T>();
+        for (int j = 0; j < 4; j++) acc[i][j] = zero<CT>();
 
     // K slice of this CTA (the whole K unless split)
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         if (k0 + GBK < kend) load_tiles(k0 + GBK, kend);
 #pragma unroll
         for (int k = 0; k < GBK; k++) {
-            T a[4], b[4];
+            CT a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; i++) a[i] = As[k][tm + 16 * i];
 #pragma unroll
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int64_t m = m0 + tm + 16 * i, n = n0 + tn + 16 * j;
-                if (m < d.M && n < d.N) P[n * d.M + m] = acc[i][j];
+                if (m < d.M && n < d.N) P[n * d.M + m] = up(acc[i][j]);
             }
         return;
     }
@@ -336,7 +347,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            if (rv[i] && cv[j]) C[ro[i] + co[j]] = axpy(d.beta, old[i][j], scal(d.alpha, acc[i][j]));
+            if (rv[i] && cv[j]) C[ro[i] + co[j]] = axpy(d.beta, old[i][j], scal(d.alpha, up(acc[i][j])));
 }
 
 // ------------------------------------------------------------------ gemv
@@ -464,7 +475,7 @@ cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double 
     return splitk_reduce_t<double>(M, N, splitk, partials, cm, cn, alpha, beta, C, s);
 }
 
-template <typename T>
+template <typename T, typename CT>
 static cudaError_t gemm_t(const GemmF64Desc &d, const T *A, const T *B, T *C, T *partials, cudaStream_t s) {
     if (d.K == 1 && d.M > 1 && d.N > 1) {
         int64_t sm = d.cm.nd ? d.cm.str[d.cm.nd - 1] : 0, sn = d.cn.nd ? d.cn.str[d.cn.nd - 1] : 0;
@@ -492,10 +503,10 @@ static cudaError_t gemm_t(const GemmF64Desc &d, const T *A, const T *B, T *C, T 
     const bool ak = d.sAk == 1 && !(d.sAm == 1 && d.K == 1);
     const bool bk = d.sBk == 1 && !(d.sBn == 1 && d.K == 1);
     if (zs > 1) m_fast = 1;
-    if (ak && bk) gemm_f64_kernel<T, true, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
-    else if (ak) gemm_f64_kernel<T, true, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
-    else if (bk) gemm_f64_kernel<T, false, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
-    else gemm_f64_kernel<T, false, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    if (ak && bk) gemm_f64_kernel<T, CT, true, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else if (ak) gemm_f64_kernel<T, CT, true, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else if (bk) gemm_f64_kernel<T, CT, false, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
+    else gemm_f64_kernel<T, CT, false, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || zs == 1) return e;
     return splitk_reduce_t<T>(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
@@ -505,9 +516,10 @@ cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double 
                             cudaStream_t s) {
     if (d.M <= 0 || d.N <= 0) return cudaSuccess;
     if (d.cplx)
-        return gemm_t<double2>(d, reinterpret_cast<const double2 *>(A), reinterpret_cast<const double2 *>(B),
-                               reinterpret_cast<double2 *>(C), reinterpret_cast<double2 *>(partials), s);
-    return gemm_t<double>(d, A, B, C, partials, s);
+        return gemm_t<double2, double2>(d, reinterpret_cast<const double2 *>(A), reinterpret_cast<const double2 *>(B),
+                                        reinterpret_cast<double2 *>(C), reinterpret_cast<double2 *>(partials), s);
+    if (d.f32) return gemm_t<double, float>(d, A, B, C, partials, s);
+    return gemm_t<double, double>(d, A, B, C, partials, s);
 }
 
 // ------------------------------------------------------- iteration kernels

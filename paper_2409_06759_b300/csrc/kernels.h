@@ -47,6 +47,8 @@ struct AccumDesc {
 // partials[z][n][m] (m fastest) and launch_splitk_reduce applies alpha/beta.
 // cplx: complex double operands and output (strides in complex elements, four
 // real FMAs per complex product); conj_a / conj_b conjugate A / B.
+// f32 (real only): operands rounded to FP32 as they are staged and multiplied
+// and accumulated in FP32 (the SIMT FP32 rate); output FP64.
 struct GemmF64Desc {
     int64_t M, N, K;
     int64_t sAm, sAk, sBk, sBn;
@@ -54,6 +56,7 @@ struct GemmF64Desc {
     double alpha, beta;
     int splitk;
     int cplx, conj_a, conj_b;
+    int f32;
 };
 
 // Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes

@@ -652,8 +652,21 @@ struct Planner {
         scratch_need = 0;
         // split-bf16 route: contractions of >= 2e8 flops that are real GEMMs
         // (matrix-vector shapes stay on the memory-bound FP64 kernels)
-        const bool use_mixed = plan.precision != 0 &&
-                               (mixed_all || (flops >= 2.0e8 && Mx > 1 && Nx > 1 && Kx > 1));
+        bool use_mixed = plan.precision != 0 &&
+                         (mixed_all || (flops >= 2.0e8 && Mx > 1 && Nx > 1 && Kx > 1));
+        // Tensor tiles are 128 x bn x 64: a contraction that fills them poorly
+        // (a short K or N, e.g. the rank-o updates of T3) runs as an FP64-data
+        // GEMM with FP32 arithmetic instead (real), or in FP64 (complex).
+        bool use_f32 = false;
+        if (use_mixed && !mixed_all) {
+            const int64_t bn = Nx <= 64 ? 64 : Nx <= 128 ? 128 : 256;
+            const double eff = (double)Mx * (double)Nx * (double)Kx /
+                               ((double)align_up(Mx, 128) * (double)align_up(Nx, bn) * (double)align_up(Kx, 64));
+            if (eff < 0.5) {
+                use_mixed = false;
+                use_f32 = !cplx;
+            }
+        }
 
         Step g;
         g.kind = StepKind::GEMM;
@@ -778,6 +791,7 @@ struct Planner {
             g.gemm.cn = cn;
             g.gemm.alpha = galpha;
             g.gemm.beta = gbeta;
+            g.gemm.f32 = use_f32 ? 1 : 0;
             g.gemm.cplx = cplx ? 1 : 0;
             g.gemm.conj_a = cplx && A.conj ? 1 : 0;
             g.gemm.conj_b = cplx && B.conj ? 1 : 0;
@@ -959,7 +973,7 @@ std::string describe_plan(const Plan &plan) {
     for (size_t k = 0; k < plan.steps.size(); k++) {
         const Step &s = plan.steps[k];
         os << (k ? "," : "") << "{\"stmt\":" << s.stmt << ",\"kind\":\""
-           << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : "gemm_f64")
+           << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : s.gemm.f32 ? "gemm_f32" : "gemm_f64")
                                         : s.kind == StepKind::ACCUM ? "accum" : "zero")
            << "\",\"note\":\"" << s.note << "\"";
         if (s.kind == StepKind::GEMM && !s.mixed) {

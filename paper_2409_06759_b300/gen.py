@@ -348,8 +348,9 @@ def _op_expansions(letters):
 
 
 def diagrams(k, terms):
-    """Groups the terms of R_k into diagrams: [(coef, text_of_P_ops, key)],
-    each standing for sum over its P expansion of sign * coef * term."""
+    """Groups the terms of R_k into diagrams: [(coef, text_of_P_ops, key,
+    nterms)], each standing for the sum over its P expansion (nterms signed
+    relabellings) of sign * coef * term."""
     left = dict(terms)
     out = []
     occ_ops = _op_expansions(list(OCC_EXT[:k]))
@@ -374,7 +375,7 @@ def diagrams(k, terms):
             if contrib and all(left.get(x) == y for x, y in contrib.items()):
                 for x in contrib:
                     del left[x]
-                out.append((c, text, rep))
+                out.append((c, text, rep, len(exp)))
                 done = True
                 break
         if not done:
@@ -428,7 +429,9 @@ class Factoriser:
     def num(f):
         return f"{f.numerator}" if f.denominator == 1 else f"{f.numerator}/{f.denominator}"
 
-    def emit(self, k, coef, ptext, key):
+    def emit(self, k, coef, ptext, key, target=None, first=False):
+        """Statements of one diagram.  target: write the unsymmetrised term into
+        this accumulator instead of R_k (no P operators; '=' when first)."""
         hk, hl, tls = key_to_term(key)
         occ, vir = OCC_EXT[:k], VIR_EXT[:k]
         free_o = [c for c in "ijklmn" if c not in occ] + [f"h{q}" for q in range(1, 10)]
@@ -457,6 +460,8 @@ class Factoriser:
 
         res = "R%d" % k
         head = f"{res}[{''.join(out)}] += {self.num(coef)}{(' ' + ptext) if ptext else ''} "
+        if target is not None:
+            head = f"{target}[{''.join(out)}] {'=' if first else '+='} {self.num(coef)} "
         if not seq:
             self.lines.append(head + tensor_text(*ref(("t", 0))))
             return
@@ -517,9 +522,20 @@ class Factoriser:
 METHODS = {"ccd": (2,), "ccsd": (1, 2), "ccsdt": (1, 2, 3)}
 
 
-def generate(method, o, v, cap=None, header=""):
+FULL_P = {2: "P(ij) P(ab)", 3: "P(i/jk) P(jk) P(a/bc) P(bc)"}
+
+
+def generate(method, o, v, cap=None, header="", defer=True):
     """Contraction list text of a method (METHODS) for extents (o, v), which
-    only steer the factorisation order and the intermediate cap."""
+    only steer the factorisation order and the intermediate cap.
+
+    defer: the unsymmetrised term X of every diagram of R_k (k >= 2) is
+    accumulated into one buffer Z_k with weight nterms / (k!)^2, and R_k gets
+    the full antisymmetriser A of Z_k once.  X is antisymmetric under the
+    stabiliser H of its orbit (|H| = (k!)^2 / nterms), so the diagram's
+    P-operator sum equals A(X) / |H|: one antisymmetrising pass per residual
+    instead of one per diagram.  This holds for antisymmetric amplitudes, the
+    convention of every tensor the lists read."""
     ranks = METHODS[method]
     cap = cap if cap is not None else (o ** 3) * (v ** 3)
     fz = Factoriser(o, v, cap)
@@ -528,8 +544,16 @@ def generate(method, o, v, cap=None, header=""):
         terms = derive(k, ranks)
         dg = diagrams(k, terms)
         fz.lines.append(f"# R{k}: {len(dg)} diagrams")
-        for coef, ptext, key in dg:
-            fz.emit(k, coef, ptext, key)
+        use_z = defer and k >= 2
+        for q, (coef, ptext, key, nterms) in enumerate(dg):
+            if use_z:
+                w = coef * Fraction(nterms, factorial(k) ** 2)
+                fz.emit(k, w, "", key, target=f"Z{k}", first=q == 0)
+            else:
+                fz.emit(k, coef, ptext, key)
+        if use_z:
+            idx = OCC_EXT[:k] + VIR_EXT[:k]
+            fz.lines.append(f"R{k}[{idx}] += {FULL_P[k]} Z{k}[{idx}]")
     return "\n".join(lines + fz.lines) + "\n"
 
 

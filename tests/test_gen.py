@@ -79,6 +79,20 @@ def test_ccsdt_list_factorisation_keeps_the_triples_ladder_as_one_gemm():
     """The o^3 v^5 particle ladder 1/2 <ab||ef> t_ijk^efc is one contraction
     of T3 with the vvvv block (trailing virtual pair contracted, no T3 copy)."""
     text = open(os.path.join(LISTS, "ccsdt.txt")).read()
-    lad = [l for l in text.splitlines() if l.startswith("R3") and "V[" in l and "T3[" in l
+    lad = [l for l in text.splitlines() if l.startswith("Z3") and "V[" in l and "T3[" in l
            and all(c in "abcdefg" for c in l.split("V[")[1][:4])]
     assert len(lad) == 1
+
+
+def test_deferred_antisymmetrisation_matches_per_diagram_operators():
+    """One full antisymmetriser over the weighted sum of unsymmetrised terms
+    equals the per-diagram P(..) operators (both against the brute force's
+    reference values through the einsum reading)."""
+    o, v = 3, 5
+    s = ccinputs.make_system(o, v, L=6, seed=9)
+    V = oracle.antisym_integrals(o, v, s.B * 6.0)
+    t1, t2, t3 = ccinputs.random_amplitudes(o, v, seed=9, scale1=0.1, scale2=0.1, triples=True)
+    a = list_exec.run_list(gen.generate("ccsdt", 8, 64, defer=False), o, v, s.eps, V, t1, t2, t3)
+    b = list_exec.run_list(gen.generate("ccsdt", 8, 64, defer=True), o, v, s.eps, V, t1, t2, t3)
+    for x, y in zip(a, b):
+        assert np.abs(x - y).max() < 1e-14

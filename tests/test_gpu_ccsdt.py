@@ -148,3 +148,23 @@ def test_ccsdt_full_size_sampled_elements(cc):
     assert np.abs(g + g.transpose(1, 0, 2, 3, 4, 5)).max() <= 1e-13 * scale
     assert np.abs(g - g.transpose(1, 2, 0, 3, 4, 5)).max() <= 1e-13 * scale
     assert np.abs(g + g.transpose(0, 1, 2, 4, 3, 5)).max() <= 1e-13 * scale
+
+
+def test_ccsdt_default_mixed_plan_matches_fp64(cc):
+    """The bench's mixed plan (tensor-core route for the contractions that fill
+    128 x bn x 64 tiles, FP32 arithmetic for the skinny rank-o updates of T3)
+    against the FP64 plan, o=8 v=40."""
+    _, engine = cc
+    o, v = 8, 40
+    s, B, t1, t2, t3 = case(o, v, 5, L=16, scale=1.0, tscale=0.01)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
+    T = (dev(t1), dev(t2), dev(t3))
+    f = engine.Engine(dsys, list_name="ccsdt").residual(T[0], T[1], t3=T[2])
+    f = [x.cpu() for x in f]
+    mixed = engine.Engine(dsys, list_name="ccsdt", precision="bf16x3")
+    kinds = {st["kind"] for st in mixed.plan.describe()["steps"]}
+    assert {"gemm_f32", "gemm_bf16split"} <= kinds
+    m = [x.cpu() for x in mixed.residual(T[0], T[1], t3=T[2])]
+    d = np.sqrt(sum(((a - b).numpy() ** 2).sum() for a, b in zip(f, m)))
+    n = np.sqrt(sum((a.numpy() ** 2).sum() for a in f))
+    assert d <= 1e-4 * n, (d, n)
