@@ -159,7 +159,12 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
                 }
                 break;
             case StepKind::GEMM:
-                if (!stp.mixed) {
+                if (stp.rows) {
+                    if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
+                    CC_CUDA(launch_rows_gemm(stp.rg, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
+                                             resolve(stp.out, I, A, R, w), s));
+                    pl->launches++;
+                } else if (!stp.mixed) {
                     if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
                     CC_CUDA(launch_gemm_f64(stp.gemm, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
                                             resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w), s));

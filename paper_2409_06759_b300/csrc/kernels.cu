@@ -350,6 +350,72 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
             if (rv[i] && cv[j]) C[ro[i] + co[j]] = axpy(d.beta, old[i][j], scal(d.alpha, up(acc[i][j])));
 }
 
+// ------------------------------------------------------------ rows_gemm
+// offset of a mixed-radix index below 2^32 with 32-bit divisions
+__device__ __forceinline__ int64_t grp_offset32(const Grp &g, uint32_t x) {
+    int64_t off = 0;
+    for (int k = g.nd - 1; k >= 0; k--) {
+        const uint32_t e = (uint32_t)g.ext[k];
+        const uint32_t q = x / e;
+        off += (int64_t)(x - q * e) * g.str[k];
+        x = q;
+    }
+    return off;
+}
+
+template <typename CT, int NC>
+__global__ void __launch_bounds__(256) rows_gemm_kernel(const RowsGemmDesc d, const double *__restrict__ X,
+                                                        const double *__restrict__ Y, double *__restrict__ C) {
+    __shared__ CT ys[64 * NC];
+    __shared__ int64_t xko[64], cco[NC];
+    for (int e = threadIdx.x; e < 64 * NC; e += blockDim.x) {
+        const int k = e / NC, c = e - k * NC;
+        ys[e] = (k < d.K && c < d.nc) ? down<CT>(__ldg(Y + grp_offset(d.yk, k) + grp_offset(d.yc, c))) : zero<CT>();
+    }
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) xko[k] = k < d.K ? grp_offset(d.xk, k) : 0;
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) cco[c] = c < d.nc ? grp_offset(d.cc, c) : 0;
+    __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < d.R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t xo = grp_offset32(d.xr, (uint32_t)r), co = grp_offset32(d.cr, (uint32_t)r);
+        CT acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) acc[c] = zero<CT>();
+        for (int k = 0; k < d.K; k++) {
+            const CT a = down<CT>(__ldg(X + xo + xko[k]));
+#pragma unroll
+            for (int c = 0; c < NC; c++) acc[c] = cfma(a, ys[k * NC + c], acc[c]);
+        }
+        // read-modify-write in batches of eight (loads issued before the stores)
+#pragma unroll
+        for (int c0 = 0; c0 < NC; c0 += 8) {
+            double old[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) old[j] = (d.beta != 0.0 && c0 + j < d.nc) ? C[co + cco[c0 + j]] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (c0 + j < d.nc) C[co + cco[c0 + j]] = fma(d.beta, old[j], d.alpha * up(acc[c0 + j]));
+        }
+    }
+}
+
+template <typename CT>
+static cudaError_t rows_t(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s) {
+    int64_t blocks = (d.R + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    const unsigned b = (unsigned)blocks;
+    if (d.nc <= 8) rows_gemm_kernel<CT, 8><<<b, 256, 0, s>>>(d, X, Y, C);
+    else if (d.nc <= 16) rows_gemm_kernel<CT, 16><<<b, 256, 0, s>>>(d, X, Y, C);
+    else if (d.nc <= 32) rows_gemm_kernel<CT, 32><<<b, 256, 0, s>>>(d, X, Y, C);
+    else rows_gemm_kernel<CT, 64><<<b, 256, 0, s>>>(d, X, Y, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s) {
+    if (d.R <= 0) return cudaSuccess;
+    if (d.nc < 1 || d.nc > 64 || d.K < 1 || d.K > 64 || d.R > 0xffffffffLL) return cudaErrorInvalidValue;
+    return d.f32 ? rows_t<float>(d, X, Y, C, s) : rows_t<double>(d, X, Y, C, s);
+}
+
 // ------------------------------------------------------------------ gemv
 // y(r) = alpha * sum_k X(r,k) x(k) + beta * y(r): the GEMM shapes with one
 // output dimension of extent 1 are memory-bound matrix-vector products.

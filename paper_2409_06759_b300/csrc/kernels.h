@@ -59,6 +59,22 @@ struct GemmF64Desc {
     int f32;
 };
 
+// Narrow GEMM: C(r, c) = alpha * sum_k X(r, k) Y(k, c) + beta * C(r, c) for
+// many rows r, at most 64 columns c and a contraction of at most 64: the
+// rank-o updates of T3 and similar shapes that tensor tiles would pad.  Every
+// operand and the output are read through mixed-radix groups, so no operand is
+// permuted first; one thread per row, Y staged in shared memory.
+// f32: products and sums in FP32 (FP64 data, one rounding per operand).
+struct RowsGemmDesc {
+    int64_t R;
+    int nc, K;
+    Grp xr, xk;     // X(r, k) = X[xr(r) + xk(k)]
+    Grp yk, yc;     // Y(k, c) = Y[yk(k) + yc(c)]
+    Grp cr, cc;     // C(r, c) = C[cr(r) + cc(c)]
+    double alpha, beta;
+    int f32;
+};
+
 // Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes
 // bf16 planes P_p[r][k] of a padded K-major matrix [Rp][Kp]:
 //   hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); rows >= R and
@@ -101,6 +117,7 @@ cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double 
 // C(m,n) = alpha * sum_z partials[z][n][m] + beta * C(m,n) (fixed summation order)
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
                                  double alpha, double beta, double *C, cudaStream_t s);
+cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s);
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s);
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C,
                            double *partials, int *err_flag, cudaStream_t s);

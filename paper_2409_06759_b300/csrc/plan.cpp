@@ -675,7 +675,22 @@ struct Planner {
         g.note = plan.tensors[A.tensor].name + "*" + plan.tensors[B.tensor].name + " -> " + T.name;
         std::vector<int> fa_order, fb_order, k_order;
 
-        if (use_mixed) {
+        // narrow contractions (short K, one short free side): one thread per
+        // row of the long side, every operand read in place through its strides
+        const bool rows_ok = !cplx && !use_mixed && !mixed_all && Kx >= 2 && Kx <= 64 &&
+                             std::min(Mx, Nx) >= 2 && std::min(Mx, Nx) <= 64 && std::max(Mx, Nx) >= 4096 &&
+                             std::max(Mx, Nx) <= 0xffffffffLL;
+        if (rows_ok) {
+            const bool direct0 = perms.size() == 1 && perms[0].sigma.empty();
+            fa_order = direct0 ? fusable(out, FA).order : fusable(A, FA).order;
+            fb_order = direct0 ? fusable(out, FB).order : fusable(B, FB).order;
+            k_order = Mx >= Nx ? fusable(A, K).order : fusable(B, K).order;
+            g.rows = true;
+            g.gemm.M = Mx;
+            g.gemm.N = Nx;
+            g.gemm.K = Kx;
+            g.gemm.f32 = use_f32 ? 1 : 0;
+        } else if (use_mixed) {
             // The split kernels read any strided view: no permutes on this route,
             // and the row/column orders are free.  Rows and columns follow the
             // output's stride order (consecutive rows -> the output's fastest
@@ -786,7 +801,27 @@ struct Planner {
         g.out = cref;
         g.a = aref;
         g.b = bref;
-        if (!g.mixed) {
+        if (g.rows) {
+            RowsGemmDesc &r = g.rg;
+            const bool xa = Mx >= Nx;
+            const View &X = xa ? A : B, &Y = xa ? B : A;
+            const std::vector<int> &rord = xa ? fa_order : fb_order, &cord = xa ? fb_order : fa_order;
+            r.R = xa ? Mx : Nx;
+            r.nc = (int)(xa ? Nx : Mx);
+            r.K = (int)Kx;
+            r.xr = make_grp(rord, X, X);
+            r.xk = make_grp(k_order, X, X);
+            r.yk = make_grp(k_order, Y, Y);
+            r.yc = make_grp(cord, Y, Y);
+            r.cr = make_grp(rord, X, Cv);
+            r.cc = make_grp(cord, Y, Cv);
+            if (!err.empty()) return false;
+            r.alpha = galpha;
+            r.beta = gbeta;
+            r.f32 = use_f32 ? 1 : 0;
+            g.a = xa ? aref : bref;
+            g.b = xa ? bref : aref;
+        } else if (!g.mixed) {
             g.gemm.cm = cm;
             g.gemm.cn = cn;
             g.gemm.alpha = galpha;
@@ -973,7 +1008,8 @@ std::string describe_plan(const Plan &plan) {
     for (size_t k = 0; k < plan.steps.size(); k++) {
         const Step &s = plan.steps[k];
         os << (k ? "," : "") << "{\"stmt\":" << s.stmt << ",\"kind\":\""
-           << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : s.gemm.f32 ? "gemm_f32" : "gemm_f64")
+           << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : s.rows ? (s.gemm.f32 ? "gemm_rows_f32" : "gemm_rows")
+                                                   : s.gemm.f32 ? "gemm_f32" : "gemm_f64")
                                         : s.kind == StepKind::ACCUM ? "accum" : "zero")
            << "\",\"note\":\"" << s.note << "\"";
         if (s.kind == StepKind::GEMM && !s.mixed) {

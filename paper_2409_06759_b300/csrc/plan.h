@@ -62,6 +62,8 @@ struct Step {
     bool a_static = false, b_static = false;     // operand is an integral block (cacheable)
     bool static_src = false;                     // ACCUM permute of an integral block into the cache
     bool skip_a = false, skip_b = false;         // planes already split by an earlier step (same source version)
+    bool rows = false;                           // narrow GEMM (one thread per row, operands in place)
+    RowsGemmDesc rg{};
     double flops = 0.0;
     std::string note;
 };

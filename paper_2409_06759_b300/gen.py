@@ -553,7 +553,12 @@ def generate(method, o, v, cap=None, header="", defer=True):
                 fz.emit(k, coef, ptext, key)
         if use_z:
             idx = OCC_EXT[:k] + VIR_EXT[:k]
-            fz.lines.append(f"R{k}[{idx}] += {FULL_P[k]} Z{k}[{idx}]")
+            if k == 3:
+                # A = A_occ A_vir: two passes of six terms instead of one of 36
+                fz.lines.append(f"W3[{idx}] = P(a/bc) P(bc) Z3[{idx}]")
+                fz.lines.append(f"R3[{idx}] += P(i/jk) P(jk) W3[{idx}]")
+            else:
+                fz.lines.append(f"R{k}[{idx}] += {FULL_P[k]} Z{k}[{idx}]")
     return "\n".join(lines + fz.lines) + "\n"
 
 

@@ -127,3 +127,24 @@ def test_accurate_mixed_solve_small_config(cc):
     res = engine.Solver(mixed, refine=engine.Engine(dsys, list_name="ccsd")).solve(b1, b2, max_iter=60, tol=1e-8,
                                                                                   switch_tol=1e-7)
     assert res.converged and abs(res.energy - ref["energy"]) < 1e-10
+
+
+@pytest.mark.parametrize("prec,kind,rel", [("fp64", "gemm_rows", 1e-13), ("bf16x3", "gemm_rows_f32", 2e-6)])
+def test_narrow_gemm_route(cc, prec, kind, rel):
+    """Rank-o updates (short K and one short free side) run on the narrow
+    kernel, reading T2 in place: FP64 arithmetic on the FP64 plan, FP32 on the
+    mixed plan (error bound K * 2^-24 relative to sum |a||b|)."""
+    ccm, engine = cc
+    o, v = 24, 100
+    text = "X[mj] = V[mnje] * T1[ne]\nR2[ijab] = -1 P(ij) T2[imab] * X[mj]"
+    s, B, t1, t2 = small_case(o, v, 21, L=8, scale=6.0, tscale=0.05)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV, blocks=("ooov",))
+    eng = engine.Engine(dsys, list_text=text, precision=prec)
+    assert kind in [st["kind"] for st in eng.plan.describe()["steps"]]
+    r1 = torch.zeros(o, v, dtype=torch.float64, device=DEV)
+    r2 = torch.zeros(o, o, v, v, dtype=torch.float64, device=DEV)
+    ccm.cc_residual(eng.plan, dsys.ints(), to_dev(t1), to_dev(t2), r1, r2, eng.ws)
+    torch.cuda.synchronize()
+    e1, e2 = list_exec.run_list(text, o, v, s.eps, oracle_V(o, v, B), t1, t2)
+    err = np.abs(r2.cpu().numpy() - e2).max()
+    assert err <= rel * np.abs(e2).max(), err
