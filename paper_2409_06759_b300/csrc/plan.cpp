@@ -654,17 +654,26 @@ struct Planner {
         // (matrix-vector shapes stay on the memory-bound FP64 kernels)
         bool use_mixed = plan.precision != 0 &&
                          (mixed_all || (flops >= 2.0e8 && Mx > 1 && Nx > 1 && Kx > 1));
-        // Tensor tiles are 128 x bn x 64: a contraction that fills them poorly
-        // (a short K or N, e.g. the rank-o updates of T3) runs as an FP64-data
-        // GEMM with FP32 arithmetic instead (real), or in FP64 (complex).
+        // Tensor tiles are 128 x bn x 64.  A narrow contraction (K <= 64 and one
+        // free side <= 64, e.g. the rank-o updates of T3) that fills them less
+        // than half is memory-bound: it runs on the narrow kernel with FP32
+        // arithmetic.  Anything else stays on the tensor cores unless they
+        // would waste more than ~85% of the tile (then: FP32 SIMT GEMM).
+        const bool narrow = !cplx && Kx >= 2 && Kx <= 64 && std::min(Mx, Nx) >= 2 && std::min(Mx, Nx) <= 64 &&
+                            std::max(Mx, Nx) >= 4096 && std::max(Mx, Nx) <= 0xffffffffLL;
         bool use_f32 = false;
+        bool use_rows = narrow;
         if (use_mixed && !mixed_all) {
             const int64_t bn = Nx <= 64 ? 64 : Nx <= 128 ? 128 : 256;
             const double eff = (double)Mx * (double)Nx * (double)Kx /
                                ((double)align_up(Mx, 128) * (double)align_up(Nx, bn) * (double)align_up(Kx, 64));
-            if (eff < 0.5) {
+            if (narrow && eff < 0.5) {
                 use_mixed = false;
-                use_f32 = !cplx;
+                use_rows = true;
+                use_f32 = true;
+            } else if (eff < 0.15 && !cplx) {
+                use_mixed = false;
+                use_f32 = true;
             }
         }
 
@@ -677,10 +686,7 @@ struct Planner {
 
         // narrow contractions (short K, one short free side): one thread per
         // row of the long side, every operand read in place through its strides
-        const bool rows_ok = !cplx && !use_mixed && !mixed_all && Kx >= 2 && Kx <= 64 &&
-                             std::min(Mx, Nx) >= 2 && std::min(Mx, Nx) <= 64 && std::max(Mx, Nx) >= 4096 &&
-                             std::max(Mx, Nx) <= 0xffffffffLL;
-        if (rows_ok) {
+        if (use_rows && !use_mixed) {
             const bool direct0 = perms.size() == 1 && perms[0].sigma.empty();
             fa_order = direct0 ? fusable(out, FA).order : fusable(A, FA).order;
             fb_order = direct0 ? fusable(out, FB).order : fusable(B, FB).order;
