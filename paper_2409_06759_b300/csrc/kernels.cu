@@ -327,16 +327,20 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
             }
         return;
     }
+    // the tile's row and column offsets, decomposed once per CTA
+    __shared__ int64_t s_ro[GBM], s_co[GBN];
+    __syncthreads();
+    if (tid < GBM) s_ro[tid] = m0 + tid < d.M ? grp_offset(d.cm, m0 + tid) : 0;
+    else if (tid < GBM + GBN) s_co[tid - GBM] = n0 + tid - GBM < d.N ? grp_offset(d.cn, n0 + tid - GBM) : 0;
+    __syncthreads();
     int64_t ro[4], co[4];
     bool rv[4], cv[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        int64_t m = m0 + tm + 16 * i;
-        rv[i] = m < d.M;
-        ro[i] = rv[i] ? grp_offset(d.cm, m) : 0;
-        int64_t n = n0 + tn + 16 * i;
-        cv[i] = n < d.N;
-        co[i] = cv[i] ? grp_offset(d.cn, n) : 0;
+        rv[i] = m0 + tm + 16 * i < d.M;
+        ro[i] = s_ro[tm + 16 * i];
+        cv[i] = n0 + tn + 16 * i < d.N;
+        co[i] = s_co[tn + 16 * i];
     }
     T old[4][4];
 #pragma unroll
@@ -380,10 +384,15 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const RowsGemmDesc d, co
         CT acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; c++) acc[c] = zero<CT>();
-        for (int k = 0; k < d.K; k++) {
-            const CT a = down<CT>(__ldg(X + xo + xko[k]));
+        // eight loads in flight per thread before their products (ys rows k >= K are zero)
+        for (int k0 = 0; k0 < d.K; k0 += 8) {
+            CT a[8];
 #pragma unroll
-            for (int c = 0; c < NC; c++) acc[c] = cfma(a, ys[k * NC + c], acc[c]);
+            for (int j = 0; j < 8; j++) a[j] = k0 + j < d.K ? down<CT>(__ldg(X + xo + xko[k0 + j])) : zero<CT>();
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+#pragma unroll
+                for (int c = 0; c < NC; c++) acc[c] = cfma(a[j], ys[(k0 + j) * NC + c], acc[c]);
         }
         // read-modify-write in batches of eight (loads issued before the stores)
 #pragma unroll
