@@ -225,6 +225,28 @@ CC_API cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opt
 CC_API cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const cc_solve_opts *opts,
                           cc_solve_report *report, void *ws, size_t ws_bytes, void *stream);
 
+/* cc_solve_batched -- Jacobi + DIIS on n independent systems at once (their
+ * own plans, integrals and amplitudes; sizes may differ).  Iteration 0 runs
+ * each system's residual directly (filling the static caches); later
+ * iterations replay one CUDA graph holding every system's residual, energy and
+ * norm as independent branches, then four batched kernels (Jacobi, Gram row,
+ * DIIS solve, combine) update all systems that are still iterating, driven by
+ * a per-system table the host rewrites each iteration.  The per-system
+ * arithmetic and stopping rule are those of cc_solve (converged systems stop
+ * updating; their residuals are still evaluated by the graph).
+ *   plans: n distinct plans (one per system), each writing R2.
+ *   ints, amps: arrays of n structs; amps in = start, out = final iterates.
+ *   opts: shared options (refine_plan and resume are not supported: CC_ERR_UNSUPPORTED).
+ *   reports: NULL or n reports (their optional arrays as in cc_solve).
+ *   ws: cc_solve_batched_workspace_bytes bytes, 256-byte aligned.
+ * Returns CC_OK when every system converged, CC_ERR_NOT_CONVERGED otherwise
+ * (the message counts them). */
+CC_API cc_status cc_solve_batched_workspace_bytes(int n, const cc_plan *plans, const cc_solve_opts *opts,
+                                                  size_t *bytes);
+CC_API cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints, cc_amps *amps,
+                                  const cc_solve_opts *opts, cc_solve_report *reports, void *ws, size_t ws_bytes,
+                                  void *stream);
+
 /* Integral construction (setup step):  (pq|rs) = sum_L B[L][p][q] B[L][r][s]
  * and <pq||rs> = (pr|qs) - (ps|qr) for the six canonical blocks (Eq. ham2q).
  *   B: device [L][n][n] (n = o + v, occupied first), double or complex

@@ -32,7 +32,7 @@ EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_
            "cc_plan_profile_enable", "cc_plan_profile_read", "cc_plan_launch_count",
            "cc_residual", "cc_energy", "cc_solve_workspace_bytes", "cc_solve", "cc_integral_block_elems",
            "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_status_string",
-           "cc_last_error", "cc_version"]
+           "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libccb300.so is not built ({LIB_PATH}); run paper_2409_06759_b300/build.py "
@@ -91,6 +91,9 @@ _sig = {
     "cc_build_integrals": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "cc_energy_noalloc": (c_int, [c_int, c_int, _P(cc_integrals), _P(cc_amps), c_void_p, c_void_p]),
+    "cc_solve_batched_workspace_bytes": (c_int, [c_int, _P(c_void_p), _P(cc_solve_opts), _P(c_size_t)]),
+    "cc_solve_batched": (c_int, [c_int, _P(c_void_p), _P(cc_integrals), _P(cc_amps), _P(cc_solve_opts),
+                                 _P(cc_solve_report), c_void_p, c_size_t, c_void_p]),
     "cc_status_string": (ctypes.c_char_p, [c_int]),
     "cc_last_error": (ctypes.c_char_p, []),
     "cc_version": (ctypes.c_char_p, []),
@@ -301,6 +304,43 @@ def cc_solve(plan: Plan, ints: dict, t1, t2, ws, max_iter: int = 100, tol: float
                            [complex(a, b) for a, b in zip(en[:k], ei[:k])], list(rn[:k]))
     return SolveResult(st, k, bool(rep.converged), rep.switched_at, rep.energy, rep.rnorm, list(en[:k]),
                        list(rn[:k]))
+
+
+def cc_solve_batched_workspace_bytes(plans, diis_max: int = 8) -> int:
+    arr = (c_void_p * len(plans))(*[p.handle for p in plans])
+    o = _solve_opts(100, 1e-8, diis_max, 0, None, 0.0, 0)
+    n = c_size_t()
+    _check(_lib.cc_solve_batched_workspace_bytes(len(plans), arr, ctypes.byref(o), ctypes.byref(n)),
+           "cc_solve_batched_workspace_bytes")
+    return n.value
+
+
+def cc_solve_batched(plans, ints, amps, ws, max_iter: int = 100, tol: float = 1e-8, diis_max: int = 8,
+                     stream=None):
+    """Jacobi + DIIS on len(plans) independent systems.  ints: list of integral
+    dicts; amps: list of (t1, t2[, t3]) device tensors (updated in place).
+    Returns (status, [SolveResult per system])."""
+    n = len(plans)
+    parr = (c_void_p * n)(*[p.handle for p in plans])
+    I = (cc_integrals * n)(*[integrals_struct(x) for x in ints])
+    A = (cc_amps * n)(*[cc_amps(_ptr(a[0]), _ptr(a[1]), _ptr(a[2]) if len(a) > 2 else None) for a in amps])
+    o = _solve_opts(max_iter, tol, diis_max, 0, None, 0.0, 0)
+    bufs = [((c_double * max(max_iter, 1))(), (c_double * max(max_iter, 1))(), (c_double * max(max_iter, 1))())
+            for _ in range(n)]
+    reps = (cc_solve_report * n)(*[cc_solve_report(0, 0, -1, 0.0, 0.0, ctypes.cast(b[0], _P(c_double)),
+                                                   ctypes.cast(b[1], _P(c_double)), 0.0,
+                                                   ctypes.cast(b[2], _P(c_double))) for b in bufs])
+    st = _lib.cc_solve_batched(n, parr, I, A, ctypes.byref(o), reps, _ptr(ws), _nbytes(ws), _stream(stream))
+    _check(st, "cc_solve_batched", ok=(0, 7))
+    out = []
+    for p, r, b in zip(plans, reps, bufs):
+        k = r.iterations
+        if p.dtype == CC_C128:
+            out.append(SolveResult(st, k, bool(r.converged), -1, complex(r.energy, r.energy_im), r.rnorm,
+                                   [complex(x, y) for x, y in zip(b[0][:k], b[2][:k])], list(b[1][:k])))
+        else:
+            out.append(SolveResult(st, k, bool(r.converged), -1, r.energy, r.rnorm, list(b[0][:k]), list(b[1][:k])))
+    return st, out
 
 
 BLOCKS = ("oooo", "ooov", "oovv", "ovov", "ovvv", "vvvv")

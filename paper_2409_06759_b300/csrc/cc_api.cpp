@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -642,6 +643,294 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     if (result != CC_OK && g_err.empty()) g_err = "maximum iterations reached";
     return result;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched
+namespace {
+
+struct BatchLayout {
+    std::vector<int64_t> base, pw;      // per system: region start, plan workspace bytes
+    std::vector<SolverLayout> L;
+    int64_t tab = 0, scal = 0, used = 0, bytes = 0;
+};
+
+BatchLayout batch_layout(int n, const cc_plan *plans, int diis) {
+    BatchLayout B;
+    int64_t off = 0;
+    for (int i = 0; i < n; i++) {
+        B.base.push_back(off);
+        const int64_t pw = al(plans[i]->plan.ws_bytes);
+        B.pw.push_back(pw);
+        B.L.push_back(solver_layout(plans[i]->plan, diis));
+        off += pw + al(B.L.back().bytes);
+    }
+    B.tab = off; off += al((int64_t)n * (int64_t)sizeof(BatchSys));
+    B.scal = off; off += al((int64_t)n * 8 * 8);
+    B.used = off; off += al((int64_t)n * 4);
+    B.bytes = off;
+    return B;
+}
+
+// host resources of one batched call, released on every exit path
+struct BatchHost {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    BatchSys *tab = nullptr;
+    double *scal = nullptr;
+    int *used = nullptr, *flags = nullptr;
+    ~BatchHost() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto e : ev) cudaEventDestroy(e);
+        for (auto x : st) cudaStreamDestroy(x);
+        if (tab) cudaFreeHost(tab);
+        if (scal) cudaFreeHost(scal);
+        if (used) cudaFreeHost(used);
+        if (flags) cudaFreeHost(flags);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+cc_status cc_solve_batched_workspace_bytes(int n, const cc_plan *plans, const cc_solve_opts *opts, size_t *bytes) {
+    if (n < 1 || !plans || !bytes) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    for (int i = 0; i < n; i++)
+        if (!plans[i]) return fail(CC_ERR_INVALID_ARG, "NULL plan in the batch");
+    const int diis = opts ? opts->diis_max : 8;
+    if (diis < 0 || diis > 16) return fail(CC_ERR_INVALID_ARG, "diis_max must be in [0, 16]");
+    *bytes = (size_t)batch_layout(n, plans, diis).bytes;
+    return CC_OK;
+}
+
+cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints, cc_amps *amps,
+                           const cc_solve_opts *opts, cc_solve_report *reports, void *ws, size_t ws_bytes,
+                           void *stream) {
+    if (n < 1 || !plans || !ints || !amps) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    cc_solve_opts o{};
+    o.struct_size = sizeof(o);
+    o.max_iter = 100;
+    o.tol = 1e-8;
+    o.diis_max = 8;
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || o.diis_max < 0 || o.diis_max > 16) return fail(CC_ERR_INVALID_ARG, "bad solve options");
+    if (o.refine_plan) return fail(CC_ERR_UNSUPPORTED, "cc_solve_batched takes no refine plan");
+    if (o.resume) return fail(CC_ERR_UNSUPPORTED, "cc_solve_batched does not resume");
+    for (int i = 0; i < n; i++) {
+        if (!plans[i]) return fail(CC_ERR_INVALID_ARG, "NULL plan in the batch");
+        if (!plans[i]->plan.res_used[2]) return fail(CC_ERR_INVALID_ARG, "every plan must write R2");
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) return fail(CC_ERR_INVALID_ARG, "each system needs a plan of its own");
+    }
+    const BatchLayout BL = batch_layout(n, plans, o.diis_max);
+    if ((int64_t)ws_bytes < BL.bytes || !ws || !aligned256(ws))
+        return fail(CC_ERR_WORKSPACE, "batched workspace too small: need " + std::to_string(BL.bytes));
+    cudaStream_t s = (cudaStream_t)stream;
+    char *W = (char *)ws;
+    BatchHost H;
+    CC_CUDA(cudaMallocHost(&H.tab, sizeof(BatchSys) * n));
+    CC_CUDA(cudaMallocHost(&H.scal, sizeof(double) * 8 * n));
+    CC_CUDA(cudaMallocHost(&H.used, sizeof(int) * n));
+    CC_CUDA(cudaMallocHost(&H.flags, sizeof(int) * n));
+    BatchSys *d_tab = (BatchSys *)(W + BL.tab);
+    double *d_scal = (double *)(W + BL.scal);
+    int *d_used = (int *)(W + BL.used);
+    CC_CUDA(cudaMemsetAsync(d_used, 0, sizeof(int) * n, s));
+    CC_CUDA(cudaMemsetAsync(d_scal, 0, sizeof(double) * 8 * n, s));
+
+    // per-system views
+    std::vector<std::array<double *, 4>> r(n), t(n);
+    std::vector<cc_resid> R(n);
+    std::vector<SolverState> S(n);
+    std::vector<int> state(n, 0);        // 0 active, 1 converged, 2 stopped (divergence)
+    std::vector<double> last_e(n, NAN), last_ei(n, NAN), last_rn(n, NAN);
+    std::vector<int> iters(n, 0);
+    for (int i = 0; i < n; i++) {
+        const Plan &P = plans[i]->plan;
+        const SolverLayout &L = BL.L[i];
+        char *sreg = W + BL.base[i] + BL.pw[i];
+        t[i] = {nullptr, (double *)amps[i].t1, (double *)amps[i].t2, (double *)amps[i].t3};
+        for (int l = 0; l < 4; l++) r[i][l] = nullptr;
+        for (int l = 1; l <= 3; l++)
+            if (P.res_used[l]) {
+                r[i][l] = (double *)(sreg + L.r_off[l]);
+                if (!t[i][l]) return fail(CC_ERR_INVALID_ARG, "amplitude buffer missing for a residual the list writes");
+            }
+        R[i] = cc_resid{r[i][1], r[i][2], r[i][3]};
+        plans[i]->cache_filled = false;
+        if (reports) { reports[i].iterations = 0; reports[i].converged = 0; reports[i].switched_at = -1; }
+    }
+    g_err.clear();
+
+    // residual phase of every system: run_residual + energy/norm into d_scal[i]
+    auto residual_phase = [&](bool capture) -> cc_status {
+        for (int i = 0; i < n; i++) {
+            cudaStream_t si = capture ? H.st[i] : s;
+            if (capture) CC_CUDA(cudaStreamWaitEvent(si, H.ev[0], 0));
+            const Plan &P = plans[i]->plan;
+            const SolverLayout &L = BL.L[i];
+            char *sreg = W + BL.base[i] + BL.pw[i];
+            cc_status st = run_residual(plans[i], &ints[i], &amps[i], &R[i], W + BL.base[i], (size_t)BL.pw[i], si,
+                                        true);
+            if (st != CC_OK) return st;
+            double *rr[4] = {nullptr, r[i][1], r[i][2], r[i][3]};
+            st = reduce_energy_norm(P, &ints[i], &amps[i], rr, L.n, (double *)(sreg + L.partials), d_scal + 8 * i, si);
+            if (st != CC_OK) return st;
+            plans[i]->launches += 2 + (rr[1] != nullptr) + (rr[2] != nullptr) + (rr[3] != nullptr);
+            if (capture) {
+                CC_CUDA(cudaEventRecord(H.ev[1 + i], si));
+                CC_CUDA(cudaStreamWaitEvent(s, H.ev[1 + i], 0));
+            }
+        }
+        CC_CUDA(cudaMemcpyAsync(H.scal, d_scal, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(H.used, d_used, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        for (int i = 0; i < n; i++)
+            CC_CUDA(cudaMemcpyAsync(H.flags + i, W + BL.base[i] + plans[i]->plan.flags_off, sizeof(int),
+                                    cudaMemcpyDeviceToHost, s));
+        return CC_OK;
+    };
+
+    // iteration 0 runs directly (it fills the static caches); later ones replay a graph
+    cc_status st = residual_phase(false);
+    if (st != CC_OK) return st;
+    CC_CUDA(cudaStreamSynchronize(s));
+    std::vector<long long> per_replay(n, 0);
+    if (o.max_iter > 1) {
+        H.st.resize(n);
+        for (int i = 0; i < n; i++) CC_CUDA(cudaStreamCreateWithFlags(&H.st[i], cudaStreamNonBlocking));
+        H.ev.resize(n + 1);
+        for (int i = 0; i <= n; i++) CC_CUDA(cudaEventCreateWithFlags(&H.ev[i], cudaEventDisableTiming));
+        std::vector<long long> before(n);
+        for (int i = 0; i < n; i++) before[i] = plans[i]->launches;
+        CC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cc_status cst = cudaEventRecord(H.ev[0], s) == cudaSuccess ? residual_phase(true)
+                                                                   : fail(CC_ERR_CUDA, "event record in capture");
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(s, &g);
+        H.graph = g;
+        if (cst != CC_OK) return cst;
+        if (ce != cudaSuccess) return fail(CC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        CC_CUDA(cudaGraphInstantiate(&H.exec, H.graph, 0));
+        for (int i = 0; i < n; i++) {
+            per_replay[i] = plans[i]->launches - before[i];
+            plans[i]->launches = before[i];
+        }
+    }
+
+    cc_status result = CC_OK;
+    int k = 0;
+    for (k = 0; k < o.max_iter; k++) {
+        if (k > 0) {
+            CC_CUDA(cudaGraphLaunch(H.exec, s));
+            CC_CUDA(cudaStreamSynchronize(s));
+            for (int i = 0; i < n; i++) plans[i]->launches += per_replay[i];
+        }
+        int nact = 0;
+        for (int i = 0; i < n; i++) {
+            BatchSys &b = H.tab[i];
+            std::memset(&b, 0, sizeof(b));
+            if (state[i] != 0) continue;
+            const Plan &P = plans[i]->plan;
+            SolverState &Z = S[i];
+            if (P.flops_mixed > 0 && H.flags[i] != 0)
+                return fail(CC_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired (system " +
+                                                std::to_string(i) + ")");
+            if (Z.pending_m >= 2) {
+                const int keep = H.used[i] == 0 ? 2 : H.used[i];
+                while (Z.nstored > keep) {
+                    for (int q = 0; q + 1 < Z.nstored; q++) Z.order[q] = Z.order[q + 1];
+                    Z.nstored--;
+                }
+                Z.pending_m = 0;
+            }
+            double rr = 0.0;
+            for (int l = 1, c = 2; l <= 3; l++)
+                if (r[i][l]) rr += H.scal[8 * i + c++];
+            const double e = H.scal[8 * i], rn = std::sqrt(rr);
+            last_e[i] = e;
+            last_ei[i] = H.scal[8 * i + 1];
+            last_rn[i] = rn;
+            if (reports && reports[i].energies) reports[i].energies[k] = e;
+            if (reports && reports[i].energies_im) reports[i].energies_im[k] = H.scal[8 * i + 1];
+            if (reports && reports[i].rnorms) reports[i].rnorms[k] = rn;
+            iters[i] = k + 1;
+            if (!std::isfinite(rn) || rn > 1e3 * Z.best) { state[i] = 2; continue; }
+            if (rn < Z.best) Z.best = rn;
+            if (o.tol > 0 && rn < o.tol) { state[i] = 1; continue; }
+            // Jacobi step into a history slot (the same bookkeeping as cc_solve)
+            int slot = 0;
+            if (o.diis_max > 0 && Z.nstored == o.diis_max) {
+                slot = Z.order[0];
+                for (int q = 0; q + 1 < Z.nstored; q++) Z.order[q] = Z.order[q + 1];
+                Z.nstored--;
+            } else if (o.diis_max > 0) {
+                for (;; slot++) {
+                    bool busy = false;
+                    for (int q = 0; q < Z.nstored; q++) busy |= Z.order[q] == slot;
+                    if (!busy) break;
+                }
+            }
+            if (o.diis_max > 0) Z.order[Z.nstored++] = slot;
+            const SolverLayout &L = BL.L[i];
+            char *sreg = W + BL.base[i] + BL.pw[i];
+            b.active = 1;
+            b.o = P.o;
+            b.v = P.v;
+            b.cplx = P.dtype == CC_C128;
+            b.fo = ints[i].f_occ;
+            b.fv = ints[i].f_vir;
+            for (int l = 1; l <= 3; l++) {
+                b.t[l] = r[i][l] ? t[i][l] : nullptr;
+                b.r[l] = r[i][l];
+                b.n[l] = r[i][l] ? L.n[l] : 0;
+            }
+            b.nx = L.nx;
+            b.hx = (double *)(sreg + L.hist_x);
+            b.he = (double *)(sreg + L.hist_e);
+            b.slot = slot;
+            b.nstored = o.diis_max > 0 ? Z.nstored : 0;
+            for (int q = 0; q < 16; q++) b.order[q] = Z.order[q];
+            b.gram = (double *)(sreg + L.gram);
+            b.coef = (double *)(sreg + L.coef);
+            b.used = d_used + i;
+            b.partials = (double *)(sreg + L.partials);
+            Z.pending_m = b.nstored;
+            Z.iter++;
+            nact++;
+        }
+        if (nact == 0) { k++; break; }
+        CC_CUDA(cudaMemcpyAsync(d_tab, H.tab, sizeof(BatchSys) * n, cudaMemcpyHostToDevice, s));
+        CC_CUDA(launch_batched_jacobi(d_tab, n, s));
+        CC_CUDA(launch_batched_diis(d_tab, n, s));
+        CC_CUDA(launch_batched_combine(d_tab, n, s));
+        plans[0]->launches += 4;
+    }
+    CC_CUDA(cudaStreamSynchronize(s));
+    int nconv = 0;
+    for (int i = 0; i < n; i++) {
+        nconv += state[i] == 1;
+        if (reports) {
+            reports[i].iterations = iters[i];
+            reports[i].converged = state[i] == 1;
+            reports[i].energy = last_e[i];
+            reports[i].energy_im = last_ei[i];
+            reports[i].rnorm = last_rn[i];
+        }
+    }
+    if (nconv < n) {
+        result = CC_ERR_NOT_CONVERGED;
+        g_err = std::to_string(n - nconv) + " of " + std::to_string(n) + " systems did not converge";
+    }
+    return result;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 cc_status cc_integral_block_elems(int o, int v, size_t elems[6]) {
     if (o < 1 || v < 1 || !elems) return fail(CC_ERR_INVALID_ARG, "bad arguments");

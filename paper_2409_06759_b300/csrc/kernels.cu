@@ -771,14 +771,12 @@ struct Order {
 // DIIS: the bordered system [B 1; 1^T 0][c; l] = [0; 1] with B scaled by
 // 1/max(diag B), Gaussian elimination with partial pivoting; while a pivot is
 // below 1e-14 the oldest vector is dropped and the solve repeated (down to
-// two vectors).  status[0] = number of newest vectors used (0: none usable).
-__global__ void diis_solve_kernel(const double *gram16, Order ord, int m, double *coef, int *status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int used = 0;
+// two vectors).  Returns the number of newest vectors used (0: none usable).
+__device__ int diis_solve_dev(const double *gram16, const int *ord, int m, double *coef) {
     for (int mm = m; mm >= 2; mm--) {
         const int off = m - mm;     // drop the `off` oldest
         const int N = mm + 1;
-        auto G = [&](int r, int c) { return gram16[ord.s[off + r] * 16 + ord.s[off + c]]; };
+        auto G = [&](int r, int c) { return gram16[ord[off + r] * 16 + ord[off + c]]; };
         double Am[17][18];
         double dmax = 0.0;
         for (int k = 0; k < mm; k++) dmax = fmax(dmax, G(k, k));
@@ -812,10 +810,14 @@ __global__ void diis_solve_kernel(const double *gram16, Order ord, int m, double
             x[r] = s / Am[r][r];
         }
         for (int k = 0; k < mm; k++) coef[k] = x[k];
-        used = mm;
-        break;
+        return mm;
     }
-    status[0] = used;
+    return 0;
+}
+
+__global__ void diis_solve_kernel(const double *gram16, Order ord, int m, double *coef, int *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    status[0] = diis_solve_dev(gram16, ord.s, m, coef);
 }
 
 cudaError_t launch_diis_solve(const double *gram16, const int *order_host, int m, double *coef, int *status,
@@ -823,6 +825,109 @@ cudaError_t launch_diis_solve(const double *gram16, const int *order_host, int m
     Order o{};
     for (int k = 0; k < m && k < 16; k++) o.s[k] = order_host[k];
     diis_solve_kernel<<<1, 32, 0, s>>>(gram16, o, m, coef, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched
+// offset of rank l inside a system's x vector
+__device__ __forceinline__ int64_t rank_offset(const BatchSys &b, int l) {
+    int64_t off = 0;
+    for (int q = 1; q < l; q++) off += b.n[q];
+    return off;
+}
+
+__global__ void __launch_bounds__(256) batched_jacobi_kernel(const BatchSys *__restrict__ sys) {
+    const BatchSys &b = sys[blockIdx.y];
+    if (!b.active) return;
+    double *xs = b.hx + (int64_t)b.slot * b.nx, *es = b.he + (int64_t)b.slot * b.nx;
+    for (int l = 1; l <= 3; l++) {
+        if (!b.t[l]) continue;
+        const int64_t off = rank_offset(b, l);
+        int64_t ncol = 1;
+        for (int q = 0; q < l; q++) ncol *= b.v;
+        ncol <<= b.cplx;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b.n[l];
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t row = e / ncol, col = e - row * ncol;
+            const double D = occ_sum(l, b.o, b.fo, row) - vir_sum(l, b.v, b.fv, (uint32_t)(col >> b.cplx));
+            const double q = b.r[l][e] / D;
+            es[off + e] = q;
+            xs[off + e] = b.t[l][e] + q;
+        }
+    }
+}
+
+// block partials of <e_slot | e_order[q]>, q < nstored: partials[q][blockIdx.x]
+__global__ void __launch_bounds__(256) batched_dots_kernel(const BatchSys *__restrict__ sys) {
+    const BatchSys &b = sys[blockIdx.y];
+    if (!b.active) return;
+    const double *es = b.he + (int64_t)b.slot * b.nx;
+    for (int q = 0; q < b.nstored; q++) {
+        const double *eq = b.he + (int64_t)b.order[q] * b.nx;
+        double acc = 0.0;
+        for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < b.nx; e += (int64_t)kBatchBlocks * 256)
+            acc = fma(es[e], eq[e], acc);
+        acc = block_sum(acc);
+        if (threadIdx.x == 0) b.partials[q * kBatchBlocks + blockIdx.x] = acc;
+    }
+}
+
+// one block per system: the Gram row of the new slot, then the DIIS solve
+__global__ void __launch_bounds__(256) batched_gram_solve_kernel(const BatchSys *__restrict__ sys) {
+    const BatchSys &b = sys[blockIdx.x];
+    if (!b.active) return;
+    for (int q = 0; q < b.nstored; q++) {
+        double x = threadIdx.x < kBatchBlocks ? b.partials[q * kBatchBlocks + threadIdx.x] : 0.0;
+        x = block_sum(x);
+        if (threadIdx.x == 0) {
+            b.gram[b.slot * 16 + b.order[q]] = x;
+            b.gram[b.order[q] * 16 + b.slot] = x;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *b.used = b.nstored >= 2 ? diis_solve_dev(b.gram, b.order, b.nstored, b.coef) : 0;
+}
+
+__global__ void __launch_bounds__(256) batched_combine_kernel(const BatchSys *__restrict__ sys) {
+    const BatchSys &b = sys[blockIdx.y];
+    if (!b.active) return;
+    const int m = b.nstored;
+    const int used = m >= 2 ? *b.used : 0;
+    for (int l = 1; l <= 3; l++) {
+        if (!b.t[l]) continue;
+        const int64_t off = rank_offset(b, l);
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b.n[l];
+             e += (int64_t)gridDim.x * blockDim.x) {
+            double x;
+            if (used == 0) {
+                x = b.hx[(int64_t)(m >= 2 ? b.order[m - 1] : b.slot) * b.nx + off + e];
+            } else {
+                x = 0.0;
+                for (int k = 0; k < used; k++) x += b.coef[k] * b.hx[(int64_t)b.order[m - used + k] * b.nx + off + e];
+            }
+            b.t[l][e] = x;
+        }
+    }
+}
+
+cudaError_t launch_batched_jacobi(const BatchSys *sys, int nsys, cudaStream_t s) {
+    if (nsys <= 0) return cudaSuccess;
+    batched_jacobi_kernel<<<dim3(kBatchBlocks, (unsigned)nsys), 256, 0, s>>>(sys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_diis(const BatchSys *sys, int nsys, cudaStream_t s) {
+    if (nsys <= 0) return cudaSuccess;
+    batched_dots_kernel<<<dim3(kBatchBlocks, (unsigned)nsys), 256, 0, s>>>(sys);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batched_gram_solve_kernel<<<(unsigned)nsys, 256, 0, s>>>(sys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_combine(const BatchSys *sys, int nsys, cudaStream_t s) {
+    if (nsys <= 0) return cudaSuccess;
+    batched_combine_kernel<<<dim3(kBatchBlocks, (unsigned)nsys), 256, 0, s>>>(sys);
     return cudaGetLastError();
 }
 

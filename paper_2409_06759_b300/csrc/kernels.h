@@ -154,4 +154,33 @@ cudaError_t launch_gram_scatter(const double *partials, int count, const int *a_
 cudaError_t launch_combine(const double *const *xs_host, const double *coef, const int *used_dev, int m, int64_t n,
                            double *x, cudaStream_t s);
 
+// ---- batched Jacobi + DIIS (many independent systems, one launch per kernel)
+// One system of a batched iteration; the host rewrites the table every
+// iteration (one copy) and the four kernels below read it on the device.
+constexpr int kBatchBlocks = 64;    // blocks per system of the batched kernels
+struct BatchSys {
+    int active;                // 0: converged or stopped (the kernels skip it)
+    int o, v, cplx;
+    const double *fo, *fv;
+    double *t[4], *r[4];       // amplitudes and residuals by rank (NULL: absent)
+    int64_t n[4];              // doubles per rank
+    int64_t nx;                // doubles of x (the ranks concatenated)
+    double *hx, *he;           // DIIS history (x', e) slots of nx doubles
+    int slot;                  // the slot this iteration's Jacobi step writes
+    int nstored;               // stored slots after this step (order[] oldest first)
+    int order[16];
+    double *gram;              // [16][16] by slot
+    double *coef;              // [16]
+    int *used;                 // newest vectors the DIIS solve used (0: none)
+    double *partials;          // [16][kBatchBlocks]
+};
+// x'_slot = t + R/D, e_slot = R/D for every active system
+cudaError_t launch_batched_jacobi(const BatchSys *sys, int nsys, cudaStream_t s);
+// <e_slot | e_order[q]> for q < nstored, reduced into gram; the DIIS solve when
+// nstored >= 2 (coef, used); deterministic fixed-grid reductions
+cudaError_t launch_batched_diis(const BatchSys *sys, int nsys, cudaStream_t s);
+// t = sum_k coef_k x'_order[nstored-used+k] (used == 0: the newest x'), or the
+// new x' when fewer than two are stored
+cudaError_t launch_batched_combine(const BatchSys *sys, int nsys, cudaStream_t s);
+
 }  // namespace ccb

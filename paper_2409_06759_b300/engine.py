@@ -9,8 +9,8 @@ from __future__ import annotations
 import torch
 
 from . import (BLOCKS, CC_C128, CC_F64, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
-               cc_integral_block_elems, cc_plan_create, cc_residual, cc_solve, cc_solve_workspace_bytes,
-               load_list)
+               cc_integral_block_elems, cc_plan_create, cc_residual, cc_solve, cc_solve_batched,
+               cc_solve_batched_workspace_bytes, cc_solve_workspace_bytes, load_list)
 
 
 def alloc_ws(nbytes: int, device) -> torch.Tensor:
@@ -112,3 +112,18 @@ class Solver:
                         diis_max=self.diis_max, resume=resume,
                         refine_plan=self.refine.plan if self.refine else None, switch_tol=switch_tol,
                         verbose=verbose, stream=stream, t3=t3)
+
+
+class BatchSolver:
+    """cc_solve_batched over several engines (one system each), one workspace."""
+
+    def __init__(self, engines, diis_max: int = 8):
+        self.engines, self.diis_max = list(engines), diis_max
+        nb = cc_solve_batched_workspace_bytes([e.plan for e in self.engines], diis_max)
+        self.ws = alloc_ws(nb, self.engines[0].sys.device)
+
+    def solve(self, amps, max_iter=100, tol=1e-8, stream=None):
+        """amps: list of (t1, t2[, t3]) per engine, updated in place.
+        Returns (status, [SolveResult])."""
+        return cc_solve_batched([e.plan for e in self.engines], [e.sys.ints() for e in self.engines], amps,
+                                self.ws, max_iter=max_iter, tol=tol, diis_max=self.diis_max, stream=stream)

@@ -141,3 +141,15 @@ def test_complex_split_route_doubles_k(cc):
     assert g["flops"] == 8.0 * o * o * v ** 4
     small = "a" if g["M"] == 2 * o * o else "b"
     assert g["cplx_" + small] == 2 and g["cplx_" + ("b" if small == "a" else "a")] == 1
+
+
+def test_batched_argument_checks(cc):
+    """cc_solve_batched validates before any device work: one plan per system."""
+    p = cc.cc_plan_create(cc.load_list("ccsd"), 3, 5)
+    q = cc.cc_plan_create(cc.load_list("ccsd"), 4, 6)
+    n1 = cc.cc_solve_batched_workspace_bytes([p])
+    n2 = cc.cc_solve_batched_workspace_bytes([p, q])
+    assert 0 < n1 < n2
+    with pytest.raises(cc.CCError) as ei:
+        cc.cc_solve_batched([p, p], [{}, {}], [(None, None), (None, None)], None)
+    assert "plan of its own" in str(ei.value)
