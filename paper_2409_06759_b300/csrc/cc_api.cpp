@@ -678,6 +678,8 @@ struct BatchHost {
     std::vector<cudaEvent_t> ev;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t main = nullptr;
+    cudaEvent_t sync_ev = nullptr;
     BatchSys *tab = nullptr;
     double *scal = nullptr;
     int *used = nullptr, *flags = nullptr;
@@ -686,6 +688,8 @@ struct BatchHost {
         if (graph) cudaGraphDestroy(graph);
         for (auto e : ev) cudaEventDestroy(e);
         for (auto x : st) cudaStreamDestroy(x);
+        if (sync_ev) cudaEventDestroy(sync_ev);
+        if (main) cudaStreamDestroy(main);
         if (tab) cudaFreeHost(tab);
         if (scal) cudaFreeHost(scal);
         if (used) cudaFreeHost(used);
@@ -729,9 +733,16 @@ cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints
     const BatchLayout BL = batch_layout(n, plans, o.diis_max);
     if ((int64_t)ws_bytes < BL.bytes || !ws || !aligned256(ws))
         return fail(CC_ERR_WORKSPACE, "batched workspace too small: need " + std::to_string(BL.bytes));
-    cudaStream_t s = (cudaStream_t)stream;
     char *W = (char *)ws;
     BatchHost H;
+    // the work runs on a stream of its own (capturable even when the caller
+    // passes the legacy default stream), ordered after and before the caller's
+    cudaStream_t user = (cudaStream_t)stream;
+    CC_CUDA(cudaStreamCreateWithFlags(&H.main, cudaStreamNonBlocking));
+    CC_CUDA(cudaEventCreateWithFlags(&H.sync_ev, cudaEventDisableTiming));
+    CC_CUDA(cudaEventRecord(H.sync_ev, user));
+    CC_CUDA(cudaStreamWaitEvent(H.main, H.sync_ev, 0));
+    cudaStream_t s = H.main;
     CC_CUDA(cudaMallocHost(&H.tab, sizeof(BatchSys) * n));
     CC_CUDA(cudaMallocHost(&H.scal, sizeof(double) * 8 * n));
     CC_CUDA(cudaMallocHost(&H.used, sizeof(int) * n));
@@ -910,6 +921,8 @@ cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints
         plans[0]->launches += 4;
     }
     CC_CUDA(cudaStreamSynchronize(s));
+    CC_CUDA(cudaEventRecord(H.sync_ev, s));
+    CC_CUDA(cudaStreamWaitEvent(user, H.sync_ev, 0));
     int nconv = 0;
     for (int i = 0; i < n; i++) {
         nconv += state[i] == 1;
