@@ -6,7 +6,7 @@ cc_solve: the full residual (every statement of the contraction list), the
 energy, |R|, the Jacobi update and the DIIS extrapolation.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
-                  [--dtype f64|c128]
+                  [--dtype f64|c128] [--workload ccsd|ccsdt|batched]
 
 --dtype c128 runs the same workload with complex spin orbitals (complex
 Hermitian integrals, complex amplitudes; every complex product is four real
@@ -206,6 +206,217 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+WORKLOAD_T = "spin-orbital CCSDT o=8 v=64 L=96 seed=0, FP64 real, synthetic integrals, generated list"
+
+
+def run_ccsdt(args, world, rank, local):
+    """CCSDT workload: s/iter of the FP64 and split-bf16 plans of the generated
+    list, the o^3 v^5 terms timed separately, time to |R| < 1e-7."""
+    import numpy as np
+    import torch
+
+    import ccinputs
+    import paper_2409_06759_b300 as cc
+    from paper_2409_06759_b300.engine import DeviceSystem, Engine, Solver
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = dict(ccinputs.CONFIG_CCSDT)
+    o, v = cfg["o"], cfg["v"]
+    pk, pk_kind = peaks()
+    text = cc.load_list("ccsdt")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        sm = ccinputs.make_system(**cfg)
+        a1, a2, a3 = ccinputs.random_amplitudes(o, v, seed=0, scale1=0.01, scale2=0.01, triples=True)
+        idx = np.array([[0, 1, 2, 0, 1, 2], [1, 3, 5, 2, 7, 9], [o - 1, o - 2, o - 3, v - 1, v - 2, v - 3]])
+        flops = cc.cc_plan_create(text, o, v).flops
+        t0 = time.perf_counter()
+        oracle.cc_definition_elements(o, v, sm.B, sm.eps, a1, a2, a3, rank=3, idx=idx)
+        dt = time.perf_counter() - t0
+        share = len(idx) / float(o ** 3 * v ** 3)
+        cpu = {"value": flops * share / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{len(idx)} R3 elements of the o={o} v={v} CCSDT residual by the definition oracle "
+                         "(CI coefficients of exp(T) Phi_0, Slater-Condon); value = residual flops x "
+                         f"{len(idx)}/(o^3 v^3) / time"}
+    sysm = ccinputs.make_system(**cfg)
+    dsys = DeviceSystem.from_system(sysm, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    z = lambda: [torch.zeros(*sh, dtype=torch.float64, device=dev) for sh in
+                 ((o, v), (o, o, v, v), (o, o, o, v, v, v))]
+    plans = {"fp64": Engine(dsys, list_text=text), args.precision: Engine(dsys, list_text=text,
+                                                                          precision=args.precision)}
+    out = {}
+    for name, eng in plans.items():
+        t1, t2, t3 = z()
+        sol = Solver(eng)
+        sol.solve(t1, t2, t3=t3, max_iter=args.warmup, tol=0.0, stream=stream)
+        cc.cc_plan_profile_enable(eng.plan, True)
+        n0 = cc.cc_plan_launch_count(eng.plan)
+        torch.cuda.synchronize()
+        barrier(world)
+        with Clocks(local) as clk:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sol.solve(t1, t2, t3=t3, max_iter=args.steps, tol=0.0, resume=True, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        dt = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+        ms_step, ms_kernel, calls = cc.cc_plan_profile_read(eng.plan)
+        cc.cc_plan_profile_enable(eng.plan, False)
+        desc = eng.plan.describe()
+        steps = desc["steps"]
+        # the o^3 v^5 terms: the GEMM steps of that size and their statements' epilogues
+        big = {s_["stmt"] for s_ in steps if s_["kind"].startswith("gemm") and s_.get("flops", 0) >= o ** 3 * v ** 5}
+        t_big = sum(ms_step[k] for k, s_ in enumerate(steps) if s_["stmt"] in big) / calls / 1e3
+        k_dom = max(range(len(ms_kernel)), key=lambda k: ms_kernel[k])
+        st = steps[k_dom]
+        t_k = ms_kernel[k_dom] / calls / 1e3
+        out[name] = {"s_per_iter": dt / args.steps, "tflops": world * eng.plan.flops * args.steps / dt / 1e12,
+                     "o3v5_s_per_iter": t_big, "o3v5_statements": len(big),
+                     "launches": cc.cc_plan_launch_count(eng.plan) - n0,
+                     "dominant": {"kernel": st["note"], "kind": st["kind"], "ms_per_launch": t_k * 1e3,
+                                  "fp64_equiv_tflops": st.get("flops", 0) / t_k / 1e12,
+                                  "shape": [st.get("M"), st.get("N"), st.get("K")]},
+                     "clocks": clk.summary()}
+        if st["kind"] == "gemm_bf16split":
+            ach = st["products"] * 2.0 * st["M"] * st["N"] * st["K"] / t_k / 1e12
+            out[name]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"],
+                                     "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops"], "traffic": None,
+                                     "kernel": "tc_gemm (" + st["note"] + ")",
+                                     "peak_kind": f"{pk_kind} bf16 burst"}
+        del sol, t1, t2, t3
+        torch.cuda.empty_cache()
+    # time to |R| < 1e-7: FP64 alone, and the accurate split route with FP64 defect correction
+    tts = {}
+    if not args.no_tts:
+        acc = Engine(dsys, list_text=text, precision="bf16x6")
+        for name, eng, ref in (("fp64", plans["fp64"], None), ("bf16x6_refined", acc, plans["fp64"])):
+            t1, t2, t3 = z()
+            sol = Solver(eng, refine=ref)
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            r = sol.solve(t1, t2, t3=t3, max_iter=80, tol=1e-7, stream=stream,
+                          switch_tol=1e-6 if ref is not None else 0.0)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            tts[name] = {"s": g0.elapsed_time(g1) / 1e3, "iterations": r.iterations, "energy": r.energy,
+                         "converged": r.converged}
+            del sol, t1, t2, t3
+            torch.cuda.empty_cache()
+        tts["speedup"] = tts["fp64"]["s"] / tts["bf16x6_refined"]["s"]
+        tts["delta_E"] = abs(tts["fp64"]["energy"] - tts["bf16x6_refined"]["energy"])
+    m = out[args.precision]
+    line = {"metric": METRIC, "value": m["tflops"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["s_per_iter"] * 1e3, "s_per_iter": m["s_per_iter"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"{args.precision}: bf16 tensor-core products, fp32 accumulation, fp64 outputs/energy/DIIS",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_T, "precision": args.precision, "list": "ccsdt (generated)",
+                       "flops_per_iter": plans["fp64"].plan.flops, "replicas": world,
+                       "l2": "inputs larger than L2 (T3 1.07 GB)"},
+            "roofline": m.get("roofline"), "gpu_launches": m["launches"], "clocks": m["clocks"],
+            "plans": out, "tts": tts}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+WORKLOAD_B = "batched CCSD: 64 systems, o ~ U[4,16], v ~ U[20,80], L=120, sub-seeds 0..63, FP64 real, synthetic"
+
+
+def run_batched(args, world, rank, local):
+    """64 independent CCSD systems of uneven size solved together
+    (cc_solve_batched) to |R| < 1e-8: aggregate TFLOP/s of the FP64 and the
+    split-bf16 plans, per-system |dE| between them, and the same systems solved
+    one after another for comparison."""
+    import torch
+
+    import ccinputs
+    import paper_2409_06759_b300 as cc
+    from paper_2409_06759_b300.engine import BatchSolver, DeviceSystem, Engine, Solver
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = ccinputs.batched_sizes(64, seed=0)
+    sysl = [ccinputs.make_system(o, v, L=120, seed=sd) for o, v, sd in sizes]
+    dsys = [DeviceSystem.from_system(s, device=dev) for s in sysl]
+    stream = torch.cuda.current_stream(dev)
+    zeros = lambda s: (torch.zeros(s.o, s.v, dtype=torch.float64, device=dev),
+                       torch.zeros(s.o, s.o, s.v, s.v, dtype=torch.float64, device=dev))
+    out = {}
+    K = max(args.steps, 2) * 2
+
+    def timed(solver, iters, tol):
+        amps = [zeros(s) for s in sysl]
+        torch.cuda.synchronize()
+        barrier(world)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        st, res = solver.solve(amps, max_iter=iters, tol=tol, stream=stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(g0.elapsed_time(g1) / 1e3, world), res
+
+    with Clocks(local) as clk:
+        for name, lst, prec in (("fp64", "ccsd", "fp64"), ("bf16x3", "ccsd_vvvv", "bf16x3"),
+                                ("bf16x6", "ccsd_vvvv", "bf16x6")):
+            engs = [Engine(d, list_name=lst, precision=prec) for d in dsys]
+            flops = [e.plan.flops for e in engs]
+            solver = BatchSolver(engs)
+            timed(solver, 2, 0.0)                          # warm-up
+            # steady state: (2 + K) minus 2 iterations, each system's own iteration counts
+            n0 = sum(cc.cc_plan_launch_count(e.plan) for e in engs)
+            ta, ra = timed(solver, 2, 0.0)
+            n1 = sum(cc.cc_plan_launch_count(e.plan) for e in engs)
+            tb, rb = timed(solver, 2 + K, 0.0)
+            n2 = sum(cc.cc_plan_launch_count(e.plan) for e in engs)
+            work = sum(f * (b.iterations - a.iterations) for f, a, b in zip(flops, ra, rb))
+            steady = (tb - ta)
+            # the whole solve to |R| < 1e-8 (setup included: static caches, graph capture)
+            tts, res = timed(solver, 60, 1e-8)
+            out[name] = {"steady_s_per_iter": steady / K, "steady_tflops": world * work / steady / 1e12,
+                         "steady_launches_per_iter": ((n2 - n1) - (n1 - n0)) / K,
+                         "solve_s": tts, "solve_tflops": world * sum(f * r.iterations for f, r in zip(flops, res))
+                         / tts / 1e12, "converged": sum(r.converged for r in res),
+                         "iterations": [r.iterations for r in res], "energies": [r.energy for r in res]}
+            del solver, engs
+            torch.cuda.empty_cache()
+        # the FP64 systems one after another (single-system cc_solve), for comparison
+        t_seq = 0.0
+        for d, s in zip(dsys, sysl):
+            e = Engine(d, list_name="ccsd")
+            a1, a2 = zeros(s)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            Solver(e).solve(a1, a2, max_iter=60, tol=1e-8, stream=stream)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            t_seq += g0.elapsed_time(g1) / 1e3
+    ef = out["fp64"]["energies"]
+    for name in ("bf16x3", "bf16x6"):
+        out[name]["max_abs_dE_vs_fp64"] = max(abs(a - b) for a, b in zip(out[name]["energies"], ef))
+    for v_ in out.values():
+        del v_["energies"]
+    m = out["bf16x3"]
+    line = {"metric": METRIC, "value": m["steady_tflops"], "unit": "TFLOP/s", "n_gpus": world, "steps": K,
+            "warmup": 2, "ms_per_step": m["steady_s_per_iter"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "bf16x3: bf16 tensor-core products, fp32 accumulation, fp64 outputs/energy/DIIS",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_B, "step": "one batched iteration of all 64 systems (graph replay + "
+                       "batched updates); steady state = (2+K)-iteration call minus 2-iteration call",
+                       "systems": len(sizes), "sizes": [[o, v] for o, v, _ in sizes]},
+            "roofline": None, "gpu_launches": int(m["steady_launches_per_iter"] * K), "clocks": clk.summary(),
+            "variants": out, "fp64_sequential_solve_s": t_seq,
+            "batching_speedup_fp64_solve": t_seq / out["fp64"]["solve_s"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,10 +429,18 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ref-samples", type=int, default=2)
     ap.add_argument("--dtype", default="f64", choices=["f64", "c128"])
+    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "ccsdt", "batched"],
+                    help="ccsdt: the o=8 v=64 CCSDT workload (generated list); batched: 64 uneven CCSD systems")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload in ("ccsdt", "batched"):
+        (run_ccsdt if args.workload == "ccsdt" else run_batched)(args, world, rank, local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
 
     import torch

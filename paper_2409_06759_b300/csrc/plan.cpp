@@ -663,6 +663,11 @@ struct Planner {
                             std::max(Mx, Nx) >= 4096 && std::max(Mx, Nx) <= 0xffffffffLL;
         bool use_f32 = false;
         bool use_rows = narrow;
+        // bf16x3 plans carry ~2^-16 relative error on their bulk contractions:
+        // the contractions below the tensor-route size run in FP32 arithmetic
+        // there (the SIMT FP32 rate, ~60x the FP64 pipe); bf16x6 and FP64 plans
+        // keep FP64 for them
+        if (!use_mixed && !mixed_all && plan.precision == 2 && !cplx && Mx > 1 && Nx > 1 && Kx > 1) use_f32 = true;
         if (use_mixed && !mixed_all) {
             const int64_t bn = Nx <= 64 ? 64 : Nx <= 128 ? 128 : 256;
             const double eff = (double)Mx * (double)Nx * (double)Kx /
