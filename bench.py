@@ -366,6 +366,11 @@ def run_batched(args, world, rank, local):
                                 ("bf16x6", "ccsd_vvvv", "bf16x6")):
             engs = [Engine(d, list_name=lst, precision=prec) for d in dsys]
             flops = [e.plan.flops for e in engs]
+            t_tune = time.perf_counter()
+            for e_, s_ in zip(engs, sysl):                 # tile widths and split-K picked by timing
+                e_.autotune(*zeros(s_), reps=2, stream=stream)
+                e_.release()
+            t_tune = time.perf_counter() - t_tune
             solver = BatchSolver(engs)
             timed(solver, 2, 0.0)                          # warm-up
             # steady state: (2 + K) minus 2 iterations, each system's own iteration counts
@@ -382,7 +387,8 @@ def run_batched(args, world, rank, local):
                          "steady_launches_per_iter": ((n2 - n1) - (n1 - n0)) / K,
                          "solve_s": tts, "solve_tflops": world * sum(f * r.iterations for f, r in zip(flops, res))
                          / tts / 1e12, "converged": sum(r.converged for r in res),
-                         "iterations": [r.iterations for r in res], "energies": [r.energy for r in res]}
+                         "iterations": [r.iterations for r in res], "energies": [r.energy for r in res],
+                         "autotune_s": t_tune}
             del solver, engs
             torch.cuda.empty_cache()
         # the FP64 systems one after another (single-system cc_solve), for comparison

@@ -169,6 +169,19 @@ CC_API cc_status cc_plan_launch_count(cc_plan plan, long long *count);
 CC_API cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res,
                              void *ws, size_t ws_bytes, void *stream);
 
+/* cc_plan_autotune -- picks, for every contraction of the plan, the GEMM
+ * configuration (tensor-core tile width 64/128/256 and split-K factor on the
+ * split-bf16 route; split-K factor on the FP64/FP32 tiled route) that runs
+ * fastest on this device for these inputs: each candidate the plan prepared
+ * room for is timed reps times (CUDA events, minimum taken) in place of the
+ * planned one, the steps running in list order so every operand is real.
+ * Results stay in the plan (cc_plan_describe reports "tuned").  The paper has
+ * no counterpart (its contractions run in ExaTENSOR).
+ *   ints, amps, ws: as for cc_residual.  res: receives unspecified values.
+ *   reps: 1..100 timings per candidate.  Synchronises the stream. */
+CC_API cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res,
+                                  void *ws, size_t ws_bytes, void *stream, int reps);
+
 /* cc_energy -- E_CC - E_ref = 1/4 sum <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b
  * (f_ia = 0).  e_dev: device double[2] receiving (Re E, Im E) (Im E = 0 for
  * CC_F64).  Uses the first 10 KiB of ws as scratch. */

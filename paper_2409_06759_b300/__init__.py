@@ -32,7 +32,8 @@ EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_
            "cc_plan_profile_enable", "cc_plan_profile_read", "cc_plan_launch_count",
            "cc_residual", "cc_energy", "cc_solve_workspace_bytes", "cc_solve", "cc_integral_block_elems",
            "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_status_string",
-           "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched"]
+           "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched",
+           "cc_plan_autotune"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libccb300.so is not built ({LIB_PATH}); run paper_2409_06759_b300/build.py "
@@ -94,6 +95,8 @@ _sig = {
     "cc_solve_batched_workspace_bytes": (c_int, [c_int, _P(c_void_p), _P(cc_solve_opts), _P(c_size_t)]),
     "cc_solve_batched": (c_int, [c_int, _P(c_void_p), _P(cc_integrals), _P(cc_amps), _P(cc_solve_opts),
                                  _P(cc_solve_report), c_void_p, c_size_t, c_void_p]),
+    "cc_plan_autotune": (c_int, [c_void_p, _P(cc_integrals), _P(cc_amps), _P(cc_resid), c_void_p, c_size_t, c_void_p,
+                                 c_int]),
     "cc_status_string": (ctypes.c_char_p, [c_int]),
     "cc_last_error": (ctypes.c_char_p, []),
     "cc_version": (ctypes.c_char_p, []),
@@ -243,6 +246,16 @@ def cc_residual(plan: Plan, ints: dict, t1, t2, r1, r2, ws, stream=None, t3=None
     R = cc_resid(_ptr(r1), _ptr(r2), _ptr(r3))
     _check(_lib.cc_residual(plan.handle, ctypes.byref(I), ctypes.byref(A), ctypes.byref(R), _ptr(ws), _nbytes(ws),
                             _stream(stream)), "cc_residual")
+
+
+def cc_plan_autotune(plan: Plan, ints: dict, t1, t2, r1, r2, ws, reps: int = 3, stream=None, t3=None, r3=None):
+    """Times the GEMM candidates of every contraction and keeps the fastest
+    (the residual buffers receive unspecified values)."""
+    I = integrals_struct(ints)
+    A = cc_amps(_ptr(t1), _ptr(t2), _ptr(t3))
+    R = cc_resid(_ptr(r1), _ptr(r2), _ptr(r3))
+    _check(_lib.cc_plan_autotune(plan.handle, ctypes.byref(I), ctypes.byref(A), ctypes.byref(R), _ptr(ws),
+                                 _nbytes(ws), _stream(stream), reps), "cc_plan_autotune")
 
 
 def cc_energy(plan: Plan, ints: dict, t1, t2, e_dev, ws, stream=None):

@@ -130,6 +130,55 @@ cc_status harvest_profile(cc_plan_s *pl) {
     return CC_OK;
 }
 
+// One step of a plan.  splits: run the operand splits of a split-bf16 GEMM
+// (false re-runs only its GEMM, for autotuning).  mark: event recorded after
+// the splits, just before the GEMM kernel (profiling), or NULL.
+cc_status exec_step(cc_plan_s *pl, const Step &stp, const cc_integrals *I, const cc_amps *A, const cc_resid *R,
+                    char *w, cudaStream_t s, bool splits, cudaEvent_t mark) {
+    const Plan &P = pl->plan;
+    switch (stp.kind) {
+        case StepKind::ZERO:
+            CC_CUDA(launch_zero(resolve(stp.out, I, A, R, w), stp.zero_elems, s));
+            pl->launches++;
+            break;
+        case StepKind::ACCUM:
+            if (!(stp.static_src && pl->cache_filled)) {
+                CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s,
+                                     stp.acc.two_src ? resolve(stp.b, I, A, R, w) : nullptr));
+                pl->launches++;
+            }
+            break;
+        case StepKind::GEMM:
+            if (stp.rows) {
+                if (mark) CC_CUDA(cudaEventRecord(mark, s));
+                CC_CUDA(launch_rows_gemm(stp.rg, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
+                                         resolve(stp.out, I, A, R, w), s));
+                pl->launches++;
+            } else if (!stp.mixed) {
+                if (mark) CC_CUDA(cudaEventRecord(mark, s));
+                CC_CUDA(launch_gemm_f64(stp.gemm, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
+                                        resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w), s));
+                pl->launches += stp.gemm.splitk > 1 ? 2 : 1;
+            } else {
+                void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
+                if (splits && !(stp.a_static && pl->cache_filled) && !stp.skip_a) {
+                    CC_CUDA(launch_split_bf16(stp.split_a, resolve(stp.a, I, A, R, w), pa, s));
+                    pl->launches++;
+                }
+                if (splits && !(stp.b_static && pl->cache_filled) && !stp.skip_b) {
+                    CC_CUDA(launch_split_bf16(stp.split_b, resolve(stp.b, I, A, R, w), pb, s));
+                    pl->launches++;
+                }
+                if (mark) CC_CUDA(cudaEventRecord(mark, s));
+                CC_CUDA(launch_tc_gemm(stp.tc, pa, pb, resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w),
+                                       (int *)(w + P.flags_off), s));
+                pl->launches += stp.tc.splitk > 1 ? 2 : 1;
+            }
+            break;
+    }
+    return CC_OK;
+}
+
 cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, const cc_resid *R, void *ws,
                        size_t wsb, cudaStream_t s, bool use_cache) {
     const Plan &P = pl->plan;
@@ -147,46 +196,8 @@ cc_status run_residual(cc_plan_s *pl, const cc_integrals *I, const cc_amps *A, c
         CC_CUDA(cudaMemsetAsync(w + P.flags_off, 0, sizeof(int), s));
     for (const Step &stp : P.steps) {
         if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si], s));
-        switch (stp.kind) {
-            case StepKind::ZERO:
-                CC_CUDA(launch_zero(resolve(stp.out, I, A, R, w), stp.zero_elems, s));
-                pl->launches++;
-                break;
-            case StepKind::ACCUM:
-                if (!(stp.static_src && pl->cache_filled)) {
-                    CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s,
-                                         stp.acc.two_src ? resolve(stp.b, I, A, R, w) : nullptr));
-                    pl->launches++;
-                }
-                break;
-            case StepKind::GEMM:
-                if (stp.rows) {
-                    if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
-                    CC_CUDA(launch_rows_gemm(stp.rg, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
-                                             resolve(stp.out, I, A, R, w), s));
-                    pl->launches++;
-                } else if (!stp.mixed) {
-                    if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
-                    CC_CUDA(launch_gemm_f64(stp.gemm, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
-                                            resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w), s));
-                    pl->launches += stp.gemm.splitk > 1 ? 2 : 1;
-                } else {
-                    void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
-                    if (!(stp.a_static && pl->cache_filled) && !stp.skip_a) {
-                        CC_CUDA(launch_split_bf16(stp.split_a, resolve(stp.a, I, A, R, w), pa, s));
-                        pl->launches++;
-                    }
-                    if (!(stp.b_static && pl->cache_filled) && !stp.skip_b) {
-                        CC_CUDA(launch_split_bf16(stp.split_b, resolve(stp.b, I, A, R, w), pb, s));
-                        pl->launches++;
-                    }
-                    if (pf.on) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
-                    CC_CUDA(launch_tc_gemm(stp.tc, pa, pb, resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w),
-                                           (int *)(w + P.flags_off), s));
-                    pl->launches += stp.tc.splitk > 1 ? 2 : 1;
-                }
-                break;
-        }
+        st = exec_step(pl, stp, I, A, R, w, s, true, pf.on ? pf.ev[3 * si + 1] : nullptr);
+        if (st != CC_OK) return st;
         if (pf.on) {
             if (stp.kind != StepKind::GEMM) CC_CUDA(cudaEventRecord(pf.ev[3 * si + 1], s));
             CC_CUDA(cudaEventRecord(pf.ev[3 * si + 2], s));
@@ -399,6 +410,69 @@ cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_amps *amp
                       size_t ws_bytes, void *stream) {
     if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
     return run_residual(plan, ints, amps, res, ws, ws_bytes, (cudaStream_t)stream, false);
+}
+
+cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res, void *ws,
+                           size_t ws_bytes, void *stream, int reps) {
+    if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
+    if (plan->prof.on) return fail(CC_ERR_INVALID_ARG, "disable profiling before autotuning");
+    if (reps < 1 || reps > 100) return fail(CC_ERR_INVALID_ARG, "reps must be in [1, 100]");
+    cudaStream_t s = (cudaStream_t)stream;
+    // one full residual first: static caches filled, kernels warm
+    cc_status st = run_residual(plan, ints, amps, res, ws, ws_bytes, s, false);
+    if (st != CC_OK) return st;
+    plan->cache_filled = true;
+    Plan &P = plan->plan;
+    char *w = (char *)ws;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CC_CUDA(cudaEventCreate(&e0));
+    CC_CUDA(cudaEventCreate(&e1));
+    cc_status result = CC_OK;
+    for (Step &stp : P.steps) {
+        // the step once as planned (its operands are then in place), then every candidate
+        st = exec_step(plan, stp, ints, amps, res, w, s, true, nullptr);
+        if (st != CC_OK) { result = st; break; }
+        if (stp.cands.size() < 2) continue;
+        double best = 1e30;
+        std::array<int, 2> pick = stp.cands[0];
+        for (const auto &c : stp.cands) {
+            Step trial = stp;
+            if (trial.mixed) {
+                trial.tc.bn = c[0];
+                trial.tc.splitk = c[1];
+            } else {
+                trial.gemm.splitk = c[1];
+            }
+            float ms = 0.f, acc = 0.f;
+            for (int r = 0; r < reps; r++) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) { result = fail(CC_ERR_CUDA, "event record"); break; }
+                st = exec_step(plan, trial, ints, amps, res, w, s, false, nullptr);
+                if (st != CC_OK) { result = st; break; }
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    result = fail(CC_ERR_CUDA, "event timing");
+                    break;
+                }
+                acc = r == 0 ? ms : std::min(acc, ms);
+            }
+            if (result != CC_OK) break;
+            if (acc < best) { best = acc; pick = c; }
+        }
+        if (result != CC_OK) break;
+        if (stp.mixed) {
+            stp.tc.bn = pick[0];
+            stp.tc.splitk = pick[1];
+        } else {
+            stp.gemm.splitk = pick[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result == CC_OK) {
+        P.tuned = true;
+        plan->cache_filled = false;
+    }
+    return result;
 }
 
 cc_status cc_energy(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, double *e_dev, void *ws,

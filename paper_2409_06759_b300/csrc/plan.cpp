@@ -784,11 +784,21 @@ struct Planner {
                 int64_t sk = (592 + tiles - 1) / tiles;
                 sk = std::min<int64_t>(sk, g.gemm.K / 128);
                 sk = std::min<int64_t>(sk, 256);
-                if (sk > 1) {
-                    g.gemm.splitk = (int)sk;
-                    g.partials = scratch(sk * g.gemm.M * g.gemm.N * esz);
-                }
+                if (sk > 1) g.gemm.splitk = (int)sk;
             }
+            // autotuning candidates: split-K factors (the partials buffer takes the largest)
+            int64_t skmax = g.gemm.splitk;
+            if (g.gemm.M > 1 && g.gemm.N > 1 && g.gemm.K > 1) {
+                g.cands.push_back({0, 1});
+                for (int sk : {2, 4, 8, 16, 32, 64})
+                    if (sk <= g.gemm.K / 64 && sk * g.gemm.M * g.gemm.N * esz <= (int64_t)512 << 20) {
+                        g.cands.push_back({0, sk});
+                        skmax = std::max<int64_t>(skmax, sk);
+                    }
+                if (g.gemm.splitk > 1) g.cands.push_back({0, g.gemm.splitk});
+                if (g.cands.size() < 2) g.cands.clear();
+            }
+            if (skmax > 1) g.partials = scratch(skmax * g.gemm.M * g.gemm.N * esz);
         }
 
         // output: direct (generalised strides) or scratch + antisymmetrising epilogue
@@ -859,19 +869,32 @@ struct Planner {
             t.M = Mr;
             t.N = Nr;
             t.bn = Nr <= 64 ? 64 : (Nr <= 128 || np == 3) ? 128 : 256;
+            // planes padded for the widest tile an autotuner may pick (the
+            // kernels run ceil(N / bn) column tiles whatever the padding)
+            const int bn_max = np == 3 ? (Nr <= 64 ? 64 : 128) : (Nr <= 64 ? 64 : Nr <= 128 ? 128 : 256);
             t.Mp = align_up(Mr, 128);
-            t.Np = align_up(Nr, t.bn);
+            t.Np = align_up(Nr, bn_max);
             t.Kp = align_up(Kr, 64);
             // split K when the output tiles cannot fill the 148 SMs
-            const int64_t tiles = (t.Mp / 128) * (t.Np / t.bn), kblocks = t.Kp / 64;
+            const int64_t tiles = (t.Mp / 128) * ((Nr + t.bn - 1) / t.bn), kblocks = t.Kp / 64;
             t.splitk = 1;
             if (tiles < 148 && kblocks >= 8) {
                 int64_t sk = std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
-                if (sk > 1) {
-                    t.splitk = (int)sk;
-                    g.partials = scratch(sk * Mr * Nr * 8);
-                }
+                if (sk > 1) t.splitk = (int)sk;
             }
+            // autotuning candidates: tile width x split-K factor
+            int64_t skmax = t.splitk;
+            for (int bn : {64, 128, 256}) {
+                if (bn > bn_max) continue;
+                for (int sk : {1, 2, 4, 8, 16})
+                    if (sk == 1 || (sk <= kblocks / 4 && sk * Mr * Nr * 8 <= (int64_t)512 << 20)) {
+                        g.cands.push_back({bn, sk});
+                        skmax = std::max<int64_t>(skmax, sk);
+                    }
+                if (bn == t.bn && t.splitk > 16) g.cands.push_back({bn, t.splitk});
+            }
+            if (g.cands.size() < 2) g.cands.clear();
+            if (skmax > 1) g.partials = scratch(skmax * Mr * Nr * 8);
             t.nplanes_a = t.nplanes_b = np;
             if (np == 2) {
                 const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
@@ -1009,7 +1032,7 @@ std::string describe_plan(const Plan &plan) {
        << ",\"workspace_bytes\":" << plan.ws_bytes << ",\"interm_bytes\":" << plan.interm_bytes
        << ",\"scratch_bytes\":" << plan.scratch_bytes << ",\"splits_bytes\":" << plan.splits_bytes
        << ",\"cache_bytes\":" << plan.cache_bytes << ",\"flops\":" << plan.flops
-       << ",\"flops_mixed\":" << plan.flops_mixed << ",\"tensors\":[";
+       << ",\"flops_mixed\":" << plan.flops_mixed << ",\"tuned\":" << (plan.tuned ? 1 : 0) << ",\"tensors\":[";
     for (size_t k = 0; k < plan.tensors.size(); k++) {
         const Tensor &t = plan.tensors[k];
         os << (k ? "," : "") << "{\"name\":\"" << t.name << "\",\"spaces\":\""
@@ -1025,7 +1048,7 @@ std::string describe_plan(const Plan &plan) {
            << "\",\"note\":\"" << s.note << "\"";
         if (s.kind == StepKind::GEMM && !s.mixed) {
             os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
-               << ",\"splitk\":" << s.gemm.splitk
+               << ",\"splitk\":" << s.gemm.splitk << ",\"candidates\":" << s.cands.size()
                << ",\"sAm\":" << s.gemm.sAm << ",\"sAk\":" << s.gemm.sAk << ",\"sBk\":" << s.gemm.sBk
                << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta
                << ",\"conj_a\":" << s.gemm.conj_a << ",\"conj_b\":" << s.gemm.conj_b << ",\"cm\":";
@@ -1037,7 +1060,7 @@ std::string describe_plan(const Plan &plan) {
                << ",\"products\":" << s.tc.nprod << ",\"a_static\":" << (s.a_static ? 1 : 0)
                << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta
                << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp << ",\"bn\":" << s.tc.bn
-               << ",\"splitk\":" << s.tc.splitk
+               << ",\"splitk\":" << s.tc.splitk << ",\"candidates\":" << s.cands.size()
                << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off
                << ",\"reuse_a\":" << (s.skip_a ? 1 : 0) << ",\"reuse_b\":" << (s.skip_b ? 1 : 0)
                << ",\"cplx_a\":" << s.split_a.cplx << ",\"cplx_b\":" << s.split_b.cplx

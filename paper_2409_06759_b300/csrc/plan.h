@@ -7,6 +7,7 @@
 //   permutes of the operands into GEMM-ready layout (TTGT, Sec. I C),
 //   one GEMM, and an antisymmetrising epilogue when P(..) operators are present.
 #pragma once
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -62,6 +63,7 @@ struct Step {
     bool a_static = false, b_static = false;     // operand is an integral block (cacheable)
     bool static_src = false;                     // ACCUM permute of an integral block into the cache
     bool skip_a = false, skip_b = false;         // planes already split by an earlier step (same source version)
+    std::vector<std::array<int, 2>> cands;       // autotuning candidates (tile width or 0, split-K)
     bool rows = false;                           // narrow GEMM (one thread per row, operands in place)
     RowsGemmDesc rg{};
     double flops = 0.0;
@@ -84,6 +86,7 @@ struct Plan {
     int64_t splits_off = 0, splits_bytes = 0; // per-iteration split planes shared between steps
     double flops = 0.0;
     double flops_mixed = 0.0;   // flops of steps on the split-bf16 route (fp64-equivalent)
+    bool tuned = false;         // GEMM configurations picked by cc_plan_autotune
     int verbose = 0;
 };
 

@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(192, 1)
     int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = (int)(d.Np / BN);
+    const int n_tiles = (int)((d.N + BN - 1) / BN);   // tiles past N would read padding only
     const int tile = blockIdx.x;
     const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
     const int64_t n0 = (int64_t)(tile % n_tiles) * BN;
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(192, 1)
     int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);   // [BN]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = (int)(d.Np / BN);
+    const int n_tiles = (int)((d.N + BN - 1) / BN);   // tiles past N would read padding only
     const int kb_total = (int)(d.Kp / BK);
     const int64_t total = ntiles * nslices;
 
@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(320, 1)
     int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = (int)(d.Np / BN);
+    const int n_tiles = (int)((d.N + BN - 1) / BN);   // tiles past N would read padding only
     const int tile = blockIdx.x;
     const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
     const int64_t n0 = (int64_t)(tile % n_tiles) * BN;
@@ -907,7 +907,7 @@ static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B,
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
         return cudaErrorInvalidValue;
-    const int64_t tiles = (d.Mp / BM) * (d.Np / BN);
+    const int64_t tiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
     const int kb_total = (int)(d.Kp / BK);
     const int sk = d.splitk > 1 ? d.splitk : 1;
@@ -937,7 +937,7 @@ static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const v
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
         return cudaErrorInvalidValue;
-    const int64_t ntiles = (d.Mp / BM) * (d.Np / BN);
+    const int64_t ntiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     const int kb_total = (int)(d.Kp / BK);
     const int sk = d.splitk > 1 ? d.splitk : 1;
     const int per = (kb_total + sk - 1) / sk;
@@ -966,7 +966,7 @@ static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
         return cudaErrorInvalidValue;
-    const int64_t tiles = (d.Mp / BM) * (d.Np / BN);
+    const int64_t tiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
     const int kb_total = (int)(d.Kp / BK);
     const int sk = d.splitk > 1 ? d.splitk : 1;

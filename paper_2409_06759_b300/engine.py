@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import torch
 
-from . import (BLOCKS, CC_C128, CC_F64, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
+from . import (BLOCKS, CC_C128, CC_F64, cc_plan_autotune, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
                cc_integral_block_elems, cc_plan_create, cc_residual, cc_solve, cc_solve_batched,
                cc_solve_batched_workspace_bytes, cc_solve_workspace_bytes, load_list)
 
@@ -74,6 +74,14 @@ class Engine:
         if self._ws is None:
             self._ws = alloc_ws(max(self.plan.workspace_bytes, 16384), self.sys.device)
         return self._ws
+
+    def autotune(self, t1, t2, reps: int = 3, t3=None, stream=None):
+        """cc_plan_autotune on these amplitudes (scratch residual buffers)."""
+        o, v, dev, dt = self.sys.o, self.sys.v, self.sys.device, self.sys.tdtype
+        r1 = torch.empty(o, v, dtype=dt, device=dev)
+        r2 = torch.empty(o, o, v, v, dtype=dt, device=dev)
+        r3 = torch.empty(o, o, o, v, v, v, dtype=dt, device=dev) if t3 is not None else None
+        cc_plan_autotune(self.plan, self.sys.ints(), t1, t2, r1, r2, self.ws, reps=reps, stream=stream, t3=t3, r3=r3)
 
     def release(self):
         """Drops the workspace (allocated again on the next residual or energy)."""

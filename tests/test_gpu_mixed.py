@@ -148,3 +148,23 @@ def test_narrow_gemm_route(cc, prec, kind, rel):
     e1, e2 = list_exec.run_list(text, o, v, s.eps, oracle_V(o, v, B), t1, t2)
     err = np.abs(r2.cpu().numpy() - e2).max()
     assert err <= rel * np.abs(e2).max(), err
+
+
+@pytest.mark.parametrize("prec,rel", [("fp64", 1e-12), ("bf16x3", 2e-4)])
+def test_autotuned_plan_keeps_the_residual(cc, prec, rel):
+    """cc_plan_autotune changes only tile widths and split-K factors: the
+    residual of the tuned plan matches the oracle like the planned one."""
+    ccm, engine = cc
+    o, v = 10, 40
+    s, B, t1, t2 = small_case(o, v, 31, L=16, scale=6.0, tscale=0.05)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
+    eng = engine.Engine(dsys, list_name="ccsd" if prec == "fp64" else "ccsd_vvvv", precision=prec)
+    T1, T2 = to_dev(t1), to_dev(t2)
+    eng.autotune(T1, T2, reps=2)
+    d = eng.plan.describe()
+    assert d["tuned"] == 1 and any(st.get("candidates", 0) > 1 for st in d["steps"])
+    r1, r2 = eng.residual(T1, T2)
+    torch.cuda.synchronize()
+    o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
+    dd = np.sqrt(np.sum((r1.cpu().numpy() - o1) ** 2) + np.sum((r2.cpu().numpy() - o2) ** 2))
+    assert dd <= rel * np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
