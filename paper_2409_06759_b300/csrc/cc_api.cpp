@@ -148,6 +148,16 @@ cc_status exec_step(cc_plan_s *pl, const Step &stp, const cc_integrals *I, const
                 pl->launches++;
             }
             break;
+        case StepKind::PACK:
+            if (!(stp.static_src && pl->cache_filled)) {
+                CC_CUDA(launch_pack_pairs(stp.pk, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s));
+                pl->launches++;
+            }
+            break;
+        case StepKind::UNPACK:
+            CC_CUDA(launch_unpack_pairs(stp.up, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s));
+            pl->launches++;
+            break;
         case StepKind::GEMM:
             if (stp.rows) {
                 if (mark) CC_CUDA(cudaEventRecord(mark, s));

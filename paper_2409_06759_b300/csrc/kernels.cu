@@ -354,6 +354,73 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
             if (rv[i] && cv[j]) C[ro[i] + co[j]] = axpy(d.beta, old[i][j], scal(d.alpha, up(acc[i][j])));
 }
 
+// ------------------------------------------------------------ packed pairs
+__device__ __forceinline__ int64_t pair_start(int64_t p, int64_t n) { return p * (2 * n - p - 1) / 2; }
+// (p, q), p < q, of the packed index P
+__device__ __forceinline__ void pair_of(int64_t P, int64_t n, int64_t &p, int64_t &q) {
+    const double b = 2.0 * (double)n - 1.0;
+    int64_t x = (int64_t)((b - sqrt(b * b - 8.0 * (double)P)) * 0.5);
+    if (x < 0) x = 0;
+    while (x + 1 < n && pair_start(x + 1, n) <= P) x++;
+    while (x > 0 && pair_start(x, n) > P) x--;
+    p = x;
+    q = P - pair_start(x, n) + x + 1;
+}
+
+__global__ void __launch_bounds__(256) pack_pairs_kernel(const PackDesc d, const double *__restrict__ src,
+                                                         double *__restrict__ dst) {
+    const int64_t total = d.P1 * d.P2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = e / d.P2, J = e - I * d.P2;
+        int64_t p, q, r, u;
+        pair_of(I, d.n1, p, q);
+        pair_of(J, d.n2, r, u);
+        dst[e] = d.scale * __ldg(src + p * d.s0 + q * d.s1 + r * d.s2 + u * d.s3);
+    }
+}
+
+__global__ void __launch_bounds__(256) unpack_pairs_kernel(const UnpackDesc d, const double *__restrict__ C,
+                                                           double *__restrict__ out) {
+    const int64_t total = d.ext[0] * d.ext[1] * d.ext[2] * d.ext[3];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t dig[4], x = e, off = 0;
+        for (int k = 3; k >= 0; k--) {
+            dig[k] = x % d.ext[k];
+            x /= d.ext[k];
+            off += dig[k] * d.ostr[k];
+        }
+        const int64_t a1 = dig[d.da1], a2 = dig[d.da2], b1 = dig[d.db1], b2 = dig[d.db2];
+        double val = 0.0;
+        if (a1 != a2 && b1 != b2) {
+            const int64_t pa = a1 < a2 ? pair_start(a1, d.nA) + a2 - a1 - 1 : pair_start(a2, d.nA) + a1 - a2 - 1;
+            const int64_t pb = b1 < b2 ? pair_start(b1, d.nB) + b2 - b1 - 1 : pair_start(b2, d.nB) + b1 - b2 - 1;
+            val = __ldg(C + pa * d.cA + pb * d.cB);
+            if ((a1 > a2) != (b1 > b2)) val = -val;
+        }
+        double r = d.alpha * val;
+        if (d.beta != 0.0) r = fma(d.beta, out[off], r);
+        out[off] = r;
+    }
+}
+
+cudaError_t launch_pack_pairs(const PackDesc &d, const double *src, double *dst, cudaStream_t s) {
+    const int64_t total = d.P1 * d.P2;
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    pack_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_pairs(const UnpackDesc &d, const double *C, double *out, cudaStream_t s) {
+    const int64_t total = d.ext[0] * d.ext[1] * d.ext[2] * d.ext[3];
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    unpack_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, C, out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ rows_gemm
 // offset of a mixed-radix index below 2^32 with 32-bit divisions
 __device__ __forceinline__ int64_t grp_offset32(const Grp &g, uint32_t x) {

@@ -75,6 +75,29 @@ struct RowsGemmDesc {
     int f32;
 };
 
+// Packed index pairs.  A pair (p < q) of letters with extent n has the index
+// P(p, q) = p (2n - p - 1) / 2 + (q - p - 1): q runs fastest.
+// pack:   dst[P1][P2] = scale * src[p s0 + q s1 + r s2 + u s3] over p < q
+//         (extent n1) and r < u (extent n2), dst contiguous
+struct PackDesc {
+    int64_t n1, n2, P1, P2;
+    int64_t s0, s1, s2, s3;
+    double scale;
+};
+// unpack: out(x) = beta * out(x) + alpha * sign * C[PA(a1, a2) cA + PB(b1, b2) cB]
+// over the 4-index output box (dims in storage order, ext/ostr), where
+// (a1, a2) = the digits at dims da1, da2 and (b1, b2) those at db1, db2; a
+// digit pair out of order takes the swapped pair with a minus sign; equal
+// digits give 0
+struct UnpackDesc {
+    int64_t ext[4], ostr[4];
+    int da1, da2, db1, db2;
+    int64_t nA, nB, cA, cB;
+    double alpha, beta;
+};
+cudaError_t launch_pack_pairs(const PackDesc &d, const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_unpack_pairs(const UnpackDesc &d, const double *C, double *out, cudaStream_t s);
+
 // Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes
 // bf16 planes P_p[r][k] of a padded K-major matrix [Rp][Kp]:
 //   hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); rows >= R and

@@ -8,6 +8,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <array>
 #include <cctype>
 #include <cmath>
 #include <cstdio>
@@ -33,6 +34,7 @@ int64_t align_up(int64_t x, int64_t a = kAlign) { return (x + a - 1) / a * a; }
 struct Ref {
     std::string name;
     std::vector<int> letters;   // letter ids in written order
+    std::vector<std::array<int, 2>> pairs;   // declared antisymmetric pairs "(pq)": positions in letters
 };
 
 struct Stmt {
@@ -77,13 +79,35 @@ struct Parser {
         return (int)tokens.size() - 1;
     }
     // reads [a-z][0-9]* tokens until the closing bracket
-    bool letters_until(char close, std::vector<int> &out, std::vector<int> *slash_pos = nullptr) {
+    bool letters_until(char close, std::vector<int> &out, std::vector<int> *slash_pos = nullptr,
+                       std::vector<std::array<int, 2>> *pairs = nullptr) {
+        int open = -1;   // position where a "(pq)" pair started
         for (;;) {
             ws();
             if (p >= s.size()) { err = "missing closing bracket"; return false; }
             char c = s[p];
-            if (c == close) { p++; return true; }
+            if (c == close) {
+                if (open >= 0) { err = "unclosed '(' in index list"; return false; }
+                p++;
+                return true;
+            }
             if (c == ',') { p++; continue; }
+            if (c == '(' && pairs) {
+                if (open >= 0) { err = "nested '(' in index list"; return false; }
+                open = (int)out.size();
+                p++;
+                continue;
+            }
+            if (c == ')' && pairs) {
+                if (open < 0 || (int)out.size() - open != 2) {
+                    err = "'(..)' must enclose exactly two indices";
+                    return false;
+                }
+                pairs->push_back({open, open + 1});
+                open = -1;
+                p++;
+                continue;
+            }
             if (c == '/' && slash_pos) { slash_pos->push_back((int)out.size()); p++; continue; }
             if (!(c >= 'a' && c <= 'z')) { err = std::string("unexpected character '") + c + "' in index list"; return false; }
             std::string tok(1, c);
@@ -102,7 +126,7 @@ struct Parser {
         r.name = s.substr(q, p - q);
         bool any = false;
         while (eat('[')) {
-            if (!letters_until(']', r.letters)) return false;
+            if (!letters_until(']', r.letters, nullptr, &r.pairs)) return false;
             any = true;
         }
         if (!any) { err = "tensor '" + r.name + "' has no index brackets"; return false; }
@@ -275,6 +299,10 @@ struct Planner {
     }
 
     explicit Planner(Plan &pl) : plan(pl), o(pl.o), v(pl.v), cplx(pl.dtype == 1), esz(pl.dtype == 1 ? 16 : 8) {}
+    // 'o', 'v': orbital indices; 'O', 'V': packed pairs p < q of them
+    int64_t space_extent(char sp) const {
+        return sp == 'o' ? o : sp == 'v' ? v : sp == 'O' ? (int64_t)o * (o - 1) / 2 : (int64_t)v * (v - 1) / 2;
+    }
     const bool cplx;            // complex double elements (interleaved re, im)
     const int64_t esz;          // bytes per element
 
@@ -301,7 +329,7 @@ struct Planner {
         int64_t e = 1;
         t.ext.resize(sp.size());
         t.str.resize(sp.size());
-        for (size_t d = 0; d < sp.size(); d++) t.ext[d] = sp[d] == 'o' ? o : v;
+        for (size_t d = 0; d < sp.size(); d++) t.ext[d] = space_extent(sp[d]);
         for (int d = (int)sp.size() - 1; d >= 0; d--) { t.str[d] = e; e *= t.ext[d]; }
         t.elems = e;
         if (k == TKind::INTERM) { t.ws_off = interm_need; interm_need += align_up(e * esz); }
@@ -549,6 +577,115 @@ struct Planner {
 
     int last_out = 0;
 
+    // The pair letters of declared pair q of a reference, in written order.
+    static std::array<int, 2> pair_letters(const Ref &r, int q) {
+        return {r.letters[r.pairs[q][0]], r.letters[r.pairs[q][1]]};
+    }
+
+    // A packed operand: a PACK step from view X into a new intermediate
+    // [free pair][contracted pair] (static when X is an integral block).
+    int pack_operand(const View &X, std::array<int, 2> fp, std::array<int, 2> kp, char sf, char sk,
+                     const std::string &name, int si) {
+        const int id = add_tensor(name, TKind::INTERM, std::vector<char>{sf, sk}, 0);
+        initialized[id] = true;
+        Step st;
+        st.kind = StepKind::PACK;
+        st.stmt = si;
+        st.a = tensor_ref(X.tensor);
+        st.out = tensor_ref(id);
+        PackDesc &d = st.pk;
+        d.n1 = ext_of(X, fp[0]);
+        d.n2 = ext_of(X, kp[0]);
+        d.P1 = d.n1 * (d.n1 - 1) / 2;
+        d.P2 = d.n2 * (d.n2 - 1) / 2;
+        d.s0 = str_of(X, fp[0]);
+        d.s1 = str_of(X, fp[1]);
+        d.s2 = str_of(X, kp[0]);
+        d.s3 = str_of(X, kp[1]);
+        d.scale = 1.0;
+        if (plan.tensors[X.tensor].kind == TKind::INTEGRAL) {
+            st.static_src = true;
+            plan.tensors[id].static_data = true;
+        }
+        st.note = "pack " + plan.tensors[X.tensor].name;
+        plan.steps.push_back(st);
+        return id;
+    }
+
+    // out = alpha sum_{k1 k2} A(a1 a2 k1 k2) B(b1 b2 k1 k2) (+ beta out) with A
+    // antisymmetric in (a1 a2), (k1 k2) and B in (b1 b2), (k1 k2), as declared:
+    // the k-sum runs over k1 < k2 (factor 2) and only a1 < a2, b1 < b2 are
+    // computed; the output is filled from them by antisymmetry.
+    bool plan_packed(const Stmt &s, const std::vector<char> &lsp, int si, const View &out, BufRef outref,
+                     const std::vector<View> &in, double alpha, double beta) {
+        if (cplx) { err = "packed index pairs are implemented for real tensors"; return false; }
+        const Ref &ra = s.rhs[0], &rb = s.rhs[1];
+        std::set<int> Ls(s.rhs[1].letters.begin(), s.rhs[1].letters.end());
+        int ka = -1, kb = -1;
+        for (int q = 0; q < 2; q++) {
+            auto pa = pair_letters(ra, q), pb = pair_letters(rb, q);
+            if (Ls.count(pa[0]) && Ls.count(pa[1])) ka = q;
+            std::set<int> La(ra.letters.begin(), ra.letters.end());
+            if (La.count(pb[0]) && La.count(pb[1])) kb = q;
+        }
+        if (ka < 0 || kb < 0) { err = "packed pairs: the contracted indices must form a declared pair in both operands"; return false; }
+        const auto kpair = pair_letters(ra, ka);               // contracted pair, A's orientation
+        const auto fa = pair_letters(ra, 1 - ka), fb = pair_letters(rb, 1 - kb);
+        for (const auto &pr : {kpair, fa, fb})
+            if (lsp[pr[0]] != lsp[pr[1]]) { err = "a declared pair mixes occupied and virtual indices"; return false; }
+        auto up = [](char c) { return c == 'o' ? 'O' : 'V'; };
+        std::vector<char> lsp2 = lsp;
+        const int LP = (int)lsp2.size(), LQ = LP + 1, LK = LP + 2;
+        lsp2.push_back(up(lsp[fa[0]]));
+        lsp2.push_back(up(lsp[fb[0]]));
+        lsp2.push_back(up(lsp[kpair[0]]));
+        const std::string tag = std::to_string(si);
+        const int tA = pack_operand(in[0], fa, kpair, lsp2[LP], lsp2[LK], "%pa" + tag, si);
+        const int tB = pack_operand(in[1], fb, kpair, lsp2[LQ], lsp2[LK], "%pb" + tag, si);
+        if (!err.empty()) return false;
+        // C[Q][P] = 2 alpha sum_K Ap[P][K] Bp[Q][K]: an ordinary dense contraction
+        Stmt g;
+        g.line = s.line;
+        g.op = 0;
+        g.factor = 2.0 * alpha;
+        g.out = Ref{"%pc" + tag, {LQ, LP}, {}};
+        g.rhs = {Ref{plan.tensors[tA].name, {LP, LK}, {}}, Ref{plan.tensors[tB].name, {LQ, LK}, {}}};
+        if (!plan_stmt(g, lsp2, si)) return false;
+        const int tC = last_out;
+        version[tC]++;
+        last_out = out.tensor;
+        // unpack into the output
+        Step u;
+        u.kind = StepKind::UNPACK;
+        u.stmt = si;
+        u.a = tensor_ref(tC);
+        u.out = outref;
+        UnpackDesc &d = u.up;
+        if (out.idx.size() != 4) { err = "packed pairs: the output needs four indices"; return false; }
+        for (int k = 0; k < 4; k++) {
+            d.ext[k] = out.ext[k];
+            d.ostr[k] = out.str[k];
+        }
+        auto pos = [&](int l) {
+            for (int k = 0; k < 4; k++)
+                if (out.idx[k] == l) return k;
+            return -1;
+        };
+        d.da1 = pos(fa[0]);
+        d.da2 = pos(fa[1]);
+        d.db1 = pos(fb[0]);
+        d.db2 = pos(fb[1]);
+        d.nA = ext_of(in[0], fa[0]);
+        d.nB = ext_of(in[1], fb[0]);
+        d.cA = 1;                                   // C[Q][P]: P fastest
+        d.cB = d.nA * (d.nA - 1) / 2;
+        d.alpha = 1.0;
+        d.beta = beta;
+        u.note = "unpack -> " + plan.tensors[out.tensor].name;
+        plan.steps.push_back(u);
+        return true;
+    }
+
     bool plan_stmt(const Stmt &s, const std::vector<char> &lsp, int si) {
         View out;
         if (!resolve(s.out, true, s.op, lsp, out)) return false;
@@ -611,6 +748,12 @@ struct Planner {
         F.insert(FA.begin(), FA.end());
         F.insert(FB.begin(), FB.end());
         if (F != O) { err = "output indices must be exactly the uncontracted operand indices"; return false; }
+
+        // packed pairs: each operand is two declared antisymmetric pairs, one of
+        // them contracted (e.g. the particle ladder tau[(ij)(ef)] * V[(ab)(ef)])
+        if (s.rhs[0].pairs.size() == 2 && s.rhs[1].pairs.size() == 2 && s.rhs[0].letters.size() == 4 &&
+            s.rhs[1].letters.size() == 4 && K.size() == 2 && perms.size() == 1 && perms[0].sigma.empty())
+            return plan_packed(s, lsp, si, out, outref, in, alpha, beta);
 
         if (K.empty()) {
             // outer product: each output element is formed directly as a sum of
@@ -925,8 +1068,8 @@ struct Planner {
                 sa.conj = A.conj ? 1 : 0;
                 sb.conj = B.conj ? 1 : 0;
             }
-            g.a_static = plan.tensors[A.tensor].kind == TKind::INTEGRAL;
-            g.b_static = plan.tensors[B.tensor].kind == TKind::INTEGRAL;
+            g.a_static = plan.tensors[A.tensor].kind == TKind::INTEGRAL || plan.tensors[A.tensor].static_data;
+            g.b_static = plan.tensors[B.tensor].kind == TKind::INTEGRAL || plan.tensors[B.tensor].static_data;
             const int64_t bytes_a = t.Mp * t.Kp * 2 * np, bytes_b = t.Np * t.Kp * 2 * np;
             // static planes live in the cache; other planes in the split region, shared by
             // every later step that splits the same version of the same view
@@ -1044,7 +1187,8 @@ std::string describe_plan(const Plan &plan) {
         os << (k ? "," : "") << "{\"stmt\":" << s.stmt << ",\"kind\":\""
            << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : s.rows ? (s.gemm.f32 ? "gemm_rows_f32" : "gemm_rows")
                                                    : s.gemm.f32 ? "gemm_f32" : "gemm_f64")
-                                        : s.kind == StepKind::ACCUM ? "accum" : "zero")
+                                        : s.kind == StepKind::ACCUM ? "accum" : s.kind == StepKind::PACK ? "pack"
+                                        : s.kind == StepKind::UNPACK ? "unpack" : "zero")
            << "\",\"note\":\"" << s.note << "\"";
         if (s.kind == StepKind::GEMM && !s.mixed) {
             os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
@@ -1068,6 +1212,10 @@ std::string describe_plan(const Plan &plan) {
         } else if (s.kind == StepKind::ACCUM) {
             os << ",\"elems\":" << s.acc.total << ",\"terms\":" << s.acc.nperm << ",\"alpha\":" << s.acc.alpha
                << ",\"beta\":" << s.acc.beta << ",\"conj_a\":" << s.acc.conj_a << ",\"conj_b\":" << s.acc.conj_b;
+        } else if (s.kind == StepKind::PACK) {
+            os << ",\"elems\":" << s.pk.P1 * s.pk.P2;
+        } else if (s.kind == StepKind::UNPACK) {
+            os << ",\"elems\":" << s.up.ext[0] * s.up.ext[1] * s.up.ext[2] * s.up.ext[3];
         } else {
             os << ",\"elems\":" << s.zero_elems;
         }

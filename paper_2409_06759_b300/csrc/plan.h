@@ -27,6 +27,7 @@ struct Tensor {
     int64_t elems = 0;
     int slot = 0;               // AMP/RES: rank/2 (1..3); INTEGRAL: block 0..5
     int64_t ws_off = -1;        // INTERM: byte offset of its buffer in the workspace
+    bool static_data = false;   // INTERM filled once per solve from integrals (packed blocks)
 };
 
 // Memory a step reads or writes, resolved at run time.
@@ -45,7 +46,7 @@ struct View {
     bool conj = false;
 };
 
-enum class StepKind { ZERO, ACCUM, GEMM };
+enum class StepKind { ZERO, ACCUM, GEMM, PACK, UNPACK };
 
 struct Step {
     StepKind kind;
@@ -64,6 +65,8 @@ struct Step {
     bool static_src = false;                     // ACCUM permute of an integral block into the cache
     bool skip_a = false, skip_b = false;         // planes already split by an earlier step (same source version)
     std::vector<std::array<int, 2>> cands;       // autotuning candidates (tile width or 0, split-K)
+    PackDesc pk{};                               // PACK: out = packed pairs of a
+    UnpackDesc up{};                             // UNPACK: out (antisymmetric) from packed a
     bool rows = false;                           // narrow GEMM (one thread per row, operands in place)
     RowsGemmDesc rg{};
     double flops = 0.0;

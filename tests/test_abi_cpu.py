@@ -153,3 +153,36 @@ def test_batched_argument_checks(cc):
     with pytest.raises(cc.CCError) as ei:
         cc.cc_solve_batched([p, p], [{}, {}], [(None, None), (None, None)], None)
     assert "plan of its own" in str(ei.value)
+
+
+def test_packed_pairs_plan(cc):
+    """Declared pairs: the ladder runs as pack + one GEMM over pairs + unpack,
+    with the pair-count flops; the integral operand is packed once (static)."""
+    o, v = 8, 30
+    p = cc.cc_plan_create(cc.load_list("ccsd_packed"), o, v)
+    q = cc.cc_plan_create(cc.load_list("ccsd_vvvv"), o, v)
+    d = p.describe()
+    kinds = [s["kind"] for s in d["steps"]]
+    assert kinds.count("pack") == 4 and kinds.count("unpack") == 2
+    P, Q = o * (o - 1) // 2, v * (v - 1) // 2
+    lad = [s for s in d["steps"] if s["kind"].startswith("gemm") and s["K"] == Q and Q in (s["M"], s["N"])]
+    assert lad and lad[0]["flops"] == 2.0 * P * Q * Q
+    assert p.flops < q.flops - 2.0 * o * o * v ** 4 * 0.8
+
+
+@pytest.mark.parametrize("text,frag", [
+    ("R2[ijab] = 0.5 T2[(ij)(ef)] * V[(ab)(fe)] * T1[ia]", "binary"),
+    ("R2[ijab] = T2[(ij)(ef)] * V[(ae)(bf)]", "declared pair"),
+    ("R2[ijab] = T2[(i)(jab)]", "exactly two"),
+    ("R2[ijab] = T2[(ij(ab))]", "nested"),
+])
+def test_packed_pair_errors(cc, text, frag):
+    with pytest.raises(cc.CCError) as ei:
+        cc.cc_plan_create(text, 3, 5)
+    assert frag in str(ei.value)
+
+
+def test_packed_pairs_reject_complex(cc):
+    with pytest.raises(cc.CCError) as ei:
+        cc.cc_plan_create(cc.load_list("ccsd_packed"), 3, 5, dtype=cc.CC_C128)
+    assert "real" in str(ei.value)

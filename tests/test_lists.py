@@ -12,7 +12,7 @@ import oracle
 LISTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2409_06759_b300", "lists")
 
 
-@pytest.mark.parametrize("name", ["ccsd", "ccsd_vvvv"])
+@pytest.mark.parametrize("name", ["ccsd", "ccsd_vvvv", "ccsd_packed"])
 @pytest.mark.parametrize("o,v,seed", [(2, 3, 1), (3, 4, 2), (4, 5, 3)])
 def test_list_matches_oracle(name, o, v, seed):
     text = open(os.path.join(LISTS, name + ".txt")).read()
@@ -25,7 +25,7 @@ def test_list_matches_oracle(name, o, v, seed):
     assert np.abs(r2 - l2).max() < 1e-13
 
 
-@pytest.mark.parametrize("name", ["ccsd", "ccsd_vvvv"])
+@pytest.mark.parametrize("name", ["ccsd", "ccsd_vvvv", "ccsd_packed"])
 @pytest.mark.parametrize("o,v,seed", [(2, 3, 11), (3, 5, 12)])
 def test_list_matches_complex_oracle(name, o, v, seed):
     """Complex orbitals: the lists name each integral in the orientation the
