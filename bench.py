@@ -435,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ref-samples", type=int, default=2)
     ap.add_argument("--dtype", default="f64", choices=["f64", "c128"])
+    ap.add_argument("--packed", action="store_true",
+                    help="lists with packed index pairs (ladder over e<f; flops counted packed)")
     ap.add_argument("--workload", default="ccsd", choices=["ccsd", "ccsdt", "batched"],
                     help="ccsdt: the o=8 v=64 CCSDT workload (generated list); batched: 64 uneven CCSD systems")
     args = ap.parse_args()
@@ -475,8 +477,10 @@ def main():
     t0 = time.perf_counter()
     dsys = DeviceSystem.from_system(sysm, device=dev)
     t_int = time.perf_counter() - t0
-    mixed = Engine(dsys, list_name="ccsd_vvvv", precision=args.precision)
-    fp64 = Engine(dsys, list_name="ccsd")
+    mixed_list = "ccsd_packed" if args.packed else "ccsd_vvvv"
+    fp64_list = "ccsd_packed" if args.packed else "ccsd"
+    mixed = Engine(dsys, list_name=mixed_list, precision=args.precision)
+    fp64 = Engine(dsys, list_name=fp64_list)
     stream = torch.cuda.current_stream(dev)
     z = lambda: (torch.zeros(o, v, dtype=tdt, device=dev),
                  torch.zeros(o, o, v, v, dtype=tdt, device=dev))
@@ -561,7 +565,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": f"{args.precision}: bf16 tensor-core products, fp32 "
             "accumulation, fp64 outputs/energy/DIIS" + (" (complex128 tensors)" if cplx else ""), "data": "synthetic",
             "config": {"workload": workload_name(args), "precision": args.precision,
-                       "list": "ccsd_vvvv", "flops_per_iter": flops, "replicas": world,
+                       "list": mixed_list, "fp64_list": fp64_list, "flops_per_iter": flops, "replicas": world,
+                       "flops_counted": "packed (pair-count) flops" if args.packed else "unpacked flops",
                        "l2": "inputs larger than L2 (<ab||ef> split planes %.1f GB, T2 %d MB)"
                              % (6.4 * (2 if cplx else 1), 512 * (2 if cplx else 1)),
                        "integral_build_s": t_int},
@@ -576,7 +581,7 @@ def main():
         del sol, t1, t2
         torch.cuda.empty_cache()
         fpk = fp64_peak_live(torch)
-        acc = Engine(dsys, list_name="ccsd_vvvv", precision="bf16x6")
+        acc = Engine(dsys, list_name=mixed_list, precision="bf16x6")
 
         def timed_solve(eng, refine=None, **kw):
             a1, a2 = z()

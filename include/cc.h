@@ -89,6 +89,10 @@ typedef struct {
     const void *ovov;   /* [o][v][o][v] */
     const void *ovvv;   /* [o][v][v][v] */
     const void *vvvv;   /* [v][v][v][v] */
+    /* optional: <ab||ef> for a < b, e < f as a dense [P(a,b)][P(e,f)] matrix,
+     * P(p,q) = p (2v - p - 1)/2 + (q - p - 1) (a quarter of vvvv; real only).
+     * Read instead of vvvv by plans created with packed_vvvv = 1. */
+    const void *vvvv_packed;
 } cc_integrals;
 
 /* Cluster amplitudes: t1[i][a], t2[i][j][a][b], t3[i][j][k][a][b][c] (NULL when
@@ -110,6 +114,8 @@ typedef struct {
     int struct_size;      /* sizeof(cc_plan_opts) */
     int verbose;          /* 1: print the plan to stderr at creation */
     int fuse_permutes;    /* reserved, 0 */
+    int packed_vvvv;      /* 1: a packed-pair contraction over <ab||ef> in its stored
+                           * orientation (declared (ab)(ef)) reads ints->vvvv_packed */
 } cc_plan_opts;
 
 /* cc_plan_create -- parse a contraction list and plan its execution.
@@ -269,6 +275,12 @@ CC_API cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integral
  *   cc_integral_block_elems (elements).
  *   ws: device workspace of cc_build_integrals_workspace_bytes. */
 CC_API cc_status cc_integral_block_elems(int o, int v, size_t elems[6]);
+/* The packed <ab||ef> block (cc_integrals.vvvv_packed) from B, built in chunks
+ * of a so that the full vvvv block is never held (real only: CC_F64).
+ *   out: device, (v(v-1)/2)^2 doubles.  ws: cc_build_vvvv_packed_workspace_bytes. */
+CC_API cc_status cc_build_vvvv_packed_workspace_bytes(int o, int v, int L, cc_dtype dtype, size_t *bytes);
+CC_API cc_status cc_build_vvvv_packed(int o, int v, int L, cc_dtype dtype, const void *B, void *out, void *ws,
+                                      size_t ws_bytes, void *stream);
 CC_API cc_status cc_build_integrals_workspace_bytes(int o, int v, int L, cc_dtype dtype, size_t *bytes);
 CC_API cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const void *B, void *oooo, void *ooov,
                                     void *oovv, void *ovov, void *ovvv, void *vvvv, void *ws, size_t ws_bytes,

@@ -33,7 +33,7 @@ EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_
            "cc_residual", "cc_energy", "cc_solve_workspace_bytes", "cc_solve", "cc_integral_block_elems",
            "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_status_string",
            "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched",
-           "cc_plan_autotune"]
+           "cc_plan_autotune", "cc_build_vvvv_packed_workspace_bytes", "cc_build_vvvv_packed"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libccb300.so is not built ({LIB_PATH}); run paper_2409_06759_b300/build.py "
@@ -46,7 +46,8 @@ c_void_p, c_int, c_size_t, c_double = ctypes.c_void_p, ctypes.c_int, ctypes.c_si
 
 class cc_integrals(ctypes.Structure):
     _fields_ = [("f_occ", c_void_p), ("f_vir", c_void_p), ("oooo", c_void_p), ("ooov", c_void_p),
-                ("oovv", c_void_p), ("ovov", c_void_p), ("ovvv", c_void_p), ("vvvv", c_void_p)]
+                ("oovv", c_void_p), ("ovov", c_void_p), ("ovvv", c_void_p), ("vvvv", c_void_p),
+                ("vvvv_packed", c_void_p)]
 
 
 class cc_amps(ctypes.Structure):
@@ -58,7 +59,7 @@ class cc_resid(ctypes.Structure):
 
 
 class cc_plan_opts(ctypes.Structure):
-    _fields_ = [("struct_size", c_int), ("verbose", c_int), ("fuse_permutes", c_int)]
+    _fields_ = [("struct_size", c_int), ("verbose", c_int), ("fuse_permutes", c_int), ("packed_vvvv", c_int)]
 
 
 class cc_solve_opts(ctypes.Structure):
@@ -97,6 +98,8 @@ _sig = {
                                  _P(cc_solve_report), c_void_p, c_size_t, c_void_p]),
     "cc_plan_autotune": (c_int, [c_void_p, _P(cc_integrals), _P(cc_amps), _P(cc_resid), c_void_p, c_size_t, c_void_p,
                                  c_int]),
+    "cc_build_vvvv_packed_workspace_bytes": (c_int, [c_int, c_int, c_int, c_int, _P(c_size_t)]),
+    "cc_build_vvvv_packed": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "cc_status_string": (ctypes.c_char_p, [c_int]),
     "cc_last_error": (ctypes.c_char_p, []),
     "cc_version": (ctypes.c_char_p, []),
@@ -183,12 +186,12 @@ def load_list(name: str) -> str:
 
 
 def cc_plan_create(text: str, o: int, v: int, dtype: int = CC_F64, precision=CC_PREC_FP64, verbose: int = 0,
-                   _route_all: bool = False) -> Plan:
+                   _route_all: bool = False, packed_vvvv: bool = False) -> Plan:
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     prec = precision + (100 if _route_all else 0)   # test hook: every GEMM on the split route
     h = c_void_p()
-    opts = cc_plan_opts(ctypes.sizeof(cc_plan_opts), verbose, 0)
+    opts = cc_plan_opts(ctypes.sizeof(cc_plan_opts), verbose, 0, int(packed_vvvv))
     _check(_lib.cc_plan_create(text.encode(), o, v, dtype, prec, ctypes.byref(opts), ctypes.byref(h)),
            "cc_plan_create")
     return Plan(h.value, o, v, precision, text, dtype)
@@ -237,7 +240,7 @@ def cc_plan_launch_count(plan: Plan) -> int:
 
 def integrals_struct(ints: dict) -> cc_integrals:
     return cc_integrals(*(_ptr(ints.get(k)) for k in ("f_occ", "f_vir", "oooo", "ooov", "oovv", "ovov", "ovvv",
-                                                       "vvvv")))
+                                                       "vvvv", "vvvv_packed")))
 
 
 def cc_residual(plan: Plan, ints: dict, t1, t2, r1, r2, ws, stream=None, t3=None, r3=None):
@@ -375,3 +378,15 @@ def cc_build_integrals_workspace_bytes(o: int, v: int, L: int, dtype: int = CC_F
 def cc_build_integrals(o: int, v: int, L: int, B, blocks: dict, ws, dtype: int = CC_F64, stream=None):
     _check(_lib.cc_build_integrals(o, v, L, dtype, _ptr(B), *(_ptr(blocks.get(k)) for k in BLOCKS), _ptr(ws),
                                    _nbytes(ws), _stream(stream)), "cc_build_integrals")
+
+
+def cc_build_vvvv_packed_workspace_bytes(o: int, v: int, L: int, dtype: int = CC_F64) -> int:
+    n = c_size_t()
+    _check(_lib.cc_build_vvvv_packed_workspace_bytes(o, v, L, dtype, ctypes.byref(n)),
+           "cc_build_vvvv_packed_workspace_bytes")
+    return n.value
+
+
+def cc_build_vvvv_packed(o: int, v: int, L: int, B, out, ws, dtype: int = CC_F64, stream=None):
+    _check(_lib.cc_build_vvvv_packed(o, v, L, dtype, _ptr(B), _ptr(out), _ptr(ws), _nbytes(ws), _stream(stream)),
+           "cc_build_vvvv_packed")

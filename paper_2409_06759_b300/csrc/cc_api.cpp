@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -76,7 +77,7 @@ struct cc_plan_s {
 namespace {
 
 const void *block_ptr(const cc_integrals *I, int b) {
-    const void *p[6] = {I->oooo, I->ooov, I->oovv, I->ovov, I->ovvv, I->vvvv};
+    const void *p[7] = {I->oooo, I->ooov, I->oovv, I->ovov, I->ovvv, I->vvvv, I->vvvv_packed};
     return p[b];
 }
 
@@ -329,7 +330,10 @@ cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_prec
     cc_plan_s *pl = new (std::nothrow) cc_plan_s();
     if (!pl) return fail(CC_ERR_OOM, "plan allocation failed");
     std::string err;
-    if (!build_plan(text, o, v, (int)dtype, prec, pl->plan, err)) {
+    int flags = 0;
+    if (opts && opts->struct_size >= (int)(offsetof(cc_plan_opts, packed_vvvv) + sizeof(int)) && opts->packed_vvvv)
+        flags |= 1;
+    if (!build_plan(text, o, v, (int)dtype, prec, pl->plan, err, flags)) {
         delete pl;
         return fail(err.find("index spaces") != std::string::npos ? CC_ERR_SHAPE : CC_ERR_PARSE, err);
     }
@@ -1028,6 +1032,76 @@ cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints
 }  // extern "C"
 
 extern "C" {
+
+cc_status cc_build_vvvv_packed_workspace_bytes(int o, int v, int L, cc_dtype dtype, size_t *bytes) {
+    if (o < 1 || v < 2 || L < 1 || !bytes) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    if (dtype != CC_F64) return fail(CC_ERR_UNSUPPORTED, "the packed vvvv block is real only");
+    const int64_t v3 = (int64_t)v * v * v;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(v, ((int64_t)1 << 30) / (v3 * 8)));
+    *bytes = (size_t)(al((int64_t)L * v * v * 8) + al(chunk * v3 * 8));
+    return CC_OK;
+}
+
+cc_status cc_build_vvvv_packed(int o, int v, int L, cc_dtype dtype, const void *B, void *out, void *ws,
+                               size_t ws_bytes, void *stream) {
+    size_t need = 0;
+    cc_status st = cc_build_vvvv_packed_workspace_bytes(o, v, L, dtype, &need);
+    if (st != CC_OK) return st;
+    if (!B || !out || !ws || ws_bytes < need || !aligned256(ws)) return fail(CC_ERR_WORKSPACE, "bad B, out or workspace");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = o + v, v2 = (int64_t)v * v, v3 = v2 * v;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(v, ((int64_t)1 << 30) / (v3 * 8)));
+    double *Bvv = (double *)ws;                                   // [L][v][v]
+    double *S = (double *)((char *)ws + al((int64_t)L * v2 * 8)); // [a - a0][b][e][f] of one chunk
+    {
+        AccumDesc d{};
+        d.nd = 3;
+        d.nperm = 1;
+        d.ext[0] = L; d.ext[1] = v; d.ext[2] = v;
+        d.ostr[0] = v2; d.ostr[1] = v; d.ostr[2] = 1;
+        d.sstr[0][0] = n * n; d.sstr[0][1] = n; d.sstr[0][2] = 1;
+        d.total = (int64_t)L * v2;
+        d.sign[0] = 1.0;
+        d.alpha = 1.0;
+        CC_CUDA(launch_accum(d, (const double *)B + (int64_t)o * n + o, Bvv, s));
+    }
+    const int64_t P = (int64_t)v * (v - 1) / 2;
+    auto start = [&](int64_t a) { return a * (2 * (int64_t)v - a - 1) / 2; };
+    for (int64_t a0 = 0; a0 < v - 1; a0 += chunk) {
+        const int64_t a1 = std::min<int64_t>(a0 + chunk, v - 1), ca = a1 - a0;
+        // S[a][b][e][f] = sum_L Bvv[a][e] Bvv[b][f] - Bvv[a][f] Bvv[b][e] for a in [a0, a1)
+        for (int term = 0; term < 2; term++) {
+            GemmF64Desc g{};
+            g.M = ca * v;            // rows (a, e) or (a, f)
+            g.N = v2;                // cols (b, f) or (b, e)
+            g.K = L;
+            g.sAm = 1;
+            g.sAk = v2;
+            g.sBk = v2;
+            g.sBn = 1;
+            g.cm.nd = 2; g.cm.ext[0] = ca; g.cm.ext[1] = v; g.cm.str[0] = v3;
+            g.cn.nd = 2; g.cn.ext[0] = v; g.cn.ext[1] = v; g.cn.str[0] = v2;
+            g.cm.str[1] = term == 0 ? v : 1;     // e | f
+            g.cn.str[1] = term == 0 ? 1 : v;     // f | e
+            g.alpha = term == 0 ? 1.0 : -1.0;
+            g.beta = term == 0 ? 0.0 : 1.0;
+            g.splitk = 1;
+            CC_CUDA(launch_gemm_f64(g, Bvv + a0 * v, Bvv, S, nullptr, s));
+        }
+        PackDesc pd{};
+        pd.n1 = v;
+        pd.n2 = v;
+        pd.P1 = P;
+        pd.P2 = P;
+        pd.s0 = v3; pd.s1 = v2; pd.s2 = v; pd.s3 = 1;
+        pd.scale = 1.0;
+        pd.row0 = start(a0);
+        pd.rows = start(a1) - start(a0);
+        pd.pbase = a0;
+        CC_CUDA(launch_pack_pairs(pd, S, (double *)out + pd.row0 * P, s));
+    }
+    return CC_OK;
+}
 
 cc_status cc_integral_block_elems(int o, int v, size_t elems[6]) {
     if (o < 1 || v < 1 || !elems) return fail(CC_ERR_INVALID_ARG, "bad arguments");

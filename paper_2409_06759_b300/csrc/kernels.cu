@@ -369,13 +369,13 @@ __device__ __forceinline__ void pair_of(int64_t P, int64_t n, int64_t &p, int64_
 
 __global__ void __launch_bounds__(256) pack_pairs_kernel(const PackDesc d, const double *__restrict__ src,
                                                          double *__restrict__ dst) {
-    const int64_t total = d.P1 * d.P2;
+    const int64_t total = d.rows * d.P2;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t I = e / d.P2, J = e - I * d.P2;
         int64_t p, q, r, u;
-        pair_of(I, d.n1, p, q);
+        pair_of(d.row0 + I, d.n1, p, q);
         pair_of(J, d.n2, r, u);
-        dst[e] = d.scale * __ldg(src + p * d.s0 + q * d.s1 + r * d.s2 + u * d.s3);
+        dst[e] = d.scale * __ldg(src + (p - d.pbase) * d.s0 + q * d.s1 + r * d.s2 + u * d.s3);
     }
 }
 
@@ -404,7 +404,8 @@ __global__ void __launch_bounds__(256) unpack_pairs_kernel(const UnpackDesc d, c
 }
 
 cudaError_t launch_pack_pairs(const PackDesc &d, const double *src, double *dst, cudaStream_t s) {
-    const int64_t total = d.P1 * d.P2;
+    if (d.row0 < 0 || d.rows < 0 || d.row0 + d.rows > d.P1) return cudaErrorInvalidValue;
+    const int64_t total = d.rows * d.P2;
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;

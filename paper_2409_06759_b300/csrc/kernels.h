@@ -79,10 +79,14 @@ struct RowsGemmDesc {
 // P(p, q) = p (2n - p - 1) / 2 + (q - p - 1): q runs fastest.
 // pack:   dst[P1][P2] = scale * src[p s0 + q s1 + r s2 + u s3] over p < q
 //         (extent n1) and r < u (extent n2), dst contiguous
+// row0, rows: the launch covers packed rows [row0, row0 + rows) and writes
+// them to dst[0 ..); pbase is subtracted from the first letter before its
+// stride s0 (a source holding only part of that letter's range).
 struct PackDesc {
     int64_t n1, n2, P1, P2;
     int64_t s0, s1, s2, s3;
     double scale;
+    int64_t row0, rows, pbase;
 };
 // unpack: out(x) = beta * out(x) + alpha * sign * C[PA(a1, a2) cA + PB(b1, b2) cB]
 // over the 4-index output box (dims in storage order, ext/ostr), where

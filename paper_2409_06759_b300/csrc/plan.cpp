@@ -586,6 +586,14 @@ struct Planner {
     // [free pair][contracted pair] (static when X is an integral block).
     int pack_operand(const View &X, std::array<int, 2> fp, std::array<int, 2> kp, char sf, char sk,
                      const std::string &name, int si) {
+        // <ab||ef> packed in its stored orientation is an input of its own
+        const Tensor &TX = plan.tensors[X.tensor];
+        if (plan.packed_vvvv && TX.kind == TKind::INTEGRAL && TX.slot == 5 && X.idx.size() == 4 &&
+            X.idx[0] == fp[0] && X.idx[1] == fp[1] && X.idx[2] == kp[0] && X.idx[3] == kp[1]) {
+            auto it = by_name.find("V_vvvv_packed");
+            return it != by_name.end() ? it->second
+                                       : add_tensor("V_vvvv_packed", TKind::INTEGRAL, std::vector<char>{'V', 'V'}, 6);
+        }
         const int id = add_tensor(name, TKind::INTERM, std::vector<char>{sf, sk}, 0);
         initialized[id] = true;
         Step st;
@@ -603,6 +611,9 @@ struct Planner {
         d.s2 = str_of(X, kp[0]);
         d.s3 = str_of(X, kp[1]);
         d.scale = 1.0;
+        d.row0 = 0;
+        d.rows = d.P1;
+        d.pbase = 0;
         if (plan.tensors[X.tensor].kind == TKind::INTEGRAL) {
             st.static_src = true;
             plan.tensors[id].static_data = true;
@@ -1094,10 +1105,12 @@ struct Planner {
 
 }  // namespace
 
-bool build_plan(const std::string &text, int o, int v, int dtype, int precision, Plan &plan, std::string &err) {
+bool build_plan(const std::string &text, int o, int v, int dtype, int precision, Plan &plan, std::string &err,
+                int flags) {
     plan = Plan();
     plan.o = o;
     plan.v = v;
+    plan.packed_vvvv = (flags & 1) != 0;
     plan.dtype = dtype;
     plan.precision = precision >= 100 ? precision - 100 : precision;
     Planner P(plan);

@@ -25,7 +25,7 @@ struct Tensor {
     std::vector<int64_t> ext;
     std::vector<int64_t> str;   // element strides (row-major)
     int64_t elems = 0;
-    int slot = 0;               // AMP/RES: rank/2 (1..3); INTEGRAL: block 0..5
+    int slot = 0;               // AMP/RES: rank/2 (1..3); INTEGRAL: block 0..5, 6 = packed vvvv
     int64_t ws_off = -1;        // INTERM: byte offset of its buffer in the workspace
     bool static_data = false;   // INTERM filled once per solve from integrals (packed blocks)
 };
@@ -90,13 +90,15 @@ struct Plan {
     double flops = 0.0;
     double flops_mixed = 0.0;   // flops of steps on the split-bf16 route (fp64-equivalent)
     bool tuned = false;         // GEMM configurations picked by cc_plan_autotune
+    bool packed_vvvv = false;   // packed <ab||ef> is an input (integral slot 6)
     int verbose = 0;
 };
 
 // Parses and plans; on failure returns false and sets err (with line number).
 // precision >= 100 is a test hook: precision - 100, every GEMM on the split route.
+// flags bit 0: packed <ab||ef> read from the vvvv_packed input (slot 6).
 bool build_plan(const std::string &text, int o, int v, int dtype, int precision, Plan &plan,
-                std::string &err);
+                std::string &err, int flags = 0);
 
 std::string describe_plan(const Plan &plan);
 

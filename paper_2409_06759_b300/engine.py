@@ -8,7 +8,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (BLOCKS, CC_C128, CC_F64, cc_plan_autotune, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
+from . import (BLOCKS, CC_C128, CC_F64, cc_build_vvvv_packed, cc_build_vvvv_packed_workspace_bytes,
+               cc_plan_autotune, cc_build_integrals, cc_build_integrals_workspace_bytes, cc_energy,
                cc_integral_block_elems, cc_plan_create, cc_residual, cc_solve, cc_solve_batched,
                cc_solve_batched_workspace_bytes, cc_solve_workspace_bytes, load_list)
 
@@ -24,7 +25,10 @@ class DeviceSystem:
     """Orbital energies and the six integral blocks of one system, on the device.
     A complex factor B (complex spin orbitals) gives complex128 blocks."""
 
-    def __init__(self, o: int, v: int, eps_occ, eps_vir, B, device="cuda:0", blocks=BLOCKS, stream=None):
+    def __init__(self, o: int, v: int, eps_occ, eps_vir, B, device="cuda:0", blocks=BLOCKS, stream=None,
+                 packed_vvvv: bool = False):
+        """packed_vvvv: build <ab||ef> only packed (a < b, e < f; a quarter of the
+        block, never holding the full one) and leave vvvv out."""
         self.o, self.v, self.device = o, v, torch.device(device)
         self.f_occ = torch.as_tensor(eps_occ, dtype=torch.float64).to(self.device)
         self.f_vir = torch.as_tensor(eps_vir, dtype=torch.float64).to(self.device)
@@ -34,9 +38,18 @@ class DeviceSystem:
         Bd = Bt.to(self.tdtype).to(self.device).contiguous()
         L = Bd.shape[0]
         elems = cc_integral_block_elems(o, v)
+        if packed_vvvv:
+            blocks = tuple(k for k in blocks if k != "vvvv")
+        self.packed_vvvv = packed_vvvv
         self.blocks = {k: torch.empty(elems[k], dtype=self.tdtype, device=self.device) for k in blocks}
         ws = alloc_ws(cc_build_integrals_workspace_bytes(o, v, L, self.dtype), self.device)
         cc_build_integrals(o, v, L, Bd, self.blocks, ws, dtype=self.dtype, stream=stream)
+        if packed_vvvv:
+            P = v * (v - 1) // 2
+            self.blocks["vvvv_packed"] = torch.empty(P * P, dtype=torch.float64, device=self.device)
+            del ws
+            ws = alloc_ws(cc_build_vvvv_packed_workspace_bytes(o, v, L, self.dtype), self.device)
+            cc_build_vvvv_packed(o, v, L, Bd, self.blocks["vvvv_packed"], ws, dtype=self.dtype, stream=stream)
         torch.cuda.synchronize(self.device)
         del ws, Bd
 
@@ -63,7 +76,8 @@ class Engine:
             list_text = load_list(list_name or ("ccsd" if precision == "fp64" else "ccsd_vvvv"))
         self.triples = "T3[" in list_text
         self.sys = system
-        self.plan = cc_plan_create(list_text, system.o, system.v, system.dtype, precision, _route_all=route_all)
+        self.plan = cc_plan_create(list_text, system.o, system.v, system.dtype, precision, _route_all=route_all,
+                                   packed_vvvv=getattr(system, "packed_vvvv", False))
         self._ws = None
 
     @property

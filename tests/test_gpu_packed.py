@@ -94,3 +94,66 @@ def test_packed_full_size_matches_unpacked(cc):
     idx = np.array([[0, 1, 0, 1], [o - 1, o - 2, v - 1, v - 2], [3, 17, 150, 42]])
     want = oracle.ccsd_r2_sample(o, v, s.B, s.eps, t1, t2, idx)
     assert np.abs(p2.numpy()[tuple(idx.T)] - want).max() < 1e-9
+
+
+def _pair(p, q, n):
+    return p * (2 * n - p - 1) // 2 + (q - p - 1)
+
+
+@pytest.mark.parametrize("o,v", [(3, 7), (4, 25)])
+def test_packed_vvvv_block_matches_oracle(cc, o, v):
+    _, engine = cc
+    s, B, _, _ = small_case(o, v, 41, L=8)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV, packed_vvvv=True)
+    assert "vvvv" not in dsys.blocks
+    V = oracle_V(o, v, B)[o:, o:, o:, o:]
+    P = v * (v - 1) // 2
+    iu = [(a, b) for a in range(v) for b in range(a + 1, v)]
+    assert [_pair(a, b, v) for a, b in iu] == list(range(P))
+    want = np.array([[V[a, b, e, f] for e, f in iu] for a, b in iu])
+    got = dsys.blocks["vvvv_packed"].view(P, P).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-14 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_packed_vvvv_residual_matches_oracle(cc, prec):
+    """A system holding <ab||ef> only packed: the packed list reads it in place."""
+    _, engine = cc
+    o, v = 6, 30
+    s, B, t1, t2 = small_case(o, v, 42, L=8, scale=6.0, tscale=0.05)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV, packed_vvvv=True)
+    eng = engine.Engine(dsys, list_name="ccsd_packed", precision=prec, route_all=prec != "fp64")
+    names = {t["name"] for t in eng.plan.describe()["tensors"]}
+    assert "V_vvvv_packed" in names and "V_vvvv" not in names
+    r1, r2 = eng.residual(to_dev(t1), to_dev(t2))
+    torch.cuda.synchronize()
+    o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
+    d = np.sqrt(np.sum((r1.cpu().numpy() - o1) ** 2) + np.sum((r2.cpu().numpy() - o2) ** 2))
+    assert d <= (1e-13 if prec == "fp64" else 2e-4) * np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
+
+
+@pytest.mark.slow
+def test_packed_vvvv_full_size(cc):
+    """o=40, v=200: the chunked packed builder against the full block, and the
+    packed-input residual against the unpacked plan."""
+    _, engine = cc
+    s = ccinputs.make_system(**ccinputs.CONFIG_LADDER)
+    o, v = s.o, s.v
+    full = engine.DeviceSystem.from_system(s, device=DEV)
+    pk = engine.DeviceSystem.from_system(s, device=DEV, packed_vvvv=True)
+    P = v * (v - 1) // 2
+    rng = np.random.default_rng(3)
+    ab = rng.integers(0, v, (64, 4))
+    ab = ab[(ab[:, 0] < ab[:, 1]) & (ab[:, 2] < ab[:, 3])]
+    Vf = full.block("vvvv")
+    Vp = pk.blocks["vvvv_packed"].view(P, P)
+    for a, b, e, f in ab:
+        assert abs(Vp[_pair(a, b, v), _pair(e, f, v)].item() - Vf[a, b, e, f].item()) < 1e-15
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=0, scale1=0.01, scale2=0.01)
+    T1, T2 = to_dev(t1), to_dev(t2)
+    r = [x.cpu() for x in engine.Engine(pk, list_name="ccsd_packed").residual(T1, T2)]
+    del pk
+    u = [x.cpu() for x in engine.Engine(full, list_name="ccsd_vvvv").residual(T1, T2)]
+    d = torch.sqrt(sum(((a - b) ** 2).sum() for a, b in zip(r, u))).item()
+    n = torch.sqrt(sum((b ** 2).sum() for b in u)).item()
+    assert d <= 1e-12 * n
