@@ -99,7 +99,7 @@ cc_status check_inputs(const Plan &P, const cc_integrals *I, const cc_amps *A, c
     if (!I->f_occ || !I->f_vir) return fail(CC_ERR_INVALID_ARG, "NULL orbital energies");
     for (auto &t : P.tensors) {
         if (t.kind == TKind::INTEGRAL) {
-            if (!block_ptr(I, t.slot))
+            if (P.integ_used[t.slot] && !block_ptr(I, t.slot))
                 return fail(CC_ERR_INVALID_ARG, "integral block " + t.name + " is NULL but the list uses it");
         } else if (t.kind == TKind::AMP) {
             void *p = t.slot == 1 ? A->t1 : t.slot == 2 ? A->t2 : A->t3;

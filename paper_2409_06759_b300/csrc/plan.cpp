@@ -422,7 +422,8 @@ struct Planner {
             } else {
                 id = it->second;
                 const Tensor &t = plan.tensors[id];
-                if (t.kind != TKind::INTERM) { err = "name '" + nm + "' is reserved"; return false; }
+                // (internal '%' names: packed operands, which may be integral inputs)
+                if (t.kind != TKind::INTERM && nm[0] != '%') { err = "name '" + nm + "' is reserved"; return false; }
                 if (t.spaces != sp) { err = "index spaces of '" + nm + "' differ from its definition"; return false; }
             }
             vw.tensor = id;
@@ -590,9 +591,9 @@ struct Planner {
         const Tensor &TX = plan.tensors[X.tensor];
         if (plan.packed_vvvv && TX.kind == TKind::INTEGRAL && TX.slot == 5 && X.idx.size() == 4 &&
             X.idx[0] == fp[0] && X.idx[1] == fp[1] && X.idx[2] == kp[0] && X.idx[3] == kp[1]) {
-            auto it = by_name.find("V_vvvv_packed");
+            auto it = by_name.find("%V_vvvv_packed");
             return it != by_name.end() ? it->second
-                                       : add_tensor("V_vvvv_packed", TKind::INTEGRAL, std::vector<char>{'V', 'V'}, 6);
+                                       : add_tensor("%V_vvvv_packed", TKind::INTEGRAL, std::vector<char>{'V', 'V'}, 6);
         }
         const int id = add_tensor(name, TKind::INTERM, std::vector<char>{sf, sk}, 0);
         initialized[id] = true;
@@ -1161,6 +1162,8 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     off += P.cache_need;
     plan.ws_bytes = off;
     for (auto &st : plan.steps) {
+        for (BufRef *r : {&st.a, &st.b})
+            if (r->where == BufRef::INTEG && r->slot >= 0 && r->slot < 7) plan.integ_used[r->slot] = true;
         for (BufRef *r : {&st.out, &st.a, &st.b, &st.partials}) {
             if (r->where == BufRef::WS && r->slot == 1) { r->off += plan.scratch_off; r->slot = 0; }
             if (r->where == BufRef::WS && r->slot == 2) { r->off += plan.cache_off; r->slot = 0; }
@@ -1188,7 +1191,15 @@ std::string describe_plan(const Plan &plan) {
        << ",\"workspace_bytes\":" << plan.ws_bytes << ",\"interm_bytes\":" << plan.interm_bytes
        << ",\"scratch_bytes\":" << plan.scratch_bytes << ",\"splits_bytes\":" << plan.splits_bytes
        << ",\"cache_bytes\":" << plan.cache_bytes << ",\"flops\":" << plan.flops
-       << ",\"flops_mixed\":" << plan.flops_mixed << ",\"tuned\":" << (plan.tuned ? 1 : 0) << ",\"tensors\":[";
+       << ",\"flops_mixed\":" << plan.flops_mixed << ",\"tuned\":" << (plan.tuned ? 1 : 0)
+       << ",\"integrals_used\":[";
+    {
+        static const char *nm7[7] = {"oooo", "ooov", "oovv", "ovov", "ovvv", "vvvv", "vvvv_packed"};
+        bool first = true;
+        for (int b = 0; b < 7; b++)
+            if (plan.integ_used[b]) { os << (first ? "" : ",") << "\"" << nm7[b] << "\""; first = false; }
+    }
+    os << "],\"tensors\":[";
     for (size_t k = 0; k < plan.tensors.size(); k++) {
         const Tensor &t = plan.tensors[k];
         os << (k ? "," : "") << "{\"name\":\"" << t.name << "\",\"spaces\":\""

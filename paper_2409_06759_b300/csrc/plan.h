@@ -91,6 +91,7 @@ struct Plan {
     double flops_mixed = 0.0;   // flops of steps on the split-bf16 route (fp64-equivalent)
     bool tuned = false;         // GEMM configurations picked by cc_plan_autotune
     bool packed_vvvv = false;   // packed <ab||ef> is an input (integral slot 6)
+    bool integ_used[7] = {false, false, false, false, false, false, false};   // blocks some step reads
     int verbose = 0;
 };
 

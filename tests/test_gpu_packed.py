@@ -123,8 +123,8 @@ def test_packed_vvvv_residual_matches_oracle(cc, prec):
     s, B, t1, t2 = small_case(o, v, 42, L=8, scale=6.0, tscale=0.05)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV, packed_vvvv=True)
     eng = engine.Engine(dsys, list_name="ccsd_packed", precision=prec, route_all=prec != "fp64")
-    names = {t["name"] for t in eng.plan.describe()["tensors"]}
-    assert "V_vvvv_packed" in names and "V_vvvv" not in names
+    used = eng.plan.describe()["integrals_used"]
+    assert "vvvv_packed" in used and "vvvv" not in used
     r1, r2 = eng.residual(to_dev(t1), to_dev(t2))
     torch.cuda.synchronize()
     o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
