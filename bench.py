@@ -475,8 +475,10 @@ def main():
 
     sysm = ccinputs.make_system(**cfg, complex_=cplx)
     t0 = time.perf_counter()
-    dsys = DeviceSystem.from_system(sysm, device=dev)
+    # --packed: <ab||ef> held only packed (a < b, e < f), the full block never built
+    dsys = DeviceSystem.from_system(sysm, device=dev, packed_vvvv=bool(args.packed and not cplx))
     t_int = time.perf_counter() - t0
+    int_bytes = sum(b.numel() * b.element_size() for b in dsys.blocks.values())
     mixed_list = "ccsd_packed" if args.packed else "ccsd_vvvv"
     fp64_list = "ccsd_packed" if args.packed else "ccsd"
     mixed = Engine(dsys, list_name=mixed_list, precision=args.precision)
@@ -569,7 +571,7 @@ def main():
                        "flops_counted": "packed (pair-count) flops" if args.packed else "unpacked flops",
                        "l2": "inputs larger than L2 (<ab||ef> split planes %.1f GB, T2 %d MB)"
                              % (6.4 * (2 if cplx else 1), 512 * (2 if cplx else 1)),
-                       "integral_build_s": t_int},
+                       "integral_build_s": t_int, "integral_bytes": int_bytes},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -624,6 +626,39 @@ def main():
                        "energy_fp64": jsonable(rf.energy), "energy_mixed_refined": jsonable(rm.energy),
                        "rnorms_mixed_refined": [float(f"{x:.3e}") for x in rm.rnorms],
                        "rnorms_fp64": [float(f"{x:.3e}") for x in rf.rnorms]}
+    # ---- packed index pairs (lists/ccsd_packed.txt, <ab||ef> held only packed):
+    #      s/iter of both plans and time to solution; flops counted packed
+    if not args.no_tts and not args.packed and not cplx:
+        del mixed, fp64, acc, dsys, sol
+        torch.cuda.empty_cache()
+        pk = DeviceSystem.from_system(sysm, device=dev, packed_vvvv=True)
+        pm = Engine(pk, list_name="ccsd_packed", precision=args.precision)
+        pf = Engine(pk, list_name="ccsd_packed")
+        pa = Engine(pk, list_name="ccsd_packed", precision="bf16x6")
+        a1, a2 = z()
+        psol = Solver(pm)
+        psol.solve(a1, a2, max_iter=args.warmup, tol=0.0, stream=stream)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        psol.solve(a1, a2, max_iter=args.steps, tol=0.0, resume=True, stream=stream)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        p_iter = h0.elapsed_time(h1) / 1e3 / args.steps
+        del psol, a1, a2
+        torch.cuda.empty_cache()
+        rpf, tts_pf = timed_solve(pf)
+        rpm, tts_pm = timed_solve(pa, refine=pf, switch_tol=1e-7)
+        line["packed"] = {"list": "ccsd_packed", "integral_bytes": sum(b.numel() * b.element_size()
+                                                                       for b in pk.blocks.values()),
+                          "flops_per_iter": pm.plan.flops, "mixed_s_per_iter": p_iter,
+                          "mixed_tflops_packed_flops": pm.plan.flops / p_iter / 1e12,
+                          "fp64_time_to_solution_s": tts_pf, "fp64_iterations": rpf.iterations,
+                          "fp64_s_per_iter": tts_pf / max(rpf.iterations, 1),
+                          "mixed_refined_s": tts_pm, "mixed_refined_iterations": rpm.iterations,
+                          "speedup": tts_pf / tts_pm, "delta_E": abs(rpm.energy - rpf.energy),
+                          "delta_E_vs_unpacked_fp64": abs(rpf.energy - rf.energy),
+                          "converged": rpf.converged and rpm.converged}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
