@@ -629,7 +629,7 @@ def main():
     # ---- packed index pairs (lists/ccsd_packed.txt, <ab||ef> held only packed):
     #      s/iter of both plans and time to solution; flops counted packed
     if not args.no_tts and not args.packed and not cplx:
-        del mixed, fp64, acc, dsys, sol
+        del mixed, fp64, acc, dsys
         torch.cuda.empty_cache()
         pk = DeviceSystem.from_system(sysm, device=dev, packed_vvvv=True)
         pm = Engine(pk, list_name="ccsd_packed", precision=args.precision)
