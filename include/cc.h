@@ -305,6 +305,15 @@ CC_API cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const v
 CC_API cc_status cc_energy_noalloc(int o, int v, const cc_integrals *ints, const cc_amps *amps, double *e_dev,
                                    void *stream);
 
+/* cc_selftest_wait_timeout -- checks the bounded-wait mechanism of the
+ * tensor-core kernels on this device: one CTA waits, with the kernels' own
+ * bounded mbarrier wait and a budget of budget_cycles (1e3..4e9 SM cycles), on
+ * a barrier that nothing arrives at.  Returns CC_ERR_TIMEOUT when the wait
+ * gave up and the kernel returned (the expected outcome; the context stays
+ * usable), CC_ERR_CUDA otherwise.  Diagnostic; the paper has no counterpart.
+ * Allocates and frees 4 bytes of device memory and synchronises. */
+CC_API cc_status cc_selftest_wait_timeout(long long budget_cycles);
+
 CC_API const char *cc_status_string(cc_status s);
 CC_API const char *cc_last_error(void);
 

@@ -1103,6 +1103,20 @@ cc_status cc_build_vvvv_packed(int o, int v, int L, cc_dtype dtype, const void *
     return CC_OK;
 }
 
+cc_status cc_selftest_wait_timeout(long long budget_cycles) {
+    if (budget_cycles < 1000 || budget_cycles > 4000000000LL)
+        return fail(CC_ERR_INVALID_ARG, "budget_cycles must be in [1e3, 4e9]");
+    int *d = nullptr, h = -1;
+    CC_CUDA(cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) e = launch_wait_selftest(budget_cycles, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CC_ERR_CUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+    if (h == 1) return fail(CC_ERR_TIMEOUT, "the bounded wait gave up as designed");
+    return fail(CC_ERR_CUDA, "the never-satisfied wait did not time out");
+}
+
 cc_status cc_integral_block_elems(int o, int v, size_t elems[6]) {
     if (o < 1 || v < 1 || !elems) return fail(CC_ERR_INVALID_ARG, "bad arguments");
     for (int b = 0; b < 6; b++) {

@@ -145,6 +145,8 @@ cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double 
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
                                  double alpha, double beta, double *C, cudaStream_t s);
 cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s);
+// one CTA whose mbarrier wait is never satisfied: *timed_out = 1 after budget_cycles
+cudaError_t launch_wait_selftest(long long budget_cycles, int *timed_out, cudaStream_t s);
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s);
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C,
                            double *partials, int *err_flag, cudaStream_t s);

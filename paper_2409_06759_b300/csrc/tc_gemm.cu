@@ -202,12 +202,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // false when the budget runs out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget = kWaitBudget) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitBudget) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
+}
+
+// Self-test of the bounded wait: an mbarrier that expects one arrival nobody
+// makes.  The wait gives up after `budget` cycles and the kernel records it and
+// returns normally (nothing is in flight).
+__global__ void wait_selftest_kernel(long long budget, int *timed_out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) *timed_out = mbar_wait(&bar, 0, budget) ? 0 : 1;
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
@@ -982,6 +993,12 @@ static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void
 }
 
 }  // namespace tc
+
+cudaError_t launch_wait_selftest(long long budget_cycles, int *timed_out, cudaStream_t s) {
+    if (budget_cycles < 0 || budget_cycles > tc::kWaitBudget) return cudaErrorInvalidValue;
+    tc::wait_selftest_kernel<<<1, 32, 0, s>>>(budget_cycles, timed_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C, double *partials,
                            int *err_flag, cudaStream_t s) {

@@ -186,3 +186,7 @@ def test_packed_pairs_reject_complex(cc):
     with pytest.raises(cc.CCError) as ei:
         cc.cc_plan_create(cc.load_list("ccsd_packed"), 3, 5, dtype=cc.CC_C128)
     assert "real" in str(ei.value)
+
+
+def test_wait_selftest_budget_checked_before_device_work(cc):
+    assert cc.cc_selftest_wait_timeout(10) == 1          # CC_ERR_INVALID_ARG
