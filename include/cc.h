@@ -231,7 +231,8 @@ CC_API cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opt
  * oldest vector dropped while a pivot is below 1e-14).
  *   amps: in = start (zeros give MP2 at k = 1); out = the converged x_k, or,
  *   when max_iter ends the call, the next iterate x_{k+1} (resume = 1 continues
- *   from it with the DIIS history kept in ws).
+ *   from it with the DIIS history and the static integral caches kept in ws:
+ *   resume only with the same integrals, plan and ws).
  * With refine_plan (an FP64 plan of the same system), iterations run on `plan`
  * until |R| < max(switch_tol, tol) or |R| stops improving for two iterations;
  * then the DIIS history restarts and the iteration turns defect-corrected: an

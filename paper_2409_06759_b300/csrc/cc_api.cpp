@@ -573,8 +573,12 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     if (!h_scal) CC_CUDA(cudaMallocHost(&h_scal, 128));
     if (report) { report->iterations = 0; report->converged = 0; report->switched_at = -1; }
     const int cplx = P.dtype == CC_C128;
-    plan->cache_filled = false;
-    if (refine) refine->cache_filled = false;
+    // the static caches (permuted and split integral blocks) are rebuilt at the
+    // start of a solve; a resumed solve continues with them
+    if (!o.resume) {
+        plan->cache_filled = false;
+        if (refine) refine->cache_filled = false;
+    }
     g_err.clear();
     cc_status result = CC_ERR_NOT_CONVERGED;
     double last_e = NAN, last_ei = NAN, last_rn = NAN;
