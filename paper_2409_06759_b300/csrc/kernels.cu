@@ -173,32 +173,47 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
 
 // Two-source accumulate (outer products with permutation operators): one warp
 // per output row (all dims but the innermost), lanes along the innermost dim;
-// each term's row offsets are formed once per row.
-template <typename T>
+// each term's row offsets are formed once per row and kept in registers
+// (NP: the term count rounded up to 1, 2, 4 or 8).
+template <typename T, int NP>
 __global__ void __launch_bounds__(256) accum_outer_rows_kernel(const AccumDesc d, const T *__restrict__ src,
                                                                const T *__restrict__ src2, T *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int d0 = d.nd - 1;
     const int64_t E0 = d.ext[d0], rows = d.total / E0;
     const int64_t w0 = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), nw = (int64_t)gridDim.x * 8;
+    int64_t s0[NP], s02[NP];
+    double sg[NP];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        s0[p] = p < d.nperm ? d.sstr[p][d0] : 0;
+        s02[p] = p < d.nperm ? d.sstr2[p][d0] : 0;
+        sg[p] = p < d.nperm ? d.sign[p] : 0.0;
+    }
+    const int64_t os0 = d.ostr[d0];
     for (int64_t row = w0; row < rows; row += nw) {
-        int64_t x = row, obase = 0, sb[kMaxPerms], sb2[kMaxPerms];
-        for (int p = 0; p < d.nperm; p++) sb[p] = sb2[p] = 0;
+        int64_t x = row, obase = 0, sb[NP], sb2[NP];
+#pragma unroll
+        for (int p = 0; p < NP; p++) sb[p] = sb2[p] = 0;
         for (int k = d0 - 1; k >= 0; k--) {
             const int64_t dig = x % d.ext[k];
             x /= d.ext[k];
             obase += dig * d.ostr[k];
-            for (int p = 0; p < d.nperm; p++) {
-                sb[p] += dig * d.sstr[p][k];
-                sb2[p] += dig * d.sstr2[p][k];
-            }
+#pragma unroll
+            for (int p = 0; p < NP; p++)
+                if (p < d.nperm) {
+                    sb[p] += dig * d.sstr[p][k];
+                    sb2[p] += dig * d.sstr2[p][k];
+                }
         }
         for (int64_t i = lane; i < E0; i += 32) {
             T acc = zero<T>();
-            for (int p = 0; p < d.nperm; p++)
-                acc = axpy(d.sign[p], mul(cj(ld(src + sb[p] + i * d.sstr[p][d0]), d.conj_a),
-                                          cj(ld(src2 + sb2[p] + i * d.sstr2[p][d0]), d.conj_b)), acc);
-            T *o = out + obase + i * d.ostr[d0];
+#pragma unroll
+            for (int p = 0; p < NP; p++)
+                if (p < d.nperm)
+                    acc = axpy(sg[p], mul(cj(ld(src + sb[p] + i * s0[p]), d.conj_a),
+                                          cj(ld(src2 + sb2[p] + i * s02[p]), d.conj_b)), acc);
+            T *o = out + obase + i * os0;
             T val = scal(d.alpha, acc);
             if (d.beta != 0.0) val = axpy(d.beta, *o, val);
             *o = val;
@@ -207,12 +222,25 @@ __global__ void __launch_bounds__(256) accum_outer_rows_kernel(const AccumDesc d
 }
 
 template <typename T>
+static cudaError_t accum_generic(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
+    int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
+    int64_t blocks = (runs + 7) / 8;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    accum_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, src, out, src2);
+    return cudaGetLastError();
+}
+
+template <typename T>
 static cudaError_t accum_t(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
     if (d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 32) {
         const int64_t rows = d.total / d.ext[d.nd - 1];
         int64_t blocks = (rows + 7) / 8;
         if (blocks > 148 * 16) blocks = 148 * 16;
-        accum_outer_rows_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
+        if (d.nperm <= 1) accum_outer_rows_kernel<T, 1><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
+        else if (d.nperm <= 2) accum_outer_rows_kernel<T, 2><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
+        else if (d.nperm <= 4) accum_outer_rows_kernel<T, 4><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
+        else if (d.nperm <= 8) accum_outer_rows_kernel<T, 8><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
+        else return accum_generic(d, src, out, s, src2);
         return cudaGetLastError();
     }
     // tiled path: the output's innermost dim and a partner dim both of extent >= 16
@@ -244,11 +272,7 @@ static cudaError_t accum_t(const AccumDesc &d, const T *src, T *out, cudaStream_
             }
         }
     }
-    int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
-    int64_t blocks = (runs + 7) / 8;
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    accum_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, src, out, src2);
-    return cudaGetLastError();
+    return accum_generic(d, src, out, s, src2);
 }
 
 cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s, const double *src2) {

@@ -462,9 +462,11 @@ __global__ void __launch_bounds__(192, 1)
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... of the (tile, K-slice) space.
 // The producer streams K blocks of consecutive tiles through the stage ring
 // without a break; the MMA issuer alternates between two TMEM accumulators so
-// the epilogue of one tile overlaps the main loop of the next.
+// the epilogue of one tile overlaps the main loop of the next.  Eight epilogue
+// warps (2..9): warp w reads TMEM lanes 32*(w%4).. and the column half (w-2)/4
+// of the tile, so twice as many output loads are in flight as with four.
 template <int NP, int BN, int STAGES>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                               const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials,
                               int kb_per_split, int nslices, int64_t ntiles, int *err_flag) {
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 4);              // one arrival per epilogue warp
+            mbar_init(&acce[b], 8);              // one arrival per epilogue warp
         }
         *abort_flag = 0;
         *epi_abort = 0;
@@ -594,7 +596,8 @@ __global__ void __launch_bounds__(192, 1)
         __syncwarp();
     } else {
         const int q = warp & 3;
-        const int et = threadIdx.x - 64;         // 0..127
+        const int half = (warp - 2) >> 2;        // column half of the tile
+        const int et = threadIdx.x - 64;         // 0..255
         int j = 0;
         for (int64_t t = blockIdx.x; t < total; t += gridDim.x, j++) {
             int64_t m0, n0;
@@ -602,21 +605,21 @@ __global__ void __launch_bounds__(192, 1)
             tile_coords(t, m0, n0, kb0, kb1);
             const int b = j & 1;
             const bool split = nslices > 1;
-            asm volatile("bar.sync 1, 128;" ::: "memory");   // previous tile's coloff reads are done
-            for (int c = et; c < BN; c += 128) {
+            asm volatile("bar.sync 1, 256;" ::: "memory");   // previous tile's coloff reads are done
+            for (int c = et; c < BN; c += 256) {
                 const int64_t n = n0 + c;
                 coloff[c] = n < d.N ? (split ? n : grp_off(d.cn, n)) : -1;
             }
             const int64_t m = m0 + q * 32 + lane;
             const bool mok = m < d.M;
             const int64_t roff = mok ? (split ? 0 : grp_off(d.cm, m)) : 0;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, 256;" ::: "memory");
             bool ok = mbar_wait(&accf[b], (uint32_t)(j >> 1) & 1u);
             fence_after();
             ok = __all_sync(0xffffffffu, ok && !*abort_flag);
             if (!ok) *epi_abort = 1;
-            // all four epilogue warps take the same decision (only they write epi_abort)
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            // all eight epilogue warps take the same decision (only they write epi_abort)
+            asm volatile("bar.sync 1, 256;" ::: "memory");
             if (*epi_abort) {
                 *abort_flag = 1;
                 if (lane == 0) atomicOr(err_flag, 1);
@@ -624,7 +627,8 @@ __global__ void __launch_bounds__(192, 1)
             }
             double *P = split ? partials + (t / ntiles) * d.M * d.N : nullptr;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int cc = 0; cc < BN / 2; cc += 32) {
+                const int c0 = half * (BN / 2) + cc;
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), r);
                 tmem_ld_wait();
@@ -636,16 +640,21 @@ __global__ void __launch_bounds__(192, 1)
                             if (n >= 0) P[n * d.M + m] = (double)__uint_as_float(r[jj]);
                         }
                     } else {
-                        double old[32];
+                        // read-modify-write in two batches of 16 (loads issued before the stores)
 #pragma unroll
-                        for (int jj = 0; jj < 32; jj++) {
-                            const int64_t co = coloff[c0 + jj];
-                            old[jj] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
-                        }
+                        for (int h = 0; h < 32; h += 16) {
+                            double old[16];
 #pragma unroll
-                        for (int jj = 0; jj < 32; jj++) {
-                            const int64_t co = coloff[c0 + jj];
-                            if (co >= 0) C[roff + co] = d.alpha * (double)__uint_as_float(r[jj]) + d.beta * old[jj];
+                            for (int jj = 0; jj < 16; jj++) {
+                                const int64_t co = coloff[c0 + h + jj];
+                                old[jj] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
+                            }
+#pragma unroll
+                            for (int jj = 0; jj < 16; jj++) {
+                                const int64_t co = coloff[c0 + h + jj];
+                                if (co >= 0)
+                                    C[roff + co] = d.alpha * (double)__uint_as_float(r[h + jj]) + d.beta * old[jj];
+                            }
                         }
                     }
                 }
@@ -956,7 +965,7 @@ static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const v
     if (zs > 1 && !partials) return cudaErrorInvalidValue;
     const int64_t total = ntiles * zs;
     const int grid = (int)(total < 148 ? total : 148);
-    tc_gemm_persistent_kernel<NP, BN, STAGES><<<grid, 192, G::SMEM, s>>>(ma, mb, d, C, partials, per, zs, ntiles, err);
+    tc_gemm_persistent_kernel<NP, BN, STAGES><<<grid, 320, G::SMEM, s>>>(ma, mb, d, C, partials, per, zs, ntiles, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || zs == 1) return e;
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
