@@ -435,6 +435,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ref-samples", type=int, default=2)
     ap.add_argument("--dtype", default="f64", choices=["f64", "c128"])
+    ap.add_argument("--no-tune", action="store_true", help="skip cc_plan_autotune on the timed plan")
     ap.add_argument("--packed", action="store_true",
                     help="lists with packed index pairs (ladder over e<f; flops counted packed)")
     ap.add_argument("--workload", default="ccsd", choices=["ccsd", "ccsdt", "batched"],
@@ -486,6 +487,15 @@ def main():
     stream = torch.cuda.current_stream(dev)
     z = lambda: (torch.zeros(o, v, dtype=tdt, device=dev),
                  torch.zeros(o, o, v, v, dtype=tdt, device=dev))
+
+    # tile widths and split-K factors of the mixed plan picked by timing (cc_plan_autotune)
+    t_tune = None
+    if not args.no_tune:
+        tt = time.perf_counter()
+        mixed.autotune(*z(), reps=3, stream=stream)
+        mixed.release()
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - tt
 
     # ---- device-timed steps on the split-bf16 plan
     t1, t2 = z()
@@ -571,7 +581,7 @@ def main():
                        "flops_counted": "packed (pair-count) flops" if args.packed else "unpacked flops",
                        "l2": "inputs larger than L2 (<ab||ef> split planes %.1f GB, T2 %d MB)"
                              % (6.4 * (2 if cplx else 1), 512 * (2 if cplx else 1)),
-                       "integral_build_s": t_int, "integral_bytes": int_bytes},
+                       "integral_build_s": t_int, "integral_bytes": int_bytes, "autotune_s": t_tune},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
