@@ -315,6 +315,12 @@ CC_API cc_status cc_energy_noalloc(int o, int v, const cc_integrals *ints, const
  * Allocates and frees 4 bytes of device memory and synchronises. */
 CC_API cc_status cc_selftest_wait_timeout(long long budget_cycles);
 
+/* cc_selftest_convert -- the split kernels' double -> float rounding (integer
+ * pipe, round to nearest even) next to the library conversion, for testing:
+ * in: device double[n]; mine, ref: device float[n].  Synchronises.
+ * Diagnostic; the paper has no counterpart. */
+CC_API cc_status cc_selftest_convert(const double *in, long long n, float *mine, float *ref);
+
 CC_API const char *cc_status_string(cc_status s);
 CC_API const char *cc_last_error(void);
 

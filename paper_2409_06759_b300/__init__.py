@@ -34,7 +34,7 @@ EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_
            "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_status_string",
            "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched",
            "cc_plan_autotune", "cc_build_vvvv_packed_workspace_bytes", "cc_build_vvvv_packed",
-           "cc_selftest_wait_timeout"]
+           "cc_selftest_wait_timeout", "cc_selftest_convert"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libccb300.so is not built ({LIB_PATH}); run paper_2409_06759_b300/build.py "
@@ -102,6 +102,7 @@ _sig = {
     "cc_build_vvvv_packed_workspace_bytes": (c_int, [c_int, c_int, c_int, c_int, _P(c_size_t)]),
     "cc_build_vvvv_packed": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "cc_selftest_wait_timeout": (c_int, [ctypes.c_longlong]),
+    "cc_selftest_convert": (c_int, [c_void_p, ctypes.c_longlong, c_void_p, c_void_p]),
     "cc_status_string": (ctypes.c_char_p, [c_int]),
     "cc_last_error": (ctypes.c_char_p, []),
     "cc_version": (ctypes.c_char_p, []),
@@ -397,3 +398,8 @@ def cc_build_vvvv_packed(o: int, v: int, L: int, B, out, ws, dtype: int = CC_F64
 def cc_selftest_wait_timeout(budget_cycles: int = 2_000_000) -> int:
     """Runs the bounded-wait self-test; returns the status (CC_ERR_TIMEOUT = 8 expected)."""
     return _lib.cc_selftest_wait_timeout(budget_cycles)
+
+
+def cc_selftest_convert(x, mine, ref):
+    """The split kernels' double -> float rounding and the library's, into mine / ref."""
+    _check(_lib.cc_selftest_convert(_ptr(x), x.numel(), _ptr(mine), _ptr(ref)), "cc_selftest_convert")

@@ -246,7 +246,7 @@ struct SolverLayout {
     int64_t nx = 0;                 // elements of x = concatenation of the ranks in use
     int64_t r_off[4] = {0, 0, 0, 0};
     int64_t hist_x = 0, hist_e = 0; // diis_max vectors of nx each
-    int64_t gram = 0, coef = 0, used = 0, scal = 0, partials = 0, delta = 0;
+    int64_t gram = 0, coef = 0, used = 0, scal = 0, partials = 0, delta = 0, dinv = 0;
     int64_t bytes = 0;
     int diis = 0;
 };
@@ -267,6 +267,8 @@ SolverLayout solver_layout(const Plan &P, int diis_max) {
     L.hist_e = off;
     off += al((int64_t)L.diis * L.nx * 8);
     L.delta = off;
+    off += al(L.nx * 8);
+    L.dinv = off;                   // 1/D of every amplitude (Jacobi), set at the start of a solve
     off += al(L.nx * 8);
     L.gram = off; off += al(256 * 8);
     L.coef = off; off += al(16 * 8);
@@ -591,6 +593,16 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
             if (r[l]) { dlr[l] = dl + off; off += L.n[l]; }
     }
     cc_resid Rd{dlr[1], dlr[2], dlr[3]};
+    double *dinv = (double *)(sreg + L.dinv);
+    {
+        int64_t off = 0;
+        for (int l = 1; l <= 3; l++) {
+            if (!r[l]) continue;
+            CC_CUDA(launch_inv_denominators(l, o_, v_, ints->f_occ, ints->f_vir, dinv + off, cplx, s));
+            plan->launches++;
+            off += L.n[l];
+        }
+    }
     for (k = 0; k < o.max_iter; k++) {
         const bool corrected = S.phase == 1 && refine != nullptr;
         const bool outer = corrected && S.inner == 0;
@@ -687,7 +699,7 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         int64_t off = 0;
         for (int l = 1; l <= 3; l++) {
             if (!r[l]) continue;
-            CC_CUDA(launch_jacobi(l, o_, v_, ints->f_occ, ints->f_vir, t[l], r[l], xs + off, es + off, cplx, s));
+            CC_CUDA(launch_jacobi_inv(L.n[l], t[l], r[l], dinv + off, xs + off, es + off, s));
             plan->launches++;
             off += L.n[l];
         }
@@ -1104,6 +1116,13 @@ cc_status cc_build_vvvv_packed(int o, int v, int L, cc_dtype dtype, const void *
         pd.pbase = a0;
         CC_CUDA(launch_pack_pairs(pd, S, (double *)out + pd.row0 * P, s));
     }
+    return CC_OK;
+}
+
+cc_status cc_selftest_convert(const double *in, long long n, float *mine, float *ref) {
+    if (!in || !mine || !ref || n < 0) return fail(CC_ERR_INVALID_ARG, "bad arguments");
+    CC_CUDA(launch_convert_selftest(in, n, mine, ref, nullptr));
+    CC_CUDA(cudaDeviceSynchronize());
     return CC_OK;
 }
 

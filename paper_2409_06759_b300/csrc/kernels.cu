@@ -40,6 +40,28 @@ __device__ __forceinline__ double up(double x) { return x; }
 __device__ __forceinline__ double up(float x) { return (double)x; }
 __device__ __forceinline__ double2 up(double2 x) { return x; }
 __device__ __forceinline__ float cfma(float a, float b, float acc) { return fmaf(a, b, acc); }
+// B300's FP64 pipe issues ~2 operations per clock per SM: the elementwise
+// kernels spend at most one FP64 operation per term.  A +-1 sign is an add or
+// a subtract (the first term a free negation); alpha = +-1 and beta in {0, 1}
+// cost nothing or one add.
+__device__ __forceinline__ double neg(double x) { return -x; }
+__device__ __forceinline__ double2 neg(double2 x) { return make_double2(-x.x, -x.y); }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double sub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// acc (+|-) x, the first term taken as +-x
+template <typename T> __device__ __forceinline__ T signed_term(bool first, double sign, T x, T acc) {
+    if (first) return sign < 0.0 ? neg(x) : x;
+    return sign < 0.0 ? sub(acc, x) : add(acc, x);
+}
+// alpha * acc + beta * old with the cheap cases folded
+template <typename T> __device__ __forceinline__ T finish(double alpha, T acc, double beta, const T *o) {
+    T v = alpha == 1.0 ? acc : alpha == -1.0 ? neg(acc) : scal(alpha, acc);
+    if (beta == 1.0) return add(v, *o);
+    if (beta != 0.0) return axpy(beta, *o, v);
+    return v;
+}
 // acc + a * b over complex (or real) numbers
 __device__ __forceinline__ double cfma(double a, double b, double acc) { return fma(a, b, acc); }
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
@@ -87,11 +109,9 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
                     for (int k = 0; k < d.nd; k++) so2 += dig[k] * d.sstr2[p][k];
                     x = mul(x, cj(ld(src2 + so2), d.conj_b));
                 }
-                acc = axpy(d.sign[p], x, acc);
+                acc = signed_term(p == 0, d.sign[p], x, acc);
             }
-            T val = scal(d.alpha, acc);
-            if (d.beta != 0.0) val = axpy(d.beta, out[oo], val);
-            out[oo] = val;
+            out[oo] = finish(d.alpha, acc, d.beta, out + oo);
             // advance by 32 elements (compare-and-subtract carries)
             e += 32;
             int carry = 32;
@@ -133,6 +153,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
     const int64_t i0b = t0 * 32, i1b = t1 * 32;
     const int64_t E0 = d.ext[d0], E1 = d.ext[d1];
     T acc[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
+    // rows of the tile outside the box never have their values stored
     for (int p = 0; p < d.nperm; p++) {
         const int64_t s0 = d.sstr[p][d0], s1 = d.sstr[p][d1];
         const int64_t base = sbase[p] + i0b * s0 + i1b * s1;
@@ -141,7 +162,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
             for (int r = 0; r < 4; r++) {
                 const int64_t i1 = ty + 8 * r;
                 if (i0b + tx < E0 && i1b + i1 < E1)
-                    acc[r] = axpy(d.sign[p], cj(ld(src + base + tx * s0 + i1 * s1), d.conj_a), acc[r]);
+                    acc[r] = signed_term(p == 0, d.sign[p], cj(ld(src + base + tx * s0 + i1 * s1), d.conj_a), acc[r]);
             }
         } else {
             __syncthreads();
@@ -152,7 +173,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
             }
             __syncthreads();
 #pragma unroll
-            for (int r = 0; r < 4; r++) acc[r] = axpy(d.sign[p], cj(sm[ty + 8 * r][tx], d.conj_a), acc[r]);
+            for (int r = 0; r < 4; r++) acc[r] = signed_term(p == 0, d.sign[p], cj(sm[ty + 8 * r][tx], d.conj_a), acc[r]);
         }
     }
     const int64_t os0 = d.ostr[d0], os1 = d.ostr[d1];
@@ -167,7 +188,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
     for (int r = 0; r < 4; r++) {
         const int64_t i1 = ty + 8 * r;
         if (i0b + tx < E0 && i1b + i1 < E1)
-            out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = axpy(d.beta, old[r], scal(d.alpha, acc[r]));
+            out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = finish(d.alpha, acc[r], d.beta, &old[r]);
     }
 }
 
@@ -178,6 +199,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) accum_outer_rows_kernel(const AccumDesc d, const T *__restrict__ src,
                                                                const T *__restrict__ src2, T *__restrict__ out) {
+    constexpr int RCH = 16;                      // consecutive rows per warp: one decomposition, then steps
     const int lane = threadIdx.x & 31;
     const int d0 = d.nd - 1;
     const int64_t E0 = d.ext[d0], rows = d.total / E0;
@@ -191,32 +213,60 @@ __global__ void __launch_bounds__(256) accum_outer_rows_kernel(const AccumDesc d
         sg[p] = p < d.nperm ? d.sign[p] : 0.0;
     }
     const int64_t os0 = d.ostr[d0];
-    for (int64_t row = w0; row < rows; row += nw) {
-        int64_t x = row, obase = 0, sb[NP], sb2[NP];
+    for (int64_t c = w0; c * RCH < rows; c += nw) {
+        const int64_t r0 = c * RCH;
+        // row digits of r0 (rows < 2^32: 32-bit divisions)
+        uint32_t dig[kMaxDims];
+        int64_t obase = 0, sb[NP], sb2[NP];
 #pragma unroll
         for (int p = 0; p < NP; p++) sb[p] = sb2[p] = 0;
+        uint32_t x = (uint32_t)r0;
         for (int k = d0 - 1; k >= 0; k--) {
-            const int64_t dig = x % d.ext[k];
-            x /= d.ext[k];
-            obase += dig * d.ostr[k];
+            const uint32_t e = (uint32_t)d.ext[k], q = x / e;
+            dig[k] = x - q * e;
+            x = q;
+            obase += (int64_t)dig[k] * d.ostr[k];
 #pragma unroll
             for (int p = 0; p < NP; p++)
                 if (p < d.nperm) {
-                    sb[p] += dig * d.sstr[p][k];
-                    sb2[p] += dig * d.sstr2[p][k];
+                    sb[p] += (int64_t)dig[k] * d.sstr[p][k];
+                    sb2[p] += (int64_t)dig[k] * d.sstr2[p][k];
                 }
         }
-        for (int64_t i = lane; i < E0; i += 32) {
-            T acc = zero<T>();
+        const int nr = rows - r0 < RCH ? (int)(rows - r0) : RCH;
+        for (int rr = 0; rr < nr; rr++) {
+            for (int64_t i = lane; i < E0; i += 32) {
+                T acc = zero<T>();
 #pragma unroll
-            for (int p = 0; p < NP; p++)
-                if (p < d.nperm)
-                    acc = axpy(sg[p], mul(cj(ld(src + sb[p] + i * s0[p]), d.conj_a),
-                                          cj(ld(src2 + sb2[p] + i * s02[p]), d.conj_b)), acc);
-            T *o = out + obase + i * os0;
-            T val = scal(d.alpha, acc);
-            if (d.beta != 0.0) val = axpy(d.beta, *o, val);
-            *o = val;
+                for (int p = 0; p < NP; p++)
+                    if (p < d.nperm) {
+                        const T a = cj(ld(src + sb[p] + i * s0[p]), d.conj_a);
+                        const T b = cj(ld(src2 + sb2[p] + i * s02[p]), d.conj_b);
+                        // one product per term, the sign folded into it
+                        acc = p == 0 ? mul(sg[p] < 0.0 ? neg(a) : a, b) : cfma(sg[p] < 0.0 ? neg(a) : a, b, acc);
+                    }
+                T *o = out + obase + i * os0;
+                *o = finish(d.alpha, acc, d.beta, o);
+            }
+            // next row: odometer step with carries
+            for (int k = d0 - 1; k >= 0; k--) {
+                obase += d.ostr[k];
+#pragma unroll
+                for (int p = 0; p < NP; p++)
+                    if (p < d.nperm) {
+                        sb[p] += d.sstr[p][k];
+                        sb2[p] += d.sstr2[p][k];
+                    }
+                if (++dig[k] < (uint32_t)d.ext[k]) break;
+                dig[k] = 0;
+                obase -= d.ext[k] * d.ostr[k];
+#pragma unroll
+                for (int p = 0; p < NP; p++)
+                    if (p < d.nperm) {
+                        sb[p] -= d.ext[k] * d.sstr[p][k];
+                        sb2[p] -= d.ext[k] * d.sstr2[p][k];
+                    }
+            }
         }
     }
 }
@@ -232,9 +282,9 @@ static cudaError_t accum_generic(const AccumDesc &d, const T *src, T *out, cudaS
 
 template <typename T>
 static cudaError_t accum_t(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
-    if (d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 32) {
+    if (d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 32 && d.total / d.ext[d.nd - 1] < 0xffffffffLL) {
         const int64_t rows = d.total / d.ext[d.nd - 1];
-        int64_t blocks = (rows + 7) / 8;
+        int64_t blocks = (rows / 16 + 8) / 8;
         if (blocks > 148 * 16) blocks = 148 * 16;
         if (d.nperm <= 1) accum_outer_rows_kernel<T, 1><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
         else if (d.nperm <= 2) accum_outer_rows_kernel<T, 2><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
@@ -569,9 +619,6 @@ __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_
 __device__ __forceinline__ double2 shfl_xor(double2 v, int o) {
     return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
-__device__ __forceinline__ double add(double a, double b) { return a + b; }
-__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-
 template <typename T>
 __global__ void __launch_bounds__(256) gemv_rowwarp_kernel(int64_t R, int64_t K, const T *__restrict__ X, int64_t sr,
                                                            const T *__restrict__ x, int64_t incx, const Grp gy,
@@ -800,6 +847,46 @@ cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double
     rows_cols(rank, o, v, rows, nvt);
     int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
     jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, rows, nvt, cplx ? 1 : 0);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) inv_denominators_kernel(int rank, int o, int v, const double *fo,
+                                                                const double *fv, double *out, int64_t rows,
+                                                                uint32_t nvt, int cplx) {
+    const uint32_t ncol = nvt << cplx;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const double so = occ_sum(rank, o, fo, row);
+        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x)
+            out[row * ncol + c] = 1.0 / (so - vir_sum(rank, v, fv, c >> cplx));
+    }
+}
+
+cudaError_t launch_inv_denominators(int rank, int o, int v, const double *fo, const double *fv, double *out, int cplx,
+                                    cudaStream_t s) {
+    int64_t rows;
+    uint32_t nvt;
+    rows_cols(rank, o, v, rows, nvt);
+    int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
+    inv_denominators_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, out, rows, nvt, cplx ? 1 : 0);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) jacobi_inv_kernel(int64_t n, const double *__restrict__ t,
+                                                         const double *__restrict__ r, const double *__restrict__ dinv,
+                                                         double *__restrict__ xo, double *__restrict__ eo) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double q = r[e] * dinv[e];
+        eo[e] = q;
+        xo[e] = t[e] + q;
+    }
+}
+
+cudaError_t launch_jacobi_inv(int64_t n, const double *t, const double *r, const double *dinv, double *xo, double *eo,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    jacobi_inv_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, t, r, dinv, xo, eo);
     return cudaGetLastError();
 }
 

@@ -145,6 +145,14 @@ cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double 
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
                                  double alpha, double beta, double *C, cudaStream_t s);
 cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s);
+// the split kernels' double -> float rounding (mine) next to the library's (ref)
+cudaError_t launch_convert_selftest(const double *in, int64_t n, float *mine, float *ref, cudaStream_t s);
+// 1/D for rank 1..3 amplitude arrays (complex: the same value on both parts)
+cudaError_t launch_inv_denominators(int rank, int o, int v, const double *fo, const double *fv, double *out, int cplx,
+                                    cudaStream_t s);
+// Jacobi step with precomputed 1/D over n doubles: e = r * dinv, x' = t + e
+cudaError_t launch_jacobi_inv(int64_t n, const double *t, const double *r, const double *dinv, double *xo, double *eo,
+                              cudaStream_t s);
 // one CTA whose mbarrier wait is never satisfied: *timed_out = 1 after budget_cycles
 cudaError_t launch_wait_selftest(long long budget_cycles, int *timed_out, cudaStream_t s);
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s);

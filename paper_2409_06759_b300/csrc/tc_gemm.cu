@@ -31,8 +31,37 @@ __device__ __forceinline__ int64_t grp_off(const Grp &g, int64_t x) {
 // bits, as many as three bf16 planes hold): the remainders x_f - hi and
 // r - mid are exact in FP32, and the FP64 pipe of sm_103a -- a few
 // operations per clock per SM -- is used only for that one conversion.
+// double -> float, round to nearest even, on the integer pipe (B300's FP64
+// pipe, which a conversion instruction would occupy, issues ~2 operations per
+// clock per SM).  IEEE 754 binary64 -> binary32: keep the top 23 of the 52
+// mantissa bits, round on the 29 dropped ones (ties to even; a carry moves into
+// the exponent, up to infinity).  Zeros and double subnormals give +-0; results
+// in the float subnormal or overflow range, infinities and NaNs take the
+// library conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+    const unsigned int sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0) return __uint_as_float(sign);
+    const int ef = e - 1023 + 127;
+    if (ef <= 0 || ef >= 255) return __double2float_rn(x);
+    const unsigned int m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned int rem = lo & 0x1fffffffu;
+    unsigned int f = sign | ((unsigned int)ef << 23) | m;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) f += 1u;
+    return __uint_as_float(f);
+}
+
+__global__ void convert_selftest_kernel(const double *in, int64_t n, float *mine, float *ref) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        mine[e] = f64_to_f32_rn(in[e]);
+        ref[e] = __double2float_rn(in[e]);
+    }
+}
+
 __device__ __forceinline__ void split3(double x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
-    const float xf = __double2float_rn(x);
+    const float xf = f64_to_f32_rn(x);
     h = __float2bfloat16_rn(xf);
     const float r1 = xf - __bfloat162float(h);
     m = __float2bfloat16_rn(r1);
@@ -1002,6 +1031,14 @@ static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void
 }
 
 }  // namespace tc
+
+cudaError_t launch_convert_selftest(const double *in, int64_t n, float *mine, float *ref, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    convert_selftest_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, n, mine, ref);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_wait_selftest(long long budget_cycles, int *timed_out, cudaStream_t s) {
     if (budget_cycles < 0 || budget_cycles > tc::kWaitBudget) return cudaErrorInvalidValue;

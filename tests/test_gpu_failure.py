@@ -33,3 +33,28 @@ def test_bounded_wait_times_out_and_context_survives(cc):
     torch.cuda.synchronize()
     o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
     assert np.abs(r2.cpu().numpy() - o2).max() <= 1e-5 * np.abs(o2).max()
+
+
+def test_split_rounding_matches_the_library_conversion(cc):
+    """The split kernels round double -> float on the integer pipe; the result is
+    bit-identical to the library conversion over normal, tie, carry, tiny,
+    huge, signed-zero and special values."""
+    ccm, _ = cc
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([
+        rng.standard_normal(200000) * 10.0 ** rng.integers(-30, 30, 200000),
+        np.array([0.0, -0.0, 1.0, -1.0, 3.0e38, -3.4028234663852886e38, 3.4028235677973366e38, 1e-38, 1e-40, 1e-46,
+                  5e-324, float("inf"), -float("inf"), float("nan")]),
+        # exact ties between two floats, and values just off them
+        ((2.0 ** 23 + rng.integers(0, 2 ** 23, 4096)) + 0.5) * 2.0 ** rng.integers(-60, 60, 4096).astype(float),
+        1.0 + np.arange(0, 2000) * 2.0 ** -52,
+    ])
+    x = torch.tensor(vals, dtype=torch.float64, device=DEV)
+    mine = torch.empty(x.numel(), dtype=torch.float32, device=DEV)
+    ref = torch.empty_like(mine)
+    ccm.cc_selftest_convert(x, mine, ref)
+    a = mine.cpu().numpy().view(np.uint32)
+    b = ref.cpu().numpy().view(np.uint32)
+    nan = np.isnan(ref.cpu().numpy())
+    assert np.array_equal(a[~nan], b[~nan])
+    assert np.isnan(mine.cpu().numpy()[nan]).all()
