@@ -13,7 +13,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
-SOURCES = ["kernels.cu", "tc_gemm.cu", "no_alloc.cu", "plan.cpp", "cc_api.cpp"]
+SOURCES = ["kernels.cu", "accum.cu", "tc_gemm.cu", "no_alloc.cu", "plan.cpp", "cc_api.cpp"]
 
 
 def _mtime(p: str) -> float:
@@ -22,7 +22,7 @@ def _mtime(p: str) -> float:
 
 def build(verbose: bool = False, force: bool = False, ptxas_v: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "cc.h"))
     newest_header = max(_mtime(h) for h in headers)
     objs = []

@@ -1,0 +1,569 @@
+// accum.cu -- the elementwise half of the TTGT residual (sm_103a): permuted
+// copies, outer products with permutation operators, and the antisymmetrising
+// epilogues out = beta * out + alpha * sum_p sign_p * src[sigma_p(idx)].
+//
+// These steps move whole amplitude-sized arrays (o^2 v^2 doubles) and do a
+// few operations per element, so HBM bandwidth is their roofline.  Two rules
+// follow from B300's shape: keep many independent loads in flight per thread
+// (each kernel issues all of an element batch's loads before its arithmetic),
+// and spend as few FP64 instructions per element as the sum itself needs --
+// the FP64 pipe issues ~2 per clock per SM, so one FP64 instruction per
+// element of a 64M-element array costs ~0.1 ms, the time HBM takes to move
+// 700 MB.  Signs, alpha = +-2^k and beta in {0, 1} therefore cost integer
+// operations or one add (scalar.cuh, fp_bits.cuh).
+//
+// Kernel choice (launch_accum), after merging dims that are contiguous in
+// every operand:
+//   antisym_pairs   out = alpha P(ij) P(ab) src (4 terms, same index order):
+//                   each orbit {ijab, jiab, ijba, jiba} is read and written once
+//   accum_rows      every term reads its sources with stride 0 or 1 along the
+//                   output's innermost dim (copies, outer products T1 x T1)
+//   accum_tiled     some term runs along another dim: 32 x 32 tiles through
+//                   shared memory (TTGT transposes, P(..) gathers)
+//   accum_kernel    anything else (odometer over the flat output index)
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "scalar.cuh"
+
+namespace ccb {
+
+// ------------------------------------------------------------ generic path
+// Each warp owns a contiguous run of 32*kAccChunk output elements; lane l
+// visits run_start + l + 32*j, so stores to a contiguous output coalesce.
+// The multi-index is decomposed once per run and advanced as an odometer.
+constexpr int kAccChunk = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *__restrict__ src,
+                                                    T *__restrict__ out, const T *__restrict__ src2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t run = 32 * kAccChunk;
+    for (int64_t r0 = warp * run; r0 < d.total; r0 += nwarps * run) {
+        int64_t e = r0 + lane;
+        if (e >= d.total) continue;
+        int dig[kMaxDims];
+        {
+            int64_t x = e;
+            for (int k = d.nd - 1; k >= 0; k--) {
+                dig[k] = (int)(x % d.ext[k]);
+                x /= d.ext[k];
+            }
+        }
+        for (int j = 0; j < kAccChunk && e < d.total; j++) {
+            int64_t oo = 0;
+            for (int k = 0; k < d.nd; k++) oo += dig[k] * d.ostr[k];
+            T acc = zero<T>();
+            for (int p = 0; p < d.nperm; p++) {
+                int64_t so = 0;
+                for (int k = 0; k < d.nd; k++) so += dig[k] * d.sstr[p][k];
+                T x = cj(ld(src + so), d.conj_a);
+                if (d.two_src) {
+                    int64_t so2 = 0;
+                    for (int k = 0; k < d.nd; k++) so2 += dig[k] * d.sstr2[p][k];
+                    x = mul(x, cj(ld(src2 + so2), d.conj_b));
+                }
+                acc = signed_term(p == 0, (d.negmask >> p) & 1ull, x, acc);
+            }
+            out[oo] = finish(d.as, acc, d.bcase, d.beta, out + oo);
+            // advance by 32 elements (compare-and-subtract carries)
+            e += 32;
+            int carry = 32;
+            for (int k = d.nd - 1; k >= 0 && carry; k--) {
+                int t = dig[k] + carry;
+                carry = 0;
+                const int ex = (int)d.ext[k];
+                while (t >= ex) { t -= ex; carry++; }
+                dig[k] = t;
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------- row path
+// Work item = (chunk of rch consecutive output rows, block of 32*kRowU
+// columns of the innermost dim d0 = nd-1).  A warp decomposes the chunk's
+// first row once (32-bit divisions; rows < 2^32) and then steps the row
+// digits as an odometer, keeping each term's row offsets in registers; lane l
+// handles columns cb + l + 32u, u < kRowU, with every load of the batch issued
+// before the arithmetic.  NP: the term count rounded up (1, 2, 4, 8).
+constexpr int kRowU = 8;
+
+template <typename T, int NP, bool TWO>
+__global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, const T *__restrict__ src,
+                                                         const T *__restrict__ src2, T *__restrict__ out,
+                                                         uint32_t rows, int rch, uint32_t ncb) {
+    const int lane = threadIdx.x & 31;
+    const int d0 = d.nd - 1;
+    const int64_t E0 = d.ext[d0];
+    int64_t s0[NP], s02[NP];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        s0[p] = p < d.nperm ? d.sstr[p][d0] : 0;
+        s02[p] = (TWO && p < d.nperm) ? d.sstr2[p][d0] : 0;
+    }
+    const int64_t os0 = d.ostr[d0];
+    const uint32_t nchunks = (uint32_t)((rows + (uint32_t)rch - 1) / (uint32_t)rch);
+    const uint64_t items = (uint64_t)nchunks * ncb;
+    for (uint64_t it = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < items; it += (uint64_t)gridDim.x * 8) {
+        const uint32_t chunk = (uint32_t)(it / ncb);
+        const int64_t cb = (int64_t)(it - (uint64_t)chunk * ncb) * (32 * kRowU);
+        const uint32_t r0 = chunk * (uint32_t)rch;
+        // row digits of r0 over dims d0-1 .. 0, unrolled so they live in registers
+        uint32_t dig[kMaxDims - 1];
+        int64_t obase = 0, sb[NP], sb2[NP];
+#pragma unroll
+        for (int p = 0; p < NP; p++) sb[p] = sb2[p] = 0;
+        uint32_t x = r0;
+#pragma unroll
+        for (int k = kMaxDims - 2; k >= 0; k--) {
+            dig[k] = 0;
+            if (k < d0) {
+                const uint32_t e = (uint32_t)d.ext[k], q = x / e;
+                dig[k] = x - q * e;
+                x = q;
+                obase += (int64_t)dig[k] * d.ostr[k];
+#pragma unroll
+                for (int p = 0; p < NP; p++)
+                    if (p < d.nperm) {
+                        sb[p] += (int64_t)dig[k] * d.sstr[p][k];
+                        if (TWO) sb2[p] += (int64_t)dig[k] * d.sstr2[p][k];
+                    }
+            }
+        }
+        const int nr = rows - r0 < (uint32_t)rch ? (int)(rows - r0) : rch;
+        for (int rr = 0; rr < nr; rr++) {
+            T old[kRowU], acc[kRowU];
+#pragma unroll
+            for (int u = 0; u < kRowU; u++) {
+                const int64_t i = cb + lane + 32 * u;
+                old[u] = (d.bcase != 0 && i < E0) ? out[obase + i * os0] : zero<T>();
+            }
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+                if (p >= d.nperm) break;
+                const bool ng = (d.negmask >> p) & 1ull;
+                T a[kRowU], b[kRowU];
+#pragma unroll
+                for (int u = 0; u < kRowU; u++) {
+                    const int64_t i = cb + lane + 32 * u;
+                    a[u] = i < E0 ? cj(ld(src + sb[p] + i * s0[p]), d.conj_a) : zero<T>();
+                    if (TWO) b[u] = i < E0 ? cj(ld(src2 + sb2[p] + i * s02[p]), d.conj_b) : zero<T>();
+                }
+#pragma unroll
+                for (int u = 0; u < kRowU; u++) {
+                    if (TWO) {
+                        const T sa = ng ? neg(a[u]) : a[u];            // the sign rides on a factor
+                        acc[u] = p == 0 ? mul(sa, b[u]) : cfma(sa, b[u], acc[u]);
+                    } else {
+                        acc[u] = signed_term(p == 0, ng, a[u], acc[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kRowU; u++) {
+                const int64_t i = cb + lane + 32 * u;
+                if (i < E0) out[obase + i * os0] = finish(d.as, acc[u], d.bcase, d.beta, &old[u]);
+            }
+            // next row: odometer step with carries
+#pragma unroll
+            for (int k = kMaxDims - 2; k >= 0; k--) {
+                if (k < d0) {
+                    obase += d.ostr[k];
+#pragma unroll
+                    for (int p = 0; p < NP; p++)
+                        if (p < d.nperm) {
+                            sb[p] += d.sstr[p][k];
+                            if (TWO) sb2[p] += d.sstr2[p][k];
+                        }
+                    if (++dig[k] < (uint32_t)d.ext[k]) break;
+                    dig[k] = 0;
+                    obase -= d.ext[k] * d.ostr[k];
+#pragma unroll
+                    for (int p = 0; p < NP; p++)
+                        if (p < d.nperm) {
+                            sb[p] -= d.ext[k] * d.sstr[p][k];
+                            if (TWO) sb2[p] -= d.ext[k] * d.sstr2[p][k];
+                        }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- tiled path
+// 32 x 32 tiles over two output dims, d0 = the innermost output dim and d1 = a
+// dim that carries some term's unit source stride; every other dim is a batch
+// index of the tile.  Each term reads its source tile either directly (lanes
+// along d0) or through shared memory (lanes along d1, then transposed), so
+// reads and writes stay coalesced for the P(..) gathers.  Blocks loop over
+// tiles; tile and batch indices are decomposed with 32-bit divisions.
+template <typename T>
+__global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, const T *__restrict__ src,
+                                                          T *__restrict__ out, int d0, int d1, uint64_t tmask,
+                                                          uint32_t tiles0, uint32_t tiles1, uint32_t ntiles) {
+    __shared__ T sm[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
+    const int64_t E0 = d.ext[d0], E1 = d.ext[d1];
+    const int64_t os0 = d.ostr[d0], os1 = d.ostr[d1];
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint32_t bid = t;
+        const uint32_t t0 = bid % tiles0;
+        bid /= tiles0;
+        const uint32_t t1 = bid % tiles1;
+        bid /= tiles1;
+        // batch digits (all dims except d0, d1), row-major over the remaining dims
+        uint32_t dig[kMaxDims];
+#pragma unroll
+        for (int k = kMaxDims - 1; k >= 0; k--) {
+            dig[k] = 0;
+            if (k < d.nd && k != d0 && k != d1) {
+                const uint32_t e = (uint32_t)d.ext[k], q = bid / e;
+                dig[k] = bid - q * e;
+                bid = q;
+            }
+        }
+        int64_t obase = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxDims; k++)
+            if (k < d.nd) obase += (int64_t)dig[k] * d.ostr[k];
+        const int64_t i0b = (int64_t)t0 * 32, i1b = (int64_t)t1 * 32;
+        T acc[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
+        T old[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t i1 = ty + 8 * r;
+            const bool ok = i0b + tx < E0 && i1b + i1 < E1;
+            old[r] = (d.bcase != 0 && ok) ? out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] : zero<T>();
+        }
+        for (int p = 0; p < d.nperm; p++) {
+            int64_t base = 0;
+#pragma unroll
+            for (int k = 0; k < kMaxDims; k++)
+                if (k < d.nd) base += (int64_t)dig[k] * d.sstr[p][k];     // dig[d0] = dig[d1] = 0
+            const int64_t s0 = d.sstr[p][d0], s1 = d.sstr[p][d1];
+            base += i0b * s0 + i1b * s1;
+            const bool ng = (d.negmask >> p) & 1ull;
+            if (!((tmask >> p) & 1ull)) {
+                T x[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int64_t i1 = ty + 8 * r;
+                    x[r] = (i0b + tx < E0 && i1b + i1 < E1) ? cj(ld(src + base + tx * s0 + i1 * s1), d.conj_a)
+                                                            : zero<T>();
+                }
+#pragma unroll
+                for (int r = 0; r < 4; r++) acc[r] = signed_term(p == 0, ng, x[r], acc[r]);
+            } else {
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int64_t i0 = ty + 8 * r;
+                    sm[tx][i0] = (i1b + tx < E1 && i0b + i0 < E0) ? ld(src + base + tx * s1 + i0 * s0) : zero<T>();
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < 4; r++) acc[r] = signed_term(p == 0, ng, cj(sm[ty + 8 * r][tx], d.conj_a), acc[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t i1 = ty + 8 * r;
+            if (i0b + tx < E0 && i1b + i1 < E1)
+                out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = finish(d.as, acc[r], d.bcase, d.beta, &old[r]);
+        }
+    }
+}
+
+// ------------------------------------------------------ pair antisymmetriser
+// out(i,j,a,b) = beta out + alpha [z(ijab) - z(jiab) - z(ijba) + z(jiba)]
+// with z(i,j,a,b) = src[i S0 + j S1 + a S2 + b S3] and the output addressed by
+// O0..O3 (ext: n1 = ext i = ext j, n2 = ext a = ext b).  The value at ijab
+// fixes the whole orbit: out(jiab) = out(ijba) = -out(ijab), out(jiba) =
+// out(ijab).  A block takes one (i <= j, A <= B) pair of 32-wide a/b tiles,
+// reads the four source tiles once (two of them transposed through shared
+// memory), forms X(a,b) = (z_ij(a,b) - z_ij(b,a)) - (z_ji(a,b) - z_ji(b,a))
+// and writes the four output tiles, so every element of src and out moves
+// once.  i == j and a == b give exact zeros (x - x); A == B and i == j skip
+// the duplicate writes.
+struct PairSym {
+    int64_t n1, n2;
+    int64_t S[4], O[4];
+};
+
+template <typename T>
+__device__ __forceinline__ void pair_store(T *out, int64_t off, T v, const AccumDesc &d) {
+    T o = zero<T>();
+    if (d.bcase != 0) o = out[off];
+    out[off] = d.bcase == 0 ? v : d.bcase == 1 ? add(v, o) : axpy(d.beta, o, v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) antisym_pairs_kernel(const AccumDesc d, const PairSym g,
+                                                            const T *__restrict__ src, T *__restrict__ out,
+                                                            uint32_t nt, uint32_t items) {
+    __shared__ T s1[32][33], s2[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t n2 = g.n2;
+    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+        // item = ((i * n1 + j) * nt + A) * nt + B, only i <= j and A <= B work
+        uint32_t x = it;
+        const uint32_t B = x % nt;
+        x /= nt;
+        const uint32_t A = x % nt;
+        x /= nt;
+        const uint32_t j = x % (uint32_t)g.n1, i = x / (uint32_t)g.n1;
+        if (i > j || A > B) continue;
+        const int64_t a0 = (int64_t)A * 32, b0 = (int64_t)B * 32;
+        const int64_t zij = i * g.S[0] + j * g.S[1], zji = j * g.S[0] + i * g.S[1];
+        const int64_t oij = i * g.O[0] + j * g.O[1], oji = j * g.O[0] + i * g.O[1];
+        T z1[4], z2[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t a = a0 + ty + 8 * r, b = b0 + tx;
+            const bool ok = a < n2 && b < n2;
+            const int64_t off = a * g.S[2] + b * g.S[3];
+            z1[r] = ok ? cj(ld(src + zij + off), d.conj_a) : zero<T>();
+            z2[r] = ok ? cj(ld(src + zji + off), d.conj_a) : zero<T>();
+        }
+        __syncthreads();                    // previous item's reads of s1/s2 are done
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            // s(b', a') = z(., ., b0 + b', a0 + a'), lanes along a'
+            const int64_t bb = b0 + ty + 8 * r, aa = a0 + tx;
+            const bool ok = bb < n2 && aa < n2;
+            const int64_t off = bb * g.S[2] + aa * g.S[3];
+            s1[ty + 8 * r][tx] = ok ? cj(ld(src + zij + off), d.conj_a) : zero<T>();
+            s2[ty + 8 * r][tx] = ok ? cj(ld(src + zji + off), d.conj_a) : zero<T>();
+        }
+        __syncthreads();
+        T X[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            // z(i,j,b,a) for a = a0 + ty + 8r, b = b0 + tx sits at s(b - b0, a - a0)
+            X[r] = scale_f64(sub(sub(z1[r], s1[tx][ty + 8 * r]), sub(z2[r], s2[tx][ty + 8 * r])), d.as);
+        }
+        const bool offdiag = i != j;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t a = a0 + ty + 8 * r, b = b0 + tx;
+            if (a < n2 && b < n2) {
+                const int64_t off = a * g.O[2] + b * g.O[3];
+                pair_store(out, oij + off, X[r], d);
+                if (offdiag) pair_store(out, oji + off, neg(X[r]), d);
+            }
+        }
+        if (A != B) {
+            __syncthreads();                // s1 is reused for X
+#pragma unroll
+            for (int r = 0; r < 4; r++) s1[ty + 8 * r][tx] = X[r];     // s1(a', b') = X(a0 + a', b0 + b')
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                // out(i,j,b,a) = -X(a,b): lanes along a' = tx, b' = ty + 8r
+                const int64_t bb = b0 + ty + 8 * r, aa = a0 + tx;
+                if (bb < n2 && aa < n2) {
+                    const T v = s1[tx][ty + 8 * r];
+                    const int64_t off = bb * g.O[2] + aa * g.O[3];
+                    pair_store(out, oij + off, offdiag ? neg(v) : v, d);
+                    if (offdiag) pair_store(out, oji + off, v, d);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+// Drop unit dims and merge neighbours k, k+1 that are contiguous in the
+// output and in every term's source(s): the kernels then see the fewest dims
+// (a plain copy becomes one dim).
+static void collapse_dims(AccumDesc &d) {
+    int w = 0;
+    for (int k = 0; k < d.nd; k++) {
+        if (d.ext[k] == 1 && d.nd > 1) continue;
+        d.ext[w] = d.ext[k];
+        d.ostr[w] = d.ostr[k];
+        for (int p = 0; p < d.nperm; p++) {
+            d.sstr[p][w] = d.sstr[p][k];
+            if (d.two_src) d.sstr2[p][w] = d.sstr2[p][k];
+        }
+        w++;
+    }
+    if (w == 0) w = 1;
+    d.nd = w;
+    for (int k = d.nd - 2; k >= 0; k--) {
+        const int64_t e = d.ext[k + 1];
+        bool ok = d.ostr[k] == d.ostr[k + 1] * e;
+        for (int p = 0; p < d.nperm && ok; p++) {
+            ok = d.sstr[p][k] == d.sstr[p][k + 1] * e;
+            if (ok && d.two_src) ok = d.sstr2[p][k] == d.sstr2[p][k + 1] * e;
+        }
+        if (!ok) continue;
+        // merge k+1 into k, shift the rest down
+        d.ext[k] *= e;
+        d.ostr[k] = d.ostr[k + 1];
+        for (int p = 0; p < d.nperm; p++) {
+            d.sstr[p][k] = d.sstr[p][k + 1];
+            if (d.two_src) d.sstr2[p][k] = d.sstr2[p][k + 1];
+        }
+        for (int m = k + 1; m + 1 < d.nd; m++) {
+            d.ext[m] = d.ext[m + 1];
+            d.ostr[m] = d.ostr[m + 1];
+            for (int p = 0; p < d.nperm; p++) {
+                d.sstr[p][m] = d.sstr[p][m + 1];
+                if (d.two_src) d.sstr2[p][m] = d.sstr2[p][m + 1];
+            }
+        }
+        d.nd--;
+    }
+}
+
+// Is d the pair antisymmetriser over dims (0,1) and (2,3)?  The term with a
+// +-1 sign taken as base gives S; the other three must be its (01), (23) and
+// (01)(23) swaps with signs -, -, + relative to it.  alpha_sign gets the
+// base's sign.
+static bool match_pair_antisym(const AccumDesc &d, PairSym &g, double &alpha_sign) {
+    if (d.two_src || d.nd != 4 || d.nperm != 4) return false;
+    if (d.ext[0] != d.ext[1] || d.ext[2] != d.ext[3] || d.ext[0] < 1 || d.ext[2] < 1) return false;
+    if (d.ext[0] > 0x7fffffffLL || d.ext[2] > 0x7fffffffLL) return false;
+    for (int p = 0; p < 4; p++)
+        if (d.sign[p] != 1.0 && d.sign[p] != -1.0) return false;
+    const int64_t *S = d.sstr[0];
+    if (S[0] == S[1] || S[2] == S[3]) return false;
+    const double s0 = d.sign[0];
+    bool f01 = false, f23 = false, fb = false;
+    for (int p = 1; p < 4; p++) {
+        const int64_t *Q = d.sstr[p];
+        const double rel = d.sign[p] * s0;
+        if (Q[0] == S[1] && Q[1] == S[0] && Q[2] == S[2] && Q[3] == S[3] && rel < 0) f01 = true;
+        else if (Q[0] == S[0] && Q[1] == S[1] && Q[2] == S[3] && Q[3] == S[2] && rel < 0) f23 = true;
+        else if (Q[0] == S[1] && Q[1] == S[0] && Q[2] == S[3] && Q[3] == S[2] && rel > 0) fb = true;
+        else return false;
+    }
+    if (!(f01 && f23 && fb)) return false;
+    g.n1 = d.ext[0];
+    g.n2 = d.ext[2];
+    for (int k = 0; k < 4; k++) {
+        g.S[k] = S[k];
+        g.O[k] = d.ostr[k];
+    }
+    alpha_sign = s0;
+    return true;
+}
+
+static int64_t grid_cap(int64_t want, int64_t cap) { return want < 1 ? 1 : want > cap ? cap : want; }
+
+template <typename T>
+static cudaError_t accum_generic(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
+    int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
+    accum_kernel<T><<<(unsigned)grid_cap((runs + 7) / 8, 148 * 16), 256, 0, s>>>(d, src, out, src2);
+    return cudaGetLastError();
+}
+
+template <typename T, int NP>
+static cudaError_t rows_launch(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
+    const int64_t E0 = d.ext[d.nd - 1];
+    const int64_t rows = d.total / E0;
+    const int64_t ncb = (E0 + 32 * kRowU - 1) / (32 * kRowU);
+    // about four work items per resident warp (148 SMs x 64 warps), at most 16 rows each
+    int64_t rch = rows * ncb / (148 * 64 * 4);
+    rch = rch < 1 ? 1 : rch > 16 ? 16 : rch;
+    const int64_t items = (rows + rch - 1) / rch * ncb;
+    const unsigned blocks = (unsigned)grid_cap((items + 7) / 8, 148 * 16);
+    if (d.two_src)
+        accum_rows_kernel<T, NP, true><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
+                                                              (uint32_t)ncb);
+    else
+        accum_rows_kernel<T, NP, false><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
+                                                               (uint32_t)ncb);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream_t s, const T *src2) {
+    PairSym g;
+    double sg = 1.0;
+    if (match_pair_antisym(d0, g, sg)) {
+        AccumDesc d = d0;
+        if (sg < 0) {
+            d.alpha = -d.alpha;
+            d.as = make_scale(d.alpha);
+        }
+        const int64_t nt = (g.n2 + 31) / 32;
+        const int64_t items = g.n1 * g.n1 * nt * nt;
+        if (items <= 0xffffffffLL) {
+            antisym_pairs_kernel<T><<<(unsigned)grid_cap(items, 148 * 32), 256, 0, s>>>(d, g, src, out, (uint32_t)nt,
+                                                                                     (uint32_t)items);
+            return cudaGetLastError();
+        }
+    }
+    AccumDesc d = d0;
+    collapse_dims(d);
+    const int dl = d.nd - 1;
+    const int64_t rows = d.total / d.ext[dl];
+    // row path: every source runs with stride 0 or 1 along the innermost output dim
+    bool rowok = d.nperm <= 8 && rows <= 0xffffffffLL && d.ext[dl] >= 8;
+    for (int p = 0; p < d.nperm && rowok; p++) {
+        rowok = d.sstr[p][dl] == 0 || d.sstr[p][dl] == 1;
+        if (rowok && d.two_src) rowok = d.sstr2[p][dl] == 0 || d.sstr2[p][dl] == 1;
+    }
+    for (int k = 0; k < dl && rowok; k++) rowok = d.ext[k] <= 0xffffffffLL;
+    if (rowok) {
+        if (d.nperm <= 1) return rows_launch<T, 1>(d, src, out, s, src2);
+        if (d.nperm <= 2) return rows_launch<T, 2>(d, src, out, s, src2);
+        if (d.nperm <= 4) return rows_launch<T, 4>(d, src, out, s, src2);
+        return rows_launch<T, 8>(d, src, out, s, src2);
+    }
+    // tiled path: the output's innermost dim and a partner dim both of extent >= 16
+    if (!d.two_src && d.nd >= 2 && d.ext[dl] >= 16) {
+        int d1 = -1;
+        uint64_t tmask = 0;
+        // partner: the dim holding a term's smallest source stride, when that is not d0
+        for (int p = 0; p < d.nperm; p++) {
+            int kmin = 0;
+            for (int k = 1; k < d.nd; k++)
+                if (d.ext[k] > 1 && (d.ext[kmin] <= 1 || d.sstr[p][k] < d.sstr[p][kmin])) kmin = k;
+            if (kmin != dl && d.sstr[p][kmin] < d.sstr[p][dl]) {
+                if (d1 < 0) d1 = kmin;
+                if (kmin == d1) tmask |= 1ull << p;
+            }
+        }
+        if (d1 < 0) {
+            // no transposed term: pair d0 with the largest remaining dim
+            for (int k = 0; k < d.nd - 1; k++)
+                if (d1 < 0 || d.ext[k] > d.ext[d1]) d1 = k;
+        }
+        if (d.ext[d1] >= 16) {
+            const int64_t tiles0 = (d.ext[dl] + 31) / 32, tiles1 = (d.ext[d1] + 31) / 32;
+            const int64_t ntiles = tiles0 * tiles1 * (d.total / (d.ext[dl] * d.ext[d1]));
+            bool fits = ntiles <= 0xffffffffLL;
+            for (int k = 0; k < d.nd && fits; k++) fits = d.ext[k] <= 0xffffffffLL;
+            if (fits) {
+                accum_tiled_kernel<T><<<(unsigned)grid_cap(ntiles, 148 * 8), 256, 0, s>>>(
+                    d, src, out, dl, d1, tmask, (uint32_t)tiles0, (uint32_t)tiles1, (uint32_t)ntiles);
+                return cudaGetLastError();
+            }
+        }
+    }
+    return accum_generic(d, src, out, s, src2);
+}
+
+cudaError_t launch_accum(const AccumDesc &d0, const double *src, double *out, cudaStream_t s, const double *src2) {
+    if (d0.total <= 0) return cudaSuccess;
+    if (d0.nd < 1 || d0.nd > kMaxDims || d0.nperm < 1 || d0.nperm > kMaxPerms) return cudaErrorInvalidValue;
+    AccumDesc d = d0;
+    d.negmask = 0;
+    for (int p = 0; p < d.nperm; p++)
+        if (d.sign[p] < 0.0) d.negmask |= 1ull << p;
+    d.as = make_scale(d.alpha);
+    d.bcase = beta_case(d.beta);
+    if (d.cplx)
+        return accum_t<double2>(d, reinterpret_cast<const double2 *>(src), reinterpret_cast<double2 *>(out), s,
+                                reinterpret_cast<const double2 *>(src2));
+    return accum_t<double>(d, src, out, s, src2);
+}
+
+}  // namespace ccb

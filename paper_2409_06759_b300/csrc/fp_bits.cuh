@@ -1,0 +1,81 @@
+// fp_bits.cuh -- conversions and power-of-two scalings done on the integer
+// pipe.  B300 issues FP64 instructions (adds, multiplies, compares and the
+// FP32 <-> FP64 conversions) at ~2 per clock per SM, 1/64 of its FP32 rate, so
+// an elementwise kernel over 64M doubles pays ~0.1 ms per FP64 instruction per
+// element: more than the HBM time of moving those doubles once.  The routines
+// below are exact re-encodings of IEEE-754 bit patterns (no rounding beyond
+// what the formats define) and hand the rare special operands (subnormals,
+// infinities, NaN, results leaving the normal range) to the FP64 instruction.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace ccb {
+
+// double -> float, round to nearest even.  Normal results are formed from the
+// bit pattern: the 29 dropped mantissa bits decide the rounding (ties to the
+// even neighbour; a carry out of the mantissa bumps the exponent, which is the
+// correctly rounded result, infinity included at the top of the range).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+    const unsigned int sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0) return __uint_as_float(sign);             // zero, or a double subnormal (below every float)
+    const int ef = e - 1023 + 127;
+    if (ef <= 0 || ef >= 255) return __double2float_rn(x);
+    const unsigned int m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned int rem = lo & 0x1fffffffu;
+    unsigned int f = sign | ((unsigned int)ef << 23) | m;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) f += 1u;
+    return __uint_as_float(f);
+}
+
+// alpha * (double)f, exact when alpha = +-2^k: a normal float's exponent is
+// rebiased (127 -> 1023) and shifted by k, its 23 mantissa bits move to the
+// top of the double's 52; zeros keep their (flipped) sign.
+__device__ __forceinline__ double f32_to_f64_scaled(float f, const Scale &s) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint32_t flip = s.general ? 0u : s.sflip;
+    uint32_t hi, lo;
+    if (e - 1u < 254u) {
+        const int ee = (int)e + 896 + (s.general ? 0 : s.kexp);
+        hi = ((u & 0x80000000u) ^ flip) | ((uint32_t)ee << 20) | ((u >> 3) & 0xfffffu);
+        lo = u << 29;
+    } else if ((u & 0x7fffffffu) == 0u) {
+        hi = (u & 0x80000000u) ^ flip;
+        lo = 0u;
+    } else {
+        return (double)f * s.value;                        // subnormal, inf, NaN
+    }
+    const double r = __hiloint2double((int)hi, (int)lo);
+    return s.general ? r * s.value : r;
+}
+
+// alpha * x, exact for alpha = +-2^k when x and the result are normal
+// (exponent field shift), and for +-1 or a zero (sign bit); subnormals,
+// inf/NaN and range exits multiply.
+__device__ __forceinline__ double scale_f64(double x, const Scale &s) {
+    if (s.general) return x * s.value;
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const int ee = e + s.kexp;
+    if (e >= 1 && e <= 2046 && ee >= 1 && ee <= 2046)
+        return __hiloint2double((int)((hi + ((uint32_t)s.kexp << 20)) ^ s.sflip), (int)lo);
+    if (s.kexp == 0 || ((hi & 0x7fffffffu) | lo) == 0u)    // +-1, or a zero: sign only
+        return __hiloint2double((int)(hi ^ s.sflip), (int)lo);
+    return x * s.value;
+}
+__device__ __forceinline__ double2 scale_f64(double2 x, const Scale &s) {
+    return make_double2(scale_f64(x.x, s), scale_f64(x.y, s));
+}
+
+// alpha * acc of an epilogue, whatever the accumulator type
+__device__ __forceinline__ double epi_scale(float acc, const Scale &s) { return f32_to_f64_scaled(acc, s); }
+__device__ __forceinline__ double epi_scale(double acc, const Scale &s) { return scale_f64(acc, s); }
+__device__ __forceinline__ double2 epi_scale(double2 acc, const Scale &s) { return scale_f64(acc, s); }
+
+}  // namespace ccb

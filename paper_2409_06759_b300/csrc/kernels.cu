@@ -1,337 +1,13 @@
 // kernels.cu -- FP64 kernels of the TTGT residual path (sm_103a):
-//   accum        generic strided permute / copy / antisymmetrising epilogue
 //   gemm_f64     FP64 SIMT GEMM with generalised (mixed-radix) output addressing
 //   denom/jacobi/energy/dot reductions and the DIIS solve of the iteration
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "scalar.cuh"
 
 namespace ccb {
-
-// ------------------------------------------------------------------ scalars
-// The kernels below are written once over the element type T: double, or
-// double2 holding an interleaved complex double (re, im).
-__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
-__device__ __forceinline__ double2 ld(const double2 *p) { return __ldg(p); }
-__device__ __forceinline__ double cj(double x, int) { return x; }
-__device__ __forceinline__ double2 cj(double2 x, int c) { return c ? make_double2(x.x, -x.y) : x; }
-__device__ __forceinline__ double mul(double a, double b) { return a * b; }
-__device__ __forceinline__ double2 mul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-// acc + s * x, s real
-__device__ __forceinline__ double axpy(double s, double x, double acc) { return fma(s, x, acc); }
-__device__ __forceinline__ double2 axpy(double s, double2 x, double2 acc) {
-    return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
-}
-__device__ __forceinline__ double scal(double s, double x) { return s * x; }
-__device__ __forceinline__ double2 scal(double s, double2 x) { return make_double2(s * x.x, s * x.y); }
-template <typename T> __device__ __forceinline__ T zero();
-template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
-template <> __device__ __forceinline__ double2 zero<double2>() { return make_double2(0.0, 0.0); }
-template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
-// element type T -> compute type CT (FP64 data multiplied in FP32: one rounding) and back
-template <typename CT> __device__ __forceinline__ CT down(double x);
-template <> __device__ __forceinline__ double down<double>(double x) { return x; }
-template <> __device__ __forceinline__ float down<float>(double x) { return __double2float_rn(x); }
-template <typename CT> __device__ __forceinline__ CT down(double2 x) { return x; }
-__device__ __forceinline__ double up(double x) { return x; }
-__device__ __forceinline__ double up(float x) { return (double)x; }
-__device__ __forceinline__ double2 up(double2 x) { return x; }
-__device__ __forceinline__ float cfma(float a, float b, float acc) { return fmaf(a, b, acc); }
-// B300's FP64 pipe issues ~2 operations per clock per SM: the elementwise
-// kernels spend at most one FP64 operation per term.  A +-1 sign is an add or
-// a subtract (the first term a free negation); alpha = +-1 and beta in {0, 1}
-// cost nothing or one add.
-__device__ __forceinline__ double neg(double x) { return -x; }
-__device__ __forceinline__ double2 neg(double2 x) { return make_double2(-x.x, -x.y); }
-__device__ __forceinline__ double add(double a, double b) { return a + b; }
-__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double sub(double a, double b) { return a - b; }
-__device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-// acc (+|-) x, the first term taken as +-x
-template <typename T> __device__ __forceinline__ T signed_term(bool first, double sign, T x, T acc) {
-    if (first) return sign < 0.0 ? neg(x) : x;
-    return sign < 0.0 ? sub(acc, x) : add(acc, x);
-}
-// alpha * acc + beta * old with the cheap cases folded
-template <typename T> __device__ __forceinline__ T finish(double alpha, T acc, double beta, const T *o) {
-    T v = alpha == 1.0 ? acc : alpha == -1.0 ? neg(acc) : scal(alpha, acc);
-    if (beta == 1.0) return add(v, *o);
-    if (beta != 0.0) return axpy(beta, *o, v);
-    return v;
-}
-// acc + a * b over complex (or real) numbers
-__device__ __forceinline__ double cfma(double a, double b, double acc) { return fma(a, b, acc); }
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
-    acc.x = fma(a.x, b.x, acc.x);
-    acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y);
-    acc.y = fma(a.y, b.x, acc.y);
-    return acc;
-}
-
-// ------------------------------------------------------------------ accum
-// Each warp owns a contiguous run of 32*kAccChunk output elements; lane l
-// visits run_start + l + 32*j, so stores to a contiguous output coalesce.
-// The multi-index is decomposed once per run and advanced as an odometer.
-constexpr int kAccChunk = 8;
-
-template <typename T>
-__global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *__restrict__ src,
-                                                    T *__restrict__ out, const T *__restrict__ src2) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t run = 32 * kAccChunk;
-    for (int64_t r0 = warp * run; r0 < d.total; r0 += nwarps * run) {
-        int64_t e = r0 + lane;
-        if (e >= d.total) continue;
-        int dig[kMaxDims];
-        {
-            int64_t x = e;
-            for (int k = d.nd - 1; k >= 0; k--) {
-                dig[k] = (int)(x % d.ext[k]);
-                x /= d.ext[k];
-            }
-        }
-        for (int j = 0; j < kAccChunk && e < d.total; j++) {
-            int64_t oo = 0;
-            for (int k = 0; k < d.nd; k++) oo += dig[k] * d.ostr[k];
-            T acc = zero<T>();
-            for (int p = 0; p < d.nperm; p++) {
-                int64_t so = 0;
-                for (int k = 0; k < d.nd; k++) so += dig[k] * d.sstr[p][k];
-                T x = cj(ld(src + so), d.conj_a);
-                if (d.two_src) {
-                    int64_t so2 = 0;
-                    for (int k = 0; k < d.nd; k++) so2 += dig[k] * d.sstr2[p][k];
-                    x = mul(x, cj(ld(src2 + so2), d.conj_b));
-                }
-                acc = signed_term(p == 0, d.sign[p], x, acc);
-            }
-            out[oo] = finish(d.alpha, acc, d.beta, out + oo);
-            // advance by 32 elements (compare-and-subtract carries)
-            e += 32;
-            int carry = 32;
-            for (int k = d.nd - 1; k >= 0 && carry; k--) {
-                int t = dig[k] + carry;
-                carry = 0;
-                const int ex = (int)d.ext[k];
-                while (t >= ex) { t -= ex; carry++; }
-                dig[k] = t;
-            }
-        }
-    }
-}
-
-// Tiled variant: 32 x 32 tiles over two output dims, d0 = the innermost output
-// dim and d1 = a dim that carries some term's unit source stride; every other
-// dim is a batch index of the block.  Each term reads its source tile either
-// directly (lanes along d0) or through shared memory (lanes along d1, then
-// transposed), so reads and writes stay coalesced for the P(..) gathers.
-template <typename T>
-__global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, const T *__restrict__ src,
-                                                          T *__restrict__ out, int d0, int d1, uint64_t tmask,
-                                                          int64_t tiles0, int64_t tiles1) {
-    __shared__ T sm[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
-    int64_t bid = blockIdx.x;
-    const int64_t t0 = bid % tiles0; bid /= tiles0;
-    const int64_t t1 = bid % tiles1; bid /= tiles1;
-    // batch digits (all dims except d0, d1), row-major over the remaining dims
-    int64_t obase = 0, sbase[kMaxPerms];
-    for (int p = 0; p < d.nperm; p++) sbase[p] = 0;
-    for (int k = d.nd - 1; k >= 0; k--) {
-        if (k == d0 || k == d1) continue;
-        const int64_t dig = bid % d.ext[k];
-        bid /= d.ext[k];
-        obase += dig * d.ostr[k];
-        for (int p = 0; p < d.nperm; p++) sbase[p] += dig * d.sstr[p][k];
-    }
-    const int64_t i0b = t0 * 32, i1b = t1 * 32;
-    const int64_t E0 = d.ext[d0], E1 = d.ext[d1];
-    T acc[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
-    // rows of the tile outside the box never have their values stored
-    for (int p = 0; p < d.nperm; p++) {
-        const int64_t s0 = d.sstr[p][d0], s1 = d.sstr[p][d1];
-        const int64_t base = sbase[p] + i0b * s0 + i1b * s1;
-        if (!((tmask >> p) & 1ull)) {
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int64_t i1 = ty + 8 * r;
-                if (i0b + tx < E0 && i1b + i1 < E1)
-                    acc[r] = signed_term(p == 0, d.sign[p], cj(ld(src + base + tx * s0 + i1 * s1), d.conj_a), acc[r]);
-            }
-        } else {
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int64_t i0 = ty + 8 * r;
-                sm[tx][i0] = (i1b + tx < E1 && i0b + i0 < E0) ? ld(src + base + tx * s1 + i0 * s0) : zero<T>();
-            }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < 4; r++) acc[r] = signed_term(p == 0, d.sign[p], cj(sm[ty + 8 * r][tx], d.conj_a), acc[r]);
-        }
-    }
-    const int64_t os0 = d.ostr[d0], os1 = d.ostr[d1];
-    T old[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-        const int64_t i1 = ty + 8 * r;
-        const bool ok = i0b + tx < E0 && i1b + i1 < E1;
-        old[r] = (d.beta != 0.0 && ok) ? out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] : zero<T>();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-        const int64_t i1 = ty + 8 * r;
-        if (i0b + tx < E0 && i1b + i1 < E1)
-            out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = finish(d.alpha, acc[r], d.beta, &old[r]);
-    }
-}
-
-// Two-source accumulate (outer products with permutation operators): one warp
-// per output row (all dims but the innermost), lanes along the innermost dim;
-// each term's row offsets are formed once per row and kept in registers
-// (NP: the term count rounded up to 1, 2, 4 or 8).
-template <typename T, int NP>
-__global__ void __launch_bounds__(256) accum_outer_rows_kernel(const AccumDesc d, const T *__restrict__ src,
-                                                               const T *__restrict__ src2, T *__restrict__ out) {
-    constexpr int RCH = 16;                      // consecutive rows per warp: one decomposition, then steps
-    const int lane = threadIdx.x & 31;
-    const int d0 = d.nd - 1;
-    const int64_t E0 = d.ext[d0], rows = d.total / E0;
-    const int64_t w0 = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), nw = (int64_t)gridDim.x * 8;
-    int64_t s0[NP], s02[NP];
-    double sg[NP];
-#pragma unroll
-    for (int p = 0; p < NP; p++) {
-        s0[p] = p < d.nperm ? d.sstr[p][d0] : 0;
-        s02[p] = p < d.nperm ? d.sstr2[p][d0] : 0;
-        sg[p] = p < d.nperm ? d.sign[p] : 0.0;
-    }
-    const int64_t os0 = d.ostr[d0];
-    for (int64_t c = w0; c * RCH < rows; c += nw) {
-        const int64_t r0 = c * RCH;
-        // row digits of r0 (rows < 2^32: 32-bit divisions)
-        uint32_t dig[kMaxDims];
-        int64_t obase = 0, sb[NP], sb2[NP];
-#pragma unroll
-        for (int p = 0; p < NP; p++) sb[p] = sb2[p] = 0;
-        uint32_t x = (uint32_t)r0;
-        for (int k = d0 - 1; k >= 0; k--) {
-            const uint32_t e = (uint32_t)d.ext[k], q = x / e;
-            dig[k] = x - q * e;
-            x = q;
-            obase += (int64_t)dig[k] * d.ostr[k];
-#pragma unroll
-            for (int p = 0; p < NP; p++)
-                if (p < d.nperm) {
-                    sb[p] += (int64_t)dig[k] * d.sstr[p][k];
-                    sb2[p] += (int64_t)dig[k] * d.sstr2[p][k];
-                }
-        }
-        const int nr = rows - r0 < RCH ? (int)(rows - r0) : RCH;
-        for (int rr = 0; rr < nr; rr++) {
-            for (int64_t i = lane; i < E0; i += 32) {
-                T acc = zero<T>();
-#pragma unroll
-                for (int p = 0; p < NP; p++)
-                    if (p < d.nperm) {
-                        const T a = cj(ld(src + sb[p] + i * s0[p]), d.conj_a);
-                        const T b = cj(ld(src2 + sb2[p] + i * s02[p]), d.conj_b);
-                        // one product per term, the sign folded into it
-                        acc = p == 0 ? mul(sg[p] < 0.0 ? neg(a) : a, b) : cfma(sg[p] < 0.0 ? neg(a) : a, b, acc);
-                    }
-                T *o = out + obase + i * os0;
-                *o = finish(d.alpha, acc, d.beta, o);
-            }
-            // next row: odometer step with carries
-            for (int k = d0 - 1; k >= 0; k--) {
-                obase += d.ostr[k];
-#pragma unroll
-                for (int p = 0; p < NP; p++)
-                    if (p < d.nperm) {
-                        sb[p] += d.sstr[p][k];
-                        sb2[p] += d.sstr2[p][k];
-                    }
-                if (++dig[k] < (uint32_t)d.ext[k]) break;
-                dig[k] = 0;
-                obase -= d.ext[k] * d.ostr[k];
-#pragma unroll
-                for (int p = 0; p < NP; p++)
-                    if (p < d.nperm) {
-                        sb[p] -= d.ext[k] * d.sstr[p][k];
-                        sb2[p] -= d.ext[k] * d.sstr2[p][k];
-                    }
-            }
-        }
-    }
-}
-
-template <typename T>
-static cudaError_t accum_generic(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
-    int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
-    int64_t blocks = (runs + 7) / 8;
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    accum_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, src, out, src2);
-    return cudaGetLastError();
-}
-
-template <typename T>
-static cudaError_t accum_t(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
-    if (d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 32 && d.total / d.ext[d.nd - 1] < 0xffffffffLL) {
-        const int64_t rows = d.total / d.ext[d.nd - 1];
-        int64_t blocks = (rows / 16 + 8) / 8;
-        if (blocks > 148 * 16) blocks = 148 * 16;
-        if (d.nperm <= 1) accum_outer_rows_kernel<T, 1><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
-        else if (d.nperm <= 2) accum_outer_rows_kernel<T, 2><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
-        else if (d.nperm <= 4) accum_outer_rows_kernel<T, 4><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
-        else if (d.nperm <= 8) accum_outer_rows_kernel<T, 8><<<(unsigned)blocks, 256, 0, s>>>(d, src, src2, out);
-        else return accum_generic(d, src, out, s, src2);
-        return cudaGetLastError();
-    }
-    // tiled path: the output's innermost dim and a partner dim both of extent >= 16
-    if (!d.two_src && d.nd >= 2 && d.ext[d.nd - 1] >= 16) {
-        const int d0 = d.nd - 1;
-        int d1 = -1;
-        uint64_t tmask = 0;
-        // partner: the dim holding a term's smallest source stride, when that is not d0
-        for (int p = 0; p < d.nperm; p++) {
-            int kmin = 0;
-            for (int k = 1; k < d.nd; k++)
-                if (d.ext[k] > 1 && (d.ext[kmin] <= 1 || d.sstr[p][k] < d.sstr[p][kmin])) kmin = k;
-            if (kmin != d0 && d.sstr[p][kmin] < d.sstr[p][d0]) {
-                if (d1 < 0) d1 = kmin;
-                if (kmin == d1) tmask |= 1ull << p;
-            }
-        }
-        if (d1 < 0) {
-            // no transposed term: pair d0 with the largest remaining dim
-            for (int k = 0; k < d.nd - 1; k++)
-                if (d1 < 0 || d.ext[k] > d.ext[d1]) d1 = k;
-        }
-        if (d.ext[d1] >= 16) {
-            const int64_t tiles0 = (d.ext[d0] + 31) / 32, tiles1 = (d.ext[d1] + 31) / 32;
-            const int64_t blocks = tiles0 * tiles1 * (d.total / (d.ext[d0] * d.ext[d1]));
-            if (blocks <= 0x7fffffffLL) {
-                accum_tiled_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(d, src, out, d0, d1, tmask, tiles0, tiles1);
-                return cudaGetLastError();
-            }
-        }
-    }
-    return accum_generic(d, src, out, s, src2);
-}
-
-cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s, const double *src2) {
-    if (d.total <= 0) return cudaSuccess;
-    if (d.cplx)
-        return accum_t<double2>(d, reinterpret_cast<const double2 *>(src), reinterpret_cast<double2 *>(out), s,
-                                reinterpret_cast<const double2 *>(src2));
-    return accum_t<double>(d, src, out, s, src2);
-}
 
 __global__ void zero_kernel(double *p, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -462,12 +138,15 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) old[i][j] = (d.beta != 0.0 && rv[i] && cv[j]) ? C[ro[i] + co[j]] : zero<T>();
+        for (int j = 0; j < 4; j++) old[i][j] = (d.bcase != 0 && rv[i] && cv[j]) ? C[ro[i] + co[j]] : zero<T>();
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            if (rv[i] && cv[j]) C[ro[i] + co[j]] = axpy(d.beta, old[i][j], scal(d.alpha, up(acc[i][j])));
+            if (rv[i] && cv[j]) {
+                const T v = epi_scale(acc[i][j], d.as);
+                C[ro[i] + co[j]] = d.bcase == 0 ? v : d.bcase == 1 ? add(v, old[i][j]) : axpy(d.beta, old[i][j], v);
+            }
 }
 
 // ------------------------------------------------------------ packed pairs
@@ -513,8 +192,9 @@ __global__ void __launch_bounds__(256) unpack_pairs_kernel(const UnpackDesc d, c
             val = __ldg(C + pa * d.cA + pb * d.cB);
             if ((a1 > a2) != (b1 > b2)) val = -val;
         }
-        double r = d.alpha * val;
-        if (d.beta != 0.0) r = fma(d.beta, out[off], r);
+        double r = scale_f64(val, d.as);
+        if (d.bcase == 1) r += out[off];
+        else if (d.bcase == 2) r = fma(d.beta, out[off], r);
         out[off] = r;
     }
 }
@@ -529,7 +209,10 @@ cudaError_t launch_pack_pairs(const PackDesc &d, const double *src, double *dst,
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_pairs(const UnpackDesc &d, const double *C, double *out, cudaStream_t s) {
+cudaError_t launch_unpack_pairs(const UnpackDesc &d0, const double *C, double *out, cudaStream_t s) {
+    UnpackDesc d = d0;
+    d.bcase = beta_case(d.beta);
+    d.as = make_scale(d.alpha);
     const int64_t total = d.ext[0] * d.ext[1] * d.ext[2] * d.ext[3];
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
@@ -583,10 +266,13 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const RowsGemmDesc d, co
         for (int c0 = 0; c0 < NC; c0 += 8) {
             double old[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) old[j] = (d.beta != 0.0 && c0 + j < d.nc) ? C[co + cco[c0 + j]] : 0.0;
+            for (int j = 0; j < 8; j++) old[j] = (d.bcase != 0 && c0 + j < d.nc) ? C[co + cco[c0 + j]] : 0.0;
 #pragma unroll
             for (int j = 0; j < 8; j++)
-                if (c0 + j < d.nc) C[co + cco[c0 + j]] = fma(d.beta, old[j], d.alpha * up(acc[c0 + j]));
+                if (c0 + j < d.nc) {
+                    const double v = epi_scale(acc[c0 + j], d.as);
+                    C[co + cco[c0 + j]] = d.bcase == 0 ? v : d.bcase == 1 ? v + old[j] : fma(d.beta, old[j], v);
+                }
         }
     }
 }
@@ -603,8 +289,11 @@ static cudaError_t rows_t(const RowsGemmDesc &d, const double *X, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s) {
-    if (d.R <= 0) return cudaSuccess;
+cudaError_t launch_rows_gemm(const RowsGemmDesc &d0, const double *X, const double *Y, double *C, cudaStream_t s) {
+    if (d0.R <= 0) return cudaSuccess;
+    RowsGemmDesc d = d0;
+    d.bcase = beta_case(d.beta);
+    d.as = make_scale(d.alpha);
     if (d.nc < 1 || d.nc > 64 || d.K < 1 || d.K > 64 || d.R > 0xffffffffLL) return cudaErrorInvalidValue;
     return d.f32 ? rows_t<float>(d, X, Y, C, s) : rows_t<double>(d, X, Y, C, s);
 }
@@ -768,9 +457,12 @@ static cudaError_t gemm_t(const GemmF64Desc &d, const T *A, const T *B, T *C, T 
     return splitk_reduce_t<T>(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
-cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, double *partials,
+cudaError_t launch_gemm_f64(const GemmF64Desc &d0, const double *A, const double *B, double *C, double *partials,
                             cudaStream_t s) {
-    if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+    if (d0.M <= 0 || d0.N <= 0) return cudaSuccess;
+    GemmF64Desc d = d0;
+    d.bcase = beta_case(d.beta);
+    d.as = make_scale(d.alpha);
     if (d.cplx)
         return gemm_t<double2, double2>(d, reinterpret_cast<const double2 *>(A), reinterpret_cast<const double2 *>(B),
                                         reinterpret_cast<double2 *>(C), reinterpret_cast<double2 *>(partials), s);

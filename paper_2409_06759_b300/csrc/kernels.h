@@ -10,6 +10,28 @@ namespace ccb {
 constexpr int kMaxDims = 8;     // dims of one tensor view
 constexpr int kMaxPerms = 36;   // terms of an expanded permutation operator (3! x 3! for triples)
 
+// Multiplication by a constant alpha, classified on the host.  alpha = +-2^k
+// (|k| < 512) is applied exactly with integer operations on the exponent and
+// sign bits (B300 issues FP64 instructions, conversions included, at ~1/64 of
+// the FP32 rate); any other alpha is a plain FP64 multiply.
+struct Scale {
+    int general;                    // 1: multiply by value
+    int kexp;                       // alpha = (sflip ? -1 : 1) * 2^kexp when !general
+    uint32_t sflip;                 // 0x80000000 when alpha < 0
+    double value;                   // alpha
+};
+inline Scale make_scale(double a) {
+    Scale s{1, 0, 0u, a};
+    if (a != 0.0 && a == a) {
+        double m = a < 0 ? -a : a;
+        int k = 0;
+        while (m >= 2.0 && k < 512) { m *= 0.5; k++; }
+        while (m < 1.0 && k > -512) { m *= 2.0; k--; }
+        if (m == 1.0 && k > -512 && k < 512) { s.general = 0; s.kexp = k; s.sflip = a < 0 ? 0x80000000u : 0u; }
+    }
+    return s;
+}
+
 // Mixed-radix index group: a fused matrix index decomposed into nd digits
 // (digit 0 outermost, digit nd-1 fastest); offset = sum digit_d * str[d].
 struct Grp {
@@ -38,7 +60,15 @@ struct AccumDesc {
     int two_src;
     int64_t sstr2[kMaxPerms][kMaxDims];
     int cplx, conj_a, conj_b;
+    // set by launch_accum from sign/alpha/beta (the kernels never compare
+    // doubles per element: those compares run on the narrow FP64 pipe)
+    unsigned long long negmask;     // bit p: sign[p] < 0
+    Scale as;                       // make_scale(alpha)
+    int bcase;                      // beta_case(beta)
 };
+
+// beta classes for epilogues: 0 -> 0, 1 -> 1, other -> 2
+inline int beta_case(double b) { return b == 0.0 ? 0 : b == 1.0 ? 1 : 2; }
 
 // C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), FP64.
 // A(m,k) = A[m*sAm + k*sAk] with sAm == 1 or sAk == 1; B(k,n) = B[k*sBk + n*sBn]
@@ -57,6 +87,8 @@ struct GemmF64Desc {
     int splitk;
     int cplx, conj_a, conj_b;
     int f32;
+    int bcase;                      // set by launch_gemm_f64 from beta
+    Scale as;                       // make_scale(alpha), same launcher
 };
 
 // Narrow GEMM: C(r, c) = alpha * sum_k X(r, k) Y(k, c) + beta * C(r, c) for
@@ -73,6 +105,8 @@ struct RowsGemmDesc {
     Grp cr, cc;     // C(r, c) = C[cr(r) + cc(c)]
     double alpha, beta;
     int f32;
+    int bcase;                      // set by launch_rows_gemm from beta
+    Scale as;                       // make_scale(alpha), same launcher
 };
 
 // Packed index pairs.  A pair (p < q) of letters with extent n has the index
@@ -98,6 +132,8 @@ struct UnpackDesc {
     int da1, da2, db1, db2;
     int64_t nA, nB, cA, cB;
     double alpha, beta;
+    int bcase;                      // set by launch_unpack_pairs from beta
+    Scale as;                       // make_scale(alpha), same launcher
 };
 cudaError_t launch_pack_pairs(const PackDesc &d, const double *src, double *dst, cudaStream_t s);
 cudaError_t launch_unpack_pairs(const UnpackDesc &d, const double *C, double *out, cudaStream_t s);
@@ -134,6 +170,8 @@ struct TcGemmDesc {
     double alpha, beta;
     int bn;
     int splitk;
+    int bcase;                      // set by launch_tc_gemm from beta
+    Scale as;                       // make_scale(alpha), same launcher
 };
 
 cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s,

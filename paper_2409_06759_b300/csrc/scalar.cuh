@@ -1,0 +1,79 @@
+// scalar.cuh -- element-type helpers shared by the FP64 kernels: each kernel
+// is written once over T = double or double2 (an interleaved complex double).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fp_bits.cuh"
+#include "kernels.h"
+
+namespace ccb {
+
+// ------------------------------------------------------------------ scalars
+// The kernels below are written once over the element type T: double, or
+// double2 holding an interleaved complex double (re, im).
+__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ double cj(double x, int) { return x; }
+__device__ __forceinline__ double2 cj(double2 x, int c) { return c ? make_double2(x.x, -x.y) : x; }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 mul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + s * x, s real
+__device__ __forceinline__ double axpy(double s, double x, double acc) { return fma(s, x, acc); }
+__device__ __forceinline__ double2 axpy(double s, double2 x, double2 acc) {
+    return make_double2(fma(s, x.x, acc.x), fma(s, x.y, acc.y));
+}
+__device__ __forceinline__ double scal(double s, double x) { return s * x; }
+__device__ __forceinline__ double2 scal(double s, double2 x) { return make_double2(s * x.x, s * x.y); }
+template <typename T> __device__ __forceinline__ T zero();
+template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ double2 zero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
+// element type T -> compute type CT (FP64 data multiplied in FP32: one rounding) and back
+template <typename CT> __device__ __forceinline__ CT down(double x);
+template <> __device__ __forceinline__ double down<double>(double x) { return x; }
+template <> __device__ __forceinline__ float down<float>(double x) { return f64_to_f32_rn(x); }
+template <typename CT> __device__ __forceinline__ CT down(double2 x) { return x; }
+__device__ __forceinline__ double up(double x) { return x; }
+__device__ __forceinline__ double up(float x) { return f32_to_f64_scaled(x, Scale{0, 0, 0u, 1.0}); }
+__device__ __forceinline__ double2 up(double2 x) { return x; }
+__device__ __forceinline__ float cfma(float a, float b, float acc) { return fmaf(a, b, acc); }
+// B300's FP64 pipe issues ~2 operations per clock per SM: the elementwise
+// kernels spend at most one FP64 operation per term.  A +-1 sign is an add or
+// a subtract (the first term a free negation); alpha = +-1 and beta in {0, 1}
+// cost nothing or one add.
+__device__ __forceinline__ double neg(double x) {           // sign bit only (no FP64 instruction)
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ double2 neg(double2 x) { return make_double2(neg(x.x), neg(x.y)); }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double sub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// acc (+|-) x, the first term taken as +-x
+template <typename T> __device__ __forceinline__ T signed_term(bool first, bool negative, T x, T acc) {
+    if (first) return negative ? neg(x) : x;
+    return negative ? sub(acc, x) : add(acc, x);
+}
+// alpha * acc + beta * old: alpha = +-2^k on the integer pipe, beta in {0, 1}
+// at most one FP64 add (bcase = beta_case(beta))
+template <typename T>
+__device__ __forceinline__ T finish(const Scale &as, T acc, int bcase, double beta, const T *o) {
+    const T v = scale_f64(acc, as);
+    if (bcase == 1) return add(v, *o);
+    if (bcase == 2) return axpy(beta, *o, v);
+    return v;
+}
+// acc + a * b over complex (or real) numbers
+__device__ __forceinline__ double cfma(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+
+}  // namespace ccb

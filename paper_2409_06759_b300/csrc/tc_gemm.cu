@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "fp_bits.cuh"
 #include "kernels.h"
 
 namespace ccb {
@@ -31,26 +32,10 @@ __device__ __forceinline__ int64_t grp_off(const Grp &g, int64_t x) {
 // bits, as many as three bf16 planes hold): the remainders x_f - hi and
 // r - mid are exact in FP32, and the FP64 pipe of sm_103a -- a few
 // operations per clock per SM -- is used only for that one conversion.
-// double -> float, round to nearest even, on the integer pipe (B300's FP64
-// pipe, which a conversion instruction would occupy, issues ~2 operations per
-// clock per SM).  IEEE 754 binary64 -> binary32: keep the top 23 of the 52
-// mantissa bits, round on the 29 dropped ones (ties to even; a carry moves into
-// the exponent, up to infinity).  Zeros and double subnormals give +-0; results
-// in the float subnormal or overflow range, infinities and NaNs take the
-// library conversion.
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
-    const unsigned int sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    if (e == 0) return __uint_as_float(sign);
-    const int ef = e - 1023 + 127;
-    if (ef <= 0 || ef >= 255) return __double2float_rn(x);
-    const unsigned int m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned int rem = lo & 0x1fffffffu;
-    unsigned int f = sign | ((unsigned int)ef << 23) | m;
-    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) f += 1u;
-    return __uint_as_float(f);
+// the unit scale, and v + beta * old with beta classified (bcase)
+__device__ __forceinline__ Scale unit_scale() { return Scale{0, 0, 0u, 1.0}; }
+__device__ __forceinline__ double epi_out(double v, const TcGemmDesc &d, double old) {
+    return d.bcase == 0 ? v : d.bcase == 1 ? v + old : fma(d.beta, old, v);
 }
 
 __global__ void convert_selftest_kernel(const double *in, int64_t n, float *mine, float *ref) {
@@ -452,7 +437,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int64_t n = n0 + c0 + j;
-                        if (n < d.N) P[n * d.M + m] = (double)__uint_as_float(r[j]);
+                        if (n < d.N) P[n * d.M + m] = f32_to_f64_scaled(__uint_as_float(r[j]), unit_scale());
                     }
                 }
             }
@@ -468,12 +453,12 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int64_t co = coloff[c0 + j];
-                        old[j] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
+                        old[j] = (d.bcase != 0 && co >= 0) ? C[roff + co] : 0.0;
                     }
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int64_t co = coloff[c0 + j];
-                        if (co >= 0) C[roff + co] = d.alpha * (double)__uint_as_float(r[j]) + d.beta * old[j];
+                        if (co >= 0) C[roff + co] = epi_out(f32_to_f64_scaled(__uint_as_float(r[j]), d.as), d, old[j]);
                     }
                 }
             }
@@ -666,7 +651,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                         for (int jj = 0; jj < 32; jj++) {
                             const int64_t n = coloff[c0 + jj];
-                            if (n >= 0) P[n * d.M + m] = (double)__uint_as_float(r[jj]);
+                            if (n >= 0) P[n * d.M + m] = f32_to_f64_scaled(__uint_as_float(r[jj]), unit_scale());
                         }
                     } else {
                         // read-modify-write in two batches of 16 (loads issued before the stores)
@@ -676,13 +661,13 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                             for (int jj = 0; jj < 16; jj++) {
                                 const int64_t co = coloff[c0 + h + jj];
-                                old[jj] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
+                                old[jj] = (d.bcase != 0 && co >= 0) ? C[roff + co] : 0.0;
                             }
 #pragma unroll
                             for (int jj = 0; jj < 16; jj++) {
                                 const int64_t co = coloff[c0 + h + jj];
                                 if (co >= 0)
-                                    C[roff + co] = d.alpha * (double)__uint_as_float(r[h + jj]) + d.beta * old[jj];
+                                    C[roff + co] = epi_out(f32_to_f64_scaled(__uint_as_float(r[h + jj]), d.as), d, old[jj]);
                             }
                         }
                     }
@@ -882,7 +867,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                 for (int j = 0; j < HALF; j++) {
                     const int64_t n = n0 + h * HALF + j;
-                    if (n < d.N) P[n * d.M + m] = (double)hi[j] + (double)lo[j];
+                    if (n < d.N) P[n * d.M + m] = f32_to_f64_scaled(hi[j], unit_scale()) + f32_to_f64_scaled(lo[j], unit_scale());
                 }
             } else {
 #pragma unroll
@@ -891,13 +876,15 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
                         const int64_t co = coloff[h * HALF + j0 + j];
-                        old[j] = (d.beta != 0.0 && co >= 0) ? C[roff + co] : 0.0;
+                        old[j] = (d.bcase != 0 && co >= 0) ? C[roff + co] : 0.0;
                     }
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
                         const int64_t co = coloff[h * HALF + j0 + j];
                         if (co >= 0)
-                            C[roff + co] = d.alpha * ((double)hi[j0 + j] + (double)lo[j0 + j]) + d.beta * old[j];
+                            C[roff + co] = epi_out(scale_f64(f32_to_f64_scaled(hi[j0 + j], unit_scale()) +
+                                                                 f32_to_f64_scaled(lo[j0 + j], unit_scale()), d.as),
+                                                   d, old[j]);
                     }
                 }
             }
@@ -1046,9 +1033,12 @@ cudaError_t launch_wait_selftest(long long budget_cycles, int *timed_out, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C, double *partials,
+cudaError_t launch_tc_gemm(const TcGemmDesc &d0, const void *Aplanes, const void *Bplanes, double *C, double *partials,
                            int *err_flag, cudaStream_t s) {
-    if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+    if (d0.M <= 0 || d0.N <= 0) return cudaSuccess;
+    TcGemmDesc d = d0;
+    d.bcase = beta_case(d.beta);
+    d.as = make_scale(d.alpha);
     if (d.nplanes_a != d.nplanes_b || d.nprod < 1 || d.nprod > 8) return cudaErrorInvalidValue;
     if (((uintptr_t)Aplanes & 1023) || ((uintptr_t)Bplanes & 1023) || d.Kp < 64) {
         // TMA needs 16-byte aligned bases; the planner hands out 256-byte aligned workspace
