@@ -35,7 +35,7 @@ namespace ccb {
 // The multi-index is decomposed once per run and advanced as an odometer.
 constexpr int kAccChunk = 8;
 
-template <typename T>
+template <typename T, bool ACC>
 __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *__restrict__ src,
                                                     T *__restrict__ out, const T *__restrict__ src2) {
     const int lane = threadIdx.x & 31;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
                 }
                 acc = signed_term(p == 0, (d.negmask >> p) & 1ull, x, acc);
             }
-            out[oo] = finish(d.as, acc, d.bcase, d.beta, out + oo);
+            out[oo] = finish<ACC>(d.as, acc, ACC ? out[oo] : zero<T>());
             // advance by 32 elements (compare-and-subtract carries)
             e += 32;
             int carry = 32;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
 // before the arithmetic.  NP: the term count rounded up (1, 2, 4, 8).
 constexpr int kRowU = 8;
 
-template <typename T, int NP, bool TWO>
+template <typename T, int NP, bool TWO, bool ACC>
 __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, const T *__restrict__ src,
                                                          const T *__restrict__ src2, T *__restrict__ out,
                                                          uint32_t rows, int rch, uint32_t ncb) {
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
 #pragma unroll
             for (int u = 0; u < kRowU; u++) {
                 const int64_t i = cb + lane + 32 * u;
-                old[u] = (d.bcase != 0 && i < E0) ? out[obase + i * os0] : zero<T>();
+                old[u] = (ACC && i < E0) ? out[obase + i * os0] : zero<T>();
             }
 #pragma unroll
             for (int p = 0; p < NP; p++) {
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
 #pragma unroll
             for (int u = 0; u < kRowU; u++) {
                 const int64_t i = cb + lane + 32 * u;
-                if (i < E0) out[obase + i * os0] = finish(d.as, acc[u], d.bcase, d.beta, &old[u]);
+                if (i < E0) out[obase + i * os0] = finish<ACC>(d.as, acc[u], old[u]);
             }
             // next row: odometer step with carries
 #pragma unroll
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
 // along d0) or through shared memory (lanes along d1, then transposed), so
 // reads and writes stay coalesced for the P(..) gathers.  Blocks loop over
 // tiles; tile and batch indices are decomposed with 32-bit divisions.
-template <typename T>
+template <typename T, bool ACC>
 __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, const T *__restrict__ src,
                                                           T *__restrict__ out, int d0, int d1, uint64_t tmask,
                                                           uint32_t tiles0, uint32_t tiles1, uint32_t ntiles) {
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
         for (int r = 0; r < 4; r++) {
             const int64_t i1 = ty + 8 * r;
             const bool ok = i0b + tx < E0 && i1b + i1 < E1;
-            old[r] = (d.bcase != 0 && ok) ? out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] : zero<T>();
+            old[r] = (ACC && ok) ? out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] : zero<T>();
         }
         for (int p = 0; p < d.nperm; p++) {
             int64_t base = 0;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) accum_tiled_kernel(const AccumDesc d, con
         for (int r = 0; r < 4; r++) {
             const int64_t i1 = ty + 8 * r;
             if (i0b + tx < E0 && i1b + i1 < E1)
-                out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = finish(d.as, acc[r], d.bcase, d.beta, &old[r]);
+                out[obase + (i0b + tx) * os0 + (i1b + i1) * os1] = finish<ACC>(d.as, acc[r], old[r]);
         }
     }
 }
@@ -294,14 +294,11 @@ struct PairSym {
     int64_t S[4], O[4];
 };
 
-template <typename T>
-__device__ __forceinline__ void pair_store(T *out, int64_t off, T v, const AccumDesc &d) {
-    T o = zero<T>();
-    if (d.bcase != 0) o = out[off];
-    out[off] = d.bcase == 0 ? v : d.bcase == 1 ? add(v, o) : axpy(d.beta, o, v);
+template <bool ACC, typename T> __device__ __forceinline__ void pair_store(T *out, int64_t off, T v) {
+    out[off] = ACC ? add(v, out[off]) : v;
 }
 
-template <typename T>
+template <typename T, bool ACC>
 __global__ void __launch_bounds__(256) antisym_pairs_kernel(const AccumDesc d, const PairSym g,
                                                             const T *__restrict__ src, T *__restrict__ out,
                                                             uint32_t nt, uint32_t items) {
@@ -352,8 +349,8 @@ __global__ void __launch_bounds__(256) antisym_pairs_kernel(const AccumDesc d, c
             const int64_t a = a0 + ty + 8 * r, b = b0 + tx;
             if (a < n2 && b < n2) {
                 const int64_t off = a * g.O[2] + b * g.O[3];
-                pair_store(out, oij + off, X[r], d);
-                if (offdiag) pair_store(out, oji + off, neg(X[r]), d);
+                pair_store<ACC>(out, oij + off, X[r]);
+                if (offdiag) pair_store<ACC>(out, oji + off, neg(X[r]));
             }
         }
         if (A != B) {
@@ -368,8 +365,8 @@ __global__ void __launch_bounds__(256) antisym_pairs_kernel(const AccumDesc d, c
                 if (bb < n2 && aa < n2) {
                     const T v = s1[tx][ty + 8 * r];
                     const int64_t off = bb * g.O[2] + aa * g.O[3];
-                    pair_store(out, oij + off, offdiag ? neg(v) : v, d);
-                    if (offdiag) pair_store(out, oji + off, v, d);
+                    pair_store<ACC>(out, oij + off, offdiag ? neg(v) : v);
+                    if (offdiag) pair_store<ACC>(out, oji + off, v);
                 }
             }
         }
@@ -456,14 +453,28 @@ static bool match_pair_antisym(const AccumDesc &d, PairSym &g, double &alpha_sig
 
 static int64_t grid_cap(int64_t want, int64_t cap) { return want < 1 ? 1 : want > cap ? cap : want; }
 
+// out *= beta over the output view (a general beta before an accumulating pass)
 template <typename T>
+__global__ void __launch_bounds__(256) scale_view_kernel(const AccumDesc d, T *__restrict__ out, double beta) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = e, off = 0;
+        for (int k = d.nd - 1; k >= 0; k--) {
+            const int64_t q = x / d.ext[k];
+            off += (x - q * d.ext[k]) * d.ostr[k];
+            x = q;
+        }
+        out[off] = scal(beta, out[off]);
+    }
+}
+
+template <typename T, bool ACC>
 static cudaError_t accum_generic(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
     int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
-    accum_kernel<T><<<(unsigned)grid_cap((runs + 7) / 8, 148 * 16), 256, 0, s>>>(d, src, out, src2);
+    accum_kernel<T, ACC><<<(unsigned)grid_cap((runs + 7) / 8, 148 * 16), 256, 0, s>>>(d, src, out, src2);
     return cudaGetLastError();
 }
 
-template <typename T, int NP>
+template <typename T, int NP, bool ACC>
 static cudaError_t rows_launch(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
     const int64_t E0 = d.ext[d.nd - 1];
     const int64_t rows = d.total / E0;
@@ -474,15 +485,15 @@ static cudaError_t rows_launch(const AccumDesc &d, const T *src, T *out, cudaStr
     const int64_t items = (rows + rch - 1) / rch * ncb;
     const unsigned blocks = (unsigned)grid_cap((items + 7) / 8, 148 * 16);
     if (d.two_src)
-        accum_rows_kernel<T, NP, true><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
-                                                              (uint32_t)ncb);
+        accum_rows_kernel<T, NP, true, ACC><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
+                                                                   (uint32_t)ncb);
     else
-        accum_rows_kernel<T, NP, false><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
-                                                               (uint32_t)ncb);
+        accum_rows_kernel<T, NP, false, ACC><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
+                                                                    (uint32_t)ncb);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool ACC>
 static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream_t s, const T *src2) {
     PairSym g;
     double sg = 1.0;
@@ -495,8 +506,8 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
         const int64_t nt = (g.n2 + 31) / 32;
         const int64_t items = g.n1 * g.n1 * nt * nt;
         if (items <= 0xffffffffLL) {
-            antisym_pairs_kernel<T><<<(unsigned)grid_cap(items, 148 * 32), 256, 0, s>>>(d, g, src, out, (uint32_t)nt,
-                                                                                     (uint32_t)items);
+            antisym_pairs_kernel<T, ACC><<<(unsigned)grid_cap(items, 148 * 32), 256, 0, s>>>(
+                d, g, src, out, (uint32_t)nt, (uint32_t)items);
             return cudaGetLastError();
         }
     }
@@ -512,10 +523,10 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
     }
     for (int k = 0; k < dl && rowok; k++) rowok = d.ext[k] <= 0xffffffffLL;
     if (rowok) {
-        if (d.nperm <= 1) return rows_launch<T, 1>(d, src, out, s, src2);
-        if (d.nperm <= 2) return rows_launch<T, 2>(d, src, out, s, src2);
-        if (d.nperm <= 4) return rows_launch<T, 4>(d, src, out, s, src2);
-        return rows_launch<T, 8>(d, src, out, s, src2);
+        if (d.nperm <= 1) return rows_launch<T, 1, ACC>(d, src, out, s, src2);
+        if (d.nperm <= 2) return rows_launch<T, 2, ACC>(d, src, out, s, src2);
+        if (d.nperm <= 4) return rows_launch<T, 4, ACC>(d, src, out, s, src2);
+        return rows_launch<T, 8, ACC>(d, src, out, s, src2);
     }
     // tiled path: the output's innermost dim and a partner dim both of extent >= 16
     if (!d.two_src && d.nd >= 2 && d.ext[dl] >= 16) {
@@ -542,13 +553,25 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
             bool fits = ntiles <= 0xffffffffLL;
             for (int k = 0; k < d.nd && fits; k++) fits = d.ext[k] <= 0xffffffffLL;
             if (fits) {
-                accum_tiled_kernel<T><<<(unsigned)grid_cap(ntiles, 148 * 8), 256, 0, s>>>(
+                accum_tiled_kernel<T, ACC><<<(unsigned)grid_cap(ntiles, 148 * 8), 256, 0, s>>>(
                     d, src, out, dl, d1, tmask, (uint32_t)tiles0, (uint32_t)tiles1, (uint32_t)ntiles);
                 return cudaGetLastError();
             }
         }
     }
-    return accum_generic(d, src, out, s, src2);
+    return accum_generic<T, ACC>(d, src, out, s, src2);
+}
+
+template <typename T>
+static cudaError_t accum_dispatch(AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
+    if (d.bcase == 2) {
+        // general beta: out *= beta first, then accumulate with beta = 1
+        scale_view_kernel<T><<<(unsigned)grid_cap((d.total + 255) / 256, 148 * 16), 256, 0, s>>>(d, out, d.beta);
+        if (cudaError_t e = cudaGetLastError()) return e;
+        d.beta = 1.0;
+        d.bcase = 1;
+    }
+    return d.bcase ? accum_t<T, true>(d, src, out, s, src2) : accum_t<T, false>(d, src, out, s, src2);
 }
 
 cudaError_t launch_accum(const AccumDesc &d0, const double *src, double *out, cudaStream_t s, const double *src2) {
@@ -561,9 +584,9 @@ cudaError_t launch_accum(const AccumDesc &d0, const double *src, double *out, cu
     d.as = make_scale(d.alpha);
     d.bcase = beta_case(d.beta);
     if (d.cplx)
-        return accum_t<double2>(d, reinterpret_cast<const double2 *>(src), reinterpret_cast<double2 *>(out), s,
-                                reinterpret_cast<const double2 *>(src2));
-    return accum_t<double>(d, src, out, s, src2);
+        return accum_dispatch<double2>(d, reinterpret_cast<const double2 *>(src), reinterpret_cast<double2 *>(out), s,
+                                       reinterpret_cast<const double2 *>(src2));
+    return accum_dispatch<double>(d, src, out, s, src2);
 }
 
 }  // namespace ccb

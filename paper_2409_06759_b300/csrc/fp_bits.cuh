@@ -14,6 +14,14 @@
 
 namespace ccb {
 
+// Rare-path fallbacks live in non-inlined functions: a call is a real branch,
+// whereas an inlined FP64 multiply or conversion on a rarely taken side of a
+// select is often executed speculatively for every element (if-conversion),
+// which would put it back on the FP64 pipe.
+static __device__ __noinline__ float d2f_slow(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double f2d_mul_slow(float f, double a) { return (double)f * a; }
+static __device__ __noinline__ double dmul_slow(double x, double a) { return x * a; }
+
 // double -> float, round to nearest even.  Normal results are formed from the
 // bit pattern: the 29 dropped mantissa bits decide the rounding (ties to the
 // even neighbour; a carry out of the mantissa bumps the exponent, which is the
@@ -25,7 +33,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
     const int e = (int)((hi >> 20) & 0x7ffu);
     if (e == 0) return __uint_as_float(sign);             // zero, or a double subnormal (below every float)
     const int ef = e - 1023 + 127;
-    if (ef <= 0 || ef >= 255) return __double2float_rn(x);
+    if (ef <= 0 || ef >= 255) return d2f_slow(x);
     const unsigned int m = ((hi & 0xfffffu) << 3) | (lo >> 29);
     const unsigned int rem = lo & 0x1fffffffu;
     unsigned int f = sign | ((unsigned int)ef << 23) | m;
@@ -49,17 +57,17 @@ __device__ __forceinline__ double f32_to_f64_scaled(float f, const Scale &s) {
         hi = (u & 0x80000000u) ^ flip;
         lo = 0u;
     } else {
-        return (double)f * s.value;                        // subnormal, inf, NaN
+        return f2d_mul_slow(f, s.value);                   // subnormal, inf, NaN
     }
     const double r = __hiloint2double((int)hi, (int)lo);
-    return s.general ? r * s.value : r;
+    return s.general ? dmul_slow(r, s.value) : r;
 }
 
 // alpha * x, exact for alpha = +-2^k when x and the result are normal
 // (exponent field shift), and for +-1 or a zero (sign bit); subnormals,
 // inf/NaN and range exits multiply.
 __device__ __forceinline__ double scale_f64(double x, const Scale &s) {
-    if (s.general) return x * s.value;
+    if (s.general) return dmul_slow(x, s.value);
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
     const int e = (int)((hi >> 20) & 0x7ffu);
     const int ee = e + s.kexp;
@@ -67,7 +75,7 @@ __device__ __forceinline__ double scale_f64(double x, const Scale &s) {
         return __hiloint2double((int)((hi + ((uint32_t)s.kexp << 20)) ^ s.sflip), (int)lo);
     if (s.kexp == 0 || ((hi & 0x7fffffffu) | lo) == 0u)    // +-1, or a zero: sign only
         return __hiloint2double((int)(hi ^ s.sflip), (int)lo);
-    return x * s.value;
+    return dmul_slow(x, s.value);
 }
 __device__ __forceinline__ double2 scale_f64(double2 x, const Scale &s) {
     return make_double2(scale_f64(x.x, s), scale_f64(x.y, s));

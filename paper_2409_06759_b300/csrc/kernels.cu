@@ -22,6 +22,35 @@ cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ scale_grp
+// C(m,n) *= beta over an output addressed by two mixed-radix groups (applies a
+// general beta before an accumulating epilogue; the planner itself only emits
+// beta = 0 or 1)
+__device__ __forceinline__ int64_t grp_offset(const Grp &g, int64_t x);
+
+template <typename T>
+__global__ void __launch_bounds__(256) scale_grp_kernel(int64_t M, int64_t N, const Grp cm, const Grp cn, double beta,
+                                                        T *__restrict__ C) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = e / M, m = e - n * M;
+        T *p = C + grp_offset(cm, m) + grp_offset(cn, n);
+        *p = scal(beta, *p);
+    }
+}
+
+template <typename T>
+static cudaError_t scale_grp_t(int64_t M, int64_t N, const Grp &cm, const Grp &cn, double beta, T *C, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    int64_t blocks = (M * N + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    scale_grp_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(M, N, cm, cn, beta, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_grp(int64_t M, int64_t N, const Grp &cm, const Grp &cn, double beta, double *C, cudaStream_t s) {
+    return scale_grp_t<double>(M, N, cm, cn, beta, C, s);
+}
+
 // --------------------------------------------------------------- gemm_f64
 // 64x64 output tile, BK = 16, 256 threads as 16x16, each thread a 4x4
 // strided micro-tile.  Operand tiles go global -> registers -> shared memory
@@ -134,19 +163,26 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
         cv[i] = n0 + tn + 16 * i < d.N;
         co[i] = s_co[tn + 16 * i];
     }
-    T old[4][4];
+    // beta is 0 or 1 here (a general beta was applied to C beforehand); the
+    // branch is taken once, so the FP64 add exists only on the accumulating side
+    if (d.bcase == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+        for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) old[i][j] = (d.bcase != 0 && rv[i] && cv[j]) ? C[ro[i] + co[j]] : zero<T>();
+            for (int j = 0; j < 4; j++)
+                if (rv[i] && cv[j]) C[ro[i] + co[j]] = epi_scale(acc[i][j], d.as);
+    } else {
+        T old[4][4];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+        for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            if (rv[i] && cv[j]) {
-                const T v = epi_scale(acc[i][j], d.as);
-                C[ro[i] + co[j]] = d.bcase == 0 ? v : d.bcase == 1 ? add(v, old[i][j]) : axpy(d.beta, old[i][j], v);
-            }
+            for (int j = 0; j < 4; j++) old[i][j] = (rv[i] && cv[j]) ? C[ro[i] + co[j]] : zero<T>();
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (rv[i] && cv[j]) C[ro[i] + co[j]] = add(epi_scale(acc[i][j], d.as), old[i][j]);
+    }
 }
 
 // ------------------------------------------------------------ packed pairs
@@ -193,8 +229,7 @@ __global__ void __launch_bounds__(256) unpack_pairs_kernel(const UnpackDesc d, c
             if ((a1 > a2) != (b1 > b2)) val = -val;
         }
         double r = scale_f64(val, d.as);
-        if (d.bcase == 1) r += out[off];
-        else if (d.bcase == 2) r = fma(d.beta, out[off], r);
+        if (d.bcase != 0) r += out[off];           // a general beta was applied to out before
         out[off] = r;
     }
 }
@@ -213,6 +248,13 @@ cudaError_t launch_unpack_pairs(const UnpackDesc &d0, const double *C, double *o
     UnpackDesc d = d0;
     d.bcase = beta_case(d.beta);
     d.as = make_scale(d.alpha);
+    if (d.bcase == 2) {
+        // out *= beta over the 4-index view first (rows of the two outer indices)
+        Grp gm{2, {d.ext[0], d.ext[1]}, {d.ostr[0], d.ostr[1]}}, gn{2, {d.ext[2], d.ext[3]}, {d.ostr[2], d.ostr[3]}};
+        if (cudaError_t e = launch_scale_grp(d.ext[0] * d.ext[1], d.ext[2] * d.ext[3], gm, gn, d.beta, out, s)) return e;
+        d.beta = 1.0;
+        d.bcase = 1;
+    }
     const int64_t total = d.ext[0] * d.ext[1] * d.ext[2] * d.ext[3];
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
@@ -234,8 +276,13 @@ __device__ __forceinline__ int64_t grp_offset32(const Grp &g, uint32_t x) {
     return off;
 }
 
+// resident blocks per SM the accumulators allow without spilling
+template <typename CT, int NC> constexpr int rows_min_blocks() {
+    return sizeof(CT) == 4 ? (NC <= 40 ? 3 : 2) : (NC <= 24 ? 3 : NC <= 48 ? 2 : 1);
+}
+
 template <typename CT, int NC>
-__global__ void __launch_bounds__(256) rows_gemm_kernel(const RowsGemmDesc d, const double *__restrict__ X,
+__global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kernel(const RowsGemmDesc d, const double *__restrict__ X,
                                                         const double *__restrict__ Y, double *__restrict__ C) {
     __shared__ CT ys[64 * NC];
     __shared__ int64_t xko[64], cco[NC];
@@ -261,18 +308,22 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const RowsGemmDesc d, co
 #pragma unroll
                 for (int c = 0; c < NC; c++) acc[c] = cfma(a[j], ys[(k0 + j) * NC + c], acc[c]);
         }
-        // read-modify-write in batches of eight (loads issued before the stores)
+        // beta 0: plain stores; beta 1: read-modify-write in batches of eight
+        // (loads issued before the stores); a general beta was applied before
+        if (d.bcase == 0) {
 #pragma unroll
-        for (int c0 = 0; c0 < NC; c0 += 8) {
-            double old[8];
+            for (int c = 0; c < NC; c++)
+                if (c < d.nc) C[co + cco[c]] = epi_scale(acc[c], d.as);
+        } else {
 #pragma unroll
-            for (int j = 0; j < 8; j++) old[j] = (d.bcase != 0 && c0 + j < d.nc) ? C[co + cco[c0 + j]] : 0.0;
+            for (int c0 = 0; c0 < NC; c0 += 8) {
+                double old[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++)
-                if (c0 + j < d.nc) {
-                    const double v = epi_scale(acc[c0 + j], d.as);
-                    C[co + cco[c0 + j]] = d.bcase == 0 ? v : d.bcase == 1 ? v + old[j] : fma(d.beta, old[j], v);
-                }
+                for (int j = 0; j < 8; j++) old[j] = c0 + j < d.nc ? C[co + cco[c0 + j]] : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (c0 + j < d.nc) C[co + cco[c0 + j]] = epi_scale(acc[c0 + j], d.as) + old[j];
+            }
         }
     }
 }
@@ -280,12 +331,18 @@ __global__ void __launch_bounds__(256) rows_gemm_kernel(const RowsGemmDesc d, co
 template <typename CT>
 static cudaError_t rows_t(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s) {
     int64_t blocks = (d.R + 255) / 256;
-    if (blocks > 148 * 8) blocks = 148 * 8;
+    if (blocks > 148 * 3) blocks = 148 * 3;
     const unsigned b = (unsigned)blocks;
-    if (d.nc <= 8) rows_gemm_kernel<CT, 8><<<b, 256, 0, s>>>(d, X, Y, C);
-    else if (d.nc <= 16) rows_gemm_kernel<CT, 16><<<b, 256, 0, s>>>(d, X, Y, C);
-    else if (d.nc <= 32) rows_gemm_kernel<CT, 32><<<b, 256, 0, s>>>(d, X, Y, C);
-    else rows_gemm_kernel<CT, 64><<<b, 256, 0, s>>>(d, X, Y, C);
+    // accumulators: the column count rounded up to a multiple of 8
+    switch ((d.nc + 7) / 8) {
+        case 1: rows_gemm_kernel<CT, 8><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        case 2: rows_gemm_kernel<CT, 16><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        case 3: rows_gemm_kernel<CT, 24><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        case 4: rows_gemm_kernel<CT, 32><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        case 5: rows_gemm_kernel<CT, 40><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        case 6: rows_gemm_kernel<CT, 48><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        default: rows_gemm_kernel<CT, 64><<<b, 256, 0, s>>>(d, X, Y, C); break;
+    }
     return cudaGetLastError();
 }
 
@@ -295,6 +352,11 @@ cudaError_t launch_rows_gemm(const RowsGemmDesc &d0, const double *X, const doub
     d.bcase = beta_case(d.beta);
     d.as = make_scale(d.alpha);
     if (d.nc < 1 || d.nc > 64 || d.K < 1 || d.K > 64 || d.R > 0xffffffffLL) return cudaErrorInvalidValue;
+    if (d.bcase == 2) {
+        if (cudaError_t e = launch_scale_grp(d.R, d.nc, d.cr, d.cc, d.beta, C, s)) return e;
+        d.beta = 1.0;
+        d.bcase = 1;
+    }
     return d.f32 ? rows_t<float>(d, X, Y, C, s) : rows_t<double>(d, X, Y, C, s);
 }
 
@@ -421,7 +483,7 @@ cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double 
 }
 
 template <typename T, typename CT>
-static cudaError_t gemm_t(const GemmF64Desc &d, const T *A, const T *B, T *C, T *partials, cudaStream_t s) {
+static cudaError_t gemm_t(GemmF64Desc d, const T *A, const T *B, T *C, T *partials, cudaStream_t s) {
     if (d.K == 1 && d.M > 1 && d.N > 1) {
         int64_t sm = d.cm.nd ? d.cm.str[d.cm.nd - 1] : 0, sn = d.cn.nd ? d.cn.str[d.cn.nd - 1] : 0;
         int64_t blocks = (d.M * d.N + 255) / 256;
@@ -448,6 +510,12 @@ static cudaError_t gemm_t(const GemmF64Desc &d, const T *A, const T *B, T *C, T 
     const bool ak = d.sAk == 1 && !(d.sAm == 1 && d.K == 1);
     const bool bk = d.sBk == 1 && !(d.sBn == 1 && d.K == 1);
     if (zs > 1) m_fast = 1;
+    if (zs == 1 && d.bcase == 2) {
+        // general beta: C *= beta first, then the kernel accumulates
+        if (cudaError_t e = scale_grp_t<T>(d.M, d.N, d.cm, d.cn, d.beta, C, s)) return e;
+        d.beta = 1.0;
+        d.bcase = 1;
+    }
     if (ak && bk) gemm_f64_kernel<T, CT, true, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
     else if (ak) gemm_f64_kernel<T, CT, true, false><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);
     else if (bk) gemm_f64_kernel<T, CT, false, true><<<grid, 256, 0, s>>>(d, A, B, C, partials, m_fast, kchunk);

@@ -183,6 +183,8 @@ cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double 
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
                                  double alpha, double beta, double *C, cudaStream_t s);
 cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s);
+// C(m,n) *= beta over an M x N output addressed by two mixed-radix groups
+cudaError_t launch_scale_grp(int64_t M, int64_t N, const Grp &cm, const Grp &cn, double beta, double *C, cudaStream_t s);
 // the split kernels' double -> float rounding (mine) next to the library's (ref)
 cudaError_t launch_convert_selftest(const double *in, int64_t n, float *mine, float *ref, cudaStream_t s);
 // 1/D for rank 1..3 amplitude arrays (complex: the same value on both parts)

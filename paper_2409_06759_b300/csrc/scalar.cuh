@@ -14,8 +14,12 @@ namespace ccb {
 // double2 holding an interleaved complex double (re, im).
 __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
 __device__ __forceinline__ double2 ld(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ double neg(double x) {           // sign bit only (no FP64 instruction)
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ double2 neg(double2 x) { return make_double2(neg(x.x), neg(x.y)); }
 __device__ __forceinline__ double cj(double x, int) { return x; }
-__device__ __forceinline__ double2 cj(double2 x, int c) { return c ? make_double2(x.x, -x.y) : x; }
+__device__ __forceinline__ double2 cj(double2 x, int c) { return c ? make_double2(x.x, neg(x.y)) : x; }
 __device__ __forceinline__ double mul(double a, double b) { return a * b; }
 __device__ __forceinline__ double2 mul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -44,27 +48,23 @@ __device__ __forceinline__ float cfma(float a, float b, float acc) { return fmaf
 // kernels spend at most one FP64 operation per term.  A +-1 sign is an add or
 // a subtract (the first term a free negation); alpha = +-1 and beta in {0, 1}
 // cost nothing or one add.
-__device__ __forceinline__ double neg(double x) {           // sign bit only (no FP64 instruction)
-    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
-}
-__device__ __forceinline__ double2 neg(double2 x) { return make_double2(neg(x.x), neg(x.y)); }
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double sub(double a, double b) { return a - b; }
 __device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 // acc (+|-) x, the first term taken as +-x
+// (the sign is applied on the integer pipe, so a term is one add however the
+// compiler resolves the selects)
 template <typename T> __device__ __forceinline__ T signed_term(bool first, bool negative, T x, T acc) {
-    if (first) return negative ? neg(x) : x;
-    return negative ? sub(acc, x) : add(acc, x);
+    const T sx = negative ? neg(x) : x;
+    return first ? sx : add(acc, sx);
 }
-// alpha * acc + beta * old: alpha = +-2^k on the integer pipe, beta in {0, 1}
-// at most one FP64 add (bcase = beta_case(beta))
-template <typename T>
-__device__ __forceinline__ T finish(const Scale &as, T acc, int bcase, double beta, const T *o) {
+// alpha * acc (+ old when ACC, i.e. beta = 1): alpha = +-2^k on the integer
+// pipe, so at most one FP64 add.  A general beta is applied beforehand by a
+// separate scaling pass (the kernels are compiled for beta in {0, 1} only).
+template <bool ACC, typename T> __device__ __forceinline__ T finish(const Scale &as, T acc, const T &old) {
     const T v = scale_f64(acc, as);
-    if (bcase == 1) return add(v, *o);
-    if (bcase == 2) return axpy(beta, *o, v);
-    return v;
+    return ACC ? add(v, old) : v;
 }
 // acc + a * b over complex (or real) numbers
 __device__ __forceinline__ double cfma(double a, double b, double acc) { return fma(a, b, acc); }

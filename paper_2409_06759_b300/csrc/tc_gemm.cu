@@ -24,18 +24,25 @@ __device__ __forceinline__ int64_t grp_off(const Grp &g, int64_t x) {
     return off;
 }
 
-// Warps take (row, 1024-column span) items; lane l converts columns
-// [8l, 8l+8) of each 256-column chunk and stores 16 bytes per plane.  When the
-// K group's innermost index has unit stride and every other stride keeps
-// 16-byte alignment, the eight sources are read as four double2 loads.
-// The split runs in FP32 after one rounding of x to FP32 (24 significant
-// bits, as many as three bf16 planes hold): the remainders x_f - hi and
-// r - mid are exact in FP32, and the FP64 pipe of sm_103a -- a few
-// operations per clock per SM -- is used only for that one conversion.
-// the unit scale, and v + beta * old with beta classified (bcase)
 __device__ __forceinline__ Scale unit_scale() { return Scale{0, 0, 0u, 1.0}; }
-__device__ __forceinline__ double epi_out(double v, const TcGemmDesc &d, double old) {
-    return d.bcase == 0 ? v : d.bcase == 1 ? v + old : fma(d.beta, old, v);
+// C[roff + co[j]] = v[j] (bcase 0) or += v[j] (bcase 1; a general beta was
+// applied to C beforehand), skipping co[j] < 0.  The branch is taken once per
+// batch, so the FP64 add exists only on the accumulating side.
+template <int NB>
+__device__ __forceinline__ void store_batch(double *__restrict__ C, int64_t roff, const int64_t *co, const double *v,
+                                            int bcase) {
+    if (bcase == 0) {
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (co[j] >= 0) C[roff + co[j]] = v[j];
+    } else {
+        double old[NB];
+#pragma unroll
+        for (int j = 0; j < NB; j++) old[j] = co[j] >= 0 ? C[roff + co[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (co[j] >= 0) C[roff + co[j]] = v[j] + old[j];
+    }
 }
 
 __global__ void convert_selftest_kernel(const double *in, int64_t n, float *mine, float *ref) {
@@ -45,6 +52,9 @@ __global__ void convert_selftest_kernel(const double *in, int64_t n, float *mine
     }
 }
 
+// The split runs in FP32 after one rounding of x to FP32 on the integer pipe
+// (24 significant bits, as many as three bf16 planes hold): the remainders
+// x_f - hi and r - mid are exact in FP32, so no FP64 instruction is spent.
 __device__ __forceinline__ void split3(double x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
     const float xf = f64_to_f32_rn(x);
     h = __float2bfloat16_rn(xf);
@@ -72,6 +82,10 @@ __device__ __forceinline__ double src_at(const SplitDesc &d, const double *__res
     return neg ? -val : val;
 }
 
+// Long contiguous K: warps take (row, 1024-column span) items; lane l converts
+// columns [8l, 8l+8) of each 256-column chunk and stores 16 bytes per plane.
+// When the K group's innermost index has unit stride and every other stride
+// keeps 16-byte alignment, the eight sources are read as four double2 loads.
 __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, const double *__restrict__ x,
                                                          __nv_bfloat16 *__restrict__ planes, int vec) {
     const int64_t plane_elems = d.Rp * d.Kp;
@@ -115,39 +129,130 @@ __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, cons
     }
 }
 
-// Transposed variant for sources whose unit stride lies in the row group:
-// a 32-row x 64-column tile is read with lanes along rows (coalesced), staged
-// in shared memory, and written K-major (16 bytes per lane per plane).
-__global__ void __launch_bounds__(256) split_bf16_rows_kernel(const SplitDesc d, const double *__restrict__ x,
-                                                              __nv_bfloat16 *__restrict__ planes) {
-    __shared__ double tile[64][33];
+// Tiled split for every layout but the long contiguous-K one: a 64-row x
+// 64-column tile whose row and column offsets are decomposed once per tile
+// (one mixed-radix decomposition per row and per column, kept in shared
+// memory) instead of once per element.  LK: lanes run along K (the source's
+// unit stride is K's innermost digit), else along rows.  The 16 loads of a
+// thread are issued before any arithmetic; each value is rounded to FP32 as
+// it arrives -- alternately by the conversion instruction (FP64 pipe) and on
+// the integer pipe, so neither pipe limits the kernel -- and the FP32 tile is
+// staged in shared memory and written K-major, 16 bytes per lane per plane,
+// two values per bf16 conversion.  NPL: planes (2 or 3); CPLX: complex modes.
+__device__ __forceinline__ double src_tile(const SplitDesc &d, const double *__restrict__ x, int64_t r, int64_t ro,
+                                           int64_t k, int64_t ko) {
+    const int kc = (int)(k & 1);
+    if (d.cplx == 1) {
+        const double val = __ldg(x + ro + ko + kc);
+        return (d.conj && kc) ? -val : val;
+    }
+    const int rc = (int)(r & 1), comp = rc ^ kc;
+    const double val = __ldg(x + ro + ko + comp);
+    const bool neg = (rc == 0 && kc == 1) != (d.conj && comp == 1);
+    return neg ? -val : val;
+}
+
+// eight FP32 values -> NPL bf16 planes (hi, mid[, lo]); the remainders are exact in FP32
+template <int NPL>
+__device__ __forceinline__ void split8(const float *f, uint4 &H, uint4 &M, uint4 &L) {
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        const float2 hf = __bfloat1622float2(h2);
+        const float r0 = f[2 * j] - hf.x, r1 = f[2 * j + 1] - hf.y;
+        const __nv_bfloat162 m2 = __floats2bfloat162_rn(r0, r1);
+        h[j] = *reinterpret_cast<const uint32_t *>(&h2);
+        m[j] = *reinterpret_cast<const uint32_t *>(&m2);
+        if (NPL == 3) {
+            const float2 mf = __bfloat1622float2(m2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+            l[j] = *reinterpret_cast<const uint32_t *>(&l2);
+        } else {
+            l[j] = 0u;
+        }
+    }
+    H = make_uint4(h[0], h[1], h[2], h[3]);
+    M = make_uint4(m[0], m[1], m[2], m[3]);
+    L = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <bool LK, int NPL, bool CPLX>
+__global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, const double *__restrict__ x,
+                                                         __nv_bfloat16 *__restrict__ planes, uint32_t rtiles,
+                                                         uint32_t ntiles) {
+    __shared__ float tile[64][65];
+    __shared__ int64_t ro[64], ko[64];
     const int64_t plane_elems = d.Rp * d.Kp;
-    const int64_t rtiles = (d.Rp + 31) / 32, ktiles = d.Kp / 64;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    for (int64_t t = blockIdx.x; t < rtiles * ktiles; t += gridDim.x) {
-        const int64_t r0 = (t % rtiles) * 32, k0 = (t / rtiles) * 64;
-        const int64_t r = r0 + tx;
-        const bool rok = r < d.R;
-        const int64_t roff = rok ? row_offset(d, r) : 0;
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int64_t k = k0 + ty + 8 * j;
-            tile[ty + 8 * j][tx] = (rok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = (int64_t)(t % rtiles) * 64, k0 = (int64_t)(t / rtiles) * 64;
+        __syncthreads();                       // the previous tile's reads of tile/ro/ko are done
+        if (tid < 64) {
+            const int64_t r = r0 + tid;
+            ro[tid] = r < d.R ? row_offset(d, r) : -1;
+        } else if (tid < 128) {
+            const int64_t k = k0 + tid - 64;
+            ko[tid - 64] = k < d.K ? grp_off(d.gk, CPLX ? (k >> 1) : k) : -1;
         }
         __syncthreads();
-        // 32 rows x 64 columns = 256 runs of 8 columns: one per thread
-        const int rr = threadIdx.x >> 3, kk = (threadIdx.x & 7) * 8;
-        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+        double v[16];
+        // element e of the thread: (row, col) = LK ? (warp + 8 (e/2), lane + 32 (e%2))
+        //                                          : (lane + 32 (e%2), warp + 8 (e/2))
+        const int64_t oA = LK ? ko[lane] : ro[lane], oB = LK ? ko[lane + 32] : ro[lane + 32];
 #pragma unroll
-        for (int j = 0; j < 8; j++) split3(tile[kk + j][rr], h[j], m[j], l[j]);
-        const int64_t row = r0 + rr;
-        if (row < d.Rp) {
-            __nv_bfloat16 *p0 = planes + row * d.Kp + k0 + kk;
-            *reinterpret_cast<uint4 *>(p0) = *reinterpret_cast<const uint4 *>(h);
-            *reinterpret_cast<uint4 *>(p0 + plane_elems) = *reinterpret_cast<const uint4 *>(m);
-            if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = *reinterpret_cast<const uint4 *>(l);
+        for (int i = 0; i < 8; i++) {
+            const int w = warp + 8 * i;
+            const int64_t ow = LK ? ro[w] : ko[w];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int64_t oo = h ? oB : oA;
+                const int q = lane + 32 * h;
+                const int rr = LK ? w : q, kk = LK ? q : w;
+                const bool ok = ow >= 0 && oo >= 0;
+                if (CPLX)
+                    v[2 * i + h] = ok ? src_tile(d, x, r0 + rr, ro[rr], k0 + kk, ko[kk]) : 0.0;
+                else
+                    v[2 * i + h] = ok ? __ldg(x + ow + oo) : 0.0;
+            }
         }
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int w = warp + 8 * i, q = lane + 32 * h;
+                const float f = h ? f64_to_f32_rn(v[2 * i + h]) : __double2float_rn(v[2 * i + h]);
+                if (LK) tile[w][q] = f;
+                else tile[q][w] = f;
+            }
+        __syncthreads();
+        // 64 rows x 8 runs of 8 columns: two runs per thread
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int run = tid + 256 * q, rr = run >> 3, kk = (run & 7) * 8;
+            float f[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) f[j] = tile[rr][kk + j];
+            uint4 H, M, L;
+            split8<NPL>(f, H, M, L);
+            __nv_bfloat16 *p0 = planes + (r0 + rr) * d.Kp + k0 + kk;
+            *reinterpret_cast<uint4 *>(p0) = H;
+            *reinterpret_cast<uint4 *>(p0 + plane_elems) = M;
+            if (NPL == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = L;
+        }
+    }
+}
+
+template <bool LK>
+static void split_tile_launch(const SplitDesc &d, const double *x, void *planes, unsigned blocks, uint32_t rtiles,
+                              uint32_t ntiles, cudaStream_t s) {
+    __nv_bfloat16 *p = (__nv_bfloat16 *)planes;
+    if (d.cplx) {
+        if (d.nplanes == 3) split_tile_kernel<LK, 3, true><<<blocks, 256, 0, s>>>(d, x, p, rtiles, ntiles);
+        else split_tile_kernel<LK, 2, true><<<blocks, 256, 0, s>>>(d, x, p, rtiles, ntiles);
+    } else {
+        if (d.nplanes == 3) split_tile_kernel<LK, 3, false><<<blocks, 256, 0, s>>>(d, x, p, rtiles, ntiles);
+        else split_tile_kernel<LK, 2, false><<<blocks, 256, 0, s>>>(d, x, p, rtiles, ntiles);
     }
 }
 
@@ -160,19 +265,25 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
     const int64_t unit = d.cplx ? 2 : 1;
     const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit;
     const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == unit;
-    if (r_unit && !k_unit) {
-        const int64_t tiles = ((d.Rp + 31) / 32) * (d.Kp / 64);
-        int64_t blocks = tiles < 148 * 16 ? tiles : 148 * 16;
-        split_bf16_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes);
-        return cudaGetLastError();
-    }
-    // vector path: innermost K digit contiguous with an extent that keeps the
-    // 8-column runs inside it (4 complex elements when stacked), every other
-    // stride even (16-byte aligned double2), base aligned; not for embedded
+    // vector path: long contiguous K (whole 1024-column spans per warp item)
     int vec = d.cplx != 2 && d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit &&
               d.gk.ext[d.gk.nd - 1] % (d.cplx ? 4 : 8) == 0 && ((uintptr_t)x & 15) == 0;
     for (int q = 0; q + 1 < d.gk.nd; q++) vec &= (d.gk.str[q] % 2) == 0;
     for (int q = 0; q < d.gr.nd; q++) vec &= (d.gr.str[q] % 2) == 0;
+    const int64_t rtiles = (d.Rp + 63) / 64, ntiles = rtiles * (d.Kp / 64);
+    if (!(vec && d.K >= 512) && ntiles <= 0xffffffffLL) {
+        // lanes along K when K's innermost digit is the unit stride, or when
+        // neither side has one and K's innermost stride is the smaller
+        const int64_t ks = d.gk.nd >= 1 ? d.gk.str[d.gk.nd - 1] : 0, rs = d.gr.nd >= 1 ? d.gr.str[d.gr.nd - 1] : 0;
+        const bool lk = k_unit || (!r_unit && ks <= rs);
+        const unsigned blocks = (unsigned)(ntiles < 148 * 5 ? ntiles : 148 * 5);
+        if (lk) split_tile_launch<true>(d, x, planes, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
+        else split_tile_launch<false>(d, x, planes, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
+        return cudaGetLastError();
+    }
+    // vec: innermost K digit contiguous with an extent that keeps the 8-column
+    // runs inside it (4 complex elements when stacked), every other stride even
+    // (16-byte aligned double2), base aligned; not for embedded
     const int64_t items = d.Rp * ((d.Kp + 1023) / 1024);
     int64_t blocks = (items + 7) / 8;
     if (blocks > 148 * 16) blocks = 148 * 16;
@@ -449,17 +560,14 @@ __global__ void __launch_bounds__(192, 1)
                 tmem_ld_wait();
                 if (mok) {
                     // loads of the 32 outputs are issued together, then the stores
-                    double old[32];
+                    double v[32];
+                    int64_t co[32];
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
-                        const int64_t co = coloff[c0 + j];
-                        old[j] = (d.bcase != 0 && co >= 0) ? C[roff + co] : 0.0;
+                        co[j] = coloff[c0 + j];
+                        v[j] = f32_to_f64_scaled(__uint_as_float(r[j]), d.as);
                     }
-#pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const int64_t co = coloff[c0 + j];
-                        if (co >= 0) C[roff + co] = epi_out(f32_to_f64_scaled(__uint_as_float(r[j]), d.as), d, old[j]);
-                    }
+                    store_batch<32>(C, roff, co, v, d.bcase);
                 }
             }
         }
@@ -657,18 +765,14 @@ __global__ void __launch_bounds__(320, 1)
                         // read-modify-write in two batches of 16 (loads issued before the stores)
 #pragma unroll
                         for (int h = 0; h < 32; h += 16) {
-                            double old[16];
+                            double v[16];
+                            int64_t co[16];
 #pragma unroll
                             for (int jj = 0; jj < 16; jj++) {
-                                const int64_t co = coloff[c0 + h + jj];
-                                old[jj] = (d.bcase != 0 && co >= 0) ? C[roff + co] : 0.0;
+                                co[jj] = coloff[c0 + h + jj];
+                                v[jj] = f32_to_f64_scaled(__uint_as_float(r[h + jj]), d.as);
                             }
-#pragma unroll
-                            for (int jj = 0; jj < 16; jj++) {
-                                const int64_t co = coloff[c0 + h + jj];
-                                if (co >= 0)
-                                    C[roff + co] = epi_out(f32_to_f64_scaled(__uint_as_float(r[h + jj]), d.as), d, old[jj]);
-                            }
+                            store_batch<16>(C, roff, co, v, d.bcase);
                         }
                     }
                 }
@@ -872,20 +976,16 @@ __global__ void __launch_bounds__(320, 1)
             } else {
 #pragma unroll
                 for (int j0 = 0; j0 < HALF; j0 += 16) {
-                    double old[16];
+                    double v[16];
+                    int64_t co[16];
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
-                        const int64_t co = coloff[h * HALF + j0 + j];
-                        old[j] = (d.bcase != 0 && co >= 0) ? C[roff + co] : 0.0;
+                        co[j] = coloff[h * HALF + j0 + j];
+                        v[j] = scale_f64(f32_to_f64_scaled(hi[j0 + j], unit_scale()) +
+                                             f32_to_f64_scaled(lo[j0 + j], unit_scale()),
+                                         d.as);
                     }
-#pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const int64_t co = coloff[h * HALF + j0 + j];
-                        if (co >= 0)
-                            C[roff + co] = epi_out(scale_f64(f32_to_f64_scaled(hi[j0 + j], unit_scale()) +
-                                                                 f32_to_f64_scaled(lo[j0 + j], unit_scale()), d.as),
-                                                   d, old[j]);
-                    }
+                    store_batch<16>(C, roff, co, v, d.bcase);
                 }
             }
         }
@@ -1040,6 +1140,12 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d0, const void *Aplanes, const void
     d.bcase = beta_case(d.beta);
     d.as = make_scale(d.alpha);
     if (d.nplanes_a != d.nplanes_b || d.nprod < 1 || d.nprod > 8) return cudaErrorInvalidValue;
+    if (d.bcase == 2 && d.splitk <= 1) {
+        // general beta: C *= beta first, then accumulate
+        if (cudaError_t e = launch_scale_grp(d.M, d.N, d.cm, d.cn, d.beta, C, s)) return e;
+        d.beta = 1.0;
+        d.bcase = 1;
+    }
     if (((uintptr_t)Aplanes & 1023) || ((uintptr_t)Bplanes & 1023) || d.Kp < 64) {
         // TMA needs 16-byte aligned bases; the planner hands out 256-byte aligned workspace
         if (((uintptr_t)Aplanes & 15) || ((uintptr_t)Bplanes & 15)) return cudaErrorMisalignedAddress;
