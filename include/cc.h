@@ -176,7 +176,8 @@ CC_API cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_am
                              void *ws, size_t ws_bytes, void *stream);
 
 /* cc_plan_autotune -- picks, for every contraction of the plan, the GEMM
- * configuration (tensor-core tile width 64/128/256 and split-K factor on the
+ * configuration (tensor-core tile width 64/128/256, split-K factor and, for
+ * an accumulating contraction, read-modify-write or reduction epilogue on the
  * split-bf16 route; split-K factor on the FP64/FP32 tiled route) that runs
  * fastest on this device for these inputs: each candidate the plan prepared
  * room for is timed reps times (CUDA events, minimum taken) in place of the
@@ -187,6 +188,15 @@ CC_API cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_am
  *   reps: 1..100 timings per candidate.  Synchronises the stream. */
 CC_API cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res,
                                   void *ws, size_t ws_bytes, void *stream, int reps);
+
+/* cc_plan_set_gemm_config -- sets the configuration of one contraction step
+ * (the steps of cc_plan_describe, 0-based) to one of its autotuning
+ * candidates, e.g. to replay a configuration chosen by cc_plan_autotune.
+ *   bn: tensor-core tile width (64, 128, 256; 0 on the FP64/FP32 route);
+ *   splitk: split-K factor; red: 1 = epilogue by red.global.add.f64 (only
+ *   for accumulating contractions without split K), else 0.
+ * Returns CC_ERR_INVALID_ARG when the step has no such candidate. */
+CC_API cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red);
 
 /* cc_energy -- E_CC - E_ref = 1/4 sum <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b
  * (f_ia = 0).  e_dev: device double[2] receiving (Re E, Im E) (Im E = 0 for

@@ -33,7 +33,7 @@ EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_
            "cc_residual", "cc_energy", "cc_solve_workspace_bytes", "cc_solve", "cc_integral_block_elems",
            "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_status_string",
            "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched",
-           "cc_plan_autotune", "cc_build_vvvv_packed_workspace_bytes", "cc_build_vvvv_packed",
+           "cc_plan_autotune", "cc_plan_set_gemm_config", "cc_build_vvvv_packed_workspace_bytes", "cc_build_vvvv_packed",
            "cc_selftest_wait_timeout", "cc_selftest_convert"]
 
 if not os.path.exists(LIB_PATH):
@@ -97,6 +97,7 @@ _sig = {
     "cc_solve_batched_workspace_bytes": (c_int, [c_int, _P(c_void_p), _P(cc_solve_opts), _P(c_size_t)]),
     "cc_solve_batched": (c_int, [c_int, _P(c_void_p), _P(cc_integrals), _P(cc_amps), _P(cc_solve_opts),
                                  _P(cc_solve_report), c_void_p, c_size_t, c_void_p]),
+    "cc_plan_set_gemm_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "cc_plan_autotune": (c_int, [c_void_p, _P(cc_integrals), _P(cc_amps), _P(cc_resid), c_void_p, c_size_t, c_void_p,
                                  c_int]),
     "cc_build_vvvv_packed_workspace_bytes": (c_int, [c_int, c_int, c_int, c_int, _P(c_size_t)]),
@@ -252,6 +253,11 @@ def cc_residual(plan: Plan, ints: dict, t1, t2, r1, r2, ws, stream=None, t3=None
     R = cc_resid(_ptr(r1), _ptr(r2), _ptr(r3))
     _check(_lib.cc_residual(plan.handle, ctypes.byref(I), ctypes.byref(A), ctypes.byref(R), _ptr(ws), _nbytes(ws),
                             _stream(stream)), "cc_residual")
+
+
+def cc_plan_set_gemm_config(plan: Plan, step: int, bn: int, splitk: int, red: int = 0):
+    """Sets one contraction step to one of its autotuning candidates."""
+    _check(_lib.cc_plan_set_gemm_config(plan.handle, step, bn, splitk, red), "cc_plan_set_gemm_config")
 
 
 def cc_plan_autotune(plan: Plan, ints: dict, t1, t2, r1, r2, ws, reps: int = 3, stream=None, t3=None, r3=None):

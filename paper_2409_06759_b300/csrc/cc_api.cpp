@@ -450,12 +450,13 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
         if (st != CC_OK) { result = st; break; }
         if (stp.cands.size() < 2) continue;
         double best = 1e30;
-        std::array<int, 2> pick = stp.cands[0];
+        std::array<int, 3> pick = stp.cands[0];
         for (const auto &c : stp.cands) {
             Step trial = stp;
             if (trial.mixed) {
                 trial.tc.bn = c[0];
                 trial.tc.splitk = c[1];
+                trial.tc.red = c[2];
             } else {
                 trial.gemm.splitk = c[1];
             }
@@ -478,6 +479,7 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
         if (stp.mixed) {
             stp.tc.bn = pick[0];
             stp.tc.splitk = pick[1];
+            stp.tc.red = pick[2];
         } else {
             stp.gemm.splitk = pick[1];
         }
@@ -489,6 +491,25 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
         plan->cache_filled = false;
     }
     return result;
+}
+
+cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red) {
+    if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
+    Plan &P = plan->plan;
+    if (step < 0 || step >= (int)P.steps.size()) return fail(CC_ERR_INVALID_ARG, "step index out of range");
+    Step &stp = P.steps[step];
+    const std::array<int, 3> want{bn, splitk, red};
+    bool found = false;
+    for (const auto &c : stp.cands) found = found || c == want;
+    if (!found) return fail(CC_ERR_INVALID_ARG, "not a candidate configuration of this step");
+    if (stp.mixed) {
+        stp.tc.bn = bn;
+        stp.tc.splitk = splitk;
+        stp.tc.red = red;
+    } else {
+        stp.gemm.splitk = splitk;
+    }
+    return CC_OK;
 }
 
 cc_status cc_energy(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, double *e_dev, void *ws,
@@ -594,7 +615,8 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
     }
     cc_resid Rd{dlr[1], dlr[2], dlr[3]};
     double *dinv = (double *)(sreg + L.dinv);
-    {
+    if (!o.resume) {
+        // 1/D of every amplitude; a resumed solve (same integrals, plan and ws) keeps it
         int64_t off = 0;
         for (int l = 1; l <= 3; l++) {
             if (!r[l]) continue;

@@ -19,7 +19,6 @@ namespace ccb {
 // select is often executed speculatively for every element (if-conversion),
 // which would put it back on the FP64 pipe.
 static __device__ __noinline__ float d2f_slow(double x) { return __double2float_rn(x); }
-static __device__ __noinline__ double f2d_mul_slow(float f, double a) { return (double)f * a; }
 static __device__ __noinline__ double dmul_slow(double x, double a) { return x * a; }
 
 // double -> float, round to nearest even.  Normal results are formed from the
@@ -41,26 +40,40 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
     return __uint_as_float(f);
 }
 
-// alpha * (double)f, exact when alpha = +-2^k: a normal float's exponent is
-// rebiased (127 -> 1023) and shifted by k, its 23 mantissa bits move to the
-// top of the double's 52; zeros keep their (flipped) sign.
-__device__ __forceinline__ double f32_to_f64_scaled(float f, const Scale &s) {
+// 2^k * (+-f) as a double, exact, integer operations only (alpha = +-2^k,
+// |k| < 512, so every float -- subnormals included -- lands in the normal
+// double range): a normal float's exponent is rebiased (127 -> 1023) and
+// shifted by k and its 23 mantissa bits move to the top of the double's 52; a
+// subnormal is normalised at its leading one; zeros keep their (flipped) sign;
+// infinities and NaNs keep their payload.
+__device__ __forceinline__ double f32_to_f64_pow2(float f, int kexp, uint32_t sflip) {
     const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xffu;
-    const uint32_t flip = s.general ? 0u : s.sflip;
+    const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    const uint32_t sign = (u & 0x80000000u) ^ sflip;
     uint32_t hi, lo;
     if (e - 1u < 254u) {
-        const int ee = (int)e + 896 + (s.general ? 0 : s.kexp);
-        hi = ((u & 0x80000000u) ^ flip) | ((uint32_t)ee << 20) | ((u >> 3) & 0xfffffu);
-        lo = u << 29;
-    } else if ((u & 0x7fffffffu) == 0u) {
-        hi = (u & 0x80000000u) ^ flip;
+        hi = sign | ((uint32_t)((int)e + 896 + kexp) << 20) | (m >> 3);
+        lo = m << 29;
+    } else if (e == 255u) {
+        hi = sign | 0x7ff00000u | (m >> 3);
+        lo = m << 29;
+    } else if (m == 0u) {
+        hi = sign;
         lo = 0u;
     } else {
-        return f2d_mul_slow(f, s.value);                   // subnormal, inf, NaN
+        const int p = 31 - __clz((int)m);                       // leading one of m: value = 2^(p-149) * 1.x
+        const unsigned long long mm = ((unsigned long long)m << (52 - p)) & 0xfffffffffffffull;
+        hi = sign | ((uint32_t)(p + 874 + kexp) << 20) | (uint32_t)(mm >> 32);
+        lo = (uint32_t)mm;
     }
-    const double r = __hiloint2double((int)hi, (int)lo);
-    return s.general ? dmul_slow(r, s.value) : r;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// alpha * (double)f: the integer path for alpha = +-2^k; a general alpha
+// multiplies (callers that care choose between the two outside their loops)
+__device__ __forceinline__ double f32_to_f64_scaled(float f, const Scale &s) {
+    if (s.general) return dmul_slow((double)f, s.value);
+    return f32_to_f64_pow2(f, s.kexp, s.sflip);
 }
 
 // alpha * x, exact for alpha = +-2^k when x and the result are normal

@@ -556,15 +556,29 @@ __device__ __forceinline__ double vir_sum(int rank, int v, const double *fv, uin
 
 // cplx: the arrays are interleaved complex; column c of a row is component
 // c & 1 of virtual tuple c >> 1 (D is real).
+// sum of the rank virtual energies of a tuple with rank - 1 adds (the FP64
+// pipe issues ~2 operations per clock per SM: the per-element update below
+// is rank + 1 of them)
+__device__ __forceinline__ double vir_sum_lean(int rank, int v, const double *fv, uint32_t col) {
+    double s = fv[col % (uint32_t)v];
+    for (int k = 1; k < rank; k++) {
+        col /= (uint32_t)v;
+        s += fv[col % (uint32_t)v];
+    }
+    return s;
+}
+
 __global__ void __launch_bounds__(256) denom_sub_kernel(int rank, int o, int v, const double *fo, const double *fv,
-                                                        const double *t, double *r, int64_t rows, uint32_t nvt,
-                                                        int cplx) {
+                                                        const double *__restrict__ t, double *__restrict__ r,
+                                                        int64_t rows, uint32_t nvt, int cplx) {
     const uint32_t ncol = nvt << cplx;
     for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
         const double so = occ_sum(rank, o, fo, row);
         const int64_t base = row * ncol;
-        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x)
-            r[base + c] -= (so - vir_sum(rank, v, fv, c >> cplx)) * t[base + c];
+        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+            const double d = so - vir_sum_lean(rank, v, fv, c >> cplx);
+            r[base + c] = fma(neg(d), t[base + c], r[base + c]);
+        }
     }
 }
 
@@ -691,22 +705,29 @@ cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, dou
     return cudaGetLastError();
 }
 
+// E = sum_ijab <ij||ab> (t2_ijab / 4 + t1_ia t1_jb / 2), the spin-orbital
+// CC energy (the projection on Phi_0 of Eq. amp, Sec. II A).  Warps take rows (i, j, a) (a fixed mapping, so the
+// sum order is deterministic), lanes run along b; the row's t1_ia / 2 and the
+// t2 / 4 are exact scalings on the integer pipe, so an element costs two FMAs.
 template <typename T>
-__global__ void __launch_bounds__(256) energy_partials_kernel(int o, int v, const T *V, const T *t1, const T *t2,
+__global__ void __launch_bounds__(256) energy_partials_kernel(int o, int v, const T *__restrict__ V,
+                                                              const T *__restrict__ t1, const T *__restrict__ t2,
                                                               double *partials) {
-    const int64_t n = (int64_t)o * o * v * v;
+    const Scale half{0, -1, 0u, 0.5}, quarter{0, -2, 0u, 0.25};
+    const int lane = threadIdx.x & 31;
+    const uint32_t rows = (uint32_t)o * (uint32_t)o * (uint32_t)v;
     T s = zero<T>();
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)kRedBlocks * 256) {
-        T w = scal(0.25, t2[e]);
-        if (t1) {
-            int64_t x = e;
-            int b = (int)(x % v); x /= v;
-            int a = (int)(x % v); x /= v;
-            int j = (int)(x % o); x /= o;
-            int i = (int)x;
-            w = axpy(0.5, mul(t1[(int64_t)i * v + a], t1[(int64_t)j * v + b]), w);
+    for (uint32_t row = blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += kRedBlocks * 8) {
+        const uint32_t a = row % (uint32_t)v, ij = row / (uint32_t)v;
+        const uint32_t j = ij % (uint32_t)o, i = ij / (uint32_t)o;
+        const int64_t base = (int64_t)row * v;
+        const T c = t1 ? scale_f64(t1[(int64_t)i * v + a], half) : zero<T>();
+        const T *t1j = t1 ? t1 + (int64_t)j * v : nullptr;
+        for (int b = lane; b < v; b += 32) {
+            T w = scale_f64(t2[base + b], quarter);
+            if (t1) w = cfma(c, t1j[b], w);
+            s = cfma(V[base + b], w, s);
         }
-        s = cfma(V[e], w, s);
     }
     if constexpr (sizeof(T) == sizeof(double)) {
         const double r = block_sum(s);

@@ -944,13 +944,15 @@ struct Planner {
             // autotuning candidates: split-K factors (the partials buffer takes the largest)
             int64_t skmax = g.gemm.splitk;
             if (g.gemm.M > 1 && g.gemm.N > 1 && g.gemm.K > 1) {
-                g.cands.push_back({0, 1});
+                g.cands.push_back({0, 1, 0});
                 for (int sk : {2, 4, 8, 16, 32, 64})
                     if (sk <= g.gemm.K / 64 && sk * g.gemm.M * g.gemm.N * esz <= (int64_t)512 << 20) {
-                        g.cands.push_back({0, sk});
+                        g.cands.push_back({0, sk, 0});
                         skmax = std::max<int64_t>(skmax, sk);
                     }
-                if (g.gemm.splitk > 1) g.cands.push_back({0, g.gemm.splitk});
+                if (g.gemm.splitk > 1 &&
+                    std::find(g.cands.begin(), g.cands.end(), std::array<int, 3>{0, g.gemm.splitk, 0}) == g.cands.end())
+                    g.cands.push_back({0, g.gemm.splitk, 0});
                 if (g.cands.size() < 2) g.cands.clear();
             }
             if (skmax > 1) g.partials = scratch(skmax * g.gemm.M * g.gemm.N * esz);
@@ -1043,11 +1045,17 @@ struct Planner {
                 if (bn > bn_max) continue;
                 for (int sk : {1, 2, 4, 8, 16})
                     if (sk == 1 || (sk <= kblocks / 4 && sk * Mr * Nr * 8 <= (int64_t)512 << 20)) {
-                        g.cands.push_back({bn, sk});
+                        g.cands.push_back({bn, sk, 0});
                         skmax = std::max<int64_t>(skmax, sk);
                     }
-                if (bn == t.bn && t.splitk > 16) g.cands.push_back({bn, t.splitk});
+                // an accumulating GEMM without split K may also add its tile with
+                // fire-and-forget reductions (red.global.add.f64) instead of a
+                // read-modify-write: no load latency in the epilogue
+                if (gbeta == 1.0) g.cands.push_back({bn, 1, 1});
             }
+            // the planned configuration is always one of them
+            const std::array<int, 3> planned{t.bn, t.splitk, 0};
+            if (std::find(g.cands.begin(), g.cands.end(), planned) == g.cands.end()) g.cands.push_back(planned);
             if (g.cands.size() < 2) g.cands.clear();
             if (skmax > 1) g.partials = scratch(skmax * Mr * Nr * 8);
             t.nplanes_a = t.nplanes_b = np;
@@ -1176,6 +1184,15 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     return true;
 }
 
+// [[bn, splitk, red], ...] of a step's autotuning candidates
+static std::string cands_json(const std::vector<std::array<int, 3>> &c) {
+    std::string out = "[";
+    for (size_t k = 0; k < c.size(); k++)
+        out += (k ? ",[" : "[") + std::to_string(c[k][0]) + "," + std::to_string(c[k][1]) + "," +
+               std::to_string(c[k][2]) + "]";
+    return out + "]";
+}
+
 static void grp_json(std::ostringstream &os, const Grp &g) {
     os << "{\"ext\":[";
     for (int d = 0; d < g.nd; d++) os << (d ? "," : "") << g.ext[d];
@@ -1217,6 +1234,7 @@ std::string describe_plan(const Plan &plan) {
         if (s.kind == StepKind::GEMM && !s.mixed) {
             os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
                << ",\"splitk\":" << s.gemm.splitk << ",\"candidates\":" << s.cands.size()
+               << ",\"configs\":" << cands_json(s.cands)
                << ",\"sAm\":" << s.gemm.sAm << ",\"sAk\":" << s.gemm.sAk << ",\"sBk\":" << s.gemm.sBk
                << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta
                << ",\"conj_a\":" << s.gemm.conj_a << ",\"conj_b\":" << s.gemm.conj_b << ",\"cm\":";
@@ -1228,7 +1246,8 @@ std::string describe_plan(const Plan &plan) {
                << ",\"products\":" << s.tc.nprod << ",\"a_static\":" << (s.a_static ? 1 : 0)
                << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta
                << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp << ",\"bn\":" << s.tc.bn
-               << ",\"splitk\":" << s.tc.splitk << ",\"candidates\":" << s.cands.size()
+               << ",\"splitk\":" << s.tc.splitk << ",\"red\":" << s.tc.red << ",\"candidates\":" << s.cands.size()
+               << ",\"configs\":" << cands_json(s.cands)
                << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off
                << ",\"reuse_a\":" << (s.skip_a ? 1 : 0) << ",\"reuse_b\":" << (s.skip_b ? 1 : 0)
                << ",\"cplx_a\":" << s.split_a.cplx << ",\"cplx_b\":" << s.split_b.cplx

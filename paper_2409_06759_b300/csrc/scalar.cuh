@@ -41,7 +41,7 @@ template <> __device__ __forceinline__ double down<double>(double x) { return x;
 template <> __device__ __forceinline__ float down<float>(double x) { return f64_to_f32_rn(x); }
 template <typename CT> __device__ __forceinline__ CT down(double2 x) { return x; }
 __device__ __forceinline__ double up(double x) { return x; }
-__device__ __forceinline__ double up(float x) { return f32_to_f64_scaled(x, Scale{0, 0, 0u, 1.0}); }
+__device__ __forceinline__ double up(float x) { return f32_to_f64_pow2(x, 0, 0u); }
 __device__ __forceinline__ double2 up(double2 x) { return x; }
 __device__ __forceinline__ float cfma(float a, float b, float acc) { return fmaf(a, b, acc); }
 // B300's FP64 pipe issues ~2 operations per clock per SM: the elementwise

@@ -24,14 +24,24 @@ __device__ __forceinline__ int64_t grp_off(const Grp &g, int64_t x) {
     return off;
 }
 
-__device__ __forceinline__ Scale unit_scale() { return Scale{0, 0, 0u, 1.0}; }
 // C[roff + co[j]] = v[j] (bcase 0) or += v[j] (bcase 1; a general beta was
 // applied to C beforehand), skipping co[j] < 0.  The branch is taken once per
 // batch, so the FP64 add exists only on the accumulating side.
+// fire-and-forget FP64 add in L2 (no value returns to the SM)
+__device__ __forceinline__ void red_add(double *p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// (co may point to shared memory: each offset is read where it is used;
+// bcase 2 means red: C += v by reductions)
 template <int NB>
 __device__ __forceinline__ void store_batch(double *__restrict__ C, int64_t roff, const int64_t *co, const double *v,
                                             int bcase) {
-    if (bcase == 0) {
+    if (bcase == 2) {
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (co[j] >= 0) red_add(C + roff + co[j], v[j]);
+    } else if (bcase == 0) {
 #pragma unroll
         for (int j = 0; j < NB; j++)
             if (co[j] >= 0) C[roff + co[j]] = v[j];
@@ -42,6 +52,34 @@ __device__ __forceinline__ void store_batch(double *__restrict__ C, int64_t roff
 #pragma unroll
         for (int j = 0; j < NB; j++)
             if (co[j] >= 0) C[roff + co[j]] = v[j] + old[j];
+    }
+}
+// the same from raw FP32 accumulator bits: alpha * r[j] is formed as each
+// value is stored (integer pipe for alpha = +-2^k, a multiply otherwise, the
+// choice made once per batch), so only the bits and the old values are live
+template <int NB>
+__device__ __forceinline__ void store_batch_f32(double *__restrict__ C, int64_t roff, const int64_t *co,
+                                                const uint32_t *r, const Scale &as, int bcase) {
+    if (as.general) {
+        double v[NB];
+#pragma unroll
+        for (int j = 0; j < NB; j++) v[j] = (double)__uint_as_float(r[j]) * as.value;
+        store_batch<NB>(C, roff, co, v, bcase);
+    } else if (bcase == 0) {
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (co[j] >= 0) C[roff + co[j]] = f32_to_f64_pow2(__uint_as_float(r[j]), as.kexp, as.sflip);
+    } else if (bcase == 2) {
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (co[j] >= 0) red_add(C + roff + co[j], f32_to_f64_pow2(__uint_as_float(r[j]), as.kexp, as.sflip));
+    } else {
+        double old[NB];
+#pragma unroll
+        for (int j = 0; j < NB; j++) old[j] = co[j] >= 0 ? C[roff + co[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (co[j] >= 0) C[roff + co[j]] = f32_to_f64_pow2(__uint_as_float(r[j]), as.kexp, as.sflip) + old[j];
     }
 }
 
@@ -548,7 +586,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int64_t n = n0 + c0 + j;
-                        if (n < d.N) P[n * d.M + m] = f32_to_f64_scaled(__uint_as_float(r[j]), unit_scale());
+                        if (n < d.N) P[n * d.M + m] = f32_to_f64_pow2(__uint_as_float(r[j]), 0, 0u);
                     }
                 }
             }
@@ -560,14 +598,7 @@ __global__ void __launch_bounds__(192, 1)
                 tmem_ld_wait();
                 if (mok) {
                     // loads of the 32 outputs are issued together, then the stores
-                    double v[32];
-                    int64_t co[32];
-#pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        co[j] = coloff[c0 + j];
-                        v[j] = f32_to_f64_scaled(__uint_as_float(r[j]), d.as);
-                    }
-                    store_batch<32>(C, roff, co, v, d.bcase);
+                    store_batch_f32<32>(C, roff, coloff + c0, r, d.as, d.bcase);
                 }
             }
         }
@@ -759,21 +790,12 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                         for (int jj = 0; jj < 32; jj++) {
                             const int64_t n = coloff[c0 + jj];
-                            if (n >= 0) P[n * d.M + m] = f32_to_f64_scaled(__uint_as_float(r[jj]), unit_scale());
+                            if (n >= 0) P[n * d.M + m] = f32_to_f64_pow2(__uint_as_float(r[jj]), 0, 0u);
                         }
                     } else {
                         // read-modify-write in two batches of 16 (loads issued before the stores)
-#pragma unroll
-                        for (int h = 0; h < 32; h += 16) {
-                            double v[16];
-                            int64_t co[16];
-#pragma unroll
-                            for (int jj = 0; jj < 16; jj++) {
-                                co[jj] = coloff[c0 + h + jj];
-                                v[jj] = f32_to_f64_scaled(__uint_as_float(r[h + jj]), d.as);
-                            }
-                            store_batch<16>(C, roff, co, v, d.bcase);
-                        }
+                        store_batch_f32<16>(C, roff, coloff + c0, r, d.as, d.bcase);
+                        store_batch_f32<16>(C, roff, coloff + c0 + 16, r + 16, d.as, d.bcase);
                     }
                 }
             }
@@ -971,7 +993,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                 for (int j = 0; j < HALF; j++) {
                     const int64_t n = n0 + h * HALF + j;
-                    if (n < d.N) P[n * d.M + m] = f32_to_f64_scaled(hi[j], unit_scale()) + f32_to_f64_scaled(lo[j], unit_scale());
+                    if (n < d.N) P[n * d.M + m] = f32_to_f64_pow2(hi[j], 0, 0u) + f32_to_f64_pow2(lo[j], 0, 0u);
                 }
             } else {
 #pragma unroll
@@ -981,8 +1003,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
                         co[j] = coloff[h * HALF + j0 + j];
-                        v[j] = scale_f64(f32_to_f64_scaled(hi[j0 + j], unit_scale()) +
-                                             f32_to_f64_scaled(lo[j0 + j], unit_scale()),
+                        v[j] = scale_f64(f32_to_f64_pow2(hi[j0 + j], 0, 0u) + f32_to_f64_pow2(lo[j0 + j], 0, 0u),
                                          d.as);
                     }
                     store_batch<16>(C, roff, co, v, d.bcase);
@@ -1146,6 +1167,8 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d0, const void *Aplanes, const void
         d.beta = 1.0;
         d.bcase = 1;
     }
+    // the kernels' store mode: 0 store, 1 read-modify-write, 2 reductions
+    if (d.bcase == 1 && d.red && d.splitk <= 1) d.bcase = 2;
     if (((uintptr_t)Aplanes & 1023) || ((uintptr_t)Bplanes & 1023) || d.Kp < 64) {
         // TMA needs 16-byte aligned bases; the planner hands out 256-byte aligned workspace
         if (((uintptr_t)Aplanes & 15) || ((uintptr_t)Bplanes & 15)) return cudaErrorMisalignedAddress;

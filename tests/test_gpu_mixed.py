@@ -168,3 +168,39 @@ def test_autotuned_plan_keeps_the_residual(cc, prec, rel):
     o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
     dd = np.sqrt(np.sum((r1.cpu().numpy() - o1) ** 2) + np.sum((r2.cpu().numpy() - o2) ** 2))
     assert dd <= rel * np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
+
+
+@pytest.mark.parametrize("o,v", [(10, 40), (7, 45)])
+def test_every_gemm_configuration_gives_the_same_residual(cc, o, v):
+    """Each contraction step set, one at a time, to every autotuning candidate
+    (tile widths, split-K factors, and the reduction epilogue of accumulating
+    contractions) reproduces the planned configuration's residual: the
+    configurations differ only in the FP32 summation order inside a tile
+    column (split K) or the order in which L2 adds a tile (reductions), so the
+    difference stays at the split route's rounding level."""
+    ccm, engine = cc
+    s, B, t1, t2 = small_case(o, v, 33, L=16, scale=6.0, tscale=0.05)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
+    eng = engine.Engine(dsys, list_name="ccsd_vvvv", precision="bf16x3")
+    T1, T2 = to_dev(t1), to_dev(t2)
+    b1, b2 = eng.residual(T1, T2)
+    torch.cuda.synchronize()
+    base = torch.cat([b1.flatten(), b2.flatten()]).cpu().numpy()
+    scale = np.linalg.norm(base)
+    steps = eng.plan.describe()["steps"]
+    reds = 0
+    for k, st in enumerate(steps):
+        if st["kind"] != "gemm_bf16split" or not st.get("configs"):
+            continue
+        planned = (st["bn"], st["splitk"], st["red"])
+        for bn, sk, red in st["configs"]:
+            ccm.cc_plan_set_gemm_config(eng.plan, k, bn, sk, red)
+            r1, r2 = eng.residual(T1, T2)
+            torch.cuda.synchronize()
+            got = torch.cat([r1.flatten(), r2.flatten()]).cpu().numpy()
+            assert np.linalg.norm(got - base) <= 1e-5 * scale, (k, bn, sk, red)
+            reds += red
+        ccm.cc_plan_set_gemm_config(eng.plan, k, *planned)
+    assert reds > 0
+    with pytest.raises(RuntimeError):
+        ccm.cc_plan_set_gemm_config(eng.plan, 0, 999, 1, 0)
