@@ -48,7 +48,7 @@ def workload_name(args):
     return SMALL if args.small else WORKLOAD
 # DRAM bytes / operand-plane bytes of the ladder kernel, from its ncu capture (None until re-captured
 # after a kernel change)
-TRAFFIC_RATIO = 1.066
+TRAFFIC_RATIO = None
 
 
 def peaks():

@@ -17,7 +17,8 @@
 //   antisym_pairs   out = alpha P(ij) P(ab) src (4 terms, same index order):
 //                   each orbit {ijab, jiab, ijba, jiba} is read and written once
 //   accum_rows      every term reads its sources with stride 0 or 1 along the
-//                   output's innermost dim (copies, outer products T1 x T1)
+//                   output's innermost dim (copies, outer products T1 x T1,
+//                   and a copy fused into the next step: out = add + ...)
 //   accum_tiled     some term runs along another dim: 32 x 32 tiles through
 //                   shared memory (TTGT transposes, P(..) gathers)
 //   accum_kernel    anything else (odometer over the flat output index)
@@ -37,7 +38,8 @@ constexpr int kAccChunk = 8;
 
 template <typename T, bool ACC>
 __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *__restrict__ src,
-                                                    T *__restrict__ out, const T *__restrict__ src2) {
+                                                    T *__restrict__ out, const T *__restrict__ src2,
+                                                    const T *__restrict__ add) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -68,7 +70,17 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
                 }
                 acc = signed_term(p == 0, (d.negmask >> p) & 1ull, x, acc);
             }
-            out[oo] = finish<ACC>(d.as, acc, ACC ? out[oo] : zero<T>());
+            T old = zero<T>();
+            if (ACC) {
+                if (d.has_add) {
+                    int64_t ao = 0;
+                    for (int k = 0; k < d.nd; k++) ao += dig[k] * d.astr[k];
+                    old = add[ao];
+                } else {
+                    old = out[oo];
+                }
+            }
+            out[oo] = finish<ACC>(d.as, acc, old);
             // advance by 32 elements (compare-and-subtract carries)
             e += 32;
             int carry = 32;
@@ -95,7 +107,8 @@ constexpr int kRowU = 8;
 template <typename T, int NP, bool TWO, bool ACC>
 __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, const T *__restrict__ src,
                                                          const T *__restrict__ src2, T *__restrict__ out,
-                                                         uint32_t rows, int rch, uint32_t ncb) {
+                                                         const T *__restrict__ add, uint32_t rows, int rch,
+                                                         uint32_t ncb) {
     const int lane = threadIdx.x & 31;
     const int d0 = d.nd - 1;
     const int64_t E0 = d.ext[d0];
@@ -105,7 +118,9 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
         s0[p] = p < d.nperm ? d.sstr[p][d0] : 0;
         s02[p] = (TWO && p < d.nperm) ? d.sstr2[p][d0] : 0;
     }
-    const int64_t os0 = d.ostr[d0];
+    const int64_t os0 = d.ostr[d0], as0 = d.has_add ? d.astr[d0] : 0;
+    // the value accumulated onto: out itself, or a fused copy's source
+    const T *__restrict__ base_in = d.has_add ? add : out;
     const uint32_t nchunks = (uint32_t)((rows + (uint32_t)rch - 1) / (uint32_t)rch);
     const uint64_t items = (uint64_t)nchunks * ncb;
     for (uint64_t it = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < items; it += (uint64_t)gridDim.x * 8) {
@@ -114,7 +129,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
         const uint32_t r0 = chunk * (uint32_t)rch;
         // row digits of r0 over dims d0-1 .. 0, unrolled so they live in registers
         uint32_t dig[kMaxDims - 1];
-        int64_t obase = 0, sb[NP], sb2[NP];
+        int64_t obase = 0, abase = 0, sb[NP], sb2[NP];
 #pragma unroll
         for (int p = 0; p < NP; p++) sb[p] = sb2[p] = 0;
         uint32_t x = r0;
@@ -126,6 +141,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
                 dig[k] = x - q * e;
                 x = q;
                 obase += (int64_t)dig[k] * d.ostr[k];
+                if (ACC && d.has_add) abase += (int64_t)dig[k] * d.astr[k];
 #pragma unroll
                 for (int p = 0; p < NP; p++)
                     if (p < d.nperm) {
@@ -140,7 +156,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
 #pragma unroll
             for (int u = 0; u < kRowU; u++) {
                 const int64_t i = cb + lane + 32 * u;
-                old[u] = (ACC && i < E0) ? out[obase + i * os0] : zero<T>();
+                old[u] = (ACC && i < E0) ? base_in[(d.has_add ? abase + i * as0 : obase + i * os0)] : zero<T>();
             }
 #pragma unroll
             for (int p = 0; p < NP; p++) {
@@ -173,6 +189,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
             for (int k = kMaxDims - 2; k >= 0; k--) {
                 if (k < d0) {
                     obase += d.ostr[k];
+                    if (ACC && d.has_add) abase += d.astr[k];
 #pragma unroll
                     for (int p = 0; p < NP; p++)
                         if (p < d.nperm) {
@@ -182,6 +199,7 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
                     if (++dig[k] < (uint32_t)d.ext[k]) break;
                     dig[k] = 0;
                     obase -= d.ext[k] * d.ostr[k];
+                    if (ACC && d.has_add) abase -= d.ext[k] * d.astr[k];
 #pragma unroll
                     for (int p = 0; p < NP; p++)
                         if (p < d.nperm) {
@@ -383,6 +401,7 @@ static void collapse_dims(AccumDesc &d) {
         if (d.ext[k] == 1 && d.nd > 1) continue;
         d.ext[w] = d.ext[k];
         d.ostr[w] = d.ostr[k];
+        d.astr[w] = d.astr[k];
         for (int p = 0; p < d.nperm; p++) {
             d.sstr[p][w] = d.sstr[p][k];
             if (d.two_src) d.sstr2[p][w] = d.sstr2[p][k];
@@ -393,7 +412,7 @@ static void collapse_dims(AccumDesc &d) {
     d.nd = w;
     for (int k = d.nd - 2; k >= 0; k--) {
         const int64_t e = d.ext[k + 1];
-        bool ok = d.ostr[k] == d.ostr[k + 1] * e;
+        bool ok = d.ostr[k] == d.ostr[k + 1] * e && (!d.has_add || d.astr[k] == d.astr[k + 1] * e);
         for (int p = 0; p < d.nperm && ok; p++) {
             ok = d.sstr[p][k] == d.sstr[p][k + 1] * e;
             if (ok && d.two_src) ok = d.sstr2[p][k] == d.sstr2[p][k + 1] * e;
@@ -402,6 +421,7 @@ static void collapse_dims(AccumDesc &d) {
         // merge k+1 into k, shift the rest down
         d.ext[k] *= e;
         d.ostr[k] = d.ostr[k + 1];
+        d.astr[k] = d.astr[k + 1];
         for (int p = 0; p < d.nperm; p++) {
             d.sstr[p][k] = d.sstr[p][k + 1];
             if (d.two_src) d.sstr2[p][k] = d.sstr2[p][k + 1];
@@ -409,6 +429,7 @@ static void collapse_dims(AccumDesc &d) {
         for (int m = k + 1; m + 1 < d.nd; m++) {
             d.ext[m] = d.ext[m + 1];
             d.ostr[m] = d.ostr[m + 1];
+            d.astr[m] = d.astr[m + 1];
             for (int p = 0; p < d.nperm; p++) {
                 d.sstr[p][m] = d.sstr[p][m + 1];
                 if (d.two_src) d.sstr2[p][m] = d.sstr2[p][m + 1];
@@ -468,14 +489,15 @@ __global__ void __launch_bounds__(256) scale_view_kernel(const AccumDesc d, T *_
 }
 
 template <typename T, bool ACC>
-static cudaError_t accum_generic(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
+static cudaError_t accum_generic(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2,
+                                 const T *add) {
     int64_t runs = (d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
-    accum_kernel<T, ACC><<<(unsigned)grid_cap((runs + 7) / 8, 148 * 16), 256, 0, s>>>(d, src, out, src2);
+    accum_kernel<T, ACC><<<(unsigned)grid_cap((runs + 7) / 8, 148 * 16), 256, 0, s>>>(d, src, out, src2, add);
     return cudaGetLastError();
 }
 
 template <typename T, int NP, bool ACC>
-static cudaError_t rows_launch(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
+static cudaError_t rows_launch(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2, const T *add) {
     const int64_t E0 = d.ext[d.nd - 1];
     const int64_t rows = d.total / E0;
     const int64_t ncb = (E0 + 32 * kRowU - 1) / (32 * kRowU);
@@ -485,19 +507,19 @@ static cudaError_t rows_launch(const AccumDesc &d, const T *src, T *out, cudaStr
     const int64_t items = (rows + rch - 1) / rch * ncb;
     const unsigned blocks = (unsigned)grid_cap((items + 7) / 8, 148 * 16);
     if (d.two_src)
-        accum_rows_kernel<T, NP, true, ACC><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
+        accum_rows_kernel<T, NP, true, ACC><<<blocks, 256, 0, s>>>(d, src, src2, out, add, (uint32_t)rows, (int)rch,
                                                                    (uint32_t)ncb);
     else
-        accum_rows_kernel<T, NP, false, ACC><<<blocks, 256, 0, s>>>(d, src, src2, out, (uint32_t)rows, (int)rch,
-                                                                    (uint32_t)ncb);
+        accum_rows_kernel<T, NP, false, ACC><<<blocks, 256, 0, s>>>(d, src, src2, out, add, (uint32_t)rows,
+                                                                    (int)rch, (uint32_t)ncb);
     return cudaGetLastError();
 }
 
 template <typename T, bool ACC>
-static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream_t s, const T *src2) {
+static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream_t s, const T *src2, const T *add) {
     PairSym g;
     double sg = 1.0;
-    if (match_pair_antisym(d0, g, sg)) {
+    if (!d0.has_add && match_pair_antisym(d0, g, sg)) {
         AccumDesc d = d0;
         if (sg < 0) {
             d.alpha = -d.alpha;
@@ -523,13 +545,13 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
     }
     for (int k = 0; k < dl && rowok; k++) rowok = d.ext[k] <= 0xffffffffLL;
     if (rowok) {
-        if (d.nperm <= 1) return rows_launch<T, 1, ACC>(d, src, out, s, src2);
-        if (d.nperm <= 2) return rows_launch<T, 2, ACC>(d, src, out, s, src2);
-        if (d.nperm <= 4) return rows_launch<T, 4, ACC>(d, src, out, s, src2);
-        return rows_launch<T, 8, ACC>(d, src, out, s, src2);
+        if (d.nperm <= 1) return rows_launch<T, 1, ACC>(d, src, out, s, src2, add);
+        if (d.nperm <= 2) return rows_launch<T, 2, ACC>(d, src, out, s, src2, add);
+        if (d.nperm <= 4) return rows_launch<T, 4, ACC>(d, src, out, s, src2, add);
+        return rows_launch<T, 8, ACC>(d, src, out, s, src2, add);
     }
     // tiled path: the output's innermost dim and a partner dim both of extent >= 16
-    if (!d.two_src && d.nd >= 2 && d.ext[dl] >= 16) {
+    if (!d.two_src && !d.has_add && d.nd >= 2 && d.ext[dl] >= 16) {
         int d1 = -1;
         uint64_t tmask = 0;
         // partner: the dim holding a term's smallest source stride, when that is not d0
@@ -559,11 +581,11 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
             }
         }
     }
-    return accum_generic<T, ACC>(d, src, out, s, src2);
+    return accum_generic<T, ACC>(d, src, out, s, src2, add);
 }
 
 template <typename T>
-static cudaError_t accum_dispatch(AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2) {
+static cudaError_t accum_dispatch(AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2, const T *add) {
     if (d.bcase == 2) {
         // general beta: out *= beta first, then accumulate with beta = 1
         scale_view_kernel<T><<<(unsigned)grid_cap((d.total + 255) / 256, 148 * 16), 256, 0, s>>>(d, out, d.beta);
@@ -571,12 +593,14 @@ static cudaError_t accum_dispatch(AccumDesc &d, const T *src, T *out, cudaStream
         d.beta = 1.0;
         d.bcase = 1;
     }
-    return d.bcase ? accum_t<T, true>(d, src, out, s, src2) : accum_t<T, false>(d, src, out, s, src2);
+    return d.bcase ? accum_t<T, true>(d, src, out, s, src2, add) : accum_t<T, false>(d, src, out, s, src2, add);
 }
 
-cudaError_t launch_accum(const AccumDesc &d0, const double *src, double *out, cudaStream_t s, const double *src2) {
+cudaError_t launch_accum(const AccumDesc &d0, const double *src, double *out, cudaStream_t s, const double *src2,
+                         const double *add) {
     if (d0.total <= 0) return cudaSuccess;
     if (d0.nd < 1 || d0.nd > kMaxDims || d0.nperm < 1 || d0.nperm > kMaxPerms) return cudaErrorInvalidValue;
+    if (d0.has_add && (!add || d0.beta != 1.0)) return cudaErrorInvalidValue;
     AccumDesc d = d0;
     d.negmask = 0;
     for (int p = 0; p < d.nperm; p++)
@@ -585,8 +609,8 @@ cudaError_t launch_accum(const AccumDesc &d0, const double *src, double *out, cu
     d.bcase = beta_case(d.beta);
     if (d.cplx)
         return accum_dispatch<double2>(d, reinterpret_cast<const double2 *>(src), reinterpret_cast<double2 *>(out), s,
-                                       reinterpret_cast<const double2 *>(src2));
-    return accum_dispatch<double>(d, src, out, s, src2);
+                                       reinterpret_cast<const double2 *>(src2), reinterpret_cast<const double2 *>(add));
+    return accum_dispatch<double>(d, src, out, s, src2, add);
 }
 
 }  // namespace ccb

@@ -145,7 +145,8 @@ cc_status exec_step(cc_plan_s *pl, const Step &stp, const cc_integrals *I, const
         case StepKind::ACCUM:
             if (!(stp.static_src && pl->cache_filled)) {
                 CC_CUDA(launch_accum(stp.acc, resolve(stp.a, I, A, R, w), resolve(stp.out, I, A, R, w), s,
-                                     stp.acc.two_src ? resolve(stp.b, I, A, R, w) : nullptr));
+                                     stp.acc.two_src ? resolve(stp.b, I, A, R, w) : nullptr,
+                                     stp.acc.has_add ? resolve(stp.c, I, A, R, w) : nullptr));
                 pl->launches++;
             }
             break;

@@ -65,6 +65,10 @@ struct AccumDesc {
     unsigned long long negmask;     // bit p: sign[p] < 0
     Scale as;                       // make_scale(alpha)
     int bcase;                      // beta_case(beta)
+    // has_add (beta must be 1): the accumulated-onto value is add[sum idx_d * astr[d]]
+    // instead of out's own (a copy "out = add" fused into the step: out = add + alpha sum ...)
+    int has_add;
+    int64_t astr[kMaxDims];
 };
 
 // beta classes for epilogues: 0 -> 0, 1 -> 1, other -> 2
@@ -176,7 +180,7 @@ struct TcGemmDesc {
 };
 
 cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s,
-                         const double *src2 = nullptr);
+                         const double *src2 = nullptr, const double *add = nullptr);
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
 cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double *B, double *C, double *partials,
                             cudaStream_t s);

@@ -809,6 +809,16 @@ struct Planner {
         // (matrix-vector shapes stay on the memory-bound FP64 kernels)
         bool use_mixed = plan.precision != 0 &&
                          (mixed_all || (flops >= 2.0e8 && Mx > 1 && Nx > 1 && Kx > 1));
+        // except a matrix-vector product against a large integral block: its
+        // split planes are cached once per solve, so the tensor route streams
+        // half the bytes of the FP64 block (the idle tile columns cost nothing
+        // next to that)
+        const auto big_static = [&](const View &X) {
+            return plan.tensors[X.tensor].kind == TKind::INTEGRAL && view_elems(X) >= 100000000;
+        };
+        const bool static_mv = plan.precision != 0 && !mixed_all && Kx > 1 && (Mx == 1) != (Nx == 1) &&
+                               (big_static(A) || big_static(B));
+        use_mixed = use_mixed || static_mv;
         // Tensor tiles are 128 x bn x 64.  A narrow contraction (K <= 64 and one
         // free side <= 64, e.g. the rank-o updates of T3) that fills them less
         // than half is memory-bound: it runs on the narrow kernel with FP32
@@ -831,7 +841,7 @@ struct Planner {
                 use_mixed = false;
                 use_rows = true;
                 use_f32 = true;
-            } else if (eff < 0.15 && !cplx) {
+            } else if (eff < 0.15 && !cplx && !static_mv) {
                 use_mixed = false;
                 use_f32 = true;
             }
@@ -1026,8 +1036,8 @@ struct Planner {
             t.M = Mr;
             t.N = Nr;
             t.bn = Nr <= 64 ? 64 : (Nr <= 128 || np == 3) ? 128 : 256;
-            // planes padded for the widest tile an autotuner may pick (the
-            // kernels run ceil(N / bn) column tiles whatever the padding)
+            // column tiles of the widest tile an autotuner may pick (the kernels
+            // run ceil(N / bn) column tiles; the planes themselves hold N rows)
             const int bn_max = np == 3 ? (Nr <= 64 ? 64 : 128) : (Nr <= 64 ? 64 : Nr <= 128 ? 128 : 256);
             t.Mp = align_up(Mr, 128);
             t.Np = align_up(Nr, bn_max);
@@ -1073,11 +1083,12 @@ struct Planner {
             t.alpha = galpha;
             t.beta = gbeta;
             SplitDesc &sa = g.split_a;
-            sa.R = Mr; sa.K = Kr; sa.Rp = t.Mp; sa.Kp = t.Kp; sa.nplanes = np;
+            // planes hold the real rows only: the tile padding is read as zeros by TMA
+            sa.R = Mr; sa.K = Kr; sa.Rp = Mr; sa.Kp = t.Kp; sa.nplanes = np;
             sa.gr = make_grp(fa_order, A, A);
             sa.gk = make_grp(k_order, A, A);
             SplitDesc &sb = g.split_b;
-            sb.R = Nr; sb.K = Kr; sb.Rp = t.Np; sb.Kp = t.Kp; sb.nplanes = np;
+            sb.R = Nr; sb.K = Kr; sb.Rp = Nr; sb.Kp = t.Kp; sb.nplanes = np;
             sb.gr = make_grp(fb_order, B, B);
             sb.gk = make_grp(k_order, B, B);
             if (cplx) {
@@ -1090,7 +1101,7 @@ struct Planner {
             }
             g.a_static = plan.tensors[A.tensor].kind == TKind::INTEGRAL || plan.tensors[A.tensor].static_data;
             g.b_static = plan.tensors[B.tensor].kind == TKind::INTEGRAL || plan.tensors[B.tensor].static_data;
-            const int64_t bytes_a = t.Mp * t.Kp * 2 * np, bytes_b = t.Np * t.Kp * 2 * np;
+            const int64_t bytes_a = Mr * t.Kp * 2 * np, bytes_b = Nr * t.Kp * 2 * np;
             // static planes live in the cache; other planes in the split region, shared by
             // every later step that splits the same version of the same view
             if (g.a_static) { g.planes_a_off = cache_need; cache_need += align_up(bytes_a); }
@@ -1113,6 +1124,43 @@ struct Planner {
 };
 
 }  // namespace
+
+static bool same_ref(const BufRef &x, const BufRef &y) {
+    return x.where == y.where && x.slot == y.slot && x.off == y.off;
+}
+
+// "T = X" (a plain one-term copy) directly followed by "T += alpha P(..) A * B"
+// (an outer product accumulated onto T): one pass T = X + alpha sum ..., so T
+// is written once and X read once instead of T being written, read and
+// written again.
+static void fuse_copies(Plan &plan) {
+    std::vector<Step> out;
+    for (size_t k = 0; k < plan.steps.size(); k++) {
+        const Step &c = plan.steps[k];
+        if (k + 1 < plan.steps.size()) {
+            const Step &n = plan.steps[k + 1];
+            const AccumDesc &a = c.acc, &b = n.acc;
+            bool ok = c.kind == StepKind::ACCUM && n.kind == StepKind::ACCUM && !c.static_src && !n.static_src &&
+                      !a.two_src && a.nperm == 1 && a.alpha == 1.0 && a.beta == 0.0 && a.sign[0] == 1.0 &&
+                      !a.conj_a && b.two_src && b.beta == 1.0 && !b.has_add && a.cplx == b.cplx && a.nd == b.nd &&
+                      same_ref(c.out, n.out) && !same_ref(n.a, n.out) && !same_ref(n.b, n.out) &&
+                      !same_ref(c.a, n.out);
+            for (int d = 0; ok && d < a.nd; d++) ok = a.ext[d] == b.ext[d] && a.ostr[d] == b.ostr[d];
+            if (ok) {
+                Step f = n;
+                f.acc.has_add = 1;
+                for (int d = 0; d < a.nd; d++) f.acc.astr[d] = a.sstr[0][d];
+                f.c = c.a;
+                f.note = c.note + " + " + n.note;
+                out.push_back(f);
+                k++;
+                continue;
+            }
+        }
+        out.push_back(c);
+    }
+    plan.steps.swap(out);
+}
 
 bool build_plan(const std::string &text, int o, int v, int dtype, int precision, Plan &plan, std::string &err,
                 int flags) {
@@ -1155,6 +1203,7 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
         max_scratch = std::max(max_scratch, P.scratch_need);
     }
     if (plan.stmt_text.empty()) { err = "empty contraction list"; return false; }
+    fuse_copies(plan);
     // workspace: [status word][intermediates][scratch arena][static plane cache]
     plan.flags_off = 0;
     int64_t off = P.interm_need;
@@ -1170,9 +1219,9 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     off += P.cache_need;
     plan.ws_bytes = off;
     for (auto &st : plan.steps) {
-        for (BufRef *r : {&st.a, &st.b})
+        for (BufRef *r : {&st.a, &st.b, &st.c})
             if (r->where == BufRef::INTEG && r->slot >= 0 && r->slot < 7) plan.integ_used[r->slot] = true;
-        for (BufRef *r : {&st.out, &st.a, &st.b, &st.partials}) {
+        for (BufRef *r : {&st.out, &st.a, &st.b, &st.c, &st.partials}) {
             if (r->where == BufRef::WS && r->slot == 1) { r->off += plan.scratch_off; r->slot = 0; }
             if (r->where == BufRef::WS && r->slot == 2) { r->off += plan.cache_off; r->slot = 0; }
         }

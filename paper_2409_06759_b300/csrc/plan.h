@@ -52,6 +52,7 @@ struct Step {
     StepKind kind;
     int stmt = -1;              // statement index (0-based)
     BufRef out, a, b;           // ACCUM: out, src=a; GEMM: C=out, A=a, B=b; ZERO: out
+    BufRef c;                   // ACCUM with acc.has_add: the fused copy's source
     int64_t zero_elems = 0;
     AccumDesc acc{};
     GemmF64Desc gemm{};

@@ -273,10 +273,12 @@ __global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, c
             for (int j = 0; j < 8; j++) f[j] = tile[rr][kk + j];
             uint4 H, M, L;
             split8<NPL>(f, H, M, L);
-            __nv_bfloat16 *p0 = planes + (r0 + rr) * d.Kp + k0 + kk;
-            *reinterpret_cast<uint4 *>(p0) = H;
-            *reinterpret_cast<uint4 *>(p0 + plane_elems) = M;
-            if (NPL == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = L;
+            if (r0 + rr < d.Rp) {
+                __nv_bfloat16 *p0 = planes + (r0 + rr) * d.Kp + k0 + kk;
+                *reinterpret_cast<uint4 *>(p0) = H;
+                *reinterpret_cast<uint4 *>(p0 + plane_elems) = M;
+                if (NPL == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = L;
+            }
         }
     }
 }
@@ -384,11 +386,13 @@ __global__ void wait_selftest_kernel(long long budget, int *timed_out) {
     if (threadIdx.x == 0) *timed_out = mbar_wait(&bar, 0, budget) ? 0 : 1;
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+// box {64 columns, rows, 1 plane} at column x (a multiple of 64), row y, plane z;
+// rows past the plane's row count arrive as zeros (the tile padding)
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
         : "memory");
 }
 
@@ -518,10 +522,9 @@ __global__ void __launch_bounds__(192, 1)
                 uint8_t *st = tiles + s * G::STAGE_BYTES;
                 mbar_expect_tx(&full[s], G::STAGE_BYTES);
                 for (int p = 0; p < NP; p++)
-                    tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)(p * d.Mp + m0));
+                    tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)m0, p);
                 for (int q = 0; q < NP; q++)
-                    tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK,
-                                (int)(q * d.Np + n0));
+                    tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK, (int)n0, q);
                 issued = kb + 1;
             }
             if (*abort_flag) {
@@ -691,10 +694,9 @@ __global__ void __launch_bounds__(320, 1)
                     uint8_t *st = tiles + s * G::STAGE_BYTES;
                     mbar_expect_tx(&full[s], G::STAGE_BYTES);
                     for (int p = 0; p < NP; p++)
-                        tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], kb * BK, (int)(p * d.Mp + m0));
+                        tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], kb * BK, (int)m0, p);
                     for (int q = 0; q < NP; q++)
-                        tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BK,
-                                    (int)(q * d.Np + n0));
+                        tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BK, (int)n0, q);
                 }
             }
             if (stop) {
@@ -889,10 +891,9 @@ __global__ void __launch_bounds__(320, 1)
                 uint8_t *st = tiles + s * G::STAGE_BYTES;
                 mbar_expect_tx(&full[s], G::STAGE_BYTES);
                 for (int p = 0; p < NP; p++)
-                    tma_load_2d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)(p * d.Mp + m0));
+                    tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)m0, p);
                 for (int q = 0; q < NP; q++)
-                    tma_load_2d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK,
-                                (int)(q * d.Np + n0));
+                    tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK, (int)n0, q);
                 issued = kb + 1;
             }
             if (*abort_flag) {
@@ -1035,15 +1036,16 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D map over planes stacked as rows: [nplanes * rows][Kp] bf16, box {64, box_rows}
-static bool make_map(CUtensorMap *map, const void *base, int64_t rows_total, int64_t Kp, int box_rows) {
+// 3-D map over the planes [nplanes][rows][Kp] bf16 (rows unpadded: the
+// box rows past `rows` read as zeros), box {64, box_rows, 1}
+static bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t Kp, int nplanes, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows_total};
-    cuuint64_t strides[1] = {(cuuint64_t)(Kp * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nplanes};
+    cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -1060,10 +1062,9 @@ static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B,
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (d.Np % BN || d.Mp % BM || d.Kp % BK) return cudaErrorInvalidValue;
+    if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
-        return cudaErrorInvalidValue;
+    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mb, B, d.N, d.Kp, NP, BN)) return cudaErrorInvalidValue;
     const int64_t tiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
     const int kb_total = (int)(d.Kp / BK);
@@ -1090,10 +1091,9 @@ static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const v
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (d.Np % BN || d.Mp % BM || d.Kp % BK) return cudaErrorInvalidValue;
+    if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
-        return cudaErrorInvalidValue;
+    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mb, B, d.N, d.Kp, NP, BN)) return cudaErrorInvalidValue;
     const int64_t ntiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     const int kb_total = (int)(d.Kp / BK);
     const int sk = d.splitk > 1 ? d.splitk : 1;
@@ -1119,10 +1119,9 @@ static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (d.Np % BN || d.Mp % BM || d.Kp % BK) return cudaErrorInvalidValue;
+    if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, NP * d.Mp, d.Kp, BM) || !make_map(&mb, B, NP * d.Np, d.Kp, BN))
-        return cudaErrorInvalidValue;
+    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mb, B, d.N, d.Kp, NP, BN)) return cudaErrorInvalidValue;
     const int64_t tiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
     const int kb_total = (int)(d.Kp / BK);

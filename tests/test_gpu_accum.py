@@ -41,6 +41,8 @@ LISTS = [
     "R2[ijab] = T2[ijab]\nR2[ijab] += 0.5 P(ab) T1[ia] * T1[jb]",
     "R2[ijab] = P(ij) P(ab) T1[ia] * T1[jb]",
     "R2[ijab] = -3 P(ij) T2[ijab]",
+    # a permuted copy fused with the outer product that follows it
+    "R2[ijab] = T2[jiba]\nR2[ijab] += -0.25 P(ij) T1[ia] * T1[jb]",
     # tiled kernel: transposed sources, mixed direct / transposed terms
     "R2[ijab] = T2[jiba]",
     "R2[ijab] = 0.25 V[abij]",
@@ -89,7 +91,7 @@ def test_accumulate_statement_real(cc, k, o, v):
 
 
 @pytest.mark.parametrize("o,v", [(3, 20), (5, 45)])
-@pytest.mark.parametrize("k", [0, 1, 3, 6, 7])
+@pytest.mark.parametrize("k", [0, 1, 3, 6, 7, 8])
 def test_accumulate_statement_complex(cc, k, o, v):
     g1, g2, e1, e2 = _run(cc, LISTS[k], o, v, 90 + k, True)
     scale = max(1.0, np.abs(e1).max(), np.abs(e2).max())
