@@ -297,6 +297,22 @@ CC_API cc_status cc_build_integrals(int o, int v, int L, cc_dtype dtype, const v
                                     void *oovv, void *ovov, void *ovvv, void *vvvv, void *ws, size_t ws_bytes,
                                     void *stream);
 
+/* cc_pack_t2 / cc_unpack_t2 -- the doubles amplitudes t_ij^ab are
+ * antisymmetric in (i, j) and in (a, b) (Eq. amp), so their unique content is
+ * the i < j, a < b quarter.  Packed layout: t_packed[P(i,j)][P(a,b)] with the
+ * pair index P(p, q) = p (2n - p - 1) / 2 + (q - p - 1) (q fastest; n = o for
+ * (i, j), v for (a, b)), cc_packed_t2_elems(o, v) elements.  Moving amplitudes
+ * between host and device in this form carries a quarter of the bytes.
+ *   pack:   t_full (device, o*o*v*v, [i][j][a][b]) -> t_packed (device); reads
+ *           only the i < j, a < b elements.
+ *   unpack: t_packed -> t_full, writing every element (sign-flipped orbit
+ *           members, exact zeros on i = j or a = b).
+ * Elements are doubles (CC_F64) or interleaved complex doubles (CC_C128).
+ * Asynchronous on stream; no workspace. */
+CC_API int64_t cc_packed_t2_elems(int o, int v);
+CC_API cc_status cc_pack_t2(int o, int v, cc_dtype dtype, const void *t_full, void *t_packed, void *stream);
+CC_API cc_status cc_unpack_t2(int o, int v, cc_dtype dtype, const void *t_packed, void *t_full, void *stream);
+
 /* cc_energy_noalloc -- the same energy as cc_energy, for callers that cannot
  * allocate device memory: code running under a host application that owns the
  * device heap, or in a region where a cudaMalloc would be refused or would

@@ -31,7 +31,8 @@ STATUS = ["CC_OK", "CC_ERR_INVALID_ARG", "CC_ERR_PARSE", "CC_ERR_SHAPE", "CC_ERR
 EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_plan_flops", "cc_plan_destroy",
            "cc_plan_profile_enable", "cc_plan_profile_read", "cc_plan_launch_count",
            "cc_residual", "cc_energy", "cc_solve_workspace_bytes", "cc_solve", "cc_integral_block_elems",
-           "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_status_string",
+           "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_packed_t2_elems",
+           "cc_pack_t2", "cc_unpack_t2", "cc_status_string",
            "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched",
            "cc_plan_autotune", "cc_plan_set_gemm_config", "cc_build_vvvv_packed_workspace_bytes", "cc_build_vvvv_packed",
            "cc_selftest_wait_timeout", "cc_selftest_convert"]
@@ -101,6 +102,9 @@ _sig = {
     "cc_plan_autotune": (c_int, [c_void_p, _P(cc_integrals), _P(cc_amps), _P(cc_resid), c_void_p, c_size_t, c_void_p,
                                  c_int]),
     "cc_build_vvvv_packed_workspace_bytes": (c_int, [c_int, c_int, c_int, c_int, _P(c_size_t)]),
+    "cc_packed_t2_elems": (ctypes.c_int64, [c_int, c_int]),
+    "cc_pack_t2": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "cc_unpack_t2": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "cc_build_vvvv_packed": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "cc_selftest_wait_timeout": (c_int, [ctypes.c_longlong]),
     "cc_selftest_convert": (c_int, [c_void_p, ctypes.c_longlong, c_void_p, c_void_p]),
@@ -399,6 +403,21 @@ def cc_build_vvvv_packed_workspace_bytes(o: int, v: int, L: int, dtype: int = CC
 def cc_build_vvvv_packed(o: int, v: int, L: int, B, out, ws, dtype: int = CC_F64, stream=None):
     _check(_lib.cc_build_vvvv_packed(o, v, L, dtype, _ptr(B), _ptr(out), _ptr(ws), _nbytes(ws), _stream(stream)),
            "cc_build_vvvv_packed")
+
+
+def cc_packed_t2_elems(o: int, v: int) -> int:
+    """Elements of the packed (i < j, a < b) doubles amplitudes."""
+    return int(_lib.cc_packed_t2_elems(o, v))
+
+
+def cc_pack_t2(o: int, v: int, t_full, t_packed, dtype: int = CC_F64, stream=None):
+    """t_packed[P(i,j)][P(a,b)] = t_full[i][j][a][b] over i < j, a < b (device arrays)."""
+    _check(_lib.cc_pack_t2(o, v, dtype, _ptr(t_full), _ptr(t_packed), _stream(stream)), "cc_pack_t2")
+
+
+def cc_unpack_t2(o: int, v: int, t_packed, t_full, dtype: int = CC_F64, stream=None):
+    """The full antisymmetric [o][o][v][v] array from its packed quarter (device arrays)."""
+    _check(_lib.cc_unpack_t2(o, v, dtype, _ptr(t_packed), _ptr(t_full), _stream(stream)), "cc_unpack_t2")
 
 
 def cc_selftest_wait_timeout(budget_cycles: int = 2_000_000) -> int:

@@ -494,6 +494,35 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
     return result;
 }
 
+int64_t cc_packed_t2_elems(int o, int v) {
+    if (o < 0 || v < 0) return 0;
+    return ((int64_t)o * (o - 1) / 2) * ((int64_t)v * (v - 1) / 2);
+}
+
+static cc_status t2_pack_args(int o, int v, cc_dtype dtype, const void *x, const void *y) {
+    if (o < 1 || v < 1 || o > 4096 || v > 65535) return fail(CC_ERR_INVALID_ARG, "o, v out of range");
+    if (dtype != CC_F64 && dtype != CC_C128) return fail(CC_ERR_INVALID_ARG, "unknown dtype");
+    if (!x || !y) return fail(CC_ERR_INVALID_ARG, "NULL array");
+    if ((uintptr_t)x % (dtype == CC_C128 ? 16 : 8) || (uintptr_t)y % (dtype == CC_C128 ? 16 : 8))
+        return fail(CC_ERR_INVALID_ARG, "arrays must be aligned to their element size");
+    return CC_OK;
+}
+
+cc_status cc_pack_t2(int o, int v, cc_dtype dtype, const void *t_full, void *t_packed, void *stream) {
+    cc_status st = t2_pack_args(o, v, dtype, t_full, t_packed);
+    if (st != CC_OK) return st;
+    CC_CUDA(launch_pack_t2(o, v, dtype == CC_C128, (const double *)t_full, (double *)t_packed, (cudaStream_t)stream));
+    return CC_OK;
+}
+
+cc_status cc_unpack_t2(int o, int v, cc_dtype dtype, const void *t_packed, void *t_full, void *stream) {
+    cc_status st = t2_pack_args(o, v, dtype, t_packed, t_full);
+    if (st != CC_OK) return st;
+    CC_CUDA(launch_unpack_t2(o, v, dtype == CC_C128, (const double *)t_packed, (double *)t_full,
+                             (cudaStream_t)stream));
+    return CC_OK;
+}
+
 cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red) {
     if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
     Plan &P = plan->plan;

@@ -234,6 +234,72 @@ __global__ void __launch_bounds__(256) unpack_pairs_kernel(const UnpackDesc d, c
     }
 }
 
+// Amplitude packing.  pack: one block per packed row P(i, j), i < j (found
+// once per block); the block walks a = 0..v-2 and its lanes the run b = a+1..
+// v-1, which is contiguous in both arrays.  unpack: one block per full row
+// (i, j); column (a, b) reads packed[P(min)][P(a, b) or P(b, a)] with the sign
+// of the two swaps, and i = j or a = b write exact zeros.
+template <typename T>
+__global__ void __launch_bounds__(256) pack_t2_kernel(int o, int v, const T *__restrict__ full, T *__restrict__ packed) {
+    const int64_t P2 = (int64_t)v * (v - 1) / 2;
+    const int64_t prow = blockIdx.x;
+    int64_t i, j;
+    pair_of(prow, o, i, j);
+    const T *src = full + (i * o + j) * (int64_t)v * v;
+    T *dst = packed + prow * P2;
+    for (int a = 0; a + 1 < v; a++) {
+        const int64_t pa = pair_start(a, v) - a - 1;                 // + b gives P(a, b)
+        for (int b = a + 1 + (int)threadIdx.x; b < v; b += blockDim.x) dst[pa + b] = src[(int64_t)a * v + b];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) unpack_t2_kernel(int o, int v, const T *__restrict__ packed, T *__restrict__ full) {
+    const int64_t P2 = (int64_t)v * (v - 1) / 2;
+    const uint32_t row = blockIdx.x, i = row / (uint32_t)o, j = row - i * (uint32_t)o;
+    const uint32_t ncol = (uint32_t)v * (uint32_t)v;
+    T *dst = full + (int64_t)row * ncol;
+    if (i == j) {
+        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) dst[c] = zero<T>();
+        return;
+    }
+    const int64_t pij = i < j ? pair_start(i, o) + j - i - 1 : pair_start(j, o) + i - j - 1;
+    const bool nrow = i > j;
+    const T *src = packed + pij * P2;
+    for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+        const uint32_t a = c / (uint32_t)v, b = c - a * (uint32_t)v;
+        T x = zero<T>();
+        if (a != b) {
+            const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+            x = src[pair_start(lo, v) + hi - lo - 1];
+            if (nrow != (a > b)) x = neg(x);
+        }
+        dst[c] = x;
+    }
+}
+
+cudaError_t launch_pack_t2(int o, int v, int cplx, const double *full, double *packed, cudaStream_t s) {
+    if (o < 2 || v < 2) return cudaSuccess;
+    const unsigned rows = (unsigned)((int64_t)o * (o - 1) / 2);
+    if (cplx)
+        pack_t2_kernel<double2><<<rows, 256, 0, s>>>(o, v, reinterpret_cast<const double2 *>(full),
+                                                     reinterpret_cast<double2 *>(packed));
+    else
+        pack_t2_kernel<double><<<rows, 256, 0, s>>>(o, v, full, packed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_t2(int o, int v, int cplx, const double *packed, double *full, cudaStream_t s) {
+    if (o < 1 || v < 1) return cudaSuccess;
+    const unsigned rows = (unsigned)((int64_t)o * o);
+    if (cplx)
+        unpack_t2_kernel<double2><<<rows, 256, 0, s>>>(o, v, reinterpret_cast<const double2 *>(packed),
+                                                       reinterpret_cast<double2 *>(full));
+    else
+        unpack_t2_kernel<double><<<rows, 256, 0, s>>>(o, v, packed, full);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_pairs(const PackDesc &d, const double *src, double *dst, cudaStream_t s) {
     if (d.row0 < 0 || d.rows < 0 || d.row0 + d.rows > d.P1) return cudaErrorInvalidValue;
     const int64_t total = d.rows * d.P2;

@@ -140,6 +140,10 @@ struct UnpackDesc {
     Scale as;                       // make_scale(alpha), same launcher
 };
 cudaError_t launch_pack_pairs(const PackDesc &d, const double *src, double *dst, cudaStream_t s);
+// amplitude packing of a [o][o][v][v] array antisymmetric in both pairs
+// (cplx: interleaved complex elements): packed[P(i,j)][P(a,b)] over i<j, a<b
+cudaError_t launch_pack_t2(int o, int v, int cplx, const double *full, double *packed, cudaStream_t s);
+cudaError_t launch_unpack_t2(int o, int v, int cplx, const double *packed, double *full, cudaStream_t s);
 cudaError_t launch_unpack_pairs(const UnpackDesc &d, const double *C, double *out, cudaStream_t s);
 
 // Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes
