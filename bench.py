@@ -48,7 +48,7 @@ def workload_name(args):
     return SMALL if args.small else WORKLOAD
 # DRAM bytes / operand-plane bytes of the ladder kernel, from its ncu capture (None until re-captured
 # after a kernel change)
-TRAFFIC_RATIO = None
+TRAFFIC_RATIO = 1.052
 
 
 def peaks():
@@ -436,6 +436,9 @@ def main():
     ap.add_argument("--ref-samples", type=int, default=2)
     ap.add_argument("--dtype", default="f64", choices=["f64", "c128"])
     ap.add_argument("--no-tune", action="store_true", help="skip cc_plan_autotune on the timed plan")
+    ap.add_argument("--save-tune", default=None, help="write the timed plan's GEMM configurations (JSON)")
+    ap.add_argument("--load-tune", default=None, help="set the timed plan's GEMM configurations from a file "
+                    "written by --save-tune instead of autotuning")
     ap.add_argument("--packed", action="store_true",
                     help="lists with packed index pairs (ladder over e<f; flops counted packed)")
     ap.add_argument("--workload", default="ccsd", choices=["ccsd", "ccsdt", "batched"],
@@ -490,12 +493,21 @@ def main():
 
     # tile widths and split-K factors of the mixed plan picked by timing (cc_plan_autotune)
     t_tune = None
-    if not args.no_tune:
+    if args.load_tune:
+        # replay a configuration saved by an earlier run (e.g. for a profiler run,
+        # where timings taken under the profiler would mislead the autotuner)
+        for k, bn, sk, red in json.load(open(args.load_tune)):
+            cc.cc_plan_set_gemm_config(mixed.plan, k, bn, sk, red)
+    elif not args.no_tune:
         tt = time.perf_counter()
         mixed.autotune(*z(), reps=3, stream=stream)
         mixed.release()
         torch.cuda.synchronize()
         t_tune = time.perf_counter() - tt
+    if args.save_tune and rank == 0:
+        cfgs = [[k, st.get("bn", 0), st["splitk"], st.get("red", 0)] for k, st in
+                enumerate(mixed.plan.describe()["steps"]) if st.get("configs")]
+        json.dump(cfgs, open(args.save_tune, "w"))
 
     # ---- device-timed steps on the split-bf16 plan
     t1, t2 = z()
@@ -537,7 +549,7 @@ def main():
         # the operand bytes that dominate it (profiles/tc_gemm_ladder_o20_v100.md); None until captured
         traffic = None
         if not cplx and TRAFFIC_RATIO is not None and st["M"] == v * v and st["N"] == o * o and st["K"] == v * v:
-            traffic = TRAFFIC_RATIO * (st["Mp"] * st["Kp"] * 4 + st["Np"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
+            traffic = TRAFFIC_RATIO * (st["M"] * st["Kp"] * 4 + st["N"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": "tc_gemm_kernel (" + st["note"] + ")",
