@@ -100,32 +100,40 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
 // columns of the innermost dim d0 = nd-1).  A warp decomposes the chunk's
 // first row once (32-bit divisions; rows < 2^32) and then steps the row
 // digits as an odometer, keeping each term's row offsets in registers; lane l
-// handles columns cb + l + 32u, u < kRowU, with every load of the batch issued
-// before the arithmetic.  NP: the term count rounded up (1, 2, 4, 8).
-constexpr int kRowU = 8;
+// handles columns cb + l + 32u, u < U, with every load of the batch issued
+// before the arithmetic.  NP: the term count rounded up (1, 2, 4, 8).  U: 8
+// columns per lane for one-source terms, 4 for products (their operand pairs
+// would otherwise cost the occupancy that hides the loads' latency).
+template <bool TWO> __host__ __device__ constexpr int rows_u() { return TWO ? 4 : 8; }
 
 template <typename T, int NP, bool TWO, bool ACC>
 __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, const T *__restrict__ src,
                                                          const T *__restrict__ src2, T *__restrict__ out,
                                                          const T *__restrict__ add, uint32_t rows, int rch,
                                                          uint32_t ncb) {
+    constexpr int kRowU = rows_u<TWO>();
     const int lane = threadIdx.x & 31;
     const int d0 = d.nd - 1;
-    const int64_t E0 = d.ext[d0];
-    int64_t s0[NP], s02[NP];
+    const int E0 = (int)d.ext[d0];                     // < 2^31 (launch_accum checks)
+    // along the innermost dim every source (and the addend) has stride 0 or 1
+    // and the output stride 1: a column's offset is its index or 0
+    bool u0[NP], u02[NP];
 #pragma unroll
     for (int p = 0; p < NP; p++) {
-        s0[p] = p < d.nperm ? d.sstr[p][d0] : 0;
-        s02[p] = (TWO && p < d.nperm) ? d.sstr2[p][d0] : 0;
+        u0[p] = p < d.nperm && d.sstr[p][d0] != 0;
+        u02[p] = TWO && p < d.nperm && d.sstr2[p][d0] != 0;
     }
-    const int64_t os0 = d.ostr[d0], as0 = d.has_add ? d.astr[d0] : 0;
-    // the value accumulated onto: out itself, or a fused copy's source
-    const T *__restrict__ base_in = d.has_add ? add : out;
+    const bool ua = d.has_add && d.astr[d0] != 0;
     const uint32_t nchunks = (uint32_t)((rows + (uint32_t)rch - 1) / (uint32_t)rch);
     const uint64_t items = (uint64_t)nchunks * ncb;
+    // accumulating outer products start from the old value and add each term
+    // with one FMA, alpha (+-2^k) riding on a factor: nterms FP64 operations per
+    // element instead of nterms + 1
+    const bool chain = TWO && ACC && !d.as.general;
+    const bool fold = chain && !(d.as.kexp == 0 && d.as.sflip == 0);
     for (uint64_t it = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < items; it += (uint64_t)gridDim.x * 8) {
         const uint32_t chunk = (uint32_t)(it / ncb);
-        const int64_t cb = (int64_t)(it - (uint64_t)chunk * ncb) * (32 * kRowU);
+        const int cb = (int)(it - (uint64_t)chunk * ncb) * (32 * kRowU);
         const uint32_t r0 = chunk * (uint32_t)rch;
         // row digits of r0 over dims d0-1 .. 0, unrolled so they live in registers
         uint32_t dig[kMaxDims - 1];
@@ -152,28 +160,40 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
         }
         const int nr = rows - r0 < (uint32_t)rch ? (int)(rows - r0) : rch;
         for (int rr = 0; rr < nr; rr++) {
+            // the row's base pointers
+            T *orow = out + obase;
+            const T *irow = d.has_add ? add + abase : orow;
             T old[kRowU], acc[kRowU];
 #pragma unroll
             for (int u = 0; u < kRowU; u++) {
-                const int64_t i = cb + lane + 32 * u;
-                old[u] = (ACC && i < E0) ? base_in[(d.has_add ? abase + i * as0 : obase + i * os0)] : zero<T>();
+                const int i = cb + lane + 32 * u;
+                old[u] = (ACC && i < E0) ? irow[d.has_add ? (ua ? i : 0) : i] : zero<T>();
+                acc[u] = old[u];
             }
 #pragma unroll
             for (int p = 0; p < NP; p++) {
                 if (p >= d.nperm) break;
                 const bool ng = (d.negmask >> p) & 1ull;
+                const T *arow = src + sb[p];
+                const T *brow = TWO ? src2 + sb2[p] : nullptr;
                 T a[kRowU], b[kRowU];
 #pragma unroll
                 for (int u = 0; u < kRowU; u++) {
-                    const int64_t i = cb + lane + 32 * u;
-                    a[u] = i < E0 ? cj(ld(src + sb[p] + i * s0[p]), d.conj_a) : zero<T>();
-                    if (TWO) b[u] = i < E0 ? cj(ld(src2 + sb2[p] + i * s02[p]), d.conj_b) : zero<T>();
+                    const int i = cb + lane + 32 * u;
+                    a[u] = i < E0 ? cj(ld(arow + (u0[p] ? i : 0)), d.conj_a) : zero<T>();
+                    if (TWO) b[u] = i < E0 ? cj(ld(brow + (u02[p] ? i : 0)), d.conj_b) : zero<T>();
                 }
 #pragma unroll
                 for (int u = 0; u < kRowU; u++) {
+                    if (cb + 32 * u >= E0) continue;             // the whole warp is past the row's end
                     if (TWO) {
-                        const T sa = ng ? neg(a[u]) : a[u];            // the sign rides on a factor
-                        acc[u] = p == 0 ? mul(sa, b[u]) : cfma(sa, b[u], acc[u]);
+                        T sa = ng ? neg(a[u]) : a[u];              // the sign rides on a factor
+                        if (chain) {
+                            if (fold) sa = scale_f64(sa, d.as);
+                            acc[u] = cfma(sa, b[u], acc[u]);
+                        } else {
+                            acc[u] = p == 0 ? mul(sa, b[u]) : cfma(sa, b[u], acc[u]);
+                        }
                     } else {
                         acc[u] = signed_term(p == 0, ng, a[u], acc[u]);
                     }
@@ -181,8 +201,8 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
             }
 #pragma unroll
             for (int u = 0; u < kRowU; u++) {
-                const int64_t i = cb + lane + 32 * u;
-                if (i < E0) out[obase + i * os0] = finish<ACC>(d.as, acc[u], old[u]);
+                const int i = cb + lane + 32 * u;
+                if (i < E0) orow[i] = chain ? acc[u] : finish<ACC>(d.as, acc[u], old[u]);
             }
             // next row: odometer step with carries
 #pragma unroll
@@ -500,7 +520,9 @@ template <typename T, int NP, bool ACC>
 static cudaError_t rows_launch(const AccumDesc &d, const T *src, T *out, cudaStream_t s, const T *src2, const T *add) {
     const int64_t E0 = d.ext[d.nd - 1];
     const int64_t rows = d.total / E0;
-    const int64_t ncb = (E0 + 32 * kRowU - 1) / (32 * kRowU);
+    constexpr int U1 = rows_u<false>(), U2 = rows_u<true>();
+    const int64_t cw = 32 * (d.two_src ? U2 : U1);                 // columns per work item
+    const int64_t ncb = (E0 + cw - 1) / cw;
     // about four work items per resident warp (148 SMs x 64 warps), at most 16 rows each
     int64_t rch = rows * ncb / (148 * 64 * 4);
     rch = rch < 1 ? 1 : rch > 16 ? 16 : rch;
@@ -537,8 +559,10 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
     collapse_dims(d);
     const int dl = d.nd - 1;
     const int64_t rows = d.total / d.ext[dl];
-    // row path: every source runs with stride 0 or 1 along the innermost output dim
-    bool rowok = d.nperm <= 8 && rows <= 0xffffffffLL && d.ext[dl] >= 8;
+    // row path: every source (and a fused copy's source) runs with stride 0 or 1
+    // along the innermost output dim, and the output with stride 1
+    bool rowok = d.nperm <= 8 && rows <= 0xffffffffLL && d.ext[dl] >= 8 && d.ext[dl] < 0x7fff0000LL &&
+                 d.ostr[dl] == 1 && (!d.has_add || d.astr[dl] == 0 || d.astr[dl] == 1);
     for (int p = 0; p < d.nperm && rowok; p++) {
         rowok = d.sstr[p][dl] == 0 || d.sstr[p][dl] == 1;
         if (rowok && d.two_src) rowok = d.sstr2[p][dl] == 0 || d.sstr2[p][dl] == 1;
