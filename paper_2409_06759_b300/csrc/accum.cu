@@ -411,6 +411,117 @@ __global__ void __launch_bounds__(256) antisym_pairs_kernel(const AccumDesc d, c
     }
 }
 
+// ------------------------------------------------ triple-orbit antisymmetriser
+// out(., t, .) (+)= alpha sum_p sign_p src(., pi_p t, .) where t = (t0, t1, t2)
+// runs over three dims of equal extent n and the six terms are the six
+// permutations of those dims with their parities (the full antisymmetriser
+// of a triple, e.g. P(i/jk) P(jk) of the triples residual, Eq. amp).  The dims
+// before the triple form a batch index (stride sb / ob) and the dims after it
+// one contiguous run of C elements.  A work item is (multiset i <= j <= k,
+// batch, 256-column chunk): for i < j < k the six source rows are read once,
+// X = sum_p sign_p src_p formed (five adds) and sgn(sigma) X written to the six
+// output rows sigma(i, j, k), so every element moves once; a multiset with a
+// repeated index is an exact zero (skipped when accumulating, written as
+// zeros otherwise).
+struct TripleSym {
+    int64_t n, C, nb;
+    int64_t S[6][3];      // term p's source strides of the three dims
+    int64_t O[3];         // output strides of the three dims
+    int64_t sb, ob;       // batch strides (one collapsed batch dim)
+};
+
+// sigma applied to (i, j, k): the six orderings with their parities
+__device__ __forceinline__ void triple_perm(int q, int64_t i, int64_t j, int64_t k, int64_t &a, int64_t &b,
+                                            int64_t &c, bool &odd) {
+    switch (q) {
+        case 0: a = i; b = j; c = k; odd = false; break;
+        case 1: a = j; b = i; c = k; odd = true; break;
+        case 2: a = i; b = k; c = j; odd = true; break;
+        case 3: a = k; b = j; c = i; odd = true; break;
+        case 4: a = j; b = k; c = i; odd = false; break;
+        default: a = k; b = i; c = j; odd = false; break;
+    }
+}
+
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(256) antisym_triple_rows_kernel(const AccumDesc d, const TripleSym g,
+                                                                  const T *__restrict__ src, T *__restrict__ out,
+                                                                  uint32_t nms, uint32_t nchunk, uint64_t items) {
+    constexpr int U = 4;                          // columns per thread per item: chunk = 1024
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        uint64_t x = it;
+        const uint32_t ch = (uint32_t)(x % nchunk);
+        x /= nchunk;
+        const uint32_t ms = (uint32_t)(x % nms);
+        const int64_t bidx = (int64_t)(x / nms);
+        // multiset index -> i <= j <= k (k fastest)
+        int64_t i = 0, j = 0, k = 0;
+        {
+            uint32_t r = ms;
+            for (i = 0; i < g.n; i++) {
+                const uint32_t cnt = (uint32_t)((g.n - i) * (g.n - i + 1) / 2);   // pairs j <= k in [i, n)
+                if (r < cnt) break;
+                r -= cnt;
+            }
+            for (j = i; j < g.n; j++) {
+                const uint32_t cnt = (uint32_t)(g.n - j);
+                if (r < cnt) break;
+                r -= cnt;
+            }
+            k = j + r;
+        }
+        const bool distinct = i < j && j < k;
+        if (!distinct && ACC) continue;                    // adds an exact zero
+        const int64_t c0 = (int64_t)ch * (256 * U);
+        const int64_t sbase = bidx * g.sb, obase = bidx * g.ob;
+        if (!distinct) {
+            // rows of a repeated index: the distinct orderings of the multiset get zeros
+            for (int q = 0; q < 6; q++) {
+                int64_t a, b, c;
+                bool odd;
+                triple_perm(q, i, j, k, a, b, c, odd);
+                T *orow = out + obase + a * g.O[0] + b * g.O[1] + c * g.O[2];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int64_t col = c0 + threadIdx.x + 256 * u;
+                    if (col < g.C) orow[col] = zero<T>();
+                }
+            }
+            continue;
+        }
+        const T *srow[6];
+#pragma unroll
+        for (int p = 0; p < 6; p++) srow[p] = src + sbase + i * g.S[p][0] + j * g.S[p][1] + k * g.S[p][2];
+        T X[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t col = c0 + threadIdx.x + 256 * u;
+            T w[6];
+#pragma unroll
+            for (int p = 0; p < 6; p++) w[p] = col < g.C ? cj(ld(srow[p] + col), d.conj_a) : zero<T>();
+            T acc = zero<T>();
+#pragma unroll
+            for (int p = 0; p < 6; p++) acc = signed_term(p == 0, (d.negmask >> p) & 1ull, w[p], acc);
+            X[u] = scale_f64(acc, d.as);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            int64_t a, b, c;
+            bool odd;
+            triple_perm(q, i, j, k, a, b, c, odd);
+            T *orow = out + obase + a * g.O[0] + b * g.O[1] + c * g.O[2];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t col = c0 + threadIdx.x + 256 * u;
+                if (col < g.C) {
+                    const T v = odd ? neg(X[u]) : X[u];
+                    orow[col] = ACC ? add(v, orow[col]) : v;
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host side
 // Drop unit dims and merge neighbours k, k+1 that are contiguous in the
 // output and in every term's source(s): the kernels then see the fewest dims
@@ -492,6 +603,73 @@ static bool match_pair_antisym(const AccumDesc &d, PairSym &g, double &alpha_sig
     return true;
 }
 
+// Is d the triple antisymmetriser over three consecutive dims t..t+2 (equal
+// extents), with one batch dim before them (or none) and a contiguous run
+// after them (unit strides in src and out)?  Term p's strides on the three
+// dims must be a permutation of term 0's, and its sign term 0's times the
+// permutation's parity.
+static bool match_triple_antisym(const AccumDesc &d0, TripleSym &g) {
+    if (d0.two_src || d0.has_add || d0.nperm != 6) return false;
+    AccumDesc d = d0;
+    for (int t = 0; t + 2 < d.nd; t++) {
+        const int64_t n = d.ext[t];
+        if (n < 3 || d.ext[t + 1] != n || d.ext[t + 2] != n || n > 4096) continue;
+        // every other dim: the same stride in all terms
+        bool ok = true;
+        for (int k = 0; k < d.nd && ok; k++) {
+            if (k >= t && k <= t + 2) continue;
+            for (int p = 1; p < 6 && ok; p++) ok = d.sstr[p][k] == d.sstr[0][k];
+        }
+        if (!ok) continue;
+        // the inner run: dims after t+2 contiguous with unit innermost stride in src and out
+        int64_t C = 1, so = 1, oo = 1;
+        for (int k = d.nd - 1; k > t + 2 && ok; k--) {
+            ok = d.sstr[0][k] == so && d.ostr[k] == oo;
+            so *= d.ext[k];
+            oo *= d.ext[k];
+            C *= d.ext[k];
+        }
+        if (!ok || C < 64) continue;
+        // the batch: dims before t collapse into one strided index
+        int64_t nb = 1, sb = 0, ob = 0;
+        for (int k = t - 1; k >= 0 && ok; k--) {
+            if (d.ext[k] == 1) continue;
+            if (nb == 1) { sb = d.sstr[0][k]; ob = d.ostr[k]; nb = d.ext[k]; }
+            else if (d.sstr[0][k] == sb * nb && d.ostr[k] == ob * nb) nb *= d.ext[k];
+            else ok = false;
+        }
+        if (!ok) continue;
+        // the six terms: permutations of term 0's strides with parity signs
+        const int64_t *B = &d.sstr[0][t];
+        if (B[0] == B[1] || B[1] == B[2] || B[0] == B[2]) continue;
+        bool seen[6] = {false, false, false, false, false, false};
+        static const int perm[6][3] = {{0, 1, 2}, {1, 0, 2}, {0, 2, 1}, {2, 1, 0}, {1, 2, 0}, {2, 0, 1}};
+        static const bool odd[6] = {false, true, true, true, false, false};
+        for (int p = 0; p < 6 && ok; p++) {
+            int hit = -1;
+            for (int q = 0; q < 6; q++)
+                if (d.sstr[p][t] == B[perm[q][0]] && d.sstr[p][t + 1] == B[perm[q][1]] &&
+                    d.sstr[p][t + 2] == B[perm[q][2]])
+                    hit = q;
+            if (hit < 0 || seen[hit]) { ok = false; break; }
+            seen[hit] = true;
+            const double want = odd[hit] ? -d.sign[0] : d.sign[0];
+            ok = d.sign[p] == want && (d.sign[p] == 1.0 || d.sign[p] == -1.0);
+        }
+        if (!ok) continue;
+        g.n = n;
+        g.C = C;
+        g.nb = nb;
+        g.sb = sb;
+        g.ob = ob;
+        for (int p = 0; p < 6; p++)
+            for (int q = 0; q < 3; q++) g.S[p][q] = d.sstr[p][t + q];
+        for (int q = 0; q < 3; q++) g.O[q] = d.ostr[t + q];
+        return true;
+    }
+    return false;
+}
+
 static int64_t grid_cap(int64_t want, int64_t cap) { return want < 1 ? 1 : want > cap ? cap : want; }
 
 // out *= beta over the output view (a general beta before an accumulating pass)
@@ -554,6 +732,15 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
                 d, g, src, out, (uint32_t)nt, (uint32_t)items);
             return cudaGetLastError();
         }
+    }
+    TripleSym tg;
+    if (match_triple_antisym(d0, tg)) {
+        const int64_t nms = tg.n * (tg.n + 1) * (tg.n + 2) / 6;          // multisets i <= j <= k
+        const int64_t nchunk = (tg.C + 1023) / 1024;
+        const uint64_t items = (uint64_t)nms * (uint64_t)tg.nb * (uint64_t)nchunk;
+        antisym_triple_rows_kernel<T, ACC><<<(unsigned)grid_cap((int64_t)items, 148 * 16), 256, 0, s>>>(
+            d0, tg, src, out, (uint32_t)nms, (uint32_t)nchunk, items);
+        return cudaGetLastError();
     }
     AccumDesc d = d0;
     collapse_dims(d);
