@@ -496,8 +496,8 @@ def main():
     if args.load_tune:
         # replay a configuration saved by an earlier run (e.g. for a profiler run,
         # where timings taken under the profiler would mislead the autotuner)
-        for k, bn, sk, red in json.load(open(args.load_tune)):
-            cc.cc_plan_set_gemm_config(mixed.plan, k, bn, sk, red)
+        for k, bn, sk, red, bk in json.load(open(args.load_tune)):
+            cc.cc_plan_set_gemm_config(mixed.plan, k, bn, sk, red, bk)
     elif not args.no_tune:
         tt = time.perf_counter()
         mixed.autotune(*z(), reps=3, stream=stream)
@@ -505,7 +505,7 @@ def main():
         torch.cuda.synchronize()
         t_tune = time.perf_counter() - tt
     if args.save_tune and rank == 0:
-        cfgs = [[k, st.get("bn", 0), st["splitk"], st.get("red", 0)] for k, st in
+        cfgs = [[k, st.get("bn", 0), st["splitk"], st.get("red", 0), st.get("bk", 64)] for k, st in
                 enumerate(mixed.plan.describe()["steps"]) if st.get("configs")]
         json.dump(cfgs, open(args.save_tune, "w"))
 

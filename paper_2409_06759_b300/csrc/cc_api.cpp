@@ -451,13 +451,14 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
         if (st != CC_OK) { result = st; break; }
         if (stp.cands.size() < 2) continue;
         double best = 1e30;
-        std::array<int, 3> pick = stp.cands[0];
+        std::array<int, 4> pick = stp.cands[0];
         for (const auto &c : stp.cands) {
             Step trial = stp;
             if (trial.mixed) {
                 trial.tc.bn = c[0];
                 trial.tc.splitk = c[1];
                 trial.tc.red = c[2];
+                trial.tc.bk = c[3];
             } else {
                 trial.gemm.splitk = c[1];
             }
@@ -481,6 +482,7 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
             stp.tc.bn = pick[0];
             stp.tc.splitk = pick[1];
             stp.tc.red = pick[2];
+            stp.tc.bk = pick[3];
         } else {
             stp.gemm.splitk = pick[1];
         }
@@ -523,12 +525,12 @@ cc_status cc_unpack_t2(int o, int v, cc_dtype dtype, const void *t_packed, void 
     return CC_OK;
 }
 
-cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red) {
+cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red, int bk) {
     if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
     Plan &P = plan->plan;
     if (step < 0 || step >= (int)P.steps.size()) return fail(CC_ERR_INVALID_ARG, "step index out of range");
     Step &stp = P.steps[step];
-    const std::array<int, 3> want{bn, splitk, red};
+    const std::array<int, 4> want{bn, splitk, red, bk};
     bool found = false;
     for (const auto &c : stp.cands) found = found || c == want;
     if (!found) return fail(CC_ERR_INVALID_ARG, "not a candidate configuration of this step");
@@ -536,6 +538,7 @@ cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, in
         stp.tc.bn = bn;
         stp.tc.splitk = splitk;
         stp.tc.red = red;
+        stp.tc.bk = bk;
     } else {
         stp.gemm.splitk = splitk;
     }
