@@ -751,24 +751,35 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
             }
         }
         double *xs = hx + (int64_t)slot * L.nx, *es = he + (int64_t)slot * L.nx;
-        int64_t off = 0;
-        for (int l = 1; l <= 3; l++) {
-            if (!r[l]) continue;
-            CC_CUDA(launch_jacobi_inv(L.n[l], t[l], r[l], dinv + off, xs + off, es + off, s));
-            plan->launches++;
-            off += L.n[l];
-        }
         if (o.diis_max > 0) {
+            // Jacobi step and the new Gram row <e_new, e_q> in one pass
             S.order[S.nstored++] = slot;
-            int a_[16], b_[16];
-            for (int q = 0; q < S.nstored; q++) {
-                const int sq = S.order[q];
-                CC_CUDA(launch_dot_partials(es, he + (int64_t)sq * L.nx, L.nx, partials + (int64_t)q * kRedBlocks, s));
-                a_[q] = slot;
-                b_[q] = sq;
+            JacobiSegs g{};
+            for (int l = 1; l <= 3; l++) {
+                if (!r[l]) continue;
+                g.t[g.nseg] = t[l];
+                g.r[g.nseg] = r[l];
+                g.n[g.nseg] = L.n[l];
+                g.nseg++;
             }
+            int a_[16], b_[16];
+            g.m = S.nstored;
+            for (int q = 0; q < S.nstored; q++) {
+                g.he[q] = he + (int64_t)S.order[q] * L.nx;
+                a_[q] = slot;
+                b_[q] = S.order[q];
+            }
+            CC_CUDA(launch_jacobi_dots(g, dinv, xs, es, partials, s));
             CC_CUDA(launch_gram_scatter(partials, S.nstored, a_, b_, gram, s));
-            plan->launches += S.nstored + 1;
+            plan->launches += 2;
+        } else {
+            int64_t off = 0;
+            for (int l = 1; l <= 3; l++) {
+                if (!r[l]) continue;
+                CC_CUDA(launch_jacobi_inv(L.n[l], t[l], r[l], dinv + off, xs + off, es + off, s));
+                plan->launches++;
+                off += L.n[l];
+            }
         }
         if (S.nstored >= 2) {
             CC_CUDA(launch_diis_solve(gram, S.order, S.nstored, coef, used_dev, s));

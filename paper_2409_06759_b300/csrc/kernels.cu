@@ -766,6 +766,53 @@ __global__ void __launch_bounds__(256) dot_partials_kernel(const double *x, cons
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// One pass over e: each thread walks its fixed strided slice of the vector,
+// issuing every overlap's load for an element before its FMAs; one block sum
+// per overlap.  The history vectors are read once and the new error vector is
+// never re-read, so m overlaps cost (m + 3.5) vector passes instead of 2m + 5.
+template <int M>
+__global__ void __launch_bounds__(256) jacobi_dots_kernel(const JacobiSegs g, const double *__restrict__ dinv,
+                                                          double *__restrict__ xo, double *__restrict__ eo,
+                                                          double *__restrict__ partials) {
+    double acc[M];
+#pragma unroll
+    for (int h = 0; h < M; h++) acc[h] = 0.0;
+    int64_t base = 0;
+    for (int l = 0; l < g.nseg; l++) {
+        const double *__restrict__ t = g.t[l];
+        const double *__restrict__ r = g.r[l];
+        const int64_t n = g.n[l];
+        for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)kRedBlocks * 256) {
+            const int64_t x = base + e;
+            const double q = r[e] * dinv[x];
+            eo[x] = q;
+            xo[x] = t[e] + q;
+            double hv[M];
+#pragma unroll
+            for (int h = 0; h < M; h++) hv[h] = (h < g.m && g.he[h] != eo) ? g.he[h][x] : q;
+#pragma unroll
+            for (int h = 0; h < M; h++)
+                if (h < g.m) acc[h] = fma(q, hv[h], acc[h]);
+        }
+        base += n;
+    }
+#pragma unroll
+    for (int h = 0; h < M; h++) {
+        if (h >= g.m) break;
+        const double sum = block_sum(acc[h]);
+        if (threadIdx.x == 0) partials[(int64_t)h * kRedBlocks + blockIdx.x] = sum;
+    }
+}
+
+cudaError_t launch_jacobi_dots(const JacobiSegs &g, const double *dinv, double *xo, double *eo, double *partials,
+                               cudaStream_t s) {
+    if (g.nseg < 1 || g.nseg > 3 || g.m < 0 || g.m > 16) return cudaErrorInvalidValue;
+    if (g.m <= 4) jacobi_dots_kernel<4><<<kRedBlocks, 256, 0, s>>>(g, dinv, xo, eo, partials);
+    else if (g.m <= 8) jacobi_dots_kernel<8><<<kRedBlocks, 256, 0, s>>>(g, dinv, xo, eo, partials);
+    else jacobi_dots_kernel<16><<<kRedBlocks, 256, 0, s>>>(g, dinv, xo, eo, partials);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *partials, cudaStream_t s) {
     dot_partials_kernel<<<kRedBlocks, 256, 0, s>>>(x, y, n, partials);
     return cudaGetLastError();

@@ -220,6 +220,21 @@ cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double
 cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s);
 // partial sums for dot products: partials[b] = sum over block b of x*y (fixed grid)
 constexpr int kRedBlocks = 592;
+// Jacobi step over the concatenated amplitude vector (up to three rank
+// segments of seg_n[l] doubles: t[l], r[l]) fused with the DIIS overlaps of the
+// new error vector: e = r * dinv, x' = t + e written to xo / eo (contiguous),
+// and partials[h][block] of <e, he[h]> for h < m (he[h] == eo: the new vector
+// itself).  Fixed grid and order: deterministic.
+struct JacobiSegs {
+    int nseg;
+    int64_t n[3];
+    const double *t[3];
+    const double *r[3];
+    const double *he[16];
+    int m;
+};
+cudaError_t launch_jacobi_dots(const JacobiSegs &g, const double *dinv, double *xo, double *eo, double *partials,
+                               cudaStream_t s);
 cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, double *partials,
                                 cudaStream_t s);
 // energy partials: sum_ijab V[ijab] (1/4 t2[ijab] + 1/2 t1[ia] t1[jb]); t1 may be NULL.
