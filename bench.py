@@ -248,6 +248,14 @@ def run_ccsdt(args, world, rank, local):
     plans = {"fp64": Engine(dsys, list_text=text), args.precision: Engine(dsys, list_text=text,
                                                                           precision=args.precision)}
     out = {}
+    t_tune = None
+    if not args.no_tune:
+        # GEMM configurations of the mixed plan picked by timing (cc_plan_autotune)
+        tt = time.perf_counter()
+        plans[args.precision].autotune(*z()[:2], reps=2, stream=stream, t3=z()[2])
+        plans[args.precision].release()
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - tt
     for name, eng in plans.items():
         t1, t2, t3 = z()
         sol = Solver(eng)
@@ -316,7 +324,7 @@ def run_ccsdt(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_T, "precision": args.precision, "list": "ccsdt (generated)",
                        "flops_per_iter": plans["fp64"].plan.flops, "replicas": world,
-                       "l2": "inputs larger than L2 (T3 1.07 GB)"},
+                       "l2": "inputs larger than L2 (T3 1.07 GB)", "autotune_s": t_tune},
             "roofline": m.get("roofline"), "gpu_launches": m["launches"], "clocks": m["clocks"],
             "plans": out, "tts": tts}
     if cpu is not None:
@@ -602,7 +610,10 @@ def main():
                        "flops_counted": "packed (pair-count) flops" if args.packed else "unpacked flops",
                        "l2": "inputs larger than L2 (<ab||ef> split planes %.1f GB, T2 %d MB)"
                              % (6.4 * (2 if cplx else 1), 512 * (2 if cplx else 1)),
-                       "integral_build_s": t_int, "integral_bytes": int_bytes, "autotune_s": t_tune},
+                       "integral_build_s": t_int, "integral_bytes": int_bytes, "autotune_s": t_tune,
+                       "gemm_configs": {st["note"]: [st.get("bn", 0), st["splitk"], st.get("red", 0),
+                                                     st.get("bk", 64)]
+                                        for st in desc["steps"] if st.get("configs")}},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -461,6 +461,8 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
                 trial.tc.bk = c[3];
             } else {
                 trial.gemm.splitk = c[1];
+                trial.gemm.red = c[2];
+                trial.rg.red = c[2];
             }
             float ms = 0.f, acc = 0.f;
             for (int r = 0; r < reps; r++) {
@@ -485,6 +487,8 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
             stp.tc.bk = pick[3];
         } else {
             stp.gemm.splitk = pick[1];
+            stp.gemm.red = pick[2];
+            stp.rg.red = pick[2];
         }
     }
     cudaEventDestroy(e0);
@@ -541,6 +545,8 @@ cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, in
         stp.tc.bk = bk;
     } else {
         stp.gemm.splitk = splitk;
+        stp.gemm.red = red;
+        stp.rg.red = red;
     }
     return CC_OK;
 }

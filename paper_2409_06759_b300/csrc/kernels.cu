@@ -171,6 +171,12 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmF64Desc d, cons
 #pragma unroll
             for (int j = 0; j < 4; j++)
                 if (rv[i] && cv[j]) C[ro[i] + co[j]] = epi_scale(acc[i][j], d.as);
+    } else if (d.red) {
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (rv[i] && cv[j]) red_add(C + ro[i] + co[j], epi_scale(acc[i][j], d.as));
     } else {
         T old[4][4];
 #pragma unroll
@@ -380,6 +386,10 @@ __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kern
 #pragma unroll
             for (int c = 0; c < NC; c++)
                 if (c < d.nc) C[co + cco[c]] = epi_scale(acc[c], d.as);
+        } else if (d.red) {
+#pragma unroll
+            for (int c = 0; c < NC; c++)
+                if (c < d.nc) red_add(C + co + cco[c], epi_scale(acc[c], d.as));
         } else {
 #pragma unroll
             for (int c0 = 0; c0 < NC; c0 += 8) {

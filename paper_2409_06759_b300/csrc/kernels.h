@@ -93,6 +93,7 @@ struct GemmF64Desc {
     int f32;
     int bcase;                      // set by launch_gemm_f64 from beta
     Scale as;                       // make_scale(alpha), same launcher
+    int red;                        // beta = 1, no split K: add C by red.global.add.f64 (no read)
 };
 
 // Narrow GEMM: C(r, c) = alpha * sum_k X(r, k) Y(k, c) + beta * C(r, c) for
@@ -111,6 +112,7 @@ struct RowsGemmDesc {
     int f32;
     int bcase;                      // set by launch_rows_gemm from beta
     Scale as;                       // make_scale(alpha), same launcher
+    int red;                        // beta = 1: add C by red.global.add.f64 (no read)
 };
 
 // Packed index pairs.  A pair (p < q) of letters with extent n has the index

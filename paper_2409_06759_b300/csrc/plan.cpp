@@ -862,6 +862,7 @@ struct Planner {
             fb_order = direct0 ? fusable(out, FB).order : fusable(B, FB).order;
             k_order = Mx >= Nx ? fusable(A, K).order : fusable(B, K).order;
             g.rows = true;
+            g.gemm.splitk = 1;
             g.gemm.M = Mx;
             g.gemm.N = Nx;
             g.gemm.K = Kx;
@@ -1008,6 +1009,8 @@ struct Planner {
             r.alpha = galpha;
             r.beta = gbeta;
             r.f32 = use_f32 ? 1 : 0;
+            // an accumulating narrow GEMM may add its outputs with reductions
+            if (gbeta == 1.0) g.cands = {{0, 1, 0, 64}, {0, 1, 1, 64}};
             g.a = xa ? aref : bref;
             g.b = xa ? bref : aref;
         } else if (!g.mixed) {
@@ -1015,6 +1018,8 @@ struct Planner {
             g.gemm.cn = cn;
             g.gemm.alpha = galpha;
             g.gemm.beta = gbeta;
+            // an accumulating tiled GEMM may add its outputs with reductions
+            if (gbeta == 1.0 && !g.cands.empty()) g.cands.push_back({0, 1, 1, 64});
             g.gemm.f32 = use_f32 ? 1 : 0;
             g.gemm.cplx = cplx ? 1 : 0;
             g.gemm.conj_a = cplx && A.conj ? 1 : 0;
@@ -1292,7 +1297,8 @@ std::string describe_plan(const Plan &plan) {
            << "\",\"note\":\"" << s.note << "\"";
         if (s.kind == StepKind::GEMM && !s.mixed) {
             os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
-               << ",\"splitk\":" << s.gemm.splitk << ",\"candidates\":" << s.cands.size()
+               << ",\"splitk\":" << s.gemm.splitk << ",\"red\":" << (s.rows ? s.rg.red : s.gemm.red)
+               << ",\"candidates\":" << s.cands.size()
                << ",\"configs\":" << cands_json(s.cands)
                << ",\"sAm\":" << s.gemm.sAm << ",\"sAk\":" << s.gemm.sAk << ",\"sBk\":" << s.gemm.sBk
                << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta

@@ -66,6 +66,14 @@ template <bool ACC, typename T> __device__ __forceinline__ T finish(const Scale 
     const T v = scale_f64(acc, as);
     return ACC ? add(v, old) : v;
 }
+// *p += v by a fire-and-forget reduction in L2 (no value returns to the SM)
+__device__ __forceinline__ void red_add(double *p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double2 *p, double2 v) {
+    red_add(reinterpret_cast<double *>(p), v.x);
+    red_add(reinterpret_cast<double *>(p) + 1, v.y);
+}
 // acc + a * b over complex (or real) numbers
 __device__ __forceinline__ double cfma(double a, double b, double acc) { return fma(a, b, acc); }
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {

@@ -28,7 +28,7 @@ __device__ __forceinline__ int64_t grp_off(const Grp &g, int64_t x) {
 // applied to C beforehand), skipping co[j] < 0.  The branch is taken once per
 // batch, so the FP64 add exists only on the accumulating side.
 // fire-and-forget FP64 add in L2 (no value returns to the SM)
-__device__ __forceinline__ void red_add(double *p, double v) {
+__device__ __forceinline__ void red_add_tc(double *p, double v) {
     asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
@@ -40,7 +40,7 @@ __device__ __forceinline__ void store_batch(double *__restrict__ C, int64_t roff
     if (bcase == 2) {
 #pragma unroll
         for (int j = 0; j < NB; j++)
-            if (co[j] >= 0) red_add(C + roff + co[j], v[j]);
+            if (co[j] >= 0) red_add_tc(C + roff + co[j], v[j]);
     } else if (bcase == 0) {
 #pragma unroll
         for (int j = 0; j < NB; j++)
@@ -72,7 +72,7 @@ __device__ __forceinline__ void store_batch_f32(double *__restrict__ C, int64_t 
     } else if (bcase == 2) {
 #pragma unroll
         for (int j = 0; j < NB; j++)
-            if (co[j] >= 0) red_add(C + roff + co[j], f32_to_f64_pow2(__uint_as_float(r[j]), as.kexp, as.sflip));
+            if (co[j] >= 0) red_add_tc(C + roff + co[j], f32_to_f64_pow2(__uint_as_float(r[j]), as.kexp, as.sflip));
     } else {
         double old[NB];
 #pragma unroll

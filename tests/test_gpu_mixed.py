@@ -190,9 +190,9 @@ def test_every_gemm_configuration_gives_the_same_residual(cc, o, v):
     steps = eng.plan.describe()["steps"]
     reds = bk32 = 0
     for k, st in enumerate(steps):
-        if st["kind"] != "gemm_bf16split" or not st.get("configs"):
+        if not st.get("configs"):
             continue
-        planned = (st["bn"], st["splitk"], st["red"], st["bk"])
+        planned = (st.get("bn", 0), st["splitk"], st.get("red", 0), st.get("bk", 64))
         for bn, sk, red, bk in st["configs"]:
             ccm.cc_plan_set_gemm_config(eng.plan, k, bn, sk, red, bk)
             r1, r2 = eng.residual(T1, T2)
