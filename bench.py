@@ -504,8 +504,8 @@ def main():
     if args.load_tune:
         # replay a configuration saved by an earlier run (e.g. for a profiler run,
         # where timings taken under the profiler would mislead the autotuner)
-        for k, bn, sk, red, bk in json.load(open(args.load_tune)):
-            cc.cc_plan_set_gemm_config(mixed.plan, k, bn, sk, red, bk)
+        for k, bn, sk, red in json.load(open(args.load_tune)):
+            cc.cc_plan_set_gemm_config(mixed.plan, k, bn, sk, red)
     elif not args.no_tune:
         tt = time.perf_counter()
         mixed.autotune(*z(), reps=3, stream=stream)
@@ -513,7 +513,7 @@ def main():
         torch.cuda.synchronize()
         t_tune = time.perf_counter() - tt
     if args.save_tune and rank == 0:
-        cfgs = [[k, st.get("bn", 0), st["splitk"], st.get("red", 0), st.get("bk", 64)] for k, st in
+        cfgs = [[k, st.get("bn", 0), st["splitk"], st.get("red", 0)] for k, st in
                 enumerate(mixed.plan.describe()["steps"]) if st.get("configs")]
         json.dump(cfgs, open(args.save_tune, "w"))
 
@@ -611,8 +611,7 @@ def main():
                        "l2": "inputs larger than L2 (<ab||ef> split planes %.1f GB, T2 %d MB)"
                              % (6.4 * (2 if cplx else 1), 512 * (2 if cplx else 1)),
                        "integral_build_s": t_int, "integral_bytes": int_bytes, "autotune_s": t_tune,
-                       "gemm_configs": {st["note"]: [st.get("bn", 0), st["splitk"], st.get("red", 0),
-                                                     st.get("bk", 64)]
+                       "gemm_configs": {st["note"]: [st.get("bn", 0), st["splitk"], st.get("red", 0)]
                                         for st in desc["steps"] if st.get("configs")}},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
     if cpu is not None:

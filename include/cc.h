@@ -194,10 +194,9 @@ CC_API cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const 
  * candidates, e.g. to replay a configuration chosen by cc_plan_autotune.
  *   bn: tensor-core tile width (64, 128, 256; 0 on the FP64/FP32 route);
  *   splitk: split-K factor; red: 1 = epilogue by red.global.add.f64 (only
- *   for accumulating contractions without split K), else 0; bk: K block
- *   width of the tensor-core pipeline (64, or 32 for bn 256: twice the stages).
+ *   for accumulating contractions without split K), else 0.
  * Returns CC_ERR_INVALID_ARG when the step has no such candidate. */
-CC_API cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red, int bk);
+CC_API cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red);
 
 /* cc_energy -- E_CC - E_ref = 1/4 sum <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b
  * (f_ia = 0).  e_dev: device double[2] receiving (Re E, Im E) (Im E = 0 for

@@ -98,7 +98,7 @@ _sig = {
     "cc_solve_batched_workspace_bytes": (c_int, [c_int, _P(c_void_p), _P(cc_solve_opts), _P(c_size_t)]),
     "cc_solve_batched": (c_int, [c_int, _P(c_void_p), _P(cc_integrals), _P(cc_amps), _P(cc_solve_opts),
                                  _P(cc_solve_report), c_void_p, c_size_t, c_void_p]),
-    "cc_plan_set_gemm_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int]),
+    "cc_plan_set_gemm_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "cc_plan_autotune": (c_int, [c_void_p, _P(cc_integrals), _P(cc_amps), _P(cc_resid), c_void_p, c_size_t, c_void_p,
                                  c_int]),
     "cc_build_vvvv_packed_workspace_bytes": (c_int, [c_int, c_int, c_int, c_int, _P(c_size_t)]),
@@ -259,9 +259,9 @@ def cc_residual(plan: Plan, ints: dict, t1, t2, r1, r2, ws, stream=None, t3=None
                             _stream(stream)), "cc_residual")
 
 
-def cc_plan_set_gemm_config(plan: Plan, step: int, bn: int, splitk: int, red: int = 0, bk: int = 64):
+def cc_plan_set_gemm_config(plan: Plan, step: int, bn: int, splitk: int, red: int = 0):
     """Sets one contraction step to one of its autotuning candidates."""
-    _check(_lib.cc_plan_set_gemm_config(plan.handle, step, bn, splitk, red, bk), "cc_plan_set_gemm_config")
+    _check(_lib.cc_plan_set_gemm_config(plan.handle, step, bn, splitk, red), "cc_plan_set_gemm_config")
 
 
 def cc_plan_autotune(plan: Plan, ints: dict, t1, t2, r1, r2, ws, reps: int = 3, stream=None, t3=None, r3=None):

@@ -451,14 +451,13 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
         if (st != CC_OK) { result = st; break; }
         if (stp.cands.size() < 2) continue;
         double best = 1e30;
-        std::array<int, 4> pick = stp.cands[0];
+        std::array<int, 3> pick = stp.cands[0];
         for (const auto &c : stp.cands) {
             Step trial = stp;
             if (trial.mixed) {
                 trial.tc.bn = c[0];
                 trial.tc.splitk = c[1];
                 trial.tc.red = c[2];
-                trial.tc.bk = c[3];
             } else {
                 trial.gemm.splitk = c[1];
                 trial.gemm.red = c[2];
@@ -484,7 +483,6 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
             stp.tc.bn = pick[0];
             stp.tc.splitk = pick[1];
             stp.tc.red = pick[2];
-            stp.tc.bk = pick[3];
         } else {
             stp.gemm.splitk = pick[1];
             stp.gemm.red = pick[2];
@@ -529,12 +527,12 @@ cc_status cc_unpack_t2(int o, int v, cc_dtype dtype, const void *t_packed, void 
     return CC_OK;
 }
 
-cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red, int bk) {
+cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red) {
     if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
     Plan &P = plan->plan;
     if (step < 0 || step >= (int)P.steps.size()) return fail(CC_ERR_INVALID_ARG, "step index out of range");
     Step &stp = P.steps[step];
-    const std::array<int, 4> want{bn, splitk, red, bk};
+    const std::array<int, 3> want{bn, splitk, red};
     bool found = false;
     for (const auto &c : stp.cands) found = found || c == want;
     if (!found) return fail(CC_ERR_INVALID_ARG, "not a candidate configuration of this step");
@@ -542,7 +540,6 @@ cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, in
         stp.tc.bn = bn;
         stp.tc.splitk = splitk;
         stp.tc.red = red;
-        stp.tc.bk = bk;
     } else {
         stp.gemm.splitk = splitk;
         stp.gemm.red = red;

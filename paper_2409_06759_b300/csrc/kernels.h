@@ -183,7 +183,6 @@ struct TcGemmDesc {
     int bcase;                      // set by launch_tc_gemm from beta
     Scale as;                       // make_scale(alpha), same launcher
     int red;                        // beta = 1, no split K: add the tile with red.global.add.f64
-    int bk;                         // K block width: 64 (SWIZZLE_128B), or 32 (bn 256: four stages)
 };
 
 cudaError_t launch_accum(const AccumDesc &d, const double *src, double *out, cudaStream_t s,

@@ -955,16 +955,15 @@ struct Planner {
             // autotuning candidates: split-K factors (the partials buffer takes the largest)
             int64_t skmax = g.gemm.splitk;
             if (g.gemm.M > 1 && g.gemm.N > 1 && g.gemm.K > 1) {
-                g.cands.push_back({0, 1, 0, 64});
+                g.cands.push_back({0, 1, 0});
                 for (int sk : {2, 4, 8, 16, 32, 64})
                     if (sk <= g.gemm.K / 64 && sk * g.gemm.M * g.gemm.N * esz <= (int64_t)512 << 20) {
-                        g.cands.push_back({0, sk, 0, 64});
+                        g.cands.push_back({0, sk, 0});
                         skmax = std::max<int64_t>(skmax, sk);
                     }
                 if (g.gemm.splitk > 1 &&
-                    std::find(g.cands.begin(), g.cands.end(), std::array<int, 4>{0, g.gemm.splitk, 0, 64}) ==
-                        g.cands.end())
-                    g.cands.push_back({0, g.gemm.splitk, 0, 64});
+                    std::find(g.cands.begin(), g.cands.end(), std::array<int, 3>{0, g.gemm.splitk, 0}) == g.cands.end())
+                    g.cands.push_back({0, g.gemm.splitk, 0});
                 if (g.cands.size() < 2) g.cands.clear();
             }
             if (skmax > 1) g.partials = scratch(skmax * g.gemm.M * g.gemm.N * esz);
@@ -1010,7 +1009,7 @@ struct Planner {
             r.beta = gbeta;
             r.f32 = use_f32 ? 1 : 0;
             // an accumulating narrow GEMM may add its outputs with reductions
-            if (gbeta == 1.0) g.cands = {{0, 1, 0, 64}, {0, 1, 1, 64}};
+            if (gbeta == 1.0) g.cands = {{0, 1, 0}, {0, 1, 1}};
             g.a = xa ? aref : bref;
             g.b = xa ? bref : aref;
         } else if (!g.mixed) {
@@ -1019,7 +1018,7 @@ struct Planner {
             g.gemm.alpha = galpha;
             g.gemm.beta = gbeta;
             // an accumulating tiled GEMM may add its outputs with reductions
-            if (gbeta == 1.0 && !g.cands.empty()) g.cands.push_back({0, 1, 1, 64});
+            if (gbeta == 1.0 && !g.cands.empty()) g.cands.push_back({0, 1, 1});
             g.gemm.f32 = use_f32 ? 1 : 0;
             g.gemm.cplx = cplx ? 1 : 0;
             g.gemm.conj_a = cplx && A.conj ? 1 : 0;
@@ -1061,25 +1060,16 @@ struct Planner {
                 if (bn > bn_max) continue;
                 for (int sk : {1, 2, 4, 8, 16})
                     if (sk == 1 || (sk <= kblocks / 4 && sk * Mr * Nr * 8 <= (int64_t)512 << 20)) {
-                        g.cands.push_back({bn, sk, 0, 64});
+                        g.cands.push_back({bn, sk, 0});
                         skmax = std::max<int64_t>(skmax, sk);
                     }
                 // an accumulating GEMM without split K may also add its tile with
                 // fire-and-forget reductions (red.global.add.f64) instead of a
                 // read-modify-write: no load latency in the epilogue
-                if (gbeta == 1.0) g.cands.push_back({bn, 1, 1, 64});
-            }
-            // the widest tile with half-width K blocks: four pipeline stages in the
-            // shared memory two full-width ones take (more loads in flight)
-            if (np == 2 && bn_max == 256) {
-                for (int sk : {1, 2, 4})
-                    if (sk == 1 || (sk <= kblocks / 4 && sk * Mr * Nr * 8 <= (int64_t)512 << 20))
-                        g.cands.push_back({256, sk, 0, 32});
-                if (gbeta == 1.0) g.cands.push_back({256, 1, 1, 32});
+                if (gbeta == 1.0) g.cands.push_back({bn, 1, 1});
             }
             // the planned configuration is always one of them
-            t.bk = 64;
-            const std::array<int, 4> planned{t.bn, t.splitk, 0, 64};
+            const std::array<int, 3> planned{t.bn, t.splitk, 0};
             if (std::find(g.cands.begin(), g.cands.end(), planned) == g.cands.end()) g.cands.push_back(planned);
             if (g.cands.size() < 2) g.cands.clear();
             if (skmax > 1) g.partials = scratch(skmax * Mr * Nr * 8);
@@ -1248,12 +1238,12 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     return true;
 }
 
-// [[bn, splitk, red, bk], ...] of a step's autotuning candidates
-static std::string cands_json(const std::vector<std::array<int, 4>> &c) {
+// [[bn, splitk, red], ...] of a step's autotuning candidates
+static std::string cands_json(const std::vector<std::array<int, 3>> &c) {
     std::string out = "[";
     for (size_t k = 0; k < c.size(); k++)
         out += (k ? ",[" : "[") + std::to_string(c[k][0]) + "," + std::to_string(c[k][1]) + "," +
-               std::to_string(c[k][2]) + "," + std::to_string(c[k][3]) + "]";
+               std::to_string(c[k][2]) + "]";
     return out + "]";
 }
 
@@ -1311,8 +1301,7 @@ std::string describe_plan(const Plan &plan) {
                << ",\"products\":" << s.tc.nprod << ",\"a_static\":" << (s.a_static ? 1 : 0)
                << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta
                << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp << ",\"bn\":" << s.tc.bn
-               << ",\"splitk\":" << s.tc.splitk << ",\"red\":" << s.tc.red << ",\"bk\":" << (s.tc.bk ? s.tc.bk : 64)
-               << ",\"candidates\":" << s.cands.size()
+               << ",\"splitk\":" << s.tc.splitk << ",\"red\":" << s.tc.red << ",\"candidates\":" << s.cands.size()
                << ",\"configs\":" << cands_json(s.cands)
                << ",\"planes_a_off\":" << s.planes_a_off << ",\"planes_b_off\":" << s.planes_b_off
                << ",\"reuse_a\":" << (s.skip_a ? 1 : 0) << ",\"reuse_b\":" << (s.skip_b ? 1 : 0)

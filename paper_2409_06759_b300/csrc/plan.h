@@ -65,8 +65,7 @@ struct Step {
     bool a_static = false, b_static = false;     // operand is an integral block (cacheable)
     bool static_src = false;                     // ACCUM permute of an integral block into the cache
     bool skip_a = false, skip_b = false;         // planes already split by an earlier step (same source version)
-    std::vector<std::array<int, 4>> cands;       // autotuning candidates (tile width or 0, split-K, red epilogue,
-                                                 // K block width)
+    std::vector<std::array<int, 3>> cands;       // autotuning candidates (tile width or 0, split-K, red epilogue)
     PackDesc pk{};                               // PACK: out = packed pairs of a
     UnpackDesc up{};                             // UNPACK: out (antisymmetric) from packed a
     bool rows = false;                           // narrow GEMM (one thread per row, operands in place)

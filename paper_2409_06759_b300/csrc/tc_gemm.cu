@@ -448,30 +448,15 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// The same for tiles written with SWIZZLE_64B (32-column K blocks): rows of 64
-// bytes, 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset between 8-row groups
-    d |= (uint64_t)1 << 46;                     // descriptor version of tcgen05
-    d |= (uint64_t)4 << 61;                     // SWIZZLE_64B
-    return d;
-}
-template <int BKc> __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
-    return BKc == 64 ? sw128_desc(saddr) : sw64_desc(saddr);
-}
-
 // Instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-template <int NP, int BN, int STAGES, int BKc = BK>
+template <int NP, int BN, int STAGES>
 struct Cfg {
-    static constexpr int A_BYTES = BM * BKc * 2;
-    static constexpr int B_BYTES = BN * BKc * 2;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 1024 /*barriers, offsets*/ + BN * 8;
     static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
@@ -636,12 +621,12 @@ __global__ void __launch_bounds__(192, 1)
 // the epilogue of one tile overlaps the main loop of the next.  Eight epilogue
 // warps (2..9): warp w reads TMEM lanes 32*(w%4).. and the column half (w-2)/4
 // of the tile, so twice as many output loads are in flight as with four.
-template <int NP, int BN, int STAGES, int BKc>
+template <int NP, int BN, int STAGES>
 __global__ void __launch_bounds__(320, 1)
     tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                               const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials,
                               int kb_per_split, int nslices, int64_t ntiles, int *err_flag) {
-    using G = Cfg<NP, BN, STAGES, BKc>;
+    using G = Cfg<NP, BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *tiles = smem;
@@ -656,7 +641,7 @@ __global__ void __launch_bounds__(320, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (int)((d.N + BN - 1) / BN);   // tiles past N would read padding only
-    const int kb_total = (int)(d.Kp / BKc);
+    const int kb_total = (int)(d.Kp / BK);
     const int64_t total = ntiles * nslices;
 
     if (threadIdx.x == 0) {
@@ -709,9 +694,9 @@ __global__ void __launch_bounds__(320, 1)
                     uint8_t *st = tiles + s * G::STAGE_BYTES;
                     mbar_expect_tx(&full[s], G::STAGE_BYTES);
                     for (int p = 0; p < NP; p++)
-                        tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], kb * BKc, (int)m0, p);
+                        tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], kb * BK, (int)m0, p);
                     for (int q = 0; q < NP; q++)
-                        tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BKc, (int)n0, q);
+                        tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BK, (int)n0, q);
                 }
             }
             if (stop) {
@@ -754,8 +739,8 @@ __global__ void __launch_bounds__(320, 1)
                         const uint32_t a0 = st + d.prod_a[pr] * G::A_BYTES;
                         const uint32_t b0 = st + NP * G::A_BYTES + d.prod_b[pr] * G::B_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < BKc / 16; kk++)
-                            mma_bf16(dt, kmajor_desc<BKc>(a0 + kk * 32), kmajor_desc<BKc>(b0 + kk * 32), idesc,
+                        for (int kk = 0; kk < BK / 16; kk++)
+                            mma_bf16(dt, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
                                      ((kb - kb0) | pr | kk) != 0);
                     }
                     mma_commit(&empty[s]);
@@ -1053,17 +1038,15 @@ static EncodeTiledFn encode_fn() {
 
 // 3-D map over the planes [nplanes][rows][Kp] bf16 (rows unpadded: the
 // box rows past `rows` read as zeros), box {64, box_rows, 1}
-static bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t Kp, int nplanes, int box_rows,
-                     int box_k = BK) {
+static bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t Kp, int nplanes, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
-    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -1097,31 +1080,29 @@ static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B,
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
-template <int NP, int BN, int STAGES, int BKc = BK>
+template <int NP, int BN, int STAGES>
 static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials,
                                      int *err, cudaStream_t s) {
-    using G = Cfg<NP, BN, STAGES, BKc>;
+    using G = Cfg<NP, BN, STAGES>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_persistent_kernel<NP, BN, STAGES, BKc>,
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_persistent_kernel<NP, BN, STAGES>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (d.Mp % BM || d.Kp % BKc || d.Mp < d.M) return cudaErrorInvalidValue;
+    if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, d.M, d.Kp, NP, BM, BKc) || !make_map(&mb, B, d.N, d.Kp, NP, BN, BKc))
-        return cudaErrorInvalidValue;
+    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mb, B, d.N, d.Kp, NP, BN)) return cudaErrorInvalidValue;
     const int64_t ntiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
-    const int kb_total = (int)(d.Kp / BKc);
+    const int kb_total = (int)(d.Kp / BK);
     const int sk = d.splitk > 1 ? d.splitk : 1;
     const int per = (kb_total + sk - 1) / sk;
     const int zs = (kb_total + per - 1) / per;
     if (zs > 1 && !partials) return cudaErrorInvalidValue;
     const int64_t total = ntiles * zs;
     const int grid = (int)(total < 148 ? total : 148);
-    tc_gemm_persistent_kernel<NP, BN, STAGES, BKc><<<grid, 320, G::SMEM, s>>>(ma, mb, d, C, partials, per, zs, ntiles,
-                                                                            err);
+    tc_gemm_persistent_kernel<NP, BN, STAGES><<<grid, 320, G::SMEM, s>>>(ma, mb, d, C, partials, per, zs, ntiles, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || zs == 1) return e;
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
@@ -1192,9 +1173,6 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d0, const void *Aplanes, const void
         if (((uintptr_t)Aplanes & 15) || ((uintptr_t)Bplanes & 15)) return cudaErrorMisalignedAddress;
     }
     if (d.nplanes_a == 2) {
-        // bk 32: half-width K blocks (SWIZZLE_64B), twice the pipeline stages in the same shared memory
-        if (d.bn == 256 && d.bk == 32)
-            return tc::launch_persistent<2, 256, 4, 32>(d, Aplanes, Bplanes, C, partials, err_flag, s);
         if (d.bn == 256) return tc::launch_persistent<2, 256, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
         if (d.bn == 128) return tc::launch_persistent<2, 128, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
         if (d.bn == 64) return tc::launch_persistent<2, 64, 4>(d, Aplanes, Bplanes, C, partials, err_flag, s);
