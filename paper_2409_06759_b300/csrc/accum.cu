@@ -16,6 +16,8 @@
 // every operand:
 //   antisym_pairs   out = alpha P(ij) P(ab) src (4 terms, same index order):
 //                   each orbit {ijab, jiab, ijba, jiba} is read and written once
+//   antisym_triple  the six-term antisymmetriser of a triple of dims (leading
+//                   or innermost), one orbit read and written once
 //   accum_rows      every term reads its sources with stride 0 or 1 along the
 //                   output's innermost dim (copies, outer products T1 x T1,
 //                   and a copy fused into the next step: out = add + ...)
@@ -522,6 +524,71 @@ __global__ void __launch_bounds__(256) antisym_triple_rows_kernel(const AccumDes
     }
 }
 
+// The same antisymmetriser over the three innermost dims (e.g. the virtual
+// triple of W3 = P(a/bc) P(bc) Z3): the orbit {sigma(a, b, c)} spans a whole
+// n^3 cube of one batch row, so its members are strided.  A work item is
+// (batch row, eight pairs a < b); warp w takes one pair and its lanes the c >
+// b, reading the six orbit members, forming X once and writing +-X to all
+// six.  Consecutive items share a row, so the blocks running at once work on a
+// few cubes that L2 holds, and every element still moves once through HBM.
+// In store mode, items past the orbits zero the cube's repeated-index planes.
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(256) antisym_triple_inner_kernel(const AccumDesc d, const TripleSym g,
+                                                                   const T *__restrict__ src, T *__restrict__ out,
+                                                                   uint32_t npair_items, uint64_t items) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = g.n;
+    const uint64_t orbit_items = (uint64_t)g.nb * npair_items;
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        if (it >= orbit_items) {
+            // store mode: zero the planes with a repeated index, row (it - orbit_items) / n, plane x
+            const uint64_t z = it - orbit_items;
+            const int64_t row = (int64_t)(z / (uint64_t)n), x = (int64_t)(z % (uint64_t)n);
+            T *o = out + row * g.ob;
+            for (int64_t y = threadIdx.x; y < n; y += blockDim.x) {
+                o[x * g.O[0] + x * g.O[1] + y * g.O[2]] = zero<T>();
+                o[x * g.O[0] + y * g.O[1] + x * g.O[2]] = zero<T>();
+                o[y * g.O[0] + x * g.O[1] + x * g.O[2]] = zero<T>();
+            }
+            continue;
+        }
+        const int64_t row = (int64_t)(it / npair_items);
+        const uint32_t pi = (uint32_t)(it % npair_items) * 8 + warp;       // this warp's pair index
+        // pair index -> a < b (b fastest)
+        int64_t a = 0, b = 0;
+        {
+            uint32_t r = pi;
+            bool found = false;
+            for (a = 0; a + 1 < n; a++) {
+                const uint32_t cnt = (uint32_t)(n - 1 - a);
+                if (r < cnt) { b = a + 1 + r; found = true; break; }
+                r -= cnt;
+            }
+            if (!found) continue;                                          // past the last pair
+        }
+        const T *sr = src + row * g.sb;
+        T *orow = out + row * g.ob;
+        for (int64_t c = b + 1 + lane; c < n; c += 32) {
+            T acc = zero<T>();
+#pragma unroll
+            for (int p = 0; p < 6; p++) {
+                const T w = cj(ld(sr + a * g.S[p][0] + b * g.S[p][1] + c * g.S[p][2]), d.conj_a);
+                acc = signed_term(p == 0, (d.negmask >> p) & 1ull, w, acc);
+            }
+            const T X = scale_f64(acc, d.as);
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                int64_t x, y, z;
+                bool odd;
+                triple_perm(q, a, b, c, x, y, z, odd);
+                T *op = orow + x * g.O[0] + y * g.O[1] + z * g.O[2];
+                const T v = odd ? neg(X) : X;
+                *op = ACC ? add(v, *op) : v;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host side
 // Drop unit dims and merge neighbours k, k+1 that are contiguous in the
 // output and in every term's source(s): the kernels then see the fewest dims
@@ -608,10 +675,10 @@ static bool match_pair_antisym(const AccumDesc &d, PairSym &g, double &alpha_sig
 // after them (unit strides in src and out)?  Term p's strides on the three
 // dims must be a permutation of term 0's, and its sign term 0's times the
 // permutation's parity.
-static bool match_triple_antisym(const AccumDesc &d0, TripleSym &g) {
+static bool match_triple_antisym(const AccumDesc &d0, TripleSym &g, bool inner = false) {
     if (d0.two_src || d0.has_add || d0.nperm != 6) return false;
     AccumDesc d = d0;
-    for (int t = 0; t + 2 < d.nd; t++) {
+    for (int t = inner ? d.nd - 3 : 0; t >= 0 && t + 2 < d.nd; t++) {
         const int64_t n = d.ext[t];
         if (n < 3 || d.ext[t + 1] != n || d.ext[t + 2] != n || n > 4096) continue;
         // every other dim: the same stride in all terms
@@ -629,7 +696,7 @@ static bool match_triple_antisym(const AccumDesc &d0, TripleSym &g) {
             oo *= d.ext[k];
             C *= d.ext[k];
         }
-        if (!ok || C < 64) continue;
+        if (!ok || (inner ? t + 3 != d.nd : C < 64)) continue;
         // the batch: dims before t collapse into one strided index
         int64_t nb = 1, sb = 0, ob = 0;
         for (int k = t - 1; k >= 0 && ok; k--) {
@@ -741,6 +808,16 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
         antisym_triple_rows_kernel<T, ACC><<<(unsigned)grid_cap((int64_t)items, 148 * 16), 256, 0, s>>>(
             d0, tg, src, out, (uint32_t)nms, (uint32_t)nchunk, items);
         return cudaGetLastError();
+    }
+    if (match_triple_antisym(d0, tg, true) && tg.n <= 4096) {
+        const int64_t npairs = tg.n * (tg.n - 1) / 2;
+        const int64_t npair_items = (npairs + 7) / 8;
+        const uint64_t items = (uint64_t)tg.nb * (uint64_t)npair_items + (ACC ? 0 : (uint64_t)tg.nb * (uint64_t)tg.n);
+        if (npair_items <= 0xffffffffLL) {
+            antisym_triple_inner_kernel<T, ACC><<<(unsigned)grid_cap((int64_t)items, 148 * 16), 256, 0, s>>>(
+                d0, tg, src, out, (uint32_t)npair_items, items);
+            return cudaGetLastError();
+        }
     }
     AccumDesc d = d0;
     collapse_dims(d);

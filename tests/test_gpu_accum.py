@@ -127,10 +127,12 @@ TRIPLE_LISTS = [
     "R3[ijkabc] = T3[ijkabc]\nR3[ijkabc] += -0.5 P(i/jk) P(jk) T3[ijkabc]",
     "R3[ijkabc] = 0.25 P(i/jk) P(jk) T3[jikabc]",
     "R3[ijkabc] = P(a/bc) P(bc) T3[ijkabc]",
+    "R3[ijkabc] = T3[ijkabc]\nR3[ijkabc] += 0.5 P(a/bc) P(bc) T3[ijkabc]",
+    "R3[ijkabc] = -2 P(a/bc) P(bc) T3[ijkacb]",
 ]
 
 
-@pytest.mark.parametrize("o,v", [(4, 6), (5, 5), (3, 9)])
+@pytest.mark.parametrize("o,v", [(4, 6), (5, 5), (3, 9), (3, 37)])
 @pytest.mark.parametrize("k", range(len(TRIPLE_LISTS)))
 def test_triple_antisymmetrisers(cc, k, o, v):
     """Six-term antisymmetrisers of a rank-3 array (plain random, so every

@@ -170,8 +170,9 @@ def test_autotuned_plan_keeps_the_residual(cc, prec, rel):
     assert dd <= rel * np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
 
 
-@pytest.mark.parametrize("o,v", [(10, 40), (7, 45)])
-def test_every_gemm_configuration_gives_the_same_residual(cc, o, v):
+@pytest.mark.parametrize("list_name,prec,o,v", [("ccsd_vvvv", "bf16x3", 10, 40), ("ccsd_vvvv", "bf16x3", 7, 45),
+                                                 ("ccsd", "fp64", 9, 30)])
+def test_every_gemm_configuration_gives_the_same_residual(cc, list_name, prec, o, v):
     """Each contraction step set, one at a time, to every autotuning candidate
     (tile widths, split-K factors, and the reduction epilogue of accumulating
     contractions) reproduces the planned configuration's residual: the
@@ -181,7 +182,7 @@ def test_every_gemm_configuration_gives_the_same_residual(cc, o, v):
     ccm, engine = cc
     s, B, t1, t2 = small_case(o, v, 33, L=16, scale=6.0, tscale=0.05)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
-    eng = engine.Engine(dsys, list_name="ccsd_vvvv", precision="bf16x3")
+    eng = engine.Engine(dsys, list_name=list_name, precision=prec)
     T1, T2 = to_dev(t1), to_dev(t2)
     b1, b2 = eng.residual(T1, T2)
     torch.cuda.synchronize()
@@ -198,7 +199,8 @@ def test_every_gemm_configuration_gives_the_same_residual(cc, o, v):
             r1, r2 = eng.residual(T1, T2)
             torch.cuda.synchronize()
             got = torch.cat([r1.flatten(), r2.flatten()]).cpu().numpy()
-            assert np.linalg.norm(got - base) <= 1e-5 * scale, (k, bn, sk, red)
+            tol = 1e-5 if prec != "fp64" else 1e-13
+            assert np.linalg.norm(got - base) <= tol * scale, (k, bn, sk, red)
             reds += red
         ccm.cc_plan_set_gemm_config(eng.plan, k, *planned)
     assert reds > 0
