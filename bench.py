@@ -560,7 +560,7 @@ def main():
             traffic = TRAFFIC_RATIO * (st["M"] * st["Kp"] * 4 + st["N"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
-                "kernel": "tc_gemm_kernel (" + st["note"] + ")",
+                "kernel": "tc_gemm_persistent_kernel (" + st["note"] + ")",
                 "fp64_equiv_tflops": st["flops"] / t_kernel / 1e12, "ms_per_launch": t_kernel * 1e3,
                 "gemm_shape": [st["M"], st["N"], st["K"]],
                 "frac_of_sustained": achieved / pk["bf16_tflops_sustained"],

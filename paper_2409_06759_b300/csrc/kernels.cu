@@ -675,31 +675,6 @@ cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const dou
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) jacobi_kernel(int rank, int o, int v, const double *fo, const double *fv,
-                                                     const double *t, const double *r, double *xo, double *eo,
-                                                     int64_t rows, uint32_t nvt, int cplx) {
-    const uint32_t ncol = nvt << cplx;
-    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        const double so = occ_sum(rank, o, fo, row);
-        const int64_t base = row * ncol;
-        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
-            const double q = r[base + c] / (so - vir_sum(rank, v, fv, c >> cplx));
-            eo[base + c] = q;
-            xo[base + c] = t[base + c] + q;
-        }
-    }
-}
-
-cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
-                          const double *r, double *xo, double *eo, int cplx, cudaStream_t s) {
-    int64_t rows;
-    uint32_t nvt;
-    rows_cols(rank, o, v, rows, nvt);
-    int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
-    jacobi_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, xo, eo, rows, nvt, cplx ? 1 : 0);
-    return cudaGetLastError();
-}
-
 __global__ void __launch_bounds__(256) inv_denominators_kernel(int rank, int o, int v, const double *fo,
                                                                 const double *fv, double *out, int64_t rows,
                                                                 uint32_t nvt, int cplx) {

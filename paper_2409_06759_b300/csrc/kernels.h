@@ -214,9 +214,6 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void 
 // cplx: t and r are interleaved complex.
 cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv,
                              const double *t, double *r, int cplx, cudaStream_t s);
-// Jacobi step: e = r / D, x' = t + e (written to xo, eo).
-cudaError_t launch_jacobi(int rank, int o, int v, const double *fo, const double *fv, const double *t,
-                          const double *r, double *xo, double *eo, int cplx, cudaStream_t s);
 // y = a*x + b*y over n elements
 cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s);
 // partial sums for dot products: partials[b] = sum over block b of x*y (fixed grid)

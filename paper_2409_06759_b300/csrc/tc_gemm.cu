@@ -332,13 +332,14 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
 }
 
 // ------------------------------------------------------------------ tcgen05
-// One CTA computes a 128 x BN tile of D = sum_products A_p B_q^T:
+// Split-bf16 GEMM D = sum_products A_p B_q^T on the tensor cores.  One CTA per
+// SM (persistent) computes 128 x BN output tiles:
 //   warp 0      TMA producer (one elected lane): all A and B planes of a
 //               64-wide K block land in one pipeline stage (SWIZZLE_128B)
 //   warp 1      TMEM allocator + MMA issuer (one lane): tcgen05.mma kind::f16,
-//               bf16 x bf16 -> fp32 accumulator of 128 lanes x BN columns
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, FP64 alpha/beta
-//               update of the output through the mixed-radix addressing
+//               bf16 x bf16 -> fp32 accumulators of 128 lanes x BN columns
+//   warps 2..   epilogue: tcgen05.ld of the accumulator, alpha/beta update of
+//               the FP64 output through the mixed-radix addressing
 // Every mbarrier wait is bounded (clock64 budget); on expiry the CTA sets
 // err_flag, stops issuing work, waits (bounded) for what it already issued,
 // frees its TMEM and returns.
@@ -459,160 +460,7 @@ struct Cfg {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 1024 /*barriers, offsets*/ + BN * 8;
-    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
 };
-
-template <int NP, int BN, int STAGES>
-__global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials, int kb_per_split,
-                   int *err_flag) {
-    using G = Cfg<NP, BN, STAGES>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *tiles = smem;
-    uint64_t *full = (uint64_t *)(smem + STAGES * G::STAGE_BYTES);
-    uint64_t *empty = full + STAGES;
-    uint64_t *accum = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
-    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    volatile int *consumed = abort_flag + 1;
-    int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = (int)((d.N + BN - 1) / BN);   // tiles past N would read padding only
-    const int tile = blockIdx.x;
-    const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
-    const int64_t n0 = (int64_t)(tile % n_tiles) * BN;
-    // K blocks of this CTA: all of them, or one slice when K is split
-    const int kb_total = (int)(d.Kp / BK);
-    const int kb0 = (int)blockIdx.y * kb_per_split;
-    const int kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
-    const int kblocks = kb1 - kb0;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; s++) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        mbar_init(accum, 1);
-        *abort_flag = 0;
-        *consumed = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 1) {
-        tmem_alloc(tmem_slot, G::TMEM_COLS);
-        tmem_relinquish();
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < kblocks; kb++) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                uint8_t *st = tiles + s * G::STAGE_BYTES;
-                mbar_expect_tx(&full[s], G::STAGE_BYTES);
-                for (int p = 0; p < NP; p++)
-                    tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)m0, p);
-                for (int q = 0; q < NP; q++)
-                    tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK, (int)n0, q);
-                issued = kb + 1;
-            }
-            if (*abort_flag) {
-                // let the copies already in flight land before the CTA exits (kb counts from this slice's start)
-                for (int kb = *consumed; kb < issued; kb++) mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
-                atomicOr(err_flag, 1);
-            }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
-            for (int kb = 0; kb < kblocks; kb++) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                if (*abort_flag || !mbar_wait(&full[s], ph)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                fence_after();
-                const uint32_t st = smem_u32(tiles + s * G::STAGE_BYTES);
-                for (int pr = 0; pr < d.nprod; pr++) {
-                    const uint32_t a0 = st + d.prod_a[pr] * G::A_BYTES;
-                    const uint32_t b0 = st + NP * G::A_BYTES + d.prod_b[pr] * G::B_BYTES;
-#pragma unroll
-                    for (int kk = 0; kk < BK / 16; kk++)
-                        mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
-                                 (kb | pr | kk) != 0);
-                }
-                mma_commit(&empty[s]);   // frees the stage when these MMAs complete
-                *consumed = kb + 1;
-            }
-            mma_commit(accum);           // accumulator complete (or, on abort, all issued MMAs done)
-        }
-        __syncwarp();
-    } else {
-        // epilogue warpgroup: warp w reads TMEM lanes 32*(w%4) .. +31
-        const int q = warp & 3;
-        const int et = threadIdx.x - 64;                 // 0..127
-        for (int c = et; c < BN; c += 128) {
-            const int64_t n = n0 + c;
-            coloff[c] = n < d.N ? grp_off(d.cn, n) : -1;
-        }
-        const int64_t m = m0 + q * 32 + lane;
-        const bool mok = m < d.M;
-        const int64_t roff = mok ? grp_off(d.cm, m) : 0;
-        asm volatile("bar.sync 1, 128;" ::: "memory");   // coloff visible to the epilogue warps
-        bool ok = mbar_wait(accum, 0);
-        fence_after();
-        ok = __all_sync(0xffffffffu, ok && !*abort_flag);   // tcgen05.ld below is warp-collective
-        if (!ok) {
-            *abort_flag = 1;
-            if (lane == 0) atomicOr(err_flag, 1);
-        } else if (gridDim.y > 1) {
-            // split K: raw partial tile, partials[z][n][m] (rows coalesce across the warp)
-            double *P = partials + (int64_t)blockIdx.y * d.M * d.N;
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-                tmem_ld_wait();
-                if (mok) {
-#pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const int64_t n = n0 + c0 + j;
-                        if (n < d.N) P[n * d.M + m] = f32_to_f64_pow2(__uint_as_float(r[j]), 0, 0u);
-                    }
-                }
-            }
-        } else {
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-                tmem_ld_wait();
-                if (mok) {
-                    // loads of the 32 outputs are issued together, then the stores
-                    store_batch_f32<32>(C, roff, coloff + c0, r, d.as, d.bcase);
-                }
-            }
-        }
-    }
-    fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        fence_after();
-        tmem_dealloc(tmem, G::TMEM_COLS);
-    }
-}
 
 // ---- persistent variant (two planes): one CTA per SM walks the tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... of the (tile, K-slice) space.
@@ -1049,35 +897,6 @@ static bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t K
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
-}
-
-template <int NP, int BN, int STAGES>
-static cudaError_t launch_cfg(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials, int *err,
-                              cudaStream_t s) {
-    using G = Cfg<NP, BN, STAGES>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NP, BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             G::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mb, B, d.N, d.Kp, NP, BN)) return cudaErrorInvalidValue;
-    const int64_t tiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
-    if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    const int kb_total = (int)(d.Kp / BK);
-    const int sk = d.splitk > 1 ? d.splitk : 1;
-    const int per = (kb_total + sk - 1) / sk;
-    const int zs = (kb_total + per - 1) / per;
-    if (zs > 1 && !partials) return cudaErrorInvalidValue;
-    if (zs > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)tiles, (unsigned)zs);
-    tc_gemm_kernel<NP, BN, STAGES><<<grid, 192, G::SMEM, s>>>(ma, mb, d, C, partials, per, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || zs == 1) return e;
-    return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
 template <int NP, int BN, int STAGES>
