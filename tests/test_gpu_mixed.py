@@ -170,9 +170,11 @@ def test_autotuned_plan_keeps_the_residual(cc, prec, rel):
     assert dd <= rel * np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
 
 
-@pytest.mark.parametrize("list_name,prec,o,v", [("ccsd_vvvv", "bf16x3", 10, 40), ("ccsd_vvvv", "bf16x3", 7, 45),
-                                                 ("ccsd", "fp64", 9, 30)])
-def test_every_gemm_configuration_gives_the_same_residual(cc, list_name, prec, o, v):
+@pytest.mark.parametrize("list_name,prec,o,v,cplx", [("ccsd_vvvv", "bf16x3", 10, 40, False),
+                                                      ("ccsd_vvvv", "bf16x3", 7, 45, False),
+                                                      ("ccsd", "fp64", 9, 30, False),
+                                                      ("ccsd_vvvv", "bf16x3", 9, 36, True)])
+def test_every_gemm_configuration_gives_the_same_residual(cc, list_name, prec, o, v, cplx):
     """Each contraction step set, one at a time, to every autotuning candidate
     (tile widths, split-K factors, and the reduction epilogue of accumulating
     contractions) reproduces the planned configuration's residual: the
@@ -180,13 +182,20 @@ def test_every_gemm_configuration_gives_the_same_residual(cc, list_name, prec, o
     column (split K) or the order in which L2 adds a tile (reductions), so the
     difference stays at the split route's rounding level."""
     ccm, engine = cc
-    s, B, t1, t2 = small_case(o, v, 33, L=16, scale=6.0, tscale=0.05)
+    if cplx:
+        s = ccinputs.make_system(o, v, L=16, seed=33, complex_=True)
+        B = s.B * 6.0
+        t1, t2 = ccinputs.random_amplitudes(o, v, seed=33, scale1=0.05, scale2=0.05, complex_=True)
+        T1 = torch.tensor(t1, dtype=torch.complex128, device=DEV)
+        T2 = torch.tensor(t2, dtype=torch.complex128, device=DEV)
+    else:
+        s, B, t1, t2 = small_case(o, v, 33, L=16, scale=6.0, tscale=0.05)
+        T1, T2 = to_dev(t1), to_dev(t2)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
     eng = engine.Engine(dsys, list_name=list_name, precision=prec)
-    T1, T2 = to_dev(t1), to_dev(t2)
     b1, b2 = eng.residual(T1, T2)
     torch.cuda.synchronize()
-    base = torch.cat([b1.flatten(), b2.flatten()]).cpu().numpy()
+    base = torch.cat([b1.flatten(), b2.flatten()]).cpu().numpy()  # complex or real
     scale = np.linalg.norm(base)
     steps = eng.plan.describe()["steps"]
     reds = 0
