@@ -249,13 +249,20 @@ def run_ccsdt(args, world, rank, local):
                                                                           precision=args.precision)}
     out = {}
     t_tune = None
-    if not args.no_tune:
+    mp = plans[args.precision]
+    if args.load_tune:
+        for k, bn, sk, red in json.load(open(args.load_tune)):
+            cc.cc_plan_set_gemm_config(mp.plan, k, bn, sk, red)
+    elif not args.no_tune:
         # GEMM configurations of the mixed plan picked by timing (cc_plan_autotune)
         tt = time.perf_counter()
-        plans[args.precision].autotune(*z()[:2], reps=2, stream=stream, t3=z()[2])
-        plans[args.precision].release()
+        mp.autotune(*z()[:2], reps=2, stream=stream, t3=z()[2])
+        mp.release()
         torch.cuda.synchronize()
         t_tune = time.perf_counter() - tt
+    if args.save_tune and rank == 0:
+        json.dump([[k, st.get("bn", 0), st["splitk"], st.get("red", 0)] for k, st in
+                   enumerate(mp.plan.describe()["steps"]) if st.get("configs")], open(args.save_tune, "w"))
     for name, eng in plans.items():
         t1, t2, t3 = z()
         sol = Solver(eng)
