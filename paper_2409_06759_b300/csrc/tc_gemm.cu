@@ -454,6 +454,21 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Column tiles of an N-column output at tile width BN: the n_tiles =
+// ceil(N / BN) tiles share the ceil(N / 16) 16-column units (16 is the MMA's
+// N step at M = 128) as evenly as possible, the first `extra` tiles one unit
+// wider; a tile's last columns may pass N by less than 16 (TMA reads zeros).
+struct ColSplit {
+    int base, extra;
+    __host__ __device__ int width(int nb) const { return 16 * (base + (nb < extra ? 1 : 0)); }
+    __host__ __device__ int64_t n0(int nb) const { return 16 * ((int64_t)nb * base + (nb < extra ? nb : extra)); }
+    __host__ __device__ int wide() const { return 16 * (base + (extra > 0 ? 1 : 0)); }
+};
+static inline ColSplit col_split(int64_t N, int BN) {
+    const int64_t n_tiles = (N + BN - 1) / BN, units = (N + 15) / 16;
+    return ColSplit{(int)(units / n_tiles), (int)(units % n_tiles)};
+}
+
 template <int NP, int BN, int STAGES>
 struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
@@ -469,11 +484,16 @@ struct Cfg {
 // the epilogue of one tile overlaps the main loop of the next.  Eight epilogue
 // warps (2..9): warp w reads TMEM lanes 32*(w%4).. and the column half (w-2)/4
 // of the tile, so twice as many output loads are in flight as with four.
+// Column tiles share N evenly (ColSplit): e.g. N = 1600 at BN = 256 runs two
+// 240-wide and five 224-wide tiles instead of six full ones and a quarter-full
+// seventh, so no MMA works on padding and tiles of one row block cost about
+// the same (their CTAs stay in step, which keeps the shared A block in L2).
 template <int NP, int BN, int STAGES>
 __global__ void __launch_bounds__(320, 1)
-    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                              const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials,
-                              int kb_per_split, int nslices, int64_t ntiles, int *err_flag) {
+    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBw,
+                              const __grid_constant__ CUtensorMap mapBn, const TcGemmDesc d,
+                              double *__restrict__ C, double *__restrict__ partials, int kb_per_split, int nslices,
+                              int64_t ntiles, const ColSplit cs, int *err_flag) {
     using G = Cfg<NP, BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -514,11 +534,13 @@ __global__ void __launch_bounds__(320, 1)
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    auto tile_coords = [&](int64_t t, int64_t &m0, int64_t &n0, int &kb0, int &kb1) {
+    auto tile_coords = [&](int64_t t, int64_t &m0, int64_t &n0, int &nw, int &kb0, int &kb1) {
         const int64_t tile = t % ntiles;
         const int z = (int)(t / ntiles);
         m0 = (tile / n_tiles) * BM;
-        n0 = (tile % n_tiles) * BN;
+        const int nb = (int)(tile % n_tiles);
+        n0 = cs.n0(nb);
+        nw = cs.width(nb);
         kb0 = z * kb_per_split;
         kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
     };
@@ -529,8 +551,10 @@ __global__ void __launch_bounds__(320, 1)
             bool stop = false;
             for (int64_t t = blockIdx.x; t < total && !stop; t += gridDim.x) {
                 int64_t m0, n0;
-                int kb0, kb1;
-                tile_coords(t, m0, n0, kb0, kb1);
+                int nw, kb0, kb1;
+                tile_coords(t, m0, n0, nw, kb0, kb1);
+                const CUtensorMap *mb = nw == cs.wide() ? &mapBw : &mapBn;
+                const uint32_t bytes = (uint32_t)(NP * (G::A_BYTES + nw * BK * 2));
                 for (int kb = kb0; kb < kb1; kb++, g++) {
                     const int s = (int)(g % STAGES);
                     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -540,11 +564,11 @@ __global__ void __launch_bounds__(320, 1)
                         break;
                     }
                     uint8_t *st = tiles + s * G::STAGE_BYTES;
-                    mbar_expect_tx(&full[s], G::STAGE_BYTES);
+                    mbar_expect_tx(&full[s], bytes);
                     for (int p = 0; p < NP; p++)
                         tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], kb * BK, (int)m0, p);
                     for (int q = 0; q < NP; q++)
-                        tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], kb * BK, (int)n0, q);
+                        tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, mb, &full[s], kb * BK, (int)n0, q);
                 }
             }
             if (stop) {
@@ -556,14 +580,14 @@ __global__ void __launch_bounds__(320, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
             int64_t g = 0;
             int j = 0;                           // local tile counter
             for (int64_t t = blockIdx.x; t < total; t += gridDim.x, j++) {
                 if (*abort_flag) break;
                 int64_t m0, n0;
-                int kb0, kb1;
-                tile_coords(t, m0, n0, kb0, kb1);
+                int nw, kb0, kb1;
+                tile_coords(t, m0, n0, nw, kb0, kb1);
+                const uint32_t idesc = idesc_bf16(BM, nw);
                 const int b = j & 1;
                 if (j >= 2) {
                     if (!mbar_wait(&acce[b], (uint32_t)((j >> 1) - 1) & 1u)) {
@@ -604,14 +628,14 @@ __global__ void __launch_bounds__(320, 1)
         int j = 0;
         for (int64_t t = blockIdx.x; t < total; t += gridDim.x, j++) {
             int64_t m0, n0;
-            int kb0, kb1;
-            tile_coords(t, m0, n0, kb0, kb1);
+            int nw, kb0, kb1;
+            tile_coords(t, m0, n0, nw, kb0, kb1);
             const int b = j & 1;
             const bool split = nslices > 1;
             asm volatile("bar.sync 1, 256;" ::: "memory");   // previous tile's coloff reads are done
             for (int c = et; c < BN; c += 256) {
                 const int64_t n = n0 + c;
-                coloff[c] = n < d.N ? (split ? n : grp_off(d.cn, n)) : -1;
+                coloff[c] = (c < nw && n < d.N) ? (split ? n : grp_off(d.cn, n)) : -1;
             }
             const int64_t m = m0 + q * 32 + lane;
             const bool mok = m < d.M;
@@ -632,6 +656,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll 1
             for (int cc = 0; cc < BN / 2; cc += 32) {
                 const int c0 = half * (BN / 2) + cc;
+                if (c0 >= nw) break;             // warp-uniform: past the tile's columns
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), r);
                 tmem_ld_wait();
@@ -676,9 +701,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 
 template <int NP, int BN, int STAGES, int CH>
 __global__ void __launch_bounds__(320, 1)
-    tc_gemm_chunked_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                           const TcGemmDesc d, double *__restrict__ C, double *__restrict__ partials, int kb_per_split,
-                           int *err_flag) {
+    tc_gemm_chunked_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBw,
+                           const __grid_constant__ CUtensorMap mapBn, const TcGemmDesc d, double *__restrict__ C,
+                           double *__restrict__ partials, int kb_per_split, const ColSplit cs, int *err_flag) {
     using G = Cfg<NP, BN, STAGES>;
     constexpr int HALF = BN / 2;                 // columns per epilogue warp
     extern __shared__ uint8_t smem_raw[];
@@ -697,7 +722,8 @@ __global__ void __launch_bounds__(320, 1)
     const int n_tiles = (int)((d.N + BN - 1) / BN);   // tiles past N would read padding only
     const int tile = blockIdx.x;
     const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
-    const int64_t n0 = (int64_t)(tile % n_tiles) * BN;
+    const int64_t n0 = cs.n0(tile % n_tiles);     // column tiles share N evenly (as the persistent kernel)
+    const int nw = cs.width(tile % n_tiles);
     const int kb_total = (int)(d.Kp / BK);
     const int kb0 = (int)blockIdx.y * kb_per_split;
     const int kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
@@ -737,11 +763,12 @@ __global__ void __launch_bounds__(320, 1)
                     break;
                 }
                 uint8_t *st = tiles + s * G::STAGE_BYTES;
-                mbar_expect_tx(&full[s], G::STAGE_BYTES);
+                mbar_expect_tx(&full[s], (uint32_t)(NP * (G::A_BYTES + nw * BK * 2)));
                 for (int p = 0; p < NP; p++)
                     tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, (int)m0, p);
                 for (int q = 0; q < NP; q++)
-                    tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK, (int)n0, q);
+                    tma_load_3d(st + NP * G::A_BYTES + q * G::B_BYTES, nw == cs.wide() ? &mapBw : &mapBn,
+                                &full[s], (kb0 + kb) * BK, (int)n0, q);
                 issued = kb + 1;
             }
             if (*abort_flag) {
@@ -751,7 +778,7 @@ __global__ void __launch_bounds__(320, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            const uint32_t idesc = idesc_bf16(BM, nw);
             int committed = -1;              // last chunk whose accumulator was committed
             for (int kb = 0; kb < kblocks; kb++) {
                 const int c = kb / CH, b = c & 1;
@@ -798,7 +825,7 @@ __global__ void __launch_bounds__(320, 1)
         const int et = threadIdx.x - 64;            // 0..255
         for (int c = et; c < BN; c += 256) {
             const int64_t n = n0 + c;
-            coloff[c] = n < d.N ? grp_off(d.cn, n) : -1;
+            coloff[c] = (c < nw && n < d.N) ? grp_off(d.cn, n) : -1;
         }
         const int64_t m = m0 + q * 32 + lane;
         const bool mok = m < d.M;
@@ -842,7 +869,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                 for (int j = 0; j < HALF; j++) {
                     const int64_t n = n0 + h * HALF + j;
-                    if (n < d.N) P[n * d.M + m] = f32_to_f64_pow2(hi[j], 0, 0u) + f32_to_f64_pow2(lo[j], 0, 0u);
+                    if (h * HALF + j < nw && n < d.N) P[n * d.M + m] = f32_to_f64_pow2(hi[j], 0, 0u) + f32_to_f64_pow2(lo[j], 0, 0u);
                 }
             } else {
 #pragma unroll
@@ -911,8 +938,11 @@ static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const v
         attr = true;
     }
     if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mb, B, d.N, d.Kp, NP, BN)) return cudaErrorInvalidValue;
+    const ColSplit cs = col_split(d.N, BN);
+    CUtensorMap ma, mbw, mbn;
+    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mbw, B, d.N, d.Kp, NP, cs.wide()) ||
+        !make_map(&mbn, B, d.N, d.Kp, NP, 16 * cs.base))
+        return cudaErrorInvalidValue;
     const int64_t ntiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     const int kb_total = (int)(d.Kp / BK);
     const int sk = d.splitk > 1 ? d.splitk : 1;
@@ -921,7 +951,8 @@ static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const v
     if (zs > 1 && !partials) return cudaErrorInvalidValue;
     const int64_t total = ntiles * zs;
     const int grid = (int)(total < 148 ? total : 148);
-    tc_gemm_persistent_kernel<NP, BN, STAGES><<<grid, 320, G::SMEM, s>>>(ma, mb, d, C, partials, per, zs, ntiles, err);
+    tc_gemm_persistent_kernel<NP, BN, STAGES>
+        <<<grid, 320, G::SMEM, s>>>(ma, mbw, mbn, d, C, partials, per, zs, ntiles, cs, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || zs == 1) return e;
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
@@ -939,8 +970,11 @@ static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void
         attr = true;
     }
     if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mb, B, d.N, d.Kp, NP, BN)) return cudaErrorInvalidValue;
+    const ColSplit cs = col_split(d.N, BN);
+    CUtensorMap ma, mbw, mbn;
+    if (!make_map(&ma, A, d.M, d.Kp, NP, BM) || !make_map(&mbw, B, d.N, d.Kp, NP, cs.wide()) ||
+        !make_map(&mbn, B, d.N, d.Kp, NP, 16 * cs.base))
+        return cudaErrorInvalidValue;
     const int64_t tiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
     if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
     const int kb_total = (int)(d.Kp / BK);
@@ -950,7 +984,7 @@ static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void
     if (zs > 1 && !partials) return cudaErrorInvalidValue;
     if (zs > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)tiles, (unsigned)zs);
-    tc_gemm_chunked_kernel<NP, BN, STAGES, CH><<<grid, 320, G::SMEM, s>>>(ma, mb, d, C, partials, per, err);
+    tc_gemm_chunked_kernel<NP, BN, STAGES, CH><<<grid, 320, G::SMEM, s>>>(ma, mbw, mbn, d, C, partials, per, cs, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || zs == 1) return e;
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);

@@ -73,6 +73,43 @@ def test_split_gemm_statement(cc, prec, first, o, v, k):
     assert err <= 1e-3 * mag
 
 
+@pytest.mark.parametrize("prec,first", [("bf16x3", 3 * 2.0 ** -16), ("bf16x6", 3 * 2.0 ** -24)])
+@pytest.mark.parametrize("o", [23, 31, 16, 25])
+def test_ragged_column_tiles(cc, prec, first, o):
+    """The ladder statement with N = o^2 columns at every tile width the step
+    offers.  The ceil(N / BN) column tiles share N's 16-column units evenly, so
+    tiles of two widths meet inside the output and the last one may pass N by
+    up to 15 columns: N = 529 runs 192+176+176 at width 256, 3x112+2x96 at 128,
+    6x64+3x48 at 64; N = 961 runs 256+3x240, 5x128+3x112, 13x64+3x48; N = 256
+    runs full tiles; N = 625 runs 224+2x208, and 5x128 / 10x64 ending 15
+    columns past N.  M = v^2 = 144 leaves a 16-row last row tile and K = 144 a
+    ragged K block.  R2 starts as NaN, so a column no tile stores shows up."""
+    ccm, engine = cc
+    v = 12
+    text, kfun, nterms = STATEMENTS[0]
+    s, B, t1, t2 = small_case(o, v, 300 + o, L=8, scale=6.0, tscale=0.1)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
+    eng = engine.Engine(dsys, list_text=text, precision=prec, route_all=True)
+    steps = eng.plan.describe()["steps"]
+    k = next(i for i, st in enumerate(steps) if st["kind"] == "gemm_bf16split")
+    assert steps[k]["N"] == o * o and steps[k]["M"] == v * v
+    V = oracle_V(o, v, B)
+    e1, e2 = list_exec.run_list(text, o, v, s.eps, V, t1, t2)
+    kacc = kfun(o, v) if prec == "bf16x3" else min(kfun(o, v), 128)
+    tol = nterms * 0.5 * (first + kacc * 2.0 ** -24) * _abs_bound(text, o, v, s.eps, V, t1, t2) + 1e-15
+    widths = set()
+    for bn, sk, red in steps[k]["configs"]:
+        ccm.cc_plan_set_gemm_config(eng.plan, k, bn, sk, red)
+        r2 = torch.full((o, o, v, v), float("nan"), dtype=torch.float64, device=DEV)
+        r1 = torch.zeros(o, v, dtype=torch.float64, device=DEV)
+        ccm.cc_residual(eng.plan, dsys.ints(), to_dev(t1), to_dev(t2), r1, r2, eng.ws)
+        torch.cuda.synchronize()
+        err = np.abs(r2.cpu().numpy() - e2).max()      # a column the kernel skipped stays NaN
+        assert err <= tol, (bn, err, tol)
+        widths.add(bn)
+    assert {64, 128} <= widths
+
+
 @pytest.mark.parametrize("prec,rel", [("bf16x3", 2e-4), ("bf16x6", 1e-6)])
 @pytest.mark.parametrize("o,v", [(3, 8), (6, 30)])
 def test_mixed_full_residual_vs_oracle(cc, prec, rel, o, v):
