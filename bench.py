@@ -46,9 +46,11 @@ def workload_name(args):
     if args.dtype == "c128":
         return SMALL_C if args.small else WORKLOAD_C
     return SMALL if args.small else WORKLOAD
-# DRAM bytes / operand-plane bytes of the ladder kernel, from its ncu capture (None until re-captured
-# after a kernel change)
-TRAFFIC_RATIO = 1.052
+# DRAM bytes (read + write) of one launch of the o=40 v=200 ladder step in this benchmark's own
+# iteration, from a one-pass ncu capture of the current kernel version (set to None when the kernel
+# changes, until it is captured again): 11.06 GB read, mostly the <ab||ef> planes once and the tau
+# planes once per wave of 148 tiles, plus 0.49 GB written
+LADDER_TRAFFIC = 11.55e9
 
 
 def peaks():
@@ -340,6 +342,70 @@ def run_ccsdt(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+LADDER_TEXT = "R2[ijab] = 0.5 T2[ijef] * V[abef]"
+
+
+def run_ladder(args, world, rank, local):
+    """The particle ladder R2 = 1/2 sum_ef t_ij^ef <ab||ef> alone (Eq. 2's
+    o^2 v^4 term, one split-route GEMM step): the dominant kernel of the CCSD
+    iteration in isolation, at a size (--ladder-size o,v) where a profiler
+    capture of every metric ends quickly."""
+    import torch
+
+    import ccinputs
+    import paper_2409_06759_b300 as cc
+    from paper_2409_06759_b300.engine import DeviceSystem, Engine
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    o, v = (int(x) for x in args.ladder_size.split(","))
+    pk, pk_kind = peaks()
+    dsys = DeviceSystem.from_system(ccinputs.make_system(o=o, v=v, L=120, seed=0), device=dev)
+    eng = Engine(dsys, list_text=LADDER_TEXT, precision=args.precision)
+    a1, a2 = ccinputs.random_amplitudes(o, v, seed=0)
+    t1 = torch.tensor(a1, device=dev)
+    t2 = torch.tensor(a2, device=dev)
+    r1, r2 = torch.empty_like(t1), torch.empty_like(t2)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        eng.residual(t1, t2, r1, r2, stream=stream)
+    cc.cc_plan_profile_enable(eng.plan, True)
+    n0 = cc.cc_plan_launch_count(eng.plan)
+    torch.cuda.synchronize()
+    barrier(world)
+    with Clocks(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            eng.residual(t1, t2, r1, r2, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    dt = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    ms_step, ms_kernel, calls = cc.cc_plan_profile_read(eng.plan)
+    steps = eng.plan.describe()["steps"]
+    k = next(i for i, st in enumerate(steps) if st["kind"] == "gemm_bf16split")
+    st = steps[k]
+    t_k = ms_kernel[k] / calls / 1e3
+    tflop = st["products"] * 2.0 * st["M"] * st["N"] * st["K"]
+    ach = tflop / t_k / 1e12
+    value = world * eng.plan.flops * args.steps / dt / 1e12
+    line = {"metric": "particle-ladder contraction TFLOP/s on 1 B300", "value": value, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"{args.precision}: bf16 tensor-core products, fp32 accumulation, fp64 output",
+            "data": "synthetic",
+            "config": {"workload": f"particle ladder {LADDER_TEXT} o={o} v={v} L=120 seed=0",
+                       "gemm_shape": [st["M"], st["N"], st["K"]], "tile_width": st.get("bn"),
+                       "l2": "operands larger than L2 at o>=20 v>=100 (<ab||ef> planes >= 400 MB)"},
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": ach / pk["bf16_tflops"], "traffic": None,
+                         "kernel": "tc_gemm_persistent_kernel (" + st["note"] + ")", "ms_per_launch": t_k * 1e3,
+                         "peak_kind": f"{pk_kind} bf16 burst (tensor-pipe flops = {st['products']} products x 2MNK)"},
+            "gpu_launches": cc.cc_plan_launch_count(eng.plan) - n0, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 WORKLOAD_B = "batched CCSD: 64 systems, o ~ U[4,16], v ~ U[20,80], L=120, sub-seeds 0..63, FP64 real, synthetic"
 
 
@@ -456,15 +522,17 @@ def main():
                     "written by --save-tune instead of autotuning")
     ap.add_argument("--packed", action="store_true",
                     help="lists with packed index pairs (ladder over e<f; flops counted packed)")
-    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "ccsdt", "batched"],
-                    help="ccsdt: the o=8 v=64 CCSDT workload (generated list); batched: 64 uneven CCSD systems")
+    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "ccsdt", "batched", "ladder"],
+                    help="ccsdt: the o=8 v=64 CCSDT workload (generated list); batched: 64 uneven CCSD systems; "
+                         "ladder: the particle-ladder contraction alone (profiler captures)")
+    ap.add_argument("--ladder-size", default="20,100", help="o,v of --workload ladder")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.workload in ("ccsdt", "batched"):
-        (run_ccsdt if args.workload == "ccsdt" else run_batched)(args, world, rank, local)
+    if args.workload in ("ccsdt", "batched", "ladder"):
+        {"ccsdt": run_ccsdt, "batched": run_batched, "ladder": run_ladder}[args.workload](args, world, rank, local)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
@@ -560,11 +628,10 @@ def main():
         achieved = tflop / t_kernel / 1e12
         # the kernel runs ~10 ms inside a ~50 ms step: the burst figure is the denominator
         peak = pk["bf16_tflops"]
-        # DRAM bytes of one launch, from the ncu capture of this kernel version at o=20 v=100, scaled by
-        # the operand bytes that dominate it (profiles/tc_gemm_ladder_o20_v100.md); None until captured
+        # DRAM bytes of one launch, measured by ncu on this workload (None until captured)
         traffic = None
-        if not cplx and TRAFFIC_RATIO is not None and st["M"] == v * v and st["N"] == o * o and st["K"] == v * v:
-            traffic = TRAFFIC_RATIO * (st["M"] * st["Kp"] * 4 + st["N"] * st["Kp"] * 4) + st["M"] * st["N"] * 8
+        if not cplx and not args.small and not args.packed and st["M"] == v * v and st["N"] == o * o:
+            traffic = LADDER_TRAFFIC
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": "tc_gemm_persistent_kernel (" + st["note"] + ")",
