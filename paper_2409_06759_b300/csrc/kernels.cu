@@ -762,22 +762,62 @@ __global__ void __launch_bounds__(256) jacobi_dots_kernel(const JacobiSegs g, co
     double acc[M];
 #pragma unroll
     for (int h = 0; h < M; h++) acc[h] = 0.0;
+    const int64_t stride = (int64_t)kRedBlocks * 256;
     int64_t base = 0;
     for (int l = 0; l < g.nseg; l++) {
         const double *__restrict__ t = g.t[l];
         const double *__restrict__ r = g.r[l];
         const int64_t n = g.n[l];
-        for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)kRedBlocks * 256) {
-            const int64_t x = base + e;
-            const double q = r[e] * dinv[x];
-            eo[x] = q;
-            xo[x] = t[e] + q;
-            double hv[M];
+        if constexpr (M <= 4) {
+            // up to four overlaps: two elements per pass, every load of both
+            // issued before the stores (a history slot is not known not to alias
+            // the outputs, so the compiler would not move a later element's loads
+            // above them).  The per-thread order of the dot-product terms is the
+            // plain grid-stride order, as below.
+            for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += 2 * stride) {
+                const int64_t e1 = e + stride;
+                const bool two = e1 < n;
+                const int64_t x0 = base + e, x1 = base + e1;
+                const double r0 = r[e], d0 = dinv[x0], t0 = t[e];
+                const double r1 = two ? r[e1] : 0.0, d1 = two ? dinv[x1] : 0.0, t1 = two ? t[e1] : 0.0;
+                double h0[M], h1[M];
 #pragma unroll
-            for (int h = 0; h < M; h++) hv[h] = (h < g.m && g.he[h] != eo) ? g.he[h][x] : q;
+                for (int h = 0; h < M; h++) {
+                    // g.he[h] == eo: the slot the new error vector goes to (its overlap is q.q)
+                    const bool rd = h < g.m && g.he[h] != eo;
+                    h0[h] = rd ? g.he[h][x0] : 0.0;
+                    h1[h] = rd && two ? g.he[h][x1] : 0.0;
+                }
+                const double q0 = r0 * d0, q1 = r1 * d1;
+                eo[x0] = q0;
+                xo[x0] = t0 + q0;
+                if (two) {
+                    eo[x1] = q1;
+                    xo[x1] = t1 + q1;
+                }
 #pragma unroll
-            for (int h = 0; h < M; h++)
-                if (h < g.m) acc[h] = fma(q, hv[h], acc[h]);
+                for (int h = 0; h < M; h++)
+                    if (h < g.m) {
+                        const bool c = g.he[h] == eo;
+                        acc[h] = fma(q0, c ? q0 : h0[h], acc[h]);
+                        if (two) acc[h] = fma(q1, c ? q1 : h1[h], acc[h]);
+                    }
+            }
+        } else {
+            // more overlaps: one element per pass (the registers of a second
+            // element would cut the resident warps)
+            for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += stride) {
+                const int64_t x = base + e;
+                const double q = r[e] * dinv[x];
+                eo[x] = q;
+                xo[x] = t[e] + q;
+                double hv[M];
+#pragma unroll
+                for (int h = 0; h < M; h++) hv[h] = (h < g.m && g.he[h] != eo) ? g.he[h][x] : q;
+#pragma unroll
+                for (int h = 0; h < M; h++)
+                    if (h < g.m) acc[h] = fma(q, hv[h], acc[h]);
+            }
         }
         base += n;
     }
@@ -804,37 +844,42 @@ cudaError_t launch_dot_partials(const double *x, const double *y, int64_t n, dou
 }
 
 // E = sum_ijab <ij||ab> (t2_ijab / 4 + t1_ia t1_jb / 2), the spin-orbital
-// CC energy (the projection on Phi_0 of Eq. amp, Sec. II A).  Warps take rows (i, j, a) (a fixed mapping, so the
-// sum order is deterministic), lanes run along b; the row's t1_ia / 2 and the
-// t2 / 4 are exact scalings on the integer pipe, so an element costs two FMAs.
+// CC energy (the projection on Phi_0 of Eq. amp, Sec. II A), summed as
+// 1/4 sum V (t2 + 2 t1_ia t1_jb): the factor 4 is a power of two, so the
+// scaling commutes with every rounding (no subnormals) and is applied once per
+// block.  Warps take rows (i, j, a) (a fixed mapping, so the sum order is
+// deterministic), lanes run along b; the row's 2 t1_ia is formed once, so an
+// element costs two FMAs and the loop body holds only loads and FMAs (no call
+// that would keep the next iteration's loads from being issued early).
 template <typename T>
 __global__ void __launch_bounds__(256) energy_partials_kernel(int o, int v, const T *__restrict__ V,
                                                               const T *__restrict__ t1, const T *__restrict__ t2,
                                                               double *partials) {
-    const Scale half{0, -1, 0u, 0.5}, quarter{0, -2, 0u, 0.25};
     const int lane = threadIdx.x & 31;
     const uint32_t rows = (uint32_t)o * (uint32_t)o * (uint32_t)v;
     T s = zero<T>();
     for (uint32_t row = blockIdx.x * 8 + (threadIdx.x >> 5); row < rows; row += kRedBlocks * 8) {
         const uint32_t a = row % (uint32_t)v, ij = row / (uint32_t)v;
         const uint32_t j = ij % (uint32_t)o, i = ij / (uint32_t)o;
-        const int64_t base = (int64_t)row * v;
-        const T c = t1 ? scale_f64(t1[(int64_t)i * v + a], half) : zero<T>();
-        const T *t1j = t1 ? t1 + (int64_t)j * v : nullptr;
-        for (int b = lane; b < v; b += 32) {
-            T w = scale_f64(t2[base + b], quarter);
-            if (t1) w = cfma(c, t1j[b], w);
-            s = cfma(V[base + b], w, s);
+        const T *__restrict__ vr = V + (int64_t)row * v;
+        const T *__restrict__ tr = t2 + (int64_t)row * v;
+        if (t1) {
+            const T x = ld(t1 + (int64_t)i * v + a);
+            const T c = add(x, x);
+            const T *__restrict__ t1j = t1 + (int64_t)j * v;
+            for (int b = lane; b < v; b += 32) s = cfma(ld(vr + b), cfma(c, ld(t1j + b), ld(tr + b)), s);
+        } else {
+            for (int b = lane; b < v; b += 32) s = cfma(ld(vr + b), ld(tr + b), s);
         }
     }
     if constexpr (sizeof(T) == sizeof(double)) {
         const double r = block_sum(s);
-        if (threadIdx.x == 0) partials[blockIdx.x] = r;
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0.25 * r;
     } else {
         const double re = block_sum(s.x), im = block_sum(s.y);
         if (threadIdx.x == 0) {
-            partials[blockIdx.x] = re;
-            partials[kRedBlocks + blockIdx.x] = im;
+            partials[blockIdx.x] = 0.25 * re;
+            partials[kRedBlocks + blockIdx.x] = 0.25 * im;
         }
     }
 }
