@@ -333,12 +333,13 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
 
 // ------------------------------------------------------------------ tcgen05
 // Split-bf16 GEMM D = sum_products A_p B_q^T on the tensor cores.  One CTA per
-// SM (persistent) computes 128 x BN output tiles:
+// SM (persistent) computes output tiles of 128 rows by at most BN columns (the
+// column tiles share N evenly, in steps of 16):
 //   warp 0      TMA producer (one elected lane): all A and B planes of a
 //               64-wide K block land in one pipeline stage (SWIZZLE_128B)
 //   warp 1      TMEM allocator + MMA issuer (one lane): tcgen05.mma kind::f16,
 //               bf16 x bf16 -> fp32 accumulators of 128 lanes x BN columns
-//   warps 2..   epilogue: tcgen05.ld of the accumulator, alpha/beta update of
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator, alpha/beta update of
 //               the FP64 output through the mixed-radix addressing
 // Every mbarrier wait is bounded (clock64 budget); on expiry the CTA sets
 // err_flag, stops issuing work, waits (bounded) for what it already issued,
