@@ -3,6 +3,7 @@
 //                TTGT transpose fused into the precision split
 //   tc_gemm      tcgen05 GEMM over the plane products, FP32 accumulation in
 //                TMEM, FP64 epilogue into the output
+#include <atomic>
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -927,17 +928,27 @@ static bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t K
     return r == CUDA_SUCCESS;
 }
 
+// The dynamic shared-memory opt-in of a kernel holds per device: it is set once
+// on each device the kernel runs on (bit `dev` of *done; a device index past 63
+// sets it at every launch).  Setting it twice is harmless, so racing threads
+// need no lock.
+template <typename K>
+static cudaError_t smem_opt_in(K *kernel, int bytes, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    if (cudaError_t e = cudaGetDevice(&dev)) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    if (cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) return e;
+    done.fetch_or(bit, std::memory_order_relaxed);
+    return cudaSuccess;
+}
+
 template <int NP, int BN, int STAGES>
 static cudaError_t launch_persistent(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials,
                                      int *err, cudaStream_t s) {
     using G = Cfg<NP, BN, STAGES>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_persistent_kernel<NP, BN, STAGES>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> opted{0};
+    if (cudaError_t e = smem_opt_in(tc_gemm_persistent_kernel<NP, BN, STAGES>, G::SMEM, opted)) return e;
     if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
     const ColSplit cs = col_split(d.N, BN);
     CUtensorMap ma, mbw, mbn;
@@ -963,13 +974,8 @@ template <int NP, int BN, int STAGES, int CH>
 static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials,
                                   int *err, cudaStream_t s) {
     using G = Cfg<NP, BN, STAGES>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_chunked_kernel<NP, BN, STAGES, CH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> opted{0};
+    if (cudaError_t e = smem_opt_in(tc_gemm_chunked_kernel<NP, BN, STAGES, CH>, G::SMEM, opted)) return e;
     if (d.Mp % BM || d.Kp % BK || d.Mp < d.M) return cudaErrorInvalidValue;
     const ColSplit cs = col_split(d.N, BN);
     CUtensorMap ma, mbw, mbn;
