@@ -1291,7 +1291,8 @@ std::string describe_plan(const Plan &plan) {
                << ",\"candidates\":" << s.cands.size()
                << ",\"configs\":" << cands_json(s.cands)
                << ",\"sAm\":" << s.gemm.sAm << ",\"sAk\":" << s.gemm.sAk << ",\"sBk\":" << s.gemm.sBk
-               << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << s.gemm.alpha << ",\"beta\":" << s.gemm.beta
+               << ",\"sBn\":" << s.gemm.sBn << ",\"alpha\":" << (s.rows ? s.rg.alpha : s.gemm.alpha)
+               << ",\"beta\":" << (s.rows ? s.rg.beta : s.gemm.beta)
                << ",\"conj_a\":" << s.gemm.conj_a << ",\"conj_b\":" << s.gemm.conj_b << ",\"cm\":";
             grp_json(os, s.gemm.cm);
             os << ",\"cn\":";

@@ -190,3 +190,38 @@ def test_packed_pairs_reject_complex(cc):
 
 def test_wait_selftest_budget_checked_before_device_work(cc):
     assert cc.cc_selftest_wait_timeout(10) == 1          # CC_ERR_INVALID_ARG
+
+
+def test_autotune_candidates_and_config_replay(cc):
+    """Host-side candidate lists of the o=40 v=200 split-bf16 plan: every
+    tunable step offers its planned configuration; on the tensor route the
+    tile widths are 64/128/256; accumulating steps without split K also offer
+    the reduction epilogue; cc_plan_set_gemm_config takes exactly the listed
+    configurations and the description reports the one set."""
+    o, v = 40, 200
+    p = cc.cc_plan_create(cc.load_list("ccsd_vvvv"), o, v, precision="bf16x3")
+    steps = p.describe()["steps"]
+    tunable = [(k, s) for k, s in enumerate(steps) if s.get("configs")]
+    assert len(tunable) >= 10
+    reds = 0
+    for k, s in tunable:
+        cfgs = [tuple(c) for c in s["configs"]]
+        planned = (s.get("bn", 0), s["splitk"], s.get("red", 0))
+        assert planned in cfgs, (k, planned, cfgs)
+        assert len(set(cfgs)) == len(cfgs)
+        if s["kind"] == "gemm_bf16split":
+            assert {c[0] for c in cfgs} <= {64, 128, 256}
+        for bn, sk, red in cfgs:
+            if red:
+                assert sk == 1 and s["beta"] == 1, (k, s["note"])
+                reds += 1
+    assert reds > 0
+    k, s = next((k, s) for k, s in tunable if any(c[2] for c in s["configs"]))
+    bn, sk, red = next(c for c in s["configs"] if c[2])
+    cc.cc_plan_set_gemm_config(p, k, bn, sk, red)
+    got = p.describe()["steps"][k]
+    assert (got.get("bn", 0), got["splitk"], got.get("red", 0)) == (bn, sk, red)
+    with pytest.raises(RuntimeError):
+        cc.cc_plan_set_gemm_config(p, k, 96, 1, 0)
+    with pytest.raises(RuntimeError):
+        cc.cc_plan_set_gemm_config(p, len(steps), bn, sk, red)
