@@ -154,3 +154,35 @@ def test_triple_antisymmetrisers(cc, k, o, v):
     g3 = r3.cpu().numpy()
     scale = max(1.0, np.abs(e3).max())
     assert np.abs(g3 - e3).max() <= 8 * 4e-15 * scale
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+@pytest.mark.parametrize("o,v", [(3, 7), (5, 37)])
+def test_every_integral_orientation_copies_exactly(cc, o, v, complex_):
+    """R2[ijab] = V[p q r s] for all 24 orders of the letters i, j, a, b: each
+    resolves onto a stored block through <pq||rs> = -<qp||rs> = -<pq||sr> =
+    <rs||pq>* (a sign and, for complex orbitals, a conjugation), then a
+    permuted copy.  The device blocks are loaded with the oracle's own
+    integrals and T = 0, so the result must equal the einsum reading bit for
+    bit (signs, conjugations and copies are exact)."""
+    import itertools
+    ccm, engine = cc
+    s = ccinputs.make_system(o, v, L=6, seed=11, complex_=complex_)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, s.B, device=DEV)
+    V = oracle.antisym_integrals(o, v, s.B)
+    sl = {"o": slice(0, o), "v": slice(o, o + v)}
+    for name, blk in dsys.blocks.items():
+        sub = V[sl[name[0]], sl[name[1]], sl[name[2]], sl[name[3]]]
+        blk.copy_(torch.from_numpy(np.ascontiguousarray(sub).reshape(-1)).to(blk.dtype))
+    dt = torch.complex128 if complex_ else torch.float64
+    npdt = np.complex128 if complex_ else np.float64
+    T1 = torch.zeros(o, v, dtype=dt, device=DEV)
+    T2 = torch.zeros(o, o, v, v, dtype=dt, device=DEV)
+    z1, z2 = np.zeros((o, v), dtype=npdt), np.zeros((o, o, v, v), dtype=npdt)
+    for perm in itertools.permutations("ijab"):
+        text = "R2[ijab] = V[" + "".join(perm) + "]"
+        eng = engine.Engine(dsys, list_text=text, precision="fp64")
+        r1, r2 = eng.residual(T1, T2)
+        torch.cuda.synchronize()
+        _, e2 = list_exec.run_list(text, o, v, s.eps, V, z1, z2)
+        assert np.array_equal(r2.cpu().numpy(), e2), text
