@@ -225,3 +225,18 @@ def test_autotune_candidates_and_config_replay(cc):
         cc.cc_plan_set_gemm_config(p, k, 96, 1, 0)
     with pytest.raises(RuntimeError):
         cc.cc_plan_set_gemm_config(p, len(steps), bn, sk, red)
+
+
+@pytest.mark.parametrize("name", ["ccsd", "ccsd_vvvv", "ccsd_packed", "ccsdt"])
+def test_parser_round_trips_its_statements(cc, name):
+    """The planner's normalised rendering of each statement (factor, P(..)
+    operators, operands, packed-pair declarations) parses back to the same
+    plan: identical statements, steps and flop count."""
+    o, v = (4, 9) if name != "ccsdt" else (3, 5)
+    p = cc.cc_plan_create(cc.load_list(name), o, v, precision="fp64")
+    d = p.describe()
+    q = cc.cc_plan_create("\n".join(d["statements"]), o, v, precision="fp64")
+    e = q.describe()
+    assert e["statements"] == d["statements"]
+    assert e["steps"] == d["steps"]
+    assert q.flops == p.flops
