@@ -58,3 +58,45 @@ def test_split_rounding_matches_the_library_conversion(cc):
     nan = np.isnan(ref.cpu().numpy())
     assert np.array_equal(a[~nan], b[~nan])
     assert np.isnan(mine.cpu().numpy()[nan]).all()
+
+
+def _solver_case(engine, o=3, v=8):
+    s, B, t1, t2 = small_case(o, v, 5, L=6, scale=6.0, tscale=0.05)
+    dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
+    return engine.Engine(dsys, list_name="ccsd"), o, v
+
+
+def test_solve_reports_max_iterations_without_converging(cc):
+    """max_iter reached: CC_ERR_NOT_CONVERGED (7) with every iteration's finite
+    energy and |R| reported, and the amplitudes left at the last iterate."""
+    ccm, engine = cc
+    eng, o, v = _solver_case(engine)
+    t1 = torch.zeros(o, v, dtype=torch.float64, device=DEV)
+    t2 = torch.zeros(o, o, v, v, dtype=torch.float64, device=DEV)
+    res = engine.Solver(eng).solve(t1, t2, max_iter=3, tol=1e-300)
+    assert res.status == 7 and not res.converged and res.iterations == 3
+    assert "maximum iterations" in ccm.cc_last_error()
+    assert all(np.isfinite(res.rnorms)) and all(np.isfinite(res.energies))
+    assert res.rnorms[-1] < res.rnorms[0]
+    assert torch.isfinite(t2).all() and t2.abs().max().item() > 0
+
+
+def test_solve_stops_on_a_non_finite_residual(cc):
+    """A NaN placed in the starting amplitudes on the host (the injected fault)
+    makes |R| non-finite in the first iteration: cc_solve stops there with
+    CC_ERR_NOT_CONVERGED and says why, and the next solve on clean inputs in
+    the same context converges."""
+    ccm, engine = cc
+    eng, o, v = _solver_case(engine)
+    t1 = torch.zeros(o, v, dtype=torch.float64, device=DEV)
+    h2 = torch.zeros(o, o, v, v, dtype=torch.float64)
+    h2[0, 1, 2, 3] = float("nan")
+    t2 = h2.to(DEV)
+    res = engine.Solver(eng).solve(t1, t2, max_iter=20, tol=1e-8)
+    assert res.status == 7 and not res.converged and res.iterations == 1
+    assert "divergence" in ccm.cc_last_error()
+    assert not np.isfinite(res.rnorms[0])
+    t1.zero_()
+    t2.zero_()
+    ok = engine.Solver(eng).solve(t1, t2, max_iter=60, tol=1e-8)
+    assert ok.status == 0 and ok.converged
