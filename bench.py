@@ -630,7 +630,8 @@ def main():
         peak = pk["bf16_tflops"]
         # DRAM bytes of one launch, measured by ncu on this workload (None until captured)
         traffic = None
-        if not cplx and not args.small and not args.packed and st["M"] == v * v and st["N"] == o * o:
+        if (not cplx and not args.small and not args.packed and args.precision == "bf16x3"
+                and st["M"] == v * v and st["N"] == o * o):
             traffic = LADDER_TRAFFIC
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
