@@ -149,9 +149,10 @@ cudaError_t launch_unpack_t2(int o, int v, int cplx, const double *packed, doubl
 cudaError_t launch_unpack_pairs(const UnpackDesc &d, const double *C, double *out, cudaStream_t s);
 
 // Split an FP64 strided view X(r, k) (r, k mixed-radix groups) into nplanes
-// bf16 planes P_p[r][k] of a padded K-major matrix [Rp][Kp]:
+// bf16 planes P_p[r][k] of a K-major matrix [Rp][Kp]:
 //   hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); rows >= R and
-//   columns >= K are written as zeros.
+//   columns >= K are written as zeros.  The planner passes Rp = R: the
+//   tensor-core kernels read the rows past a plane as zeros through TMA.
 // Complex sources (gr, gk give complex-element offsets in doubles) enter the
 // real GEMM that carries a complex product C = A B (4M, one GEMM):
 //   cplx 1, stacked:  X(r, 2k + c) = component c of X(r, k)
@@ -169,8 +170,9 @@ struct SplitDesc {
 
 // Split-bf16 GEMM on tcgen05: D[m][n] = sum_{(p,q) in products} A_p[m][:] . B_q[n][:]
 // (fp32 in TMEM), then C(m,n) = alpha * D + beta * C(m,n) in FP64.
-// bn: N tile (64, 128 or 256); splitk > 1: each CTA covers one slice of the
-// K blocks and stores its raw fp32 tile (as double) to partials[z][n][m].
+// bn: N tile (64, 128 or 256; the ceil(N / bn) column tiles share N evenly);
+// splitk > 1: each CTA covers one slice of the K blocks and stores its raw
+// fp32 tile (as double) to partials[z][n][m].
 struct TcGemmDesc {
     int64_t M, N, Mp, Np, Kp;
     int nplanes_a, nplanes_b;
