@@ -1,7 +1,7 @@
 """FP64 CPU oracle for the spin-orbital CC residual (test infrastructure).
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
-may import this package.  It wraps ``cc_oracle.c`` (the CCSD equations, plain
+Only ``tests/``, ``__graft_entry__.smoke()``, ``bench.py``'s CPU legs and the
+cache writer ``oracle/cache_energies.py`` may import this package.  It wraps ``cc_oracle.c`` (the CCSD equations, plain
 C, explicit loops, OpenMP over outer loops) and ``cc_definition.c`` (residual
 elements of any rank up to triples straight from <Phi_l| exp(-T) H_N exp(T)
 |Phi_0>, no CC equations) through ctypes, both compiled for double and complex
@@ -12,11 +12,18 @@ Parity pins (all in ``tests/test_oracle_pins.py``):
   <Phi_l| exp(-T) H_N exp(T) |Phi_0> (Eq. amp), random T, tiny o/v;
 * converged CCSD energy vs FCI for two electrons;
 * first-iteration energy vs the MP2 closed form computed in determinant space;
-* antisymmetry of the residual; lambda-scaling of the energy.
+* antisymmetry of the residual; lambda-scaling of the energy: the lambda^2
+  coefficient is MP2 and the lambda^3 coefficient the MP3 closed form (itself
+  checked against determinant-space third-order perturbation theory).
 
-``ccsd_r2_sample`` evaluates selected residual elements of large systems from
-B directly (same equations); it is pinned against the brute force and the
-full residual at small sizes.
+``ccsd_r2_sample`` (and ``R2Sampler``, which builds the shared part once)
+evaluates selected residual elements of large systems from B directly (same
+equations); it is pinned against the brute force and the full residual at
+small sizes.
+
+``cc_blocks`` is the same CCSD in block form (numpy, one library contraction
+per term of the equations) for sizes the explicit loops cannot reach; its
+pins are in ``tests/test_oracle_blocks.py``.
 """
 from __future__ import annotations
 
@@ -81,6 +88,12 @@ def lib():
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
         L.orz_ccsd_r2_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp, vp, vp, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), vp]
+        for pre in ("orc", "orz"):
+            f = getattr(L, pre + "_ccsd_r2_sample_prepare")
+            f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp, vp, vp]
+            f.restype = vp
+            getattr(L, pre + "_ccsd_r2_sample_eval").argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
+            getattr(L, pre + "_ccsd_r2_sample_free").argtypes = [vp]
         _lib = L
     return _lib
 
@@ -164,6 +177,50 @@ def ccsd_r2_sample(o, v, B, eps, t1, t2, idx):
     if rc != 0:
         raise MemoryError("oracle sampled residual failed")
     return out
+
+
+class R2Sampler:
+    """Selected R2 elements of one (B, t1, t2), the shared part (integral
+    blocks oovv/ooov/ovvv, tau, tau~, one-particle intermediates) built once at
+    construction; ``eval(idx)`` evaluates the rows (i, j, a, b) of idx.  The
+    same arithmetic as ``ccsd_r2_sample``; use as a context manager."""
+
+    def __init__(self, o, v, B, eps, t1, t2):
+        self.cplx = _cplx(B, t1, t2)
+        dt = np.complex128 if self.cplx else np.float64
+        self._keep = [np.ascontiguousarray(B, dtype=dt), np.ascontiguousarray(eps, dtype=np.float64),
+                      np.ascontiguousarray(t1, dtype=dt), np.ascontiguousarray(t2, dtype=dt)]
+        B_, eps_, t1_, t2_ = self._keep
+        pre = "orz" if self.cplx else "orc"
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        self._eval = getattr(lib(), pre + "_ccsd_r2_sample_eval")
+        self._free = getattr(lib(), pre + "_ccsd_r2_sample_free")
+        self.h = getattr(lib(), pre + "_ccsd_r2_sample_prepare")(o, v, B_.shape[0], vp(B_), _p(eps_), vp(t1_),
+                                                                   vp(t2_))
+        if not self.h:
+            raise MemoryError("oracle sampled residual: prepare failed")
+
+    def eval(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 4)
+        out = np.empty(idx.shape[0], dtype=np.complex128 if self.cplx else np.float64)
+        if self._eval(self.h, idx.shape[0], idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      ctypes.c_void_p(out.ctypes.data)) != 0:
+            raise RuntimeError("oracle sampled residual failed")
+        return out
+
+    def close(self):
+        if self.h:
+            self._free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        self.close()
 
 
 def ccsd_energy(o, v, V, t1, t2):

@@ -538,10 +538,32 @@ static sc ring_x(const vsrc *Sp, const sc *t1, const sc *t2, int p, int q, int c
     return x;
 }
 
-int FN(ccsd_r2_sample)(int o, int v, int L, const sc *B, const double *eps, const sc *t1,
-                       const sc *t2, int ns, const int *idx, sc *out)
+/* What the per-element evaluation reads: the integral source, tau, tau~ and the
+ * one-particle intermediates, built once per (B, t1, t2). */
+typedef struct {
+    vsrc S;
+    const double *eps;
+    const sc *t1, *t2;
+    sc *Bt, *tau, *taut, *Fae, *Fmi, *Fme, *Fbe2, *Fmj2;
+} FN(r2s);
+
+void FN(ccsd_r2_sample_free)(void *h)
+{
+    FN(r2s) *R = (FN(r2s) *)h;
+    if (!R) return;
+    free(R->Bt); free(R->S.oovv); free(R->S.ooov); free(R->S.ovvv); free(R->tau); free(R->taut);
+    free(R->Fae); free(R->Fmi); free(R->Fme); free(R->Fbe2); free(R->Fmj2);
+    free(R);
+}
+
+/* Builds the shared part; eps, t1, t2 are kept by pointer and must outlive the
+ * handle.  Returns NULL when an allocation fails. */
+void *FN(ccsd_r2_sample_prepare)(int o, int v, int L, const sc *B, const double *eps, const sc *t1,
+                                 const sc *t2)
 {
     const ll n = o + v;
+    FN(r2s) *R = calloc(1, sizeof(FN(r2s)));
+    if (!R) return NULL;
     vsrc S;
     S.o = o; S.v = v; S.n = (int)n; S.L = L;
     sc *Bt = malloc(sizeof(sc) * n * n * L);
@@ -552,7 +574,12 @@ int FN(ccsd_r2_sample)(int o, int v, int L, const sc *B, const double *eps, cons
     sc *Fae = malloc(sizeof(sc) * v * v), *Fmi = malloc(sizeof(sc) * o * o);
     sc *Fme = malloc(sizeof(sc) * o * v), *Fbe2 = malloc(sizeof(sc) * v * v);
     sc *Fmj2 = malloc(sizeof(sc) * o * o);
-    if (!Bt || !S.oovv || !S.ooov || !S.ovvv || !tau || !taut || !Fae || !Fmi || !Fme || !Fbe2 || !Fmj2) return 1;
+    R->Bt = Bt; R->S = S; R->tau = tau; R->taut = taut; R->Fae = Fae; R->Fmi = Fmi; R->Fme = Fme;
+    R->Fbe2 = Fbe2; R->Fmj2 = Fmj2; R->eps = eps; R->t1 = t1; R->t2 = t2;
+    if (!Bt || !S.oovv || !S.ooov || !S.ovvv || !tau || !taut || !Fae || !Fmi || !Fme || !Fbe2 || !Fmj2) {
+        FN(ccsd_r2_sample_free)(R);
+        return NULL;
+    }
 #pragma omp parallel for
     for (ll pr = 0; pr < n * n; pr++)
         for (int l = 0; l < L; l++) Bt[pr * L + l] = B[(ll)l * n * n + pr];
@@ -618,6 +645,19 @@ int FN(ccsd_r2_sample)(int o, int v, int L, const sc *B, const double *eps, cons
             for (int e = 0; e < v; e++) s += 0.5 * T1(j, e) * Fme[m * v + e];
             Fmj2[m * o + j] = s;
         }
+    R->S = S;
+    return R;
+}
+
+/* R_ij^ab for each row (i, j, a, b) of idx[ns][4], from a prepared handle. */
+int FN(ccsd_r2_sample_eval)(void *h, int ns, const int *idx, sc *out)
+{
+    const FN(r2s) *R = (const FN(r2s) *)h;
+    if (!R) return 1;
+    const vsrc S = R->S;
+    const int o = S.o, v = S.v;
+    const double *eps = R->eps;
+    const sc *t1 = R->t1, *t2 = R->t2, *tau = R->tau, *Fbe2 = R->Fbe2, *Fmj2 = R->Fmj2;
 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < ns; k++) {
@@ -654,7 +694,15 @@ int FN(ccsd_r2_sample)(int o, int v, int L, const sc *B, const double *eps, cons
             r -= T1(m, a) * vint(&S, m, o + b, i, j) - T1(m, b) * vint(&S, m, o + a, i, j);
         out[k] = r;
     }
-    free(Bt); free(S.oovv); free(S.ooov); free(S.ovvv); free(tau); free(taut);
-    free(Fae); free(Fmi); free(Fme); free(Fbe2); free(Fmj2);
     return 0;
+}
+
+int FN(ccsd_r2_sample)(int o, int v, int L, const sc *B, const double *eps, const sc *t1,
+                       const sc *t2, int ns, const int *idx, sc *out)
+{
+    void *h = FN(ccsd_r2_sample_prepare)(o, v, L, B, eps, t1, t2);
+    if (!h) return 1;
+    int rc = FN(ccsd_r2_sample_eval)(h, ns, idx, out);
+    FN(ccsd_r2_sample_free)(h);
+    return rc;
 }

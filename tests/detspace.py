@@ -216,3 +216,36 @@ def mp2_det_space(o, v, eps, V):
         ed = sum(eps[p] for p in range(ds.n) if (d >> p) & 1)
         tot += abs(H[k, c0]) ** 2 / (e0 - ed)
     return tot
+
+
+def mp3_det_space(o, v, eps, V):
+    """Third-order Moller-Plesset energy from determinant-space H elements:
+    Rayleigh-Schroedinger E3 = <Psi1| (W - E1) |Psi1> with H0 = sum_p eps_p a+_p a_p,
+    W = H - H0, E1 = <Phi_0|W|Phi_0> and Psi1 = sum_K |K> <K|W|Phi_0> / (E0_0 - E0_K)."""
+    ds = DetSpace(o, v)
+    h, _ = one_body_from_fock(eps, V, o)
+    H = ds.hamiltonian(h, V)
+    e0 = np.array([sum(eps[p] for p in range(ds.n) if (d >> p) & 1) for d in ds.dets])
+    W = H - np.diag(e0)
+    c0 = ds.index[ds.ref]
+    denom = e0[c0] - e0
+    denom[c0] = 1.0
+    psi1 = W[:, c0] / denom
+    psi1[c0] = 0.0
+    e1 = W[c0, c0]
+    return np.vdot(psi1, (W - e1 * np.eye(ds.dim)) @ psi1)
+
+
+def mp3_closed_form(o, v, eps, V):
+    """Spin-orbital MP3 energy with unrestricted sums and D_ij^ab = e_i + e_j - e_a - e_b:
+    1/8 sum <ij||ab><ab||cd><cd||ij>/(D_ij^ab D_ij^cd)   (particle ladder)
+    + 1/8 sum <ij||ab><kl||ij><ab||kl>/(D_ij^ab D_kl^ab) (hole ladder)
+    + sum <ij||ab><kb||cj><ac||ik>/(D_ij^ab D_ik^ac)     (ring)."""
+    eo, ev = eps[:o], eps[o:]
+    D = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    oovv, vvvv, oooo = V[:o, :o, o:, o:], V[o:, o:, o:, o:], V[:o, :o, :o, :o]
+    ovvo, vvoo = V[:o, o:, o:, :o], V[o:, o:, :o, :o]
+    w = oovv / D
+    t = vvoo.transpose(2, 3, 0, 1) / D
+    return (0.125 * np.einsum("ijab,abcd,ijcd->", w, vvvv, t) + 0.125 * np.einsum("ijab,klij,klab->", w, oooo, t)
+            + np.einsum("ijab,kbcj,ikac->", w, ovvo, t))

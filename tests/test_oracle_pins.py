@@ -7,7 +7,9 @@
   second-order Moller-Plesset perturbation theory on determinant-space H elements;
 * antisymmetry of R2 in (ij) and (ab); integral symmetries;
 * DIIS coefficients vs the closed form c = B^-1 1 / (1^T B^-1 1);
-* lambda scaling: E(lambda V) = lambda^2 E2 + O(lambda^3), E2 the MP2 energy.
+* lambda scaling: E(lambda V) = lambda^2 E2 + lambda^3 E3 + O(lambda^4), E2 the MP2
+  energy and E3 the spin-orbital MP3 closed form (itself checked against
+  third-order perturbation theory in determinant space).
 """
 import numpy as np
 import pytest
@@ -93,20 +95,42 @@ def test_diis_coefficients_closed_form(m):
     assert abs(c.sum() - 1.0) < 1e-13
 
 
-def test_energy_lambda_scaling_leading_order_is_mp2():
-    o, v = 2, 4
-    s, B = _system(o, v, 41)
-    V = oracle.antisym_integrals(o, v, B)
-    e2 = detspace.mp2_det_space(o, v, s.eps, V)
-    lam = np.array([0.02, 0.04, 0.08])
-    es = []
-    for x in lam:
-        res = oracle.ccsd_solve(o, v, s.eps, V * x, tol=1e-13, maxiter=100)
-        es.append(res["energy"])
-    # E(l) = l^2 E2 + l^3 E3 + l^4 E4 + ...: fit the first three coefficients
-    A = np.stack([lam ** 2, lam ** 3, lam ** 4], 1)
-    coef = np.linalg.solve(A, np.array(es))
-    assert abs(coef[0] - e2) < 1e-6 * abs(e2) + 1e-12
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 61), (2, 4, 62), (3, 5, 63)])
+def test_mp3_closed_form_equals_third_order_perturbation_theory(cplx, o, v, seed):
+    """The MP3 closed form used by the lambda pin, against Rayleigh-Schroedinger
+    third order on the determinant-space Hamiltonian (no closed form involved)."""
+    s = ccinputs.make_system(o, v, L=6, seed=seed, complex_=cplx)
+    V = oracle.antisym_integrals(o, v, s.B * 6.0)
+    e3 = detspace.mp3_closed_form(o, v, s.eps, V)
+    assert abs(e3 - detspace.mp3_det_space(o, v, s.eps, V)) < 1e-13 * max(1.0, abs(e3))
+
+
+def lambda_coefficients(solve, lam):
+    """Coefficients of E(l) = sum_k l^k E_k, k = 2 .. 1 + len(lam), fitted exactly
+    through the converged energies at the given scales of the integrals."""
+    lam = np.asarray(lam, dtype=float)
+    A = np.stack([lam ** k for k in range(2, 2 + lam.size)], 1)
+    return np.linalg.solve(A, np.array([solve(x) for x in lam]))
+
+
+LAMBDAS = [0.01, 0.02, 0.03, 0.04, 0.05]
+
+
+@pytest.mark.parametrize("o,v,seed,L", [(2, 4, 41, 6), (3, 8, 42, 6), (5, 16, 43, 12)])
+def test_energy_lambda_expansion_is_mp2_then_mp3(o, v, seed, L):
+    """E_CCSD(lambda V) = lambda^2 E_MP2 + lambda^3 E_MP3 + O(lambda^4): CCSD is
+    exact through third order, so the lambda^3 coefficient pins the first-order
+    T2 response of the particle ladder, the hole ladder and the ring terms."""
+    s = ccinputs.make_system(o, v, L=L, seed=seed)
+    V = oracle.antisym_integrals(o, v, s.B * 6.0)
+    c = lambda_coefficients(lambda x: oracle.ccsd_solve(o, v, s.eps, V * x, tol=1e-15, maxiter=200)["energy"],
+                            LAMBDAS)
+    e2 = detspace.mp2_det_space(o, v, s.eps, V) if o + v <= 8 else None
+    e3 = detspace.mp3_closed_form(o, v, s.eps, V)
+    if e2 is not None:
+        assert abs(c[0] - e2) < 1e-10 * abs(e2)
+    assert abs(c[1] - e3) < 1e-7 * abs(e3)
 
 
 @pytest.mark.parametrize("o,v,seed", [(2, 3, 51), (3, 5, 52), (4, 4, 53)])
@@ -223,3 +247,19 @@ def test_definition_oracle_agrees_with_the_ccsd_equations(cplx):
     idx1 = np.stack([rng.integers(0, o, 4), rng.integers(0, v, 4)], 1)
     got1 = oracle.cc_definition_elements(o, v, B, s.eps, t1, t2, None, rank=1, idx=idx1)
     assert np.abs(got1 - r1[tuple(idx1.T)]).max() < 1e-12
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_prepared_sampler_equals_one_shot_sampling(cplx):
+    """The prepared sampled-element oracle (shared part built once) returns what
+    the one-shot routine returns, bit for bit, over several evaluations."""
+    o, v = 3, 5
+    s = ccinputs.make_system(o, v, L=6, seed=57, complex_=cplx)
+    t1, t2 = ccinputs.random_amplitudes(o, v, seed=57, scale1=0.1, scale2=0.1, complex_=cplx)
+    idx = np.array([[0, 1, 0, 1], [2, 0, 4, 3], [1, 2, 3, 0], [1, 1, 2, 3]])
+    want = oracle.ccsd_r2_sample(o, v, s.B, s.eps, t1, t2, idx)
+    with oracle.R2Sampler(o, v, s.B, s.eps, t1, t2) as smp:
+        for _ in range(2):
+            got = smp.eval(idx)
+            assert np.array_equal(got, want)
+        assert np.array_equal(smp.eval(idx[1:3]), want[1:3])
