@@ -119,6 +119,9 @@ typedef struct {
 } cc_plan_opts;
 
 /* cc_plan_create -- parse a contraction list and plan its execution.
+ * Defined by: Sec. II C (the residual as an ordered list of binary
+ * "Contraction" objects, their text form in Fig. representations) and
+ * Sec. I C (each contraction executed transpose-transpose-GEMM-transpose).
  *   text: one statement per line, '#' starts a comment:
  *       OUT[idx]..  (=|+=|-=)  [factor] [P(pq)|P(p/qr)]...  A[idx].. [* B[idx]..]
  *     Index letters i..n (or h1, h2, ...) are occupied, a..h (or p1, p2, ...)
@@ -169,6 +172,8 @@ CC_API cc_status cc_plan_profile_read(cc_plan plan, double *ms_step, double *ms_
 CC_API cc_status cc_plan_launch_count(cc_plan plan, long long *count);
 
 /* cc_residual -- evaluate R1, R2 (, R3) for the given amplitudes.
+ * Defined by: Sec. II A, Eq. amp (R_l = <Phi_l| exp(-T) H_N exp(T) |Phi_0>,
+ * projected on singles, doubles and triples), with H_N of Eq. ham2q.
  *   ints, amps: inputs (device, unchanged).  res: outputs (device), fully
  *   overwritten.  ws: device workspace of at least cc_plan_workspace_bytes.
  * Ownership: nothing is retained after the call returns. */
@@ -199,7 +204,8 @@ CC_API cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const 
 CC_API cc_status cc_plan_set_gemm_config(cc_plan plan, int step, int bn, int splitk, int red);
 
 /* cc_energy -- E_CC - E_ref = 1/4 sum <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b
- * (f_ia = 0).  e_dev: device double[2] receiving (Re E, Im E) (Im E = 0 for
+ * (f_ia = 0).  Defined by: Sec. II A, Eq. amp (the Phi_0 projection of
+ * exp(-T) H_N exp(T)).  e_dev: device double[2] receiving (Re E, Im E) (Im E = 0 for
  * CC_F64).  Uses the first 10 KiB of ws as scratch. */
 CC_API cc_status cc_energy(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, double *e_dev,
                            void *ws, size_t ws_bytes, void *stream);
@@ -231,7 +237,10 @@ typedef struct {
  * residual buffers (and the refine plan's workspace when given). */
 CC_API cc_status cc_solve_workspace_bytes(cc_plan plan, const cc_solve_opts *opts, size_t *bytes);
 
-/* cc_solve -- Jacobi + DIIS on x = (t1, t2[, t3]).  Iteration k evaluates
+/* cc_solve -- Jacobi + DIIS on x = (t1, t2[, t3]).  Solves the equations of
+ * Sec. II A, Eq. amp; the paper leaves the iteration to DIRAC-ExaCorr and
+ * reports only "the norm of the residual vector" (Tables h2o/lih), so the
+ * Jacobi + Pulay DIIS reading below is this library's.  Iteration k evaluates
  * R_k = R(x_k), E_k = E(x_k) and |R_k|_2 (Frobenius norm over the full stored
  * residual arrays) and stops when |R_k| < tol; otherwise x'_{k+1} = x_k + R_k/D,
  * e_k = R_k/D, the last diis_max pairs (x', e) are kept and, once two are
@@ -277,7 +286,8 @@ CC_API cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integral
                                   const cc_solve_opts *opts, cc_solve_report *reports, void *ws, size_t ws_bytes,
                                   void *stream);
 
-/* Integral construction (setup step):  (pq|rs) = sum_L B[L][p][q] B[L][r][s]
+/* Integral construction (setup step; the antisymmetrised integrals of Eq.
+ * ham2q, Sec. III B):  (pq|rs) = sum_L B[L][p][q] B[L][r][s]
  * and <pq||rs> = (pr|qs) - (ps|qr) for the six canonical blocks (Eq. ham2q).
  *   B: device [L][n][n] (n = o + v, occupied first), double or complex
  *   double (dtype); complex B gives <pq||rs> = sum_L B_pr B_qs - B_ps B_qr
@@ -313,24 +323,29 @@ CC_API int64_t cc_packed_t2_elems(int o, int v);
 CC_API cc_status cc_pack_t2(int o, int v, cc_dtype dtype, const void *t_full, void *t_packed, void *stream);
 CC_API cc_status cc_unpack_t2(int o, int v, cc_dtype dtype, const void *t_packed, void *t_full, void *stream);
 
-/* cc_energy_noalloc -- the same energy as cc_energy, for callers that cannot
- * allocate device memory: code running under a host application that owns the
- * device heap, or in a region where a cudaMalloc would be refused or would
- * synchronise the device.  The paper has no counterpart; it is a convenience
- * of this library.  The block partial sums live in a fixed device array of
- * the library (32 KiB, 4096 partials of 16384 elements each), held on every
- * GPU that loads the library until the process exits; nothing is allocated
- * and no workspace is taken.
+/* cc_energy_noalloc -- the energy of cc_energy (E_CC - E_ref = 1/4 sum
+ * <ij||ab> t_ij^ab + 1/2 sum <ij||ab> t_i^a t_j^b, FP64 or complex128) for
+ * callers that cannot allocate device memory: code running under a host
+ * application that owns the device heap, or in a region where a cudaMalloc
+ * would be refused or would synchronise the device.  The paper has no
+ * counterpart; it is a convenience of this library.  The block partial sums
+ * live in a fixed device array of the library (64 KiB: 4096 real and 4096
+ * imaginary partials, each covering 16384 elements), held on every GPU that
+ * loads the library until the process exits; nothing is allocated and no
+ * workspace is taken.
  *   o, v: extents; o^2 v^2 must not exceed 67,108,864, otherwise the call
  *   returns CC_ERR_INVALID_ARG before touching any pointer.
+ *   dtype: CC_F64 (double tensors) or CC_C128 (interleaved complex double);
+ *   it says how ints->oovv, amps->t1 and amps->t2 are read.
  *   ints->oovv, amps->t2 (and amps->t1, may be NULL): device inputs.
- *   e_dev: device double[2] receiving (E, 0).
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
+ *   e_dev: device double[2] receiving (Re E, Im E) (Im E = 0 for CC_F64).
+ * The array's device address is looked up on every call with the caller's
+ * device current; the first call on a device may load the library's device
+ * code there, so make that first call before any stream capture.  All calls
  * share the one array and it keeps the last call's partials: calls that
  * overlap on the GPU (different streams or threads, same device) race. */
-CC_API cc_status cc_energy_noalloc(int o, int v, const cc_integrals *ints, const cc_amps *amps, double *e_dev,
-                                   void *stream);
+CC_API cc_status cc_energy_noalloc(int o, int v, cc_dtype dtype, const cc_integrals *ints, const cc_amps *amps,
+                                   double *e_dev, void *stream);
 
 /* cc_selftest_wait_timeout -- checks the bounded-wait mechanism of the
  * tensor-core kernels on this device: one CTA waits, with the kernels' own

@@ -94,7 +94,7 @@ _sig = {
     "cc_build_integrals_workspace_bytes": (c_int, [c_int, c_int, c_int, c_int, _P(c_size_t)]),
     "cc_build_integrals": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
-    "cc_energy_noalloc": (c_int, [c_int, c_int, _P(cc_integrals), _P(cc_amps), c_void_p, c_void_p]),
+    "cc_energy_noalloc": (c_int, [c_int, c_int, c_int, _P(cc_integrals), _P(cc_amps), c_void_p, c_void_p]),
     "cc_solve_batched_workspace_bytes": (c_int, [c_int, _P(c_void_p), _P(cc_solve_opts), _P(c_size_t)]),
     "cc_solve_batched": (c_int, [c_int, _P(c_void_p), _P(cc_integrals), _P(cc_amps), _P(cc_solve_opts),
                                  _P(cc_solve_report), c_void_p, c_size_t, c_void_p]),
@@ -281,11 +281,14 @@ def cc_energy(plan: Plan, ints: dict, t1, t2, e_dev, ws, stream=None):
                           _stream(stream)), "cc_energy")
 
 
-def cc_energy_noalloc(o: int, v: int, ints: dict, t1, t2, e_dev, stream=None):
-    """cc_energy without a workspace, for callers that cannot allocate (see include/cc.h)."""
+def cc_energy_noalloc(o: int, v: int, ints: dict, t1, t2, e_dev, stream=None, dtype=None):
+    """cc_energy without a workspace, for callers that cannot allocate (see
+    include/cc.h).  dtype: CC_F64 / CC_C128; by default that of t2."""
+    if dtype is None:
+        dtype = CC_C128 if getattr(t2, "is_complex", lambda: False)() else CC_F64
     I = integrals_struct(ints)
     A = cc_amps(_ptr(t1), _ptr(t2), None)
-    _check(_lib.cc_energy_noalloc(o, v, ctypes.byref(I), ctypes.byref(A), _ptr(e_dev), _stream(stream)),
+    _check(_lib.cc_energy_noalloc(o, v, dtype, ctypes.byref(I), ctypes.byref(A), _ptr(e_dev), _stream(stream)),
            "cc_energy_noalloc")
 
 

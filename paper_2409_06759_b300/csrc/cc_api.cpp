@@ -627,9 +627,10 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
         S = SolverState();
         CC_CUDA(cudaMemsetAsync(used_dev, 0, 16, s));
     }
-    // pinned host staging for the per-iteration scalars (one per thread)
-    static thread_local double *h_scal = nullptr;
-    if (!h_scal) CC_CUDA(cudaMallocHost(&h_scal, 128));
+    // host staging for the per-iteration scalars (E, |R|, DIIS bookkeeping):
+    // 56 bytes read once per iteration right before the stream synchronisation,
+    // so plain stack memory serves (no host or device allocation in the call)
+    alignas(16) double h_scal[16] = {};
     if (report) { report->iterations = 0; report->converged = 0; report->switched_at = -1; }
     const int cplx = P.dtype == CC_C128;
     // the static caches (permuted and split integral blocks) are rebuilt at the

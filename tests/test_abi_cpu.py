@@ -240,3 +240,13 @@ def test_parser_round_trips_its_statements(cc, name):
     assert e["statements"] == d["statements"]
     assert e["steps"] == d["steps"]
     assert q.flops == p.flops
+
+
+def test_bench_flop_constants_match_the_plans(cc):
+    """bench.py records the timed plan's flops so that its reference arm never
+    loads this library; they must equal cc_plan_flops."""
+    import bench
+    for (name, o, v, dt), flops in bench.PLAN_FLOPS.items():
+        p = cc.cc_plan_create(cc.load_list(name), o, v, dtype=cc.CC_C128 if dt == "c128" else cc.CC_F64,
+                              precision=cc.CC_PREC_BF16X3)
+        assert p.flops == flops, (name, o, v, dt)

@@ -13,7 +13,7 @@ import ccinputs
 import detspace
 import list_exec
 import oracle
-from gpu_util import DEV
+from gpu_util import DEV, assert_elementwise, list_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -106,16 +106,37 @@ def test_ccsdt_three_electrons_equals_fci(cc):
     assert np.abs(r3).max() < 1e-8
 
 
+def _reference_with_bounds(ccm, o, v, s, B, t1, t2, t3, plans, n_def=40, seed=0):
+    """The einsum reading of the CCSDT list (values and the element-wise bound of
+    each plan's routes), itself checked on sampled elements against the
+    definition oracle, which shares nothing with the list."""
+    V = oracle.antisym_integrals(o, v, B)
+    vals, bounds = list_bounds(ccm.load_list("ccsdt"), o, v, s.eps, V, t1, t2, plans, t3=t3)
+    rng = np.random.default_rng(seed)
+    idx3 = np.concatenate([rng.integers(0, o, (n_def, 3)), rng.integers(0, v, (n_def, 3))], 1)
+    want = oracle.cc_definition_elements(o, v, B, s.eps, t1, t2, t3, rank=3, idx=idx3)
+    assert np.abs(vals[2][tuple(idx3.T)] - want).max() < 1e-12 * max(1.0, np.abs(want).max())
+    return vals, bounds
+
+
 @pytest.mark.parametrize("prec,rel", [("bf16x3", 1e-4), ("bf16x6", 1e-6)])
-def test_ccsdt_split_route_matches_fp64(cc, prec, rel):
-    _, engine = cc
+def test_ccsdt_split_route_matches_reference(cc, prec, rel):
+    """Every R1, R2, R3 element of the all-tensor-core route within the
+    element-wise bound of its routes; the FP64 route within 1e-9; the error
+    norm against the FP64 route as an extra check."""
+    ccm, engine = cc
     o, v = 4, 20
     s, B, t1, t2, t3 = case(o, v, 4, L=8, tscale=0.05)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
     T = (dev(t1), dev(t2), dev(t3))
-    f = engine.Engine(dsys, list_name="ccsdt").residual(T[0], T[1], t3=T[2])
-    m = engine.Engine(dsys, list_name="ccsdt", precision=prec, route_all=True).residual(T[0], T[1], t3=T[2])
+    fe = engine.Engine(dsys, list_name="ccsdt")
+    me = engine.Engine(dsys, list_name="ccsdt", precision=prec, route_all=True)
+    f = fe.residual(T[0], T[1], t3=T[2])
+    m = me.residual(T[0], T[1], t3=T[2])
     torch.cuda.synchronize()
+    vals, [bound] = _reference_with_bounds(ccm, o, v, s, B, t1, t2, t3, [me.plan])
+    assert_elementwise(m, vals, bound, what=f"ccsdt {prec}")
+    assert_elementwise(f, vals, [np.full(x.shape, 1e-9) for x in vals], slack=1e-12, what="ccsdt fp64")
     d = np.sqrt(sum(((a - b).cpu().numpy() ** 2).sum() for a, b in zip(f, m)))
     n = np.sqrt(sum((a.cpu().numpy() ** 2).sum() for a in f))
     assert d <= rel * n, (d, n)
@@ -150,12 +171,13 @@ def test_ccsdt_full_size_sampled_elements(cc):
     assert np.abs(g + g.transpose(0, 1, 2, 4, 3, 5)).max() <= 1e-13 * scale
 
 
-def test_ccsdt_default_mixed_plan_matches_fp64(cc):
+def test_ccsdt_default_mixed_plan_matches_reference(cc):
     """The bench's mixed plan (tensor-core route for the contractions that fill
-    128 x bn x 64 tiles, FP32 arithmetic for the skinny rank-o updates of T3)
-    against the FP64 plan, o=8 v=40."""
-    _, engine = cc
-    o, v = 8, 40
+    128 x bn x 64 tiles, FP32 arithmetic for the skinny rank-o updates of T3),
+    o=6 v=36: every element within the element-wise bound of its routes, and
+    the error norm against the FP64 plan as an extra check."""
+    ccm, engine = cc
+    o, v = 6, 36
     s, B, t1, t2, t3 = case(o, v, 5, L=16, scale=1.0, tscale=0.01)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
     T = (dev(t1), dev(t2), dev(t3))
@@ -163,8 +185,10 @@ def test_ccsdt_default_mixed_plan_matches_fp64(cc):
     f = [x.cpu() for x in f]
     mixed = engine.Engine(dsys, list_name="ccsdt", precision="bf16x3")
     kinds = {st["kind"] for st in mixed.plan.describe()["steps"]}
-    assert {"gemm_f32", "gemm_bf16split"} <= kinds
+    assert "gemm_bf16split" in kinds and kinds & {"gemm_f32", "gemm_rows_f32"}
     m = [x.cpu() for x in mixed.residual(T[0], T[1], t3=T[2])]
+    vals, [bound] = _reference_with_bounds(ccm, o, v, s, B, t1, t2, t3, [mixed.plan], n_def=12)
+    assert_elementwise(m, vals, bound, what="ccsdt default mixed plan")
     d = np.sqrt(sum(((a - b).numpy() ** 2).sum() for a, b in zip(f, m)))
     n = np.sqrt(sum((a.numpy() ** 2).sum() for a in f))
     assert d <= 1e-4 * n, (d, n)

@@ -16,7 +16,7 @@ import torch
 import ccinputs
 import list_exec
 import oracle
-from gpu_util import DEV, block_slices
+from gpu_util import DEV, assert_elementwise, block_slices, list_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -147,15 +147,21 @@ def test_complex_split_statement(cc, prec, first, o, v, k):
 
 
 @pytest.mark.parametrize("prec,rel", [("bf16x3", 4e-4), ("bf16x6", 2e-6)])
-@pytest.mark.parametrize("o,v", [(3, 8), (6, 30)])
-def test_complex_mixed_full_residual_vs_oracle(cc, prec, rel, o, v):
-    _, engine = cc
+@pytest.mark.parametrize("o,v,route_all", [(3, 8, True), (6, 30, True), (9, 37, False)])
+def test_complex_mixed_full_residual_vs_oracle(cc, prec, rel, o, v, route_all):
+    """Every complex R1, R2 element of the split route against the complex
+    oracle within the element-wise bound of the plan's routes (moduli, twice
+    the real rule), and the error norm as an extra check."""
+    ccm, engine = cc
     s, B, t1, t2 = complex_case(o, v, 9, L=8)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
-    eng = engine.Engine(dsys, list_name="ccsd_vvvv", precision=prec, route_all=True)
+    eng = engine.Engine(dsys, list_name="ccsd_vvvv", precision=prec, route_all=route_all)
     r1, r2 = eng.residual(zdev(t1), zdev(t2))
     torch.cuda.synchronize()
-    o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle.antisym_integrals(o, v, B), t1, t2)
+    V = oracle.antisym_integrals(o, v, B)
+    o1, o2 = oracle.ccsd_residual(o, v, s.eps, V, t1, t2)
+    _, [(e1, e2)] = list_bounds(ccm.load_list("ccsd_vvvv"), o, v, s.eps, V, t1, t2, [eng.plan])
+    assert_elementwise([r1, r2], [o1, o2], [e1, e2], what=f"complex {prec} o={o} v={v}")
     d = np.sqrt(np.sum(np.abs(r1.cpu().numpy() - o1) ** 2) + np.sum(np.abs(r2.cpu().numpy() - o2) ** 2))
     ref = np.sqrt(np.sum(np.abs(o1) ** 2) + np.sum(np.abs(o2) ** 2))
     assert d <= rel * ref

@@ -16,7 +16,7 @@ import torch
 import ccinputs
 import list_exec
 import oracle
-from gpu_util import DEV, oracle_V, small_case, to_dev
+from gpu_util import DEV, assert_elementwise, list_bounds, oracle_V, small_case, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -111,15 +111,24 @@ def test_ragged_column_tiles(cc, prec, first, o):
 
 
 @pytest.mark.parametrize("prec,rel", [("bf16x3", 2e-4), ("bf16x6", 1e-6)])
-@pytest.mark.parametrize("o,v", [(3, 8), (6, 30)])
-def test_mixed_full_residual_vs_oracle(cc, prec, rel, o, v):
-    _, engine = cc
+@pytest.mark.parametrize("o,v,route_all", [(3, 8, True), (6, 30, True), (10, 40, False), (13, 57, False)])
+def test_mixed_full_residual_vs_oracle(cc, prec, rel, o, v, route_all):
+    """Every R1 and R2 element of the split route against the oracle, within the
+    element-wise bound of the plan's routes propagated through the list
+    (list_exec.run_list_bounds); the Frobenius norm of the error as an extra
+    check.  route_all sends every contraction to the tensor cores; otherwise
+    the plan's own route choice (tensor cores, FP32 narrow and tiled, FP64)."""
+    ccm, engine = cc
     s, B, t1, t2 = small_case(o, v, 7, L=8, scale=6.0, tscale=0.05)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
-    eng = engine.Engine(dsys, list_name="ccsd_vvvv", precision=prec, route_all=True)
+    eng = engine.Engine(dsys, list_name="ccsd_vvvv", precision=prec, route_all=route_all)
     r1, r2 = eng.residual(to_dev(t1), to_dev(t2))
     torch.cuda.synchronize()
-    o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
+    V = oracle_V(o, v, B)
+    o1, o2 = oracle.ccsd_residual(o, v, s.eps, V, t1, t2)
+    (x1, x2), [(e1, e2)] = list_bounds(ccm.load_list("ccsd_vvvv"), o, v, s.eps, V, t1, t2, [eng.plan])
+    assert np.abs(x2 - o2).max() < 1e-13 and np.abs(x1 - o1).max() < 1e-13   # the einsum reading is the oracle's
+    assert_elementwise([r1, r2], [o1, o2], [e1, e2], what=f"{prec} o={o} v={v}")
     d = np.sqrt(np.sum((r1.cpu().numpy() - o1) ** 2) + np.sum((r2.cpu().numpy() - o2) ** 2))
     ref = np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
     assert d <= rel * ref
@@ -182,27 +191,36 @@ def test_narrow_gemm_route(cc, prec, kind, rel):
     r2 = torch.zeros(o, o, v, v, dtype=torch.float64, device=DEV)
     ccm.cc_residual(eng.plan, dsys.ints(), to_dev(t1), to_dev(t2), r1, r2, eng.ws)
     torch.cuda.synchronize()
-    e1, e2 = list_exec.run_list(text, o, v, s.eps, oracle_V(o, v, B), t1, t2)
+    (e1, e2), [(b1, b2)] = list_bounds(text, o, v, s.eps, oracle_V(o, v, B), t1, t2, [eng.plan])
+    assert_elementwise([r2], [e2], [b2], slack=1e-14, what=f"narrow route {prec}")
     err = np.abs(r2.cpu().numpy() - e2).max()
     assert err <= rel * np.abs(e2).max(), err
 
 
 @pytest.mark.parametrize("prec,rel", [("fp64", 1e-12), ("bf16x3", 2e-4)])
 def test_autotuned_plan_keeps_the_residual(cc, prec, rel):
-    """cc_plan_autotune changes only tile widths and split-K factors: the
-    residual of the tuned plan matches the oracle like the planned one."""
+    """cc_plan_autotune changes only tile widths and split-K factors: every
+    element of the tuned plan's residual matches the oracle within the bound
+    of its (tuned) routes, 1e-9 for FP64."""
     ccm, engine = cc
     o, v = 10, 40
     s, B, t1, t2 = small_case(o, v, 31, L=16, scale=6.0, tscale=0.05)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
-    eng = engine.Engine(dsys, list_name="ccsd" if prec == "fp64" else "ccsd_vvvv", precision=prec)
+    name = "ccsd" if prec == "fp64" else "ccsd_vvvv"
+    eng = engine.Engine(dsys, list_name=name, precision=prec)
     T1, T2 = to_dev(t1), to_dev(t2)
     eng.autotune(T1, T2, reps=2)
     d = eng.plan.describe()
     assert d["tuned"] == 1 and any(st.get("candidates", 0) > 1 for st in d["steps"])
     r1, r2 = eng.residual(T1, T2)
     torch.cuda.synchronize()
-    o1, o2 = oracle.ccsd_residual(o, v, s.eps, oracle_V(o, v, B), t1, t2)
+    V = oracle_V(o, v, B)
+    o1, o2 = oracle.ccsd_residual(o, v, s.eps, V, t1, t2)
+    if prec == "fp64":
+        assert_elementwise([r1, r2], [o1, o2], [np.full(o1.shape, 1e-9), np.full(o2.shape, 1e-9)], slack=1e-12)
+    else:
+        _, [(e1, e2)] = list_bounds(ccm.load_list(name), o, v, s.eps, V, t1, t2, [eng.plan])
+        assert_elementwise([r1, r2], [o1, o2], [e1, e2], what="tuned bf16x3")
     dd = np.sqrt(np.sum((r1.cpu().numpy() - o1) ** 2) + np.sum((r2.cpu().numpy() - o2) ** 2))
     assert dd <= rel * np.sqrt(np.sum(o1 ** 2) + np.sum(o2 ** 2))
 
@@ -234,6 +252,13 @@ def test_every_gemm_configuration_gives_the_same_residual(cc, list_name, prec, o
     torch.cuda.synchronize()
     base = torch.cat([b1.flatten(), b2.flatten()]).cpu().numpy()  # complex or real
     scale = np.linalg.norm(base)
+    # every configuration and the planned one lie within the bound of the
+    # loosest candidate (no split K) of the truth, so within twice it of each other
+    _, [(e1, e2)] = list_bounds(ccm.load_list(list_name), o, v, s.eps, oracle.antisym_integrals(o, v, B), t1, t2,
+                                [eng.plan], use_splitk=False)
+    if prec == "fp64":
+        e1, e2 = np.full(e1.shape, 1e-12), np.full(e2.shape, 1e-12)
+    ebound = 2.0 * np.concatenate([e1.ravel(), e2.ravel()])
     steps = eng.plan.describe()["steps"]
     reds = 0
     for k, st in enumerate(steps):
@@ -245,6 +270,7 @@ def test_every_gemm_configuration_gives_the_same_residual(cc, list_name, prec, o
             r1, r2 = eng.residual(T1, T2)
             torch.cuda.synchronize()
             got = torch.cat([r1.flatten(), r2.flatten()]).cpu().numpy()
+            assert_elementwise([got], [base], [ebound], what=f"step {k} bn={bn} splitk={sk} red={red}")
             tol = 1e-5 if prec != "fp64" else 1e-13
             assert np.linalg.norm(got - base) <= tol * scale, (k, bn, sk, red)
             reds += red
