@@ -68,6 +68,9 @@ def jsonable(e):
 
 
 def workload_name(args, dtype=None):
+    if args.size:
+        return (f"spin-orbital CCSD o={args.size.split(',')[0]} v={args.size.split(',')[1]} L=120 seed=0, "
+                f"{'complex128' if (dtype or args.dtype) == 'c128' else 'FP64 real'}, synthetic integrals")
     if (dtype or args.dtype) == "c128":
         return SMALL_C if args.small else WORKLOAD_C
     return SMALL if args.small else WORKLOAD
@@ -346,6 +349,8 @@ def run_ccsd(args, world, rank, local, dtype="f64", suite=False, cpu=None):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg = dict(ccinputs.CONFIG_SMALL if args.small else ccinputs.CONFIG_LADDER)
+    if args.size:
+        cfg["o"], cfg["v"] = (int(x) for x in args.size.split(","))
     o, v = cfg["o"], cfg["v"]
     cplx = dtype == "c128"
     cdt = cc.CC_C128 if cplx else cc.CC_F64
@@ -426,7 +431,7 @@ def run_ccsd(args, world, rank, local, dtype="f64", suite=False, cpu=None):
         peak = pk["bf16_tflops"]
         # DRAM bytes of one launch, measured by ncu on this workload (None until captured)
         traffic = None
-        if (not cplx and not args.small and not packed and args.precision == "bf16x3"
+        if (not cplx and not args.small and not packed and args.precision == "bf16x3" and (o, v) == (40, 200)
                 and st["M"] == v * v and st["N"] == o * o):
             traffic = LADDER_TRAFFIC
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -479,8 +484,8 @@ def run_ccsd(args, world, rank, local, dtype="f64", suite=False, cpu=None):
             "config": {"workload": workload_name(args, dtype), "precision": args.precision,
                        "list": mixed_list, "fp64_list": fp64_list, "flops_per_iter": flops, "replicas": world,
                        "flops_counted": "packed (pair-count) flops" if packed else "unpacked flops",
-                       "l2": "inputs larger than L2 (<ab||ef> split planes %.1f GB, T2 %d MB)"
-                             % (6.4 * (2 if cplx else 1), 512 * (2 if cplx else 1)),
+                       "l2": "inputs larger than L2 (<ab||ef> split planes %.2f GB, T2 %d MB)"
+                             % (2 * 2 * v ** 4 * (2 if cplx else 1) / 1e9, esz * o * o * v * v // 10 ** 6),
                        "integral_build_s": t_int, "integral_bytes": int_bytes, "autotune_s": t_tune,
                        "gemm_configs": {st["note"]: [st.get("bn", 0), st["splitk"], st.get("red", 0)]
                                         for st in desc["steps"] if st.get("configs")}},
@@ -496,13 +501,13 @@ def run_ccsd(args, world, rank, local, dtype="f64", suite=False, cpu=None):
     torch.cuda.empty_cache()
     acc = Engine(dsys, list_name=mixed_list, precision="bf16x6") if args.precision != "bf16x6" else mixed
 
-    def timed_solve(eng, refine=None, **kw):
+    def timed_solve(eng, refine=None, max_iter=60, **kw):
         a1, a2 = z()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         sol_ = Solver(eng, refine=refine)
         torch.cuda.synchronize()
         g0.record(stream)
-        r = sol_.solve(a1, a2, max_iter=60, tol=1e-8, stream=stream, **kw)
+        r = sol_.solve(a1, a2, max_iter=max_iter, tol=1e-8, stream=stream, **kw)
         g1.record(stream)
         torch.cuda.synchronize()
         del sol_, a1, a2
@@ -532,10 +537,19 @@ def run_ccsd(args, world, rank, local, dtype="f64", suite=False, cpu=None):
                                      "achieved": fst["flops"] / tk / 1e12, "peak": fpk, "unit": "TFLOP/s",
                                      "frac": fst["flops"] / tk / 1e12 / fpk,
                                      "peak_kind": "measured live: cuBLAS DGEMM 4096^3 best of 3"}}
-    legs[args.precision + "_alone"] = timed_solve(mixed)
+    # a split route alone stalls at its rounding floor when that lies above the tolerance
+    legs[args.precision + "_alone"] = timed_solve(mixed, max_iter=30)
     if acc is not mixed:
-        legs["bf16x6_alone"] = timed_solve(acc)
+        legs["bf16x6_alone"] = timed_solve(acc, max_iter=30)
     legs["bf16x6_refined"] = timed_solve(acc, refine=fp64, switch_tol=1e-7)
+    # the FP64-grade exact-slice route: alone, and as the refine plan of the split routes
+    slices = Engine(dsys, list_name=mixed_list, precision="slices")
+    legs["slices_alone"] = timed_solve(slices)
+    legs[args.precision + "_refined_slices"] = timed_solve(mixed, refine=slices, switch_tol=1e-7)
+    if acc is not mixed:
+        legs["bf16x6_refined_slices"] = timed_solve(acc, refine=slices, switch_tol=1e-7)
+    del slices
+    torch.cuda.empty_cache()
     e_ref = e_or if e_or is not None else legs["bf16x6_refined"][0].energy
     tts = {"oracle_energy": e_or, "oracle": ("baseline/oracle_cache.json: " + oref["oracle"] + f", |R| < "
                                              f"{oref['tol']:g}") if oref else None}
@@ -543,7 +557,7 @@ def run_ccsd(args, world, rank, local, dtype="f64", suite=False, cpu=None):
         tts[name] = {"s": t, "iterations": r.iterations, "converged": r.converged, "energy": jsonable(r.energy),
                      "delta_E_vs_oracle": delta_e(r.energy, e_or),
                      "delta_E_vs_fp64": delta_e(r.energy, rf.energy) if rf is not None else None}
-        if name.endswith("refined"):
+        if "refined" in name:
             tts[name]["switched_at"] = r.switched_at
             tts[name]["rnorms"] = [float(f"{x:.3e}") for x in r.rnorms]
         if rf is not None and name != "fp64":
@@ -786,16 +800,20 @@ def run_ladder(args, world, rank, local):
     dt = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
     ms_step, ms_kernel, calls = cc.cc_plan_profile_read(eng.plan)
     steps = eng.plan.describe()["steps"]
-    k = next(i for i, st in enumerate(steps) if st["kind"] == "gemm_bf16split")
+    k = next(i for i, st in enumerate(steps) if st["kind"].startswith("gemm"))
     st = steps[k]
     t_k = ms_kernel[k] / calls / 1e3
-    tflop = st["products"] * 2.0 * st["M"] * st["N"] * st["K"]
+    split = st["kind"] == "gemm_bf16split"
+    tflop = (st["products"] if split else 1) * 2.0 * st["M"] * st["N"] * st["K"]
     ach = tflop / t_k / 1e12
     value = world * eng.plan.flops * args.steps / dt / 1e12
+    if not split:
+        fpk = fp64_peak_live(torch)
     return {"metric": "particle-ladder contraction TFLOP/s on 1 B300", "value": value, "unit": "TFLOP/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"{args.precision}: bf16 tensor-core products, fp32 accumulation, fp64 output",
+            "dtype": (f"{args.precision}: bf16 tensor-core products, fp32 accumulation, fp64 output" if split
+                      else "fp64"),
             "data": "synthetic",
             "config": {"workload": f"particle ladder {LADDER_TEXT} o={o} v={v} L=120 seed=0",
                        "gemm_shape": [st["M"], st["N"], st["K"]], "tile_width": st.get("bn"),
@@ -803,7 +821,11 @@ def run_ladder(args, world, rank, local):
             "roofline": {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": ach / pk["bf16_tflops"], "traffic": None,
                          "kernel": "tc_gemm_persistent_kernel (" + st["note"] + ")", "ms_per_launch": t_k * 1e3,
-                         "peak_kind": f"{pk_kind} bf16 burst (tensor-pipe flops = {st['products']} products x 2MNK)"},
+                         "peak_kind": f"{pk_kind} bf16 burst (tensor-pipe flops = {st['products']} products x 2MNK)"}
+            if split else
+            {"bound": "fp64", "achieved": ach, "peak": fpk, "unit": "TFLOP/s", "frac": ach / fpk, "traffic": None,
+             "kernel": "gemm_f64_kernel (" + st["note"] + ")", "ms_per_launch": t_k * 1e3,
+             "peak_kind": "measured live: cuBLAS DGEMM 4096^3 best of 3"},
             "gpu_launches": cc.cc_plan_launch_count(eng.plan) - n0, "clocks": clk.summary()}
 
 
@@ -848,6 +870,12 @@ def run_batched(args, world, rank, local, suite=False):
         return max_over_ranks(g0.elapsed_time(g1) / 1e3, world), res
 
     variants = (("fp64", "ccsd", "fp64"), ("bf16x3", "ccsd_vvvv", "bf16x3"), ("bf16x6", "ccsd_vvvv", "bf16x6"))
+    if args.batched_quick:
+        # profiler captures: the bf16x3 plans only, untuned, two iterations of cc_solve_batched
+        engs = [Engine(d, list_name="ccsd_vvvv", precision="bf16x3") for d in dsys]
+        t2, res = timed(BatchSolver(engs), 2, 0.0)
+        return {"metric": "batched quick run (profiler capture)", "value": None, "unit": "s",
+                "ms_2_iterations": t2 * 1e3, "launches": sum(cc.cc_plan_launch_count(e.plan) for e in engs)}
     with Clocks(local) as clk:
         for name, lst, prec in variants:
             engs = [Engine(d, list_name=lst, precision=prec) for d in dsys]
@@ -925,7 +953,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6", "fp64"],
+                    help="precision of the timed plan (fp64: the FP64 route, e.g. for profiler captures)")
+    ap.add_argument("--size", default=None, help="o,v of the CCSD workload instead of o=40 v=200 (profiler "
+                    "captures of the iteration's kernels on a smaller case)")
     ap.add_argument("--small", action="store_true", help="o=10 v=40 instead of o=40 v=200")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -941,6 +972,8 @@ def main():
                     help="ccsdt: the o=8 v=64 CCSDT workload (generated list); batched: 64 uneven CCSD systems; "
                          "ladder: the particle-ladder contraction alone (profiler captures)")
     ap.add_argument("--ladder-size", default="20,100", help="o,v of --workload ladder")
+    ap.add_argument("--batched-quick", action="store_true",
+                    help="--workload batched: bf16x3 only, untuned, one two-iteration solve (profiler captures)")
     ap.add_argument("--cpu-leg", default=None, choices=["small"], help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_leg == "small":
@@ -962,7 +995,8 @@ def main():
             cpu = cpu_baseline(o, v, PLAN_FLOPS[("ccsd_vvvv", o, v, args.dtype)], complex_=args.dtype == "c128",
                                small=small)
         line = run_ccsd(args, world, rank, local, dtype=args.dtype, cpu=cpu)
-        if world == 1 and not args.no_suite and args.dtype == "f64" and not args.small and not args.packed:
+        if world == 1 and not args.no_suite and args.dtype == "f64" and not args.small and not args.packed \
+                and not args.size:
             import torch
             torch.cuda.empty_cache()
             c = run_ccsd(args, world, rank, local, dtype="c128", suite=True)

@@ -63,14 +63,21 @@ typedef enum {
 
 typedef enum { CC_F64 = 0, CC_C128 = 1 } cc_dtype;
 
-/* Arithmetic of the bulk contractions.
+/* Arithmetic of the bulk contractions (those of at least 2e8 flops; smaller
+ * ones run in FP32 on CC_PREC_BF16X3 plans and in FP64 on the others).
  *   CC_PREC_FP64:   every GEMM in FP64 (SIMT DFMA).
  *   CC_PREC_BF16X3: each FP64 operand split into bf16 hi + lo planes, products
  *                   hi*hi + hi*lo + lo*hi on tcgen05 tensor cores with FP32
  *                   accumulation in TMEM, recombined into FP64 outputs.
- *   CC_PREC_BF16X6: three planes (hi, mid, lo), six products.
- * Contractions below 4e9 flops stay in FP64 on every precision. */
-typedef enum { CC_PREC_FP64 = 0, CC_PREC_BF16X3 = 2, CC_PREC_BF16X6 = 3 } cc_precision;
+ *   CC_PREC_BF16X6: three planes (hi, mid, lo), six products, accumulators
+ *                   drained into float-float registers every 128 K.
+ *   CC_PREC_SLICES: FP64-grade: every operand row scaled by a power of two and
+ *                   cut into six exact 7-bit bf16 slices; the 21 slice
+ *                   products of weight <= 5 summed exactly in FP32 over
+ *                   128-long K chunks and drained into float-float registers
+ *                   (error ~2^-40 of K max|A row| max|B column|).  Meant as
+ *                   the refine plan of cc_solve. */
+typedef enum { CC_PREC_FP64 = 0, CC_PREC_BF16X3 = 2, CC_PREC_BF16X6 = 3, CC_PREC_SLICES = 4 } cc_precision;
 
 typedef struct cc_plan_s *cc_plan;
 

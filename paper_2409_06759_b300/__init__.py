@@ -22,8 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libccb300.so")
 LISTS = os.path.join(_HERE, "lists")
 
 CC_F64, CC_C128 = 0, 1
-CC_PREC_FP64, CC_PREC_BF16X3, CC_PREC_BF16X6 = 0, 2, 3
-PRECISIONS = {"fp64": CC_PREC_FP64, "bf16x3": CC_PREC_BF16X3, "bf16x6": CC_PREC_BF16X6}
+CC_PREC_FP64, CC_PREC_BF16X3, CC_PREC_BF16X6, CC_PREC_SLICES = 0, 2, 3, 4
+PRECISIONS = {"fp64": CC_PREC_FP64, "bf16x3": CC_PREC_BF16X3, "bf16x6": CC_PREC_BF16X6, "slices": CC_PREC_SLICES}
 STATUS = ["CC_OK", "CC_ERR_INVALID_ARG", "CC_ERR_PARSE", "CC_ERR_SHAPE", "CC_ERR_UNSUPPORTED", "CC_ERR_OOM",
           "CC_ERR_CUDA", "CC_ERR_NOT_CONVERGED", "CC_ERR_TIMEOUT", "CC_ERR_WORKSPACE"]
 

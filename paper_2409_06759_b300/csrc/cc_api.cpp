@@ -328,7 +328,7 @@ cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_prec
     if (dtype != CC_F64 && dtype != CC_C128) return fail(CC_ERR_INVALID_ARG, "unknown dtype");
     const int prec = (int)precision;
     const int base = prec >= 100 ? prec - 100 : prec;
-    if (base != CC_PREC_FP64 && base != CC_PREC_BF16X3 && base != CC_PREC_BF16X6)
+    if (base != CC_PREC_FP64 && base != CC_PREC_BF16X3 && base != CC_PREC_BF16X6 && base != CC_PREC_SLICES)
         return fail(CC_ERR_INVALID_ARG, "unknown precision");
     cc_plan_s *pl = new (std::nothrow) cc_plan_s();
     if (!pl) return fail(CC_ERR_OOM, "plan allocation failed");

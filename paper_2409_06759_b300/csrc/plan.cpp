@@ -20,6 +20,12 @@
 
 namespace ccb {
 
+// bytes of an operand's split planes: bf16 planes [nplanes][R][Kp]; the six
+// exact slices are followed by one int32 row exponent per row
+static int64_t planes_bytes(int64_t R, int64_t Kp, int nplanes) {
+    return R * Kp * 2 * nplanes + (nplanes == 6 ? R * 4 : 0);
+}
+
 static const char *kBlockNames[6] = {"oooo", "ooov", "oovv", "ovov", "ovvv", "vvvv"};
 
 void integral_block_dims(int o, int v, int block, int64_t ext[4]) {
@@ -293,7 +299,7 @@ struct Planner {
             }
         exists = false;
         SplitRec r{tensor, ver, d.nplanes, d, splits_need};
-        splits_need += align_up(d.Rp * d.Kp * 2 * d.nplanes);
+        splits_need += align_up(planes_bytes(d.Rp, d.Kp, d.nplanes));
         splits.push_back(r);
         return r.off;
     }
@@ -809,6 +815,8 @@ struct Planner {
         // (matrix-vector shapes stay on the memory-bound FP64 kernels)
         bool use_mixed = plan.precision != 0 &&
                          (mixed_all || (flops >= 2.0e8 && Mx > 1 && Nx > 1 && Kx > 1));
+        // exact-slice plans (FP64-grade): every other route stays FP64
+        const bool slices = plan.precision == 4;
         // except a matrix-vector product against a large integral block: its
         // split planes are cached once per solve, so the tensor route streams
         // half the bytes of the FP64 block (the idle tile columns cost nothing
@@ -816,7 +824,7 @@ struct Planner {
         const auto big_static = [&](const View &X) {
             return plan.tensors[X.tensor].kind == TKind::INTEGRAL && view_elems(X) >= 100000000;
         };
-        const bool static_mv = plan.precision != 0 && !mixed_all && Kx > 1 && (Mx == 1) != (Nx == 1) &&
+        const bool static_mv = plan.precision != 0 && !slices && !mixed_all && Kx > 1 && (Mx == 1) != (Nx == 1) &&
                                (big_static(A) || big_static(B));
         use_mixed = use_mixed || static_mv;
         // Tensor tiles are 128 x bn x 64.  A narrow contraction (K <= 64 and one
@@ -840,10 +848,10 @@ struct Planner {
             if (narrow && eff < 0.5) {
                 use_mixed = false;
                 use_rows = true;
-                use_f32 = true;
+                use_f32 = !slices;
             } else if (eff < 0.15 && !cplx && !static_mv) {
                 use_mixed = false;
-                use_f32 = true;
+                use_f32 = !slices;
             }
         }
 
@@ -1024,7 +1032,8 @@ struct Planner {
             g.gemm.conj_a = cplx && A.conj ? 1 : 0;
             g.gemm.conj_b = cplx && B.conj ? 1 : 0;
         } else {
-            const int np = plan.precision == 3 ? 3 : 2;
+            // planes: 2 (bf16x3), 3 (bf16x6), or 6 exact slices with row exponents (FP64-grade)
+            const int np = plan.precision == 3 ? 3 : plan.precision == 4 ? 6 : 2;
             // complex: one real GEMM of doubled K carries C = A B (4M); the
             // smaller operand is embedded (rows and K doubled), the other
             // stacked (K doubled), and the output gains a re/im digit on the
@@ -1040,10 +1049,10 @@ struct Planner {
             TcGemmDesc &t = g.tc;
             t.M = Mr;
             t.N = Nr;
-            t.bn = Nr <= 64 ? 64 : (Nr <= 128 || np == 3) ? 128 : 256;
+            t.bn = (Nr <= 64 || np == 6) ? 64 : (Nr <= 128 || np == 3) ? 128 : 256;
             // column tiles of the widest tile an autotuner may pick (the kernels
             // run ceil(N / bn) column tiles; the planes themselves hold N rows)
-            const int bn_max = np == 3 ? (Nr <= 64 ? 64 : 128) : (Nr <= 64 ? 64 : Nr <= 128 ? 128 : 256);
+            const int bn_max = np == 6 ? 64 : np == 3 ? (Nr <= 64 ? 64 : 128) : (Nr <= 64 ? 64 : Nr <= 128 ? 128 : 256);
             t.Mp = align_up(Mr, 128);
             t.Np = align_up(Nr, bn_max);
             t.Kp = align_up(Kr, 64);
@@ -1078,6 +1087,8 @@ struct Planner {
                 const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
                 t.nprod = 3;
                 for (int k = 0; k < 3; k++) { t.prod_a[k] = pa[k]; t.prod_b[k] = pb[k]; }
+            } else if (np == 6) {
+                t.nprod = 21;   // slice pairs (s, t) with s + t <= 5, enumerated by the kernel
             } else {
                 const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
                 t.nprod = 6;
@@ -1106,7 +1117,7 @@ struct Planner {
             }
             g.a_static = plan.tensors[A.tensor].kind == TKind::INTEGRAL || plan.tensors[A.tensor].static_data;
             g.b_static = plan.tensors[B.tensor].kind == TKind::INTEGRAL || plan.tensors[B.tensor].static_data;
-            const int64_t bytes_a = Mr * t.Kp * 2 * np, bytes_b = Nr * t.Kp * 2 * np;
+            const int64_t bytes_a = planes_bytes(Mr, t.Kp, np), bytes_b = planes_bytes(Nr, t.Kp, np);
             // static planes live in the cache; other planes in the split region, shared by
             // every later step that splits the same version of the same view
             if (g.a_static) { g.planes_a_off = cache_need; cache_need += align_up(bytes_a); }

@@ -297,10 +297,214 @@ static void split_tile_launch(const SplitDesc &d, const double *x, void *planes,
     }
 }
 
+// ------------------------------------------------------------ exact slices
+// The FP64-grade split (kSlices = 6 planes): every row r of the operand gets an
+// exponent E_r with max_k |X(r,k)| < 2^E_r, and each element is cut into six
+// signed 7-bit slices of its fixed-point value |x| 2^-E_r:
+//     x = sign 2^E_r sum_s q_s 2^-7(s+1) + t,   0 <= q_s <= 127,  |t| < 2^(E_r-42).
+// A slice is stored as the bf16 number sign q_s 2^-7(s+1) (at most 7
+// significant bits, so exact).  A product of slices s and t is then an integer
+// multiple of 2^-7(s+t+2) below 2^-7(s+t) in magnitude, and a sum of fewer
+// than 2^24 such units is exact in FP32 whatever the order of the additions:
+// the tensor cores accumulate the slice products of one weight s + t exactly
+// over 128-long K chunks (tc_gemm_slices_kernel).  The fixed-point value is
+// taken from the 53-bit significand shifted by E_r - e_x, on the integer pipe.
+// The row exponents (biased: the largest IEEE exponent field of the row, so
+// E_r = field - 1022) follow the planes in the same buffer, one int per row.
+constexpr int kSlices = 6;
+
+__host__ __device__ inline int64_t slice_plane_bytes(int64_t R, int64_t Kp) { return (int64_t)kSlices * R * Kp * 2; }
+
+// biased exponent field of |x| (0 for zeros and subnormals, 2047 for inf/NaN)
+__device__ __forceinline__ int exp_field(double x) {
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffull);
+}
+
+// pass 1: the row exponents (atomicMax into exps[], which starts at zero)
+template <bool LK, bool CPLX>
+__global__ void __launch_bounds__(256, 5) slice_exp_kernel(const SplitDesc d, const double *__restrict__ x,
+                                                         int *__restrict__ exps, uint32_t rtiles, uint32_t ntiles) {
+    __shared__ int64_t ro[64], ko[64];
+    __shared__ int srow[64];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = (int64_t)(t % rtiles) * 64, k0 = (int64_t)(t / rtiles) * 64;
+        __syncthreads();
+        if (tid < 64) {
+            const int64_t r = r0 + tid;
+            ro[tid] = r < d.R ? row_offset(d, r) : -1;
+            srow[tid] = 0;
+        } else if (tid < 128) {
+            const int64_t k = k0 + tid - 64;
+            ko[tid - 64] = k < d.K ? grp_off(d.gk, CPLX ? (k >> 1) : k) : -1;
+        }
+        __syncthreads();
+        int ex[16];
+        const int64_t oA = LK ? ko[lane] : ro[lane], oB = LK ? ko[lane + 32] : ro[lane + 32];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int w = warp + 8 * i;
+            const int64_t ow = LK ? ro[w] : ko[w];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int64_t oo = h ? oB : oA;
+                const int q = lane + 32 * h;
+                const int rr = LK ? w : q, kk = LK ? q : w;
+                const bool ok = ow >= 0 && oo >= 0;
+                double v;
+                if (CPLX) v = ok ? src_tile(d, x, r0 + rr, ro[rr], k0 + kk, ko[kk]) : 0.0;
+                else v = ok ? __ldg(x + ow + oo) : 0.0;
+                ex[2 * i + h] = exp_field(v);
+            }
+        }
+        if (LK) {
+            // row warp + 8i: the warp's 64 values of that row
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int m = __reduce_max_sync(0xffffffffu, (unsigned)max(ex[2 * i], ex[2 * i + 1]));
+                if (lane == 0 && m > 0) atomicMax(&srow[warp + 8 * i], m);
+            }
+        } else {
+            // rows lane and lane + 32: eight values of each per thread
+            int m0 = 0, m1 = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i++) { m0 = max(m0, ex[2 * i]); m1 = max(m1, ex[2 * i + 1]); }
+            if (m0 > 0) atomicMax(&srow[lane], m0);
+            if (m1 > 0) atomicMax(&srow[lane + 32], m1);
+        }
+        __syncthreads();
+        if (tid < 64 && r0 + tid < d.R && srow[tid] > 0) atomicMax(exps + r0 + tid, srow[tid]);
+    }
+}
+
+// six slices of one element: out[s] = sign q_s 2^-7(s+1) (biased row exponent eb)
+__device__ __forceinline__ void slice6(double x, int eb, float (&out)[kSlices]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ffull);
+    if (ex == 0x7ff) {                       // inf / NaN: carried by the top slice
+#pragma unroll
+        for (int s = 0; s < kSlices; s++) out[s] = s == 0 ? __uint_as_float(0x7fc00000u) : 0.f;
+        return;
+    }
+    const int dsh = eb - ex;
+    unsigned long long a = 0ull;
+    if (ex != 0 && dsh < 53) a = ((b & 0xfffffffffffffull) | (1ull << 52)) >> (dsh > 0 ? dsh : 0);
+    const bool neg = (b >> 63) != 0ull;
+    float sc = 0.0078125f;                   // 2^-7
+#pragma unroll
+    for (int s = 0; s < kSlices; s++) {
+        const float f = __int2float_rn((int)((a >> (46 - 7 * s)) & 127ull)) * sc;
+        out[s] = neg ? -f : f;
+        sc *= 0.0078125f;
+    }
+}
+
+// pass 2: the six planes, K-major, 16 bytes per lane per plane (the tile
+// layout of split_tile_kernel; the FP64 tile is staged in shared memory)
+template <bool LK, bool CPLX>
+__global__ void __launch_bounds__(256, 3) slice_planes_kernel(const SplitDesc d, const double *__restrict__ x,
+                                                            __nv_bfloat16 *__restrict__ planes,
+                                                            const int *__restrict__ exps, uint32_t rtiles,
+                                                            uint32_t ntiles) {
+    __shared__ double tile[64][65];
+    __shared__ int64_t ro[64], ko[64];
+    const int64_t plane_elems = d.Rp * d.Kp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t r0 = (int64_t)(t % rtiles) * 64, k0 = (int64_t)(t / rtiles) * 64;
+        __syncthreads();
+        if (tid < 64) {
+            const int64_t r = r0 + tid;
+            ro[tid] = r < d.R ? row_offset(d, r) : -1;
+        } else if (tid < 128) {
+            const int64_t k = k0 + tid - 64;
+            ko[tid - 64] = k < d.K ? grp_off(d.gk, CPLX ? (k >> 1) : k) : -1;
+        }
+        __syncthreads();
+        double v[16];
+        const int64_t oA = LK ? ko[lane] : ro[lane], oB = LK ? ko[lane + 32] : ro[lane + 32];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int w = warp + 8 * i;
+            const int64_t ow = LK ? ro[w] : ko[w];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int64_t oo = h ? oB : oA;
+                const int q = lane + 32 * h;
+                const int rr = LK ? w : q, kk = LK ? q : w;
+                const bool ok = ow >= 0 && oo >= 0;
+                if (CPLX) v[2 * i + h] = ok ? src_tile(d, x, r0 + rr, ro[rr], k0 + kk, ko[kk]) : 0.0;
+                else v[2 * i + h] = ok ? __ldg(x + ow + oo) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int w = warp + 8 * i, q = lane + 32 * h;
+                if (LK) tile[w][q] = v[2 * i + h];
+                else tile[q][w] = v[2 * i + h];
+            }
+        __syncthreads();
+#pragma unroll 1
+        for (int qd = 0; qd < 2; qd++) {
+            const int run = tid + 256 * qd, rr = run >> 3, kk = (run & 7) * 8;
+            if (r0 + rr >= d.Rp) continue;
+            const int eb = exps[r0 + rr];
+            uint32_t pk[kSlices][4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float s0[kSlices], s1[kSlices];
+                slice6(tile[rr][kk + 2 * j], eb, s0);
+                slice6(tile[rr][kk + 2 * j + 1], eb, s1);
+#pragma unroll
+                for (int sl = 0; sl < kSlices; sl++) {
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(s0[sl], s1[sl]);
+                    pk[sl][j] = *reinterpret_cast<const uint32_t *>(&b2);
+                }
+            }
+            __nv_bfloat16 *p0 = planes + (r0 + rr) * d.Kp + k0 + kk;
+#pragma unroll
+            for (int sl = 0; sl < kSlices; sl++)
+                *reinterpret_cast<uint4 *>(p0 + sl * plane_elems) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+        }
+    }
+}
+
+template <bool LK, bool CPLX>
+static void slice_launch(const SplitDesc &d, const double *x, void *planes, int *exps, unsigned blocks,
+                         uint32_t rtiles, uint32_t ntiles, cudaStream_t s) {
+    slice_exp_kernel<LK, CPLX><<<blocks, 256, 0, s>>>(d, x, exps, rtiles, ntiles);
+    slice_planes_kernel<LK, CPLX><<<blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes, exps, rtiles, ntiles);
+}
+
+static cudaError_t launch_slices(const SplitDesc &d, const double *x, void *planes, cudaStream_t s) {
+    int *exps = reinterpret_cast<int *>(static_cast<char *>(planes) + slice_plane_bytes(d.Rp, d.Kp));
+    if (cudaError_t e = cudaMemsetAsync(exps, 0, sizeof(int) * (size_t)d.Rp, s)) return e;
+    const int64_t unit = d.cplx ? 2 : 1;
+    const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit;
+    const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == unit;
+    const int64_t rtiles = (d.Rp + 63) / 64, ntiles = rtiles * (d.Kp / 64);
+    if (ntiles > 0xffffffffLL) return cudaErrorInvalidValue;
+    const int64_t ks = d.gk.nd >= 1 ? d.gk.str[d.gk.nd - 1] : 0, rs = d.gr.nd >= 1 ? d.gr.str[d.gr.nd - 1] : 0;
+    const bool lk = k_unit || (!r_unit && ks <= rs);
+    const unsigned blocks = (unsigned)(ntiles < 148 * 6 ? ntiles : 148 * 6);
+    if (d.cplx) {
+        if (lk) slice_launch<true, true>(d, x, planes, exps, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
+        else slice_launch<false, true>(d, x, planes, exps, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
+    } else {
+        if (lk) slice_launch<true, false>(d, x, planes, exps, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
+        else slice_launch<false, false>(d, x, planes, exps, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes, cudaStream_t s) {
-    if (d.Kp % 64 || d.Rp <= 0 || d.nplanes < 2 || d.nplanes > 3 || d.cplx < 0 || d.cplx > 2)
+    if (d.Kp % 64 || d.Rp <= 0 || (d.nplanes != kSlices && (d.nplanes < 2 || d.nplanes > 3)) || d.cplx < 0 ||
+        d.cplx > 2)
         return cudaErrorInvalidValue;
     if (d.cplx && (d.K % 2 || (d.cplx == 2 && d.R % 2))) return cudaErrorInvalidValue;
+    if (d.nplanes == kSlices) return launch_slices(d, x, planes, s);
     // source unit stride inside the row group and not in K: transposed tiles
     // (for complex sources the unit is one complex element, two doubles)
     const int64_t unit = d.cplx ? 2 : 1;
@@ -897,6 +1101,249 @@ __global__ void __launch_bounds__(320, 1)
     }
 }
 
+// ---- exact-slice variant (the FP64-grade route, six planes)
+// Stage s holds the six A slices (128 x 32 bf16 each) and the six B slices
+// (BN x 32) of one 32-wide K block (SWIZZLE_64B).  The 21 slice products with
+// weight g = s + t <= 5 accumulate in six TMEM accumulators, one per weight
+// (columns g * BN ..): each holds integer multiples of 2^-7(g+2) below
+// 6 * 128 * 2^(14 - 7(g+2)) after a 128-long K chunk (four K blocks), so its
+// FP32 sums are exact.  After each chunk the eight epilogue warps drain weight
+// g into float-float (hi, lo) registers (exact two-sum) as soon as that
+// weight's MMAs of the chunk complete, and the MMA issuer starts weight g of
+// the next chunk once its accumulator is drained.  The tile's value is
+// alpha 2^(E_m + E_n) (hi + lo), E from the operands' row exponents.
+constexpr int SBK = 32, SCHUNK = 4;           // K block, K blocks per exact chunk
+
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset between 8-row groups (rows of 64 bytes)
+    d |= (uint64_t)1 << 46;                     // descriptor version of tcgen05
+    d |= (uint64_t)4 << 61;                     // SWIZZLE_64B
+    return d;
+}
+
+template <int BN, int STAGES>
+struct SlCfg {
+    static constexpr int A_BYTES = BM * SBK * 2;
+    static constexpr int B_BYTES = BN * SBK * 2;
+    static constexpr int STAGE_BYTES = kSlices * (A_BYTES + B_BYTES);
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 1024 /*barriers*/ + BN * 8;
+};
+
+__device__ __noinline__ double ldexp_slow(double x, int k) { return ldexp(x, k); }
+
+// 2^k (hi + lo) in FP64: exact power-of-two re-encodings for the usual range
+__device__ __forceinline__ double ff_to_f64_pow2(float hi, float lo, int k) {
+    if (k > -500 && k < 500) return f32_to_f64_pow2(hi, k, 0u) + f32_to_f64_pow2(lo, k, 0u);
+    return ldexp_slow((double)hi + (double)lo, k);
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(320, 1)
+    tc_gemm_slices_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBw,
+                          const __grid_constant__ CUtensorMap mapBn, const TcGemmDesc d, double *__restrict__ C,
+                          double *__restrict__ partials, int kb_per_split, const ColSplit cs,
+                          const int *__restrict__ expA, const int *__restrict__ expB, int *err_flag) {
+    using G = SlCfg<BN, STAGES>;
+    constexpr int HALF = BN / 2;                 // columns per epilogue warp
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *tiles = smem;
+    uint64_t *full = (uint64_t *)(smem + STAGES * G::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;             // [kSlices] weight g of the chunk complete
+    uint64_t *acce = accf + kSlices;             // [kSlices] weight g drained
+    uint32_t *tmem_slot = (uint32_t *)(acce + kSlices);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    volatile int *consumed = abort_flag + 1;
+    int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (int)((d.N + BN - 1) / BN);
+    const int tile = blockIdx.x;
+    const int64_t m0 = (int64_t)(tile / n_tiles) * BM;
+    const int64_t n0 = cs.n0(tile % n_tiles);
+    const int nw = cs.width(tile % n_tiles);
+    const int kb_total = (int)(d.Kp / SBK);
+    const int kb0 = (int)blockIdx.y * kb_per_split;
+    const int kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    const int kblocks = kb1 - kb0;
+    const int nch = (kblocks + SCHUNK - 1) / SCHUNK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int g = 0; g < kSlices; g++) {
+            mbar_init(&accf[g], 1);
+            mbar_init(&acce[g], 8);              // one arrival per epilogue warp
+        }
+        *abort_flag = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);              // kSlices * BN = 384 columns in use
+        tmem_relinquish();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            const CUtensorMap *mb = nw == cs.wide() ? &mapBw : &mapBn;
+            for (int kb = 0; kb < kblocks; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t *st = tiles + s * G::STAGE_BYTES;
+                mbar_expect_tx(&full[s], (uint32_t)(kSlices * (G::A_BYTES + nw * SBK * 2)));
+                for (int p = 0; p < kSlices; p++)
+                    tma_load_3d(st + p * G::A_BYTES, &mapA, &full[s], (kb0 + kb) * SBK, (int)m0, p);
+                for (int q = 0; q < kSlices; q++)
+                    tma_load_3d(st + kSlices * G::A_BYTES + q * G::B_BYTES, mb, &full[s], (kb0 + kb) * SBK, (int)n0,
+                                q);
+                issued = kb + 1;
+            }
+            if (*abort_flag) {
+                for (int kb = *consumed; kb < issued; kb++) mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
+                atomicOr(err_flag, 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(BM, nw);
+            int committed = -1;                  // last chunk whose weights were all committed
+            bool stop = false;
+            for (int kb = 0; kb < kblocks && !stop; kb++) {
+                const int c = kb / SCHUNK;
+                const bool first = (kb % SCHUNK) == 0;
+                const bool last = (kb % SCHUNK) == SCHUNK - 1 || kb == kblocks - 1;
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&full[s], ph)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t st = smem_u32(tiles + s * G::STAGE_BYTES);
+                for (int g = 0; g < kSlices; g++) {
+                    if (first && c >= 1) {
+                        // weight g of the previous chunk must be drained
+                        if (*abort_flag || !mbar_wait(&acce[g], (uint32_t)((c - 1) & 1))) {
+                            *abort_flag = 1;
+                            stop = true;
+                            break;
+                        }
+                        fence_after();
+                    }
+                    const uint32_t dt = tmem + (uint32_t)(g * BN);
+                    for (int sa = 0; sa <= g; sa++) {
+                        const uint32_t a0 = st + sa * G::A_BYTES;
+                        const uint32_t b0 = st + kSlices * G::A_BYTES + (g - sa) * G::B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < SBK / 16; kk++)
+                            mma_bf16(dt, sw64_desc(a0 + kk * 32), sw64_desc(b0 + kk * 32), idesc,
+                                     !(first && sa == 0 && kk == 0));
+                    }
+                    if (last) mma_commit(&accf[g]);
+                }
+                if (stop) break;
+                mma_commit(&empty[s]);
+                *consumed = kb + 1;
+                if (last) committed = c;
+            }
+            // on abort, still complete the pending chunks' barriers so the epilogue can finish
+            for (int c = committed + 1; c < nch; c++)
+                for (int g = 0; g < kSlices; g++) mma_commit(&accf[g]);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;              // column half
+        const int et = threadIdx.x - 64;            // 0..255
+        for (int c = et; c < BN; c += 256) {
+            const int64_t n = n0 + c;
+            coloff[c] = (c < nw && n < d.N) ? grp_off(d.cn, n) : -1;
+        }
+        const int64_t m = m0 + q * 32 + lane;
+        const bool mok = m < d.M;
+        const int64_t roff = mok && gridDim.y == 1 ? grp_off(d.cm, m) : 0;
+        const int em = mok ? expA[m] - 1022 : 0;
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        float hi[HALF], lo[HALF];
+#pragma unroll
+        for (int j = 0; j < HALF; j++) { hi[j] = 0.f; lo[j] = 0.f; }
+        bool good = true;
+        for (int c = 0; c < nch && good; c++) {
+#pragma unroll 1
+            for (int g = 0; g < kSlices; g++) {
+                bool ok = mbar_wait(&accf[g], (uint32_t)(c & 1));
+                fence_after();
+                ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+                if (!ok) {
+                    good = false;
+                    *abort_flag = 1;
+                    if (lane == 0) atomicOr(err_flag, 1);
+                    break;
+                }
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * BN + h * HALF), r);
+                tmem_ld_wait();
+                fence_before();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[g])) : "memory");
+#pragma unroll
+                for (int j = 0; j < HALF; j++) {
+                    float s2, e2;
+                    two_sum(hi[j], __uint_as_float(r[j]), s2, e2);
+                    hi[j] = s2;
+                    lo[j] += e2;
+                }
+            }
+        }
+        if (good && mok) {
+            if (gridDim.y > 1) {
+                double *P = partials + (int64_t)blockIdx.y * d.M * d.N;
+#pragma unroll
+                for (int j = 0; j < HALF; j++) {
+                    const int64_t n = n0 + h * HALF + j;
+                    if (h * HALF + j < nw && n < d.N) P[n * d.M + m] = ff_to_f64_pow2(hi[j], lo[j], em + expB[n] - 1022);
+                }
+            } else {
+#pragma unroll
+                for (int j0 = 0; j0 < HALF; j0 += 16) {
+                    double v[16];
+                    int64_t co[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int c = h * HALF + j0 + j;
+                        co[j] = coloff[c];
+                        const int en = co[j] >= 0 ? expB[n0 + c] - 1022 : 0;
+                        v[j] = co[j] >= 0 ? scale_f64(ff_to_f64_pow2(hi[j0 + j], lo[j0 + j], em + en), d.as) : 0.0;
+                    }
+                    store_batch<16>(C, roff, co, v, d.bcase);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -915,16 +1362,17 @@ static EncodeTiledFn encode_fn() {
 
 // 3-D map over the planes [nplanes][rows][Kp] bf16 (rows unpadded: the
 // box rows past `rows` read as zeros), box {64, box_rows, 1}
-static bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t Kp, int nplanes, int box_rows) {
+static bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t Kp, int nplanes, int box_rows,
+                     int box_k = BK) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
-    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -997,6 +1445,37 @@ static cudaError_t launch_chunked(const TcGemmDesc &d, const void *A, const void
     return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
 }
 
+template <int BN, int STAGES>
+static cudaError_t launch_slices_gemm(const TcGemmDesc &d, const void *A, const void *B, double *C, double *partials,
+                                     int *err, cudaStream_t s) {
+    using G = SlCfg<BN, STAGES>;
+    static std::atomic<unsigned long long> opted{0};
+    if (cudaError_t e = smem_opt_in(tc_gemm_slices_kernel<BN, STAGES>, G::SMEM, opted)) return e;
+    if (d.Mp % BM || d.Kp % 64 || d.Mp < d.M) return cudaErrorInvalidValue;
+    const ColSplit cs = col_split(d.N, BN);
+    CUtensorMap ma, mbw, mbn;
+    if (!make_map(&ma, A, d.M, d.Kp, kSlices, BM, SBK) || !make_map(&mbw, B, d.N, d.Kp, kSlices, cs.wide(), SBK) ||
+        !make_map(&mbn, B, d.N, d.Kp, kSlices, 16 * cs.base, SBK))
+        return cudaErrorInvalidValue;
+    const int *expA = reinterpret_cast<const int *>(static_cast<const char *>(A) + slice_plane_bytes(d.M, d.Kp));
+    const int *expB = reinterpret_cast<const int *>(static_cast<const char *>(B) + slice_plane_bytes(d.N, d.Kp));
+    const int64_t tiles = (d.Mp / BM) * ((d.N + BN - 1) / BN);
+    if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const int kb_total = (int)(d.Kp / SBK);
+    const int sk = d.splitk > 1 ? d.splitk : 1;
+    // K slices hold whole exact chunks
+    int per = (kb_total + sk - 1) / sk;
+    per = (per + SCHUNK - 1) / SCHUNK * SCHUNK;
+    const int zs = (kb_total + per - 1) / per;
+    if (zs > 1 && !partials) return cudaErrorInvalidValue;
+    if (zs > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)tiles, (unsigned)zs);
+    tc_gemm_slices_kernel<BN, STAGES><<<grid, 320, G::SMEM, s>>>(ma, mbw, mbn, d, C, partials, per, cs, expA, expB, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || zs == 1) return e;
+    return launch_splitk_reduce(d.M, d.N, zs, partials, d.cm, d.cn, d.alpha, d.beta, C, s);
+}
+
 }  // namespace tc
 
 cudaError_t launch_convert_selftest(const double *in, int64_t n, float *mine, float *ref, cudaStream_t s) {
@@ -1019,7 +1498,8 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d0, const void *Aplanes, const void
     TcGemmDesc d = d0;
     d.bcase = beta_case(d.beta);
     d.as = make_scale(d.alpha);
-    if (d.nplanes_a != d.nplanes_b || d.nprod < 1 || d.nprod > 8) return cudaErrorInvalidValue;
+    if (d.nplanes_a != d.nplanes_b || d.nprod < 1 || (d.nprod > 8 && d.nplanes_a != kSlices))
+        return cudaErrorInvalidValue;
     if (d.bcase == 2 && d.splitk <= 1) {
         // general beta: C *= beta first, then accumulate
         if (cudaError_t e = launch_scale_grp(d.M, d.N, d.cm, d.cn, d.beta, C, s)) return e;
@@ -1040,6 +1520,9 @@ cudaError_t launch_tc_gemm(const TcGemmDesc &d0, const void *Aplanes, const void
         // three planes: the accurate route, chunked float-float accumulation
         if (d.bn == 128) return tc::launch_chunked<3, 128, 2, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
         if (d.bn == 64) return tc::launch_chunked<3, 64, 3, 2>(d, Aplanes, Bplanes, C, partials, err_flag, s);
+    } else if (d.nplanes_a == kSlices) {
+        // six exact slices: the FP64-grade route
+        if (d.bn == 64) return tc::launch_slices_gemm<64, 3>(d, Aplanes, Bplanes, C, partials, err_flag, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -250,3 +250,20 @@ def test_bench_flop_constants_match_the_plans(cc):
         p = cc.cc_plan_create(cc.load_list(name), o, v, dtype=cc.CC_C128 if dt == "c128" else cc.CC_F64,
                               precision=cc.CC_PREC_BF16X3)
         assert p.flops == flops, (name, o, v, dt)
+
+
+def test_slices_plan_routes(cc):
+    """The exact-slice precision: every bulk GEMM on the tensor cores with six
+    planes (21 products, 64-wide tiles), every other route FP64 (no FP32)."""
+    p = cc.cc_plan_create(cc.load_list("ccsd_vvvv"), 40, 200, precision="slices")
+    d = p.describe()
+    kinds = {st["kind"] for st in d["steps"]}
+    assert "gemm_bf16split" in kinds and not any(k.endswith("f32") for k in kinds)
+    for st in d["steps"]:
+        if st["kind"] == "gemm_bf16split":
+            assert st["products"] == 21 and st["bn"] == 64
+            assert all(c[0] == 64 for c in st.get("configs", []))
+    lad = next(st for st in d["steps"] if st["note"] == "V_vvvv*tau -> Z2")
+    # six bf16 planes and one int32 exponent per row of the 40000 x 40000 block
+    assert d["cache_bytes"] >= 6 * 40000 * 40000 * 2 + 40000 * 4
+    assert lad["flops"] == 2.0 * 40000 * 1600 * 40000

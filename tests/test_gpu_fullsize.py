@@ -70,9 +70,12 @@ def full():
 
 
 def test_sample_set_covers_the_tile_edges(full):
+    """(the oracle's sampled routine adds and subtracts the P(ij)P(ab) partners
+    one by one, so its i = j or a = b elements are zero to rounding only)"""
     s, t1, t2, dsys, engine, idx, want = full
     assert len(idx) >= 256
-    assert np.all(want[(idx[:, 0] == idx[:, 1]) | (idx[:, 2] == idx[:, 3])] == 0.0)
+    z = (idx[:, 0] == idx[:, 1]) | (idx[:, 2] == idx[:, 3])
+    assert z.sum() >= 4 and np.abs(want[z]).max() <= 1e-15 * np.abs(want).max()
 
 
 def test_fp64_residual_sampled_elements_match_oracle(full):
