@@ -649,8 +649,13 @@ def run_ccsdt(args, world, rank, local, suite=False):
     stream = torch.cuda.current_stream(dev)
     z = lambda: [torch.zeros(*sh, dtype=torch.float64, device=dev) for sh in
                  ((o, v), (o, o, v, v), (o, o, o, v, v, v))]
-    plans = {"fp64": Engine(dsys, list_text=text), args.precision: Engine(dsys, list_text=text,
-                                                                          precision=args.precision)}
+    # the split plan as timed (accumulating statements K-concatenated), and the same
+    # plan with one GEMM per statement for comparison
+    unmerged = args.precision + "_one_gemm_per_statement"
+    plans = {"fp64": Engine(dsys, list_text=text),
+             args.precision: Engine(dsys, list_text=text, precision=args.precision)}
+    if args.precision != "fp64" and not suite:
+        plans[unmerged] = Engine(dsys, list_text=text, precision=args.precision, kconcat=False)
     out = {}
     t_tune = None
     mp = plans[args.precision]
@@ -658,12 +663,16 @@ def run_ccsdt(args, world, rank, local, suite=False):
         for k, bn, sk, red in json.load(open(args.load_tune)):
             cc.cc_plan_set_gemm_config(mp.plan, k, bn, sk, red)
     elif not args.no_tune:
-        # GEMM configurations of the mixed plan picked by timing (cc_plan_autotune)
+        # GEMM configurations of the mixed plans picked by timing (cc_plan_autotune)
         tt = time.perf_counter()
-        mp.autotune(*z()[:2], reps=2, stream=stream, t3=z()[2])
-        mp.release()
+        for nm in (args.precision, unmerged):
+            if nm in plans and nm != "fp64":
+                plans[nm].autotune(*z()[:2], reps=2, stream=stream, t3=z()[2])
+                plans[nm].release()
+            if nm == args.precision:
+                torch.cuda.synchronize()
+                t_tune = time.perf_counter() - tt
         torch.cuda.synchronize()
-        t_tune = time.perf_counter() - tt
     if args.save_tune and rank == 0 and not suite:
         json.dump([[k, st.get("bn", 0), st["splitk"], st.get("red", 0)] for k, st in
                    enumerate(mp.plan.describe()["steps"]) if st.get("configs")], open(args.save_tune, "w"))
@@ -698,6 +707,7 @@ def run_ccsdt(args, world, rank, local, suite=False):
         t_all = sum(ms_kernel) / calls / 1e3
         t_tc = sum(ms_kernel[k] for k, s_ in enumerate(steps) if s_["kind"] == "gemm_bf16split") / calls / 1e3
         out[name] = {"s_per_iter": dt / nsteps, "tflops": world * eng.plan.flops * nsteps / dt / 1e12,
+                     "steps": len(steps), "merged_steps": sum(1 for s_ in steps if "stmts" in s_),
                      "o3v5_s_per_iter": t_big, "o3v5_statements": len(big),
                      "launches": cc.cc_plan_launch_count(eng.plan) - n0,
                      "tensor_core_share_of_step_time": t_tc / t_all if t_all > 0 else None,

@@ -123,6 +123,11 @@ typedef struct {
     int fuse_permutes;    /* reserved, 0 */
     int packed_vvvv;      /* 1: a packed-pair contraction over <ab||ef> in its stored
                            * orientation (declared (ab)(ef)) reads ints->vvvv_packed */
+    int no_kconcat;       /* 1: plan every statement on its own.  By default, on the
+                           * split-bf16 precisions (real), statements that accumulate
+                           * into the same intermediate with its indices split the same
+                           * way between their operands run as one tensor-core GEMM
+                           * whose K concatenates theirs (one pass over the output) */
 } cc_plan_opts;
 
 /* cc_plan_create -- parse a contraction list and plan its execution.

@@ -161,7 +161,17 @@ cc_status exec_step(cc_plan_s *pl, const Step &stp, const cc_integrals *I, const
             pl->launches++;
             break;
         case StepKind::GEMM:
-            if (stp.rows) {
+            if (stp.rows && !stp.kcat.empty()) {
+                RowsMultiDesc d = stp.rm;
+                for (size_t k = 0; k < stp.kcat.size(); k++) {
+                    d.m[k].X = resolve(stp.kcat[k].a, I, A, R, w);
+                    d.m[k].Y = resolve(stp.kcat[k].b, I, A, R, w);
+                }
+                d.red = stp.rg.red;
+                if (mark) CC_CUDA(cudaEventRecord(mark, s));
+                CC_CUDA(launch_rows_multi(d, resolve(stp.out, I, A, R, w), s));
+                pl->launches++;
+            } else if (stp.rows) {
                 if (mark) CC_CUDA(cudaEventRecord(mark, s));
                 CC_CUDA(launch_rows_gemm(stp.rg, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
                                          resolve(stp.out, I, A, R, w), s));
@@ -171,6 +181,20 @@ cc_status exec_step(cc_plan_s *pl, const Step &stp, const cc_integrals *I, const
                 CC_CUDA(launch_gemm_f64(stp.gemm, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
                                         resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w), s));
                 pl->launches += stp.gemm.splitk > 1 ? 2 : 1;
+            } else if (!stp.kcat.empty()) {
+                // K-concatenated members: each fills its own K columns of the shared planes
+                void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
+                if (splits) {
+                    for (const KMember &m : stp.kcat) {
+                        CC_CUDA(launch_split_bf16(m.split_a, resolve(m.a, I, A, R, w), pa, s));
+                        CC_CUDA(launch_split_bf16(m.split_b, resolve(m.b, I, A, R, w), pb, s));
+                        pl->launches += 2;
+                    }
+                }
+                if (mark) CC_CUDA(cudaEventRecord(mark, s));
+                CC_CUDA(launch_tc_gemm(stp.tc, pa, pb, resolve(stp.out, I, A, R, w), resolve(stp.partials, I, A, R, w),
+                                       (int *)(w + P.flags_off), s));
+                pl->launches += stp.tc.splitk > 1 ? 2 : 1;
             } else {
                 void *pa = w + stp.planes_a_off, *pb = w + stp.planes_b_off;
                 if (splits && !(stp.a_static && pl->cache_filled) && !stp.skip_a) {
@@ -336,6 +360,8 @@ cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_prec
     int flags = 0;
     if (opts && opts->struct_size >= (int)(offsetof(cc_plan_opts, packed_vvvv) + sizeof(int)) && opts->packed_vvvv)
         flags |= 1;
+    if (opts && opts->struct_size >= (int)(offsetof(cc_plan_opts, no_kconcat) + sizeof(int)) && opts->no_kconcat)
+        flags |= 2;
     if (!build_plan(text, o, v, (int)dtype, prec, pl->plan, err, flags)) {
         delete pl;
         return fail(err.find("index spaces") != std::string::npos ? CC_ERR_SHAPE : CC_ERR_PARSE, err);

@@ -436,6 +436,130 @@ cudaError_t launch_rows_gemm(const RowsGemmDesc &d0, const double *X, const doub
     return d.f32 ? rows_t<float>(d, X, Y, C, s) : rows_t<double>(d, X, Y, C, s);
 }
 
+// ------------------------------------------------------------ rows_multi
+// The narrow kernel over several members into one output: every member's Y
+// block (alpha_s folded in, K rounded up to 8 with zero rows) is staged in
+// shared memory, one thread per row runs through all members' K, and the row's
+// outputs are read and written once at the end.
+static inline int64_t rows_multi_krows(const RowsMultiDesc &d) {
+    int64_t k = 0;
+    for (int s = 0; s < d.nm; s++) k += (d.m[s].K + 7) / 8 * 8;
+    return k;
+}
+
+template <int NC> static int64_t rows_multi_bytes(const RowsMultiDesc &d, int esz) {
+    const int64_t kr = rows_multi_krows(d);
+    return kr * NC * esz + kr * 8 + NC * 8;
+}
+
+template <typename CT, int NC>
+__global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_multi_kernel(const RowsMultiDesc d, double *__restrict__ C) {
+    extern __shared__ __align__(16) unsigned char rm_smem[];
+    int kr = 0;
+    for (int s = 0; s < d.nm; s++) kr += (d.m[s].K + 7) / 8 * 8;
+    CT *ys = reinterpret_cast<CT *>(rm_smem);
+    int64_t *xko = reinterpret_cast<int64_t *>(rm_smem + (size_t)kr * NC * sizeof(CT));
+    int64_t *cco = xko + kr;
+    int kb = 0;
+    for (int s = 0; s < d.nm; s++) {
+        const RowsMember &m = d.m[s];
+        const int k8 = (m.K + 7) / 8 * 8;
+        for (int e = threadIdx.x; e < k8 * NC; e += blockDim.x) {
+            const int k = e / NC, c = e - k * NC;
+            ys[(kb + k) * NC + c] = (k < m.K && c < d.nc)
+                                        ? down<CT>(m.alpha * __ldg(m.Y + grp_offset(m.yk, k) + grp_offset(m.yc, c)))
+                                        : zero<CT>();
+        }
+        for (int k = threadIdx.x; k < k8; k += blockDim.x) xko[kb + k] = k < m.K ? grp_offset(m.xk, k) : 0;
+        kb += k8;
+    }
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) cco[c] = c < d.nc ? grp_offset(d.cc, c) : 0;
+    __syncthreads();
+    const Scale one = {0, 0, 0u, 1.0};
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < d.R; r += (int64_t)gridDim.x * blockDim.x) {
+        CT acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) acc[c] = zero<CT>();
+        kb = 0;
+        for (int s = 0; s < d.nm; s++) {
+            const RowsMember &m = d.m[s];
+            const double *X = m.X;
+            const int64_t xo = grp_offset32(m.xr, (uint32_t)r);
+            // eight loads in flight before their products (the padded Y rows are zero)
+            for (int k0 = 0; k0 < m.K; k0 += 8) {
+                CT a[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) a[j] = k0 + j < m.K ? down<CT>(__ldg(X + xo + xko[kb + k0 + j])) : zero<CT>();
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+#pragma unroll
+                    for (int c = 0; c < NC; c++) acc[c] = cfma(a[j], ys[(kb + k0 + j) * NC + c], acc[c]);
+            }
+            kb += (m.K + 7) / 8 * 8;
+        }
+        const int64_t co = grp_offset32(d.cr, (uint32_t)r);
+        if (d.red) {
+#pragma unroll
+            for (int c = 0; c < NC; c++)
+                if (c < d.nc) red_add(C + co + cco[c], epi_scale(acc[c], one));
+        } else {
+#pragma unroll
+            for (int c0 = 0; c0 < NC; c0 += 8) {
+                double old[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) old[j] = c0 + j < d.nc ? C[co + cco[c0 + j]] : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (c0 + j < d.nc) C[co + cco[c0 + j]] = epi_scale(acc[c0 + j], one) + old[j];
+            }
+        }
+    }
+}
+
+template <typename CT, int NC> static cudaError_t rows_multi_t(const RowsMultiDesc &d, double *C, cudaStream_t s) {
+    const int64_t smem = rows_multi_bytes<NC>(d, (int)sizeof(CT));
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        if (cudaError_t e = cudaFuncSetAttribute(rows_multi_kernel<CT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem))
+            return e;
+    }
+    int64_t blocks = (d.R + 255) / 256;
+    if (blocks > 148 * rows_min_blocks<CT, NC>()) blocks = 148 * rows_min_blocks<CT, NC>();
+    rows_multi_kernel<CT, NC><<<(unsigned)blocks, 256, (size_t)smem, s>>>(d, C);
+    return cudaGetLastError();
+}
+
+template <typename CT> static cudaError_t rows_multi_ct(const RowsMultiDesc &d, double *C, cudaStream_t s) {
+    switch ((d.nc + 7) / 8) {
+        case 1: return rows_multi_t<CT, 8>(d, C, s);
+        case 2: return rows_multi_t<CT, 16>(d, C, s);
+        case 3: return rows_multi_t<CT, 24>(d, C, s);
+        case 4: return rows_multi_t<CT, 32>(d, C, s);
+        case 5: return rows_multi_t<CT, 40>(d, C, s);
+        case 6: return rows_multi_t<CT, 48>(d, C, s);
+        default: return rows_multi_t<CT, 64>(d, C, s);
+    }
+}
+
+int64_t rows_multi_smem_bytes(const RowsMultiDesc &d) {
+    if (d.nc < 1 || d.nc > 64) return 0;
+    const int nc8 = (d.nc + 7) / 8 * 8;
+    const int64_t kr = rows_multi_krows(d);
+    const int64_t b = kr * nc8 * (d.f32 ? 4 : 8) + kr * 8 + nc8 * 8;
+    return b > 200 * 1024 ? 0 : b;
+}
+
+cudaError_t launch_rows_multi(const RowsMultiDesc &d, double *C, cudaStream_t s) {
+    if (d.R <= 0) return cudaSuccess;
+    if (d.nm < 1 || d.nm > kMaxRowsMembers || d.nc < 1 || d.nc > 64 || d.R > 0xffffffffLL ||
+        rows_multi_smem_bytes(d) == 0)
+        return cudaErrorInvalidValue;
+    for (int k = 0; k < d.nm; k++)
+        if (d.m[k].K < 1 || !d.m[k].X || !d.m[k].Y) return cudaErrorInvalidValue;
+    return d.f32 ? rows_multi_ct<float>(d, C, s) : rows_multi_ct<double>(d, C, s);
+}
+
 // ------------------------------------------------------------------ gemv
 // y(r) = alpha * sum_k X(r,k) x(k) + beta * y(r): the GEMM shapes with one
 // output dimension of extent 1 are memory-bound matrix-vector products.

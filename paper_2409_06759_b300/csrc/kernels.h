@@ -115,6 +115,31 @@ struct RowsGemmDesc {
     int red;                        // beta = 1: add C by red.global.add.f64 (no read)
 };
 
+// Several narrow GEMMs into one output, accumulated in one pass (K
+// concatenation on the narrow kernel):
+//   C(r, c) += sum_s alpha_s sum_k X_s(r, k) Y_s(k, c)
+// each member with its own operands and strides; the members' Y blocks sit in
+// shared memory one after the other (alpha_s applied there), so each output
+// element is read and written once whatever the number of members.
+constexpr int kMaxRowsMembers = 8;
+struct RowsMember {
+    Grp xr, xk;     // X_s(r, k) = X_s[xr(r) + xk(k)]
+    Grp yk, yc;     // Y_s(k, c) = Y_s[yk(k) + yc(c)]
+    int K;
+    double alpha;
+    const double *X, *Y;            // set at launch
+};
+struct RowsMultiDesc {
+    int64_t R;
+    int nc, nm;
+    Grp cr, cc;     // C(r, c) = C[cr(r) + cc(c)]
+    int f32;
+    int red;                        // add C by red.global.add.f64 (no read)
+    RowsMember m[kMaxRowsMembers];
+};
+// shared memory of one block of the multi-member narrow kernel (0: too large)
+int64_t rows_multi_smem_bytes(const RowsMultiDesc &d);
+
 // Packed index pairs.  A pair (p < q) of letters with extent n has the index
 // P(p, q) = p (2n - p - 1) / 2 + (q - p - 1): q runs fastest.
 // pack:   dst[P1][P2] = scale * src[p s0 + q s1 + r s2 + u s3] over p < q
@@ -161,11 +186,18 @@ cudaError_t launch_unpack_pairs(const UnpackDesc &d, const double *C, double *ou
 //                     s = -1 for (cr, ck) = (0, 1) (conj: also for cr ^ ck = 1)
 // so that [C_re; C_im] = embedded(A) stacked(B) and likewise with the roles of
 // the operands swapped.  R and K count the real rows and columns.
+// K concatenation (several contractions into one output, one GEMM): the
+// operand fills the plane columns [kdst, kdst + kend) of rows that are Kp long
+// (columns K..kend-1 with zeros; kend = 0 means the whole row, kdst = 0), each
+// value multiplied by `scale` first when `scaled` (the contraction's factor).
 struct SplitDesc {
     int64_t R, K, Rp, Kp;
     Grp gr, gk;
     int nplanes;
     int cplx, conj;
+    int64_t kdst, kend;
+    double scale;
+    int scaled;
 };
 
 // Split-bf16 GEMM on tcgen05: D[m][n] = sum_{(p,q) in products} A_p[m][:] . B_q[n][:]
@@ -196,6 +228,7 @@ cudaError_t launch_gemm_f64(const GemmF64Desc &d, const double *A, const double 
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double *partials, const Grp &cm, const Grp &cn,
                                  double alpha, double beta, double *C, cudaStream_t s);
 cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s);
+cudaError_t launch_rows_multi(const RowsMultiDesc &d, double *C, cudaStream_t s);
 // C(m,n) *= beta over an M x N output addressed by two mixed-radix groups
 cudaError_t launch_scale_grp(int64_t M, int64_t N, const Grp &cm, const Grp &cn, double beta, double *C, cudaStream_t s);
 // the split kernels' double -> float rounding (mine) next to the library's (ref)

@@ -271,6 +271,8 @@ struct Planner {
     int64_t interm_need = kAlign;   // [status word][intermediates...] at the start of the workspace
     int64_t splits_need = 0;        // planes of non-static split operands, kept for reuse within a residual
     bool mixed_all = false;
+    bool kcat_declined = false;    // set by plan_kcat when some members run cheaper one by one
+    std::vector<char> kcat_keep;   // with it: the members that still gain from merging
     std::vector<int> version;       // per tensor: number of statements that wrote it so far
 
     // one split of a tensor version into planes, reusable by later steps
@@ -701,6 +703,422 @@ struct Planner {
         d.beta = beta;
         u.note = "unpack -> " + plan.tensors[out.tensor].name;
         plan.steps.push_back(u);
+        return true;
+    }
+
+    // K concatenation: the statements ms (binary, no permutation operators, all
+    // accumulating into one intermediate, the output's letters split between
+    // their operands at the same positions) as one pass over the output placed
+    // at the last of them:
+    //   C(m, n) += sum_s alpha_s sum_{k in K_s} A_s(m, k) B_s(k, n).
+    // Members that contract the same view of the same larger operand (output
+    // letters at the same output positions) first have their other operands
+    // summed, A B_1 + A B_2 = A (B_1 + B_2), so that operand is read once.  The
+    // result runs on the narrow kernel (FP32 plans, one short free side, the
+    // members' Y blocks fitting shared memory) or as one split-route GEMM whose
+    // planes hold each member's K columns side by side.
+    struct KEff {
+        View a, b;                  // operands (a holds the output's innermost letter)
+        BufRef ar, br;
+        double alpha = 1.0;
+        std::vector<int> mem;       // members (indices into the group)
+        std::set<int> K;            // contracted letters (of the first member)
+        int summed = -1;            // 0 / 1: a / b is the sum of the members' operands
+        int first = 0;              // the member whose letters the view uses
+        std::vector<View> parts;    // summed: each member's operand, relabelled
+        std::vector<double> palpha;
+    };
+
+    bool plan_kcat(const std::vector<const Stmt *> &ms, const std::vector<const std::vector<char> *> &lsps,
+                   const std::vector<int> &sis) {
+        const int nm = (int)ms.size();
+        std::vector<View> outs(nm), As(nm), Bs(nm);
+        std::vector<std::set<int>> Ks(nm);
+        std::vector<double> alphas(nm);
+        for (int i = 0; i < nm; i++) {
+            const Stmt &s = *ms[i];
+            if (!resolve(s.out, true, s.op, *lsps[i], outs[i])) return false;
+            View in[2];
+            for (int k = 0; k < 2; k++)
+                if (!resolve(s.rhs[k], false, 0, *lsps[i], in[k])) return false;
+            // A holds the output's innermost letter (the GEMM rows; epilogue stores coalesce)
+            const int inner = s.out.letters.back();
+            std::set<int> L0(s.rhs[0].letters.begin(), s.rhs[0].letters.end());
+            const int ia = L0.count(inner) ? 0 : 1;
+            As[i] = in[ia];
+            Bs[i] = in[1 - ia];
+            std::set<int> LA(s.rhs[ia].letters.begin(), s.rhs[ia].letters.end());
+            for (int l : s.rhs[1 - ia].letters)
+                if (LA.count(l)) Ks[i].insert(l);
+            alphas[i] = s.factor * (s.op == -1 ? -1.0 : 1.0) * in[0].sign * in[1].sign;
+            last_out = outs[i].tensor;
+        }
+        const View &out0 = outs[0];
+        const Tensor T = plan.tensors[out0.tensor];
+        auto pos_of = [&](int i, int letter) {
+            const auto &L = ms[i]->out.letters;
+            for (size_t p = 0; p < L.size(); p++)
+                if (L[p] == letter) return (int)p;
+            return -1;
+        };
+        // the output positions of the rows (A side) and columns (B side), in the
+        // output's stride order, from the first member
+        auto positions = [&](int i, const View &X) {
+            std::set<int> F;
+            for (int l : ms[i]->out.letters)
+                for (int q : X.idx)
+                    if (q == l) F.insert(l);
+            return F;
+        };
+        const std::vector<int> fa0 = fusable(out0, positions(0, As[0])).order;
+        const std::vector<int> fb0 = fusable(out0, positions(0, Bs[0])).order;
+        std::vector<int> pa, pb;           // output positions of fa0 / fb0
+        for (int l : fa0) pa.push_back(pos_of(0, l));
+        for (int l : fb0) pb.push_back(pos_of(0, l));
+        int64_t Mr = 1, Nr = 1;
+        for (int l : fa0) Mr *= ext_of(As[0], l);
+        for (int l : fb0) Nr *= ext_of(Bs[0], l);
+
+        // ---- shared operands: member j folds into an earlier member i when its
+        // operand on side sd is the same view (output letters at the same output
+        // positions, contracted letters where i has contracted ones) of a tensor
+        // at least 4x the other operand; mp relabels j's letters as i's
+        auto shares = [&](int i, int j, int sd, std::map<int, int> &mp) {
+            const View &Xi = sd == 0 ? As[i] : Bs[i], &Xj = sd == 0 ? As[j] : Bs[j];
+            const View &Yi = sd == 0 ? Bs[i] : As[i], &Yj = sd == 0 ? Bs[j] : As[j];
+            if (Xi.tensor != Xj.tensor || Xi.idx.size() != Xj.idx.size()) return false;
+            if (view_elems(Xi) < 4 * view_elems(Yi) || view_elems(Xj) < 4 * view_elems(Yj)) return false;
+            mp.clear();
+            for (size_t d = 0; d < Xi.idx.size(); d++) {
+                const int li = Xi.idx[d], lj = Xj.idx[d];
+                const int p_i = pos_of(i, li), p_j = pos_of(j, lj);
+                if ((p_i < 0) != (p_j < 0) || p_i != p_j) return false;
+                mp[lj] = li;
+            }
+            std::set<int> got, want(Yi.idx.begin(), Yi.idx.end());
+            for (int l : Yj.idx) {
+                const int p_j = pos_of(j, l);
+                if (p_j >= 0) mp[l] = ms[i]->out.letters[p_j];
+                else if (!mp.count(l)) return false;
+                got.insert(mp[l]);
+            }
+            return got == want && got.size() == Yj.idx.size();
+        };
+        std::vector<int> rep(nm, -1), rep_side(nm, -1);
+        std::vector<std::map<int, int>> relabel(nm);
+        for (int j = 1; j < nm; j++)
+            for (int i = 0; i < j && rep[j] < 0; i++) {
+                if (rep[i] >= 0) continue;
+                for (int sd = 0; sd < 2 && rep[j] < 0; sd++) {
+                    if (rep_side[i] >= 0 && rep_side[i] != sd) continue;
+                    std::map<int, int> mp;
+                    if (shares(i, j, sd, mp)) {
+                        rep[j] = i;
+                        rep_side[i] = sd;
+                        relabel[j] = mp;
+                    }
+                }
+            }
+        std::vector<KEff> eff;
+        for (int i = 0; i < nm; i++) {
+            if (rep[i] >= 0) continue;
+            KEff e;
+            e.a = As[i];
+            e.b = Bs[i];
+            e.ar = tensor_ref(As[i].tensor);
+            e.br = tensor_ref(Bs[i].tensor);
+            e.alpha = alphas[i];
+            e.K = Ks[i];
+            e.first = i;
+            e.mem.push_back(i);
+            for (int j = i + 1; j < nm; j++)
+                if (rep[j] == i) e.mem.push_back(j);
+            if (e.mem.size() > 1) {
+                const int sd = rep_side[i];
+                e.summed = 1 - sd;
+                for (int j : e.mem) {
+                    View y = sd == 0 ? Bs[j] : As[j];
+                    if (j != i)
+                        for (int &l : y.idx) l = relabel[j][l];
+                    e.parts.push_back(y);
+                    e.palpha.push_back(alphas[j]);
+                }
+                const View &y0 = sd == 0 ? Bs[i] : As[i];
+                View w = contiguous_view(y0.idx, y0);
+                (sd == 0 ? e.b : e.a) = w;
+                e.alpha = 1.0;
+            }
+            eff.push_back(e);
+        }
+        const int ne = (int)eff.size();
+        std::vector<int64_t> kx(ne), slot(ne);
+        int64_t ktot = 0;
+        for (int i = 0; i < ne; i++) {
+            kx[i] = 1;
+            for (int l : eff[i].K) kx[i] *= ext_of(eff[i].a, l);
+            slot[i] = align_up(kx[i], 8);
+            ktot += slot[i];
+        }
+        // the members' letters for the first member's row / column / output orders
+        auto mapped = [&](const KEff &e, const std::vector<int> &ps) {
+            std::vector<int> r;
+            for (int p : ps) r.push_back(ms[e.first]->out.letters[p]);
+            return r;
+        };
+        auto sum_steps = [&](KEff &e, int si) {
+            // the summed operand: a contiguous scratch buffer in the first member's layout
+            View &w = e.summed == 0 ? e.a : e.b;
+            BufRef &wr = e.summed == 0 ? e.ar : e.br;
+            wr = scratch(view_elems(w) * esz);
+            for (size_t q = 0; q < e.parts.size(); q++) {
+                const int j = e.mem[q];
+                const View &src = e.parts[q];
+                Step st = accum_step(w, wr, src, tensor_ref(src.tensor), std::vector<Perm>(1, Perm{1.0, {}}),
+                                     e.palpha[q], q == 0 ? 0.0 : 1.0);
+                if (!err.empty()) return false;
+                st.stmt = si;
+                st.note = std::string(q == 0 ? "operand sum = " : "operand sum += ") + plan.tensors[src.tensor].name +
+                          " (statement " + std::to_string(sis[j] + 1) + ")";
+                plan.steps.push_back(st);
+            }
+            return true;
+        };
+        std::string note = "K-concatenated:";
+        for (int i = 0; i < ne; i++) {
+            note += i ? " + " : " ";
+            const KEff &e = eff[i];
+            auto nm_of = [&](int sd) {
+                if (e.summed != sd) return plan.tensors[(sd == 0 ? e.a : e.b).tensor].name;
+                std::string x = "(";
+                for (size_t q = 0; q < e.parts.size(); q++) x += (q ? "+" : "") + plan.tensors[e.parts[q].tensor].name;
+                return x + ")";
+            };
+            note += nm_of(0) + "*" + nm_of(1);
+        }
+        note += " -> " + T.name;
+
+        // ---- the narrow kernel: FP32 plans, one free side of at most 64, the long
+        // side in 32-bit range, every member's Y block in shared memory
+        const bool xa = Mr >= Nr;
+        const int64_t R = xa ? Mr : Nr, NCx = xa ? Nr : Mr;
+        if (plan.precision == 2 && !cplx && ne <= kMaxRowsMembers && NCx >= 1 && NCx <= 64 && R >= 4096 &&
+            R <= 0xffffffffLL) {
+            RowsMultiDesc d{};
+            d.R = R;
+            d.nc = (int)NCx;
+            d.nm = ne;
+            d.f32 = 1;
+            for (int i = 0; i < ne; i++) d.m[i].K = (int)kx[i];
+            if (rows_multi_smem_bytes(d) > 0 && rows_multi_smem_bytes(d) <= 96 * 1024) {
+                scratch_need = 0;
+                for (auto &e : eff)
+                    if (e.summed >= 0 && !sum_steps(e, sis.back())) return false;
+                Step g;
+                g.kind = StepKind::GEMM;
+                g.stmt = sis.back();
+                g.rows = true;
+                g.kstmts = sis;
+                g.gemm.M = Mr;
+                g.gemm.N = Nr;
+                g.gemm.K = 0;
+                g.gemm.splitk = 1;
+                g.gemm.f32 = 1;
+                const View &X0 = xa ? eff[0].a : eff[0].b, &Y0 = xa ? eff[0].b : eff[0].a;
+                d.cr = make_grp(mapped(eff[0], xa ? pa : pb), X0, outs[eff[0].first]);
+                d.cc = make_grp(mapped(eff[0], xa ? pb : pa), Y0, outs[eff[0].first]);
+                for (int i = 0; i < ne; i++) {
+                    const KEff &e = eff[i];
+                    const View &X = xa ? e.a : e.b, &Y = xa ? e.b : e.a;
+                    const std::vector<int> rord = mapped(e, xa ? pa : pb), cord = mapped(e, xa ? pb : pa);
+                    const std::vector<int> kord = fusable(X, e.K).order;
+                    RowsMember &m = d.m[i];
+                    m.xr = make_grp(rord, X, X);
+                    m.xk = make_grp(kord, X, X);
+                    m.yk = make_grp(kord, Y, Y);
+                    m.yc = make_grp(cord, Y, Y);
+                    m.alpha = e.alpha;
+                    KMember mb;
+                    mb.stmt = sis[e.first];
+                    mb.a = xa ? e.ar : e.br;     // X
+                    mb.b = xa ? e.br : e.ar;     // Y
+                    mb.flops = 2.0 * (double)Mr * (double)Nr * (double)kx[i];
+                    g.flops += mb.flops;
+                    g.gemm.K += kx[i];
+                    g.kcat.push_back(mb);
+                }
+                if (!err.empty()) return false;
+                for (int i = 0; i < nm; i++)
+                    if (rep[i] >= 0) {
+                        // folded members: their flops as if run on their own
+                        int64_t k = 1;
+                        for (int l : Ks[i]) k *= ext_of(As[i], l);
+                        g.flops += 2.0 * (double)Mr * (double)Nr * (double)k;
+                    }
+                g.rm = d;
+                g.rg.red = 0;
+                g.cands = {{0, 1, 0}, {0, 1, 1}};
+                g.out = tensor_ref(out0.tensor);
+                g.note = note;
+                plan.flops += g.flops;
+                plan.steps.push_back(g);
+                return true;
+            }
+        }
+
+        // ---- the split route: HBM bytes of the merged GEMM against the members
+        // run one by one.  The merge saves a read-modify-write pass over the
+        // output per statement and costs the planes of the whole padded K
+        // (written by the splits, read by the GEMM).  Alone, a statement takes
+        // the split route on the terms of plan_stmt (large, not narrow, tiles
+        // filled), and an integral (or integral-only) operand's planes are then
+        // cached once per solve, so only their read counts.  Effective members
+        // that cost more merged than alone are left out (kcat_keep); the rest
+        // merge if they still save bytes.
+        const int np = plan.precision == 3 ? 3 : 2;
+        {
+            const double out_rmw = 16.0 * (double)Mr * (double)Nr;
+            const double rows_x[2] = {(double)Mr, (double)Nr};
+            double merged = out_rmw + 4.0 * np * (double)(Mr + Nr) * (double)(align_up(ktot, 64) - ktot), alone = 0.0;
+            kcat_keep.assign(nm, 1);
+            int kept = 0;
+            auto alone_bytes = [&](const View &A, const View &B, int64_t K) {
+                const View *ops[2] = {&A, &B};
+                const bool narrow = K <= 64 && std::min(Mr, Nr) >= 2 && std::min(Mr, Nr) <= 64 && std::max(Mr, Nr) >= 4096;
+                const int64_t bn = Nr <= 64 ? 64 : Nr <= 128 ? 128 : 256;
+                const double eff_t = (double)Mr * (double)Nr * (double)K /
+                                     ((double)align_up(Mr, 128) * (double)align_up(Nr, bn) * (double)align_up(K, 64));
+                const bool split = 2.0 * (double)Mr * (double)Nr * (double)K >= 2.0e8 && Mr > 1 && Nr > 1 && K > 1 &&
+                                   !(narrow && eff_t < 0.5) && eff_t >= 0.15;
+                double a_i = out_rmw;
+                for (int x = 0; x < 2; x++) {
+                    const double bytes = 8.0 * (double)view_elems(*ops[x]);
+                    const double planes = 2.0 * np * rows_x[x] * (double)align_up(K, 64);
+                    const Tensor &tx = plan.tensors[ops[x]->tensor];
+                    const bool cached = tx.kind == TKind::INTEGRAL || tx.static_data;
+                    a_i += !split ? bytes : cached ? planes : bytes + 2.0 * planes;
+                }
+                return a_i;
+            };
+            for (int i = 0; i < ne; i++) {
+                const KEff &e = eff[i];
+                double m_i = 4.0 * np * (double)(Mr + Nr) * (double)slot[i], a_i = 0.0;
+                for (int j : e.mem) {
+                    int64_t k = 1;
+                    for (int l : Ks[j]) k *= ext_of(As[j], l);
+                    a_i += alone_bytes(As[j], Bs[j], k);
+                    m_i += 8.0 * (double)(view_elems(As[j]) + view_elems(Bs[j]));
+                }
+                if (e.summed >= 0) {
+                    // the shared operand is read once, the summed one written and read
+                    const View &sh = e.summed == 0 ? e.b : e.a, &sm = e.summed == 0 ? e.a : e.b;
+                    m_i -= 8.0 * (double)view_elems(sh) * (double)(e.mem.size() - 1);
+                    m_i += 16.0 * (double)view_elems(sm);
+                }
+                if (m_i >= a_i) {
+                    for (int j : e.mem) kcat_keep[j] = 0;
+                    continue;
+                }
+                kept += (int)e.mem.size();
+                merged += m_i;
+                alone += a_i;
+            }
+            if (kept < nm || merged >= alone) {
+                if (merged >= alone) kcat_keep.assign(nm, 0);
+                kcat_declined = true;
+                return true;
+            }
+        }
+        scratch_need = 0;
+        for (auto &e : eff)
+            if (e.summed >= 0 && !sum_steps(e, sis.back())) return false;
+        Step g;
+        g.kind = StepKind::GEMM;
+        g.stmt = sis.back();
+        g.mixed = true;
+        g.kstmts = sis;
+        TcGemmDesc &t = g.tc;
+        t.M = Mr;
+        t.N = Nr;
+        t.bn = Nr <= 64 ? 64 : (Nr <= 128 || np == 3) ? 128 : 256;
+        const int bn_max = np == 3 ? (Nr <= 64 ? 64 : 128) : (Nr <= 64 ? 64 : Nr <= 128 ? 128 : 256);
+        t.Mp = align_up(Mr, 128);
+        t.Np = align_up(Nr, bn_max);
+        t.Kp = align_up(ktot, 64);
+        const int64_t tiles = (t.Mp / 128) * ((Nr + t.bn - 1) / t.bn), kblocks = t.Kp / 64;
+        t.splitk = 1;
+        if (tiles < 148 && kblocks >= 8) {
+            int64_t sk = std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
+            if (sk > 1) t.splitk = (int)sk;
+        }
+        int64_t skmax = t.splitk;
+        for (int bn : {64, 128, 256}) {
+            if (bn > bn_max) continue;
+            for (int sk : {1, 2, 4, 8, 16})
+                if (sk == 1 || (sk <= kblocks / 4 && sk * Mr * Nr * 8 <= (int64_t)512 << 20)) {
+                    g.cands.push_back({bn, sk, 0});
+                    skmax = std::max<int64_t>(skmax, sk);
+                }
+            g.cands.push_back({bn, 1, 1});       // accumulating: the reduction epilogue
+        }
+        const std::array<int, 3> planned{t.bn, t.splitk, 0};
+        if (std::find(g.cands.begin(), g.cands.end(), planned) == g.cands.end()) g.cands.push_back(planned);
+        if (skmax > 1) g.partials = scratch(skmax * Mr * Nr * 8);
+        t.nplanes_a = t.nplanes_b = np;
+        if (np == 2) {
+            const int pa_[3] = {0, 0, 1}, pb_[3] = {0, 1, 0};
+            t.nprod = 3;
+            for (int k = 0; k < 3; k++) { t.prod_a[k] = pa_[k]; t.prod_b[k] = pb_[k]; }
+        } else {
+            const int pa_[6] = {0, 0, 1, 0, 1, 2}, pb_[6] = {0, 1, 0, 2, 1, 0};
+            t.nprod = 6;
+            for (int k = 0; k < 6; k++) { t.prod_a[k] = pa_[k]; t.prod_b[k] = pb_[k]; }
+        }
+        t.cm = make_grp(fa0, As[0], out0);
+        t.cn = make_grp(fb0, Bs[0], out0);
+        t.alpha = 1.0;                            // each member's factor rides on its A split
+        t.beta = 1.0;
+        g.out = tensor_ref(out0.tensor);
+        int64_t koff = 0;
+        for (int i = 0; i < ne; i++) {
+            const KEff &e = eff[i];
+            KMember mb;
+            mb.stmt = sis[e.first];
+            mb.a = e.ar;
+            mb.b = e.br;
+            const std::vector<int> fa = mapped(e, pa), fb = mapped(e, pb);
+            const View &big = view_elems(e.a) >= view_elems(e.b) ? e.a : e.b;
+            const std::vector<int> korder = fusable(big, e.K).order;
+            const int64_t kend = i == ne - 1 ? t.Kp - koff : slot[i];
+            SplitDesc &sa = mb.split_a;
+            sa.R = Mr; sa.K = kx[i]; sa.Rp = Mr; sa.Kp = t.Kp; sa.nplanes = np;
+            sa.gr = make_grp(fa, e.a, e.a);
+            sa.gk = make_grp(korder, e.a, e.a);
+            sa.kdst = koff; sa.kend = kend;
+            sa.scaled = e.alpha != 1.0;
+            sa.scale = e.alpha;
+            SplitDesc &sb = mb.split_b;
+            sb.R = Nr; sb.K = kx[i]; sb.Rp = Nr; sb.Kp = t.Kp; sb.nplanes = np;
+            sb.gr = make_grp(fb, e.b, e.b);
+            sb.gk = make_grp(korder, e.b, e.b);
+            sb.kdst = koff; sb.kend = kend;
+            if (!err.empty()) return false;
+            mb.flops = 2.0 * (double)Mr * (double)Nr * (double)kx[i];
+            koff += slot[i];
+            g.kcat.push_back(mb);
+        }
+        for (int i = 0; i < nm; i++) {
+            int64_t k = 1;
+            for (int l : Ks[i]) k *= ext_of(As[i], l);
+            g.flops += 2.0 * (double)Mr * (double)Nr * (double)k;
+        }
+        g.note = note;
+        // the merged planes are read by this step only: they live in the
+        // statement arena (rebased after planning), shared with every other step
+        g.planes_a_off = scratch(planes_bytes(Mr, t.Kp, np)).off;
+        g.planes_b_off = scratch(planes_bytes(Nr, t.Kp, np)).off;
+        plan.flops += g.flops;
+        plan.flops_mixed += g.flops;
+        plan.steps.push_back(g);
         return true;
     }
 
@@ -1178,6 +1596,78 @@ static void fuse_copies(Plan &plan) {
     plan.steps.swap(out);
 }
 
+// K-concatenation groups.  A member is a binary contraction without permutation
+// operators and without declared pairs that accumulates (+= / -=) into an
+// intermediate defined earlier.  Its key is the output name and the set of
+// output positions carried by the operand holding the output's innermost
+// letter.  A group closes when a statement reads the output, assigns it again,
+// or writes a tensor one of its members reads (so moving every member to the
+// group's last position changes no operand); groups of one are dropped.
+static void find_kcat_groups(const std::vector<Stmt> &stmts, const std::vector<std::vector<std::string>> &toks,
+                             std::vector<std::vector<int>> &groups) {
+    auto reserved = [](const std::string &n) {
+        return n.empty() || n[0] == '%' || n == "V" || n == "v" || n[0] == 'T' || n[0] == 't' || n[0] == 'R' ||
+               n[0] == 'r';
+    };
+    struct Open {
+        std::string out;
+        uint32_t key;
+        std::vector<int> members;
+        std::set<std::string> reads;
+    };
+    std::vector<Open> open;
+    std::set<std::string> defined;
+    auto close_if = [&](auto pred) {
+        for (size_t g = 0; g < open.size();) {
+            if (pred(open[g])) {
+                if (open[g].members.size() >= 2) groups.push_back(open[g].members);
+                open.erase(open.begin() + g);
+            } else {
+                g++;
+            }
+        }
+    };
+    for (size_t k = 0; k < stmts.size(); k++) {
+        const Stmt &s = stmts[k];
+        const std::string &on = s.out.name;
+        // a statement reading a grouped output, or assigning it, closes its groups
+        for (const Ref &r : s.rhs) close_if([&](const Open &o) { return o.out == r.name; });
+        if (s.op == 0) close_if([&](const Open &o) { return o.out == on; });
+        // writing a tensor a member reads closes that group
+        close_if([&](const Open &o) { return o.reads.count(on) > 0; });
+        bool member = s.op != 0 && s.rhs.size() == 2 && s.perms.empty() && !reserved(on) && defined.count(on) &&
+                      s.rhs[0].pairs.empty() && s.rhs[1].pairs.empty() && s.rhs[0].name != on &&
+                      s.rhs[1].name != on && s.out.letters.size() <= 32;
+        uint32_t key = 0;
+        if (member) {
+            const int inner = s.out.letters.back();
+            const bool a0 = std::find(s.rhs[0].letters.begin(), s.rhs[0].letters.end(), inner) != s.rhs[0].letters.end();
+            const Ref &A = s.rhs[a0 ? 0 : 1], &B = s.rhs[a0 ? 1 : 0];
+            bool contracted = false;
+            for (int l : A.letters)
+                if (std::find(B.letters.begin(), B.letters.end(), l) != B.letters.end()) contracted = true;
+            member = contracted;
+            for (size_t p = 0; p < s.out.letters.size(); p++)
+                if (std::find(A.letters.begin(), A.letters.end(), s.out.letters[p]) != A.letters.end())
+                    key |= 1u << p;
+        }
+        if (member) {
+            Open *g = nullptr;
+            for (auto &o : open)
+                if (o.out == on && o.key == key) g = &o;
+            if (!g) {
+                open.push_back(Open{on, key, {}, {}});
+                g = &open.back();
+            }
+            g->members.push_back((int)k);
+            for (const Ref &r : s.rhs) g->reads.insert(r.name);
+        }
+        if (s.op == 0) defined.insert(on);
+        (void)toks;
+    }
+    close_if([](const Open &) { return true; });
+}
+
 bool build_plan(const std::string &text, int o, int v, int dtype, int precision, Plan &plan, std::string &err,
                 int flags) {
     plan = Plan();
@@ -1192,6 +1682,9 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     std::string line;
     int lineno = 0;
     int64_t max_scratch = 0;
+    std::vector<Stmt> stmts;
+    std::vector<std::vector<std::string>> toks;
+    std::vector<std::vector<char>> spcs;
     while (std::getline(in, line)) {
         lineno++;
         size_t h = line.find('#');
@@ -1209,16 +1702,68 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
             err = "line " + std::to_string(lineno) + ": " + e;
             return false;
         }
-        int si = (int)plan.stmt_text.size();
         plan.stmt_text.push_back(line);
-        if (!P.plan_stmt(st, spaces, si)) {
-            err = "line " + std::to_string(lineno) + ": " + P.err;
-            return false;
-        }
-        P.version[P.last_out]++;   // the statement's output has a new version
-        max_scratch = std::max(max_scratch, P.scratch_need);
+        stmts.push_back(st);
+        toks.push_back(tokens);
+        spcs.push_back(spaces);
     }
     if (plan.stmt_text.empty()) { err = "empty contraction list"; return false; }
+    // K-concatenation groups (split-route precisions, real): statements that
+    // accumulate into the same intermediate with the output's letters split
+    // between their operands at the same positions
+    std::vector<int> group_of(stmts.size(), -1);
+    std::vector<std::vector<int>> groups;
+    if ((plan.precision == 2 || plan.precision == 3) && dtype == 0 && !(flags & 2)) find_kcat_groups(stmts, toks, groups);
+    for (size_t g = 0; g < groups.size(); g++)
+        for (int si : groups[g]) group_of[si] = (int)g;
+    for (size_t k = 0; k < stmts.size(); k++) {
+        const int si = (int)k;
+        bool ok = true;
+        if (group_of[si] >= 0) {
+            if (si != groups[group_of[si]].back()) continue;   // planned with the group's last member
+            // every member may run at the group's last position (the grouping
+            // rule): members left out of the merge are planned there one by
+            // one, in list order, and the rest merged again until it holds
+            std::vector<int> gm = groups[group_of[si]];
+            while (ok) {
+                std::vector<const Stmt *> ms;
+                std::vector<const std::vector<char> *> ls;
+                for (int m : gm) { ms.push_back(&stmts[m]); ls.push_back(&spcs[m]); }
+                ok = P.plan_kcat(ms, ls, gm);
+                if (!ok) break;
+                if (!P.kcat_declined) {
+                    P.version[P.last_out] += (int)gm.size();
+                    break;
+                }
+                P.kcat_declined = false;
+                std::vector<int> rest;
+                for (size_t q = 0; ok && q < gm.size(); q++) {
+                    if (P.kcat_keep[q]) { rest.push_back(gm[q]); continue; }
+                    ok = P.plan_stmt(stmts[gm[q]], spcs[gm[q]], gm[q]);
+                    if (ok) P.version[P.last_out]++;
+                    else k = gm[q];
+                }
+                if (!ok) break;
+                if (rest.size() < 2) {
+                    for (size_t q = 0; ok && q < rest.size(); q++) {
+                        ok = P.plan_stmt(stmts[rest[q]], spcs[rest[q]], rest[q]);
+                        if (ok) P.version[P.last_out]++;
+                        else k = rest[q];
+                    }
+                    break;
+                }
+                gm = rest;
+            }
+        } else {
+            ok = P.plan_stmt(stmts[k], spcs[k], si);
+            if (ok) P.version[P.last_out]++;   // the statement's output has a new version
+        }
+        if (!ok) {
+            err = "line " + std::to_string(stmts[k].line) + ": " + P.err;
+            return false;
+        }
+        max_scratch = std::max(max_scratch, P.scratch_need);
+    }
     fuse_copies(plan);
     // workspace: [status word][intermediates][scratch arena][static plane cache]
     plan.flags_off = 0;
@@ -1234,14 +1779,18 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     plan.cache_bytes = P.cache_need;
     off += P.cache_need;
     plan.ws_bytes = off;
+    auto place = [&](BufRef *r) {
+        if (r->where == BufRef::INTEG && r->slot >= 0 && r->slot < 7) plan.integ_used[r->slot] = true;
+        if (r->where == BufRef::WS && r->slot == 1) { r->off += plan.scratch_off; r->slot = 0; }
+        if (r->where == BufRef::WS && r->slot == 2) { r->off += plan.cache_off; r->slot = 0; }
+    };
     for (auto &st : plan.steps) {
-        for (BufRef *r : {&st.a, &st.b, &st.c})
-            if (r->where == BufRef::INTEG && r->slot >= 0 && r->slot < 7) plan.integ_used[r->slot] = true;
-        for (BufRef *r : {&st.out, &st.a, &st.b, &st.c, &st.partials}) {
-            if (r->where == BufRef::WS && r->slot == 1) { r->off += plan.scratch_off; r->slot = 0; }
-            if (r->where == BufRef::WS && r->slot == 2) { r->off += plan.cache_off; r->slot = 0; }
-        }
-        if (st.mixed) {
+        for (BufRef *r : {&st.out, &st.a, &st.b, &st.c, &st.partials}) place(r);
+        for (KMember &m : st.kcat) { place(&m.a); place(&m.b); }
+        if (st.mixed && !st.kcat.empty()) {
+            st.planes_a_off += plan.scratch_off;
+            st.planes_b_off += plan.scratch_off;
+        } else if (st.mixed) {
             st.planes_a_off += st.a_static ? plan.cache_off : plan.splits_off;
             st.planes_b_off += st.b_static ? plan.cache_off : plan.splits_off;
         }
@@ -1296,6 +1845,11 @@ std::string describe_plan(const Plan &plan) {
                                         : s.kind == StepKind::ACCUM ? "accum" : s.kind == StepKind::PACK ? "pack"
                                         : s.kind == StepKind::UNPACK ? "unpack" : "zero")
            << "\",\"note\":\"" << s.note << "\"";
+        if (!s.kstmts.empty()) {
+            os << ",\"stmts\":[";
+            for (size_t q = 0; q < s.kstmts.size(); q++) os << (q ? "," : "") << s.kstmts[q];
+            os << "]";
+        }
         if (s.kind == StepKind::GEMM && !s.mixed) {
             os << ",\"M\":" << s.gemm.M << ",\"N\":" << s.gemm.N << ",\"K\":" << s.gemm.K << ",\"flops\":" << s.flops
                << ",\"splitk\":" << s.gemm.splitk << ",\"red\":" << (s.rows ? s.rg.red : s.gemm.red)
@@ -1309,7 +1863,12 @@ std::string describe_plan(const Plan &plan) {
             os << ",\"cn\":";
             grp_json(os, s.gemm.cn);
         } else if (s.kind == StepKind::GEMM) {
-            os << ",\"M\":" << s.tc.M << ",\"N\":" << s.tc.N << ",\"K\":" << s.split_a.K << ",\"flops\":" << s.flops
+            int64_t K = s.split_a.K;
+            if (!s.kcat.empty()) {
+                K = 0;
+                for (const KMember &m : s.kcat) K += m.split_a.K;
+            }
+            os << ",\"M\":" << s.tc.M << ",\"N\":" << s.tc.N << ",\"K\":" << K << ",\"flops\":" << s.flops
                << ",\"products\":" << s.tc.nprod << ",\"a_static\":" << (s.a_static ? 1 : 0)
                << ",\"b_static\":" << (s.b_static ? 1 : 0) << ",\"alpha\":" << s.tc.alpha << ",\"beta\":" << s.tc.beta
                << ",\"Mp\":" << s.tc.Mp << ",\"Np\":" << s.tc.Np << ",\"Kp\":" << s.tc.Kp << ",\"bn\":" << s.tc.bn

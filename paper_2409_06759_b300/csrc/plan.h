@@ -48,6 +48,20 @@ struct View {
 
 enum class StepKind { ZERO, ACCUM, GEMM, PACK, UNPACK };
 
+// One contraction of a K-concatenated step: several statements that
+// accumulate into the same output with the same split of its indices between
+// their operands run as one pass over the output.  On the split route each
+// member's operands fill its own K columns of the shared planes (its factor
+// rides on the A split); on the narrow kernel a and b are its X and Y.  A
+// member may stand for several statements whose shared operand multiplies the
+// sum of their other operands.
+struct KMember {
+    int stmt = -1;
+    BufRef a, b;
+    SplitDesc split_a{}, split_b{};
+    double flops = 0.0;
+};
+
 struct Step {
     StepKind kind;
     int stmt = -1;              // statement index (0-based)
@@ -70,6 +84,9 @@ struct Step {
     UnpackDesc up{};                             // UNPACK: out (antisymmetric) from packed a
     bool rows = false;                           // narrow GEMM (one thread per row, operands in place)
     RowsGemmDesc rg{};
+    std::vector<KMember> kcat;                   // K-concatenated members (a, b, split_a/b unused)
+    std::vector<int> kstmts;                     // the statements a K-concatenated step carries
+    RowsMultiDesc rm{};                          // K-concatenated on the narrow kernel (rows = true)
     double flops = 0.0;
     std::string note;
 };

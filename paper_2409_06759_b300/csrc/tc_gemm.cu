@@ -130,12 +130,14 @@ __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, cons
     const int64_t plane_elems = d.Rp * d.Kp;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * 8;
+    const int64_t kcols = d.kend ? d.kend : d.Kp;       // plane columns this split fills
+    const double sc = d.scaled ? d.scale : 1.0;
     // work items: (row, 1024-column span); a warp takes one item at a time
-    const int64_t spans = (d.Kp + 1023) / 1024;
+    const int64_t spans = (kcols + 1023) / 1024;
     for (int64_t it = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < d.Rp * spans; it += nwarps) {
         const int64_t r = it / spans;
         const int64_t kspan = (it - r * spans) * 1024;
-        const int64_t kend = kspan + 1024 < d.Kp ? kspan + 1024 : d.Kp;
+        const int64_t kend = kspan + 1024 < kcols ? kspan + 1024 : kcols;
         const bool row_ok = r < d.R;
         const int64_t roff = row_ok ? row_offset(d, r) : 0;
         for (int64_t k0 = kspan + (int64_t)lane * 8; k0 < kend; k0 += 256) {
@@ -149,18 +151,19 @@ __global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, cons
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const double2 v2 = __ldg(src + j);
-                    split3(v2.x, h[2 * j], m[2 * j], l[2 * j]);
-                    split3(d.cplx ? sy * v2.y : v2.y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
+                    split3(d.scaled ? v2.x * sc : v2.x, h[2 * j], m[2 * j], l[2 * j]);
+                    const double y = d.cplx ? sy * v2.y : v2.y;
+                    split3(d.scaled ? y * sc : y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
                     const int64_t k = k0 + j;
                     const double val = (row_ok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
-                    split3(val, h[j], m[j], l[j]);
+                    split3(d.scaled ? val * sc : val, h[j], m[j], l[j]);
                 }
             }
-            __nv_bfloat16 *p0 = planes + r * d.Kp + k0;
+            __nv_bfloat16 *p0 = planes + r * d.Kp + d.kdst + k0;
             *reinterpret_cast<uint4 *>(p0) = *reinterpret_cast<const uint4 *>(h);
             *reinterpret_cast<uint4 *>(p0 + plane_elems) = *reinterpret_cast<const uint4 *>(m);
             if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = *reinterpret_cast<const uint4 *>(l);
@@ -223,6 +226,8 @@ __global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, c
     __shared__ float tile[64][65];
     __shared__ int64_t ro[64], ko[64];
     const int64_t plane_elems = d.Rp * d.Kp;
+    const int64_t kcols = d.kend ? d.kend : d.Kp;       // plane columns this split fills
+    const double sc = d.scaled ? d.scale : 1.0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t r0 = (int64_t)(t % rtiles) * 64, k0 = (int64_t)(t / rtiles) * 64;
@@ -255,6 +260,10 @@ __global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, c
                     v[2 * i + h] = ok ? __ldg(x + ow + oo) : 0.0;
             }
         }
+        if (d.scaled) {
+#pragma unroll
+            for (int e = 0; e < 16; e++) v[e] *= sc;
+        }
 #pragma unroll
         for (int i = 0; i < 8; i++)
 #pragma unroll
@@ -274,8 +283,8 @@ __global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, c
             for (int j = 0; j < 8; j++) f[j] = tile[rr][kk + j];
             uint4 H, M, L;
             split8<NPL>(f, H, M, L);
-            if (r0 + rr < d.Rp) {
-                __nv_bfloat16 *p0 = planes + (r0 + rr) * d.Kp + k0 + kk;
+            if (r0 + rr < d.Rp && k0 + kk < kcols) {
+                __nv_bfloat16 *p0 = planes + (r0 + rr) * d.Kp + d.kdst + k0 + kk;
                 *reinterpret_cast<uint4 *>(p0) = H;
                 *reinterpret_cast<uint4 *>(p0 + plane_elems) = M;
                 if (NPL == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = L;
@@ -515,7 +524,11 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
               d.gk.ext[d.gk.nd - 1] % (d.cplx ? 4 : 8) == 0 && ((uintptr_t)x & 15) == 0;
     for (int q = 0; q + 1 < d.gk.nd; q++) vec &= (d.gk.str[q] % 2) == 0;
     for (int q = 0; q < d.gr.nd; q++) vec &= (d.gr.str[q] % 2) == 0;
-    const int64_t rtiles = (d.Rp + 63) / 64, ntiles = rtiles * (d.Kp / 64);
+    // K concatenation: the split fills plane columns [kdst, kdst + kcols) in runs
+    // of eight (16-byte stores), so both stay multiples of 8
+    const int64_t kcols = d.kend ? d.kend : d.Kp;
+    if (d.kdst % 8 || kcols % 8 || d.kdst + kcols > d.Kp || kcols < d.K) return cudaErrorInvalidValue;
+    const int64_t rtiles = (d.Rp + 63) / 64, ntiles = rtiles * ((kcols + 63) / 64);
     if (!(vec && d.K >= 512) && ntiles <= 0xffffffffLL) {
         // lanes along K when K's innermost digit is the unit stride, or when
         // neither side has one and K's innermost stride is the smaller
@@ -529,7 +542,7 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
     // vec: innermost K digit contiguous with an extent that keeps the 8-column
     // runs inside it (4 complex elements when stacked), every other stride even
     // (16-byte aligned double2), base aligned; not for embedded
-    const int64_t items = d.Rp * ((d.Kp + 1023) / 1024);
+    const int64_t items = d.Rp * ((kcols + 1023) / 1024);
     int64_t blocks = (items + 7) / 8;
     if (blocks > 148 * 16) blocks = 148 * 16;
     split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, x, (__nv_bfloat16 *)planes, vec);

@@ -160,7 +160,11 @@ def route_constants(describe: dict, use_splitk: bool = True) -> dict:
     * FP64 routes: (2 + K)*2^-53; copies, permutes and antisymmetrisers: 2^-52.
     Complex statements run as real GEMMs of doubled K (4M embedding), so K
     doubles.  A statement with several steps takes the largest constant.
-    use_splitk=False takes K' = K (the bound of every split-K candidate)."""
+    use_splitk=False takes K' = K (the bound of every split-K candidate).
+    A K-concatenated step (several accumulating statements summed in one GEMM,
+    its "stmts") gives each member the constant of the whole K: the GEMM's
+    accumulation error is bounded by that constant times the sum over all
+    members of |factor| sum_k |a||b|, which is the sum of the members' bounds."""
     cplx = describe.get("dtype") == 1
     out = {}
     for st in describe["steps"]:
@@ -178,7 +182,8 @@ def route_constants(describe: dict, use_splitk: bool = True) -> dict:
             c = (2 + k) * U64
         else:
             c = 2 * U64
-        out[st["stmt"]] = max(out.get(st["stmt"], 0.0), c)
+        for si in st.get("stmts", [st["stmt"]]):
+            out[si] = max(out.get(si, 0.0), c)
     return out
 
 

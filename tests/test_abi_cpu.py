@@ -267,3 +267,55 @@ def test_slices_plan_routes(cc):
     # six bf16 planes and one int32 exponent per row of the 40000 x 40000 block
     assert d["cache_bytes"] >= 6 * 40000 * 40000 * 2 + 40000 * 4
     assert lad["flops"] == 2.0 * 40000 * 1600 * 40000
+
+
+def test_k_concatenated_steps(cc):
+    """Split-route plans merge accumulating statements into one pass over their
+    output when the output's letters fall on the same operand positions (K
+    concatenation, on the split route or the narrow kernel): every member
+    accumulates into the step's output, each statement is planned once, the
+    merged K is at most the members' total, the FLOP count is unchanged;
+    FP64, exact-slice and complex plans, and kconcat=False, merge nothing;
+    the cached ladder block is never re-split into a merged step."""
+    text = cc.load_list("ccsdt")
+    stmts = [l.split("#")[0].strip() for l in text.splitlines() if l.split("#")[0].strip()]
+    for prec in ("bf16x3", "bf16x6"):
+        d = cc.cc_plan_create(text, 8, 64, precision=prec).describe()
+        ref = cc.cc_plan_create(text, 8, 64, precision=prec, kconcat=False).describe()
+        assert not any("stmts" in st for st in ref["steps"])
+        assert d["flops"] == pytest.approx(ref["flops"], rel=1e-12)
+        merged = [st for st in d["steps"] if "stmts" in st]
+        # the sums of operands that several members share run as copies before their step
+        sums = [st for st in d["steps"] if st["note"].startswith("operand sum")]
+        assert all(st["kind"] == "accum" for st in sums) and len(sums) >= 10
+        assert len(merged) >= 8 and len(d["steps"]) - len(sums) < len(ref["steps"]) - 40
+        seen = {}
+        for st in d["steps"]:
+            if st in sums:
+                continue
+            for si in st.get("stmts", [st["stmt"]]):
+                seen.setdefault(si, set()).add(id(st))
+        assert sorted(seen) == list(range(len(stmts)))
+        kref = {}
+        for st in ref["steps"]:
+            if st["kind"].startswith("gemm"):
+                kref[st["stmt"]] = st["K"]
+        for st in merged:
+            out = st["note"].rsplit("-> ", 1)[1]
+            assert len(st["stmts"]) >= 2 and st["stmts"] == sorted(st["stmts"])
+            for si in st["stmts"]:
+                lhs, rhs = stmts[si].split("=", 1)
+                assert lhs.rstrip("+-").strip().startswith(out + "[") and lhs.rstrip()[-1] in "+-", stmts[si]
+                assert "P(" not in rhs
+                assert seen[si] == {id(st)}          # a member runs in its merged step only
+            # statements that share an operand contract it once with the sum of their
+            # other operands: K is at most the members' total
+            assert 0 < st["K"] <= sum(kref[si] for si in st["stmts"])
+            if st["kind"] == "gemm_bf16split":
+                assert st["Kp"] % 64 == 0 and st["Kp"] >= st["K"]
+    for prec, dt in (("fp64", cc.CC_F64), ("slices", cc.CC_F64), ("bf16x3", cc.CC_C128)):
+        d = cc.cc_plan_create(text, 6, 30, dtype=dt, precision=prec).describe()
+        assert not any("stmts" in st for st in d["steps"]), (prec, dt)
+    lad = cc.cc_plan_create(cc.load_list("ccsd_vvvv"), 40, 200, precision="bf16x3").describe()
+    step = next(st for st in lad["steps"] if "V_vvvv*tau" in st["note"])
+    assert "stmts" not in step and step["note"] == "V_vvvv*tau -> Z2"

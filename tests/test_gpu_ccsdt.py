@@ -119,18 +119,21 @@ def _reference_with_bounds(ccm, o, v, s, B, t1, t2, t3, plans, n_def=40, seed=0)
     return vals, bounds
 
 
+@pytest.mark.parametrize("kconcat", [True, False])
 @pytest.mark.parametrize("prec,rel", [("bf16x3", 1e-4), ("bf16x6", 1e-6)])
-def test_ccsdt_split_route_matches_reference(cc, prec, rel):
+def test_ccsdt_split_route_matches_reference(cc, prec, rel, kconcat):
     """Every R1, R2, R3 element of the all-tensor-core route within the
-    element-wise bound of its routes; the FP64 route within 1e-9; the error
-    norm against the FP64 route as an extra check."""
+    element-wise bound of its routes (accumulating statements merged into one
+    GEMM each, or one GEMM per statement); the FP64 route within 1e-9; the
+    error norm against the FP64 route as an extra check."""
     ccm, engine = cc
     o, v = 4, 20
     s, B, t1, t2, t3 = case(o, v, 4, L=8, tscale=0.05)
     dsys = engine.DeviceSystem(o, v, s.eps_occ, s.eps_vir, B, device=DEV)
     T = (dev(t1), dev(t2), dev(t3))
     fe = engine.Engine(dsys, list_name="ccsdt")
-    me = engine.Engine(dsys, list_name="ccsdt", precision=prec, route_all=True)
+    me = engine.Engine(dsys, list_name="ccsdt", precision=prec, route_all=True, kconcat=kconcat)
+    assert any("stmts" in st for st in me.plan.describe()["steps"]) == kconcat
     f = fe.residual(T[0], T[1], t3=T[2])
     m = me.residual(T[0], T[1], t3=T[2])
     torch.cuda.synchronize()
@@ -171,11 +174,13 @@ def test_ccsdt_full_size_sampled_elements(cc):
     assert np.abs(g + g.transpose(0, 1, 2, 4, 3, 5)).max() <= 1e-13 * scale
 
 
-def test_ccsdt_default_mixed_plan_matches_reference(cc):
+@pytest.mark.parametrize("kconcat", [True, False])
+def test_ccsdt_default_mixed_plan_matches_reference(cc, kconcat):
     """The bench's mixed plan (tensor-core route for the contractions that fill
-    128 x bn x 64 tiles, FP32 arithmetic for the skinny rank-o updates of T3),
-    o=6 v=36: every element within the element-wise bound of its routes, and
-    the error norm against the FP64 plan as an extra check."""
+    128 x bn x 64 tiles, FP32 arithmetic for the skinny rank-o updates of T3,
+    accumulating statements K-concatenated into one GEMM where that saves
+    output passes), o=6 v=36: every element within the element-wise bound of
+    its routes, and the error norm against the FP64 plan as an extra check."""
     ccm, engine = cc
     o, v = 6, 36
     s, B, t1, t2, t3 = case(o, v, 5, L=16, scale=1.0, tscale=0.01)
@@ -183,7 +188,8 @@ def test_ccsdt_default_mixed_plan_matches_reference(cc):
     T = (dev(t1), dev(t2), dev(t3))
     f = engine.Engine(dsys, list_name="ccsdt").residual(T[0], T[1], t3=T[2])
     f = [x.cpu() for x in f]
-    mixed = engine.Engine(dsys, list_name="ccsdt", precision="bf16x3")
+    mixed = engine.Engine(dsys, list_name="ccsdt", precision="bf16x3", kconcat=kconcat)
+    assert sum("stmts" in st for st in mixed.plan.describe()["steps"]) >= (8 if kconcat else 0)
     kinds = {st["kind"] for st in mixed.plan.describe()["steps"]}
     assert "gemm_bf16split" in kinds and kinds & {"gemm_f32", "gemm_rows_f32"}
     m = [x.cpu() for x in mixed.residual(T[0], T[1], t3=T[2])]
