@@ -161,7 +161,12 @@ cc_status exec_step(cc_plan_s *pl, const Step &stp, const cc_integrals *I, const
             pl->launches++;
             break;
         case StepKind::GEMM:
-            if (stp.rows && !stp.kcat.empty()) {
+            if (stp.nk) {
+                if (mark) CC_CUDA(cudaEventRecord(mark, s));
+                CC_CUDA(launch_narrow_k(stp.nkd, resolve(stp.a, I, A, R, w), resolve(stp.b, I, A, R, w),
+                                        resolve(stp.out, I, A, R, w), s));
+                pl->launches += stp.nkd.beta != 1.0 ? 2 : 1;
+            } else if (stp.rows && !stp.kcat.empty()) {
                 RowsMultiDesc d = stp.rm;
                 for (size_t k = 0; k < stp.kcat.size(); k++) {
                     d.m[k].X = resolve(stp.kcat[k].a, I, A, R, w);

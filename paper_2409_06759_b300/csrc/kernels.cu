@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) scale_grp_kernel(int64_t M, int64_t N, co
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = e / M, m = e - n * M;
         T *p = C + grp_offset(cm, m) + grp_offset(cn, n);
-        *p = scal(beta, *p);
+        *p = beta == 0.0 ? zero<T>() : scal(beta, *p);     // beta = 0 clears (whatever was there)
     }
 }
 
@@ -353,10 +353,33 @@ template <typename CT, int NC> constexpr int rows_min_blocks() {
     return sizeof(CT) == 4 ? (NC <= 40 ? 3 : 2) : (NC <= 24 ? 3 : NC <= 48 ? 2 : 1);
 }
 
+// acc[c] += a * y[c] over a row of NC values in shared memory (16-byte aligned),
+// read four floats or two doubles at a time: one shared load per 4 (2) FMAs
+template <int NC> __device__ __forceinline__ void row_fma(float a, const float *y, float *acc) {
+    const float4 *y4 = reinterpret_cast<const float4 *>(y);
+#pragma unroll
+    for (int c = 0; c < NC / 4; c++) {
+        const float4 v = y4[c];
+        acc[4 * c] = fmaf(a, v.x, acc[4 * c]);
+        acc[4 * c + 1] = fmaf(a, v.y, acc[4 * c + 1]);
+        acc[4 * c + 2] = fmaf(a, v.z, acc[4 * c + 2]);
+        acc[4 * c + 3] = fmaf(a, v.w, acc[4 * c + 3]);
+    }
+}
+template <int NC> __device__ __forceinline__ void row_fma(double a, const double *y, double *acc) {
+    const double2 *y2 = reinterpret_cast<const double2 *>(y);
+#pragma unroll
+    for (int c = 0; c < NC / 2; c++) {
+        const double2 v = y2[c];
+        acc[2 * c] = fma(a, v.x, acc[2 * c]);
+        acc[2 * c + 1] = fma(a, v.y, acc[2 * c + 1]);
+    }
+}
+
 template <typename CT, int NC>
 __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kernel(const RowsGemmDesc d, const double *__restrict__ X,
                                                         const double *__restrict__ Y, double *__restrict__ C) {
-    __shared__ CT ys[64 * NC];
+    __shared__ __align__(16) CT ys[64 * NC];
     __shared__ int64_t xko[64], cco[NC];
     for (int e = threadIdx.x; e < 64 * NC; e += blockDim.x) {
         const int k = e / NC, c = e - k * NC;
@@ -372,13 +395,15 @@ __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kern
         for (int c = 0; c < NC; c++) acc[c] = zero<CT>();
         // eight loads in flight per thread before their products (ys rows k >= K are zero)
         for (int k0 = 0; k0 < d.K; k0 += 8) {
+            // the eight loads first: a conversion may call out on its rare path
+            double ad[8];
             CT a[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) a[j] = k0 + j < d.K ? down<CT>(__ldg(X + xo + xko[k0 + j])) : zero<CT>();
+            for (int j = 0; j < 8; j++) ad[j] = k0 + j < d.K ? __ldg(X + xo + xko[k0 + j]) : 0.0;
 #pragma unroll
-            for (int j = 0; j < 8; j++)
+            for (int j = 0; j < 8; j++) a[j] = down<CT>(ad[j]);
 #pragma unroll
-                for (int c = 0; c < NC; c++) acc[c] = cfma(a[j], ys[(k0 + j) * NC + c], acc[c]);
+            for (int j = 0; j < 8; j++) row_fma<NC>(a[j], ys + (k0 + j) * NC, acc);
         }
         // beta 0: plain stores; beta 1: read-modify-write in batches of eight
         // (loads issued before the stores); a general beta was applied before
@@ -452,8 +477,11 @@ template <int NC> static int64_t rows_multi_bytes(const RowsMultiDesc &d, int es
     return kr * NC * esz + kr * 8 + NC * 8;
 }
 
+// blocks per SM: the staged Y blocks (up to 96 KB) allow two
+template <typename CT, int NC> constexpr int rows_multi_min_blocks() { return sizeof(CT) == 4 || NC <= 24 ? 2 : 1; }
+
 template <typename CT, int NC>
-__global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_multi_kernel(const RowsMultiDesc d, double *__restrict__ C) {
+__global__ void __launch_bounds__(256, rows_multi_min_blocks<CT, NC>()) rows_multi_kernel(const RowsMultiDesc d, double *__restrict__ C) {
     extern __shared__ __align__(16) unsigned char rm_smem[];
     int kr = 0;
     for (int s = 0; s < d.nm; s++) kr += (d.m[s].K + 7) / 8 * 8;
@@ -487,13 +515,14 @@ __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_multi_ker
             const int64_t xo = grp_offset32(m.xr, (uint32_t)r);
             // eight loads in flight before their products (the padded Y rows are zero)
             for (int k0 = 0; k0 < m.K; k0 += 8) {
+                double ad[8];
                 CT a[8];
 #pragma unroll
-                for (int j = 0; j < 8; j++) a[j] = k0 + j < m.K ? down<CT>(__ldg(X + xo + xko[kb + k0 + j])) : zero<CT>();
+                for (int j = 0; j < 8; j++) ad[j] = k0 + j < m.K ? __ldg(X + xo + xko[kb + k0 + j]) : 0.0;
 #pragma unroll
-                for (int j = 0; j < 8; j++)
+                for (int j = 0; j < 8; j++) a[j] = down<CT>(ad[j]);
 #pragma unroll
-                    for (int c = 0; c < NC; c++) acc[c] = cfma(a[j], ys[(kb + k0 + j) * NC + c], acc[c]);
+                for (int j = 0; j < 8; j++) row_fma<NC>(a[j], ys + (kb + k0 + j) * NC, acc);
             }
             kb += (m.K + 7) / 8 * 8;
         }
@@ -525,7 +554,7 @@ template <typename CT, int NC> static cudaError_t rows_multi_t(const RowsMultiDe
             return e;
     }
     int64_t blocks = (d.R + 255) / 256;
-    if (blocks > 148 * rows_min_blocks<CT, NC>()) blocks = 148 * rows_min_blocks<CT, NC>();
+    if (blocks > 148 * rows_multi_min_blocks<CT, NC>()) blocks = 148 * rows_multi_min_blocks<CT, NC>();
     rows_multi_kernel<CT, NC><<<(unsigned)blocks, 256, (size_t)smem, s>>>(d, C);
     return cudaGetLastError();
 }
@@ -558,6 +587,107 @@ cudaError_t launch_rows_multi(const RowsMultiDesc &d, double *C, cudaStream_t s)
     for (int k = 0; k < d.nm; k++)
         if (d.m[k].K < 1 || !d.m[k].X || !d.m[k].Y) return cudaErrorInvalidValue;
     return d.f32 ? rows_multi_ct<float>(d, C, s) : rows_multi_ct<double>(d, C, s);
+}
+
+// ------------------------------------------------------------ narrow_k
+// Long contraction, at most 8 columns, the large operand read in place: a warp
+// takes four rows and a segment of the contraction (seg elements of one inner
+// run, or kper whole runs); its lanes read the contiguous run of the four rows
+// (coalesced) and the matching Y values once for all four.  Each lane issues
+// the loads of two steps before converting any of them (a conversion may call
+// out on its rare path, and loads are not moved across calls).  Lane sums
+// meet in a shuffle tree and are added to C by reductions in L2 (C cleared or
+// scaled beforehand for beta != 1).
+template <typename CT, int NN>
+__global__ void __launch_bounds__(256) narrow_k_kernel(const NarrowKDesc d, const double *__restrict__ X,
+                                                       const double *__restrict__ Y, double *__restrict__ C) {
+    const int lane = threadIdx.x & 31;
+    const int64_t groups = (d.M + 3) / 4, chunks = (d.Ko + d.kper - 1) / d.kper, nseg = (d.L + d.seg - 1) / d.seg;
+    const int64_t per_group = chunks * nseg, items = groups * per_group;
+    int yn[NN];     // the columns' offsets in Y (Y below 2^31 elements: checked by the planner)
+#pragma unroll
+    for (int n = 0; n < NN; n++) yn[n] = n < d.N ? (int)grp_offset(d.yn, n) : 0;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
+        const int64_t g = it / per_group, rem = it - g * per_group;
+        const int64_t kc = rem / nseg, sg = rem - kc * nseg;
+        int64_t xr[4];
+        bool ok[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int64_t m = 4 * g + r;
+            ok[r] = m < d.M;
+            xr[r] = ok[r] ? grp_offset(d.xm, m) : 0;
+        }
+        CT acc[4][NN];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int n = 0; n < NN; n++) acc[r][n] = zero<CT>();
+        const int64_t ko1 = (kc + 1) * d.kper < d.Ko ? (kc + 1) * d.kper : d.Ko;
+        const int64_t j0 = sg * d.seg, j1 = j0 + d.seg < d.L ? j0 + d.seg : d.L;
+        for (int64_t ko = kc * d.kper; ko < ko1; ko++) {
+            const int64_t xo = grp_offset(d.xko, ko), yo = grp_offset(d.yko, ko);
+            for (int64_t j = j0 + lane; j < j1; j += 64) {
+                const bool two = j + 32 < j1;
+                double xd[2][4], yd[2][NN];
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    const int64_t jj = j + 32 * u;
+                    const bool on = u == 0 || two;
+#pragma unroll
+                    for (int n = 0; n < NN; n++) yd[u][n] = on && n < d.N ? __ldg(Y + yo + jj * d.sy + yn[n]) : 0.0;
+#pragma unroll
+                    for (int r = 0; r < 4; r++) xd[u][r] = on && ok[r] ? __ldg(X + xr[r] + xo + jj) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    CT y[NN], x[4];
+#pragma unroll
+                    for (int n = 0; n < NN; n++) y[n] = down<CT>(yd[u][n]);
+#pragma unroll
+                    for (int r = 0; r < 4; r++) x[r] = down<CT>(xd[u][r]);
+#pragma unroll
+                    for (int r = 0; r < 4; r++)
+#pragma unroll
+                        for (int n = 0; n < NN; n++) acc[r][n] = cfma(x[r], y[n], acc[r][n]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int n = 0; n < NN; n++) {
+                double v = up(acc[r][n]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && ok[r] && n < d.N)
+                    red_add(C + grp_offset(d.cm, 4 * g + r) + grp_offset(d.cn, n), d.alpha * v);
+            }
+    }
+}
+
+template <typename CT>
+static cudaError_t narrow_k_t(const NarrowKDesc &d, const double *X, const double *Y, double *C, cudaStream_t s) {
+    const int64_t items = ((d.M + 3) / 4) * ((d.Ko + d.kper - 1) / d.kper) * ((d.L + d.seg - 1) / d.seg);
+    int64_t blocks = (items + 7) / 8;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    const unsigned b = (unsigned)blocks;
+    switch (d.N) {
+        case 1: narrow_k_kernel<CT, 1><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        case 2: narrow_k_kernel<CT, 2><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        case 3: case 4: narrow_k_kernel<CT, 4><<<b, 256, 0, s>>>(d, X, Y, C); break;
+        default: narrow_k_kernel<CT, 8><<<b, 256, 0, s>>>(d, X, Y, C); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_narrow_k(const NarrowKDesc &d, const double *X, const double *Y, double *C, cudaStream_t s) {
+    if (d.M <= 0) return cudaSuccess;
+    if (d.N < 1 || d.N > 8 || d.Ko < 1 || d.L < 1 || d.kper < 1 || d.seg < 1) return cudaErrorInvalidValue;
+    if (d.beta != 1.0)
+        if (cudaError_t e = launch_scale_grp(d.M, d.N, d.cm, d.cn, d.beta, C, s)) return e;
+    return d.f32 ? narrow_k_t<float>(d, X, Y, C, s) : narrow_k_t<double>(d, X, Y, C, s);
 }
 
 // ------------------------------------------------------------------ gemv

@@ -115,6 +115,24 @@ struct RowsGemmDesc {
     int red;                        // beta = 1: add C by red.global.add.f64 (no read)
 };
 
+// Long contraction with at most 8 columns, the large operand X read in place:
+//   C(m, n) = alpha * sum_k X(m, k) Y(k, n) + beta * C(m, n),
+// k = (ko, j) with j the contraction's inner run, contiguous in X (unit
+// stride) and of stride sy in Y: X(m, k) = X[xm(m) + xko(ko) + j],
+// Y(k, n) = Y[yko(ko) + j sy + yn(n)].  A work item is four rows and either
+// seg elements of one inner run or kper whole runs (seg = L).
+// f32: products and lane sums in FP32 (FP64 data), the rest in FP64.
+struct NarrowKDesc {
+    int64_t M;
+    int N;
+    int64_t Ko, L, sy, kper, seg;
+    Grp xm, xko;
+    Grp yko, yn;
+    Grp cm, cn;
+    double alpha, beta;
+    int f32;
+};
+
 // Several narrow GEMMs into one output, accumulated in one pass (K
 // concatenation on the narrow kernel):
 //   C(r, c) += sum_s alpha_s sum_k X_s(r, k) Y_s(k, c)
@@ -229,6 +247,7 @@ cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int splitk, const double 
                                  double alpha, double beta, double *C, cudaStream_t s);
 cudaError_t launch_rows_gemm(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s);
 cudaError_t launch_rows_multi(const RowsMultiDesc &d, double *C, cudaStream_t s);
+cudaError_t launch_narrow_k(const NarrowKDesc &d, const double *X, const double *Y, double *C, cudaStream_t s);
 // C(m,n) *= beta over an M x N output addressed by two mixed-radix groups
 cudaError_t launch_scale_grp(int64_t M, int64_t N, const Grp &cm, const Grp &cn, double beta, double *C, cudaStream_t s);
 // the split kernels' double -> float rounding (mine) next to the library's (ref)

@@ -1150,13 +1150,9 @@ struct Planner {
         BufRef outref = tensor_ref(out.tensor);
         if (!initialized[out.tensor] && s.op != 0) {
             if (T.kind == TKind::INTERM) { err = "intermediate accumulated before it is defined"; return false; }
-            Step z;
-            z.kind = StepKind::ZERO;
-            z.stmt = si;
-            z.out = outref;
-            z.zero_elems = T.elems * (cplx ? 2 : 1);   // doubles
-            z.note = "zero " + T.name;
-            plan.steps.push_back(z);
+            // the first accumulation into a residual assigns it (every route
+            // writes every element of its output): no zeroing pass
+            beta = 0.0;
         }
         initialized[out.tensor] = true;
 
@@ -1273,6 +1269,38 @@ struct Planner {
             }
         }
 
+        // A long contraction with at most 8 columns on the small operand's side
+        // (the reductions of T3 against integrals and small intermediates): the
+        // large operand is read in place by the narrow_k kernel when its
+        // contraction ends in a unit-stride run of at least 32 that the other
+        // operand also holds as one strided run; no permuted copy is made.
+        const bool x_is_a = view_elems(A) >= view_elems(B);
+        const View &Xn = x_is_a ? A : B, &Yn = x_is_a ? B : A;
+        const int64_t n_free = x_is_a ? Nx : Mx, m_free = x_is_a ? Mx : Nx;
+        std::vector<int> nk_outer;
+        int64_t nk_L = 1, nk_sy = 0;
+        bool use_nk = false;
+        if (!cplx && !use_mixed && !use_rows && n_free <= 8 && Kx >= 256 && view_elems(Xn) >= ((int64_t)1 << 20) &&
+            plan.tensors[Yn.tensor].elems < ((int64_t)1 << 31)) {
+            std::vector<int> kl;
+            for (int l : fusable(Xn, K).order)
+                if (ext_of(Xn, l) > 1) kl.push_back(l);
+            size_t cut = kl.size();
+            int64_t ex = 1, ey = 0;
+            while (cut > 0) {
+                const int l = kl[cut - 1];
+                const int64_t sx = str_of(Xn, l), sy = str_of(Yn, l), e = ext_of(Xn, l);
+                if (sx != ex || (cut < kl.size() && sy != ey)) break;
+                if (cut == kl.size()) nk_sy = sy;
+                ex = sx * e;
+                ey = sy * e;
+                nk_L *= e;
+                cut--;
+            }
+            nk_outer.assign(kl.begin(), kl.begin() + cut);
+            use_nk = nk_L >= 32 && m_free >= 1;
+        }
+
         Step g;
         g.kind = StepKind::GEMM;
         g.stmt = si;
@@ -1291,6 +1319,16 @@ struct Planner {
             g.gemm.splitk = 1;
             g.gemm.M = Mx;
             g.gemm.N = Nx;
+            g.gemm.K = Kx;
+            g.gemm.f32 = use_f32 ? 1 : 0;
+        } else if (use_nk) {
+            std::set<int> FX = x_is_a ? FA : FB, FY = x_is_a ? FB : FA;
+            (x_is_a ? fa_order : fb_order) = fusable(Xn, FX).order;
+            (x_is_a ? fb_order : fa_order) = fusable(Yn, FY).order;
+            g.nk = true;
+            g.gemm.splitk = 1;
+            g.gemm.M = m_free;
+            g.gemm.N = n_free;
             g.gemm.K = Kx;
             g.gemm.f32 = use_f32 ? 1 : 0;
         } else if (use_mixed) {
@@ -1416,7 +1454,40 @@ struct Planner {
         g.out = cref;
         g.a = aref;
         g.b = bref;
-        if (g.rows) {
+        if (g.nk) {
+            NarrowKDesc &d = g.nkd;
+            const std::vector<int> &rord = x_is_a ? fa_order : fb_order, &cord = x_is_a ? fb_order : fa_order;
+            d.M = m_free;
+            d.N = (int)n_free;
+            d.L = nk_L;
+            d.sy = nk_sy;
+            d.Ko = 1;
+            for (int l : nk_outer) d.Ko *= ext_of(Xn, l);
+            d.xm = make_grp(rord, Xn, Xn);
+            d.xko = make_grp(nk_outer, Xn, Xn);
+            d.yko = make_grp(nk_outer, Yn, Yn);
+            d.yn = make_grp(cord, Yn, Yn);
+            d.cm = make_grp(rord, Xn, Cv);
+            d.cn = make_grp(cord, Yn, Cv);
+            if (!err.empty()) return false;
+            d.alpha = galpha;
+            d.beta = gbeta;
+            d.f32 = use_f32 ? 1 : 0;
+            g.gemm.alpha = galpha;
+            g.gemm.beta = gbeta;
+            g.gemm.cm = cm;
+            g.gemm.cn = cn;
+            // about 4096 elements of a row per work item (whole runs when they are
+            // shorter), but enough items to keep 48 warps on every SM
+            const int64_t groups = (d.M + 3) / 4;
+            auto items = [&] { return groups * ((d.Ko + d.kper - 1) / d.kper) * ((d.L + d.seg - 1) / d.seg); };
+            d.kper = std::max<int64_t>(1, 4096 / d.L);
+            d.seg = std::min<int64_t>(d.L, 4096);
+            while (d.kper > 1 && items() < 148 * 48) d.kper /= 2;
+            while (d.kper == 1 && d.seg > 512 && items() < 148 * 48) d.seg = align_up(d.seg / 2, 64);
+            g.a = x_is_a ? aref : bref;
+            g.b = x_is_a ? bref : aref;
+        } else if (g.rows) {
             RowsGemmDesc &r = g.rg;
             const bool xa = Mx >= Nx;
             const View &X = xa ? A : B, &Y = xa ? B : A;
@@ -1840,7 +1911,8 @@ std::string describe_plan(const Plan &plan) {
     for (size_t k = 0; k < plan.steps.size(); k++) {
         const Step &s = plan.steps[k];
         os << (k ? "," : "") << "{\"stmt\":" << s.stmt << ",\"kind\":\""
-           << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : s.rows ? (s.gemm.f32 ? "gemm_rows_f32" : "gemm_rows")
+           << (s.kind == StepKind::GEMM ? (s.mixed ? "gemm_bf16split" : s.nk ? (s.gemm.f32 ? "gemm_nk_f32" : "gemm_nk")
+                                                   : s.rows ? (s.gemm.f32 ? "gemm_rows_f32" : "gemm_rows")
                                                    : s.gemm.f32 ? "gemm_f32" : "gemm_f64")
                                         : s.kind == StepKind::ACCUM ? "accum" : s.kind == StepKind::PACK ? "pack"
                                         : s.kind == StepKind::UNPACK ? "unpack" : "zero")

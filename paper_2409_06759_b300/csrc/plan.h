@@ -84,6 +84,8 @@ struct Step {
     UnpackDesc up{};                             // UNPACK: out (antisymmetric) from packed a
     bool rows = false;                           // narrow GEMM (one thread per row, operands in place)
     RowsGemmDesc rg{};
+    bool nk = false;                             // long contraction, <= 8 columns, operands in place
+    NarrowKDesc nkd{};
     std::vector<KMember> kcat;                   // K-concatenated members (a, b, split_a/b unused)
     std::vector<int> kstmts;                     // the statements a K-concatenated step carries
     RowsMultiDesc rm{};                          // K-concatenated on the narrow kernel (rows = true)
