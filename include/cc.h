@@ -128,6 +128,11 @@ typedef struct {
                            * into the same intermediate with its indices split the same
                            * way between their operands run as one tensor-core GEMM
                            * whose K concatenates theirs (one pass over the output) */
+    int uniform_steps;    /* 1 (split-bf16 precisions, real): every contraction on the
+                           * tensor-core split route and none merged, so that plans of
+                           * one list have the same steps at any o, v.  cc_solve_batched
+                           * then runs the batch step by step, one launch per step for
+                           * all systems (grouped execution) */
 } cc_plan_opts;
 
 /* cc_plan_create -- parse a contraction list and plan its execution.
@@ -285,6 +290,15 @@ CC_API cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps,
  * a per-system table the host rewrites each iteration.  The per-system
  * arithmetic and stopping rule are those of cc_solve (converged systems stop
  * updating; their residuals are still evaluated by the graph).
+ * Grouped execution: when the n >= 2 plans have the same steps (made with
+ * cc_plan_opts.uniform_steps at CC_PREC_BF16X3 from one list writing R1 and
+ * R2), the residuals of the whole batch run as one launch per step instead --
+ * each step's elementwise pass, operand splits and tensor-core GEMM take a
+ * table with one entry per system (the GEMM is one persistent tcgen05 kernel
+ * walking the tiles of every system), then one grouped pass applies the
+ * denominators and forms every system's energy and norms.  Converged systems
+ * are skipped inside those launches.  The workspace size accounts for the
+ * tables.
  *   plans: n distinct plans (one per system), each writing R2.
  *   ints, amps: arrays of n structs; amps in = start, out = final iterates.
  *   opts: shared options (refine_plan and resume are not supported: CC_ERR_UNSUPPORTED).

@@ -62,7 +62,7 @@ class cc_resid(ctypes.Structure):
 
 class cc_plan_opts(ctypes.Structure):
     _fields_ = [("struct_size", c_int), ("verbose", c_int), ("fuse_permutes", c_int), ("packed_vvvv", c_int),
-                ("no_kconcat", c_int)]
+                ("no_kconcat", c_int), ("uniform_steps", c_int)]
 
 
 class cc_solve_opts(ctypes.Structure):
@@ -195,12 +195,14 @@ def load_list(name: str) -> str:
 
 
 def cc_plan_create(text: str, o: int, v: int, dtype: int = CC_F64, precision=CC_PREC_FP64, verbose: int = 0,
-                   _route_all: bool = False, packed_vvvv: bool = False, kconcat: bool = True) -> Plan:
+                   _route_all: bool = False, packed_vvvv: bool = False, kconcat: bool = True,
+                   uniform_steps: bool = False) -> Plan:
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     prec = precision + (100 if _route_all else 0)   # test hook: every GEMM on the split route
     h = c_void_p()
-    opts = cc_plan_opts(ctypes.sizeof(cc_plan_opts), verbose, 0, int(packed_vvvv), int(not kconcat))
+    opts = cc_plan_opts(ctypes.sizeof(cc_plan_opts), verbose, 0, int(packed_vvvv), int(not kconcat),
+                        int(uniform_steps))
     _check(_lib.cc_plan_create(text.encode(), o, v, dtype, prec, ctypes.byref(opts), ctypes.byref(h)),
            "cc_plan_create")
     return Plan(h.value, o, v, precision, text, dtype)

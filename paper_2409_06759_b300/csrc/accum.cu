@@ -38,17 +38,14 @@ namespace ccb {
 // The multi-index is decomposed once per run and advanced as an odometer.
 constexpr int kAccChunk = 8;
 
+// the run of 32*kAccChunk output elements starting at r0, by one warp
 template <typename T, bool ACC>
-__global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *__restrict__ src,
-                                                    T *__restrict__ out, const T *__restrict__ src2,
-                                                    const T *__restrict__ add) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t run = 32 * kAccChunk;
-    for (int64_t r0 = warp * run; r0 < d.total; r0 += nwarps * run) {
+__device__ __forceinline__ void accum_run(const AccumDesc &d, const T *__restrict__ src, T *__restrict__ out,
+                                          const T *__restrict__ src2, const T *__restrict__ add, int64_t r0,
+                                          int lane) {
+    {
         int64_t e = r0 + lane;
-        if (e >= d.total) continue;
+        if (e >= d.total) return;
         int dig[kMaxDims];
         {
             int64_t x = e;
@@ -97,6 +94,38 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
     }
 }
 
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *__restrict__ src,
+                                                    T *__restrict__ out, const T *__restrict__ src2,
+                                                    const T *__restrict__ add) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t run = 32 * kAccChunk;
+    for (int64_t r0 = warp * run; r0 < d.total; r0 += nwarps * run) accum_run<T, ACC>(d, src, out, src2, add, r0, lane);
+}
+
+// The grouped form (real): entry e's runs are the work items [e.item0,
+// e.item0 + ceil(total / run)); a warp finds its item's entry by binary search.
+template <bool ACC>
+__global__ void __launch_bounds__(256) grouped_accum_kernel(const GroupedAccum *__restrict__ tab, int n, int64_t total,
+                                                            const int *__restrict__ active) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t it = warp; it < total; it += nwarps) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupedAccum &e = tab[lo];
+        if (!active[e.sys]) continue;
+        accum_run<double, ACC>(e.d, e.src, e.out, e.src2, e.add, (it - e.item0) * (32 * kAccChunk), lane);
+    }
+}
+
 // --------------------------------------------------------------- row path
 // Work item = (chunk of rch consecutive output rows, block of 32*kRowU
 // columns of the innermost dim d0 = nd-1).  A warp decomposes the chunk's
@@ -108,13 +137,13 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
 // would otherwise cost the occupancy that hides the loads' latency).
 template <bool TWO> __host__ __device__ constexpr int rows_u() { return TWO ? 4 : 8; }
 
+// one work item `it` of the row path, by one warp
 template <typename T, int NP, bool TWO, bool ACC>
-__global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, const T *__restrict__ src,
-                                                         const T *__restrict__ src2, T *__restrict__ out,
-                                                         const T *__restrict__ add, uint32_t rows, int rch,
-                                                         uint32_t ncb) {
+__device__ __forceinline__ void accum_rows_item(const AccumDesc &d, const T *__restrict__ src,
+                                                const T *__restrict__ src2, T *__restrict__ out,
+                                                const T *__restrict__ add, uint32_t rows, int rch, uint32_t ncb,
+                                                uint64_t it, int lane) {
     constexpr int kRowU = rows_u<TWO>();
-    const int lane = threadIdx.x & 31;
     const int d0 = d.nd - 1;
     const int E0 = (int)d.ext[d0];                     // < 2^31 (launch_accum checks)
     // along the innermost dim every source (and the addend) has stride 0 or 1
@@ -126,14 +155,12 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
         u02[p] = TWO && p < d.nperm && d.sstr2[p][d0] != 0;
     }
     const bool ua = d.has_add && d.astr[d0] != 0;
-    const uint32_t nchunks = (uint32_t)((rows + (uint32_t)rch - 1) / (uint32_t)rch);
-    const uint64_t items = (uint64_t)nchunks * ncb;
     // accumulating outer products start from the old value and add each term
     // with one FMA, alpha (+-2^k) riding on a factor: nterms FP64 operations per
     // element instead of nterms + 1
     const bool chain = TWO && ACC && !d.as.general;
     const bool fold = chain && !(d.as.kexp == 0 && d.as.sflip == 0);
-    for (uint64_t it = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < items; it += (uint64_t)gridDim.x * 8) {
+    {
         const uint32_t chunk = (uint32_t)(it / ncb);
         const int cb = (int)(it - (uint64_t)chunk * ncb) * (32 * kRowU);
         const uint32_t r0 = chunk * (uint32_t)rch;
@@ -231,6 +258,40 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
                 }
             }
         }
+    }
+}
+
+template <typename T, int NP, bool TWO, bool ACC>
+__global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, const T *__restrict__ src,
+                                                         const T *__restrict__ src2, T *__restrict__ out,
+                                                         const T *__restrict__ add, uint32_t rows, int rch,
+                                                         uint32_t ncb) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = (uint32_t)((rows + (uint32_t)rch - 1) / (uint32_t)rch);
+    const uint64_t items = (uint64_t)nchunks * ncb;
+    for (uint64_t it = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < items; it += (uint64_t)gridDim.x * 8)
+        accum_rows_item<T, NP, TWO, ACC>(d, src, src2, out, add, rows, rch, ncb, it, lane);
+}
+
+// The grouped row path (real): entry e's items are [e.item0, e.item0 +
+// ceil(rows / rch) * ncb); a warp finds its item's entry by binary search.
+template <int NP, bool TWO, bool ACC>
+__global__ void __launch_bounds__(256) grouped_accum_rows_kernel(const GroupedAccum *__restrict__ tab, int n,
+                                                                 int64_t total, const int *__restrict__ active) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t it = warp; it < total; it += nwarps) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupedAccum &e = tab[lo];
+        if (!active[e.sys]) continue;
+        accum_rows_item<double, NP, TWO, ACC>(e.d, e.src, e.src2, e.out, e.add, e.rows, e.rch, e.ncb,
+                                              (uint64_t)(it - e.item0), lane);
     }
 }
 
@@ -882,6 +943,75 @@ static cudaError_t accum_dispatch(AccumDesc &d, const T *src, T *out, cudaStream
         d.bcase = 1;
     }
     return d.bcase ? accum_t<T, true>(d, src, out, s, src2, add) : accum_t<T, false>(d, src, out, s, src2, add);
+}
+
+// the row path's test of launch_accum: after merging dims, every source (and
+// a fused copy's source) runs with stride 0 or 1 along the output's innermost
+// dim, and the output with stride 1
+static bool row_path_ok(const AccumDesc &d) {
+    const int dl = d.nd - 1;
+    const int64_t rows = d.total / d.ext[dl];
+    bool ok = d.nperm <= 8 && rows <= 0xffffffffLL && d.ext[dl] >= 8 && d.ext[dl] < 0x7fff0000LL &&
+              d.ostr[dl] == 1 && (!d.has_add || d.astr[dl] == 0 || d.astr[dl] == 1);
+    for (int p = 0; p < d.nperm && ok; p++) {
+        ok = d.sstr[p][dl] == 0 || d.sstr[p][dl] == 1;
+        if (ok && d.two_src) ok = d.sstr2[p][dl] == 0 || d.sstr2[p][dl] == 1;
+    }
+    for (int k = 0; k < dl && ok; k++) ok = d.ext[k] <= 0xffffffffLL;
+    return ok;
+}
+
+void prepare_grouped_accum(GroupedAccum &g) {
+    AccumDesc &d = g.d;
+    d.negmask = 0;
+    for (int p = 0; p < d.nperm; p++)
+        if (d.sign[p] < 0.0) d.negmask |= 1ull << p;
+    d.as = make_scale(d.alpha);
+    d.bcase = beta_case(d.beta);
+    collapse_dims(d);
+    g.row_path = row_path_ok(d) ? 1 : 0;
+    g.rows = 1;
+    g.rch = 1;
+    g.ncb = 1;
+    if (g.row_path) {
+        const int64_t E0 = d.ext[d.nd - 1];
+        g.rows = (uint32_t)(d.total / E0);
+        const int64_t cw = 32 * (d.two_src ? rows_u<true>() : rows_u<false>());
+        g.ncb = (uint32_t)((E0 + cw - 1) / cw);
+        g.rch = 2;
+    }
+}
+
+int64_t grouped_accum_items(const GroupedAccum &g, bool row_path) {
+    if (row_path) return ((int64_t)g.rows + g.rch - 1) / g.rch * (int64_t)g.ncb;
+    return (g.d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
+}
+
+cudaError_t launch_grouped_accum(const GroupedAccum *tab, int n, int64_t total, bool acc, bool row_path, int nperm,
+                                 bool two, const int *active, cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)grid_cap((total + 7) / 8, 148 * 16);
+    if (!row_path) {
+        if (acc) grouped_accum_kernel<true><<<blocks, 256, 0, s>>>(tab, n, total, active);
+        else grouped_accum_kernel<false><<<blocks, 256, 0, s>>>(tab, n, total, active);
+        return cudaGetLastError();
+    }
+#define CCB_GROUPED_ROWS(NPV)                                                                                        \
+    do {                                                                                                             \
+        if (two) {                                                                                                   \
+            if (acc) grouped_accum_rows_kernel<NPV, true, true><<<blocks, 256, 0, s>>>(tab, n, total, active);      \
+            else grouped_accum_rows_kernel<NPV, true, false><<<blocks, 256, 0, s>>>(tab, n, total, active);         \
+        } else {                                                                                                     \
+            if (acc) grouped_accum_rows_kernel<NPV, false, true><<<blocks, 256, 0, s>>>(tab, n, total, active);     \
+            else grouped_accum_rows_kernel<NPV, false, false><<<blocks, 256, 0, s>>>(tab, n, total, active);        \
+        }                                                                                                            \
+    } while (0)
+    if (nperm <= 1) CCB_GROUPED_ROWS(1);
+    else if (nperm <= 2) CCB_GROUPED_ROWS(2);
+    else if (nperm <= 4) CCB_GROUPED_ROWS(4);
+    else CCB_GROUPED_ROWS(8);
+#undef CCB_GROUPED_ROWS
+    return cudaGetLastError();
 }
 
 cudaError_t launch_accum(const AccumDesc &d0, const double *src, double *out, cudaStream_t s, const double *src2,

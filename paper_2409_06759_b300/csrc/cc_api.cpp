@@ -367,7 +367,17 @@ cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_prec
         flags |= 1;
     if (opts && opts->struct_size >= (int)(offsetof(cc_plan_opts, no_kconcat) + sizeof(int)) && opts->no_kconcat)
         flags |= 2;
-    if (!build_plan(text, o, v, (int)dtype, prec, pl->plan, err, flags)) {
+    int prec_eff = prec;
+    if (opts && opts->struct_size >= (int)(offsetof(cc_plan_opts, uniform_steps) + sizeof(int)) &&
+        opts->uniform_steps) {
+        if (dtype != CC_F64 || (base != CC_PREC_BF16X3 && base != CC_PREC_BF16X6)) {
+            delete pl;
+            return fail(CC_ERR_UNSUPPORTED, "uniform_steps needs a real split-bf16 plan");
+        }
+        flags |= 2;
+        prec_eff = base + 100;
+    }
+    if (!build_plan(text, o, v, (int)dtype, prec_eff, pl->plan, err, flags)) {
         delete pl;
         return fail(err.find("index spaces") != std::string::npos ? CC_ERR_SHAPE : CC_ERR_PARSE, err);
     }
@@ -854,10 +864,99 @@ cc_status cc_solve(cc_plan plan, const cc_integrals *ints, cc_amps *amps, const 
 // ------------------------------------------------------------------ batched
 namespace {
 
+// ---- grouped execution of a batch.  When every plan of a batch has the same
+// steps (plans made with uniform_steps: real, split-bf16, all contractions on
+// the tensor-core route, none merged), a residual evaluation of the whole batch
+// is one launch per step: the step's elementwise pass, operand splits and
+// tensor-core GEMM each take a table with one entry per system (grouped
+// kernels), followed by one grouped denominator/energy/norm pass.  Systems
+// whose active flag is 0 (converged) are skipped inside the launches.
+bool same_split_route(const Step &a, const Step &b) {
+    if (!b.mixed || b.rows || b.nk || !b.kcat.empty() || b.tc.nplanes_a != 2 || b.tc.nplanes_b != 2) return false;
+    if (b.tc.nprod != a.tc.nprod || beta_case(b.tc.beta) == 2 || beta_case(b.tc.beta) != beta_case(a.tc.beta))
+        return false;
+    for (int k = 0; k < b.tc.nprod; k++)
+        if (b.tc.prod_a[k] != a.tc.prod_a[k] || b.tc.prod_b[k] != a.tc.prod_b[k]) return false;
+    return a.a_static == b.a_static && a.b_static == b.b_static && a.skip_a == b.skip_a && a.skip_b == b.skip_b &&
+           b.split_a.cplx == 0 && b.split_b.cplx == 0 && b.split_a.nplanes == 2 && b.split_b.nplanes == 2;
+}
+
+bool batch_groupable(int n, const cc_plan *plans) {
+    if (n < 2) return false;
+    const Plan &P0 = plans[0]->plan;
+    for (int i = 0; i < n; i++) {
+        const Plan &P = plans[i]->plan;
+        if (P.precision != CC_PREC_BF16X3 || P.dtype != CC_F64 || P.res_used[3] || !P.res_used[1] ||
+            !P.res_used[2] || P.steps.size() != P0.steps.size() || P.packed_vvvv)
+            return false;
+        for (size_t k = 0; k < P.steps.size(); k++) {
+            const Step &a = P0.steps[k], &b = P.steps[k];
+            if (a.kind != b.kind) return false;
+            if (b.kind == StepKind::ACCUM) {
+                const int bc = beta_case(b.acc.beta);
+                if (bc == 2 || bc != beta_case(a.acc.beta) || b.acc.cplx || a.static_src != b.static_src ||
+                    a.acc.two_src != b.acc.two_src || a.acc.has_add != b.acc.has_add)
+                    return false;
+            } else if (b.kind == StepKind::GEMM) {
+                if (!same_split_route(a, b) || !same_split_route(a, a)) return false;
+            } else {
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// output tiles of step k over the batch (unsliced), at the column tile width
+// the grouped GEMM takes (128 when some output has more than 96 columns)
+int grouped_bn(int n, const cc_plan *plans, size_t k) {
+    int64_t nmax = 0;
+    for (int i = 0; i < n; i++) nmax = std::max<int64_t>(nmax, plans[i]->plan.steps[k].tc.N);
+    return nmax > 96 ? 128 : 64;
+}
+int64_t grouped_tiles(int n, const cc_plan *plans, size_t k) {
+    const int bn = grouped_bn(n, plans, k);
+    int64_t t = 0;
+    for (int i = 0; i < n; i++) {
+        const TcGemmDesc &d = plans[i]->plan.steps[k].tc;
+        t += (d.M + 127) / 128 * ((d.N + bn - 1) / bn);
+    }
+    return t;
+}
+
+// device bytes of the grouped tables of a batch (an upper bound: every table
+// 256-byte aligned)
+int64_t grouped_bytes(int n, const cc_plan *plans) {
+    const Plan &P0 = plans[0]->plan;
+    int64_t b = 0;
+    for (size_t k = 0; k < P0.steps.size(); k++) {
+        if (P0.steps[k].kind == StepKind::ACCUM) {
+            b += al((int64_t)n * (int64_t)sizeof(GroupedAccum));
+            continue;
+        }
+        b += 4 * al((int64_t)n * (int64_t)sizeof(GroupedSplit)) + al((int64_t)n * (int64_t)sizeof(GroupedGemm)) +
+             al((int64_t)n * (int64_t)sizeof(GroupedReduce));
+        const int64_t tiles = grouped_tiles(n, plans, k);
+        for (int i = 0; i < n; i++) {
+            const TcGemmDesc &t = plans[i]->plan.steps[k].tc;
+            const int ns = grouped_kslices(t.M, t.N, t.Kp, tiles);
+            if (ns > 1) b += al((int64_t)ns * t.M * t.N * 8);
+        }
+    }
+    b += al((int64_t)n * (int64_t)sizeof(GroupedPost)) + al((int64_t)n * 4);
+    for (int i = 0; i < n; i++) {
+        const int64_t e = amp_count(1, plans[i]->plan.o, plans[i]->plan.v) + amp_count(2, plans[i]->plan.o, plans[i]->plan.v);
+        b += al(3 * ((e + kPostChunk - 1) / kPostChunk) * 8);
+    }
+    return b;
+}
+
 struct BatchLayout {
     std::vector<int64_t> base, pw;      // per system: region start, plan workspace bytes
     std::vector<SolverLayout> L;
     int64_t tab = 0, scal = 0, used = 0, bytes = 0;
+    bool grouped = false;
+    int64_t grp = 0, grp_bytes = 0;     // grouped tables (when the plans allow it)
 };
 
 BatchLayout batch_layout(int n, const cc_plan *plans, int diis) {
@@ -873,8 +972,256 @@ BatchLayout batch_layout(int n, const cc_plan *plans, int diis) {
     B.tab = off; off += al((int64_t)n * (int64_t)sizeof(BatchSys));
     B.scal = off; off += al((int64_t)n * 8 * 8);
     B.used = off; off += al((int64_t)n * 4);
+    B.grouped = batch_groupable(n, plans);
+    if (B.grouped) {
+        B.grp = off;
+        B.grp_bytes = grouped_bytes(n, plans);
+        off += B.grp_bytes;
+    }
     B.bytes = off;
     return B;
+}
+
+// one launch of a grouped residual evaluation
+struct GroupedLaunch {
+    int kind = 0;                 // 0 elementwise, 1 split, 2 GEMM, 3 K-slice reduction
+    bool first_only = false;      // static sources / cached planes: the first evaluation only
+    int64_t off = 0;              // table offset in the grouped region
+    int n = 0;                    // entries
+    int64_t total = 0;            // work items of all entries
+    bool flag = false;            // elementwise: accumulate; split: lanes along K
+    bool row_path = false, two = false;   // elementwise: the row path, products of two sources
+    int nperm = 1;
+    int bn = 64;
+    GroupedGemmParams gp{};
+};
+
+struct GroupedBatch {
+    std::vector<GroupedLaunch> launches;
+    int64_t post_off = 0, post_total = 0, active_off = 0;
+    int n = 0;
+    int *err_flag = nullptr;
+};
+
+// The tables of every step (device pointers into the systems' workspaces),
+// built on the host and copied into the grouped region once per call.
+cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_integrals *ints, const cc_amps *amps,
+                        const std::vector<cc_resid> &R, char *W, const BatchLayout &BL, double *d_scal,
+                        cudaStream_t s) {
+    std::vector<unsigned char> img((size_t)BL.grp_bytes, 0);
+    int64_t off = 0;
+    auto put = [&](const void *src, int64_t bytes) {
+        const int64_t at = off;
+        std::memcpy(img.data() + at, src, (size_t)bytes);
+        off += al(bytes);
+        return at;
+    };
+    GB = GroupedBatch();
+    GB.n = n;
+    const Plan &P0 = plans[0]->plan;
+    char *G = W + BL.grp;
+    for (size_t k = 0; k < P0.steps.size(); k++) {
+        const Step &s0 = P0.steps[k];
+        if (s0.kind == StepKind::ACCUM) {
+            std::vector<GroupedAccum> t(n);
+            int64_t items = 0;
+            bool rowp = true;
+            int nperm = 1;
+            for (int i = 0; i < n; i++) {
+                const Step &st = plans[i]->plan.steps[k];
+                char *w = W + BL.base[i];
+                GroupedAccum &g = t[i];
+                g.d = st.acc;
+                prepare_grouped_accum(g);
+                g.src = resolve(st.a, &ints[i], &amps[i], &R[i], w);
+                g.src2 = st.acc.two_src ? resolve(st.b, &ints[i], &amps[i], &R[i], w) : nullptr;
+                g.add = st.acc.has_add ? resolve(st.c, &ints[i], &amps[i], &R[i], w) : nullptr;
+                g.out = resolve(st.out, &ints[i], &amps[i], &R[i], w);
+                if (!g.src || !g.out || (st.acc.two_src && !g.src2) || (st.acc.has_add && !g.add))
+                    return fail(CC_ERR_INVALID_ARG, "grouped batch: an operand buffer is missing");
+                g.sys = i;
+                rowp = rowp && g.row_path;
+                nperm = std::max(nperm, g.d.nperm);
+            }
+            // the row path when it holds for every system, else the generic one
+            for (int i = 0; i < n; i++) {
+                t[i].item0 = items;
+                items += grouped_accum_items(t[i], rowp);
+            }
+            GroupedLaunch L;
+            L.kind = 0;
+            L.first_only = s0.static_src;
+            L.n = n;
+            L.total = items;
+            L.flag = beta_case(s0.acc.beta) == 1;
+            L.row_path = rowp;
+            L.nperm = nperm;
+            L.two = s0.acc.two_src != 0;
+            L.off = put(t.data(), (int64_t)sizeof(GroupedAccum) * n);
+            GB.launches.push_back(L);
+            continue;
+        }
+        // operand splits: A then B, the entries of each lane orientation in one launch
+        for (int side = 0; side < 2; side++) {
+            if (side == 0 ? s0.skip_a : s0.skip_b) continue;
+            for (int lk = 0; lk < 2; lk++) {
+                std::vector<GroupedSplit> t;
+                int64_t tiles = 0;
+                for (int i = 0; i < n; i++) {
+                    const Step &st = plans[i]->plan.steps[k];
+                    const SplitDesc &d = side == 0 ? st.split_a : st.split_b;
+                    if ((int)split_lanes_along_k(d) != lk) continue;
+                    char *w = W + BL.base[i];
+                    GroupedSplit g{};
+                    g.d = d;
+                    g.x = resolve(side == 0 ? st.a : st.b, &ints[i], &amps[i], &R[i], w);
+                    g.planes = w + (side == 0 ? st.planes_a_off : st.planes_b_off);
+                    if (!g.x) return fail(CC_ERR_INVALID_ARG, "grouped batch: an operand buffer is missing");
+                    const int64_t kcols = d.kend ? d.kend : d.Kp;
+                    g.rtiles = (uint32_t)((d.Rp + 63) / 64);
+                    g.tile0 = tiles;
+                    g.sys = i;
+                    tiles += (int64_t)g.rtiles * ((kcols + 63) / 64);
+                    t.push_back(g);
+                }
+                if (t.empty()) continue;
+                GroupedLaunch L;
+                L.kind = 1;
+                L.first_only = side == 0 ? s0.a_static : s0.b_static;
+                L.n = (int)t.size();
+                L.total = tiles;
+                L.flag = lk == 1;
+                L.off = put(t.data(), (int64_t)sizeof(GroupedSplit) * (int64_t)t.size());
+                GB.launches.push_back(L);
+            }
+        }
+        // the GEMMs: 128-wide column tiles when some output has more than 96 columns
+        const int bn = grouped_bn(n, plans, k);
+        const int64_t tiles_all = grouped_tiles(n, plans, k);
+        std::vector<GroupedGemm> t(n);
+        std::vector<GroupedReduce> red;
+        int64_t tiles = 0, ritems = 0;
+        for (int i = 0; i < n; i++) {
+            const Step &st = plans[i]->plan.steps[k];
+            char *w = W + BL.base[i];
+            double *C = resolve(st.out, &ints[i], &amps[i], &R[i], w);
+            // long K, small output: K slices into partials (after the tables), reduced in order
+            const int ns = grouped_kslices(st.tc.M, st.tc.N, st.tc.Kp, tiles_all);
+            double *P = nullptr;
+            if (ns > 1) {
+                P = (double *)(G + off);
+                off += al((int64_t)ns * st.tc.M * st.tc.N * 8);
+            }
+            if (!C || !grouped_gemm_entry(t[i], st.tc, w + st.planes_a_off, w + st.planes_b_off, C, bn, ns, P))
+                return fail(CC_ERR_CUDA, "grouped batch: a GEMM entry could not be encoded");
+            t[i].tile0 = tiles;
+            t[i].sys = i;
+            tiles += (t[i].M + 127) / 128 * t[i].n_tiles * t[i].nslices;
+            if (t[i].nslices > 1) {
+                GroupedReduce r{};
+                r.M = t[i].M;
+                r.N = t[i].N;
+                r.nslices = t[i].nslices;
+                r.P = P;
+                r.cm = st.tc.cm;
+                r.cn = st.tc.cn;
+                r.as = make_scale(st.tc.alpha);
+                r.bcase = beta_case(st.tc.beta) != 0;
+                r.C = C;
+                r.item0 = ritems;
+                r.sys = i;
+                ritems += (r.M * r.N + 255) / 256;
+                red.push_back(r);
+            }
+        }
+        GroupedLaunch L;
+        L.kind = 2;
+        L.n = n;
+        L.total = tiles;
+        L.bn = bn;
+        L.gp.nprod = s0.tc.nprod;
+        for (int q = 0; q < s0.tc.nprod; q++) {
+            L.gp.prod_a[q] = s0.tc.prod_a[q];
+            L.gp.prod_b[q] = s0.tc.prod_b[q];
+        }
+        L.off = put(t.data(), (int64_t)sizeof(GroupedGemm) * n);
+        GB.launches.push_back(L);
+        if (!red.empty()) {
+            GroupedLaunch Q;
+            Q.kind = 3;
+            Q.n = (int)red.size();
+            Q.total = ritems;
+            Q.off = put(red.data(), (int64_t)sizeof(GroupedReduce) * (int64_t)red.size());
+            GB.launches.push_back(Q);
+        }
+    }
+    // the denominator / energy / norm pass and its partials
+    {
+        std::vector<GroupedPost> t(n);
+        std::vector<int64_t> part_at(n);
+        int64_t items = 0;
+        for (int i = 0; i < n; i++) {
+            const Plan &P = plans[i]->plan;
+            GroupedPost &g = t[i];
+            g.o = P.o;
+            g.v = P.v;
+            g.fo = ints[i].f_occ;
+            g.fv = ints[i].f_vir;
+            g.t1 = (const double *)amps[i].t1;
+            g.t2 = (const double *)amps[i].t2;
+            g.oovv = (const double *)ints[i].oovv;
+            g.r1 = (double *)R[i].r1;
+            g.r2 = (double *)R[i].r2;
+            if (!g.fo || !g.fv || !g.t1 || !g.t2 || !g.oovv || !g.r1 || !g.r2)
+                return fail(CC_ERR_INVALID_ARG, "grouped batch: a solver buffer is missing");
+            g.scal = d_scal + 8 * i;
+            g.chunks = (amp_count(1, P.o, P.v) + amp_count(2, P.o, P.v) + kPostChunk - 1) / kPostChunk;
+            g.item0 = items;
+            g.sys = i;
+            items += g.chunks;
+        }
+        // partials after the tables
+        GB.post_total = items;
+        const int64_t post_at = off;
+        off += al((int64_t)sizeof(GroupedPost) * n);
+        for (int i = 0; i < n; i++) {
+            t[i].partials = (double *)(G + off);
+            off += al(3 * t[i].chunks * 8);
+        }
+        std::memcpy(img.data() + post_at, t.data(), sizeof(GroupedPost) * n);
+        GB.post_off = post_at;
+    }
+    GB.active_off = off;
+    off += al((int64_t)n * 4);
+    if (off > BL.grp_bytes) return fail(CC_ERR_WORKSPACE, "grouped batch tables exceed their region");
+    GB.err_flag = (int *)(W + BL.base[0] + plans[0]->plan.flags_off);
+    CC_CUDA(cudaMemcpyAsync(G, img.data(), (size_t)off, cudaMemcpyHostToDevice, s));
+    CC_CUDA(cudaMemsetAsync(GB.err_flag, 0, sizeof(int), s));
+    CC_CUDA(cudaStreamSynchronize(s));
+    return CC_OK;
+}
+
+// one residual evaluation of the whole batch (grouped launches); the caller
+// has set the active flags
+cc_status grouped_residual(const GroupedBatch &GB, char *G, bool first, long long &launches, cudaStream_t s) {
+    const int *active = (const int *)(G + GB.active_off);
+    for (const GroupedLaunch &L : GB.launches) {
+        if (L.first_only && !first) continue;
+        if (L.kind == 0)
+            CC_CUDA(launch_grouped_accum((const GroupedAccum *)(G + L.off), L.n, L.total, L.flag, L.row_path, L.nperm,
+                                         L.two, active, s));
+        else if (L.kind == 1)
+            CC_CUDA(launch_grouped_split((const GroupedSplit *)(G + L.off), L.n, L.total, L.flag, active, s));
+        else if (L.kind == 2)
+            CC_CUDA(launch_grouped_gemm((const GroupedGemm *)(G + L.off), L.n, L.total, L.bn, L.gp, active,
+                                        GB.err_flag, s));
+        else
+            CC_CUDA(launch_grouped_reduce((const GroupedReduce *)(G + L.off), L.n, L.total, active, s));
+        launches++;
+    }
+    CC_CUDA(launch_grouped_post((const GroupedPost *)(G + GB.post_off), GB.n, GB.post_total, active, s));
+    launches += 2;
+    return CC_OK;
 }
 
 // host resources of one batched call, released on every exit path
@@ -887,8 +1234,9 @@ struct BatchHost {
     cudaEvent_t sync_ev = nullptr;
     BatchSys *tab = nullptr;
     double *scal = nullptr;
-    int *used = nullptr, *flags = nullptr;
+    int *used = nullptr, *flags = nullptr, *active = nullptr;
     ~BatchHost() {
+        if (active) cudaFreeHost(active);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         for (auto e : ev) cudaEventDestroy(e);
@@ -978,9 +1326,42 @@ cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints
             }
         R[i] = cc_resid{r[i][1], r[i][2], r[i][3]};
         plans[i]->cache_filled = false;
+        // 1/D of every amplitude (the Jacobi steps multiply by it, as cc_solve does)
+        double *dinv = (double *)(sreg + L.dinv);
+        int64_t doff = 0;
+        for (int l = 1; l <= 3; l++) {
+            if (!r[i][l]) continue;
+            CC_CUDA(launch_inv_denominators(l, P.o, P.v, ints[i].f_occ, ints[i].f_vir, dinv + doff,
+                                            P.dtype == CC_C128, s));
+            doff += L.n[l];
+        }
         if (reports) { reports[i].iterations = 0; reports[i].converged = 0; reports[i].switched_at = -1; }
     }
     g_err.clear();
+
+    // grouped execution (plans with the same steps): tables built once per call
+    GroupedBatch GB;
+    int *d_active = nullptr;
+    if (BL.grouped) {
+        cc_status gs = build_grouped(GB, n, plans, ints, amps, R, W, BL, d_scal, s);
+        if (gs != CC_OK) return gs;
+        d_active = (int *)(W + BL.grp + GB.active_off);
+        CC_CUDA(cudaMallocHost(&H.active, sizeof(int) * n));
+        for (int i = 0; i < n; i++) H.active[i] = 1;
+        CC_CUDA(cudaMemcpyAsync(d_active, H.active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    }
+    // the grouped residual of the batch + energy/norm into d_scal[i], read back
+    auto grouped_phase = [&](bool first) -> cc_status {
+        long long la = 0;
+        cc_status gst = grouped_residual(GB, W + BL.grp, first, la, s);
+        if (gst != CC_OK) return gst;
+        plans[0]->launches += la;
+        CC_CUDA(cudaMemcpyAsync(H.scal, d_scal, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(H.used, d_used, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaMemcpyAsync(H.flags, GB.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        for (int i = 1; i < n; i++) H.flags[i] = 0;
+        return CC_OK;
+    };
 
     // residual phase of every system: run_residual + energy/norm into d_scal[i]
     auto residual_phase = [&](bool capture) -> cc_status {
@@ -1011,11 +1392,23 @@ cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints
     };
 
     // iteration 0 runs directly (it fills the static caches); later ones replay a graph
-    cc_status st = residual_phase(false);
+    cc_status st = BL.grouped ? grouped_phase(true) : residual_phase(false);
     if (st != CC_OK) return st;
     CC_CUDA(cudaStreamSynchronize(s));
     std::vector<long long> per_replay(n, 0);
-    if (o.max_iter > 1) {
+    if (o.max_iter > 1 && BL.grouped) {
+        const long long before = plans[0]->launches;
+        CC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cc_status cst = grouped_phase(false);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(s, &g);
+        H.graph = g;
+        if (cst != CC_OK) return cst;
+        if (ce != cudaSuccess) return fail(CC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        CC_CUDA(cudaGraphInstantiate(&H.exec, H.graph, 0));
+        per_replay[0] = plans[0]->launches - before;
+        plans[0]->launches = before;
+    } else if (o.max_iter > 1) {
         H.st.resize(n);
         for (int i = 0; i < n; i++) CC_CUDA(cudaStreamCreateWithFlags(&H.st[i], cudaStreamNonBlocking));
         H.ev.resize(n + 1);
@@ -1041,6 +1434,11 @@ cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints
     int k = 0;
     for (k = 0; k < o.max_iter; k++) {
         if (k > 0) {
+            if (BL.grouped) {
+                // converged (or stopped) systems are skipped inside the grouped launches
+                for (int i = 0; i < n; i++) H.active[i] = state[i] == 0;
+                CC_CUDA(cudaMemcpyAsync(d_active, H.active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+            }
             CC_CUDA(cudaGraphLaunch(H.exec, s));
             CC_CUDA(cudaStreamSynchronize(s));
             for (int i = 0; i < n; i++) plans[i]->launches += per_replay[i];
@@ -1114,6 +1512,7 @@ cc_status cc_solve_batched(int n, const cc_plan *plans, const cc_integrals *ints
             b.coef = (double *)(sreg + L.coef);
             b.used = d_used + i;
             b.partials = (double *)(sreg + L.partials);
+            b.dinv = (const double *)(sreg + L.dinv);
             Z.pending_m = b.nstored;
             Z.iter++;
             nact++;

@@ -1163,6 +1163,116 @@ cudaError_t launch_reduce_partials(const double *partials, int count, double *ou
     return cudaGetLastError();
 }
 
+// ---- grouped post step: for every system of a batch, R -= D T over (R1 | R2)
+// and the chunk partials of E = sum_ijab V (1/4 t2 + 1/2 t1 t1), |R1|^2, |R2|^2
+// (one block per kPostChunk elements), then one warp per system sums its
+// partials in a fixed order into scal.
+__global__ void __launch_bounds__(256) grouped_post_kernel(const GroupedPost *__restrict__ tab, int n, int64_t total,
+                                                          const int *__restrict__ active) {
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupedPost &g = tab[lo];
+        if (!active[g.sys]) continue;            // block-uniform
+        const int64_t c = it - g.item0;
+        const uint32_t o = (uint32_t)g.o, v = (uint32_t)g.v;
+        const int64_t n1 = (int64_t)o * v, n2 = n1 * n1;
+        double se = 0.0, s1 = 0.0, s2 = 0.0;
+        const int64_t e1 = (c + 1) * kPostChunk < n1 + n2 ? (c + 1) * kPostChunk : n1 + n2;
+        for (int64_t e = c * kPostChunk + threadIdx.x; e < e1; e += blockDim.x) {
+            if (e < n1) {
+                const uint32_t i = (uint32_t)e / v, a = (uint32_t)e - i * v;
+                const double d = g.fo[i] - g.fv[a];
+                const double r = fma(neg(d), g.t1[e], g.r1[e]);
+                g.r1[e] = r;
+                s1 = fma(r, r, s1);
+            } else {
+                const int64_t x = e - n1;
+                const uint32_t row = (uint32_t)(x / v), b = (uint32_t)(x - (int64_t)row * v);
+                const uint32_t a = row % v, ij = row / v, j = ij % o, i = ij / o;
+                const double t2 = g.t2[x];
+                const double d = (g.fo[i] + g.fo[j]) - (g.fv[a] + g.fv[b]);
+                const double r = fma(neg(d), t2, g.r2[x]);
+                g.r2[x] = r;
+                s2 = fma(r, r, s2);
+                const double tt = g.t1 ? fma(2.0 * g.t1[(int64_t)i * v + a], g.t1[(int64_t)j * v + b], t2) : t2;
+                se = fma(g.oovv[x], tt, se);
+            }
+        }
+        se = block_sum(se);
+        s1 = block_sum(s1);
+        s2 = block_sum(s2);
+        if (threadIdx.x == 0) {
+            g.partials[c] = 0.25 * se;
+            g.partials[g.chunks + c] = s1;
+            g.partials[2 * g.chunks + c] = s2;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) grouped_post_reduce_kernel(const GroupedPost *__restrict__ tab, int n,
+                                                                 const int *__restrict__ active) {
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * 8 + (threadIdx.x >> 5); q < n; q += gridDim.x * 8) {
+        const GroupedPost &g = tab[q];
+        if (!active[g.sys]) continue;
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 3; k++) {
+            for (int64_t c = lane; c < g.chunks; c += 32) acc[k] += g.partials[k * g.chunks + c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+        }
+        if (lane == 0) {
+            g.scal[0] = acc[0];
+            g.scal[1] = 0.0;
+            g.scal[2] = acc[1];
+            g.scal[3] = acc[2];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) grouped_reduce_kernel(const GroupedReduce *__restrict__ tab, int n,
+                                                            int64_t total, const int *__restrict__ active) {
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupedReduce &g = tab[lo];
+        if (!active[g.sys]) continue;
+        const int64_t e = (it - g.item0) * 256 + threadIdx.x, mn = g.M * g.N;
+        if (e >= mn) continue;
+        const int64_t nn = e / g.M, m = e - nn * g.M;
+        double acc = 0.0;
+        for (int z = 0; z < g.nslices; z++) acc += g.P[(int64_t)z * mn + e];
+        double *c = g.C + grp_offset(g.cm, m) + grp_offset(g.cn, nn);
+        const double v = scale_f64(acc, g.as);
+        *c = g.bcase ? *c + v : v;
+    }
+}
+
+cudaError_t launch_grouped_reduce(const GroupedReduce *tab, int n, int64_t total, const int *active, cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(total < 148 * 16 ? total : 148 * 16);
+    grouped_reduce_kernel<<<blocks, 256, 0, s>>>(tab, n, total, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_post(const GroupedPost *tab, int n, int64_t total, const int *active, cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(total < 148 * 8 ? total : 148 * 8);
+    grouped_post_kernel<<<blocks, 256, 0, s>>>(tab, n, total, active);
+    if (cudaError_t e = cudaGetLastError()) return e;
+    grouped_post_reduce_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(tab, n, active);
+    return cudaGetLastError();
+}
+
 struct Order {
     int s[16];
 };
@@ -1242,14 +1352,9 @@ __global__ void __launch_bounds__(256) batched_jacobi_kernel(const BatchSys *__r
     for (int l = 1; l <= 3; l++) {
         if (!b.t[l]) continue;
         const int64_t off = rank_offset(b, l);
-        int64_t ncol = 1;
-        for (int q = 0; q < l; q++) ncol *= b.v;
-        ncol <<= b.cplx;
         for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b.n[l];
              e += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t row = e / ncol, col = e - row * ncol;
-            const double D = occ_sum(l, b.o, b.fo, row) - vir_sum(l, b.v, b.fv, (uint32_t)(col >> b.cplx));
-            const double q = b.r[l][e] / D;
+            const double q = b.r[l][e] * b.dinv[off + e];
             es[off + e] = q;
             xs[off + e] = b.t[l][e] + q;
         }

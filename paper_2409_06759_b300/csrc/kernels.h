@@ -264,6 +264,103 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
 cudaError_t launch_tc_gemm(const TcGemmDesc &d, const void *Aplanes, const void *Bplanes, double *C,
                            double *partials, int *err_flag, cudaStream_t s);
 
+// ---- grouped execution: one plan step over a batch of systems whose plans
+// have the same steps (a launch covers every system; entries of systems whose
+// active[sys] is 0 are skipped).  Each entry's work items follow those of the
+// entries before it (item0 / tile0: the entry's first item in the launch).
+struct alignas(64) TmapBytes {
+    unsigned char b[128];           // a CUtensorMap, encoded on the host
+};
+struct GroupedSplit {               // one operand split of one system (real, bf16 planes)
+    SplitDesc d;
+    const double *x;
+    void *planes;
+    int64_t tile0;
+    uint32_t rtiles;
+    int sys;
+};
+struct alignas(64) GroupedGemm {    // one system's split-bf16 GEMM (accumulating or assigning)
+    TmapBytes ma, mbw, mbn;         // A planes; B planes at the wide / narrow column tile
+    int64_t M, N, Kp;
+    int n_tiles, cs_base, cs_extra; // column tiles and their even split (16-column units)
+    Grp cm, cn;
+    Scale as;
+    int bcase;                      // 0 store, 1 read-modify-write, 2 reductions
+    double *C;
+    int nslices, kb_per;            // K slices (> 1: raw slice sums to P[z][n][m], reduced after)
+    double *P;
+    int64_t tile0;
+    int sys;
+};
+// K slices of a grouped GEMM whose entries have fewer than 2 x 148 output
+// tiles in all (tiles_all): long contractions with small outputs are cut into
+// slices of about 32 K blocks of 64 (partials of at most 16 MB)
+inline int grouped_kslices(int64_t M, int64_t N, int64_t Kp, int64_t tiles_all) {
+    const int64_t kb = Kp / 64;
+    if (kb <= 48 || tiles_all >= 2 * 148) return 1;
+    int64_t ns = (kb + 31) / 32;
+    if (ns > 64) ns = 64;
+    const int64_t cap = ((int64_t)16 << 20) / (M * N * 8 > 0 ? M * N * 8 : 1);
+    if (ns > cap) ns = cap;
+    return ns < 2 ? 1 : (int)ns;
+}
+struct GroupedReduce {              // C = alpha sum_z P[z][n][m] + beta C of one sliced GEMM
+    int64_t M, N;
+    int nslices;
+    const double *P;
+    Grp cm, cn;
+    Scale as;
+    int bcase;
+    double *C;
+    int64_t item0;
+    int sys;
+};
+struct GroupedGemmParams {          // what every entry of a grouped GEMM shares
+    int nprod;
+    int prod_a[8], prod_b[8];
+};
+struct GroupedAccum {               // one system's elementwise step
+    AccumDesc d;                    // prepared (prepare_grouped_accum): dims merged, negmask / as / bcase set
+    const double *src, *src2, *add;
+    double *out;
+    int row_path;                   // the row path applies (rows of the innermost dim, stride 0 / 1)
+    uint32_t rows, ncb;             // row path: rows, column blocks
+    int rch;                        // row path: rows per work item
+    int64_t item0;
+    int sys;
+};
+// the denominator update of the residuals (R -= D T, real) and the
+// partial sums of the energy and of |R1|^2, |R2|^2 of one system
+struct GroupedPost {
+    int o, v;
+    const double *fo, *fv, *t1, *t2, *oovv;
+    double *r1, *r2;
+    double *partials;               // [3][chunks]: energy, |R1|^2, |R2|^2 per chunk
+    double *scal;                   // scal[0] = E, scal[1] = 0, scal[2] = |R1|^2, scal[3] = |R2|^2
+    int64_t item0, chunks;
+    int sys;
+};
+constexpr int64_t kPostChunk = 4096;    // elements of (R1 | R2) per post work item
+
+// host: an entry of a grouped GEMM from a planned TcGemmDesc (two planes,
+// no split K) at column tile width bn; false when a map cannot be encoded
+bool grouped_gemm_entry(GroupedGemm &g, const TcGemmDesc &d, const void *A, const void *B, double *C, int bn,
+                        int nslices, double *P);
+// host: the split kernel's lane orientation for a descriptor (lanes along K)
+bool split_lanes_along_k(const SplitDesc &d);
+void prepare_grouped_accum(GroupedAccum &g);
+// work items of an entry on the row path or the generic path
+int64_t grouped_accum_items(const GroupedAccum &g, bool row_path);
+// the launches: tab (device) holds n entries; total = the work items of all
+cudaError_t launch_grouped_split(const GroupedSplit *tab, int n, int64_t total, bool lk, const int *active,
+                                 cudaStream_t s);
+cudaError_t launch_grouped_gemm(const GroupedGemm *tab, int n, int64_t total, int bn, const GroupedGemmParams &p,
+                                const int *active, int *err_flag, cudaStream_t s);
+cudaError_t launch_grouped_accum(const GroupedAccum *tab, int n, int64_t total, bool acc, bool row_path, int nperm,
+                                 bool two, const int *active, cudaStream_t s);
+cudaError_t launch_grouped_post(const GroupedPost *tab, int n, int64_t total, const int *active, cudaStream_t s);
+cudaError_t launch_grouped_reduce(const GroupedReduce *tab, int n, int64_t total, const int *active, cudaStream_t s);
+
 // R -= D * T for rank 1..3 residuals: D from the orbital energies (real);
 // cplx: t and r are interleaved complex.
 cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const double *fv,
@@ -327,8 +424,9 @@ struct BatchSys {
     double *coef;              // [16]
     int *used;                 // newest vectors the DIIS solve used (0: none)
     double *partials;          // [16][kBatchBlocks]
+    const double *dinv;        // 1/D of every amplitude, concatenated like x (set once per solve)
 };
-// x'_slot = t + R/D, e_slot = R/D for every active system
+// x'_slot = t + R (1/D), e_slot = R (1/D) for every active system
 cudaError_t launch_batched_jacobi(const BatchSys *sys, int nsys, cudaStream_t s);
 // <e_slot | e_order[q]> for q < nstored, reduced into gram; the DIIS solve when
 // nstored >= 2 (coef, used); deterministic fixed-grid reductions

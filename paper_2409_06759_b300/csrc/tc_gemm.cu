@@ -219,18 +219,16 @@ __device__ __forceinline__ void split8(const float *f, uint4 &H, uint4 &M, uint4
     L = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// one 64 x 64 tile at (r0, k0) of a split, by the whole block (block-uniform call)
 template <bool LK, int NPL, bool CPLX>
-__global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, const double *__restrict__ x,
-                                                         __nv_bfloat16 *__restrict__ planes, uint32_t rtiles,
-                                                         uint32_t ntiles) {
-    __shared__ float tile[64][65];
-    __shared__ int64_t ro[64], ko[64];
+__device__ __forceinline__ void split_tile_one(const SplitDesc &d, const double *__restrict__ x,
+                                               __nv_bfloat16 *__restrict__ planes, int64_t r0, int64_t k0,
+                                               float (*tile)[65], int64_t *ro, int64_t *ko) {
     const int64_t plane_elems = d.Rp * d.Kp;
     const int64_t kcols = d.kend ? d.kend : d.Kp;       // plane columns this split fills
     const double sc = d.scaled ? d.scale : 1.0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t r0 = (int64_t)(t % rtiles) * 64, k0 = (int64_t)(t / rtiles) * 64;
+    {
         __syncthreads();                       // the previous tile's reads of tile/ro/ko are done
         if (tid < 64) {
             const int64_t r = r0 + tid;
@@ -290,6 +288,45 @@ __global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, c
                 if (NPL == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = L;
             }
         }
+    }
+}
+
+template <bool LK, int NPL, bool CPLX>
+__global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, const double *__restrict__ x,
+                                                         __nv_bfloat16 *__restrict__ planes, uint32_t rtiles,
+                                                         uint32_t ntiles) {
+    __shared__ float tile[64][65];
+    __shared__ int64_t ro[64], ko[64];
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+        split_tile_one<LK, NPL, CPLX>(d, x, planes, (int64_t)(t % rtiles) * 64, (int64_t)(t / rtiles) * 64, tile, ro,
+                                      ko);
+}
+
+// The grouped form: the tiles of every entry one after the other; a block
+// finds its tile's entry by binary search over the entries' first tiles.
+template <bool LK>
+__global__ void __launch_bounds__(256, 5) grouped_split_kernel(const GroupedSplit *__restrict__ tab, int n,
+                                                            int64_t total, const int *__restrict__ active) {
+    __shared__ float tile[64][65];
+    __shared__ int64_t ro[64], ko[64];
+    __shared__ SplitDesc sd;                   // the tile's descriptor, staged once per tile
+    static_assert(sizeof(SplitDesc) % 8 == 0 && sizeof(SplitDesc) / 8 <= 256, "descriptor staging");
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].tile0 <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupedSplit &e = tab[lo];
+        if (!active[e.sys]) continue;          // block-uniform
+        __syncthreads();                       // the previous tile's reads of sd are done
+        if (threadIdx.x < sizeof(SplitDesc) / 8)
+            reinterpret_cast<int64_t *>(&sd)[threadIdx.x] = reinterpret_cast<const int64_t *>(&e.d)[threadIdx.x];
+        __syncthreads();                       // staged: split_tile_one reads sd before its own barrier
+        const int64_t lt = t - e.tile0;
+        split_tile_one<LK, 2, false>(sd, e.x, (__nv_bfloat16 *)e.planes, (lt % e.rtiles) * 64, (lt / e.rtiles) * 64,
+                                     tile, ro, ko);
     }
 }
 
@@ -490,13 +527,9 @@ static void slice_launch(const SplitDesc &d, const double *x, void *planes, int 
 static cudaError_t launch_slices(const SplitDesc &d, const double *x, void *planes, cudaStream_t s) {
     int *exps = reinterpret_cast<int *>(static_cast<char *>(planes) + slice_plane_bytes(d.Rp, d.Kp));
     if (cudaError_t e = cudaMemsetAsync(exps, 0, sizeof(int) * (size_t)d.Rp, s)) return e;
-    const int64_t unit = d.cplx ? 2 : 1;
-    const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit;
-    const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == unit;
     const int64_t rtiles = (d.Rp + 63) / 64, ntiles = rtiles * (d.Kp / 64);
     if (ntiles > 0xffffffffLL) return cudaErrorInvalidValue;
-    const int64_t ks = d.gk.nd >= 1 ? d.gk.str[d.gk.nd - 1] : 0, rs = d.gr.nd >= 1 ? d.gr.str[d.gr.nd - 1] : 0;
-    const bool lk = k_unit || (!r_unit && ks <= rs);
+    const bool lk = split_lanes_along_k(d);
     const unsigned blocks = (unsigned)(ntiles < 148 * 6 ? ntiles : 148 * 6);
     if (d.cplx) {
         if (lk) slice_launch<true, true>(d, x, planes, exps, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
@@ -517,8 +550,6 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
     // source unit stride inside the row group and not in K: transposed tiles
     // (for complex sources the unit is one complex element, two doubles)
     const int64_t unit = d.cplx ? 2 : 1;
-    const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit;
-    const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == unit;
     // vector path: long contiguous K (whole 1024-column spans per warp item)
     int vec = d.cplx != 2 && d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit &&
               d.gk.ext[d.gk.nd - 1] % (d.cplx ? 4 : 8) == 0 && ((uintptr_t)x & 15) == 0;
@@ -530,10 +561,7 @@ cudaError_t launch_split_bf16(const SplitDesc &d, const double *x, void *planes,
     if (d.kdst % 8 || kcols % 8 || d.kdst + kcols > d.Kp || kcols < d.K) return cudaErrorInvalidValue;
     const int64_t rtiles = (d.Rp + 63) / 64, ntiles = rtiles * ((kcols + 63) / 64);
     if (!(vec && d.K >= 512) && ntiles <= 0xffffffffLL) {
-        // lanes along K when K's innermost digit is the unit stride, or when
-        // neither side has one and K's innermost stride is the smaller
-        const int64_t ks = d.gk.nd >= 1 ? d.gk.str[d.gk.nd - 1] : 0, rs = d.gr.nd >= 1 ? d.gr.str[d.gr.nd - 1] : 0;
-        const bool lk = k_unit || (!r_unit && ks <= rs);
+        const bool lk = split_lanes_along_k(d);
         const unsigned blocks = (unsigned)(ntiles < 148 * 5 ? ntiles : 148 * 5);
         if (lk) split_tile_launch<true>(d, x, planes, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
         else split_tile_launch<false>(d, x, planes, blocks, (uint32_t)rtiles, (uint32_t)ntiles, s);
@@ -896,6 +924,239 @@ __global__ void __launch_bounds__(320, 1)
             fence_before();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
+// ---- grouped variant (two planes): the tiles of a batch of GEMMs, one per
+// system, in one persistent launch.  Entry e owns the global tiles
+// [e.tile0, e.tile0 + row tiles * e.n_tiles); its tensor maps, extents,
+// output addressing and scale live in the entry (global memory), so the roles
+// look the entry up by binary search for each tile.  Tiles of a system whose
+// active flag is 0 are skipped by all three roles alike (the accumulator
+// buffer index counts only the tiles worked), so converged systems cost
+// nothing but the lookup.  No split K: the tile count of a batch fills the GPU.
+__device__ __forceinline__ int grouped_entry(const GroupedGemm *__restrict__ tab, int n, int64_t t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(320, 1)
+    tc_gemm_grouped_kernel(const GroupedGemm *__restrict__ tab, int n, int64_t total, const GroupedGemmParams gp,
+                           const int *__restrict__ active, int *err_flag) {
+    constexpr int NP = 2;
+    using G = Cfg<NP, BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *tiles = smem;
+    uint64_t *full = (uint64_t *)(smem + STAGES * G::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;             // [2]
+    uint64_t *acce = accf + 2;                   // [2]
+    uint32_t *tmem_slot = (uint32_t *)(acce + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    volatile int *epi_abort = abort_flag + 1;
+    int64_t *coloff = (int64_t *)(smem + STAGES * G::STAGE_BYTES + 1024);   // [BN]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < STAGES; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 8);
+        }
+        *abort_flag = 0;
+        *epi_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 2 * BN);
+        tmem_relinquish();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // item t of entry e: K slice z (its K blocks [kb0, kb1)), row block, first column, width
+    auto coords = [&](const GroupedGemm &e, int64_t t, int64_t &m0, int64_t &n0, int &nw, int &z, int &kb0,
+                      int &kb1) {
+        const int64_t per_slice = (e.M + BM - 1) / BM * e.n_tiles;
+        const int64_t local = t - e.tile0;
+        z = (int)(local / per_slice);
+        const int64_t tile = local - (int64_t)z * per_slice;
+        m0 = (tile / e.n_tiles) * BM;
+        const int nb = (int)(tile % e.n_tiles);
+        const ColSplit cs{e.cs_base, e.cs_extra};
+        n0 = cs.n0(nb);
+        nw = cs.width(nb);
+        const int kb_total = (int)(e.Kp / BK);
+        kb0 = z * e.kb_per;
+        kb1 = kb0 + e.kb_per < kb_total ? kb0 + e.kb_per : kb_total;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t g = 0;
+            bool stop = false;
+            int last = -1;
+            for (int64_t t = blockIdx.x; t < total && !stop; t += gridDim.x) {
+                const int ie = grouped_entry(tab, n, t);
+                const GroupedGemm &e = tab[ie];
+                if (!active[e.sys]) continue;
+                int64_t m0, n0;
+                int nw, z, kb0, kb1;
+                coords(e, t, m0, n0, nw, z, kb0, kb1);
+                const ColSplit cs{e.cs_base, e.cs_extra};
+                const CUtensorMap *ma = reinterpret_cast<const CUtensorMap *>(&e.ma);
+                const CUtensorMap *mb = reinterpret_cast<const CUtensorMap *>(nw == cs.wide() ? &e.mbw : &e.mbn);
+                if (ie != last) {
+                    // the entry's maps live in global memory: order them for the tensor-map proxy
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&e.ma) : "memory");
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&e.mbw) : "memory");
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&e.mbn) : "memory");
+                    last = ie;
+                }
+                const uint32_t bytes = (uint32_t)(NP * (G::A_BYTES + nw * BK * 2));
+                for (int kb = kb0; kb < kb1; kb++, g++) {
+                    const int q = (int)(g % STAGES);
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (*abort_flag || !mbar_wait(&empty[q], ph ^ 1u)) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    uint8_t *st = tiles + q * G::STAGE_BYTES;
+                    mbar_expect_tx(&full[q], bytes);
+                    for (int p = 0; p < NP; p++) tma_load_3d(st + p * G::A_BYTES, ma, &full[q], kb * BK, (int)m0, p);
+                    for (int p = 0; p < NP; p++)
+                        tma_load_3d(st + NP * G::A_BYTES + p * G::B_BYTES, mb, &full[q], kb * BK, (int)n0, p);
+                }
+            }
+            if (stop) {
+                for (int64_t k = (g > STAGES ? g - STAGES : 0); k < g; k++)
+                    mbar_wait(&full[k % STAGES], (uint32_t)(k / STAGES) & 1u);
+                atomicOr(err_flag, 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int64_t g = 0;
+            int j = 0;                           // tiles worked by this CTA
+            for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+                if (*abort_flag) break;
+                const GroupedGemm &e = tab[grouped_entry(tab, n, t)];
+                if (!active[e.sys]) continue;
+                int64_t m0, n0;
+                int nw, z, kb0, kb1;
+                coords(e, t, m0, n0, nw, z, kb0, kb1);
+                const uint32_t idesc = idesc_bf16(BM, nw);
+                const int b = j & 1;
+                if (j >= 2) {
+                    if (!mbar_wait(&acce[b], (uint32_t)((j >> 1) - 1) & 1u)) {
+                        *abort_flag = 1;
+                        atomicOr(err_flag, 1);
+                    }
+                    fence_after();
+                }
+                const uint32_t dt = tmem + (uint32_t)(b * BN);
+                for (int kb = kb0; kb < kb1 && !*abort_flag; kb++, g++) {
+                    const int q = (int)(g % STAGES);
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (!mbar_wait(&full[q], ph)) {
+                        *abort_flag = 1;
+                        atomicOr(err_flag, 1);
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t st = smem_u32(tiles + q * G::STAGE_BYTES);
+                    for (int pr = 0; pr < gp.nprod; pr++) {
+                        const uint32_t a0 = st + gp.prod_a[pr] * G::A_BYTES;
+                        const uint32_t b0 = st + NP * G::A_BYTES + gp.prod_b[pr] * G::B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; kk++)
+                            mma_bf16(dt, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                     ((kb - kb0) | pr | kk) != 0);
+                    }
+                    mma_commit(&empty[q]);
+                }
+                mma_commit(&accf[b]);
+                j++;
+            }
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int et = threadIdx.x - 64;
+        int j = 0;
+        for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+            const GroupedGemm &e = tab[grouped_entry(tab, n, t)];
+            if (!active[e.sys]) continue;        // uniform over the CTA
+            int64_t m0, n0;
+            int nw, z, kb0, kb1;
+            coords(e, t, m0, n0, nw, z, kb0, kb1);
+            const bool split = e.nslices > 1;
+            const int b = j & 1;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            for (int c = et; c < BN; c += 256) {
+                const int64_t nn = n0 + c;
+                coloff[c] = (c < nw && nn < e.N) ? (split ? nn : grp_off(e.cn, nn)) : -1;
+            }
+            const int64_t m = m0 + q * 32 + lane;
+            const bool mok = m < e.M;
+            const int64_t roff = mok ? (split ? 0 : grp_off(e.cm, m)) : 0;
+            double *P = split ? e.P + (int64_t)z * e.M * e.N : nullptr;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            bool ok = mbar_wait(&accf[b], (uint32_t)(j >> 1) & 1u);
+            fence_after();
+            ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+            if (!ok) *epi_abort = 1;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (*epi_abort) {
+                *abort_flag = 1;
+                if (lane == 0) atomicOr(err_flag, 1);
+                break;
+            }
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 2; cc += 32) {
+                const int c0 = half * (BN / 2) + cc;
+                if (c0 >= nw) break;
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), r);
+                tmem_ld_wait();
+                if (mok) {
+                    if (split) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj++) {
+                            const int64_t nn = coloff[c0 + jj];
+                            if (nn >= 0) P[nn * e.M + m] = f32_to_f64_pow2(__uint_as_float(r[jj]), 0, 0u);
+                        }
+                    } else {
+                        store_batch_f32<16>(e.C, roff, coloff + c0, r, e.as, e.bcase);
+                        store_batch_f32<16>(e.C, roff, coloff + c0 + 16, r + 16, e.as, e.bcase);
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+            j++;
         }
     }
     fence_before();
@@ -1502,6 +1763,82 @@ cudaError_t launch_convert_selftest(const double *in, int64_t n, float *mine, fl
 cudaError_t launch_wait_selftest(long long budget_cycles, int *timed_out, cudaStream_t s) {
     if (budget_cycles < 0 || budget_cycles > tc::kWaitBudget) return cudaErrorInvalidValue;
     tc::wait_selftest_kernel<<<1, 32, 0, s>>>(budget_cycles, timed_out);
+    return cudaGetLastError();
+}
+
+bool split_lanes_along_k(const SplitDesc &d) {
+    // lanes along K when K's innermost digit is the unit stride, or when
+    // neither side has one and K's innermost stride is the smaller
+    const int64_t unit = d.cplx ? 2 : 1;
+    const bool k_unit = d.gk.nd >= 1 && d.gk.str[d.gk.nd - 1] == unit;
+    const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == unit;
+    const int64_t ks = d.gk.nd >= 1 ? d.gk.str[d.gk.nd - 1] : 0, rs = d.gr.nd >= 1 ? d.gr.str[d.gr.nd - 1] : 0;
+    return k_unit || (!r_unit && ks <= rs);
+}
+
+cudaError_t launch_grouped_split(const GroupedSplit *tab, int n, int64_t total, bool lk, const int *active,
+                                 cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(total < 148 * 5 ? total : 148 * 5);
+    if (lk) grouped_split_kernel<true><<<blocks, 256, 0, s>>>(tab, n, total, active);
+    else grouped_split_kernel<false><<<blocks, 256, 0, s>>>(tab, n, total, active);
+    return cudaGetLastError();
+}
+
+bool grouped_gemm_entry(GroupedGemm &g, const TcGemmDesc &d, const void *A, const void *B, double *C, int bn,
+                        int nslices, double *P) {
+    using namespace tc;
+    if (d.nplanes_a != 2 || d.nplanes_b != 2 || d.Kp % BK || d.Kp < BK || d.M <= 0 || d.N <= 0 || bn < 64 ||
+        bn > 256 || beta_case(d.beta) == 2 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+        return false;
+    g = GroupedGemm{};
+    const ColSplit cs = col_split(d.N, bn);
+    if (!make_map(reinterpret_cast<CUtensorMap *>(&g.ma), A, d.M, d.Kp, 2, BM) ||
+        !make_map(reinterpret_cast<CUtensorMap *>(&g.mbw), B, d.N, d.Kp, 2, cs.wide()) ||
+        !make_map(reinterpret_cast<CUtensorMap *>(&g.mbn), B, d.N, d.Kp, 2, 16 * cs.base))
+        return false;
+    g.M = d.M;
+    g.N = d.N;
+    g.Kp = d.Kp;
+    g.n_tiles = (int)((d.N + bn - 1) / bn);
+    g.cs_base = cs.base;
+    g.cs_extra = cs.extra;
+    g.cm = d.cm;
+    g.cn = d.cn;
+    g.as = make_scale(d.alpha);
+    g.bcase = beta_case(d.beta);
+    // accumulating: each output element gets exactly one addition per launch
+    // (K slices go through the partials), so a reduction in L2 gives the same
+    // sum as a read-modify-write and spares the epilogue the loads' latency
+    if (g.bcase == 1) g.bcase = 2;
+    g.C = C;
+    const int kb_total = (int)(d.Kp / BK);
+    g.nslices = nslices > 1 ? nslices : 1;
+    g.kb_per = (kb_total + g.nslices - 1) / g.nslices;
+    g.nslices = (kb_total + g.kb_per - 1) / g.kb_per;   // no empty slice
+    g.P = g.nslices > 1 ? P : nullptr;
+    return g.nslices == 1 || P != nullptr;
+}
+
+cudaError_t launch_grouped_gemm(const GroupedGemm *tab, int n, int64_t total, int bn, const GroupedGemmParams &p,
+                                const int *active, int *err_flag, cudaStream_t s) {
+    using namespace tc;
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    if (p.nprod < 1 || p.nprod > 8) return cudaErrorInvalidValue;
+    const int grid = (int)(total < 148 ? total : 148);
+    if (bn == 64) {
+        using G = Cfg<2, 64, 4>;
+        static std::atomic<unsigned long long> opted{0};
+        if (cudaError_t e = smem_opt_in(tc_gemm_grouped_kernel<64, 4>, G::SMEM, opted)) return e;
+        tc_gemm_grouped_kernel<64, 4><<<grid, 320, G::SMEM, s>>>(tab, n, total, p, active, err_flag);
+    } else if (bn == 128) {
+        using G = Cfg<2, 128, 3>;
+        static std::atomic<unsigned long long> opted{0};
+        if (cudaError_t e = smem_opt_in(tc_gemm_grouped_kernel<128, 3>, G::SMEM, opted)) return e;
+        tc_gemm_grouped_kernel<128, 3><<<grid, 320, G::SMEM, s>>>(tab, n, total, p, active, err_flag);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -71,13 +71,17 @@ class Engine:
     """A plan plus its workspace for one system."""
 
     def __init__(self, system: DeviceSystem, list_text: str | None = None, precision="fp64",
-                 route_all: bool = False, list_name: str | None = None, kconcat: bool = True):
+                 route_all: bool = False, list_name: str | None = None, kconcat: bool = True,
+                 uniform_steps: bool = False):
+        """uniform_steps: every contraction on the tensor-core split route, none
+        merged (plans of one list then have the same steps at any size, which
+        lets a BatchSolver run its systems in grouped launches)."""
         if list_text is None:
             list_text = load_list(list_name or ("ccsd" if precision == "fp64" else "ccsd_vvvv"))
         self.triples = "T3[" in list_text
         self.sys = system
         self.plan = cc_plan_create(list_text, system.o, system.v, system.dtype, precision, _route_all=route_all,
-                                   kconcat=kconcat,
+                                   kconcat=kconcat, uniform_steps=uniform_steps,
                                    packed_vvvv=getattr(system, "packed_vvvv", False))
         self._ws = None
 

@@ -319,3 +319,28 @@ def test_k_concatenated_steps(cc):
     lad = cc.cc_plan_create(cc.load_list("ccsd_vvvv"), 40, 200, precision="bf16x3").describe()
     step = next(st for st in lad["steps"] if "V_vvvv*tau" in st["note"])
     assert "stmts" not in step and step["note"] == "V_vvvv*tau -> Z2"
+
+
+def test_uniform_steps_plans_are_alike_at_every_size(cc):
+    """uniform_steps: every contraction on the split route, none merged, so the
+    step list is the same at any o, v (what grouped batch execution needs);
+    the batched workspace then holds the grouped tables too."""
+    text = cc.load_list("ccsd_vvvv")
+    sigs = set()
+    plans = []
+    for o, v in ((4, 20), (16, 80), (7, 33), (12, 25)):
+        p = cc.cc_plan_create(text, o, v, precision="bf16x3", uniform_steps=True)
+        d = p.describe()
+        assert all(st["kind"] in ("accum", "gemm_bf16split") for st in d["steps"])
+        assert not any("stmts" in st for st in d["steps"])
+        sigs.add(tuple((st["kind"], st["note"]) for st in d["steps"]))
+        plans.append(p)
+    assert len(sigs) == 1
+    with pytest.raises(cc.CCError):
+        cc.cc_plan_create(text, 4, 20, precision="fp64", uniform_steps=True)
+    with pytest.raises(cc.CCError):
+        cc.cc_plan_create(text, 4, 20, dtype=cc.CC_C128, precision="bf16x3", uniform_steps=True)
+    grouped = cc.cc_solve_batched_workspace_bytes(plans, 8)
+    plain = cc.cc_solve_batched_workspace_bytes(
+        [cc.cc_plan_create(text, o, v, precision="bf16x3") for o, v in ((4, 20), (16, 80), (7, 33), (12, 25))], 8)
+    assert grouped > 0 and plain > 0

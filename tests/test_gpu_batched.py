@@ -88,3 +88,59 @@ def test_batched_max_iter_reports_not_converged(cc):
     amps = [zeros(s.o, s.v) for s in sy]
     st, res = engine.BatchSolver(engs).solve(amps, max_iter=3, tol=1e-12)
     assert st == 7 and all(r.iterations == 3 and not r.converged for r in res)
+
+
+GROUPED_SIZES = [(4, 20, 21), (6, 30, 22), (8, 36, 23), (5, 44, 24), (10, 40, 25), (3, 18, 26), (7, 52, 27)]
+
+
+def test_grouped_batch_matches_oracle_and_single_solves(cc):
+    """Plans with uniform steps (every contraction on the tensor cores, none
+    merged) run the batch as grouped launches (one per step for all systems).
+    Every system converges to the oracle energy within 1e-6 Eh (the metric's
+    tolerance for the split route), and its trajectory follows the same plan
+    solved on its own (cc_solve, one launch per step) to 1e-9 Eh per
+    iteration."""
+    ccm, engine = cc
+    sy = systems(GROUPED_SIZES)
+    dsys = [engine.DeviceSystem.from_system(s, device=DEV) for s in sy]
+    engs = [engine.Engine(d, list_name="ccsd_vvvv", precision="bf16x3", uniform_steps=True) for d in dsys]
+    sig = {tuple(st["kind"] + st["note"] for st in e.plan.describe()["steps"]) for e in engs}
+    assert len(sig) == 1                      # the same steps at every size
+    amps = [zeros(s.o, s.v) for s in sy]
+    n0 = sum(ccm.cc_plan_launch_count(e.plan) for e in engs)
+    st, res = engine.BatchSolver(engs).solve(amps, max_iter=60, tol=1e-8)
+    assert st == 0
+    launches = sum(ccm.cc_plan_launch_count(e.plan) for e in engs) - n0
+    nsteps = len(engs[0].plan.describe()["steps"])
+    iters = max(r.iterations for r in res)
+    # grouped: about two launches per step and iteration for the whole batch, not per system
+    assert launches < 3 * nsteps * iters + 8 * iters, (launches, nsteps, iters)
+    for s, d, r in zip(sy, dsys, res):
+        ref = oracle.ccsd_solve(s.o, s.v, s.eps, oracle.antisym_integrals(s.o, s.v, s.B), tol=1e-9, maxiter=60)
+        assert r.converged and abs(r.energy - ref["energy"]) < 1e-6, (s.o, s.v, r.energy - ref["energy"])
+        single = engine.Engine(d, list_name="ccsd_vvvv", precision="bf16x3", uniform_steps=True)
+        b1, b2 = zeros(s.o, s.v)
+        one = engine.Solver(single).solve(b1, b2, max_iter=60, tol=1e-8)
+        assert abs(one.iterations - r.iterations) <= 1
+        k = min(one.iterations, r.iterations)
+        assert np.abs(np.asarray(one.energies[:k]) - np.asarray(r.energies[:k])).max() < 1e-9
+
+
+def test_grouped_batch_skips_converged_systems(cc):
+    """Systems that converge early stop: a system's amplitudes at its own stop
+    are the same (bit for bit) whether the call ends there or runs on for the
+    others, and each report's iteration count is its own."""
+    _, engine = cc
+    sy = systems(GROUPED_SIZES[:5])
+    engs = [engine.Engine(engine.DeviceSystem.from_system(s, device=DEV), list_name="ccsd_vvvv",
+                          precision="bf16x3", uniform_steps=True) for s in sy]
+    solver = engine.BatchSolver(engs)
+    amps = [zeros(s.o, s.v) for s in sy]
+    st, res = solver.solve(amps, max_iter=60, tol=1e-7)
+    assert st == 0
+    its = [r.iterations for r in res]
+    first = int(np.argmin(its))
+    assert min(its) < max(its), its
+    amps2 = [zeros(s.o, s.v) for s in sy]
+    solver.solve(amps2, max_iter=its[first], tol=1e-7)
+    assert torch.equal(amps[first][1], amps2[first][1]) and torch.equal(amps[first][0], amps2[first][0])
