@@ -374,7 +374,7 @@ cc_status cc_plan_create(const char *text, int o, int v, cc_dtype dtype, cc_prec
             delete pl;
             return fail(CC_ERR_UNSUPPORTED, "uniform_steps needs a real split-bf16 plan");
         }
-        flags |= 2;
+        flags |= 2 | 4;
         prec_eff = base + 100;
     }
     if (!build_plan(text, o, v, (int)dtype, prec_eff, pl->plan, err, flags)) {
@@ -897,6 +897,10 @@ bool batch_groupable(int n, const cc_plan *plans) {
                 if (bc == 2 || bc != beta_case(a.acc.beta) || b.acc.cplx || a.static_src != b.static_src ||
                     a.acc.two_src != b.acc.two_src || a.acc.has_add != b.acc.has_add)
                     return false;
+            } else if (b.kind == StepKind::GEMM && a.rows) {
+                if (!b.rows || b.nk || !b.kcat.empty() || b.mixed || b.gemm.f32 != a.gemm.f32 ||
+                    beta_case(b.rg.beta) == 2 || beta_case(b.rg.beta) != beta_case(a.rg.beta))
+                    return false;
             } else if (b.kind == StepKind::GEMM) {
                 if (!same_split_route(a, b) || !same_split_route(a, a)) return false;
             } else {
@@ -932,6 +936,10 @@ int64_t grouped_bytes(int n, const cc_plan *plans) {
     for (size_t k = 0; k < P0.steps.size(); k++) {
         if (P0.steps[k].kind == StepKind::ACCUM) {
             b += al((int64_t)n * (int64_t)sizeof(GroupedAccum));
+            continue;
+        }
+        if (P0.steps[k].rows) {
+            b += al((int64_t)n * (int64_t)sizeof(GroupedRows));
             continue;
         }
         b += 4 * al((int64_t)n * (int64_t)sizeof(GroupedSplit)) + al((int64_t)n * (int64_t)sizeof(GroupedGemm)) +
@@ -984,7 +992,7 @@ BatchLayout batch_layout(int n, const cc_plan *plans, int diis) {
 
 // one launch of a grouped residual evaluation
 struct GroupedLaunch {
-    int kind = 0;                 // 0 elementwise, 1 split, 2 GEMM, 3 K-slice reduction
+    int kind = 0;                 // 0 elementwise, 1 split, 2 GEMM, 3 K-slice reduction, 4 narrow GEMM
     bool first_only = false;      // static sources / cached planes: the first evaluation only
     int64_t off = 0;              // table offset in the grouped region
     int n = 0;                    // entries
@@ -1058,6 +1066,40 @@ cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_
             L.nperm = nperm;
             L.two = s0.acc.two_src != 0;
             L.off = put(t.data(), (int64_t)sizeof(GroupedAccum) * n);
+            GB.launches.push_back(L);
+            continue;
+        }
+        if (s0.rows) {
+            // the narrow kernel: operands read in place, no splits
+            std::vector<GroupedRows> t(n);
+            int nc_max = 1;
+            for (int i = 0; i < n; i++) {
+                const Step &st = plans[i]->plan.steps[k];
+                char *w = W + BL.base[i];
+                GroupedRows &g = t[i];
+                g.d = st.rg;
+                prepare_grouped_rows(g);
+                g.X = resolve(st.a, &ints[i], &amps[i], &R[i], w);
+                g.Y = resolve(st.b, &ints[i], &amps[i], &R[i], w);
+                g.C = resolve(st.out, &ints[i], &amps[i], &R[i], w);
+                if (!g.X || !g.Y || !g.C || g.d.R > 0xffffffffLL)
+                    return fail(CC_ERR_INVALID_ARG, "grouped batch: a narrow GEMM operand is missing");
+                g.sys = i;
+                nc_max = std::max(nc_max, g.d.nc);
+            }
+            const int nc = grouped_rows_nc(nc_max);
+            int64_t items = 0;
+            for (int i = 0; i < n; i++) {
+                t[i].item0 = items;
+                items += grouped_rows_items(t[i], nc);
+            }
+            GroupedLaunch L;
+            L.kind = 4;
+            L.n = n;
+            L.total = items;
+            L.bn = nc;
+            L.flag = s0.gemm.f32 != 0;
+            L.off = put(t.data(), (int64_t)sizeof(GroupedRows) * n);
             GB.launches.push_back(L);
             continue;
         }
@@ -1215,6 +1257,8 @@ cc_status grouped_residual(const GroupedBatch &GB, char *G, bool first, long lon
         else if (L.kind == 2)
             CC_CUDA(launch_grouped_gemm((const GroupedGemm *)(G + L.off), L.n, L.total, L.bn, L.gp, active,
                                         GB.err_flag, s));
+        else if (L.kind == 4)
+            CC_CUDA(launch_grouped_rows((const GroupedRows *)(G + L.off), L.n, L.total, L.bn, L.flag, active, s));
         else
             CC_CUDA(launch_grouped_reduce((const GroupedReduce *)(G + L.off), L.n, L.total, active, s));
         launches++;

@@ -376,66 +376,138 @@ template <int NC> __device__ __forceinline__ void row_fma(double a, const double
     }
 }
 
+// Y rows [k0, k0 + 64) by columns [c0, c0 + NC) of a narrow GEMM, staged in
+// shared memory with the X offsets of those K indices and the C offsets of
+// those columns (block-wide; the caller places barriers around it)
+template <typename CT, int NC> struct RowsSmem {
+    __align__(16) CT ys[64 * NC];
+    int64_t xko[64], cco[NC];
+};
 template <typename CT, int NC>
-__global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kernel(const RowsGemmDesc d, const double *__restrict__ X,
-                                                        const double *__restrict__ Y, double *__restrict__ C) {
-    __shared__ __align__(16) CT ys[64 * NC];
-    __shared__ int64_t xko[64], cco[NC];
+__device__ __forceinline__ void rows_stage(const RowsGemmDesc &d, const double *__restrict__ Y, int k0, int c0,
+                                           RowsSmem<CT, NC> &S) {
     for (int e = threadIdx.x; e < 64 * NC; e += blockDim.x) {
         const int k = e / NC, c = e - k * NC;
-        ys[e] = (k < d.K && c < d.nc) ? down<CT>(__ldg(Y + grp_offset(d.yk, k) + grp_offset(d.yc, c))) : zero<CT>();
+        S.ys[e] = (k0 + k < d.K && c0 + c < d.nc)
+                      ? down<CT>(__ldg(Y + grp_offset(d.yk, k0 + k) + grp_offset(d.yc, c0 + c)))
+                      : zero<CT>();
     }
-    for (int k = threadIdx.x; k < 64; k += blockDim.x) xko[k] = k < d.K ? grp_offset(d.xk, k) : 0;
-    for (int c = threadIdx.x; c < NC; c += blockDim.x) cco[c] = c < d.nc ? grp_offset(d.cc, c) : 0;
-    __syncthreads();
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < d.R; r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t xo = grp_offset32(d.xr, (uint32_t)r), co = grp_offset32(d.cr, (uint32_t)r);
-        CT acc[NC];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) S.xko[k] = k0 + k < d.K ? grp_offset(d.xk, k0 + k) : 0;
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) S.cco[c] = c0 + c < d.nc ? grp_offset(d.cc, c0 + c) : 0;
+}
+
+// One work item of a narrow GEMM: 256 rows (one per thread) by the column
+// chunk cc (NC columns), all of K in chunks of 64 staged in shared memory.
+// `staged` (block-uniform) names the column chunk already in shared memory
+// when K fits one chunk (then Y is loaded once for many items), else -1.
+template <typename CT, int NC>
+__device__ __forceinline__ void rows_item(const RowsGemmDesc &d, const double *__restrict__ X,
+                                          const double *__restrict__ Y, double *__restrict__ C, int64_t rb, int cc,
+                                          RowsSmem<CT, NC> &S, int64_t &staged, int64_t key) {
+    const int nkc = (d.K + 63) / 64;
+    const int64_t r = rb * 256 + threadIdx.x;
+    const bool rok = r < d.R;
+    const int64_t xo = rok ? grp_offset32(d.xr, (uint32_t)r) : 0, co = rok ? grp_offset32(d.cr, (uint32_t)r) : 0;
+    const int c0 = cc * NC;
+    CT acc[NC];
 #pragma unroll
-        for (int c = 0; c < NC; c++) acc[c] = zero<CT>();
-        // eight loads in flight per thread before their products (ys rows k >= K are zero)
-        for (int k0 = 0; k0 < d.K; k0 += 8) {
-            // the eight loads first: a conversion may call out on its rare path
-            double ad[8];
-            CT a[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) ad[j] = k0 + j < d.K ? __ldg(X + xo + xko[k0 + j]) : 0.0;
-#pragma unroll
-            for (int j = 0; j < 8; j++) a[j] = down<CT>(ad[j]);
-#pragma unroll
-            for (int j = 0; j < 8; j++) row_fma<NC>(a[j], ys + (k0 + j) * NC, acc);
+    for (int c = 0; c < NC; c++) acc[c] = zero<CT>();
+    for (int kc = 0; kc < nkc; kc++) {
+        if (nkc > 1 || staged != key) {
+            __syncthreads();                     // the block is done with the staged chunk
+            rows_stage<CT, NC>(d, Y, kc * 64, c0, S);
+            __syncthreads();
+            staged = nkc == 1 ? key : -1;
         }
-        // beta 0: plain stores; beta 1: read-modify-write in batches of eight
-        // (loads issued before the stores); a general beta was applied before
-        if (d.bcase == 0) {
+        const int kn = d.K - kc * 64 < 64 ? d.K - kc * 64 : 64;
+        if (rok) {
+            // eight loads in flight per thread before their products (ys rows past K are zero)
+            for (int k0 = 0; k0 < kn; k0 += 8) {
+                // the eight loads first: a conversion may call out on its rare path
+                double ad[8];
+                CT a[8];
 #pragma unroll
-            for (int c = 0; c < NC; c++)
-                if (c < d.nc) C[co + cco[c]] = epi_scale(acc[c], d.as);
-        } else if (d.red) {
+                for (int j = 0; j < 8; j++) ad[j] = k0 + j < kn ? __ldg(X + xo + S.xko[k0 + j]) : 0.0;
 #pragma unroll
-            for (int c = 0; c < NC; c++)
-                if (c < d.nc) red_add(C + co + cco[c], epi_scale(acc[c], d.as));
-        } else {
+                for (int j = 0; j < 8; j++) a[j] = down<CT>(ad[j]);
 #pragma unroll
-            for (int c0 = 0; c0 < NC; c0 += 8) {
-                double old[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) old[j] = c0 + j < d.nc ? C[co + cco[c0 + j]] : 0.0;
-#pragma unroll
-                for (int j = 0; j < 8; j++)
-                    if (c0 + j < d.nc) C[co + cco[c0 + j]] = epi_scale(acc[c0 + j], d.as) + old[j];
+                for (int j = 0; j < 8; j++) row_fma<NC>(a[j], S.ys + (k0 + j) * NC, acc);
             }
+        }
+    }
+    if (!rok) return;
+    const int ncc = d.nc - c0 < NC ? d.nc - c0 : NC;
+    // beta 0: plain stores; beta 1: read-modify-write in batches of eight
+    // (loads issued before the stores) or reductions; a general beta was applied before
+    if (d.bcase == 0) {
+#pragma unroll
+        for (int c = 0; c < NC; c++)
+            if (c < ncc) C[co + S.cco[c]] = epi_scale(acc[c], d.as);
+    } else if (d.red) {
+#pragma unroll
+        for (int c = 0; c < NC; c++)
+            if (c < ncc) red_add(C + co + S.cco[c], epi_scale(acc[c], d.as));
+    } else {
+#pragma unroll
+        for (int cb = 0; cb < NC; cb += 8) {
+            double old[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) old[j] = cb + j < ncc ? C[co + S.cco[cb + j]] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (cb + j < ncc) C[co + S.cco[cb + j]] = epi_scale(acc[cb + j], d.as) + old[j];
         }
     }
 }
 
+// items: (column chunk, block of 256 rows), column chunk outermost so a block
+// keeps one chunk of Y staged across its items
+template <typename CT, int NC>
+__global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kernel(const RowsGemmDesc d, const double *__restrict__ X,
+                                                        const double *__restrict__ Y, double *__restrict__ C) {
+    __shared__ RowsSmem<CT, NC> S;
+    const int64_t rblocks = (d.R + 255) / 256;
+    const int64_t items = rblocks * ((d.nc + NC - 1) / NC);
+    int64_t staged = -1;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int cc = (int)(it / rblocks);
+        rows_item<CT, NC>(d, X, Y, C, it - (int64_t)cc * rblocks, cc, S, staged, cc);
+    }
+}
+
+// the grouped form: entry e's items follow item0, each entry's Y staged once
+// per (entry, column chunk) a block meets
+template <typename CT, int NC>
+__global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) grouped_rows_kernel(const GroupedRows *__restrict__ tab,
+                                                                                      int n, int64_t total,
+                                                                                      const int *__restrict__ active) {
+    __shared__ RowsSmem<CT, NC> S;
+    int64_t staged = -1;
+    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupedRows &e = tab[lo];
+        if (!active[e.sys]) continue;            // block-uniform
+        const int64_t rblocks = (e.d.R + 255) / 256, local = it - e.item0;
+        const int cc = (int)(local / rblocks);
+        rows_item<CT, NC>(e.d, e.X, e.Y, e.C, local - (int64_t)cc * rblocks, cc, S, staged, (int64_t)lo * 4096 + cc);
+    }
+}
+
+template <typename CT, int NC> constexpr int rows_grid_cap() { return 148 * rows_min_blocks<CT, NC>(); }
+
 template <typename CT>
 static cudaError_t rows_t(const RowsGemmDesc &d, const double *X, const double *Y, double *C, cudaStream_t s) {
-    int64_t blocks = (d.R + 255) / 256;
-    if (blocks > 148 * 3) blocks = 148 * 3;
+    // accumulators: the column count rounded up to a multiple of 8 (chunks of 64 beyond)
+    const int nc8 = d.nc > 64 ? 64 : (d.nc + 7) / 8 * 8;
+    const int64_t items = (d.R + 255) / 256 * ((d.nc + nc8 - 1) / nc8);
+    int64_t blocks = items < 148 * 3 ? items : 148 * 3;
     const unsigned b = (unsigned)blocks;
-    // accumulators: the column count rounded up to a multiple of 8
-    switch ((d.nc + 7) / 8) {
+    switch (nc8 / 8) {
         case 1: rows_gemm_kernel<CT, 8><<<b, 256, 0, s>>>(d, X, Y, C); break;
         case 2: rows_gemm_kernel<CT, 16><<<b, 256, 0, s>>>(d, X, Y, C); break;
         case 3: rows_gemm_kernel<CT, 24><<<b, 256, 0, s>>>(d, X, Y, C); break;
@@ -452,13 +524,50 @@ cudaError_t launch_rows_gemm(const RowsGemmDesc &d0, const double *X, const doub
     RowsGemmDesc d = d0;
     d.bcase = beta_case(d.beta);
     d.as = make_scale(d.alpha);
-    if (d.nc < 1 || d.nc > 64 || d.K < 1 || d.K > 64 || d.R > 0xffffffffLL) return cudaErrorInvalidValue;
+    if (d.nc < 1 || d.K < 1 || d.R > 0xffffffffLL) return cudaErrorInvalidValue;
     if (d.bcase == 2) {
         if (cudaError_t e = launch_scale_grp(d.R, d.nc, d.cr, d.cc, d.beta, C, s)) return e;
         d.beta = 1.0;
         d.bcase = 1;
     }
     return d.f32 ? rows_t<float>(d, X, Y, C, s) : rows_t<double>(d, X, Y, C, s);
+}
+
+void prepare_grouped_rows(GroupedRows &g) {
+    g.d.bcase = beta_case(g.d.beta);
+    g.d.as = make_scale(g.d.alpha);
+    // one addition per output element and launch: a reduction in L2 gives the
+    // same sum as a read-modify-write, without the loads' latency
+    if (g.d.bcase == 1) g.d.red = 1;
+}
+
+int grouped_rows_nc(int nc_max) { return nc_max > 48 ? 64 : (nc_max + 7) / 8 * 8; }   // the kernels' widths
+
+int64_t grouped_rows_items(const GroupedRows &g, int nc) {
+    return (g.d.R + 255) / 256 * ((g.d.nc + nc - 1) / nc);
+}
+
+cudaError_t launch_grouped_rows(const GroupedRows *tab, int n, int64_t total, int nc, bool f32, const int *active,
+                                cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(total < 148 * 3 ? total : 148 * 3);
+#define CCB_GROUPED_ROWS_NC(NCV)                                                                                     \
+    do {                                                                                                             \
+        if (f32) grouped_rows_kernel<float, NCV><<<blocks, 256, 0, s>>>(tab, n, total, active);                     \
+        else grouped_rows_kernel<double, NCV><<<blocks, 256, 0, s>>>(tab, n, total, active);                        \
+    } while (0)
+    switch (nc / 8) {
+        case 1: CCB_GROUPED_ROWS_NC(8); break;
+        case 2: CCB_GROUPED_ROWS_NC(16); break;
+        case 3: CCB_GROUPED_ROWS_NC(24); break;
+        case 4: CCB_GROUPED_ROWS_NC(32); break;
+        case 5: CCB_GROUPED_ROWS_NC(40); break;
+        case 6: CCB_GROUPED_ROWS_NC(48); break;
+        case 8: CCB_GROUPED_ROWS_NC(64); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef CCB_GROUPED_ROWS_NC
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ rows_multi

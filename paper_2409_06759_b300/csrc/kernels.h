@@ -97,10 +97,11 @@ struct GemmF64Desc {
 };
 
 // Narrow GEMM: C(r, c) = alpha * sum_k X(r, k) Y(k, c) + beta * C(r, c) for
-// many rows r, at most 64 columns c and a contraction of at most 64: the
-// rank-o updates of T3 and similar shapes that tensor tiles would pad.  Every
-// operand and the output are read through mixed-radix groups, so no operand is
-// permuted first; one thread per row, Y staged in shared memory.
+// many rows r and a short side c (the rank-o updates of T3, products with T1
+// and the F intermediates: shapes that tensor tiles would pad).  Every operand
+// and the output are read through mixed-radix groups, so no operand is
+// permuted first; one thread per row, Y staged in shared memory in chunks of
+// 64 contraction indices by up to 64 columns.
 // f32: products and sums in FP32 (FP64 data, one rounding per operand).
 struct RowsGemmDesc {
     int64_t R;
@@ -304,6 +305,18 @@ inline int grouped_kslices(int64_t M, int64_t N, int64_t Kp, int64_t tiles_all) 
     if (ns > cap) ns = cap;
     return ns < 2 ? 1 : (int)ns;
 }
+struct GroupedRows {                // one system's narrow GEMM (bcase / as prepared)
+    RowsGemmDesc d;
+    const double *X, *Y;
+    double *C;
+    int64_t item0;
+    int sys;
+};
+void prepare_grouped_rows(GroupedRows &g);
+int grouped_rows_nc(int nc_max);                       // the column chunk of a launch
+int64_t grouped_rows_items(const GroupedRows &g, int nc);
+cudaError_t launch_grouped_rows(const GroupedRows *tab, int n, int64_t total, int nc, bool f32, const int *active,
+                                cudaStream_t s);
 struct GroupedReduce {              // C = alpha sum_z P[z][n][m] + beta C of one sliced GEMM
     int64_t M, N;
     int nslices;

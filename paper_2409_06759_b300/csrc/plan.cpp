@@ -271,6 +271,7 @@ struct Planner {
     int64_t interm_need = kAlign;   // [status word][intermediates...] at the start of the workspace
     int64_t splits_need = 0;        // planes of non-static split operands, kept for reuse within a residual
     bool mixed_all = false;
+    bool uniform = false;          // uniform steps: routes fixed by the statement's form, not its extents
     bool kcat_declined = false;    // set by plan_kcat when some members run cheaper one by one
     std::vector<char> kcat_keep;   // with it: the members that still gain from merging
     std::vector<int> version;       // per tensor: number of statements that wrote it so far
@@ -1255,6 +1256,15 @@ struct Planner {
         // there (the SIMT FP32 rate, ~60x the FP64 pipe); bf16x6 and FP64 plans
         // keep FP64 for them
         if (!use_mixed && !mixed_all && plan.precision == 2 && !cplx && Mx > 1 && Nx > 1 && Kx > 1) use_f32 = true;
+        // uniform plans (the same steps at any size): a contraction with a
+        // two-index operand (T1 or an F intermediate) goes to the narrow kernel,
+        // every other one to the split route, whatever the extents
+        if (uniform) {
+            const bool mat = s.rhs[0].letters.size() == 2 || s.rhs[1].letters.size() == 2;
+            use_mixed = !mat;
+            use_rows = mat;
+            use_f32 = mat && plan.precision == 2;
+        }
         if (use_mixed && !mixed_all) {
             const int64_t bn = Nx <= 64 ? 64 : Nx <= 128 ? 128 : 256;
             const double eff = (double)Mx * (double)Nx * (double)Kx /
@@ -1749,6 +1759,7 @@ bool build_plan(const std::string &text, int o, int v, int dtype, int precision,
     plan.precision = precision >= 100 ? precision - 100 : precision;
     Planner P(plan);
     P.mixed_all = precision >= 100;
+    P.uniform = (flags & 4) != 0;
     std::istringstream in(text);
     std::string line;
     int lineno = 0;

@@ -331,7 +331,14 @@ def test_uniform_steps_plans_are_alike_at_every_size(cc):
     for o, v in ((4, 20), (16, 80), (7, 33), (12, 25)):
         p = cc.cc_plan_create(text, o, v, precision="bf16x3", uniform_steps=True)
         d = p.describe()
-        assert all(st["kind"] in ("accum", "gemm_bf16split") for st in d["steps"])
+        # contractions with a two-index operand (T1, F) on the narrow kernel, the rest on the tensor cores
+        assert all(st["kind"] in ("accum", "gemm_bf16split", "gemm_rows_f32") for st in d["steps"])
+        stmts = d["statements"]
+        for st in d["steps"]:
+            if st["kind"].startswith("gemm"):
+                ops = stmts[st["stmt"]].split("=", 1)[1]
+                two = any(len(x.split("]")[0]) == 2 for x in ops.split("[")[1:])
+                assert (st["kind"] == "gemm_rows_f32") == two, stmts[st["stmt"]]
         assert not any("stmts" in st for st in d["steps"])
         sigs.add(tuple((st["kind"], st["note"]) for st in d["steps"]))
         plans.append(p)
