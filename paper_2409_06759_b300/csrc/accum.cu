@@ -105,6 +105,83 @@ __global__ void __launch_bounds__(256) accum_kernel(const AccumDesc d, const T *
     for (int64_t r0 = warp * run; r0 < d.total; r0 += nwarps * run) accum_run<T, ACC>(d, src, out, src2, add, r0, lane);
 }
 
+// The generic path with the loads of four elements per lane in flight (one
+// or two terms): a lane takes the flat elements r0 + lane + 32 j, j < 4,
+// decomposes each once (32-bit divisions), issues every term's loads for all
+// four, then sums and stores.  TWO: products of two sources.
+template <bool ACC, int NP, bool TWO>
+__device__ __forceinline__ void accum_run4(const AccumDesc &d, const double *__restrict__ src,
+                                           double *__restrict__ out, const double *__restrict__ src2,
+                                           const double *__restrict__ add, int64_t r0, int lane) {
+    constexpr int J = 4;
+    int64_t oo[J], ao[J], so[NP][J], so2[NP][J];
+    bool ok[J];
+#pragma unroll
+    for (int j = 0; j < J; j++) {
+        const int64_t e = r0 + lane + 32 * j;
+        ok[j] = e < d.total;
+        uint32_t x = ok[j] ? (uint32_t)e : 0u;
+        oo[j] = ao[j] = 0;
+#pragma unroll
+        for (int p = 0; p < NP; p++) so[p][j] = so2[p][j] = 0;
+#pragma unroll
+        for (int k = kMaxDims - 1; k >= 0; k--) {
+            if (k >= d.nd) continue;
+            const uint32_t ex = (uint32_t)d.ext[k], q = x / ex, dg = x - q * ex;
+            x = q;
+            oo[j] += (int64_t)dg * d.ostr[k];
+            if (ACC && d.has_add) ao[j] += (int64_t)dg * d.astr[k];
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+                so[p][j] += (int64_t)dg * d.sstr[p][k];
+                if (TWO) so2[p][j] += (int64_t)dg * d.sstr2[p][k];
+            }
+        }
+    }
+    double xs[NP][J], ys[NP][J], old[J];
+#pragma unroll
+    for (int p = 0; p < NP; p++)
+#pragma unroll
+        for (int j = 0; j < J; j++) {
+            const bool on = ok[j] && p < d.nperm;
+            xs[p][j] = on ? __ldg(src + so[p][j]) : 0.0;
+            ys[p][j] = (TWO && on) ? __ldg(src2 + so2[p][j]) : 0.0;
+        }
+#pragma unroll
+    for (int j = 0; j < J; j++) old[j] = (ACC && ok[j]) ? (d.has_add ? add[ao[j]] : out[oo[j]]) : 0.0;
+#pragma unroll
+    for (int j = 0; j < J; j++) {
+        if (!ok[j]) continue;
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+            if (p >= d.nperm) break;
+            const double t = TWO ? xs[p][j] * ys[p][j] : xs[p][j];
+            acc = signed_term(p == 0, (d.negmask >> p) & 1ull, t, acc);
+        }
+        out[oo[j]] = finish<ACC>(d.as, acc, old[j]);
+    }
+}
+
+template <bool ACC, int NP, bool TWO>
+__global__ void __launch_bounds__(256) grouped_accum4_kernel(const GroupedAccum *__restrict__ tab, int n, int64_t total,
+                                                             const int *__restrict__ active) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t it = warp; it < total; it += nwarps) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupedAccum &e = tab[lo];
+        if (!active[e.sys]) continue;
+        accum_run4<ACC, NP, TWO>(e.d, e.src, e.out, e.src2, e.add, (it - e.item0) * 128, lane);
+    }
+}
+
 // The grouped form (real): entry e's runs are the work items [e.item0,
 // e.item0 + ceil(total / run)); a warp finds its item's entry by binary search.
 template <bool ACC>
@@ -982,16 +1059,30 @@ void prepare_grouped_accum(GroupedAccum &g) {
     }
 }
 
-int64_t grouped_accum_items(const GroupedAccum &g, bool row_path) {
-    if (row_path) return ((int64_t)g.rows + g.rch - 1) / g.rch * (int64_t)g.ncb;
+int64_t grouped_accum_items(const GroupedAccum &g, int mode) {
+    if (mode == 1) return ((int64_t)g.rows + g.rch - 1) / g.rch * (int64_t)g.ncb;
+    if (mode == 2) return (g.d.total + 127) / 128;
     return (g.d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
 }
 
-cudaError_t launch_grouped_accum(const GroupedAccum *tab, int n, int64_t total, bool acc, bool row_path, int nperm,
+cudaError_t launch_grouped_accum(const GroupedAccum *tab, int n, int64_t total, bool acc, int mode, int nperm,
                                  bool two, const int *active, cudaStream_t s) {
     if (n <= 0 || total <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)grid_cap((total + 7) / 8, 148 * 16);
-    if (!row_path) {
+    if (mode == 2) {
+        if (nperm > 2) return cudaErrorInvalidValue;
+#define CCB_ACC4(A, P, T) grouped_accum4_kernel<A, P, T><<<blocks, 256, 0, s>>>(tab, n, total, active)
+        if (acc) {
+            if (nperm <= 1) { if (two) CCB_ACC4(true, 1, true); else CCB_ACC4(true, 1, false); }
+            else { if (two) CCB_ACC4(true, 2, true); else CCB_ACC4(true, 2, false); }
+        } else {
+            if (nperm <= 1) { if (two) CCB_ACC4(false, 1, true); else CCB_ACC4(false, 1, false); }
+            else { if (two) CCB_ACC4(false, 2, true); else CCB_ACC4(false, 2, false); }
+        }
+#undef CCB_ACC4
+        return cudaGetLastError();
+    }
+    if (mode == 0) {
         if (acc) grouped_accum_kernel<true><<<blocks, 256, 0, s>>>(tab, n, total, active);
         else grouped_accum_kernel<false><<<blocks, 256, 0, s>>>(tab, n, total, active);
         return cudaGetLastError();

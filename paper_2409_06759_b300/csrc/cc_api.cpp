@@ -998,7 +998,8 @@ struct GroupedLaunch {
     int n = 0;                    // entries
     int64_t total = 0;            // work items of all entries
     bool flag = false;            // elementwise: accumulate; split: lanes along K
-    bool row_path = false, two = false;   // elementwise: the row path, products of two sources
+    int mode = 0;                 // elementwise: 0 generic, 1 row path, 2 generic, four loads per lane
+    bool two = false;             // elementwise: products of two sources
     int nperm = 1;
     int bn = 64;
     GroupedGemmParams gp{};
@@ -1051,10 +1052,15 @@ cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_
                 rowp = rowp && g.row_path;
                 nperm = std::max(nperm, g.d.nperm);
             }
-            // the row path when it holds for every system, else the generic one
+            // one or two terms: the generic path with four elements' loads in flight
+            // per lane (short rows leave the row path's lanes idle); else the row
+            // path when it holds for every system, else the plain generic one
+            bool small = true;            // 32-bit element indices
+            for (int i = 0; i < n; i++) small = small && t[i].d.total < ((int64_t)1 << 31);
+            const int mode = nperm <= 2 && small ? 2 : rowp ? 1 : 0;
             for (int i = 0; i < n; i++) {
                 t[i].item0 = items;
-                items += grouped_accum_items(t[i], rowp);
+                items += grouped_accum_items(t[i], mode);
             }
             GroupedLaunch L;
             L.kind = 0;
@@ -1062,7 +1068,7 @@ cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_
             L.n = n;
             L.total = items;
             L.flag = beta_case(s0.acc.beta) == 1;
-            L.row_path = rowp;
+            L.mode = mode;
             L.nperm = nperm;
             L.two = s0.acc.two_src != 0;
             L.off = put(t.data(), (int64_t)sizeof(GroupedAccum) * n);
@@ -1250,7 +1256,7 @@ cc_status grouped_residual(const GroupedBatch &GB, char *G, bool first, long lon
     for (const GroupedLaunch &L : GB.launches) {
         if (L.first_only && !first) continue;
         if (L.kind == 0)
-            CC_CUDA(launch_grouped_accum((const GroupedAccum *)(G + L.off), L.n, L.total, L.flag, L.row_path, L.nperm,
+            CC_CUDA(launch_grouped_accum((const GroupedAccum *)(G + L.off), L.n, L.total, L.flag, L.mode, L.nperm,
                                          L.two, active, s));
         else if (L.kind == 1)
             CC_CUDA(launch_grouped_split((const GroupedSplit *)(G + L.off), L.n, L.total, L.flag, active, s));

@@ -362,14 +362,15 @@ bool grouped_gemm_entry(GroupedGemm &g, const TcGemmDesc &d, const void *A, cons
 // host: the split kernel's lane orientation for a descriptor (lanes along K)
 bool split_lanes_along_k(const SplitDesc &d);
 void prepare_grouped_accum(GroupedAccum &g);
-// work items of an entry on the row path or the generic path
-int64_t grouped_accum_items(const GroupedAccum &g, bool row_path);
+// work items of an entry: mode 0 generic (runs of 256), 1 row path, 2 generic
+// with four elements' loads in flight per lane (runs of 128; one or two terms)
+int64_t grouped_accum_items(const GroupedAccum &g, int mode);
 // the launches: tab (device) holds n entries; total = the work items of all
 cudaError_t launch_grouped_split(const GroupedSplit *tab, int n, int64_t total, bool lk, const int *active,
                                  cudaStream_t s);
 cudaError_t launch_grouped_gemm(const GroupedGemm *tab, int n, int64_t total, int bn, const GroupedGemmParams &p,
                                 const int *active, int *err_flag, cudaStream_t s);
-cudaError_t launch_grouped_accum(const GroupedAccum *tab, int n, int64_t total, bool acc, bool row_path, int nperm,
+cudaError_t launch_grouped_accum(const GroupedAccum *tab, int n, int64_t total, bool acc, int mode, int nperm,
                                  bool two, const int *active, cudaStream_t s);
 cudaError_t launch_grouped_post(const GroupedPost *tab, int n, int64_t total, const int *active, cudaStream_t s);
 cudaError_t launch_grouped_reduce(const GroupedReduce *tab, int n, int64_t total, const int *active, cudaStream_t s);
