@@ -204,12 +204,22 @@ CC_API cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_am
  * fastest on this device for these inputs: each candidate the plan prepared
  * room for is timed reps times (CUDA events, minimum taken) in place of the
  * planned one, the steps running in list order so every operand is real.
- * Results stay in the plan (cc_plan_describe reports "tuned").  The paper has
- * no counterpart (its contractions run in ExaTENSOR).
+ * Results stay in the plan (cc_plan_describe reports "tuned") and in a
+ * process-wide cache keyed by the contraction's route, shape (M, N, K), product
+ * count, arithmetic, dtype, beta and candidate set: a contraction of that key
+ * in any later autotuned plan (e.g. a same-sized system of a batch) takes the
+ * stored pick without timing.  The paper has no counterpart (its contractions
+ * run in ExaTENSOR).
  *   ints, amps, ws: as for cc_residual.  res: receives unspecified values.
  *   reps: 1..100 timings per candidate.  Synchronises the stream. */
 CC_API cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res,
                                   void *ws, size_t ws_bytes, void *stream, int reps);
+
+/* cc_autotune_cache -- the process-wide tuning cache of cc_plan_autotune:
+ * clear = 1 empties it; *entries / *hits (either may be NULL) receive its size
+ * and the number of contractions served from it since the last clear.  Host
+ * only; thread-safe. */
+CC_API cc_status cc_autotune_cache(int clear, long long *entries, long long *hits);
 
 /* cc_plan_set_gemm_config -- sets the configuration of one contraction step
  * (the steps of cc_plan_describe, 0-based) to one of its autotuning

@@ -34,7 +34,8 @@ EXPORTS = ["cc_plan_create", "cc_plan_workspace_bytes", "cc_plan_describe", "cc_
            "cc_build_integrals_workspace_bytes", "cc_build_integrals", "cc_energy_noalloc", "cc_packed_t2_elems",
            "cc_pack_t2", "cc_unpack_t2", "cc_status_string",
            "cc_last_error", "cc_version", "cc_solve_batched_workspace_bytes", "cc_solve_batched",
-           "cc_plan_autotune", "cc_plan_set_gemm_config", "cc_build_vvvv_packed_workspace_bytes", "cc_build_vvvv_packed",
+           "cc_plan_autotune", "cc_autotune_cache", "cc_plan_set_gemm_config", "cc_build_vvvv_packed_workspace_bytes",
+           "cc_build_vvvv_packed",
            "cc_selftest_wait_timeout", "cc_selftest_convert"]
 
 if not os.path.exists(LIB_PATH):
@@ -339,6 +340,13 @@ def cc_solve(plan: Plan, ints: dict, t1, t2, ws, max_iter: int = 100, tol: float
                            [complex(a, b) for a, b in zip(en[:k], ei[:k])], list(rn[:k]))
     return SolveResult(st, k, bool(rep.converged), rep.switched_at, rep.energy, rep.rnorm, list(en[:k]),
                        list(rn[:k]))
+
+
+def cc_autotune_cache(clear: bool = False):
+    """(entries, hits) of the process-wide shape-keyed tuning cache; clear empties it."""
+    e, h = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.cc_autotune_cache(int(clear), ctypes.byref(e), ctypes.byref(h)), "cc_autotune_cache")
+    return e.value, h.value
 
 
 def cc_solve_batched_workspace_bytes(plans, diis_max: int = 8) -> int:

@@ -8,6 +8,9 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -470,6 +473,53 @@ cc_status cc_residual(cc_plan plan, const cc_integrals *ints, const cc_amps *amp
     return run_residual(plan, ints, amps, res, ws, ws_bytes, (cudaStream_t)stream, false);
 }
 
+}  // extern "C"
+
+namespace {
+// Shape-keyed tuning results shared by every plan of the process: a contraction
+// whose route, shape and candidate set were timed before (on any plan, e.g. a
+// same-sized system of a batch) takes the stored pick without timing again.
+struct TuneKey {
+    int route;                  // 0 tiled GEMM, 1 narrow, 2 split route
+    int64_t M, N, K;
+    int prod, f32, cplx, beta, ncand;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(route, M, N, K, prod, f32, cplx, beta, ncand) <
+               std::tie(o.route, o.M, o.N, o.K, o.prod, o.f32, o.cplx, o.beta, o.ncand);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 3>> g_tune;
+long long g_tune_hits = 0;
+
+TuneKey tune_key(const Step &st) {
+    TuneKey k{};
+    k.route = st.mixed ? 2 : st.rows ? 1 : 0;
+    k.M = st.mixed ? st.tc.M : st.gemm.M;
+    k.N = st.mixed ? st.tc.N : st.gemm.N;
+    k.K = st.mixed ? st.tc.Kp : st.gemm.K;
+    k.prod = st.mixed ? st.tc.nprod : 0;
+    k.f32 = st.gemm.f32;
+    k.cplx = st.mixed ? st.split_a.cplx : st.gemm.cplx;
+    k.beta = beta_case(st.mixed ? st.tc.beta : st.rows ? st.rg.beta : st.gemm.beta);
+    k.ncand = (int)st.cands.size();
+    return k;
+}
+}  // namespace
+
+extern "C" {
+
+cc_status cc_autotune_cache(int clear, long long *entries, long long *hits) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (clear) {
+        g_tune.clear();
+        g_tune_hits = 0;
+    }
+    if (entries) *entries = (long long)g_tune.size();
+    if (hits) *hits = g_tune_hits;
+    return CC_OK;
+}
+
 cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps *amps, cc_resid *res, void *ws,
                            size_t ws_bytes, void *stream, int reps) {
     if (!plan) return fail(CC_ERR_INVALID_ARG, "NULL plan");
@@ -491,9 +541,22 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
         st = exec_step(plan, stp, ints, amps, res, w, s, true, nullptr);
         if (st != CC_OK) { result = st; break; }
         if (stp.cands.size() < 2) continue;
-        double best = 1e30;
+        const TuneKey key = tune_key(stp);
         std::array<int, 3> pick = stp.cands[0];
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end() &&
+                std::find(stp.cands.begin(), stp.cands.end(), it->second) != stp.cands.end()) {
+                pick = it->second;
+                cached = true;
+                g_tune_hits++;
+            }
+        }
+        double best = 1e30;
         for (const auto &c : stp.cands) {
+            if (cached) break;
             Step trial = stp;
             if (trial.mixed) {
                 trial.tc.bn = c[0];
@@ -520,6 +583,10 @@ cc_status cc_plan_autotune(cc_plan plan, const cc_integrals *ints, const cc_amps
             if (acc < best) { best = acc; pick = c; }
         }
         if (result != CC_OK) break;
+        if (!cached) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = pick;
+        }
         if (stp.mixed) {
             stp.tc.bn = pick[0];
             stp.tc.splitk = pick[1];

@@ -144,3 +144,25 @@ def test_grouped_batch_skips_converged_systems(cc):
     amps2 = [zeros(s.o, s.v) for s in sy]
     solver.solve(amps2, max_iter=its[first], tol=1e-7)
     assert torch.equal(amps[first][1], amps2[first][1]) and torch.equal(amps[first][0], amps2[first][0])
+
+
+def test_autotune_cache_serves_same_shaped_contractions(cc):
+    """cc_plan_autotune keeps each pick in a process-wide cache keyed by the
+    contraction's route and shape: a second plan of the same system size takes
+    every pick from it (no timing) and ends with the same configurations."""
+    ccm, engine = cc
+    s = systems([(6, 30, 31)])[0]
+    d = engine.DeviceSystem.from_system(s, device=DEV)
+    ccm.cc_autotune_cache(clear=True)
+    a = engine.Engine(d, list_name="ccsd_vvvv", precision="bf16x3")
+    a.autotune(*zeros(s.o, s.v), reps=1)
+    n1, h1 = ccm.cc_autotune_cache()
+    tunable = sum(1 for st in a.plan.describe()["steps"] if len(st.get("configs", [])) >= 2)
+    assert n1 >= 1 and h1 <= tunable
+    b = engine.Engine(d, list_name="ccsd_vvvv", precision="bf16x3")
+    b.autotune(*zeros(s.o, s.v), reps=1)
+    n2, h2 = ccm.cc_autotune_cache()
+    assert n2 == n1 and h2 - h1 == tunable
+    pick = lambda e: [(st.get("bn"), st["splitk"], st.get("red")) for st in e.plan.describe()["steps"]
+                      if len(st.get("configs", [])) >= 2]
+    assert pick(a) == pick(b)
