@@ -854,6 +854,8 @@ def run_batched(args, world, rank, local, suite=False):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sizes = ccinputs.batched_sizes(64, seed=0)
+    if args.batched_quick and args.batched_count:
+        sizes = sizes[:args.batched_count]          # profiler captures on a smaller device footprint
     sysl = [ccinputs.make_system(o, v, L=120, seed=sd) for o, v, sd in sizes]
     dsys = [DeviceSystem.from_system(s, device=dev) for s in sysl]
     stream = torch.cuda.current_stream(dev)
@@ -990,6 +992,8 @@ def main():
                     help="ccsdt: the o=8 v=64 CCSDT workload (generated list); batched: 64 uneven CCSD systems; "
                          "ladder: the particle-ladder contraction alone (profiler captures)")
     ap.add_argument("--ladder-size", default="20,100", help="o,v of --workload ladder")
+    ap.add_argument("--batched-count", type=int, default=0,
+                    help="--batched-quick: the first N of the 64 systems (profiler captures)")
     ap.add_argument("--batched-quick", action="store_true",
                     help="--workload batched: bf16x3 only, untuned, one two-iteration solve (profiler captures)")
     ap.add_argument("--cpu-leg", default=None, choices=["small"], help=argparse.SUPPRESS)

@@ -27,6 +27,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "grouped.cuh"
 #include "kernels.h"
 #include "scalar.cuh"
 
@@ -149,6 +150,26 @@ __device__ __forceinline__ void accum_run4(const AccumDesc &d, const double *__r
         }
 #pragma unroll
     for (int j = 0; j < J; j++) old[j] = (ACC && ok[j]) ? (d.has_add ? add[ao[j]] : out[oo[j]]) : 0.0;
+    // accumulating products start from the old value and add each term with
+    // one FMA, the sign and alpha (+-2^k) riding on a factor: nterms FP64
+    // operations per element instead of 2 nterms
+    if (TWO && ACC && !d.as.general) {
+        const bool fold = !(d.as.kexp == 0 && d.as.sflip == 0);
+#pragma unroll
+        for (int j = 0; j < J; j++) {
+            if (!ok[j]) continue;
+            double acc = old[j];
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+                if (p >= d.nperm) break;
+                double sa = ((d.negmask >> p) & 1ull) ? neg(xs[p][j]) : xs[p][j];
+                if (fold) sa = scale_f64(sa, d.as);
+                acc = fma(sa, ys[p][j], acc);
+            }
+            out[oo[j]] = acc;
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < J; j++) {
         if (!ok[j]) continue;
@@ -167,39 +188,181 @@ template <bool ACC, int NP, bool TWO>
 __global__ void __launch_bounds__(256) grouped_accum4_kernel(const GroupedAccum *__restrict__ tab, int n, int64_t total,
                                                              const int *__restrict__ active) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t it = warp; it < total; it += nwarps) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const GroupedAccum &e = tab[lo];
-        if (!active[e.sys]) continue;
+    const WorkRange wr = work_range(total, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                                    (int64_t)gridDim.x * (blockDim.x >> 5));
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedAccum> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const GroupedAccum &e = tab[walk.at(it)];
+        if (!active[e.sys]) { it = walk.next - 1; continue; }   // the rest of a converged system
         accum_run4<ACC, NP, TWO>(e.d, e.src, e.out, e.src2, e.add, (it - e.item0) * 128, lane);
     }
 }
 
 // The grouped form (real): entry e's runs are the work items [e.item0,
-// e.item0 + ceil(total / run)); a warp finds its item's entry by binary search.
+// e.item0 + ceil(total / run)); each warp takes a contiguous range of items
+// (grouped.cuh).
 template <bool ACC>
 __global__ void __launch_bounds__(256) grouped_accum_kernel(const GroupedAccum *__restrict__ tab, int n, int64_t total,
                                                             const int *__restrict__ active) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t it = warp; it < total; it += nwarps) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const GroupedAccum &e = tab[lo];
-        if (!active[e.sys]) continue;
+    const WorkRange wr = work_range(total, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                                    (int64_t)gridDim.x * (blockDim.x >> 5));
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedAccum> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const GroupedAccum &e = tab[walk.at(it)];
+        if (!active[e.sys]) { it = walk.next - 1; continue; }
         accum_run<double, ACC>(e.d, e.src, e.out, e.src2, e.add, (it - e.item0) * (32 * kAccChunk), lane);
+    }
+}
+
+// ------------------------------------------------------ grouped, compact
+// The grouped elementwise pass on compact entries (GroupedEw): a warp's run
+// is kEwRun consecutive output elements, lane l taking r0 + l + 32 j.  A lane
+// decomposes its first element once and then steps its digits by 32 with
+// carries, moving each operand's 32-bit offset by the strides it crosses, so an
+// element costs a few integer adds instead of a mixed-radix decomposition.
+// Four elements' loads are issued before their arithmetic.
+template <int NP, bool TWO> struct EwLane {
+    int dig[kEwDims];
+    uint32_t oo, ao, so[NP], so2[NP];
+};
+
+template <int NP, bool TWO, bool ACC>
+__device__ __forceinline__ void ew_step32(const GroupedEw &d, EwLane<NP, TWO> &L) {
+    const int k0 = d.nd - 1;
+#pragma unroll
+    for (int k = 0; k < kEwDims; k++)            // static indices keep the digits in registers
+        if (k == k0) L.dig[k] += 32;
+    L.oo += 32u * (uint32_t)d.ostr[k0];
+    if (ACC && d.has_add) L.ao += 32u * (uint32_t)d.astr[k0];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        L.so[p] += 32u * (uint32_t)d.sstr[p][k0];
+        if (TWO) L.so2[p] += 32u * (uint32_t)d.sstr2[p][k0];
+    }
+    // carries from the innermost digit outwards (no early exit: the digits stay
+    // in registers)
+    bool carry = true;
+#pragma unroll
+    for (int k = kEwDims - 1; k > 0; k--) {
+        if (k > k0 || !carry) continue;
+        carry = L.dig[k] >= d.ext[k];
+        if (!carry) continue;
+        do {                                       // wrap digit k into digit k - 1
+            L.dig[k] -= d.ext[k];
+            L.dig[k - 1]++;
+            L.oo += (uint32_t)d.ostr[k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.ostr[k];
+            if (ACC && d.has_add) L.ao += (uint32_t)d.astr[k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.astr[k];
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+                L.so[p] += (uint32_t)d.sstr[p][k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.sstr[p][k];
+                if (TWO) L.so2[p] += (uint32_t)d.sstr2[p][k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.sstr2[p][k];
+            }
+        } while (L.dig[k] >= d.ext[k]);
+    }
+}
+
+template <bool ACC, int NP, bool TWO>
+__device__ __forceinline__ void ew_run(const GroupedEw &d, int64_t r0, int lane) {
+    constexpr int J = 4;
+    uint32_t e = (uint32_t)r0 + (uint32_t)lane;
+    if (e >= d.total) return;
+    EwLane<NP, TWO> L;
+    {
+        uint32_t x = e;
+        L.oo = L.ao = 0;
+#pragma unroll
+        for (int p = 0; p < NP; p++) L.so[p] = L.so2[p] = 0;
+#pragma unroll
+        for (int k = kEwDims - 1; k >= 0; k--) {
+            L.dig[k] = 0;
+            if (k >= d.nd) continue;
+            const uint32_t ex = (uint32_t)d.ext[k], q = x / ex, dg = x - q * ex;
+            x = q;
+            L.dig[k] = (int)dg;
+            L.oo += dg * (uint32_t)d.ostr[k];
+            if (ACC && d.has_add) L.ao += dg * (uint32_t)d.astr[k];
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+                L.so[p] += dg * (uint32_t)d.sstr[p][k];
+                if (TWO) L.so2[p] += dg * (uint32_t)d.sstr2[p][k];
+            }
+        }
+    }
+    const uint32_t end = (uint32_t)min((int64_t)d.total, r0 + kEwRun);
+    const bool chain = TWO && ACC && !d.as.general;
+    const bool fold = chain && !(d.as.kexp == 0 && d.as.sflip == 0);
+    for (int b = 0; b < (int)(kEwRun / (32 * J)); b++) {
+        uint32_t oo[J], ao[J], so[NP][J], so2[NP][J];
+        bool ok[J];
+#pragma unroll
+        for (int j = 0; j < J; j++) {
+            ok[j] = e < end;
+            oo[j] = L.oo;
+            ao[j] = L.ao;
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+                so[p][j] = L.so[p];
+                so2[p][j] = L.so2[p];
+            }
+            e += 32;
+            if (e < end) ew_step32<NP, TWO, ACC>(d, L);
+        }
+        double xs[NP][J], ys[NP][J], old[J];
+#pragma unroll
+        for (int p = 0; p < NP; p++)
+#pragma unroll
+            for (int j = 0; j < J; j++) {
+                const bool on = ok[j] && p < d.nterms;
+                xs[p][j] = on ? __ldg(d.src + so[p][j]) : 0.0;
+                ys[p][j] = (TWO && on) ? __ldg(d.src2 + so2[p][j]) : 0.0;
+            }
+#pragma unroll
+        for (int j = 0; j < J; j++) old[j] = (ACC && ok[j]) ? (d.has_add ? d.add[ao[j]] : d.out[oo[j]]) : 0.0;
+#pragma unroll
+        for (int j = 0; j < J; j++) {
+            if (!ok[j]) continue;
+            double acc;
+            if (chain) {
+                // start from the old value, one FMA per term, sign and alpha = +-2^k on a factor
+                acc = old[j];
+#pragma unroll
+                for (int p = 0; p < NP; p++) {
+                    if (p >= d.nterms) break;
+                    double sa = ((d.negmask >> p) & 1ull) ? neg(xs[p][j]) : xs[p][j];
+                    if (fold) sa = scale_f64(sa, d.as);
+                    acc = fma(sa, ys[p][j], acc);
+                }
+            } else {
+                acc = 0.0;
+#pragma unroll
+                for (int p = 0; p < NP; p++) {
+                    if (p >= d.nterms) break;
+                    const double t = TWO ? xs[p][j] * ys[p][j] : xs[p][j];
+                    acc = signed_term(p == 0, (d.negmask >> p) & 1ull, t, acc);
+                }
+                acc = finish<ACC>(d.as, acc, old[j]);
+            }
+            d.out[oo[j]] = acc;
+        }
+        if (e >= end) break;
+    }
+}
+
+template <bool ACC, int NP, bool TWO>
+__global__ void __launch_bounds__(256, 3) grouped_ew_kernel(const GroupedEw *__restrict__ tab, int n, int64_t total,
+                                                         const int *__restrict__ active) {
+    const int lane = threadIdx.x & 31;
+    const WorkRange wr = work_range(total, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                                    (int64_t)gridDim.x * (blockDim.x >> 5));
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedEw> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const GroupedEw &e = tab[walk.at(it)];
+        if (!active[e.sys]) { it = walk.next - 1; continue; }
+        ew_run<ACC, NP, TWO>(e, (it - e.item0) * kEwRun, lane);
     }
 }
 
@@ -351,22 +514,18 @@ __global__ void __launch_bounds__(256) accum_rows_kernel(const AccumDesc d, cons
 }
 
 // The grouped row path (real): entry e's items are [e.item0, e.item0 +
-// ceil(rows / rch) * ncb); a warp finds its item's entry by binary search.
+// ceil(rows / rch) * ncb); each warp takes a contiguous range of items.
 template <int NP, bool TWO, bool ACC>
 __global__ void __launch_bounds__(256) grouped_accum_rows_kernel(const GroupedAccum *__restrict__ tab, int n,
                                                                  int64_t total, const int *__restrict__ active) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t it = warp; it < total; it += nwarps) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const GroupedAccum &e = tab[lo];
-        if (!active[e.sys]) continue;
+    const WorkRange wr = work_range(total, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                                    (int64_t)gridDim.x * (blockDim.x >> 5));
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedAccum> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const GroupedAccum &e = tab[walk.at(it)];
+        if (!active[e.sys]) { it = walk.next - 1; continue; }
         accum_rows_item<double, NP, TWO, ACC>(e.d, e.src, e.src2, e.out, e.add, e.rows, e.rch, e.ncb,
                                               (uint64_t)(it - e.item0), lane);
     }
@@ -727,6 +886,128 @@ __global__ void __launch_bounds__(256) antisym_triple_inner_kernel(const AccumDe
     }
 }
 
+// The inner-triple antisymmetriser by tile orbits: a work item is (batch row,
+// tile multiset A <= B <= C) of 8 x 8 x 8 tiles of the n^3 cube.  The block
+// reads each term's source tile with lanes along that term's contiguous dim
+// (64-byte runs), sums the six signed terms into the representative tile in
+// shared memory (term by term, in the order of the terms), then writes the six
+// output tiles sigma(A, B, C), each with lanes along the output's contiguous
+// dim: every element a < b < c is written with its sign to its six orbit
+// members.  Each global access is a full 64-byte run, where the warp-per-pair
+// form's strided members touched one sector per element.
+constexpr int kTriTile = 8;
+
+// 3 x the position of each dim of a (distinct) stride triple in memory order,
+// fastest first: the shift of the dim's digit in a tile's linear index
+__device__ __forceinline__ void digit_shifts(const int64_t *st, int sh[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) sh[k] = 3 * ((st[(k + 1) % 3] < st[k]) + (st[(k + 2) % 3] < st[k]));
+}
+
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDesc d, const TripleSym g,
+                                                                   const T *__restrict__ src, T *__restrict__ out,
+                                                                   uint32_t ntm, uint64_t items) {
+    // output position m of orbit member q holds t[kPi[q][m]] (the six orderings of
+    // (a, b, c) as in triple_perm), with parity kOdd[q]
+    constexpr int kPi[6][3] = {{0, 1, 2}, {1, 0, 2}, {0, 2, 1}, {2, 1, 0}, {1, 2, 0}, {2, 0, 1}};
+    constexpr bool kOdd[6] = {false, true, true, true, false, false};
+    __shared__ T xs[kTriTile * kTriTile * kTriTile];
+    const int tid = threadIdx.x;
+    const int64_t n = g.n;
+    const int nt = (int)((n + kTriTile - 1) / kTriTile);
+    const uint64_t orbit_items = (uint64_t)g.nb * ntm;
+    int fs[6][3], gs[3];
+#pragma unroll
+    for (int p = 0; p < 6; p++) digit_shifts(g.S[p], fs[p]);
+    digit_shifts(g.O, gs);
+    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        if (it >= orbit_items) {
+            // store mode: zero the planes with a repeated index, row (it - orbit_items) / n, plane x
+            const uint64_t z = it - orbit_items;
+            const int64_t row = (int64_t)(z / (uint64_t)n), x = (int64_t)(z % (uint64_t)n);
+            T *o = out + row * g.ob;
+            for (int64_t y = tid; y < n; y += blockDim.x) {
+                o[x * g.O[0] + x * g.O[1] + y * g.O[2]] = zero<T>();
+                o[x * g.O[0] + y * g.O[1] + x * g.O[2]] = zero<T>();
+                o[y * g.O[0] + x * g.O[1] + x * g.O[2]] = zero<T>();
+            }
+            continue;
+        }
+        const int64_t row = (int64_t)(it / ntm);
+        int tl[3];                                  // tile multiset A <= B <= C
+        {
+            uint32_t r = (uint32_t)(it % ntm);
+            int A = 0, B = 0;
+            for (A = 0; A < nt; A++) {
+                const uint32_t cnt = (uint32_t)((nt - A) * (nt - A + 1) / 2);
+                if (r < cnt) break;
+                r -= cnt;
+            }
+            for (B = A; B < nt; B++) {
+                const uint32_t cnt = (uint32_t)(nt - B);
+                if (r < cnt) break;
+                r -= cnt;
+            }
+            tl[0] = A; tl[1] = B; tl[2] = B + (int)r;
+        }
+        const T *sr = src + row * g.sb;
+        T *orow = out + row * g.ob;
+        // every term's loads first: element l of the tile in the term's memory order
+        T w[6][2];
+        int xi[6][2];
+#pragma unroll
+        for (int p = 0; p < 6; p++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int l = tid + 256 * h;
+                int lt[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) lt[k] = (l >> fs[p][k]) & 7;
+                const int64_t t0 = tl[0] * kTriTile + lt[0], t1 = tl[1] * kTriTile + lt[1],
+                              t2 = tl[2] * kTriTile + lt[2];
+                xi[p][h] = (lt[0] * kTriTile + lt[1]) * kTriTile + lt[2];
+                w[p][h] = (t0 < n && t1 < n && t2 < n)
+                              ? cj(ld(sr + t0 * g.S[p][0] + t1 * g.S[p][1] + t2 * g.S[p][2]), d.conj_a)
+                              : zero<T>();
+            }
+        __syncthreads();                            // the previous item's reads of xs are done
+#pragma unroll
+        for (int p = 0; p < 6; p++) {
+            const bool ng = (d.negmask >> p) & 1ull;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                T &x = xs[xi[p][h]];
+                x = p == 0 ? (ng ? neg(w[p][h]) : w[p][h]) : signed_term(false, ng, w[p][h], x);
+            }
+            __syncthreads();
+        }
+        // the six output tiles, lanes along the output's contiguous dim
+#pragma unroll
+        for (int q = 0; q < 6; q++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int l = tid + 256 * h;
+                int lx[3];
+#pragma unroll
+                for (int m = 0; m < 3; m++) lx[m] = (l >> gs[m]) & 7;
+                int lt[3];
+                int64_t x[3], t[3];
+#pragma unroll
+                for (int m = 0; m < 3; m++) lt[kPi[q][m]] = lx[m];
+#pragma unroll
+                for (int k = 0; k < 3; k++) t[k] = (int64_t)tl[k] * kTriTile + lt[k];
+#pragma unroll
+                for (int m = 0; m < 3; m++) x[m] = t[kPi[q][m]];
+                if (!(t[0] < t[1] && t[1] < t[2] && t[2] < n)) continue;
+                const T X = scale_f64(xs[(lt[0] * kTriTile + lt[1]) * kTriTile + lt[2]], d.as);
+                T *op = orow + x[0] * g.O[0] + x[1] * g.O[1] + x[2] * g.O[2];
+                const T v = kOdd[q] ? neg(X) : X;
+                *op = ACC ? add(v, *op) : v;
+            }
+    }
+}
+
 // ---------------------------------------------------------------- host side
 // Drop unit dims and merge neighbours k, k+1 that are contiguous in the
 // output and in every term's source(s): the kernels then see the fewest dims
@@ -947,6 +1228,14 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
             d0, tg, src, out, (uint32_t)nms, (uint32_t)nchunk, items);
         return cudaGetLastError();
     }
+    if (match_triple_antisym(d0, tg, true) && tg.n >= 3 && tg.n <= 2048) {
+        const int64_t nt = (tg.n + kTriTile - 1) / kTriTile;
+        const int64_t ntm = nt * (nt + 1) * (nt + 2) / 6;                  // tile multisets
+        const uint64_t items = (uint64_t)tg.nb * (uint64_t)ntm + (ACC ? 0 : (uint64_t)tg.nb * (uint64_t)tg.n);
+        antisym_triple_tiles_kernel<T, ACC><<<(unsigned)grid_cap((int64_t)items, 148 * 8), 256, 0, s>>>(
+            d0, tg, src, out, (uint32_t)ntm, items);
+        return cudaGetLastError();
+    }
     if (match_triple_antisym(d0, tg, true) && tg.n <= 4096) {
         const int64_t npairs = tg.n * (tg.n - 1) / 2;
         const int64_t npair_items = (npairs + 7) / 8;
@@ -1063,6 +1352,69 @@ int64_t grouped_accum_items(const GroupedAccum &g, int mode) {
     if (mode == 1) return ((int64_t)g.rows + g.rch - 1) / g.rch * (int64_t)g.ncb;
     if (mode == 2) return (g.d.total + 127) / 128;
     return (g.d.total + 32 * kAccChunk - 1) / (32 * kAccChunk);
+}
+
+bool grouped_ew_from(const GroupedAccum &g, GroupedEw &e) {
+    const AccumDesc &d = g.d;
+    if (d.cplx || d.nd < 1 || d.nd > kEwDims || d.nperm < 1 || d.nperm > kEwTerms || d.total <= 0 ||
+        d.total >= ((int64_t)1 << 31) || d.bcase == 2)
+        return false;
+    // every operand's offsets (and a wrap's stride difference) below 2^31
+    auto fits = [&](const int64_t *str) {
+        int64_t m = 0;
+        for (int k = 0; k < d.nd; k++) {
+            if (str[k] < 0 || d.ext[k] >= ((int64_t)1 << 31)) return false;
+            m += (d.ext[k] - 1) * str[k];
+        }
+        return m < ((int64_t)1 << 30) && 32 * str[d.nd - 1] < ((int64_t)1 << 30);
+    };
+    if (!fits(d.ostr) || (d.has_add && !fits(d.astr))) return false;
+    for (int p = 0; p < d.nperm; p++)
+        if (!fits(d.sstr[p]) || (d.two_src && !fits(d.sstr2[p]))) return false;
+    e = GroupedEw{};
+    e.nd = d.nd;
+    e.nterms = d.nperm;
+    e.has_add = d.has_add;
+    e.total = (uint32_t)d.total;
+    e.negmask = d.negmask;
+    e.as = d.as;
+    for (int k = 0; k < d.nd; k++) {
+        e.ext[k] = (int)d.ext[k];
+        e.ostr[k] = (int)d.ostr[k];
+        e.astr[k] = d.has_add ? (int)d.astr[k] : 0;
+        for (int p = 0; p < d.nperm; p++) {
+            e.sstr[p][k] = (int)d.sstr[p][k];
+            e.sstr2[p][k] = d.two_src ? (int)d.sstr2[p][k] : 0;
+        }
+    }
+    e.src = g.src;
+    e.src2 = g.src2;
+    e.add = g.add;
+    e.out = g.out;
+    e.sys = g.sys;
+    return true;
+}
+
+cudaError_t launch_grouped_ew(const GroupedEw *tab, int n, int64_t total, bool acc, int nperm, bool two,
+                              const int *active, cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    if (nperm > kEwTerms || (two && nperm > 2)) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)grid_cap((total + 7) / 8, 148 * 16);
+#define CCB_EW(A, P, T) grouped_ew_kernel<A, P, T><<<blocks, 256, 0, s>>>(tab, n, total, active)
+    if (two) {
+        if (acc) { if (nperm <= 1) CCB_EW(true, 1, true); else CCB_EW(true, 2, true); }
+        else { if (nperm <= 1) CCB_EW(false, 1, true); else CCB_EW(false, 2, true); }
+    } else if (acc) {
+        if (nperm <= 1) CCB_EW(true, 1, false);
+        else if (nperm <= 2) CCB_EW(true, 2, false);
+        else CCB_EW(true, 4, false);
+    } else {
+        if (nperm <= 1) CCB_EW(false, 1, false);
+        else if (nperm <= 2) CCB_EW(false, 2, false);
+        else CCB_EW(false, 4, false);
+    }
+#undef CCB_EW
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grouped_accum(const GroupedAccum *tab, int n, int64_t total, bool acc, int mode, int nperm,

@@ -1057,15 +1057,20 @@ BatchLayout batch_layout(int n, const cc_plan *plans, int diis) {
     return B;
 }
 
+// compact elementwise tables take the space sized for GroupedAccum tables
+static_assert(sizeof(GroupedEw) <= sizeof(GroupedAccum), "grouped elementwise table size");
+
 // one launch of a grouped residual evaluation
 struct GroupedLaunch {
-    int kind = 0;                 // 0 elementwise, 1 split, 2 GEMM, 3 K-slice reduction, 4 narrow GEMM
+    int kind = 0;                 // 0 elementwise, 1 split, 2 GEMM, 3 K-slice reduction, 4 narrow GEMM,
+                                  // 5 one-column narrow GEMM (GEMV)
     bool first_only = false;      // static sources / cached planes: the first evaluation only
     int64_t off = 0;              // table offset in the grouped region
     int n = 0;                    // entries
     int64_t total = 0;            // work items of all entries
     bool flag = false;            // elementwise: accumulate; split: lanes along K
-    int mode = 0;                 // elementwise: 0 generic, 1 row path, 2 generic, four loads per lane
+    int mode = 0;                 // elementwise: 0 generic, 1 row path, 2 generic, four loads per lane,
+                                  // 3 compact entries (GroupedEw)
     bool two = false;             // elementwise: products of two sources
     int nperm = 1;
     int bn = 64;
@@ -1124,6 +1129,28 @@ cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_
             // path when it holds for every system, else the plain generic one
             bool small = true;            // 32-bit element indices
             for (int i = 0; i < n; i++) small = small && t[i].d.total < ((int64_t)1 << 31);
+            // every entry in compact form (32-bit running offsets): that kernel
+            std::vector<GroupedEw> te(n);
+            bool compact = nperm <= kEwTerms && (!s0.acc.two_src || nperm <= 2);
+            for (int i = 0; i < n && compact; i++) compact = grouped_ew_from(t[i], te[i]);
+            if (compact) {
+                for (int i = 0; i < n; i++) {
+                    te[i].item0 = items;
+                    items += (te[i].total + kEwRun - 1) / kEwRun;
+                }
+                GroupedLaunch L;
+                L.kind = 0;
+                L.first_only = s0.static_src;
+                L.n = n;
+                L.total = items;
+                L.flag = beta_case(s0.acc.beta) == 1;
+                L.mode = 3;
+                L.nperm = nperm;
+                L.two = s0.acc.two_src != 0;
+                L.off = put(te.data(), (int64_t)sizeof(GroupedEw) * n);
+                GB.launches.push_back(L);
+                continue;
+            }
             const int mode = nperm <= 2 && small ? 2 : rowp ? 1 : 0;
             for (int i = 0; i < n; i++) {
                 t[i].item0 = items;
@@ -1160,14 +1187,17 @@ cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_
                 g.sys = i;
                 nc_max = std::max(nc_max, g.d.nc);
             }
+            // one column in every system: the warp-per-row GEMV
+            bool gemv = true;
+            for (int i = 0; i < n && gemv; i++) gemv = grouped_gemv_ok(t[i]);
             const int nc = grouped_rows_nc(nc_max);
             int64_t items = 0;
             for (int i = 0; i < n; i++) {
                 t[i].item0 = items;
-                items += grouped_rows_items(t[i], nc);
+                items += gemv ? grouped_gemv_items(t[i]) : grouped_rows_items(t[i], nc);
             }
             GroupedLaunch L;
-            L.kind = 4;
+            L.kind = gemv ? 5 : 4;
             L.n = n;
             L.total = items;
             L.bn = nc;
@@ -1322,7 +1352,9 @@ cc_status grouped_residual(const GroupedBatch &GB, char *G, bool first, long lon
     const int *active = (const int *)(G + GB.active_off);
     for (const GroupedLaunch &L : GB.launches) {
         if (L.first_only && !first) continue;
-        if (L.kind == 0)
+        if (L.kind == 0 && L.mode == 3)
+            CC_CUDA(launch_grouped_ew((const GroupedEw *)(G + L.off), L.n, L.total, L.flag, L.nperm, L.two, active, s));
+        else if (L.kind == 0)
             CC_CUDA(launch_grouped_accum((const GroupedAccum *)(G + L.off), L.n, L.total, L.flag, L.mode, L.nperm,
                                          L.two, active, s));
         else if (L.kind == 1)
@@ -1332,6 +1364,8 @@ cc_status grouped_residual(const GroupedBatch &GB, char *G, bool first, long lon
                                         GB.err_flag, s));
         else if (L.kind == 4)
             CC_CUDA(launch_grouped_rows((const GroupedRows *)(G + L.off), L.n, L.total, L.bn, L.flag, active, s));
+        else if (L.kind == 5)
+            CC_CUDA(launch_grouped_gemv((const GroupedRows *)(G + L.off), L.n, L.total, L.flag, active, s));
         else
             CC_CUDA(launch_grouped_reduce((const GroupedReduce *)(G + L.off), L.n, L.total, active, s));
         launches++;

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "grouped.cuh"
 #include "kernels.h"
 #include "scalar.cuh"
 
@@ -475,23 +476,22 @@ __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kern
     }
 }
 
-// the grouped form: entry e's items follow item0, each entry's Y staged once
-// per (entry, column chunk) a block meets
+// the grouped form: entry e's items follow item0; each block takes a
+// contiguous range of items (grouped.cuh), so each entry's Y is staged once per
+// (entry, column chunk) the block meets
 template <typename CT, int NC>
 __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) grouped_rows_kernel(const GroupedRows *__restrict__ tab,
                                                                                       int n, int64_t total,
                                                                                       const int *__restrict__ active) {
     __shared__ RowsSmem<CT, NC> S;
     int64_t staged = -1;
-    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
-        }
+    const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedRows> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const int lo = walk.at(it);
         const GroupedRows &e = tab[lo];
-        if (!active[e.sys]) continue;            // block-uniform
+        if (!active[e.sys]) { it = walk.next - 1; continue; }   // block-uniform
         const int64_t rblocks = (e.d.R + 255) / 256, local = it - e.item0;
         const int cc = (int)(local / rblocks);
         rows_item<CT, NC>(e.d, e.X, e.Y, e.C, local - (int64_t)cc * rblocks, cc, S, staged, (int64_t)lo * 4096 + cc);
@@ -567,6 +567,112 @@ cudaError_t launch_grouped_rows(const GroupedRows *tab, int n, int64_t total, in
         default: return cudaErrorInvalidValue;
     }
 #undef CCB_GROUPED_ROWS_NC
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ grouped GEMV
+// Narrow GEMMs with one column (C(r) = alpha sum_k X(r, k) Y(k) + beta C(r))
+// in a grouped launch.  The thread-per-row kernel above leaves such steps with
+// a few hundred rows per system and K up to o v long, one dependent K loop per
+// thread and, where X runs along K, 32 sectors per warp load.  Here a warp
+// takes kGemvRQ consecutive rows and its lanes run along K, so the X loads
+// coalesce; it is used where X's unit stride runs along K (grouped_gemv_ok).
+// The block stages its entry's K offsets of X and the Y vector (in the
+// compute type) in shared memory once per entry.
+constexpr int kGemvRQ = 4;                   // rows per warp
+constexpr int kGemvRows = 8 * kGemvRQ;       // rows per work item (block of 8 warps)
+
+template <typename CT>
+__global__ void __launch_bounds__(256) grouped_gemv_kernel(const GroupedRows *__restrict__ tab, int n, int64_t total,
+                                                           const int *__restrict__ active) {
+    __shared__ int xko[kGemvKmax];
+    __shared__ CT ys[kGemvKmax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedRows> walk(tab, n, wr.begin);
+    int staged = -1;
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const int ei = walk.at(it);
+        const GroupedRows &e = tab[ei];
+        if (!active[e.sys]) { it = walk.next - 1; continue; }   // block-uniform
+        const RowsGemmDesc &d = e.d;
+        const int K = d.K;
+        if (ei != staged) {
+            __syncthreads();                     // the previous entry's reads are done
+            for (int k = threadIdx.x; k < K; k += blockDim.x) {
+                xko[k] = (int)grp_offset(d.xk, k);
+                ys[k] = down<CT>(__ldg(e.Y + grp_offset(d.yk, k)));   // column 0: yc(0) = 0
+            }
+            __syncthreads();
+            staged = ei;
+        }
+        const int64_t r0 = (it - e.item0) * kGemvRows + warp * kGemvRQ;
+        bool rok[kGemvRQ];
+        int64_t xo[kGemvRQ];
+#pragma unroll
+        for (int q = 0; q < kGemvRQ; q++) {
+            rok[q] = r0 + q < d.R;
+            xo[q] = rok[q] ? grp_offset32(d.xr, (uint32_t)(r0 + q)) : 0;
+        }
+        CT acc[kGemvRQ];
+#pragma unroll
+        for (int q = 0; q < kGemvRQ; q++) acc[q] = zero<CT>();
+        for (int kb = 0; kb < K; kb += 128) {
+            // every load of the batch before its products
+            double xv[4][kGemvRQ];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int k = kb + lane + 32 * u;
+                const int ko = k < K ? xko[k] : 0;
+#pragma unroll
+                for (int q = 0; q < kGemvRQ; q++) xv[u][q] = (k < K && rok[q]) ? __ldg(e.X + xo[q] + ko) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int k = kb + lane + 32 * u;
+                const CT y = k < K ? ys[k] : zero<CT>();
+#pragma unroll
+                for (int q = 0; q < kGemvRQ; q++) acc[q] = fma(down<CT>(xv[u][q]), y, acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kGemvRQ; q++)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+        if (lane < kGemvRQ) {
+            CT a = acc[0];
+#pragma unroll
+            for (int q = 1; q < kGemvRQ; q++)
+                if (lane == q) a = acc[q];
+            if (rok[lane]) {
+                double *c = e.C + grp_offset32(d.cr, (uint32_t)(r0 + lane));
+                if (d.bcase == 0) *c = epi_scale(a, d.as);
+                else if (d.red) red_add(c, epi_scale(a, d.as));
+                else *c = epi_scale(a, d.as) + *c;
+            }
+        }
+    }
+}
+
+bool grouped_gemv_ok(const GroupedRows &g) {
+    const RowsGemmDesc &d = g.d;
+    // lanes along K pay off where X's unit stride runs along K (the innermost K digit)
+    if (d.nc != 1 || d.K < 1 || d.K > kGemvKmax || d.R > 0xffffffffLL || d.bcase == 2) return false;
+    if (d.xk.nd < 1 || d.xk.str[d.xk.nd - 1] != 1) return false;
+    int64_t xmax = 0;
+    for (int k = 0; k < d.xk.nd; k++) xmax += (d.xk.ext[k] - 1) * d.xk.str[k];
+    return xmax >= 0 && xmax < ((int64_t)1 << 31);
+}
+
+int64_t grouped_gemv_items(const GroupedRows &g) { return (g.d.R + kGemvRows - 1) / kGemvRows; }
+
+cudaError_t launch_grouped_gemv(const GroupedRows *tab, int n, int64_t total, bool f32, const int *active,
+                                cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(total < 148 * 6 ? total : 148 * 6);
+    if (f32) grouped_gemv_kernel<float><<<blocks, 256, 0, s>>>(tab, n, total, active);
+    else grouped_gemv_kernel<double><<<blocks, 256, 0, s>>>(tab, n, total, active);
     return cudaGetLastError();
 }
 
@@ -1021,6 +1127,45 @@ __global__ void __launch_bounds__(256) denom_sub_kernel(int rank, int o, int v, 
     }
 }
 
+// The same update with a table in shared memory, two FP64 operations per
+// element instead of rank + 1.  Rank 2: the pair sums f_vir[a] + f_vir[b] of
+// all v^2 columns (formed once per block; the sum commutes, so D stays exactly
+// symmetric in a, b and the update keeps T2's antisymmetry bit for bit), d =
+// sum f_occ - pair[c].  Rank >= 3: per row, tab[q] = sum f_occ - sum f_vir over
+// the outer virtual digits q (all but the last), d = tab[q] - f_vir[c].
+constexpr int kDenomTab = 6144;              // doubles of the table (48 KB)
+__global__ void __launch_bounds__(256) denom_sub_tab_kernel(int rank, int o, int v, const double *fo,
+                                                            const double *fv, const double *__restrict__ t,
+                                                            double *__restrict__ r, int64_t rows, uint32_t nvt,
+                                                            int cplx) {
+    extern __shared__ double tab[];
+    const uint32_t vv = (uint32_t)v, nout = nvt / vv, ncol = nvt << cplx;
+    const bool pairs = rank == 2;
+    if (pairs) {
+        for (uint32_t c = threadIdx.x; c < nvt; c += blockDim.x) tab[c] = vir_sum_lean(2, v, fv, c);
+        __syncthreads();
+    }
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const double so = occ_sum(rank, o, fo, row);
+        const int64_t base = row * ncol;
+        if (pairs) {
+            for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+                const double d = so - tab[c >> cplx];
+                r[base + c] = fma(neg(d), t[base + c], r[base + c]);
+            }
+            continue;
+        }
+        __syncthreads();                         // the previous row's reads of tab are done
+        for (uint32_t q = threadIdx.x; q < nout; q += blockDim.x) tab[q] = so - vir_sum_lean(rank - 1, v, fv, q);
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+            const uint32_t x = c >> cplx, q = x / vv, b = x - q * vv;
+            const double d = tab[q] - fv[b];
+            r[base + c] = fma(neg(d), t[base + c], r[base + c]);
+        }
+    }
+}
+
 static void rows_cols(int rank, int o, int v, int64_t &rows, uint32_t &nvt) {
     rows = 1;
     int64_t c = 1;
@@ -1034,6 +1179,12 @@ cudaError_t launch_denom_sub(int rank, int o, int v, const double *fo, const dou
     uint32_t nvt;
     rows_cols(rank, o, v, rows, nvt);
     int64_t blocks = rows < 148 * 16 ? rows : 148 * 16;
+    const uint32_t ntab = rank == 2 ? nvt : nvt / (uint32_t)v;
+    if (rank >= 2 && ntab <= (uint32_t)kDenomTab) {
+        const size_t shm = (size_t)ntab * sizeof(double);
+        denom_sub_tab_kernel<<<(unsigned)blocks, 256, shm, s>>>(rank, o, v, fo, fv, t, r, rows, nvt, cplx ? 1 : 0);
+        return cudaGetLastError();
+    }
     denom_sub_kernel<<<(unsigned)blocks, 256, 0, s>>>(rank, o, v, fo, fv, t, r, rows, nvt, cplx ? 1 : 0);
     return cudaGetLastError();
 }
@@ -1278,15 +1429,12 @@ cudaError_t launch_reduce_partials(const double *partials, int count, double *ou
 // partials in a fixed order into scal.
 __global__ void __launch_bounds__(256) grouped_post_kernel(const GroupedPost *__restrict__ tab, int n, int64_t total,
                                                           const int *__restrict__ active) {
-    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const GroupedPost &g = tab[lo];
-        if (!active[g.sys]) continue;            // block-uniform
+    const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedPost> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const GroupedPost &g = tab[walk.at(it)];
+        if (!active[g.sys]) { it = walk.next - 1; continue; }   // block-uniform
         const int64_t c = it - g.item0;
         const uint32_t o = (uint32_t)g.o, v = (uint32_t)g.v;
         const int64_t n1 = (int64_t)o * v, n2 = n1 * n1;
@@ -1301,7 +1449,9 @@ __global__ void __launch_bounds__(256) grouped_post_kernel(const GroupedPost *__
                 s1 = fma(r, r, s1);
             } else {
                 const int64_t x = e - n1;
-                const uint32_t row = (uint32_t)(x / v), b = (uint32_t)(x - (int64_t)row * v);
+                // 32-bit division where the system's o^2 v^2 allows it (block-uniform)
+                const uint32_t row = n2 <= 0xffffffffLL ? (uint32_t)x / v : (uint32_t)(x / v);
+                const uint32_t b = (uint32_t)(x - (int64_t)row * v);
                 const uint32_t a = row % v, ij = row / v, j = ij % o, i = ij / o;
                 const double t2 = g.t2[x];
                 const double d = (g.fo[i] + g.fo[j]) - (g.fv[a] + g.fv[b]);
@@ -1346,15 +1496,12 @@ __global__ void __launch_bounds__(256) grouped_post_reduce_kernel(const GroupedP
 
 __global__ void __launch_bounds__(256) grouped_reduce_kernel(const GroupedReduce *__restrict__ tab, int n,
                                                             int64_t total, const int *__restrict__ active) {
-    for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const GroupedReduce &g = tab[lo];
-        if (!active[g.sys]) continue;
+    const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedReduce> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const GroupedReduce &g = tab[walk.at(it)];
+        if (!active[g.sys]) { it = walk.next - 1; continue; }
         const int64_t e = (it - g.item0) * 256 + threadIdx.x, mn = g.M * g.N;
         if (e >= mn) continue;
         const int64_t nn = e / g.M, m = e - nn * g.M;

@@ -317,6 +317,12 @@ int grouped_rows_nc(int nc_max);                       // the column chunk of a 
 int64_t grouped_rows_items(const GroupedRows &g, int nc);
 cudaError_t launch_grouped_rows(const GroupedRows *tab, int n, int64_t total, int nc, bool f32, const int *active,
                                 cudaStream_t s);
+// one-column narrow GEMMs (GEMVs) of a batch: warps over rows, lanes along K
+constexpr int kGemvKmax = 2048;                 // longest K (staged in shared memory)
+bool grouped_gemv_ok(const GroupedRows &g);     // prepared entry: nc = 1, K <= kGemvKmax, 32-bit X offsets
+int64_t grouped_gemv_items(const GroupedRows &g);
+cudaError_t launch_grouped_gemv(const GroupedRows *tab, int n, int64_t total, bool f32, const int *active,
+                                cudaStream_t s);
 struct GroupedReduce {              // C = alpha sum_z P[z][n][m] + beta C of one sliced GEMM
     int64_t M, N;
     int nslices;
@@ -342,6 +348,29 @@ struct GroupedAccum {               // one system's elementwise step
     int64_t item0;
     int sys;
 };
+// An elementwise step of one system in compact form (grouped launches): at
+// most kEwDims dims and kEwTerms terms, every offset below 2^31, so a lane keeps
+// 32-bit running offsets and steps them instead of decomposing each element.
+constexpr int kEwDims = 4;
+constexpr int kEwTerms = 4;
+struct GroupedEw {
+    int nd, nterms, has_add;
+    uint32_t total;                 // output elements
+    unsigned long long negmask;     // bit p: term p subtracts
+    Scale as;                       // alpha
+    int ext[kEwDims];
+    int ostr[kEwDims], astr[kEwDims];
+    int sstr[kEwTerms][kEwDims], sstr2[kEwTerms][kEwDims];
+    const double *src, *src2, *add;
+    double *out;
+    int64_t item0;
+    int sys;
+};
+constexpr int64_t kEwRun = 256;     // output elements per work item (a warp's run)
+// the compact form of a prepared entry; false when it does not fit
+bool grouped_ew_from(const GroupedAccum &g, GroupedEw &e);
+cudaError_t launch_grouped_ew(const GroupedEw *tab, int n, int64_t total, bool acc, int nperm, bool two,
+                              const int *active, cudaStream_t s);
 // the denominator update of the residuals (R -= D T, real) and the
 // partial sums of the energy and of |R1|^2, |R2|^2 of one system
 struct GroupedPost {

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "fp_bits.cuh"
+#include "grouped.cuh"
 #include "kernels.h"
 
 namespace ccb {
@@ -302,28 +303,31 @@ __global__ void __launch_bounds__(256, 5) split_tile_kernel(const SplitDesc d, c
                                       ko);
 }
 
-// The grouped form: the tiles of every entry one after the other; a block
-// finds its tile's entry by binary search over the entries' first tiles.
+// The grouped form: the tiles of every entry one after the other; each block
+// takes a contiguous range of tiles (grouped.cuh) and stages an entry's
+// descriptor in shared memory when it reaches the entry.
 template <bool LK>
 __global__ void __launch_bounds__(256, 5) grouped_split_kernel(const GroupedSplit *__restrict__ tab, int n,
                                                             int64_t total, const int *__restrict__ active) {
     __shared__ float tile[64][65];
     __shared__ int64_t ro[64], ko[64];
-    __shared__ SplitDesc sd;                   // the tile's descriptor, staged once per tile
+    __shared__ SplitDesc sd;                   // the current entry's descriptor
     static_assert(sizeof(SplitDesc) % 8 == 0 && sizeof(SplitDesc) / 8 <= 256, "descriptor staging");
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].tile0 <= t) lo = mid;
-            else hi = mid - 1;
+    const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedSplit> walk(tab, n, wr.begin);
+    int staged = -1;
+    for (int64_t t = wr.begin; t < wr.end; t++) {
+        const int ei = walk.at(t);
+        const GroupedSplit &e = tab[ei];
+        if (!active[e.sys]) { t = walk.next - 1; continue; }   // block-uniform
+        if (ei != staged) {
+            __syncthreads();                   // the previous tile's reads of sd are done
+            if (threadIdx.x < sizeof(SplitDesc) / 8)
+                reinterpret_cast<int64_t *>(&sd)[threadIdx.x] = reinterpret_cast<const int64_t *>(&e.d)[threadIdx.x];
+            __syncthreads();                   // staged: split_tile_one reads sd before its own barrier
+            staged = ei;
         }
-        const GroupedSplit &e = tab[lo];
-        if (!active[e.sys]) continue;          // block-uniform
-        __syncthreads();                       // the previous tile's reads of sd are done
-        if (threadIdx.x < sizeof(SplitDesc) / 8)
-            reinterpret_cast<int64_t *>(&sd)[threadIdx.x] = reinterpret_cast<const int64_t *>(&e.d)[threadIdx.x];
-        __syncthreads();                       // staged: split_tile_one reads sd before its own barrier
         const int64_t lt = t - e.tile0;
         split_tile_one<LK, 2, false>(sd, e.x, (__nv_bfloat16 *)e.planes, (lt % e.rtiles) * 64, (lt / e.rtiles) * 64,
                                      tile, ro, ko);
