@@ -904,6 +904,38 @@ __device__ __forceinline__ void digit_shifts(const int64_t *st, int sh[3]) {
     for (int k = 0; k < 3; k++) sh[k] = 3 * ((st[(k + 1) % 3] < st[k]) + (st[(k + 2) % 3] < st[k]));
 }
 
+// one term's tile of a work item: element l = tid + 256 h in the term's memory
+// order (digit shifts sh), read into w[h]
+template <typename T>
+__device__ __forceinline__ void tri_tile_load(const AccumDesc &d, const TripleSym &g, const T *__restrict__ sr,
+                                              const int tl[3], const int sh[3], int p, T w[2]) {
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int l = threadIdx.x + 256 * h;
+        const int64_t t0 = tl[0] * kTriTile + ((l >> sh[0]) & 7), t1 = tl[1] * kTriTile + ((l >> sh[1]) & 7),
+                      t2 = tl[2] * kTriTile + ((l >> sh[2]) & 7);
+        w[h] = (t0 < g.n && t1 < g.n && t2 < g.n)
+                   ? cj(ld(sr + t0 * g.S[p][0] + t1 * g.S[p][1] + t2 * g.S[p][2]), d.conj_a)
+                   : zero<T>();
+    }
+}
+
+// tile multiset index -> A <= B <= C
+__device__ __forceinline__ void tri_tiles(uint32_t r, int nt, int tl[3]) {
+    int A = 0, B = 0;
+    for (A = 0; A < nt; A++) {
+        const uint32_t cnt = (uint32_t)((nt - A) * (nt - A + 1) / 2);
+        if (r < cnt) break;
+        r -= cnt;
+    }
+    for (B = A; B < nt; B++) {
+        const uint32_t cnt = (uint32_t)(nt - B);
+        if (r < cnt) break;
+        r -= cnt;
+    }
+    tl[0] = A; tl[1] = B; tl[2] = B + (int)r;
+}
+
 template <typename T, bool ACC>
 __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDesc d, const TripleSym g,
                                                                    const T *__restrict__ src, T *__restrict__ out,
@@ -912,7 +944,8 @@ __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDe
     // (a, b, c) as in triple_perm), with parity kOdd[q]
     constexpr int kPi[6][3] = {{0, 1, 2}, {1, 0, 2}, {0, 2, 1}, {2, 1, 0}, {1, 2, 0}, {2, 0, 1}};
     constexpr bool kOdd[6] = {false, true, true, true, false, false};
-    __shared__ T xs[kTriTile * kTriTile * kTriTile];
+    constexpr int kT3 = kTriTile * kTriTile * kTriTile;
+    __shared__ T tiles[6][kT3];                 // the terms' tiles, canonical (a, b, c) order; X in tiles[0]
     const int tid = threadIdx.x;
     const int64_t n = g.n;
     const int nt = (int)((n + kTriTile - 1) / kTriTile);
@@ -921,90 +954,81 @@ __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDe
 #pragma unroll
     for (int p = 0; p < 6; p++) digit_shifts(g.S[p], fs[p]);
     digit_shifts(g.O, gs);
-    for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        if (it >= orbit_items) {
-            // store mode: zero the planes with a repeated index, row (it - orbit_items) / n, plane x
-            const uint64_t z = it - orbit_items;
-            const int64_t row = (int64_t)(z / (uint64_t)n), x = (int64_t)(z % (uint64_t)n);
-            T *o = out + row * g.ob;
-            for (int64_t y = tid; y < n; y += blockDim.x) {
-                o[x * g.O[0] + x * g.O[1] + y * g.O[2]] = zero<T>();
-                o[x * g.O[0] + y * g.O[1] + x * g.O[2]] = zero<T>();
-                o[y * g.O[0] + x * g.O[1] + x * g.O[2]] = zero<T>();
-            }
-            continue;
-        }
+    // the loads of the block's first orbit item, then per item: stage, issue the
+    // next item's loads, sum, write
+    T w[6][2];
+    uint64_t it = blockIdx.x;
+    int tl[3] = {0, 0, 0};
+    if (it < orbit_items) {
+        tri_tiles((uint32_t)(it % ntm), nt, tl);
+        const T *sr = src + (int64_t)(it / ntm) * g.sb;
+#pragma unroll
+        for (int p = 0; p < 6; p++) tri_tile_load(d, g, sr, tl, fs[p], p, w[p]);
+    }
+    for (; it < orbit_items; it += gridDim.x) {
         const int64_t row = (int64_t)(it / ntm);
-        int tl[3];                                  // tile multiset A <= B <= C
-        {
-            uint32_t r = (uint32_t)(it % ntm);
-            int A = 0, B = 0;
-            for (A = 0; A < nt; A++) {
-                const uint32_t cnt = (uint32_t)((nt - A) * (nt - A + 1) / 2);
-                if (r < cnt) break;
-                r -= cnt;
-            }
-            for (B = A; B < nt; B++) {
-                const uint32_t cnt = (uint32_t)(nt - B);
-                if (r < cnt) break;
-                r -= cnt;
-            }
-            tl[0] = A; tl[1] = B; tl[2] = B + (int)r;
-        }
-        const T *sr = src + row * g.sb;
-        T *orow = out + row * g.ob;
-        // every term's loads first: element l of the tile in the term's memory order
-        T w[6][2];
-        int xi[6][2];
+        const int ctl[3] = {tl[0], tl[1], tl[2]};
+        __syncthreads();                        // the previous item's reads of the tiles are done
 #pragma unroll
         for (int p = 0; p < 6; p++)
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int l = tid + 256 * h;
-                int lt[3];
-#pragma unroll
-                for (int k = 0; k < 3; k++) lt[k] = (l >> fs[p][k]) & 7;
-                const int64_t t0 = tl[0] * kTriTile + lt[0], t1 = tl[1] * kTriTile + lt[1],
-                              t2 = tl[2] * kTriTile + lt[2];
-                xi[p][h] = (lt[0] * kTriTile + lt[1]) * kTriTile + lt[2];
-                w[p][h] = (t0 < n && t1 < n && t2 < n)
-                              ? cj(ld(sr + t0 * g.S[p][0] + t1 * g.S[p][1] + t2 * g.S[p][2]), d.conj_a)
-                              : zero<T>();
+                tiles[p][((((l >> fs[p][0]) & 7) * kTriTile) + ((l >> fs[p][1]) & 7)) * kTriTile +
+                         ((l >> fs[p][2]) & 7)] = w[p][h];
             }
-        __syncthreads();                            // the previous item's reads of xs are done
+        __syncthreads();
+        const uint64_t nx = it + gridDim.x;
+        if (nx < orbit_items) {                 // in flight while this item is summed and written
+            tri_tiles((uint32_t)(nx % ntm), nt, tl);
+            const T *sr = src + (int64_t)(nx / ntm) * g.sb;
 #pragma unroll
-        for (int p = 0; p < 6; p++) {
-            const bool ng = (d.negmask >> p) & 1ull;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                T &x = xs[xi[p][h]];
-                x = p == 0 ? (ng ? neg(w[p][h]) : w[p][h]) : signed_term(false, ng, w[p][h], x);
-            }
-            __syncthreads();
+            for (int p = 0; p < 6; p++) tri_tile_load(d, g, sr, tl, fs[p], p, w[p]);
         }
+        // X = sum_p sign_p term_p, in the order of the terms, for this thread's two elements
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int l = tid + 256 * h;
+            T x = zero<T>();
+#pragma unroll
+            for (int p = 0; p < 6; p++) x = signed_term(p == 0, (d.negmask >> p) & 1ull, tiles[p][l], x);
+            tiles[0][l] = x;                    // only this thread reads or writes element l here
+        }
+        __syncthreads();
+        T *orow = out + row * g.ob;
         // the six output tiles, lanes along the output's contiguous dim
 #pragma unroll
         for (int q = 0; q < 6; q++)
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int l = tid + 256 * h;
-                int lx[3];
+                int lx[3], lt[3];
+                int64_t x[3], t[3];
 #pragma unroll
                 for (int m = 0; m < 3; m++) lx[m] = (l >> gs[m]) & 7;
-                int lt[3];
-                int64_t x[3], t[3];
 #pragma unroll
                 for (int m = 0; m < 3; m++) lt[kPi[q][m]] = lx[m];
 #pragma unroll
-                for (int k = 0; k < 3; k++) t[k] = (int64_t)tl[k] * kTriTile + lt[k];
+                for (int k = 0; k < 3; k++) t[k] = (int64_t)ctl[k] * kTriTile + lt[k];
 #pragma unroll
                 for (int m = 0; m < 3; m++) x[m] = t[kPi[q][m]];
                 if (!(t[0] < t[1] && t[1] < t[2] && t[2] < n)) continue;
-                const T X = scale_f64(xs[(lt[0] * kTriTile + lt[1]) * kTriTile + lt[2]], d.as);
+                const T X = scale_f64(tiles[0][(lt[0] * kTriTile + lt[1]) * kTriTile + lt[2]], d.as);
                 T *op = orow + x[0] * g.O[0] + x[1] * g.O[1] + x[2] * g.O[2];
                 const T v = kOdd[q] ? neg(X) : X;
                 *op = ACC ? add(v, *op) : v;
             }
+    }
+    // store mode: zero the planes with a repeated index, one (row, plane x) per item
+    for (uint64_t z = (it >= orbit_items ? it : orbit_items + blockIdx.x) - orbit_items; z < items - orbit_items;
+         z += gridDim.x) {
+        const int64_t row = (int64_t)(z / (uint64_t)n), x = (int64_t)(z % (uint64_t)n);
+        T *o = out + row * g.ob;
+        for (int64_t y = tid; y < n; y += blockDim.x) {
+            o[x * g.O[0] + x * g.O[1] + y * g.O[2]] = zero<T>();
+            o[x * g.O[0] + y * g.O[1] + x * g.O[2]] = zero<T>();
+            o[y * g.O[0] + x * g.O[1] + x * g.O[2]] = zero<T>();
+        }
     }
 }
 

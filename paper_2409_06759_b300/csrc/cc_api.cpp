@@ -1063,7 +1063,7 @@ static_assert(sizeof(GroupedEw) <= sizeof(GroupedAccum), "grouped elementwise ta
 // one launch of a grouped residual evaluation
 struct GroupedLaunch {
     int kind = 0;                 // 0 elementwise, 1 split, 2 GEMM, 3 K-slice reduction, 4 narrow GEMM,
-                                  // 5 one-column narrow GEMM (GEMV)
+                                  // 5 one-column narrow GEMM (GEMV), 6 long contiguous-K split
     bool first_only = false;      // static sources / cached planes: the first evaluation only
     int64_t off = 0;              // table offset in the grouped region
     int n = 0;                    // entries
@@ -1209,33 +1209,39 @@ cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_
         // operand splits: A then B, the entries of each lane orientation in one launch
         for (int side = 0; side < 2; side++) {
             if (side == 0 ? s0.skip_a : s0.skip_b) continue;
-            for (int lk = 0; lk < 2; lk++) {
+            // mode 0 / 1: tiles with lanes along rows / K; mode 2: long contiguous K
+            // (vector loads, (row, span) items)
+            for (int mode = 0; mode < 3; mode++) {
                 std::vector<GroupedSplit> t;
                 int64_t tiles = 0;
                 for (int i = 0; i < n; i++) {
                     const Step &st = plans[i]->plan.steps[k];
                     const SplitDesc &d = side == 0 ? st.split_a : st.split_b;
-                    if ((int)split_lanes_along_k(d) != lk) continue;
                     char *w = W + BL.base[i];
                     GroupedSplit g{};
                     g.d = d;
                     g.x = resolve(side == 0 ? st.a : st.b, &ints[i], &amps[i], &R[i], w);
                     g.planes = w + (side == 0 ? st.planes_a_off : st.planes_b_off);
                     if (!g.x) return fail(CC_ERR_INVALID_ARG, "grouped batch: an operand buffer is missing");
+                    // the (row, span) items where the vector loads apply, or where the
+                    // operand has fewer rows than a 64-row tile
+                    const int vk = grouped_split_vec_ok(d, g.x);
+                    const bool vec = vk == 2 || (vk == 1 && d.R < 64);
+                    if (vec ? mode != 2 : (int)split_lanes_along_k(d) != mode) continue;
                     const int64_t kcols = d.kend ? d.kend : d.Kp;
-                    g.rtiles = (uint32_t)((d.Rp + 63) / 64);
+                    g.rtiles = vec ? (uint32_t)(vk == 2) : (uint32_t)((d.Rp + 63) / 64);
                     g.tile0 = tiles;
                     g.sys = i;
-                    tiles += (int64_t)g.rtiles * ((kcols + 63) / 64);
+                    tiles += vec ? grouped_split_vec_items(d) : (int64_t)g.rtiles * ((kcols + 63) / 64);
                     t.push_back(g);
                 }
                 if (t.empty()) continue;
                 GroupedLaunch L;
-                L.kind = 1;
+                L.kind = mode == 2 ? 6 : 1;
                 L.first_only = side == 0 ? s0.a_static : s0.b_static;
                 L.n = (int)t.size();
                 L.total = tiles;
-                L.flag = lk == 1;
+                L.flag = mode == 1;
                 L.off = put(t.data(), (int64_t)sizeof(GroupedSplit) * (int64_t)t.size());
                 GB.launches.push_back(L);
             }
@@ -1366,6 +1372,8 @@ cc_status grouped_residual(const GroupedBatch &GB, char *G, bool first, long lon
             CC_CUDA(launch_grouped_rows((const GroupedRows *)(G + L.off), L.n, L.total, L.bn, L.flag, active, s));
         else if (L.kind == 5)
             CC_CUDA(launch_grouped_gemv((const GroupedRows *)(G + L.off), L.n, L.total, L.flag, active, s));
+        else if (L.kind == 6)
+            CC_CUDA(launch_grouped_split_vec((const GroupedSplit *)(G + L.off), L.n, L.total, active, s));
         else
             CC_CUDA(launch_grouped_reduce((const GroupedReduce *)(G + L.off), L.n, L.total, active, s));
         launches++;

@@ -389,12 +389,16 @@ __device__ __forceinline__ void rows_stage(const RowsGemmDesc &d, const double *
                                            RowsSmem<CT, NC> &S) {
     for (int e = threadIdx.x; e < 64 * NC; e += blockDim.x) {
         const int k = e / NC, c = e - k * NC;
+        // K and the column count are ints: 32-bit digit divisions
         S.ys[e] = (k0 + k < d.K && c0 + c < d.nc)
-                      ? down<CT>(__ldg(Y + grp_offset(d.yk, k0 + k) + grp_offset(d.yc, c0 + c)))
+                      ? down<CT>(__ldg(Y + grp_offset32(d.yk, (uint32_t)(k0 + k)) +
+                                       grp_offset32(d.yc, (uint32_t)(c0 + c))))
                       : zero<CT>();
     }
-    for (int k = threadIdx.x; k < 64; k += blockDim.x) S.xko[k] = k0 + k < d.K ? grp_offset(d.xk, k0 + k) : 0;
-    for (int c = threadIdx.x; c < NC; c += blockDim.x) S.cco[c] = c0 + c < d.nc ? grp_offset(d.cc, c0 + c) : 0;
+    for (int k = threadIdx.x; k < 64; k += blockDim.x)
+        S.xko[k] = k0 + k < d.K ? grp_offset32(d.xk, (uint32_t)(k0 + k)) : 0;
+    for (int c = threadIdx.x; c < NC; c += blockDim.x)
+        S.cco[c] = c0 + c < d.nc ? grp_offset32(d.cc, (uint32_t)(c0 + c)) : 0;
 }
 
 // One work item of a narrow GEMM: 256 rows (one per thread) by the column

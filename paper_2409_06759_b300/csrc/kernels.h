@@ -277,7 +277,7 @@ struct GroupedSplit {               // one operand split of one system (real, bf
     const double *x;
     void *planes;
     int64_t tile0;
-    uint32_t rtiles;
+    uint32_t rtiles;                // tiled splits: row tiles; long contiguous K: 1 = vector loads
     int sys;
 };
 struct alignas(64) GroupedGemm {    // one system's split-bf16 GEMM (accumulating or assigning)
@@ -395,6 +395,12 @@ void prepare_grouped_accum(GroupedAccum &g);
 // with four elements' loads in flight per lane (runs of 128; one or two terms)
 int64_t grouped_accum_items(const GroupedAccum &g, int mode);
 // the launches: tab (device) holds n entries; total = the work items of all
+// long contiguous-K splits of a batch (vector loads, warps over (row, span) items)
+// 0: not this path; 1: scalar loads; 2: vector loads
+int grouped_split_vec_ok(const SplitDesc &d, const double *x);
+int64_t grouped_split_vec_items(const SplitDesc &d);
+cudaError_t launch_grouped_split_vec(const GroupedSplit *tab, int n, int64_t total, const int *active,
+                                     cudaStream_t s);
 cudaError_t launch_grouped_split(const GroupedSplit *tab, int n, int64_t total, bool lk, const int *active,
                                  cudaStream_t s);
 cudaError_t launch_grouped_gemm(const GroupedGemm *tab, int n, int64_t total, int bn, const GroupedGemmParams &p,

@@ -126,49 +126,94 @@ __device__ __forceinline__ double src_at(const SplitDesc &d, const double *__res
 // columns [8l, 8l+8) of each 256-column chunk and stores 16 bytes per plane.
 // When the K group's innermost index has unit stride and every other stride
 // keeps 16-byte alignment, the eight sources are read as four double2 loads.
-__global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, const double *__restrict__ x,
-                                                         __nv_bfloat16 *__restrict__ planes, int vec) {
+// one work item (row r, 1024-column span from kspan) by one warp
+__device__ __forceinline__ void split_vec_item(const SplitDesc &d, const double *__restrict__ x,
+                                               __nv_bfloat16 *__restrict__ planes, int vec, int64_t r, int64_t kspan,
+                                               int lane) {
     const int64_t plane_elems = d.Rp * d.Kp;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * 8;
     const int64_t kcols = d.kend ? d.kend : d.Kp;       // plane columns this split fills
     const double sc = d.scaled ? d.scale : 1.0;
+    const int64_t kend = kspan + 1024 < kcols ? kspan + 1024 : kcols;
+    const bool row_ok = r < d.R;
+    const int64_t roff = row_ok ? row_offset(d, r) : 0;
+    for (int64_t k0 = kspan + (int64_t)lane * 8; k0 < kend; k0 += 256) {
+        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+        if (row_ok && vec && k0 + 7 < d.K) {
+            // real: eight consecutive doubles; stacked complex: four
+            // consecutive complex elements (re, im pairs)
+            const double2 *src = reinterpret_cast<const double2 *>(
+                x + roff + (d.cplx ? grp_off(d.gk, k0 >> 1) : grp_off(d.gk, k0)));
+            const double sy = (d.cplx && d.conj) ? -1.0 : 1.0;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const double2 v2 = __ldg(src + j);
+                split3(d.scaled ? v2.x * sc : v2.x, h[2 * j], m[2 * j], l[2 * j]);
+                const double y = d.cplx ? sy * v2.y : v2.y;
+                split3(d.scaled ? y * sc : y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
+            }
+        } else if (d.cplx == 0 && row_ok && d.gk.nd >= 1) {
+            // real, scalar loads: k0 decomposed once, then the innermost K digit
+            // stepped (a new decomposition only where the run crosses it); the
+            // eight loads are issued before their splits
+            const int64_t ein = d.gk.ext[d.gk.nd - 1], sin = d.gk.str[d.gk.nd - 1];
+            int64_t off = grp_off(d.gk, k0), dig = k0 % ein;
+            double v8[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int64_t k = k0 + j;
+                v8[j] = k < d.K ? __ldg(x + roff + off) : 0.0;
+                if (++dig == ein) {
+                    dig = 0;
+                    off = k + 1 < d.K ? grp_off(d.gk, k + 1) : 0;
+                } else {
+                    off += sin;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) split3(d.scaled ? v8[j] * sc : v8[j], h[j], m[j], l[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int64_t k = k0 + j;
+                const double val = (row_ok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
+                split3(d.scaled ? val * sc : val, h[j], m[j], l[j]);
+            }
+        }
+        __nv_bfloat16 *p0 = planes + r * d.Kp + d.kdst + k0;
+        *reinterpret_cast<uint4 *>(p0) = *reinterpret_cast<const uint4 *>(h);
+        *reinterpret_cast<uint4 *>(p0 + plane_elems) = *reinterpret_cast<const uint4 *>(m);
+        if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = *reinterpret_cast<const uint4 *>(l);
+    }
+}
+
+__global__ void __launch_bounds__(256) split_bf16_kernel(const SplitDesc d, const double *__restrict__ x,
+                                                         __nv_bfloat16 *__restrict__ planes, int vec) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    const int64_t kcols = d.kend ? d.kend : d.Kp;
     // work items: (row, 1024-column span); a warp takes one item at a time
     const int64_t spans = (kcols + 1023) / 1024;
     for (int64_t it = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); it < d.Rp * spans; it += nwarps) {
         const int64_t r = it / spans;
-        const int64_t kspan = (it - r * spans) * 1024;
-        const int64_t kend = kspan + 1024 < kcols ? kspan + 1024 : kcols;
-        const bool row_ok = r < d.R;
-        const int64_t roff = row_ok ? row_offset(d, r) : 0;
-        for (int64_t k0 = kspan + (int64_t)lane * 8; k0 < kend; k0 += 256) {
-            __align__(16) __nv_bfloat16 h[8], m[8], l[8];
-            if (row_ok && vec && k0 + 7 < d.K) {
-                // real: eight consecutive doubles; stacked complex: four
-                // consecutive complex elements (re, im pairs)
-                const double2 *src = reinterpret_cast<const double2 *>(
-                    x + roff + (d.cplx ? grp_off(d.gk, k0 >> 1) : grp_off(d.gk, k0)));
-                const double sy = (d.cplx && d.conj) ? -1.0 : 1.0;
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const double2 v2 = __ldg(src + j);
-                    split3(d.scaled ? v2.x * sc : v2.x, h[2 * j], m[2 * j], l[2 * j]);
-                    const double y = d.cplx ? sy * v2.y : v2.y;
-                    split3(d.scaled ? y * sc : y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const int64_t k = k0 + j;
-                    const double val = (row_ok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
-                    split3(d.scaled ? val * sc : val, h[j], m[j], l[j]);
-                }
-            }
-            __nv_bfloat16 *p0 = planes + r * d.Kp + d.kdst + k0;
-            *reinterpret_cast<uint4 *>(p0) = *reinterpret_cast<const uint4 *>(h);
-            *reinterpret_cast<uint4 *>(p0 + plane_elems) = *reinterpret_cast<const uint4 *>(m);
-            if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = *reinterpret_cast<const uint4 *>(l);
-        }
+        split_vec_item(d, x, planes, vec, r, (it - r * spans) * 1024, lane);
+    }
+}
+
+// The grouped form for long contiguous K: entry e's items are its (row,
+// 1024-column span) pairs from e.tile0 (e.rtiles: 1 where the entry takes the
+// vector loads); each warp takes a contiguous range of items (grouped.cuh).
+__global__ void __launch_bounds__(256) grouped_split_vec_kernel(const GroupedSplit *__restrict__ tab, int n,
+                                                                int64_t total, const int *__restrict__ active) {
+    const int lane = threadIdx.x & 31;
+    const WorkRange wr = work_range(total, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), (int64_t)gridDim.x * 8);
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedSplit> walk(tab, n, wr.begin);
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const GroupedSplit &e = tab[walk.at(it)];
+        if (!active[e.sys]) { it = walk.next - 1; continue; }
+        const int64_t kcols = e.d.kend ? e.d.kend : e.d.Kp;
+        const int64_t spans = (kcols + 1023) / 1024, local = it - e.tile0, r = local / spans;
+        split_vec_item(e.d, e.x, (__nv_bfloat16 *)e.planes, (int)e.rtiles, r, (local - r * spans) * 1024, lane);
     }
 }
 
@@ -1778,6 +1823,33 @@ bool split_lanes_along_k(const SplitDesc &d) {
     const bool r_unit = d.gr.nd >= 1 && d.gr.str[d.gr.nd - 1] == unit;
     const int64_t ks = d.gk.nd >= 1 ? d.gk.str[d.gk.nd - 1] : 0, rs = d.gr.nd >= 1 ? d.gr.str[d.gr.nd - 1] : 0;
     return k_unit || (!r_unit && ks <= rs);
+}
+
+int grouped_split_vec_ok(const SplitDesc &d, const double *x) {
+    // real, two or three planes, long K whose innermost digit is contiguous
+    if (d.cplx || d.nplanes < 2 || d.nplanes > 3 || d.K < 512 || d.gk.nd < 1 || d.gk.str[d.gk.nd - 1] != 1)
+        return 0;
+    const int64_t kcols = d.kend ? d.kend : d.Kp;
+    if (d.kdst % 8 || kcols % 8 || d.kdst + kcols > d.Kp || kcols < d.K) return 0;
+    // the vector loads (four double2 per lane): 16-byte aligned runs of eight
+    // inside the innermost digit (one digit: the tail takes the scalar loads)
+    bool vec = ((uintptr_t)x & 15) == 0 && (d.gk.nd == 1 || d.gk.ext[d.gk.nd - 1] % 8 == 0);
+    for (int q = 0; q + 1 < d.gk.nd; q++) vec = vec && d.gk.str[q] % 2 == 0;
+    for (int q = 0; q < d.gr.nd; q++) vec = vec && d.gr.str[q] % 2 == 0;
+    return vec ? 2 : 1;
+}
+
+int64_t grouped_split_vec_items(const SplitDesc &d) {
+    const int64_t kcols = d.kend ? d.kend : d.Kp;
+    return d.Rp * ((kcols + 1023) / 1024);
+}
+
+cudaError_t launch_grouped_split_vec(const GroupedSplit *tab, int n, int64_t total, const int *active,
+                                     cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((total + 7) / 8 < 148 * 16 ? (total + 7) / 8 : 148 * 16);
+    grouped_split_vec_kernel<<<blocks, 256, 0, s>>>(tab, n, total, active);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grouped_split(const GroupedSplit *tab, int n, int64_t total, bool lk, const int *active,
