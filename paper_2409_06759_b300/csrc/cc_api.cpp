@@ -1063,7 +1063,8 @@ static_assert(sizeof(GroupedEw) <= sizeof(GroupedAccum), "grouped elementwise ta
 // one launch of a grouped residual evaluation
 struct GroupedLaunch {
     int kind = 0;                 // 0 elementwise, 1 split, 2 GEMM, 3 K-slice reduction, 4 narrow GEMM,
-                                  // 5 one-column narrow GEMM (GEMV), 6 long contiguous-K split
+                                  // 5 one-column narrow GEMM (GEMV), 6 long contiguous-K split,
+                                  // 7 GEMV with X along the rows
     bool first_only = false;      // static sources / cached planes: the first evaluation only
     int64_t off = 0;              // table offset in the grouped region
     int n = 0;                    // entries
@@ -1188,16 +1189,18 @@ cc_status build_grouped(GroupedBatch &GB, int n, const cc_plan *plans, const cc_
                 nc_max = std::max(nc_max, g.d.nc);
             }
             // one column in every system: the warp-per-row GEMV
-            bool gemv = true;
+            // (lanes along K), or with X along the rows and a long K (lanes along rows)
+            bool gemv = true, gemvr = true;
             for (int i = 0; i < n && gemv; i++) gemv = grouped_gemv_ok(t[i]);
+            for (int i = 0; i < n && gemvr; i++) gemvr = !gemv && grouped_gemvr_ok(t[i]);
             const int nc = grouped_rows_nc(nc_max);
             int64_t items = 0;
             for (int i = 0; i < n; i++) {
                 t[i].item0 = items;
-                items += gemv ? grouped_gemv_items(t[i]) : grouped_rows_items(t[i], nc);
+                items += gemv ? grouped_gemv_items(t[i]) : gemvr ? grouped_gemvr_items(t[i]) : grouped_rows_items(t[i], nc);
             }
             GroupedLaunch L;
-            L.kind = gemv ? 5 : 4;
+            L.kind = gemv ? 5 : gemvr ? 7 : 4;
             L.n = n;
             L.total = items;
             L.bn = nc;
@@ -1372,6 +1375,8 @@ cc_status grouped_residual(const GroupedBatch &GB, char *G, bool first, long lon
             CC_CUDA(launch_grouped_rows((const GroupedRows *)(G + L.off), L.n, L.total, L.bn, L.flag, active, s));
         else if (L.kind == 5)
             CC_CUDA(launch_grouped_gemv((const GroupedRows *)(G + L.off), L.n, L.total, L.flag, active, s));
+        else if (L.kind == 7)
+            CC_CUDA(launch_grouped_gemvr((const GroupedRows *)(G + L.off), L.n, L.total, L.flag, active, s));
         else if (L.kind == 6)
             CC_CUDA(launch_grouped_split_vec((const GroupedSplit *)(G + L.off), L.n, L.total, active, s));
         else

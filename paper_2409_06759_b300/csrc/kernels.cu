@@ -405,7 +405,7 @@ __device__ __forceinline__ void rows_stage(const RowsGemmDesc &d, const double *
 // chunk cc (NC columns), all of K in chunks of 64 staged in shared memory.
 // `staged` (block-uniform) names the column chunk already in shared memory
 // when K fits one chunk (then Y is loaded once for many items), else -1.
-template <typename CT, int NC>
+template <typename CT, int NC, int KB = 8>
 __device__ __forceinline__ void rows_item(const RowsGemmDesc &d, const double *__restrict__ X,
                                           const double *__restrict__ Y, double *__restrict__ C, int64_t rb, int cc,
                                           RowsSmem<CT, NC> &S, int64_t &staged, int64_t key) {
@@ -427,16 +427,16 @@ __device__ __forceinline__ void rows_item(const RowsGemmDesc &d, const double *_
         const int kn = d.K - kc * 64 < 64 ? d.K - kc * 64 : 64;
         if (rok) {
             // eight loads in flight per thread before their products (ys rows past K are zero)
-            for (int k0 = 0; k0 < kn; k0 += 8) {
-                // the eight loads first: a conversion may call out on its rare path
-                double ad[8];
-                CT a[8];
+            for (int k0 = 0; k0 < kn; k0 += KB) {
+                // the KB loads first: a conversion may call out on its rare path
+                double ad[KB];
+                CT a[KB];
 #pragma unroll
-                for (int j = 0; j < 8; j++) ad[j] = k0 + j < kn ? __ldg(X + xo + S.xko[k0 + j]) : 0.0;
+                for (int j = 0; j < KB; j++) ad[j] = k0 + j < kn ? __ldg(X + xo + S.xko[k0 + j]) : 0.0;
 #pragma unroll
-                for (int j = 0; j < 8; j++) a[j] = down<CT>(ad[j]);
+                for (int j = 0; j < KB; j++) a[j] = down<CT>(ad[j]);
 #pragma unroll
-                for (int j = 0; j < 8; j++) row_fma<NC>(a[j], S.ys + (k0 + j) * NC, acc);
+                for (int j = 0; j < KB; j++) row_fma<NC>(a[j], S.ys + (k0 + j) * NC, acc);
             }
         }
     }
@@ -498,7 +498,10 @@ __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) grouped_rows_k
         if (!active[e.sys]) { it = walk.next - 1; continue; }   // block-uniform
         const int64_t rblocks = (e.d.R + 255) / 256, local = it - e.item0;
         const int cc = (int)(local / rblocks);
-        rows_item<CT, NC>(e.d, e.X, e.Y, e.C, local - (int64_t)cc * rblocks, cc, S, staged, (int64_t)lo * 4096 + cc);
+        // four loads per batch at the widest chunks: the grouped bookkeeping would
+        // otherwise push the accumulators into local memory
+        rows_item<CT, NC, (NC >= 40 ? 4 : 8)>(e.d, e.X, e.Y, e.C, local - (int64_t)cc * rblocks, cc, S, staged,
+                                            (int64_t)lo * 4096 + cc);
     }
 }
 
@@ -657,6 +660,86 @@ __global__ void __launch_bounds__(256) grouped_gemv_kernel(const GroupedRows *__
             }
         }
     }
+}
+
+// One-column narrow GEMMs whose large operand X runs along the rows (unit
+// stride in the rows' innermost digit) and whose K is long (the V_ovvv t1
+// contraction into F_ae, K = o v): a work item is 32 consecutive rows, lanes
+// along the rows (coalesced), and the block's eight warps each take one eighth
+// of K, so a row's K loop is spread over eight warps instead of one thread.
+// The eight partial sums of a row are added in warp order in shared memory.
+template <typename CT>
+__global__ void __launch_bounds__(256) grouped_gemvr_kernel(const GroupedRows *__restrict__ tab, int n, int64_t total,
+                                                            const int *__restrict__ active) {
+    __shared__ int xko[kGemvKmax];
+    __shared__ CT ys[kGemvKmax];
+    __shared__ CT part[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
+    if (wr.begin >= wr.end) return;
+    EntryWalk<GroupedRows> walk(tab, n, wr.begin);
+    int staged = -1;
+    for (int64_t it = wr.begin; it < wr.end; it++) {
+        const int ei = walk.at(it);
+        const GroupedRows &e = tab[ei];
+        if (!active[e.sys]) { it = walk.next - 1; continue; }   // block-uniform
+        const RowsGemmDesc &d = e.d;
+        const int K = d.K;
+        if (ei != staged) {
+            __syncthreads();                     // the previous entry's reads are done
+            for (int k = threadIdx.x; k < K; k += blockDim.x) {
+                xko[k] = (int)grp_offset(d.xk, k);
+                ys[k] = down<CT>(__ldg(e.Y + grp_offset(d.yk, k)));
+            }
+            __syncthreads();
+            staged = ei;
+        }
+        const int64_t r = (it - e.item0) * 32 + lane;
+        const bool rok = r < d.R;
+        const int64_t xo = rok ? grp_offset32(d.xr, (uint32_t)r) : 0;
+        const int kper = (K + 7) / 8, kb = warp * kper, ke = min(K, kb + kper);
+        CT acc = zero<CT>();
+        for (int k0 = kb; k0 < ke; k0 += 8) {
+            double xv[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) xv[j] = (rok && k0 + j < ke) ? __ldg(e.X + xo + xko[k0 + j]) : 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (k0 + j < ke) acc = fma(down<CT>(xv[j]), ys[k0 + j], acc);
+        }
+        part[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && rok) {
+            CT a = part[0][lane];
+#pragma unroll
+            for (int w = 1; w < 8; w++) a += part[w][lane];
+            double *c = e.C + grp_offset32(d.cr, (uint32_t)r);
+            if (d.bcase == 0) *c = epi_scale(a, d.as);
+            else if (d.red) red_add(c, epi_scale(a, d.as));
+            else *c = epi_scale(a, d.as) + *c;
+        }
+        __syncthreads();                         // part is reused by the next item
+    }
+}
+
+bool grouped_gemvr_ok(const GroupedRows &g) {
+    const RowsGemmDesc &d = g.d;
+    if (d.nc != 1 || d.K < 64 || d.K > kGemvKmax || d.R > 0xffffffffLL || d.bcase == 2) return false;
+    if (d.xr.nd < 1 || d.xr.str[d.xr.nd - 1] != 1) return false;
+    int64_t xmax = 0;
+    for (int k = 0; k < d.xk.nd; k++) xmax += (d.xk.ext[k] - 1) * d.xk.str[k];
+    return xmax >= 0 && xmax < ((int64_t)1 << 31);
+}
+
+int64_t grouped_gemvr_items(const GroupedRows &g) { return (g.d.R + 31) / 32; }
+
+cudaError_t launch_grouped_gemvr(const GroupedRows *tab, int n, int64_t total, bool f32, const int *active,
+                                 cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(total < 148 * 6 ? total : 148 * 6);
+    if (f32) grouped_gemvr_kernel<float><<<blocks, 256, 0, s>>>(tab, n, total, active);
+    else grouped_gemvr_kernel<double><<<blocks, 256, 0, s>>>(tab, n, total, active);
+    return cudaGetLastError();
 }
 
 bool grouped_gemv_ok(const GroupedRows &g) {

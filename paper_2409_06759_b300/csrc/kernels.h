@@ -321,6 +321,11 @@ cudaError_t launch_grouped_rows(const GroupedRows *tab, int n, int64_t total, in
 constexpr int kGemvKmax = 2048;                 // longest K (staged in shared memory)
 bool grouped_gemv_ok(const GroupedRows &g);     // prepared entry: nc = 1, K <= kGemvKmax, 32-bit X offsets
 int64_t grouped_gemv_items(const GroupedRows &g);
+// the same with X running along the rows and a long K: lanes along rows, K over the block's warps
+bool grouped_gemvr_ok(const GroupedRows &g);
+int64_t grouped_gemvr_items(const GroupedRows &g);
+cudaError_t launch_grouped_gemvr(const GroupedRows *tab, int n, int64_t total, bool f32, const int *active,
+                                 cudaStream_t s);
 cudaError_t launch_grouped_gemv(const GroupedRows *tab, int n, int64_t total, bool f32, const int *active,
                                 cudaStream_t s);
 struct GroupedReduce {              // C = alpha sum_z P[z][n][m] + beta C of one sliced GEMM
