@@ -351,7 +351,9 @@ __device__ __forceinline__ int64_t grp_offset32(const Grp &g, uint32_t x) {
 
 // resident blocks per SM the accumulators allow without spilling
 template <typename CT, int NC> constexpr int rows_min_blocks() {
-    return sizeof(CT) == 4 ? (NC <= 40 ? 3 : 2) : (NC <= 24 ? 3 : NC <= 48 ? 2 : 1);
+    // FP32: the 24- and 32-column instances need more than 85 registers with the
+    // K-contiguous path beside the row path
+    return sizeof(CT) == 4 ? ((NC <= 16 || NC == 40) ? 3 : 2) : (NC <= 24 ? 3 : NC <= 48 ? 2 : 1);
 }
 
 // acc[c] += a * y[c] over a row of NC values in shared memory (16-byte aligned),
@@ -401,6 +403,20 @@ __device__ __forceinline__ void rows_stage(const RowsGemmDesc &d, const double *
         S.cco[c] = c0 + c < d.nc ? grp_offset32(d.cc, (uint32_t)(c0 + c)) : 0;
 }
 
+// X running along K (unit stride in K's innermost digit) with rows that are
+// not contiguous: one row per thread would make every warp load touch 32
+// lines, and the L1 then spends a cycle per line.  Instead each warp reads its
+// 32 rows x 16 K with lanes along K (two rows per load instruction, two or
+// three lines), rounds to FP32 into a warp-private tile in shared memory, and
+// each thread then takes its own row from the tile (pitch 17: no bank
+// conflicts).  FP32 compute only (the tile would not fit beside FP64 Y chunks).
+struct RowsKc {
+    float tile[8][32][17];
+    int64_t xo[8][32];                  // the warp's row offsets (-1: past the last row)
+};
+template <typename CT> struct RowsKcSel { using type = char; };
+template <> struct RowsKcSel<float> { using type = RowsKc; };
+
 // One work item of a narrow GEMM: 256 rows (one per thread) by the column
 // chunk cc (NC columns), all of K in chunks of 64 staged in shared memory.
 // `staged` (block-uniform) names the column chunk already in shared memory
@@ -408,7 +424,7 @@ __device__ __forceinline__ void rows_stage(const RowsGemmDesc &d, const double *
 template <typename CT, int NC, int KB = 8>
 __device__ __forceinline__ void rows_item(const RowsGemmDesc &d, const double *__restrict__ X,
                                           const double *__restrict__ Y, double *__restrict__ C, int64_t rb, int cc,
-                                          RowsSmem<CT, NC> &S, int64_t &staged, int64_t key) {
+                                          RowsSmem<CT, NC> &S, int64_t &staged, int64_t key, void *kcp) {
     const int nkc = (d.K + 63) / 64;
     const int64_t r = rb * 256 + threadIdx.x;
     const bool rok = r < d.R;
@@ -425,6 +441,36 @@ __device__ __forceinline__ void rows_item(const RowsGemmDesc &d, const double *_
             staged = nkc == 1 ? key : -1;
         }
         const int kn = d.K - kc * 64 < 64 ? d.K - kc * 64 : 64;
+        if constexpr (sizeof(CT) == 4) {
+            if (d.kc) {
+                RowsKc &Kc = *reinterpret_cast<RowsKc *>(kcp);
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                Kc.xo[warp][lane] = rok ? xo : -1;
+                __syncwarp();
+                for (int k16 = 0; k16 < kn; k16 += 16) {
+                    const int kk = k16 + (lane & 15);
+                    const bool kok = kk < kn;
+                    const int64_t xk = kok ? S.xko[kk] : 0;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        double v[8];
+#pragma unroll
+                        for (int q = 0; q < 8; q++) {
+                            const int64_t ro = Kc.xo[warp][2 * (8 * h + q) + (lane >> 4)];
+                            v[q] = (kok && ro >= 0) ? __ldg(X + ro + xk) : 0.0;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 8; q++) Kc.tile[warp][2 * (8 * h + q) + (lane >> 4)][lane & 15] = down<CT>(v[q]);
+                    }
+                    __syncwarp();
+                    // tile columns past K hold zeros and so do the staged Y rows
+#pragma unroll
+                    for (int k = 0; k < 16; k++) row_fma<NC>(Kc.tile[warp][lane][k], S.ys + (k16 + k) * NC, acc);
+                    __syncwarp();               // the tile is refilled next
+                }
+                continue;
+            }
+        }
         if (rok) {
             // eight loads in flight per thread before their products (ys rows past K are zero)
             for (int k0 = 0; k0 < kn; k0 += KB) {
@@ -471,12 +517,13 @@ template <typename CT, int NC>
 __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) rows_gemm_kernel(const RowsGemmDesc d, const double *__restrict__ X,
                                                         const double *__restrict__ Y, double *__restrict__ C) {
     __shared__ RowsSmem<CT, NC> S;
+    __shared__ typename RowsKcSel<CT>::type KC;
     const int64_t rblocks = (d.R + 255) / 256;
     const int64_t items = rblocks * ((d.nc + NC - 1) / NC);
     int64_t staged = -1;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int cc = (int)(it / rblocks);
-        rows_item<CT, NC>(d, X, Y, C, it - (int64_t)cc * rblocks, cc, S, staged, cc);
+        rows_item<CT, NC>(d, X, Y, C, it - (int64_t)cc * rblocks, cc, S, staged, cc, &KC);
     }
 }
 
@@ -488,6 +535,7 @@ __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) grouped_rows_k
                                                                                       int n, int64_t total,
                                                                                       const int *__restrict__ active) {
     __shared__ RowsSmem<CT, NC> S;
+    __shared__ typename RowsKcSel<CT>::type KC;
     int64_t staged = -1;
     const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
     if (wr.begin >= wr.end) return;
@@ -501,7 +549,7 @@ __global__ void __launch_bounds__(256, rows_min_blocks<CT, NC>()) grouped_rows_k
         // four loads per batch at the widest chunks: the grouped bookkeeping would
         // otherwise push the accumulators into local memory
         rows_item<CT, NC, (NC >= 40 ? 4 : 8)>(e.d, e.X, e.Y, e.C, local - (int64_t)cc * rblocks, cc, S, staged,
-                                            (int64_t)lo * 4096 + cc);
+                                            (int64_t)lo * 4096 + cc, &KC);
     }
 }
 
@@ -526,9 +574,16 @@ static cudaError_t rows_t(const RowsGemmDesc &d, const double *X, const double *
     return cudaGetLastError();
 }
 
+// the K-contiguous path's test: X's unit stride in K's innermost digit, not
+// in the rows', FP32 compute
+static int rows_kc(const RowsGemmDesc &d) {
+    return d.f32 && d.xk.nd >= 1 && d.xk.str[d.xk.nd - 1] == 1 && !(d.xr.nd >= 1 && d.xr.str[d.xr.nd - 1] == 1);
+}
+
 cudaError_t launch_rows_gemm(const RowsGemmDesc &d0, const double *X, const double *Y, double *C, cudaStream_t s) {
     if (d0.R <= 0) return cudaSuccess;
     RowsGemmDesc d = d0;
+    d.kc = rows_kc(d);
     d.bcase = beta_case(d.beta);
     d.as = make_scale(d.alpha);
     if (d.nc < 1 || d.K < 1 || d.R > 0xffffffffLL) return cudaErrorInvalidValue;
@@ -541,6 +596,7 @@ cudaError_t launch_rows_gemm(const RowsGemmDesc &d0, const double *X, const doub
 }
 
 void prepare_grouped_rows(GroupedRows &g) {
+    g.d.kc = rows_kc(g.d);
     g.d.bcase = beta_case(g.d.beta);
     g.d.as = make_scale(g.d.alpha);
     // one addition per output element and launch: a reduction in L2 gives the

@@ -114,6 +114,7 @@ struct RowsGemmDesc {
     int bcase;                      // set by launch_rows_gemm from beta
     Scale as;                       // make_scale(alpha), same launcher
     int red;                        // beta = 1: add C by red.global.add.f64 (no read)
+    int kc;                         // set by the launchers: X read with lanes along K (FP32 only)
 };
 
 // Long contraction with at most 8 columns, the large operand X read in place:
