@@ -1340,7 +1340,10 @@ struct Planner {
             g.gemm.M = m_free;
             g.gemm.N = n_free;
             g.gemm.K = Kx;
-            g.gemm.f32 = use_f32 ? 1 : 0;
+            // bf16x3 plans: FP32 products here too, matrix-vector shapes included
+            // (their FP32 accumulation error sits far below the split route's
+            // 2^-16; in FP64 the narrow FP64 pipe bounds them)
+            g.gemm.f32 = (use_f32 || (plan.precision == 2 && !cplx)) ? 1 : 0;
         } else if (use_mixed) {
             // The split kernels read any strided view: no permutes on this route,
             // and the row/column orders are free.  Rows and columns follow the
@@ -1482,7 +1485,7 @@ struct Planner {
             if (!err.empty()) return false;
             d.alpha = galpha;
             d.beta = gbeta;
-            d.f32 = use_f32 ? 1 : 0;
+            d.f32 = g.gemm.f32;                  // as chosen with the route above
             g.gemm.alpha = galpha;
             g.gemm.beta = gbeta;
             g.gemm.cm = cm;
