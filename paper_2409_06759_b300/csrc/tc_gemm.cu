@@ -126,6 +126,31 @@ __device__ __forceinline__ double src_at(const SplitDesc &d, const double *__res
 // columns [8l, 8l+8) of each 256-column chunk and stores 16 bytes per plane.
 // When the K group's innermost index has unit stride and every other stride
 // keeps 16-byte alignment, the eight sources are read as four double2 loads.
+// eight FP32 values -> NPL bf16 planes (hi, mid[, lo]); the remainders are exact in FP32
+template <int NPL>
+__device__ __forceinline__ void split8(const float *f, uint4 &H, uint4 &M, uint4 &L) {
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        const float2 hf = __bfloat1622float2(h2);
+        const float r0 = f[2 * j] - hf.x, r1 = f[2 * j + 1] - hf.y;
+        const __nv_bfloat162 m2 = __floats2bfloat162_rn(r0, r1);
+        h[j] = *reinterpret_cast<const uint32_t *>(&h2);
+        m[j] = *reinterpret_cast<const uint32_t *>(&m2);
+        if (NPL == 3) {
+            const float2 mf = __bfloat1622float2(m2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+            l[j] = *reinterpret_cast<const uint32_t *>(&l2);
+        } else {
+            l[j] = 0u;
+        }
+    }
+    H = make_uint4(h[0], h[1], h[2], h[3]);
+    M = make_uint4(m[0], m[1], m[2], m[3]);
+    L = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 // one work item (row r, 1024-column span from kspan) by one warp
 __device__ __forceinline__ void split_vec_item(const SplitDesc &d, const double *__restrict__ x,
                                                __nv_bfloat16 *__restrict__ planes, int vec, int64_t r, int64_t kspan,
@@ -137,7 +162,10 @@ __device__ __forceinline__ void split_vec_item(const SplitDesc &d, const double 
     const bool row_ok = r < d.R;
     const int64_t roff = row_ok ? row_offset(d, r) : 0;
     for (int64_t k0 = kspan + (int64_t)lane * 8; k0 < kend; k0 += 256) {
-        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+        // the eight source values (loads first), then FP32 rounding on the integer
+        // pipe and two values per bf16 conversion (split8): the planes are built in
+        // registers
+        double v8[8];
         if (row_ok && vec && k0 + 7 < d.K) {
             // real: eight consecutive doubles; stacked complex: four
             // consecutive complex elements (re, im pairs)
@@ -147,17 +175,14 @@ __device__ __forceinline__ void split_vec_item(const SplitDesc &d, const double 
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const double2 v2 = __ldg(src + j);
-                split3(d.scaled ? v2.x * sc : v2.x, h[2 * j], m[2 * j], l[2 * j]);
-                const double y = d.cplx ? sy * v2.y : v2.y;
-                split3(d.scaled ? y * sc : y, h[2 * j + 1], m[2 * j + 1], l[2 * j + 1]);
+                v8[2 * j] = v2.x;
+                v8[2 * j + 1] = d.cplx ? sy * v2.y : v2.y;
             }
         } else if (d.cplx == 0 && row_ok && d.gk.nd >= 1) {
             // real, scalar loads: k0 decomposed once, then the innermost K digit
-            // stepped (a new decomposition only where the run crosses it); the
-            // eight loads are issued before their splits
+            // stepped (a new decomposition only where the run crosses it)
             const int64_t ein = d.gk.ext[d.gk.nd - 1], sin = d.gk.str[d.gk.nd - 1];
             int64_t off = grp_off(d.gk, k0), dig = k0 % ein;
-            double v8[8];
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const int64_t k = k0 + j;
@@ -169,20 +194,23 @@ __device__ __forceinline__ void split_vec_item(const SplitDesc &d, const double 
                     off += sin;
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 8; j++) split3(d.scaled ? v8[j] * sc : v8[j], h[j], m[j], l[j]);
         } else {
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const int64_t k = k0 + j;
-                const double val = (row_ok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
-                split3(d.scaled ? val * sc : val, h[j], m[j], l[j]);
+                v8[j] = (row_ok && k < d.K) ? src_at(d, x, r, roff, k) : 0.0;
             }
         }
+        float f[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) f[j] = f64_to_f32_rn(d.scaled ? v8[j] * sc : v8[j]);
+        uint4 H, M, L;
+        if (d.nplanes == 3) split8<3>(f, H, M, L);
+        else split8<2>(f, H, M, L);
         __nv_bfloat16 *p0 = planes + r * d.Kp + d.kdst + k0;
-        *reinterpret_cast<uint4 *>(p0) = *reinterpret_cast<const uint4 *>(h);
-        *reinterpret_cast<uint4 *>(p0 + plane_elems) = *reinterpret_cast<const uint4 *>(m);
-        if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = *reinterpret_cast<const uint4 *>(l);
+        *reinterpret_cast<uint4 *>(p0) = H;
+        *reinterpret_cast<uint4 *>(p0 + plane_elems) = M;
+        if (d.nplanes == 3) *reinterpret_cast<uint4 *>(p0 + 2 * plane_elems) = L;
     }
 }
 
@@ -238,31 +266,6 @@ __device__ __forceinline__ double src_tile(const SplitDesc &d, const double *__r
     const double val = __ldg(x + ro + ko + comp);
     const bool neg = (rc == 0 && kc == 1) != (d.conj && comp == 1);
     return neg ? -val : val;
-}
-
-// eight FP32 values -> NPL bf16 planes (hi, mid[, lo]); the remainders are exact in FP32
-template <int NPL>
-__device__ __forceinline__ void split8(const float *f, uint4 &H, uint4 &M, uint4 &L) {
-    uint32_t h[4], m[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-        const float2 hf = __bfloat1622float2(h2);
-        const float r0 = f[2 * j] - hf.x, r1 = f[2 * j + 1] - hf.y;
-        const __nv_bfloat162 m2 = __floats2bfloat162_rn(r0, r1);
-        h[j] = *reinterpret_cast<const uint32_t *>(&h2);
-        m[j] = *reinterpret_cast<const uint32_t *>(&m2);
-        if (NPL == 3) {
-            const float2 mf = __bfloat1622float2(m2);
-            const __nv_bfloat162 l2 = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-            l[j] = *reinterpret_cast<const uint32_t *>(&l2);
-        } else {
-            l[j] = 0u;
-        }
-    }
-    H = make_uint4(h[0], h[1], h[2], h[3]);
-    M = make_uint4(m[0], m[1], m[2], m[3]);
-    L = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // one 64 x 64 tile at (r0, k0) of a split, by the whole block (block-uniform call)
