@@ -936,6 +936,19 @@ __device__ __forceinline__ void tri_tiles(uint32_t r, int nt, int tl[3]) {
     tl[0] = A; tl[1] = B; tl[2] = B + (int)r;
 }
 
+// Tile-local offsets of a thread's elements, which do not change from item to
+// item: per term, the source offset of element l of the tile in that term's
+// memory order, and the output offset of element l in the output's memory
+// order (32-bit: the host takes this kernel for n^3 < 2^31 only).  With them
+// an interior tile triple A < B < C (every element valid) costs an add per
+// access instead of the digit arithmetic and bounds checks of the general path.
+struct TriTabs {
+    int src[6][kTriTile * kTriTile * kTriTile];
+    int dst[kTriTile * kTriTile * kTriTile];
+};
+template <typename T> struct TriTabsSel { using type = TriTabs; };
+template <> struct TriTabsSel<double2> { using type = char; };   // no room beside the complex tiles
+
 template <typename T, bool ACC>
 __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDesc d, const TripleSym g,
                                                                    const T *__restrict__ src, T *__restrict__ out,
@@ -945,7 +958,9 @@ __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDe
     constexpr int kPi[6][3] = {{0, 1, 2}, {1, 0, 2}, {0, 2, 1}, {2, 1, 0}, {1, 2, 0}, {2, 0, 1}};
     constexpr bool kOdd[6] = {false, true, true, true, false, false};
     constexpr int kT3 = kTriTile * kTriTile * kTriTile;
+    constexpr bool kTabs = sizeof(T) == 8;
     __shared__ T tiles[6][kT3];                 // the terms' tiles, canonical (a, b, c) order; X in tiles[0]
+    __shared__ typename TriTabsSel<T>::type tabs;
     const int tid = threadIdx.x;
     const int64_t n = g.n;
     const int nt = (int)((n + kTriTile - 1) / kTriTile);
@@ -954,17 +969,53 @@ __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDe
 #pragma unroll
     for (int p = 0; p < 6; p++) digit_shifts(g.S[p], fs[p]);
     digit_shifts(g.O, gs);
+    if constexpr (kTabs) {
+        TriTabs &tb = *reinterpret_cast<TriTabs *>(&tabs);
+        for (int l = tid; l < kT3; l += blockDim.x) {
+#pragma unroll
+            for (int p = 0; p < 6; p++) {
+                int64_t o = 0;
+#pragma unroll
+                for (int k = 0; k < 3; k++) o += (int64_t)((l >> fs[p][k]) & 7) * g.S[p][k];
+                tb.src[p][l] = (int)o;
+            }
+            int64_t o = 0;
+#pragma unroll
+            for (int m = 0; m < 3; m++) o += (int64_t)((l >> gs[m]) & 7) * g.O[m];
+            tb.dst[l] = (int)o;
+        }
+        __syncthreads();
+    }
+    // an interior triple of distinct tiles: every element is a valid orbit representative
+    auto interior = [&](const int t3[3]) {
+        return kTabs && t3[0] < t3[1] && t3[1] < t3[2] && (int64_t)(t3[2] + 1) * kTriTile <= n;
+    };
+    // the item's loads (element l of each term's tile in the term's memory order)
+    auto load_item = [&](uint64_t item, int t3[3], T wv[6][2]) {
+        tri_tiles((uint32_t)(item % ntm), nt, t3);
+        const T *sr = src + (int64_t)(item / ntm) * g.sb;
+        if constexpr (kTabs) {
+            if (interior(t3)) {
+                const TriTabs &tb = *reinterpret_cast<const TriTabs *>(&tabs);
+#pragma unroll
+                for (int p = 0; p < 6; p++) {
+                    const T *base = sr + (int64_t)t3[0] * kTriTile * g.S[p][0] + (int64_t)t3[1] * kTriTile * g.S[p][1] +
+                                    (int64_t)t3[2] * kTriTile * g.S[p][2];
+#pragma unroll
+                    for (int h = 0; h < 2; h++) wv[p][h] = cj(ld(base + tb.src[p][tid + 256 * h]), d.conj_a);
+                }
+                return;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 6; p++) tri_tile_load(d, g, sr, t3, fs[p], p, wv[p]);
+    };
     // the loads of the block's first orbit item, then per item: stage, issue the
     // next item's loads, sum, write
     T w[6][2];
     uint64_t it = blockIdx.x;
     int tl[3] = {0, 0, 0};
-    if (it < orbit_items) {
-        tri_tiles((uint32_t)(it % ntm), nt, tl);
-        const T *sr = src + (int64_t)(it / ntm) * g.sb;
-#pragma unroll
-        for (int p = 0; p < 6; p++) tri_tile_load(d, g, sr, tl, fs[p], p, w[p]);
-    }
+    if (it < orbit_items) load_item(it, tl, w);
     for (; it < orbit_items; it += gridDim.x) {
         const int64_t row = (int64_t)(it / ntm);
         const int ctl[3] = {tl[0], tl[1], tl[2]};
@@ -979,12 +1030,7 @@ __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDe
             }
         __syncthreads();
         const uint64_t nx = it + gridDim.x;
-        if (nx < orbit_items) {                 // in flight while this item is summed and written
-            tri_tiles((uint32_t)(nx % ntm), nt, tl);
-            const T *sr = src + (int64_t)(nx / ntm) * g.sb;
-#pragma unroll
-            for (int p = 0; p < 6; p++) tri_tile_load(d, g, sr, tl, fs[p], p, w[p]);
-        }
+        if (nx < orbit_items) load_item(nx, tl, w);   // in flight while this item is summed and written
         // X = sum_p sign_p term_p, in the order of the terms, for this thread's two elements
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -996,32 +1042,44 @@ __global__ void __launch_bounds__(256) antisym_triple_tiles_kernel(const AccumDe
         }
         __syncthreads();
         T *orow = out + row * g.ob;
+        const bool fast = interior(ctl);
         // the six output tiles, lanes along the output's contiguous dim
 #pragma unroll
-        for (int q = 0; q < 6; q++)
+        for (int q = 0; q < 6; q++) {
+            T *obase = orow;
+            if (fast) {
+#pragma unroll
+                for (int m = 0; m < 3; m++) obase += (int64_t)ctl[kPi[q][m]] * kTriTile * g.O[m];
+            }
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int l = tid + 256 * h;
                 int lx[3], lt[3];
-                int64_t x[3], t[3];
 #pragma unroll
                 for (int m = 0; m < 3; m++) lx[m] = (l >> gs[m]) & 7;
 #pragma unroll
                 for (int m = 0; m < 3; m++) lt[kPi[q][m]] = lx[m];
+                T *op;
+                if (fast) {
+                    if constexpr (kTabs) op = obase + reinterpret_cast<const TriTabs *>(&tabs)->dst[l];
+                    else op = nullptr;
+                } else {
+                    int64_t x[3], t[3];
 #pragma unroll
-                for (int k = 0; k < 3; k++) t[k] = (int64_t)ctl[k] * kTriTile + lt[k];
+                    for (int k = 0; k < 3; k++) t[k] = (int64_t)ctl[k] * kTriTile + lt[k];
 #pragma unroll
-                for (int m = 0; m < 3; m++) x[m] = t[kPi[q][m]];
-                if (!(t[0] < t[1] && t[1] < t[2] && t[2] < n)) continue;
+                    for (int m = 0; m < 3; m++) x[m] = t[kPi[q][m]];
+                    if (!(t[0] < t[1] && t[1] < t[2] && t[2] < n)) continue;
+                    op = orow + x[0] * g.O[0] + x[1] * g.O[1] + x[2] * g.O[2];
+                }
                 const T X = scale_f64(tiles[0][(lt[0] * kTriTile + lt[1]) * kTriTile + lt[2]], d.as);
-                T *op = orow + x[0] * g.O[0] + x[1] * g.O[1] + x[2] * g.O[2];
                 const T v = kOdd[q] ? neg(X) : X;
                 *op = ACC ? add(v, *op) : v;
             }
+        }
     }
     // store mode: zero the planes with a repeated index, one (row, plane x) per item
-    for (uint64_t z = (it >= orbit_items ? it : orbit_items + blockIdx.x) - orbit_items; z < items - orbit_items;
-         z += gridDim.x) {
+    for (uint64_t z = it - orbit_items; z < items - orbit_items; z += gridDim.x) {
         const int64_t row = (int64_t)(z / (uint64_t)n), x = (int64_t)(z % (uint64_t)n);
         T *o = out + row * g.ob;
         for (int64_t y = tid; y < n; y += blockDim.x) {
@@ -1252,7 +1310,16 @@ static cudaError_t accum_t(const AccumDesc &d0, const T *src, T *out, cudaStream
             d0, tg, src, out, (uint32_t)nms, (uint32_t)nchunk, items);
         return cudaGetLastError();
     }
-    if (match_triple_antisym(d0, tg, true) && tg.n >= 3 && tg.n <= 2048) {
+    // tile-local offsets (at most 7 per dim times a stride) kept in 32 bits
+    auto small_strides = [](const TripleSym &t) {
+        for (int k = 0; k < 3; k++) {
+            if (t.O[k] < 0 || t.O[k] >= ((int64_t)1 << 27)) return false;
+            for (int p = 0; p < 6; p++)
+                if (t.S[p][k] < 0 || t.S[p][k] >= ((int64_t)1 << 27)) return false;
+        }
+        return true;
+    };
+    if (match_triple_antisym(d0, tg, true) && tg.n >= 3 && tg.n <= 1024 && small_strides(tg)) {
         const int64_t nt = (tg.n + kTriTile - 1) / kTriTile;
         const int64_t ntm = nt * (nt + 1) * (nt + 2) / 6;                  // tile multisets
         const uint64_t items = (uint64_t)tg.nb * (uint64_t)ntm + (ACC ? 0 : (uint64_t)tg.nb * (uint64_t)tg.n);
