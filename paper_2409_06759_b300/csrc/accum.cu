@@ -235,15 +235,16 @@ __device__ __forceinline__ void ew_step32(const GroupedEw &d, EwLane<NP, TWO> &L
 #pragma unroll
     for (int k = 0; k < kEwDims; k++)            // static indices keep the digits in registers
         if (k == k0) L.dig[k] += 32;
-    L.oo += 32u * (uint32_t)d.ostr[k0];
-    if (ACC && d.has_add) L.ao += 32u * (uint32_t)d.astr[k0];
+    // the 32-element step of the innermost digit (deltas precomputed on the host)
+    L.oo += (uint32_t)d.wo[0];
+    if (ACC && d.has_add) L.ao += (uint32_t)d.wa[0];
 #pragma unroll
     for (int p = 0; p < NP; p++) {
-        L.so[p] += 32u * (uint32_t)d.sstr[p][k0];
-        if (TWO) L.so2[p] += 32u * (uint32_t)d.sstr2[p][k0];
+        L.so[p] += (uint32_t)d.ws[p][0];
+        if (TWO) L.so2[p] += (uint32_t)d.ws2[p][0];
     }
     // carries from the innermost digit outwards (no early exit: the digits stay
-    // in registers)
+    // in registers); each wrap adds its precomputed offset changes
     bool carry = true;
 #pragma unroll
     for (int k = kEwDims - 1; k > 0; k--) {
@@ -253,12 +254,12 @@ __device__ __forceinline__ void ew_step32(const GroupedEw &d, EwLane<NP, TWO> &L
         do {                                       // wrap digit k into digit k - 1
             L.dig[k] -= d.ext[k];
             L.dig[k - 1]++;
-            L.oo += (uint32_t)d.ostr[k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.ostr[k];
-            if (ACC && d.has_add) L.ao += (uint32_t)d.astr[k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.astr[k];
+            L.oo += (uint32_t)d.wo[k];
+            if (ACC && d.has_add) L.ao += (uint32_t)d.wa[k];
 #pragma unroll
             for (int p = 0; p < NP; p++) {
-                L.so[p] += (uint32_t)d.sstr[p][k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.sstr[p][k];
-                if (TWO) L.so2[p] += (uint32_t)d.sstr2[p][k - 1] - (uint32_t)d.ext[k] * (uint32_t)d.sstr2[p][k];
+                L.so[p] += (uint32_t)d.ws[p][k];
+                if (TWO) L.so2[p] += (uint32_t)d.ws2[p][k];
             }
         } while (L.dig[k] >= d.ext[k]);
     }
@@ -1477,6 +1478,19 @@ bool grouped_ew_from(const GroupedAccum &g, GroupedEw &e) {
             e.sstr[p][k] = (int)d.sstr[p][k];
             e.sstr2[p][k] = d.two_src ? (int)d.sstr2[p][k] : 0;
         }
+    }
+    // the offset deltas of the digit steps: [0] the 32-element step of the
+    // innermost digit, [k >= 1] a wrap of digit k into digit k - 1
+    const int k0 = e.nd - 1;
+    auto deltas = [&](const int *str, int *w) {
+        w[0] = 32 * str[k0];
+        for (int k = 1; k < e.nd; k++) w[k] = str[k - 1] - e.ext[k] * str[k];
+    };
+    deltas(e.ostr, e.wo);
+    deltas(e.astr, e.wa);
+    for (int p = 0; p < e.nterms; p++) {
+        deltas(e.sstr[p], e.ws[p]);
+        deltas(e.sstr2[p], e.ws2[p]);
     }
     e.src = g.src;
     e.src2 = g.src2;

@@ -367,6 +367,9 @@ struct GroupedEw {
     int ext[kEwDims];
     int ostr[kEwDims], astr[kEwDims];
     int sstr[kEwTerms][kEwDims], sstr2[kEwTerms][kEwDims];
+    // the offset change when digit k wraps into digit k - 1 (str[k-1] - ext[k] str[k], k >= 1),
+    // and at k = 0 the change of a 32-element step of the innermost digit (32 str[nd-1])
+    int wo[kEwDims], wa[kEwDims], ws[kEwTerms][kEwDims], ws2[kEwTerms][kEwDims];
     const double *src, *src2, *add;
     double *out;
     int64_t item0;
