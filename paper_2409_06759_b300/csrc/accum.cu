@@ -355,14 +355,28 @@ __device__ __forceinline__ void ew_run(const GroupedEw &d, int64_t r0, int lane)
 template <bool ACC, int NP, bool TWO>
 __global__ void __launch_bounds__(256, 3) grouped_ew_kernel(const GroupedEw *__restrict__ tab, int n, int64_t total,
                                                          const int *__restrict__ active) {
-    const int lane = threadIdx.x & 31;
-    const WorkRange wr = work_range(total, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+    // each warp keeps its current entry in shared memory: the lanes re-read its
+    // fields at every step, and shared loads return sooner than L1 hits
+    static_assert(sizeof(GroupedEw) % 16 == 0, "entry staging");
+    __shared__ GroupedEw sd[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const WorkRange wr = work_range(total, (int64_t)blockIdx.x * (blockDim.x >> 5) + warp,
                                     (int64_t)gridDim.x * (blockDim.x >> 5));
     if (wr.begin >= wr.end) return;
     EntryWalk<GroupedEw> walk(tab, n, wr.begin);
+    int staged = -1;
     for (int64_t it = wr.begin; it < wr.end; it++) {
-        const GroupedEw &e = tab[walk.at(it)];
-        if (!active[e.sys]) { it = walk.next - 1; continue; }
+        const int ei = walk.at(it);
+        if (!active[tab[ei].sys]) { it = walk.next - 1; continue; }
+        if (ei != staged) {
+            __syncwarp();                        // the lanes are done with the previous entry
+            const int4 *src4 = reinterpret_cast<const int4 *>(tab + ei);
+            int4 *dst4 = reinterpret_cast<int4 *>(&sd[warp]);
+            for (int q = lane; q < (int)(sizeof(GroupedEw) / 16); q += 32) dst4[q] = src4[q];
+            __syncwarp();
+            staged = ei;
+        }
+        const GroupedEw &e = sd[warp];
         ew_run<ACC, NP, TWO>(e, (it - e.item0) * kEwRun, lane);
     }
 }
