@@ -1572,6 +1572,7 @@ cudaError_t launch_reduce_partials(const double *partials, int count, double *ou
 // partials in a fixed order into scal.
 __global__ void __launch_bounds__(256) grouped_post_kernel(const GroupedPost *__restrict__ tab, int n, int64_t total,
                                                           const int *__restrict__ active) {
+    const Scale kTwo = {0, 1, 0u, 2.0};
     const WorkRange wr = work_range(total, blockIdx.x, gridDim.x);
     if (wr.begin >= wr.end) return;
     EntryWalk<GroupedPost> walk(tab, n, wr.begin);
@@ -1601,7 +1602,9 @@ __global__ void __launch_bounds__(256) grouped_post_kernel(const GroupedPost *__
                 const double r = fma(neg(d), t2, g.r2[x]);
                 g.r2[x] = r;
                 s2 = fma(r, r, s2);
-                const double tt = g.t1 ? fma(2.0 * g.t1[(int64_t)i * v + a], g.t1[(int64_t)j * v + b], t2) : t2;
+                // 2 t1_ia by the exponent field (exact, no FP64 instruction)
+                const double tt =
+                    g.t1 ? fma(scale_f64(g.t1[(int64_t)i * v + a], kTwo), g.t1[(int64_t)j * v + b], t2) : t2;
                 se = fma(g.oovv[x], tt, se);
             }
         }
